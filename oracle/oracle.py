@@ -1,0 +1,199 @@
+"""ctypes front-end of the FP64 CPU oracle (test infrastructure only).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It compiles ``hweno_oracle.c`` with gcc
+(no FMA contraction, OpenMP over cells) into ``liboracle.so`` beside it.
+
+States are numpy float64 arrays of shape (12, ny, nx): plane 4*m + v holds
+moment m (0 = cell average, 1 = scaled xi-moment, 2 = scaled eta-moment) of
+conserved variable v (rho, rho*u, rho*v, E).
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hweno_oracle.c")
+_HDR = os.path.join(_HERE, "oracle_tables.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3}
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
+                ("bc", ctypes.c_int * 4),
+                ("cfl", ctypes.c_double), ("b_visc", ctypes.c_double),
+                ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
+                ("max_halvings", ctypes.c_int), ("linear_weights", ctypes.c_int),
+                ("limiter", ctypes.c_int), ("pad_", ctypes.c_int)]
+
+
+def build(force=False):
+    """Compile the oracle shared library if it is missing or stale."""
+    stale = (not os.path.exists(_LIB) or
+             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+               "-std=c11", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.or_residual.argtypes = [ctypes.POINTER(_Cfg), dp, dp, dp, dp, dp, dp, dp, dp, dp]
+            lib.or_residual_cells.argtypes = [ctypes.POINTER(_Cfg), dp, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), dp, dp]
+            lib.or_step.argtypes = [ctypes.POINTER(_Cfg), dp, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, dp]
+            lib.or_advance.argtypes = [ctypes.POINTER(_Cfg), dp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, dp]
+            lib.or_fill_ghosts.argtypes = [ctypes.POINTER(_Cfg), dp, dp]
+            lib.or_hweno_scalar.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp]
+            lib.or_theta_root_export.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double]
+            lib.or_theta_root_export.restype = ctypes.c_double
+            lib.or_eigen_export.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp, dp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_cfg(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
+             bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
+             max_halvings=20, linear_weights=False, limiter=True, **_ignored):
+    c = _Cfg()
+    c.nx, c.ny = int(nx), int(ny)
+    c.x0, c.x1, c.y0, c.y1 = float(x0), float(x1), float(y0), float(y1)
+    c.gamma, c.Pr, c.Re = float(gamma), float(Pr), float(Re)
+    for k in range(4):
+        c.bc[k] = BC[bc[k]] if isinstance(bc[k], str) else int(bc[k])
+    c.cfl, c.b_visc, c.eps_pp, c.eps_weno = float(cfl), float(b_visc), float(eps_pp), float(eps_weno)
+    c.max_halvings = int(max_halvings)
+    c.linear_weights = 1 if linear_weights else 0
+    c.limiter = 1 if limiter else 0
+    mirror = any(c.bc[k] != 0 for k in range(4))
+    if mirror and (c.nx < 4 or c.ny < 4):
+        raise ValueError("mirror boundaries need at least 4 cells per direction")
+    if (c.bc[0] == 0) != (c.bc[1] == 0) or (c.bc[2] == 0) != (c.bc[3] == 0):
+        raise ValueError("periodic boundaries must be set on both sides")
+    return c
+
+
+def _state(cfg, q):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if q.shape != (12, cfg.ny, cfg.nx):
+        raise ValueError(f"state shape {q.shape} != (12, {cfg.ny}, {cfg.nx})")
+    return q
+
+
+def residual(cfg, q, dumps=False):
+    """Spatial operator: returns dict(rhs (12,ny,nx), vhat (8,ny,nx), diag) and,
+    with dumps, the intermediate fields face (48,..), vol (36,..), rm (18,..),
+    grad (126,..), theta (2,..)."""
+    lib = _load()
+    q = _state(cfg, q)
+    ny, nx = cfg.ny, cfg.nx
+    out = {"rhs": np.zeros((12, ny, nx)), "vhat": np.zeros((8, ny, nx)), "diag": np.zeros(8)}
+    d = {}
+    if dumps:
+        d = {"face": np.zeros((48, ny, nx)), "vol": np.zeros((36, ny, nx)),
+             "rm": np.zeros((18, ny, nx)), "grad": np.zeros((126, ny, nx)),
+             "theta": np.zeros((2, ny, nx))}
+    rc = lib.or_residual(ctypes.byref(cfg), _ptr(q), _ptr(out["rhs"]), _ptr(out["vhat"]),
+                         _ptr(out["diag"]), _ptr(d.get("face")), _ptr(d.get("vol")),
+                         _ptr(d.get("rm")), _ptr(d.get("grad")), _ptr(d.get("theta")))
+    if rc:
+        raise MemoryError("oracle residual failed")
+    out.update(d)
+    return out
+
+
+def residual_cells(cfg, q, ci, cj):
+    """Residual of selected cells: returns rhs (n,12), vhat (n,8)."""
+    lib = _load()
+    q = _state(cfg, q)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    cj = np.ascontiguousarray(cj, dtype=np.int32)
+    n = len(ci)
+    rhs, vh = np.zeros((n, 12)), np.zeros((n, 8))
+    rc = lib.or_residual_cells(ctypes.byref(cfg), _ptr(q), n,
+                               ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               cj.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(rhs), _ptr(vh))
+    if rc:
+        raise MemoryError("oracle residual_cells failed")
+    return rhs, vh
+
+
+def step(cfg, q, t=0.0, t_end=np.inf, dt_fixed=0.0):
+    """One SSP-RK3 step; returns (q_new, stats dict)."""
+    lib = _load()
+    q = _state(cfg, q).copy()
+    st = np.zeros(6)
+    lib.or_step(ctypes.byref(cfg), _ptr(q), float(t), float(t_end), float(dt_fixed), _ptr(st))
+    return q, {"dt": st[0], "rejections": int(st[1]), "alpha": st[2], "beta_max": st[3],
+               "pp_active": st[4], "status": int(st[5])}
+
+
+def advance(cfg, q, t0, t_end, max_steps=10 ** 9):
+    lib = _load()
+    q = _state(cfg, q).copy()
+    st = np.zeros(10)
+    lib.or_advance(ctypes.byref(cfg), _ptr(q), float(t0), float(t_end), int(max_steps), _ptr(st))
+    return q, {"dt": st[0], "status": int(st[5]), "t": st[6], "steps": int(st[7]),
+               "rejections": int(st[8]), "pp_active": st[9]}
+
+
+def fill_ghosts(cfg, q):
+    lib = _load()
+    q = _state(cfg, q)
+    out = np.zeros((12, cfg.ny + 8, cfg.nx + 8))
+    lib.or_fill_ghosts(ctypes.byref(cfg), _ptr(q), _ptr(out))
+    return out
+
+
+def hweno_scalar(d17, eps=1e-8, linear=False):
+    """One scalar reconstruction: dict(pts (21,), mom (2,), beta (5,), omega (5,), c0 (15,))."""
+    lib = _load()
+    d17 = np.ascontiguousarray(d17, dtype=np.float64)
+    assert d17.shape == (17,)
+    o = {"pts": np.zeros(21), "mom": np.zeros(2), "beta": np.zeros(5), "omega": np.zeros(5),
+         "c0": np.zeros(15)}
+    lib.or_hweno_scalar(_ptr(d17), float(eps), 1 if linear else 0, _ptr(o["pts"]), _ptr(o["mom"]),
+                        _ptr(o["beta"]), _ptr(o["omega"]), _ptr(o["c0"]))
+    return o
+
+
+def theta_root(ub, uq, eps, gamma):
+    lib = _load()
+    ub = np.ascontiguousarray(ub, dtype=np.float64)
+    uq = np.ascontiguousarray(uq, dtype=np.float64)
+    return lib.or_theta_root_export(_ptr(ub), _ptr(uq), float(eps), float(gamma))
+
+
+def eigen(ub, gamma, direction):
+    lib = _load()
+    ub = np.ascontiguousarray(ub, dtype=np.float64)
+    L, R = np.zeros((4, 4)), np.zeros((4, 4))
+    lib.or_eigen_export(_ptr(ub), float(gamma), int(direction), _ptr(L), _ptr(R))
+    return L, R
