@@ -1,0 +1,326 @@
+"""Benchmark: HWENO-GR SSP-RK3 time steps on the viscous shock tube (1024 x 512).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hweno|reference]
+
+A step is one SSP-RK3 time step (three evaluations of the spatial operator, three
+stage updates, the time-step rule and the admissibility check) of the 1024 x 512
+viscous shock-tube workload (no-slip walls, symmetry plane, Re 1000, Pr 0.73).
+The metric is Gcell-RK-stage/s = cells x stages / seconds, summed over ranks.
+
+  value     device-resident state, CUDA-event time of K steps (FP64 path)
+  e2e       the same steps through the C ABI with host buffers: each step loads
+            the state from pinned host memory and reads the new state back
+  mixed     the FP32-reconstruction path on the same steps, with its L1 error
+            against the FP64 path after the K steps
+  roofline  the dominant kernel's algorithmic FP64 flops per launch / its mean
+            event-timed duration, against the FP64 FMA peak measured live
+  cpu_baseline  the FP64 CPU oracle on the host cores, one SSP-RK3 step of the
+            same workload (rank 0, N = 1 only)
+
+--impl reference times the CPU oracle (the only other implementation of the
+method) on a bounded 256 x 128 version of the workload per step.
+
+Multi-GPU: independent replicas, one per rank (torchrun), no collective in the
+data path; the barrier and max-over-ranks timing use torch.distributed.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-RK-stage/s"
+WORKLOAD = "viscous shock tube 1024x512, no-slip walls + symmetry, Re 1000, Pr 0.73, SSP-RK3 under the CFL/viscous step rule"
+
+# Algorithmic FP64 flops per interior cell of one launch of each spatial-operator
+# kernel (an FMA counts 2, a division or square root counts 1), counted from the
+# kernels' arithmetic; the halo ring the launch also processes is not counted.
+FLOPS_PER_CELL_FP64 = {
+    "cons_recon": None,   # filled from the op count, see profiles/
+    "grad_recon": None,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hweno", choices=["hweno", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=512)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running"""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_step_rate(case, q, steps=1):
+    """FP64 CPU oracle: cell-stages per second over `steps` SSP-RK3 steps."""
+    from oracle import oracle as O
+    cfg = O.make_cfg(**case.params())
+    O.build()
+    t0 = time.perf_counter()
+    qq = q
+    for _ in range(steps):
+        qq, st = O.step(cfg, qq)
+    el = time.perf_counter() - t0
+    return case.nx * case.ny * 3.0 * steps / el, el
+
+
+def cpu_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    from paper_2608_10569_b300 import inputs as I
+    case, q = I.shock_tube(256, 128)
+    from oracle import oracle as O
+    O.build()
+    cfg = O.make_cfg(**case.params())
+    qq = q
+    for _ in range(args.warmup):
+        qq, _ = O.step(cfg, qq)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        qq, _ = O.step(cfg, qq)
+    el = time.perf_counter() - t0
+    val = case.nx * case.ny * 3.0 * args.steps / el / 1e9
+    sample = "each step: one SSP-RK3 step of the shock tube at 256x128 (1/16 of the cells)"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "256x128"},
+            "cpu_baseline": {"value": val, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2608_10569_b300 import hweno, inputs as I
+
+    case, q = I.shock_tube(args.nx, args.ny)
+    cells = case.nx * case.ny
+    stream = torch.cuda.current_stream()
+    qd = torch.from_numpy(q).cuda()
+
+    # ---- FP64 path, device-resident ------------------------------------------------
+    s = hweno.Solver(case.params(), precision="fp64", stream=stream)
+    s.set_state(qd)
+    for _ in range(args.warmup):
+        s.step()
+    peak64 = s.measure_peak(0)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    s.profile(True)
+    n0 = s.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    rejected = 0
+    for _ in range(args.steps):
+        _, rej = s.step()
+        rejected += rej
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = s.launch_count() - n0
+    clk = clocks.stop()
+    prof = s.profile_read()
+    s.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ws, ms)
+    stages = 3.0 * args.steps
+    value = ws * cells * stages / (ms_max * 1e-3) / 1e9
+    q_fp64 = s.get_state().cpu().numpy()
+    t_reached = s.diag()["t"]
+
+    # dominant kernel of the operator and its roofline against the FP64 FMA peak
+    dom = max((k for k in prof if k != "rk_update"), key=lambda k: prof[k][1])
+    n_l, tot_ms = prof[dom]
+    fpc = FLOPS_PER_CELL_FP64.get(dom)
+    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak64,
+            "peak_source": "measured FP64 FMA peak (hweno_measure_peak, this run)",
+            "launches": n_l, "mean_launch_ms": tot_ms / max(n_l, 1),
+            "share_of_step": tot_ms / ms if ms > 0 else None, "traffic": None}
+    if fpc:
+        achieved = fpc * cells / (tot_ms / n_l * 1e-3) / 1e12
+        roof.update({"achieved": achieved, "frac": achieved / peak64, "flops_per_cell": fpc})
+    else:
+        roof.update({"achieved": None, "frac": None, "flops_per_cell": None})
+    kernel_ms = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
+
+    # ---- end to end through the C ABI with host buffers ---------------------------
+    e2e = None
+    hq = torch.from_numpy(q.copy()).pin_memory()
+    hout = torch.empty_like(hq).pin_memory()
+    s.set_state(hq)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_state(hq)
+        s.step()
+        s.get_state(hout)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    el = max_over_ranks(ws, el)
+    nbytes = q.nbytes
+    e2e = {"value": ws * cells * stages / el / 1e9, "unit": METRIC, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+    s.close()
+
+    # ---- mixed precision on the same steps ----------------------------------------
+    mixed = None
+    if not args.no_mixed:
+        m = hweno.Solver(case.params(), precision="mixed", stream=stream)
+        m.set_state(qd)
+        for _ in range(args.warmup):
+            m.step()
+        peak32 = m.measure_peak(1)
+        m.set_state(qd)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            m.step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        mms = max_over_ranks(ws, ev0.elapsed_time(ev1))
+        qm = m.get_state().cpu().numpy()
+        # L1 error against the FP64 path after the same number of steps from the same state
+        # (the FP64 path matches the FP64 oracle to round-off)
+        s64 = hweno.Solver(case.params(), precision="fp64", stream=stream)
+        s64.set_state(qd)
+        for _ in range(args.steps):
+            s64.step()
+        q64 = s64.get_state().cpu().numpy()
+        s64.close()
+        l1 = float(np.abs(qm[0] - q64[0]).sum() / np.abs(q64[0]).sum())
+        linf = float(np.abs(qm[0] - q64[0]).max() / np.abs(q64[0]).max())
+        mixed = {"value": ws * cells * stages / (mms * 1e-3) / 1e9, "unit": METRIC,
+                 "ms_per_step": mms / args.steps, "fp32_peak_tflops": peak32,
+                 "rel_l1_rho_vs_fp64": l1, "rel_linf_rho_vs_fp64": linf}
+        m.close()
+
+    # ---- CPU baseline: the oracle on the host cores --------------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, el = oracle_step_rate(case, q, steps=1)
+        cpu = {"value": rate / 1e9, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
+               "sample": "one SSP-RK3 step (3 stages) of the full 1024x512 workload, %.1f s" % el}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny, "cells": cells,
+                           "stages_per_step": 3, "l2": "inputs larger than L2 (~1.5 GB state and scratch per step)",
+                           "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "t_reached": t_reached, "rejected_steps": rejected},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
+                "clocks": clk, "gpu_launches": launches, "kernel_ms": kernel_ms}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * hweno.h - C ABI of the B300 (sm_103a) HWENO-GR solver for the 2D compressible
+ * Navier-Stokes equations.
+ *
+ * Method: the fifth-order finite-volume HWENO scheme with gradient reconstruction
+ * of Guo, Fan and Zhao (arXiv 2608.10569).  Unknowns per cell are the cell average
+ * and the two scaled first moments of the four conserved variables (Sec. 3.1); the
+ * spatial operator is the semi-discrete system Eq. (3.2) with the PP local
+ * Lax-Friedrichs flux Eq. (3.3), characteristic unified-stencil HWENO traces
+ * (Eq. (3.4), Appendix A.2), the PP limiter on the conservative face states, and
+ * viscous gradients from weak-derivative moments reconstructed by the same scalar
+ * HWENO routine (Eqs. (3.6)-(3.9)).  Time stepping is SSP-RK3 with modified
+ * moments (Eq. (2.10) and its 2D analogue) under the time-step and restart rules of
+ * Sec. 5; boundary ghost cells follow Remark 4.1.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns int: HWENO_OK (0) or a negative HWENO_ERR_* code; the
+ *     message of the last failure on a handle is hweno_last_error(h).
+ *   - State layout ("q"): contiguous double array [3][4][ny][nx]: index
+ *     ((m*4 + v)*ny + j)*nx + i, moment m in {0: cell average, 1: scaled
+ *     xi-moment, 2: scaled eta-moment}, conserved variable v in
+ *     {rho, rho*u, rho*v, E}; i runs along x, j along y.
+ *   - on_device = 1: the pointer is CUDA device memory of the handle's device
+ *     (for example a torch tensor's data_ptr); 0: host memory (pinned or
+ *     pageable).  The caller owns every buffer it passes; the library never
+ *     keeps a caller pointer after the call returns.
+ *   - The library owns all its device memory, allocated in hweno_init and
+ *     released in hweno_destroy; no other call allocates.
+ *   - All device work runs on the stream given to hweno_init.  Calls that take
+ *     host buffers or return host values synchronise that stream before they
+ *     return; hweno_step/hweno_advance synchronise once per time step (to read
+ *     the admissibility flag and the time step).
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef HWENO_H
+#define HWENO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HWENO_OK 0
+#define HWENO_ERR_ARG (-1)          /* invalid argument or configuration */
+#define HWENO_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define HWENO_ERR_INADMISSIBLE (-3) /* a stage stayed inadmissible after max_halvings */
+#define HWENO_ERR_NONFINITE (-4)    /* NaN/Inf in the residual or the state */
+#define HWENO_ERR_TIMEOUT (-5)      /* a bounded device wait gave up */
+#define HWENO_ERR_STATE (-6)        /* call order: e.g. stepping before set_state */
+
+/* boundary conditions, Remark 4.1 (per side: xlo, xhi, ylo, yhi) */
+#define HWENO_BC_PERIODIC 0  /* both sides of the direction must be periodic */
+#define HWENO_BC_NOSLIP 1    /* stationary adiabatic no-slip wall: both momenta odd */
+#define HWENO_BC_SYMMETRY 2  /* reflective parity: normal momentum odd */
+#define HWENO_BC_SLIP 3      /* stationary slip wall: same parity as symmetry */
+
+/* arithmetic of the spatial operator */
+#define HWENO_FP64 0  /* everything in FP64 */
+#define HWENO_MIXED 1 /* reconstruction, weights and fluxes in FP32; the stored state,
+                         the RK update, the positivity limiter's checks and theta
+                         solve, and all reductions in FP64 */
+
+typedef struct hweno_handle hweno_handle;
+
+/* Problem statement (Sec. 3.1, Sec. 5).  Uniform cells dx = (x1-x0)/nx,
+ * dy = (y1-y0)/ny.  Re is the Reynolds number (the inverse dimensionless
+ * viscosity), Pr the Prandtl number, gamma the ratio of specific heats. */
+typedef struct {
+    int nx, ny;               /* cells; >= 4 each (a wall mirrors 4 ghost layers) */
+    double x0, x1, y0, y1;    /* domain */
+    double gamma, Pr, Re;     /* gas and flow parameters */
+    int bc[4];                /* HWENO_BC_* for xlo, xhi, ylo, yhi */
+    double cfl;               /* CFL number of dt = CFL h / alpha* (Sec. 5: 0.6) */
+    double b_visc;            /* viscous step factor of dt <= b Re h^2 (Sec. 5: 0.001) */
+    double eps_pp;            /* positivity-limiter epsilon (Sec. 5: 1e-12) */
+    double eps_weno;          /* epsilon of the nonlinear weights (Appendix A: 1e-8) */
+    int max_halvings;         /* restarts with dt/2 before HWENO_ERR_INADMISSIBLE */
+    int precision;            /* HWENO_FP64 or HWENO_MIXED */
+    int scheme;               /* 0: HWENO-GR (the only value accepted) */
+    int reserved;             /* must be 0 */
+} hweno_config;
+
+/* Diagnostics of the run so far (Sec. 5: PP-limiter percentage; Remark 3.1:
+ * global maximum of the LF coefficient). */
+typedef struct {
+    double t;                 /* time reached */
+    double dt_last;           /* last accepted time step */
+    double alpha_star;        /* face max of max(|u|+c,|v|+c) at the last step's first stage */
+    double beta_max;          /* max LF coefficient over the last step's stages */
+    double pp_active;         /* limiter activations (cell-stages) since set_state */
+    double cell_stages;       /* cell-stages evaluated since set_state (accepted steps) */
+    double min_rho, min_p;    /* over cell averages of the current state */
+    double totals[4];         /* domain integrals of rho, rho u, rho v, E (FP64,
+                                 fixed-order deterministic sum) */
+    long long steps;          /* accepted steps since set_state */
+    long long rejected;       /* rejected (halved) step attempts since set_state */
+} hweno_diag;
+
+/* Fill *cfg with the paper's defaults (Sec. 5, Appendix A): periodic boxes on
+ * [0,1]^2, gamma 1.4, Pr 0.72, Re 1000, CFL 0.6, b 0.001, eps_PP 1e-12,
+ * eps_WENO 1e-8, 20 halvings, FP64.  nx, ny are set to 0 and must be given. */
+int hweno_config_default(hweno_config* cfg);
+
+/* Create a solver on the current CUDA device.  stream: a cudaStream_t passed as
+ * void* (NULL = the legacy default stream).  Allocates all device memory
+ * (about 2.6 KB per padded cell in FP64).  Errors: HWENO_ERR_ARG for an invalid
+ * configuration, HWENO_ERR_CUDA if allocation fails.  *out is NULL on error. */
+int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out);
+
+/* Release the handle and its device memory (waits for the stream). */
+void hweno_destroy(hweno_handle* h);
+
+/* Static text of the last error on h (or of the last failed hweno_init when
+ * h is NULL).  Never NULL. */
+const char* hweno_last_error(const hweno_handle* h);
+
+/* Load the state q [3][4][ny][nx] (layout above) and set t.  Resets the
+ * diagnostics counters.  Does not check admissibility. */
+int hweno_set_state(hweno_handle* h, const double* q, int on_device);
+int hweno_set_time(hweno_handle* h, double t);
+
+/* Copy the current state out to q [3][4][ny][nx]. */
+int hweno_get_state(hweno_handle* h, double* q, int on_device);
+
+/* One evaluation of the spatial operator at the current state (Eq. (3.2)):
+ * ghost fill, characteristic HWENO traces and modified moments, PP limiter,
+ * weak-derivative moments, gradient HWENO, PP-LLF face fluxes, volume fluxes.
+ *   rhs  [3][4][ny][nx]: d/dt of the average, xi-moment and eta-moment
+ *   vhat [2][4][ny][nx]: the modified moments (xi, eta) of Eq. (3.4), or NULL
+ * Updates alpha_star/beta_max in the diagnostics; does not advance time.
+ * Errors: HWENO_ERR_STATE before set_state; HWENO_ERR_NONFINITE if any output is
+ * not finite (outputs are still written). */
+int hweno_residual(hweno_handle* h, double* rhs, double* vhat, int on_device);
+
+/* One SSP-RK3 step with modified moments (Eq. (2.10), 2D analogue).
+ *   dt > 0: trial step; dt <= 0: dt = min(CFL h / alpha*, b Re h^2) (Sec. 5).
+ * A stage whose cell averages are not all of positive density and pressure
+ * rejects the step and repeats it from t^n with dt/2 (Sec. 5), at most
+ * max_halvings times.  *dt_used, *rejections may be NULL.
+ * Errors: HWENO_ERR_INADMISSIBLE (state left at t^n), HWENO_ERR_NONFINITE. */
+int hweno_step(hweno_handle* h, double dt, double* dt_used, int* rejections);
+
+/* Step with the rule of Sec. 5 until t_end (the last step is shortened to land
+ * on t_end) or max_steps steps.  *t_reached, *steps may be NULL. */
+int hweno_advance(hweno_handle* h, double t_end, int max_steps, double* t_reached, int* steps);
+
+/* Diagnostics (min_rho, min_p and totals are computed on demand). */
+int hweno_get_diag(hweno_handle* h, hweno_diag* d);
+
+/* Intermediate fields of the last hweno_residual call, for parity checks
+ * against an independent implementation, copied to out as [n][ny][nx]:
+ *   which 0: limited face traces, n = 48 (point k*4 + conserved variable v;
+ *            points 0-2 left, 3-5 right, 6-8 bottom, 9-11 top face, Gauss order)
+ *         1: unlimited volume values, n = 36 (point (3G+H)*4 + v)
+ *         2: weak-derivative moments, n = 18 (6*w + {x0, x_xi, x_eta, y0, y_xi, y_eta},
+ *            w in {u, v, e})
+ *         3: reconstructed gradients, n = 126 (point*6 + {u_x,u_y,v_x,v_y,e_x,e_y},
+ *            points 0-11 face, 12-20 volume)
+ *         4: limiter factors theta_rho, theta_p, n = 2
+ * Errors: HWENO_ERR_ARG for an unknown 'which'; HWENO_ERR_STATE before a residual. */
+int hweno_debug_fields(hweno_handle* h, int which, double* out, int on_device);
+
+/* Kernel timing of the residual's dominant kernel: enable = 1 records CUDA events
+ * around every launch of each kernel of the spatial operator; hweno_profile_read
+ * returns, for kernel index k (0 ghost, 1 conservative reconstruction, 2 face
+ * moments, 3 weak moments, 4 gradient reconstruction, 5 face fluxes, 6 assembly,
+ * 7 RK update), the launches and the summed device milliseconds since enabling.
+ * Reading synchronises the stream. */
+int hweno_profile(hweno_handle* h, int enable);
+int hweno_profile_read(hweno_handle* h, int kernel, long long* launches, double* total_ms);
+
+/* Peak arithmetic throughput of the device, measured with chains of dependent-free
+ * FMAs (8 independent chains per thread, 8 blocks of 256 threads per SM, best of 3
+ * launches on the handle's stream): which 0 = FP64 FMA, 1 = FP32 FMA; *tflops in
+ * TFLOP/s counting an FMA as 2 flops.  The roofline denominator of the FP64 and
+ * mixed residual, whose kernels are bound by these pipes, not by HBM.  Takes about
+ * 0.1-0.3 s; synchronises the stream. */
+int hweno_measure_peak(hweno_handle* h, int which, double* tflops);
+
+/* Number of this library's kernel launches issued on the handle since set_state
+ * (the count bench tools report as gpu_launches). */
+long long hweno_launch_count(const hweno_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HWENO_H */

@@ -1,0 +1,333 @@
+// Device arithmetic of the HWENO-GR spatial operator (templated on the compute
+// type T: double for the FP64 path, float for the mixed path).
+//
+// Paper: Guo, Fan, Zhao, "An efficient and robust fifth-order HWENO scheme with
+// gradient reconstruction for compressible Navier-Stokes equations".
+//   scalar reconstruction ..... Appendix A.2, Eqs. (A.4)-(A.6)
+//   nonlinear combination ..... Eq. (3.4) / Eq. (3.9)
+//   Gauss points .............. Sec. 3.1 (offsets 0, +-sqrt(15)/10; weights 4/9, 5/18)
+//   characteristic fields ..... Sec. 3.1 (left eigenvectors of the Euler Jacobian)
+//   PP limiter ................ Sec. 3.1 and Sec. 5 (eps_PP)
+//   fluxes, LF coefficient .... Sec. 3.1 flux definitions, Eq. (3.3)
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hweno_stencil.h"
+
+namespace hw {
+
+// three-point Gauss rule on the scaled cell [-1/2, 1/2]
+constexpr double GN = 0.3872983346207416885;   // sqrt(15)/10
+constexpr double GW_OUT = 5.0 / 18.0;
+constexpr double GW_MID = 4.0 / 9.0;
+// linear weights of Appendix A.2
+constexpr double GAM0 = 0.99;
+constexpr double GAML = 0.0025;
+
+template <class T>
+__device__ __forceinline__ T gweight(int g) { return g == 1 ? T(GW_MID) : T(GW_OUT); }
+template <class T>
+__device__ __forceinline__ T gnode(int g) { return T(g - 1) * T(GN); }
+
+// ---------------------------------------------------------------------------
+// scalar unified-stencil HWENO on offset data.
+// d[0..8]: averages minus the centre average (so d[4] == 0), d[9..16]: the eight
+// first moments in the order of hweno_stencil.h.  Returns the coefficients C of the
+// nonlinear combination w0 (p0/g0 - sum gm/g0 pm) + sum wm pm of Eq. (3.4), also
+// relative to the centre average.
+// c0: the quartic's coefficients; s = (dxm, dxp, dym, dyp): the one-sided
+// differences of the averages, centre minus left, right minus centre, centre minus
+// bottom, top minus centre.  The four linear candidates share the centre average and
+// take their slopes from S1={2,4,5}: (dxm, dym), S2={2,5,6}: (dxp, dym),
+// S3={4,5,8}: (dxm, dyp), S4={5,6,8}: (dxp, dyp).
+template <class T>
+__device__ __forceinline__ void hweno_combine_coeffs(const T* c0, const T* s, T eps, T* C) {
+  const T dxm = s[0], dxp = s[1], dym = s[2], dyp = s[3];
+  const T sxm = dxm * dxm, sxp = dxp * dxp, sym = dym * dym, syp = dyp * dyp;
+  T b[5];
+  b[0] = hw_beta_quartic<T>(c0);
+  b[1] = sxm + sym;
+  b[2] = sxp + sym;
+  b[3] = sxm + syp;
+  b[4] = sxp + syp;
+  T ts = fabs(b[0] - b[1]) + fabs(b[0] - b[2]) + fabs(b[0] - b[3]) + fabs(b[0] - b[4]);
+  ts = T(0.25) * ts;
+  const T tau = ts * ts;
+  // t_m = tau/(beta_m + eps); omega_m = gamma_m (1 + t_m) / S.  The combination
+  // coefficients of Eq. (3.4) are then a0 = omega0/gamma0 = (1 + t0)/S and
+  // a_m = omega_m - a0 gamma_m = gamma_m (t_m - t0)/S for the linear candidates.
+  T t[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) t[m] = tau / (b[m] + eps);
+  const T wsum = T(GAM0) * (T(1) + t[0]) + T(GAML) * ((T(1) + t[1]) + (T(1) + t[2]) + (T(1) + t[3]) + (T(1) + t[4]));
+  const T rs = T(1) / wsum;
+  const T a0 = (T(1) + t[0]) * rs;
+  const T gl = T(GAML) * rs;
+  T a[4];
+#pragma unroll
+  for (int m = 0; m < 4; m++) a[m] = gl * (t[m + 1] - t[0]);
+#pragma unroll
+  for (int k = 0; k < 15; k++) C[k] = a0 * c0[k];
+  // sum_m a_m = 1 - a0 multiplies the (zero) centre offset: nothing to add to C[0]
+  C[1] += (a[0] + a[2]) * dxm + (a[1] + a[3]) * dxp;
+  C[2] += (a[0] + a[1]) * dym + (a[2] + a[3]) * dyp;
+}
+
+// scalar reconstruction from the 17 offset data (d[4] == 0)
+template <class T>
+__device__ __forceinline__ void hweno_combine(const T* d, T eps, T* C) {
+  T c0[15];
+  hw_p0_coeffs<T>(d, c0);
+  const T s[4] = {-d[3], d[5], -d[1], d[7]};
+  hweno_combine_coeffs<T>(c0, s, eps, C);
+}
+
+// ---------------------------------------------------------------------------
+// point evaluation of a quartic with monomial order
+// 1, x, y, x^2, xy, y^2, x^3, x^2y, xy^2, y^3, x^4, x^3y, x^2y^2, xy^3, y^4
+// collapse along x at x = +-h: even part E_q and odd part O_q of sum_p c_pq x^p
+template <class T>
+__device__ __forceinline__ void collapse_x(const T* c, T h, T* E, T* O) {
+  const T h2 = h * h;
+  E[0] = c[0] + h2 * (c[3] + h2 * c[10]);
+  O[0] = h * (c[1] + h2 * c[6]);
+  E[1] = c[2] + h2 * c[7];
+  O[1] = h * (c[4] + h2 * c[11]);
+  E[2] = c[5] + h2 * c[12];
+  O[2] = h * c[8];
+  E[3] = c[9];
+  O[3] = h * c[13];
+  E[4] = c[14];
+}
+template <class T>
+__device__ __forceinline__ void collapse_y(const T* c, T h, T* E, T* O) {
+  const T h2 = h * h;
+  E[0] = c[0] + h2 * (c[5] + h2 * c[14]);
+  O[0] = h * (c[2] + h2 * c[9]);
+  E[1] = c[1] + h2 * c[8];
+  O[1] = h * (c[4] + h2 * c[13]);
+  E[2] = c[3] + h2 * c[12];
+  O[2] = h * c[7];
+  E[3] = c[6];
+  O[3] = h * c[11];
+  E[4] = c[10];
+}
+// 1D quartic a0..a4 at t = -g, 0, +g
+template <class T>
+__device__ __forceinline__ void line3(const T* a, T* out) {
+  const T g = T(GN), g2 = g * g;
+  const T ev = a[0] + g2 * (a[2] + g2 * a[4]);
+  const T od = g * (a[1] + g2 * a[3]);
+  out[0] = ev - od;
+  out[1] = a[0];
+  out[2] = ev + od;
+}
+// values at the x-faces: [left (xi=-1/2) eta_G, right (xi=+1/2) eta_G]
+template <class T>
+__device__ __forceinline__ void eval_xfaces(const T* c, T* out) {
+  T E[5], O[4], a[5];
+  collapse_x<T>(c, T(0.5), E, O);
+#pragma unroll
+  for (int q = 0; q < 4; q++) a[q] = E[q] - O[q];
+  a[4] = E[4];
+  line3<T>(a, out);
+#pragma unroll
+  for (int q = 0; q < 4; q++) a[q] = E[q] + O[q];
+  line3<T>(a, out + 3);
+}
+// values at the y-faces: [bottom (eta=-1/2) xi_G, top (eta=+1/2) xi_G]
+template <class T>
+__device__ __forceinline__ void eval_yfaces(const T* c, T* out) {
+  T E[5], O[4], a[5];
+  collapse_y<T>(c, T(0.5), E, O);
+#pragma unroll
+  for (int q = 0; q < 4; q++) a[q] = E[q] - O[q];
+  a[4] = E[4];
+  line3<T>(a, out);
+#pragma unroll
+  for (int q = 0; q < 4; q++) a[q] = E[q] + O[q];
+  line3<T>(a, out + 3);
+}
+// values at the 9 volume points, index 3G + H at (xi_G, eta_H)
+template <class T>
+__device__ __forceinline__ void eval_vol(const T* c, T* out) {
+  T E[5], O[4], a[5], v[3];
+  collapse_x<T>(c, T(GN), E, O);
+#pragma unroll
+  for (int q = 0; q < 4; q++) a[q] = E[q] - O[q];
+  a[4] = E[4];
+  line3<T>(a, v);
+  out[0] = v[0]; out[1] = v[1]; out[2] = v[2];
+  // xi = 0: the coefficients with p = 0
+  a[0] = c[0]; a[1] = c[2]; a[2] = c[5]; a[3] = c[9]; a[4] = c[14];
+  line3<T>(a, v);
+  out[3] = v[0]; out[4] = v[1]; out[5] = v[2];
+#pragma unroll
+  for (int q = 0; q < 4; q++) a[q] = E[q] + O[q];
+  a[4] = E[4];
+  line3<T>(a, v);
+  out[6] = v[0]; out[7] = v[1]; out[8] = v[2];
+}
+
+// ---------------------------------------------------------------------------
+// eigenvectors of the Euler flux Jacobian at a state (direction dir = 0: x, 1: y).
+// Columns of R: waves u_n - c, u_n (entropy), shear, u_n + c; L = R^{-1}.
+template <class T>
+struct Eigen {
+  T L[4][4];
+  T R[4][4];
+};
+
+template <class T>
+__device__ __forceinline__ void euler_eigen(const T* ub, T gamma, int dir, Eigen<T>& e) {
+  const T rr = T(1) / ub[0];
+  const T u = ub[1] * rr, v = ub[2] * rr;
+  const T q2 = u * u + v * v;
+  const T p = (gamma - T(1)) * (ub[3] - T(0.5) * ub[0] * q2);
+  const T c2 = gamma * p * rr;
+  const T c = sqrt(c2);
+  const T rc = T(1) / c;
+  const T H = (ub[3] + p) * rr;
+  const T b1 = (gamma - T(1)) / c2, b2 = T(0.5) * b1 * q2;
+  const T un = dir == 0 ? u : v, ut = dir == 0 ? v : u;
+  const int in = dir == 0 ? 1 : 2, it = dir == 0 ? 2 : 1;
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) { e.L[a][b] = T(0); e.R[a][b] = T(0); }
+  e.R[0][0] = T(1); e.R[in][0] = un - c; e.R[it][0] = ut; e.R[3][0] = H - un * c;
+  e.R[0][1] = T(1); e.R[in][1] = un;     e.R[it][1] = ut; e.R[3][1] = T(0.5) * q2;
+  e.R[it][2] = T(1); e.R[3][2] = ut;
+  e.R[0][3] = T(1); e.R[in][3] = un + c; e.R[it][3] = ut; e.R[3][3] = H + un * c;
+  e.L[0][0] = T(0.5) * (b2 + un * rc); e.L[0][in] = T(-0.5) * (b1 * un + rc);
+  e.L[0][it] = T(-0.5) * b1 * ut;      e.L[0][3] = T(0.5) * b1;
+  e.L[1][0] = T(1) - b2; e.L[1][in] = b1 * un; e.L[1][it] = b1 * ut; e.L[1][3] = -b1;
+  e.L[2][0] = -ut; e.L[2][it] = T(1);
+  e.L[3][0] = T(0.5) * (b2 - un * rc); e.L[3][in] = T(0.5) * (rc - b1 * un);
+  e.L[3][it] = T(-0.5) * b1 * ut;      e.L[3][3] = T(0.5) * b1;
+}
+
+// ---------------------------------------------------------------------------
+// ideal gas helpers (Sec. 3.1)
+__device__ __forceinline__ double pressure(const double* u, double gamma) {
+  return (gamma - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0]);
+}
+
+// smallest t in [0,1] with p(ub + t (uq - ub)) = eps, written as the quadratic
+// (E + t dE)(rho + t drho) - |m + t dm|^2/2 - eps/(gamma-1) (rho + t drho) = 0
+__device__ __forceinline__ double theta_root(const double* ub, const double* uq, double eps,
+                                              double gamma) {
+  const double d0 = uq[0] - ub[0], d1 = uq[1] - ub[1], d2 = uq[2] - ub[2], d3 = uq[3] - ub[3];
+  const double e1 = eps / (gamma - 1.0);
+  const double a = d3 * d0 - 0.5 * (d1 * d1 + d2 * d2);
+  const double b = ub[3] * d0 + ub[0] * d3 - (ub[1] * d1 + ub[2] * d2) - e1 * d0;
+  const double cc = ub[3] * ub[0] - 0.5 * (ub[1] * ub[1] + ub[2] * ub[2]) - e1 * ub[0];
+  double t;
+  if (fabs(a) < 1e-300) {
+    t = -cc / b;
+  } else {
+    double disc = b * b - 4.0 * a * cc;
+    disc = disc < 0.0 ? 0.0 : disc;
+    const double sq = sqrt(disc);
+    const double qq = -0.5 * (b + (b >= 0.0 ? sq : -sq));
+    const double r1 = qq / a;
+    const double r2 = qq != 0.0 ? cc / qq : r1;
+    const double lo = fmin(r1, r2), hi = fmax(r1, r2);
+    t = (lo >= 0.0 && lo <= 1.0) ? lo : hi;
+  }
+  return fmin(fmax(t, 0.0), 1.0);
+}
+
+// Positivity-preserving limiter of one cell (Sec. 3.1, Sec. 5), always in FP64:
+// density scaling about the average over all 21 points, then the pressure root;
+// only the 12 face states are rescaled.  Returns 1 when it changed anything.
+__device__ __forceinline__ int pp_limit(const double* ub, double (*face)[4], const double (*vol)[4],
+                                        double gamma, double eps_pp, double* th_out) {
+  const double pb = pressure(ub, gamma);
+  th_out[0] = 1.0;
+  th_out[1] = 1.0;
+  double eps = fmin(eps_pp, fmin(ub[0], pb));
+  double rmin = ub[0];
+#pragma unroll
+  for (int k = 0; k < 12; k++) rmin = fmin(rmin, face[k][0]);
+#pragma unroll
+  for (int k = 0; k < 9; k++) rmin = fmin(rmin, vol[k][0]);
+  const double thr = rmin < eps ? (ub[0] - eps) / (ub[0] - rmin) : 1.0;
+  // pressure check with the density rescaled; p < eps  <=>  (g-1)(E rho - |m|^2/2) < eps rho
+  double thp = 1.0;
+  const double gm1 = gamma - 1.0;
+#pragma unroll 1
+  for (int k = 0; k < 21; k++) {
+    const double* s = k < 12 ? face[k] : vol[k - 12];
+    double w[4] = {ub[0] + thr * (s[0] - ub[0]), s[1], s[2], s[3]};
+    const double lhs = gm1 * (w[3] * w[0] - 0.5 * (w[1] * w[1] + w[2] * w[2]));
+    if (lhs < eps * w[0]) thp = fmin(thp, theta_root(ub, w, eps, gamma));
+  }
+  if (thr < 1.0 || thp < 1.0) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const double r = ub[0] + thr * (face[k][0] - ub[0]);
+      face[k][0] = ub[0] + thp * (r - ub[0]);
+#pragma unroll
+      for (int v = 1; v < 4; v++) face[k][v] = ub[v] + thp * (face[k][v] - ub[v]);
+    }
+  }
+  th_out[0] = thr;
+  th_out[1] = thp;
+  return (thr < 1.0 || thp < 1.0) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// physical flux in direction dir from primitive state (rho, u, v, e) and
+// gradients s = (u_x, u_y, v_x, v_y, e_x, e_y); also returns the conserved state.
+struct Phys {
+  double gamma, Pr, Re;
+};
+
+template <class T>
+__device__ __forceinline__ void phys_flux(int dir, const T* w, const T* s, T gamma, T rPr, T rRe,
+                                          T* f) {
+  const T rho = w[0], u = w[1], v = w[2], e = w[3];
+  const T p = (gamma - T(1)) * rho * e;
+  const T E = rho * (e + T(0.5) * (u * u + v * v));
+  const T txx = T(4.0 / 3.0) * s[0] - T(2.0 / 3.0) * s[3];
+  const T txy = s[1] + s[2];
+  const T tyy = T(4.0 / 3.0) * s[3] - T(2.0 / 3.0) * s[0];
+  if (dir == 0) {
+    const T m = rho * u;
+    f[0] = m;
+    f[1] = m * u + p - txx * rRe;
+    f[2] = m * v - txy * rRe;
+    f[3] = (E + p) * u - (txx * u + txy * v + gamma * s[4] * rPr) * rRe;
+  } else {
+    const T n = rho * v;
+    f[0] = n;
+    f[1] = n * u - txy * rRe;
+    f[2] = n * v + p - tyy * rRe;
+    f[3] = (E + p) * v - (txy * u + tyy * v + gamma * s[5] * rPr) * rRe;
+  }
+}
+
+// max(|u_n| + c, PP wave-speed bound of Eq. (3.3))
+template <class T>
+__device__ __forceinline__ T wave_bound(int dir, const T* w, const T* s, T gamma, T rPr, T rRe) {
+  const T rho = w[0], e = w[3];
+  const T p = (gamma - T(1)) * rho * e;
+  const T cs = sqrt(gamma * (gamma - T(1)) * e);
+  const T txx = T(4.0 / 3.0) * s[0] - T(2.0 / 3.0) * s[3];
+  const T txy = s[1] + s[2];
+  const T tyy = T(4.0 / 3.0) * s[3] - T(2.0 / 3.0) * s[0];
+  T un, q, s1, s2;
+  if (dir == 0) {
+    un = w[1]; q = gamma * s[4] * rPr * rRe; s1 = txx * rRe - p; s2 = txy * rRe;
+  } else {
+    un = w[2]; q = gamma * s[5] * rPr * rRe; s1 = txy * rRe; s2 = tyy * rRe - p;
+  }
+  const T r2e = rho * rho * e;
+  const T pp = fabs(un) + (sqrt(rho * rho * q * q + T(2) * r2e * (s1 * s1 + s2 * s2)) + rho * fabs(q)) /
+                              (T(2) * r2e);
+  return fmax(fabs(un) + cs, pp);
+}
+
+}  // namespace hw

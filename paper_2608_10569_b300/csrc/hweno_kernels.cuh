@@ -1,0 +1,204 @@
+// Kernels of the HWENO-GR spatial operator and the SSP-RK3 stage update.
+//
+// Data layout in HBM (all planes FP64, structure of arrays):
+//   padded plane: (ny + 8) rows x pitch doubles, pitch = nx + 8 rounded up to a
+//   multiple of 16 (128-byte rows); cell (i, j), i in [-4, nx+4), j in [-4, ny+4),
+//   sits at (j + 4) * pitch + (i + 4).  A "plane set" of n planes is n consecutive
+//   planes of plane_stride doubles.
+//
+// One spatial-operator evaluation runs these kernels in order (regions in cells):
+//   ghost_x / ghost_y   fill the 4 ghost layers of the 12 state planes (Remark 4.1)
+//   k_cons              characteristic HWENO traces + limiter on the interior grown by 3
+//   k_face_moments      face moments W^{x,0}, W^{x,1}, W^{y,0}, W^{y,1} (Eq. (3.6))
+//   k_weak_moments      weak-derivative moments r (Eqs. (3.7)-(3.8)) on interior + 2
+//   k_grad              gradient HWENO (Eq. (3.9)) on interior + 1
+//   k_flux              PP-LLF face fluxes (Eq. (3.3)) of the interior faces
+//   k_assemble          moment balances Eq. (3.2) on the interior
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hweno_device.cuh"
+
+namespace hw {
+
+constexpr int NG = 4;  // ghost layers
+
+struct Grid {
+  int nx, ny, pitch;
+  long long ps;  // plane stride in doubles
+  double dx, dy;
+  double gamma, Pr, Re;
+  double eps_pp, eps_weno;
+  int bc[4];
+};
+
+__device__ __forceinline__ long long cidx(const Grid& g, int i, int j) {
+  return (long long)(j + NG) * g.pitch + (i + NG);
+}
+
+// scratch planes of one spatial-operator evaluation
+struct Work {
+  double* face;   // 48 planes: point k (0..11) x (rho, u, v, e), limited
+  double* vol;    // 36 planes: point k (0..8) x (rho, u, v, e), unlimited
+  double* wbar;   // 3 planes: cell means of u, v, e (Eq. (3.8))
+  double* wx;     // 6 planes at the x-face right of a cell: W^{x,0}(u,v,e), W^{x,1}(u,v,e)
+  double* wy;     // 6 planes at the y-face above a cell
+  double* rm;     // 18 planes: 6*w + (x0, x_xi, x_eta, y0, y_xi, y_eta)
+  double* gr;     // 126 planes: point k (0..20) x (u_x, u_y, v_x, v_y, e_x, e_y)
+  double* fx;     // 12 planes: x-face right of a cell, Gauss point g x variable v
+  double* fy;     // 12 planes: y-face above a cell
+  double* theta;  // 2 planes: limiter factors
+};
+
+// device-side reductions and flags of one evaluation / step
+struct Diag {
+  unsigned long long alpha_bits;  // max of non-negative doubles via their bit patterns
+  unsigned long long beta_bits;
+  unsigned long long pp_count;    // limiter activations (interior cells)
+  unsigned int flags;             // bit 0: stage output inadmissible, bit 1: nonfinite rhs,
+                                  // bit 2: inadmissible cell average met by the limiter
+  unsigned int pad;
+  double dt;                      // time step of the current step
+};
+
+enum { FLAG_INADMISSIBLE = 1u, FLAG_NONFINITE = 2u, FLAG_BADAVG = 4u };
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
+  // ordering of non-negative IEEE doubles equals the ordering of their bit patterns;
+  // NaN patterns sort above +inf and therefore surface in the maximum
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// ghost cells (Remark 4.1).  x pass over the interior rows, then y pass over the
+// full padded width, so corners take the product of the two parities.
+// Mirror across a face with parity s per variable: ghost average = s * average,
+// moment normal to the face = -s * moment, tangential moment = s * moment.
+__device__ __forceinline__ double bc_sign(int bc, int normal_dir, int v) {
+  if (v == 0 || v == 3) return 1.0;
+  if (bc == 1) return -1.0;                 // no-slip: both momenta odd
+  return (v == 1 + normal_dir) ? -1.0 : 1.0;  // symmetry/slip: normal momentum odd
+}
+
+__global__ void k_ghost_x(Grid g, double* q) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // over 8 ghost columns x ny rows
+  if (t >= 8 * g.ny) return;
+  const int j = t / 8, c = t % 8;
+  const int side = c / 4, k = c % 4;  // side 0: i = -1-k, side 1: i = nx+k
+  const int i = side == 0 ? -1 - k : g.nx + k;
+  const int bc = g.bc[side];
+  int src;
+  if (bc == 0) src = side == 0 ? ((i % g.nx) + g.nx) % g.nx : i % g.nx;
+  else src = side == 0 ? -1 - i : 2 * g.nx - 1 - i;
+  const long long d = cidx(g, i, j), s = cidx(g, src, j);
+#pragma unroll
+  for (int m = 0; m < 3; m++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      double sg = 1.0;
+      if (bc != 0) sg = bc_sign(bc, 0, v) * (m == 1 ? -1.0 : 1.0);
+      q[(4 * m + v) * g.ps + d] = sg * q[(4 * m + v) * g.ps + s];
+    }
+}
+
+__global__ void k_ghost_y(Grid g, double* q) {
+  const int W = g.nx + 2 * NG;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // over 8 ghost rows x padded width
+  if (t >= 8 * W) return;
+  const int r = t / W, i = t % W - NG;
+  const int side = r / 4, k = r % 4;
+  const int j = side == 0 ? -1 - k : g.ny + k;
+  const int bc = g.bc[2 + side];
+  int src;
+  if (bc == 0) src = side == 0 ? ((j % g.ny) + g.ny) % g.ny : j % g.ny;
+  else src = side == 0 ? -1 - j : 2 * g.ny - 1 - j;
+  const long long d = cidx(g, i, j), s = cidx(g, i, src);
+#pragma unroll
+  for (int m = 0; m < 3; m++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      double sg = 1.0;
+      if (bc != 0) sg = bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0);
+      q[(4 * m + v) * g.ps + d] = sg * q[(4 * m + v) * g.ps + s];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gather the 17 data of one conserved variable (plane offset v) around (i, j)
+// in the order of hweno_stencil.h, as offsets from the centre average
+__device__ __forceinline__ void gather17(const Grid& g, const double* q, int v, int i, int j,
+                                         double* d) {
+  const double* A = q + (long long)v * g.ps;
+  const double* X = q + (long long)(4 + v) * g.ps;
+  const double* Y = q + (long long)(8 + v) * g.ps;
+  const double c = A[cidx(g, i, j)];
+#pragma unroll
+  for (int b = -1; b <= 1; b++)
+#pragma unroll
+    for (int a = -1; a <= 1; a++) d[(b + 1) * 3 + (a + 1)] = A[cidx(g, i + a, j + b)] - c;
+  d[4] = 0.0;
+  d[9] = X[cidx(g, i - 1, j)];
+  d[10] = X[cidx(g, i + 1, j)];
+  d[11] = Y[cidx(g, i, j - 1)];
+  d[12] = Y[cidx(g, i, j + 1)];
+  d[13] = X[cidx(g, i, j - 1)];
+  d[14] = X[cidx(g, i, j + 1)];
+  d[15] = Y[cidx(g, i - 1, j)];
+  d[16] = Y[cidx(g, i + 1, j)];
+}
+
+// characteristic reconstruction of one direction: per field, project the
+// conserved p0 coefficients and slopes, form the nonlinear combination, evaluate
+// at this direction's 6 face points, the 9 volume points and the moment, and
+// transform back.  Outputs are offsets from the centre average (moments absolute).
+template <class T, int DIR>
+__device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], const Eigen<T>& e,
+                                          T eps, double (*face)[4], double (*vol)[4], double* mom) {
+  T chf[4][6], chv[4][9], chm[4];
+#pragma unroll
+  for (int f = 0; f < 4; f++) {
+    // the projected coefficients are those of the projected data: p0 is linear
+    T c0[15];
+#pragma unroll
+    for (int k = 0; k < 15; k++)
+      c0[k] = e.L[f][0] * cc[0][k] + e.L[f][1] * cc[1][k] + e.L[f][2] * cc[2][k] + e.L[f][3] * cc[3][k];
+    // projected one-sided differences (dxm, dxp, dym, dyp)
+    T s[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      s[k] = e.L[f][0] * sl[0][k] + e.L[f][1] * sl[1][k] + e.L[f][2] * sl[2][k] + e.L[f][3] * sl[3][k];
+    T C[15];
+    hweno_combine_coeffs<T>(c0, s, eps, C);
+    if (DIR == 0) eval_xfaces<T>(C, chf[f]); else eval_yfaces<T>(C, chf[f]);
+    eval_vol<T>(C, chv[f]);
+    chm[f] = DIR == 0 ? hw_moment_xi<T>(C) : hw_moment_eta<T>(C);
+  }
+#pragma unroll
+  for (int v = 0; v < 4; v++) {
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+      face[k][v] = (double)(e.R[v][0] * chf[0][k] + e.R[v][1] * chf[1][k] + e.R[v][2] * chf[2][k] +
+                            e.R[v][3] * chf[3][k]);
+#pragma unroll
+    for (int k = 0; k < 9; k++)
+      vol[k][v] = (double)(e.R[v][0] * chv[0][k] + e.R[v][1] * chv[1][k] + e.R[v][2] * chv[2][k] +
+                           e.R[v][3] * chv[3][k]);
+    mom[v] = (double)(e.R[v][0] * chm[0] + e.R[v][1] * chm[1] + e.R[v][2] * chm[2] + e.R[v][3] * chm[3]);
+  }
+}
+
+}  // namespace hw

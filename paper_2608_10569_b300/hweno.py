@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libhweno.so (C ABI in include/hweno.h).
+
+Every function of the C ABI is exposed under the same name with the same
+arguments; ``Solver`` wraps a handle for torch tensors and numpy arrays.  This
+module only marshals arguments: every step of the method runs in the CUDA
+library, and importing fails loudly if the library is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libhweno.so")
+
+HWENO_OK = 0
+HWENO_ERR_ARG = -1
+HWENO_ERR_CUDA = -2
+HWENO_ERR_INADMISSIBLE = -3
+HWENO_ERR_NONFINITE = -4
+HWENO_ERR_TIMEOUT = -5
+HWENO_ERR_STATE = -6
+HWENO_FP64 = 0
+HWENO_MIXED = 1
+BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3}
+
+# kernel indices of hweno_profile_read
+KERNELS = ["ghost", "cons_recon", "face_moments", "weak_moments", "grad_recon", "flux", "assemble",
+           "rk_update"]
+
+
+class HwenoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hweno error %d: %s" % (code, msg))
+        self.code = code
+
+
+class hweno_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
+                ("bc", ctypes.c_int * 4),
+                ("cfl", ctypes.c_double), ("b_visc", ctypes.c_double),
+                ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
+                ("max_halvings", ctypes.c_int), ("precision", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class hweno_diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt_last", ctypes.c_double),
+                ("alpha_star", ctypes.c_double), ("beta_max", ctypes.c_double),
+                ("pp_active", ctypes.c_double), ("cell_stages", ctypes.c_double),
+                ("min_rho", ctypes.c_double), ("min_p", ctypes.c_double),
+                ("totals", ctypes.c_double * 4),
+                ("steps", ctypes.c_longlong), ("rejected", ctypes.c_longlong)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_H = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = [
+    ("hweno_config_default", ctypes.c_int, [ctypes.POINTER(hweno_config)]),
+    ("hweno_init", ctypes.c_int, [ctypes.POINTER(hweno_config), ctypes.c_void_p, ctypes.POINTER(_H)]),
+    ("hweno_destroy", None, [_H]),
+    ("hweno_last_error", ctypes.c_char_p, [_H]),
+    ("hweno_set_state", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
+    ("hweno_set_time", ctypes.c_int, [_H, ctypes.c_double]),
+    ("hweno_get_state", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
+    ("hweno_residual", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("hweno_step", ctypes.c_int, [_H, ctypes.c_double, _D, ctypes.POINTER(ctypes.c_int)]),
+    ("hweno_advance", ctypes.c_int, [_H, ctypes.c_double, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
+    ("hweno_get_diag", ctypes.c_int, [_H, ctypes.POINTER(hweno_diag)]),
+    ("hweno_debug_fields", ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    ("hweno_profile", ctypes.c_int, [_H, ctypes.c_int]),
+    ("hweno_profile_read", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D]),
+    ("hweno_launch_count", ctypes.c_longlong, [_H]),
+    ("hweno_measure_peak", ctypes.c_int, [_H, ctypes.c_int, _D]),
+]
+
+
+def load(path=LIB_PATH):
+    """Load libhweno.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("libhweno.so not found at %s: build it with "
+                              "`python -m paper_2608_10569_b300.build` (there is no CPU fallback)" % path)
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def __getattr__(name):
+    # hweno_* attributes resolve to the raw C entry points
+    if name.startswith("hweno_"):
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+def _check(h, rc):
+    if rc != HWENO_OK:
+        msg = load().hweno_last_error(h)
+        raise HwenoError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
+                bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
+                max_halvings=20, precision="fp64", **_ignored):
+    c = hweno_config()
+    load().hweno_config_default(ctypes.byref(c))
+    c.nx, c.ny = int(nx), int(ny)
+    c.x0, c.x1, c.y0, c.y1 = float(x0), float(x1), float(y0), float(y1)
+    c.gamma, c.Pr, c.Re = float(gamma), float(Pr), float(Re)
+    for k in range(4):
+        c.bc[k] = BC[bc[k]] if isinstance(bc[k], str) else int(bc[k])
+    c.cfl, c.b_visc, c.eps_pp, c.eps_weno = float(cfl), float(b_visc), float(eps_pp), float(eps_weno)
+    c.max_halvings = int(max_halvings)
+    c.precision = HWENO_MIXED if precision in ("mixed", HWENO_MIXED) else HWENO_FP64
+    return c
+
+
+def _ptr_of(a):
+    """(pointer, on_device) of a torch tensor or numpy array (must be contiguous float64)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("need a C-contiguous float64 array")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError("need a numpy array or a torch tensor")
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise ValueError("need a contiguous float64 tensor")
+    return ctypes.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0)
+
+
+class Solver:
+    """One HWENO-GR solver instance on the current CUDA device."""
+
+    def __init__(self, case_params, precision="fp64", stream=None):
+        import torch
+        self.lib = load()
+        p = dict(case_params)
+        p["precision"] = precision
+        self.cfg = make_config(**p)
+        self.nx, self.ny = self.cfg.nx, self.cfg.ny
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _H()
+        rc = self.lib.hweno_init(ctypes.byref(self.cfg), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if rc != HWENO_OK:
+            raise HwenoError(rc, self.lib.hweno_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hweno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, q):
+        ptr, dev = _ptr_of(q)
+        _check(self.h, self.lib.hweno_set_state(self.h, ptr, dev))
+
+    def set_time(self, t):
+        _check(self.h, self.lib.hweno_set_time(self.h, float(t)))
+
+    def get_state(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((12, self.ny, self.nx), dtype=torch.float64, device="cuda")
+        ptr, dev = _ptr_of(out)
+        _check(self.h, self.lib.hweno_get_state(self.h, ptr, dev))
+        return out
+
+    def residual(self, rhs=None, vhat=None):
+        import torch
+        if rhs is None:
+            rhs = torch.empty((12, self.ny, self.nx), dtype=torch.float64, device="cuda")
+        if vhat is None:
+            vhat = torch.empty((8, self.ny, self.nx), dtype=torch.float64, device="cuda")
+        pr, dr = _ptr_of(rhs)
+        pv, dv = _ptr_of(vhat)
+        if dr != dv:
+            raise ValueError("rhs and vhat must both be host or both be device buffers")
+        _check(self.h, self.lib.hweno_residual(self.h, pr, pv, dr))
+        return rhs, vhat
+
+    def step(self, dt=0.0):
+        used = ctypes.c_double(0.0)
+        rej = ctypes.c_int(0)
+        _check(self.h, self.lib.hweno_step(self.h, float(dt), ctypes.byref(used), ctypes.byref(rej)))
+        return used.value, rej.value
+
+    def advance(self, t_end, max_steps=2 ** 31 - 1):
+        t = ctypes.c_double(0.0)
+        n = ctypes.c_int(0)
+        _check(self.h, self.lib.hweno_advance(self.h, float(t_end), int(max_steps), ctypes.byref(t),
+                                              ctypes.byref(n)))
+        return t.value, n.value
+
+    def diag(self):
+        d = hweno_diag()
+        _check(self.h, self.lib.hweno_get_diag(self.h, ctypes.byref(d)))
+        return {"t": d.t, "dt_last": d.dt_last, "alpha_star": d.alpha_star, "beta_max": d.beta_max,
+                "pp_active": d.pp_active, "cell_stages": d.cell_stages, "min_rho": d.min_rho,
+                "min_p": d.min_p, "totals": list(d.totals), "steps": d.steps, "rejected": d.rejected}
+
+    def debug_fields(self, which):
+        import torch
+        n = {0: 48, 1: 36, 2: 18, 3: 126, 4: 2}[which]
+        out = torch.empty((n, self.ny, self.nx), dtype=torch.float64, device="cuda")
+        ptr, dev = _ptr_of(out)
+        _check(self.h, self.lib.hweno_debug_fields(self.h, int(which), ptr, dev))
+        return out
+
+    def profile(self, enable=True):
+        _check(self.h, self.lib.hweno_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        out = {}
+        for k, name in enumerate(KERNELS):
+            n = ctypes.c_longlong(0)
+            ms = ctypes.c_double(0.0)
+            _check(self.h, self.lib.hweno_profile_read(self.h, k, ctypes.byref(n), ctypes.byref(ms)))
+            out[name] = (n.value, ms.value)
+        return out
+
+    def launch_count(self):
+        return self.lib.hweno_launch_count(self.h)
+
+    def measure_peak(self, which):
+        """FP64 (which=0) or FP32 (which=1) FMA throughput in TFLOP/s."""
+        tf = ctypes.c_double(0.0)
+        _check(self.h, self.lib.hweno_measure_peak(self.h, int(which), ctypes.byref(tf)))
+        return tf.value

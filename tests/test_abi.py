@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry point
+that include/hweno.h declares, and validates configurations without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "hweno.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hweno_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2608_10569_b300 import build, hweno
+    build.build()
+    return hweno.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2608_10569_b300 import hweno
+    bound = {n for n, _, _ in hweno.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_config_default_matches_the_paper(lib):
+    from paper_2608_10569_b300 import hweno
+    c = hweno.hweno_config()
+    assert lib.hweno_config_default(ctypes.byref(c)) == 0
+    assert (c.cfl, c.b_visc, c.eps_pp, c.eps_weno) == (0.6, 1e-3, 1e-12, 1e-8)
+    assert (c.gamma, c.Pr, c.max_halvings) == (1.4, 0.72, 20)
+
+
+def test_invalid_configurations_are_rejected_before_any_device_call(lib):
+    from paper_2608_10569_b300 import hweno
+    h = ctypes.c_void_p()
+    bad = [dict(nx=3, ny=8), dict(nx=8, ny=8, bc=("periodic", "noslip", "periodic", "periodic")),
+           dict(nx=8, ny=8, Re=0.0), dict(nx=8, ny=8, x1=0.0), dict(nx=8, ny=8, precision=7)]
+    for kw in bad:
+        c = hweno.make_config(**kw)
+        if kw.get("precision") == 7:
+            c.precision = 7
+        rc = lib.hweno_init(ctypes.byref(c), None, ctypes.byref(h))
+        assert rc == hweno.HWENO_ERR_ARG, kw
+        assert h.value is None
+        assert lib.hweno_last_error(None)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_2608_10569_b300 import hweno
+    assert lib.hweno_step(None, 0.0, None, None) == hweno.HWENO_ERR_ARG
+    assert lib.hweno_residual(None, None, None, 0) == hweno.HWENO_ERR_ARG
+    assert lib.hweno_launch_count(None) == 0
+
+
+def test_gpu_and_oracle_tables_agree():
+    """The GPU constants (float64 numpy derivation) and the oracle constants (exact
+    rationals) are independent derivations of Appendix A.2's stencil maps."""
+    import numpy as np
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import gen_tables as g
+    Mx = np.array([[float(x) for x in r] for r in g.p0_map()])
+    Bx = np.array([[float(x) for x in r] for r in g.beta_matrix()])
+    txt = open(os.path.join(ROOT, "paper_2608_10569_b300", "csrc", "hweno_stencil.h")).read()
+    M = np.zeros((15, 17))
+    body = txt[txt.index("hw_p0_coeffs"):txt.index("hw_beta_quartic")]
+    for k, expr in re.findall(r"c\[(\d+)\] = (.*?);\n", body):
+        for v, n in re.findall(r"T\(([-0-9.e]+)\) \* d\[(\d+)\]", expr):
+            M[int(k), int(n)] = float(v)
+    assert np.abs(M - Mx).max() <= 1e-14 * np.abs(Mx).max()
+    assert np.array_equal(M != 0, Mx != 0)
+    body = txt[txt.index("hw_beta_quartic"):txt.index("hw_moment_xi")]
+    B = np.zeros((15, 15))
+    for i, expr in re.findall(r"s \+= c\[(\d+)\] \* \((.*?)\);\n", body):
+        for v, j in re.findall(r"T\(([-0-9.e]+)\) \* c\[(\d+)\]", expr):
+            i_, j_ = int(i), int(j)
+            if i_ == j_:
+                B[i_, j_] = float(v)
+            else:
+                B[i_, j_] = B[j_, i_] = float(v) / 2
+    assert np.abs(B - Bx).max() <= 1e-13 * np.abs(Bx).max()

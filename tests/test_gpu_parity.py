@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances: relative L-infinity <= 1e-12 per plane after one spatial-operator
+evaluation (normalised by the plane's largest oracle magnitude), and relative L1
+<= 1e-9 after a full run.  Sizes span several 32x4 thread tiles with ragged tails.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2608_10569_b300 import hweno, inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+RES_TOL = 1e-12
+
+
+def rel_linf(a, b, mask=None):
+    worst = 0.0
+    for k in range(a.shape[0]):
+        ak, bk = a[k], b[k]
+        if mask is not None:
+            ak, bk = ak[mask], bk[mask]
+        if ak.size == 0:
+            continue
+        s = np.abs(bk).max()
+        d = np.abs(ak - bk).max()
+        worst = max(worst, d / s if s > 0 else d)
+    return worst
+
+
+def rel_l1(a, b):
+    worst = 0.0
+    for k in range(a.shape[0]):
+        s = np.abs(b[k]).sum()
+        d = np.abs(a[k] - b[k]).sum()
+        worst = max(worst, d / s if s > 0 else d)
+    return worst
+
+
+def gpu_residual(case, q, precision="fp64", dumps=()):
+    s = hweno.Solver(case.params(), precision=precision)
+    s.set_state(torch.from_numpy(q).cuda())
+    rhs, vhat = s.residual()
+    out = {"rhs": rhs.cpu().numpy(), "vhat": vhat.cpu().numpy(), "diag": s.diag()}
+    for w in dumps:
+        out[w] = s.debug_fields(w).cpu().numpy()
+    s.close()
+    return out
+
+
+def ocfg(case):
+    return O.make_cfg(**case.params())
+
+
+CASES = {
+    "smooth_periodic_64": lambda: I.smooth_periodic(64),
+    "rough_periodic_40x36": lambda: I.random_rough(40, 36, seed=1),
+    "smooth_walls_37x29": lambda: I.random_smooth(37, 29, seed=2, bc=("noslip", "slip", "symmetry", "noslip")),
+    "rough_walls_45x21": lambda: I.random_rough(45, 21, seed=3, bc=("noslip", "noslip", "noslip", "symmetry")),
+    "shock_tube_64x32": lambda: I.shock_tube(64, 32),
+    "taylor_green_48": lambda: I.taylor_green(48, 0.4, 300.0, 1 / 1.4, rho_pert=1e-2),
+    "minimum_grid_4x4": lambda: I.random_smooth(4, 4, seed=5),
+    "thin_grid_5x70": lambda: I.random_smooth(5, 70, seed=6, bc=("slip", "slip", "periodic", "periodic")),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_residual_parity(name):
+    case, q = CASES[name]()
+    g = gpu_residual(case, q)
+    o = O.residual(ocfg(case), q)
+    assert rel_linf(g["rhs"], o["rhs"]) <= RES_TOL
+    assert rel_linf(g["vhat"], o["vhat"]) <= RES_TOL
+    assert abs(g["diag"]["alpha_star"] - o["diag"][0]) <= 1e-13 * o["diag"][0]
+    assert abs(g["diag"]["beta_max"] - o["diag"][1]) <= 1e-12 * o["diag"][1]
+
+
+def test_intermediate_fields_parity():
+    """traces, volume values, weak-derivative moments, gradients and limiter factors"""
+    case, q = I.random_rough(40, 36, seed=7, bc=("noslip", "symmetry", "periodic", "periodic"))
+    g = gpu_residual(case, q, dumps=(0, 1, 2, 3, 4))
+    o = O.residual(ocfg(case), q, dumps=True)
+    assert rel_linf(g[0], o["face"]) <= RES_TOL
+    assert rel_linf(g[1], o["vol"]) <= RES_TOL
+    assert rel_linf(g[2], o["rm"]) <= RES_TOL
+    assert rel_linf(g[3], o["grad"]) <= RES_TOL
+    assert np.abs(g[4] - o["theta"]).max() <= 1e-13
+
+
+def _far_from(mask, r):
+    """cells whose (2r+1)^2 neighbourhood (periodic) holds no True of mask"""
+    m = mask.copy()
+    out = mask.copy()
+    for dj in range(-r, r + 1):
+        for di in range(-r, r + 1):
+            out |= np.roll(np.roll(m, dj, 0), di, 1)
+    return ~out
+
+
+def test_limiter_engaged_parity():
+    """Near-vacuum colliding streams: the limiter clips face pressures to eps_PP, where
+    the residual is ill-conditioned (the wave-speed bound scales with e^-1/2 at
+    e ~ 1e-12).  Cells whose 9x9 dependency square contains no limited cell match to
+    1e-12; the limited cells satisfy the limiter's guarantees and theta matches."""
+    case, q = I.colliding_streams(48, seed=3)
+    g = gpu_residual(case, q, dumps=(0, 4))
+    o = O.residual(ocfg(case), q, dumps=True)
+    limited = (o["theta"][0] < 1) | (o["theta"][1] < 1)
+    assert limited.any() and g["diag"]["pp_active"] == 0  # residual calls do not count steps
+    far = _far_from(limited, 4)
+    assert far.any()
+    assert rel_linf(g["rhs"], o["rhs"], far) <= RES_TOL
+    assert rel_linf(g["vhat"], o["vhat"]) <= RES_TOL  # moments are never limited
+    gam = case.gamma
+    face = g[0].reshape(12, 4, 48, 48)
+    p = (gam - 1) * (face[:, 3] - 0.5 * (face[:, 1] ** 2 + face[:, 2] ** 2) / face[:, 0])
+    assert face[:, 0].min() > 0 and p.min() >= 1e-12 - 1e-12 * np.abs(face[:, 3]).max()
+    assert np.array_equal(g[4][0] < 1, o["theta"][0] < 1) or np.abs(g[4] - o["theta"]).max() < 1e-9
+    assert np.abs(g[4] - o["theta"]).max() < 1e-6
+
+
+def _sample_cells(case, n, seed):
+    rng = np.random.default_rng(seed)
+    ci = rng.integers(0, case.nx, n)
+    cj = rng.integers(0, case.ny, n)
+    # always include the corners and the edges
+    ci = np.concatenate([ci, [0, case.nx - 1, 0, case.nx - 1, case.nx // 2]])
+    cj = np.concatenate([cj, [0, 0, case.ny - 1, case.ny - 1, case.ny // 2]])
+    return ci, cj
+
+
+FULL = {
+    "shock_tube_1024x512": lambda: I.shock_tube(1024, 512),
+    "colliding_streams_2048": lambda: I.colliding_streams(2048),
+    "adjoint_tg_512": lambda: I.adjoint_taylor_green(512),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FULL))
+def test_full_size_sampled_parity(name):
+    """Full workload sizes, in the launch configuration the benchmark uses; sampled
+    cells checked one by one against the oracle."""
+    case, q = FULL[name]()
+    g = gpu_residual(case, q, dumps=(4,))
+    ci, cj = _sample_cells(case, 300, 99)
+    if name.startswith("shock"):
+        # the diaphragm is where the residual lives: sample it densely too
+        ci = np.concatenate([ci, np.full(64, case.nx // 2 - 1), np.full(64, case.nx // 2)])
+        cj = np.concatenate([cj, np.arange(64) * (case.ny // 64), np.arange(64) * (case.ny // 64)])
+    rhs, vh = O.residual_cells(ocfg(case), q, ci, cj)
+    limited = (g[4][0] < 1) | (g[4][1] < 1)
+    keep = np.array([not limited[max(0, j - 4):j + 5, max(0, i - 4):i + 5].any() for i, j in zip(ci, cj)])
+    assert keep.sum() > 0.5 * len(ci)
+    a = g["rhs"][:, cj, ci][:, keep]
+    b = rhs.T[:, keep]
+    scale = np.abs(g["rhs"]).reshape(12, -1).max(1)
+    err = (np.abs(a - b).max(1) / np.where(scale > 0, scale, 1.0)).max()
+    assert err <= RES_TOL, err
+    a = g["vhat"][:, cj, ci]
+    scale = np.abs(g["vhat"]).reshape(8, -1).max(1)
+    assert (np.abs(a - vh.T).max(1) / np.where(scale > 0, scale, 1.0)).max() <= RES_TOL
+
+
+def test_step_parity_fixed_and_rule_dt():
+    case, q = I.random_rough(33, 31, seed=4, bc=("noslip", "noslip", "noslip", "symmetry"))
+    cfg = ocfg(case)
+    s = hweno.Solver(case.params())
+    s.set_state(torch.from_numpy(q).cuda())
+    dt, rej = s.step(2e-3)
+    assert dt == 2e-3 and rej == 0
+    qo, st = O.step(cfg, q, dt_fixed=2e-3)
+    assert rel_linf(s.get_state().cpu().numpy(), qo) <= 1e-11
+    dt2, _ = s.step()
+    qo2, st2 = O.step(cfg, qo)
+    assert abs(dt2 - st2["dt"]) <= 1e-13 * st2["dt"]
+    assert rel_linf(s.get_state().cpu().numpy(), qo2) <= 1e-11
+    s.close()
+
+
+def test_full_run_smooth_periodic():
+    """64^2 periodic flow to t = 0.1 under the Sec. 5 time-step rule (about 100
+    SSP-RK3 steps): relative L1 <= 1e-9 against the oracle's run."""
+    case, q = I.smooth_periodic(64)
+    s = hweno.Solver(case.params())
+    s.set_state(torch.from_numpy(q).cuda())
+    t, n = s.advance(case.t_end)
+    qo, st = O.advance(ocfg(case), q, 0.0, case.t_end)
+    assert st["status"] == 0 and n == st["steps"] and abs(t - st["t"]) < 1e-15
+    assert rel_l1(s.get_state().cpu().numpy(), qo) <= 1e-9
+    d = s.diag()
+    tot0 = q[:4].sum(axis=(1, 2)) * case.dx * case.dy
+    assert np.abs(np.array(d["totals"]) - tot0).max() <= 1e-13 * np.abs(tot0).max()
+    s.close()
+
+
+def test_restart_on_inadmissible_stage():
+    """A forced step far above the stable size drives a stage inadmissible; the step
+    is repeated from t^n with dt/2 until admissible (Sec. 5), as in the oracle."""
+    case, q = I.colliding_streams(32, seed=3)
+    cfg = ocfg(case)
+    s = hweno.Solver(case.params())
+    s.set_state(torch.from_numpy(q).cuda())
+    dt, rej = s.step(5e-3)
+    qo, st = O.step(cfg, q, dt_fixed=5e-3)
+    assert st["status"] == 0 and rej == st["rejections"] and rej > 0
+    assert dt == st["dt"]
+    a = s.get_state().cpu().numpy()
+    assert np.isfinite(a).all() and (a[0] > 0).all()
+    s.close()
+
+
+def test_bitwise_determinism():
+    case, q = I.random_rough(40, 36, seed=8)
+    outs = []
+    for _ in range(2):
+        s = hweno.Solver(case.params())
+        s.set_state(torch.from_numpy(q).cuda())
+        s.step(1e-3)
+        s.step(1e-3)
+        outs.append(s.get_state().cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_host_and_device_buffers_agree():
+    case, q = I.random_smooth(20, 17, seed=3)
+    s = hweno.Solver(case.params())
+    s.set_state(q.copy())  # host buffer
+    rh = np.zeros((12, 17, 20))
+    vh = np.zeros((8, 17, 20))
+    s.residual(rh, vh)
+    rd, vd = s.residual()
+    assert np.array_equal(rh, rd.cpu().numpy()) and np.array_equal(vh, vd.cpu().numpy())
+    back = np.zeros_like(q)
+    s.get_state(back)
+    assert np.array_equal(back, q)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["smooth_periodic_64", "rough_walls_45x21", "shock_tube_64x32"])
+def test_mixed_precision_residual_error(name):
+    """FP32 reconstruction and fluxes with FP64 state, limiter and RK: the residual
+    stays within a few FP32 ulps of the FP64 oracle (relative to the plane scale)."""
+    case, q = CASES[name]()
+    g = gpu_residual(case, q, precision="mixed")
+    o = O.residual(ocfg(case), q)
+    assert rel_linf(g["rhs"][:4], o["rhs"][:4]) <= 2e-5
+    assert rel_linf(g["vhat"], o["vhat"]) <= 2e-5
