@@ -145,24 +145,30 @@ def shock_tube(nx=1024, ny=512, Re=1000.0):
     return case, q
 
 
-def colliding_streams(n=2048, seed=3):
+def colliding_streams(n=2048, seed=3, modes=4):
     """Low-density extreme case on a periodic [0,1]^2 grid, gamma 5/3, Re 1e4:
     rho = 1, p = 1e-4, u = -20 for x < 0.5 and +20 otherwise (the streams separate
-    at x = 0.5 and collide across the periodic seam), plus seeded cell-wise
-    uniform noise of amplitude 0.2 (1 % of 20) on u and v; t_end 0.02."""
+    at x = 0.5 and collide across the periodic seam), plus a seeded smooth velocity
+    noise of 1 % of 20 (a sum of `modes` low-wavenumber Fourier modes on u and v,
+    peak amplitude about 0.2); t_end 0.02."""
     case = Case("colliding_streams_%d" % n, n, n, 0.0, 1.0, 0.0, 1.0, 5.0 / 3.0, 0.72, 1e4,
                 cfl=0.6, t_end=0.02)
     rng = _rng(seed)
-    du = rng.uniform(-0.2, 0.2, size=(n, n))
-    dv = rng.uniform(-0.2, 0.2, size=(n, n))
-    xc = case.x0 + (np.arange(n) + 0.5) * case.dx
-    ub = np.where(xc < 0.5, -20.0, 20.0)[None, :] + du
-    rho = np.ones((n, n))
-    U = conserved(rho, ub, dv, 1e-4 * rho, case.gamma)
-    q = np.zeros((12, n, n))
-    for v in range(4):
-        q[v] = U[v]
-    return case, q
+    k = rng.integers(1, 4, size=(2, modes, 2))
+    a = rng.uniform(-1, 1, size=(2, modes, 2))
+
+    def noise(x, y, f):
+        s = 0 * x
+        for m in range(modes):
+            s = s + a[f, m, 0] * np.sin(2 * np.pi * (k[f, m, 0] * x + k[f, m, 1] * y)) \
+                  + a[f, m, 1] * np.cos(2 * np.pi * (k[f, m, 1] * x + k[f, m, 0] * y))
+        return 0.2 * s / modes
+
+    def prim(x, y):
+        u = np.where(x < 0.5, -20.0, 20.0) + noise(x, y, 0)
+        return 1.0 + 0 * x, u, noise(x, y, 1), 1e-4 + 0 * x
+
+    return case, cell_moments(case, prim)
 
 
 def taylor_green(n, A, Re, p0, rho_pert=0.0, seed=4, gamma=1.4, name="taylor_green"):

@@ -2,8 +2,13 @@
 same seeded inputs.
 
 Tolerances: relative L-infinity <= 1e-12 per plane after one spatial-operator
-evaluation (normalised by the plane's largest oracle magnitude), and relative L1
-<= 1e-9 after a full run.  Sizes span several 32x4 thread tiles with ragged tails.
+evaluation and relative L1 <= 1e-9 after a full run.  "Relative" divides by the
+larger of the plane's largest oracle magnitude and the magnitude of the terms the
+plane is computed from: the inviscid fluxes of the cell averages over h for the
+residual, the cell averages for traces and modified moments.  Round-off of the
+two implementations is proportional to the latter, which also keeps planes that
+vanish by symmetry (noise of cancelling flux differences) comparable.  Sizes span
+several 32x4 thread tiles with ragged tails.
 """
 import numpy as np
 import pytest
@@ -18,7 +23,23 @@ pytestmark = pytest.mark.gpu
 RES_TOL = 1e-12
 
 
-def rel_linf(a, b, mask=None):
+def flux_scale(case, q):
+    """per conserved variable: max over cells of (|F_v| + |G_v|)/h of the cell averages'
+    inviscid fluxes, the magnitude of the terms whose differences form a residual plane"""
+    g = case.gamma
+    rho, m, n, E = q[0], q[1], q[2], q[3]
+    u, v = m / rho, n / rho
+    p = (g - 1) * (E - 0.5 * rho * (u * u + v * v))
+    F = [m, m * u + p, m * v, (E + p) * u]
+    G = [n, n * u, n * v + p, (E + p) * v]
+    h = min(case.dx, case.dy)
+    return np.array([np.abs(F[k]).max() + np.abs(G[k]).max() for k in range(4)]) / h
+
+
+def rel_linf(a, b, scale=None, mask=None):
+    """max over planes of max|a - b| / max(max|b|, scale of the plane's variable);
+    the scale guards planes that are zero up to round-off (symmetry, divergence-free
+    fields), whose values are cancellation noise of much larger terms"""
     worst = 0.0
     for k in range(a.shape[0]):
         ak, bk = a[k], b[k]
@@ -27,9 +48,35 @@ def rel_linf(a, b, mask=None):
         if ak.size == 0:
             continue
         s = np.abs(bk).max()
+        if scale is not None:
+            s = max(s, scale[k % 4])
         d = np.abs(ak - bk).max()
         worst = max(worst, d / s if s > 0 else d)
     return worst
+
+
+def state_scale(q):
+    return np.abs(q[:4]).reshape(4, -1).max(1)
+
+
+def char_condition(case, q, n=400):
+    """largest ||L||_inf ||R||_inf of the characteristic eigenvector pairs over sampled
+    cell averages: rounding differences in characteristic space reach the traces
+    amplified by this factor (about 1e1-1e2 for ordinary flows, 5e8 for the
+    Mach-1500 colliding streams, where c ~ 0.013 and |u| = 20)"""
+    ub = q[:4].reshape(4, -1).T
+    idx = np.random.default_rng(0).choice(len(ub), min(n, len(ub)), replace=False)
+    k = 1.0
+    for u in ub[idx]:
+        for d in (0, 1):
+            L, R = O.eigen(u, case.gamma, d)
+            k = max(k, np.abs(L).sum(1).max() * np.abs(R).sum(1).max())
+    return k
+
+
+def res_tol(case, q):
+    """1e-12, or cond * 2^-52 where the characteristic projection is ill-conditioned"""
+    return max(RES_TOL, char_condition(case, q) * 2.0 ** -52)
 
 
 def rel_l1(a, b):
@@ -73,8 +120,9 @@ def test_residual_parity(name):
     case, q = CASES[name]()
     g = gpu_residual(case, q)
     o = O.residual(ocfg(case), q)
-    assert rel_linf(g["rhs"], o["rhs"]) <= RES_TOL
-    assert rel_linf(g["vhat"], o["vhat"]) <= RES_TOL
+    assert res_tol(case, q) == RES_TOL
+    assert rel_linf(g["rhs"], o["rhs"], flux_scale(case, q)) <= RES_TOL
+    assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= RES_TOL
     assert abs(g["diag"]["alpha_star"] - o["diag"][0]) <= 1e-13 * o["diag"][0]
     assert abs(g["diag"]["beta_max"] - o["diag"][1]) <= 1e-12 * o["diag"][1]
 
@@ -84,8 +132,8 @@ def test_intermediate_fields_parity():
     case, q = I.random_rough(40, 36, seed=7, bc=("noslip", "symmetry", "periodic", "periodic"))
     g = gpu_residual(case, q, dumps=(0, 1, 2, 3, 4))
     o = O.residual(ocfg(case), q, dumps=True)
-    assert rel_linf(g[0], o["face"]) <= RES_TOL
-    assert rel_linf(g[1], o["vol"]) <= RES_TOL
+    assert rel_linf(g[0], o["face"], state_scale(q)) <= RES_TOL
+    assert rel_linf(g[1], o["vol"], state_scale(q)) <= RES_TOL
     assert rel_linf(g[2], o["rm"]) <= RES_TOL
     assert rel_linf(g[3], o["grad"]) <= RES_TOL
     assert np.abs(g[4] - o["theta"]).max() <= 1e-13
@@ -103,24 +151,26 @@ def _far_from(mask, r):
 
 def test_limiter_engaged_parity():
     """Near-vacuum colliding streams: the limiter clips face pressures to eps_PP, where
-    the residual is ill-conditioned (the wave-speed bound scales with e^-1/2 at
-    e ~ 1e-12).  Cells whose 9x9 dependency square contains no limited cell match to
-    1e-12; the limited cells satisfy the limiter's guarantees and theta matches."""
+    the residual is ill-conditioned (the PP wave-speed bound grows like 1/e at
+    e ~ 1e-12).  Cells whose 9x9 dependency square holds no limited cell match to
+    1e-12, the modified moments (never limited) match everywhere, the limited face
+    states keep rho, p >= eps_PP, and the set of limited cells is the oracle's."""
     case, q = I.colliding_streams(48, seed=3)
     g = gpu_residual(case, q, dumps=(0, 4))
     o = O.residual(ocfg(case), q, dumps=True)
     limited = (o["theta"][0] < 1) | (o["theta"][1] < 1)
-    assert limited.any() and g["diag"]["pp_active"] == 0  # residual calls do not count steps
+    assert limited.any() and res_tol(case, q) > RES_TOL
     far = _far_from(limited, 4)
     assert far.any()
-    assert rel_linf(g["rhs"], o["rhs"], far) <= RES_TOL
-    assert rel_linf(g["vhat"], o["vhat"]) <= RES_TOL  # moments are never limited
+    tol = res_tol(case, q)
+    assert rel_linf(g["rhs"], o["rhs"], flux_scale(case, q), far) <= tol
+    assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= tol
     gam = case.gamma
     face = g[0].reshape(12, 4, 48, 48)
     p = (gam - 1) * (face[:, 3] - 0.5 * (face[:, 1] ** 2 + face[:, 2] ** 2) / face[:, 0])
-    assert face[:, 0].min() > 0 and p.min() >= 1e-12 - 1e-12 * np.abs(face[:, 3]).max()
-    assert np.array_equal(g[4][0] < 1, o["theta"][0] < 1) or np.abs(g[4] - o["theta"]).max() < 1e-9
-    assert np.abs(g[4] - o["theta"]).max() < 1e-6
+    assert face[:, 0].min() > 0 and p.min() >= 1e-12 - 1e-13 * np.abs(face[:, 3]).max()
+    glim = (g[4][0] < 1) | (g[4][1] < 1)
+    assert np.array_equal(glim, limited)
 
 
 def _sample_cells(case, n, seed):
@@ -155,14 +205,9 @@ def test_full_size_sampled_parity(name):
     limited = (g[4][0] < 1) | (g[4][1] < 1)
     keep = np.array([not limited[max(0, j - 4):j + 5, max(0, i - 4):i + 5].any() for i, j in zip(ci, cj)])
     assert keep.sum() > 0.5 * len(ci)
-    a = g["rhs"][:, cj, ci][:, keep]
-    b = rhs.T[:, keep]
-    scale = np.abs(g["rhs"]).reshape(12, -1).max(1)
-    err = (np.abs(a - b).max(1) / np.where(scale > 0, scale, 1.0)).max()
-    assert err <= RES_TOL, err
-    a = g["vhat"][:, cj, ci]
-    scale = np.abs(g["vhat"]).reshape(8, -1).max(1)
-    assert (np.abs(a - vh.T).max(1) / np.where(scale > 0, scale, 1.0)).max() <= RES_TOL
+    tol = res_tol(case, q)
+    assert rel_linf(g["rhs"][:, cj, ci][:, keep], rhs.T[:, keep], flux_scale(case, q)) <= tol
+    assert rel_linf(g["vhat"][:, cj, ci], vh.T, state_scale(q)) <= tol
 
 
 def test_step_parity_fixed_and_rule_dt():
@@ -173,11 +218,11 @@ def test_step_parity_fixed_and_rule_dt():
     dt, rej = s.step(2e-3)
     assert dt == 2e-3 and rej == 0
     qo, st = O.step(cfg, q, dt_fixed=2e-3)
-    assert rel_linf(s.get_state().cpu().numpy(), qo) <= 1e-11
+    assert rel_linf(s.get_state().cpu().numpy(), qo, state_scale(q)) <= 1e-12
     dt2, _ = s.step()
     qo2, st2 = O.step(cfg, qo)
     assert abs(dt2 - st2["dt"]) <= 1e-13 * st2["dt"]
-    assert rel_linf(s.get_state().cpu().numpy(), qo2) <= 1e-11
+    assert rel_linf(s.get_state().cpu().numpy(), qo2, state_scale(q)) <= 1e-12
     s.close()
 
 
@@ -198,18 +243,35 @@ def test_full_run_smooth_periodic():
 
 
 def test_restart_on_inadmissible_stage():
-    """A forced step far above the stable size drives a stage inadmissible; the step
-    is repeated from t^n with dt/2 until admissible (Sec. 5), as in the oracle."""
-    case, q = I.colliding_streams(32, seed=3)
+    """A forced step eight times the largest stable size drives a stage of the shock
+    tube inadmissible; the step is repeated from t^n with dt/2 until admissible
+    (Sec. 5): three restarts, as in the oracle, and the same state."""
+    case, q = I.shock_tube(64, 32)
     cfg = ocfg(case)
     s = hweno.Solver(case.params())
     s.set_state(torch.from_numpy(q).cuda())
-    dt, rej = s.step(5e-3)
-    qo, st = O.step(cfg, q, dt_fixed=5e-3)
-    assert st["status"] == 0 and rej == st["rejections"] and rej > 0
-    assert dt == st["dt"]
-    a = s.get_state().cpu().numpy()
-    assert np.isfinite(a).all() and (a[0] > 0).all()
+    dt, rej = s.step(0.1)
+    qo, st = O.step(cfg, q, dt_fixed=0.1)
+    assert st["status"] == 0 and rej == st["rejections"] == 3
+    assert dt == st["dt"] == 0.0125
+    assert rel_linf(s.get_state().cpu().numpy(), qo, state_scale(q)) <= 1e-12
+    assert s.diag()["rejected"] == 3
+    s.close()
+
+
+def test_inadmissible_after_max_halvings_reports_error():
+    """The low-density state whose limited face pressures drive the PP wave-speed
+    bound to ~1e11 cannot be stepped within 20 halvings: the step fails with
+    HWENO_ERR_INADMISSIBLE and leaves the state at t^n, as the oracle reports."""
+    case, q = I.random_rough(32, 32, seed=2, low=0.01)
+    _, st = O.step(ocfg(case), q, dt_fixed=1e-3)
+    assert st["status"] == -3
+    s = hweno.Solver(case.params())
+    s.set_state(torch.from_numpy(q).cuda())
+    with pytest.raises(hweno.HwenoError) as e:
+        s.step(1e-3)
+    assert e.value.code == hweno.HWENO_ERR_INADMISSIBLE
+    assert np.array_equal(s.get_state().cpu().numpy(), q)
     s.close()
 
 
@@ -248,5 +310,5 @@ def test_mixed_precision_residual_error(name):
     case, q = CASES[name]()
     g = gpu_residual(case, q, precision="mixed")
     o = O.residual(ocfg(case), q)
-    assert rel_linf(g["rhs"][:4], o["rhs"][:4]) <= 2e-5
-    assert rel_linf(g["vhat"], o["vhat"]) <= 2e-5
+    assert rel_linf(g["rhs"], o["rhs"], flux_scale(case, q)) <= 1e-5
+    assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= 1e-6
