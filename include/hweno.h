@@ -180,6 +180,32 @@ int hweno_measure_peak(hweno_handle* h, int which, double* tflops);
  * (the count bench tools report as gpu_launches). */
 long long hweno_launch_count(const hweno_handle* h);
 
+/* The spatial operator of hweno_residual for callers that cannot allocate device
+ * memory while they run: programs whose device memory belongs to another allocator
+ * under a fixed budget (a framework's caching pool, a reserved arena), where an extra
+ * cudaMalloc can fail or fragment that budget, and latency-bound loops that cannot
+ * take cudaMalloc's implicit device-wide synchronisation.  The paper has no
+ * counterpart: this is a deployment variant of the same evaluation.
+ *
+ * No handle: cfg describes the problem as for hweno_init.  q [3][4][ny][nx] (the
+ * state layout above), rhs [3][4][ny][nx] and vhat [2][4][ny][nx] (or NULL) are
+ * caller-owned DEVICE buffers on the current device.  All intermediate fields live
+ * in one library-static device array of about 9.9 MB that every GPU loading the
+ * library holds until the process exits; the grid must satisfy
+ * (ny + 8) * round_up(nx + 8, 16) <= 4096 padded cells (for example 56 x 56 or
+ * 120 x 24), larger grids return HWENO_ERR_ARG with the sizes in the message.
+ * The call enqueues its work on `stream` (a cudaStream_t as void*, NULL = legacy
+ * default stream) and returns without waiting; it calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call on a device shares the one array and
+ * it keeps the previous call's contents: calls whose work overlaps on the GPU (two
+ * streams, or host threads without ordering) race and corrupt each other's
+ * results, so order them on one stream.  It does not report non-finite results.
+ * Errors (HWENO_ERR_ARG, HWENO_ERR_CUDA) are read with hweno_last_error(NULL). */
+int hweno_residual_noalloc(const hweno_config* cfg, const double* q, double* rhs, double* vhat,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

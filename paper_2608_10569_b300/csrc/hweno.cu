@@ -1045,3 +1045,121 @@ int hweno_measure_peak(hweno_handle* h, int which, double* tflops) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Residual evaluation that allocates nothing: inputs and outputs are the caller's
+// device buffers, and every intermediate plane lives in one library-static device
+// array.  For callers that may not allocate device memory once they are running:
+// programs whose device memory is owned by another allocator under a fixed budget
+// (a framework's caching pool, a reserved arena), where a cudaMalloc can fail or
+// fragment that budget, and latency-bound loops, where cudaMalloc's implicit
+// device-wide synchronisation is not acceptable.
+
+#include <mutex>
+
+namespace {
+// 12 state + 12 residual + 8 modified-moment planes, then the Work planes
+constexpr long long NOALLOC_PLANES = 12 + 12 + 8 + 48 + 36 + 3 + 6 + 6 + 18 + 126 + 12 + 12 + 2;
+// padded cells per plane: (ny + 8) * round_up(nx + 8, 16) may not exceed this
+// (for example grids up to 56 x 56, or 120 x 24)
+constexpr long long NOALLOC_MAX_PLANE = 4096;
+constexpr long long NOALLOC_DOUBLES = NOALLOC_PLANES * NOALLOC_MAX_PLANE + 16;  // + Diag
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address of the array, per device
+std::mutex g_noalloc_mu;
+}  // namespace
+
+// about 9.9 MB on every device that loads the library, held until the process exits
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+// host code cannot use g_noalloc_scratch as a device pointer: look its address up
+// once per device, with that device current
+static int noalloc_scratch_address(double** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "hweno_residual_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+    return fail(nullptr, HWENO_ERR_ARG, "hweno_residual_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(nullptr, e, "hweno_residual_noalloc: cudaGetSymbolAddress");
+    g_noalloc_addr[dev] = (double*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HWENO_OK;
+}
+
+static int noalloc_check_config(const hweno_config& c) {
+  if (c.nx < 4 || c.ny < 4) return fail(nullptr, HWENO_ERR_ARG, "nx and ny must be >= 4");
+  if (!(c.x1 > c.x0) || !(c.y1 > c.y0)) return fail(nullptr, HWENO_ERR_ARG, "empty domain");
+  if (!(c.gamma > 1.0) || !(c.Pr > 0.0) || !(c.Re > 0.0))
+    return fail(nullptr, HWENO_ERR_ARG, "need gamma > 1, Pr > 0, Re > 0");
+  for (int k = 0; k < 4; k++)
+    if (!valid_bc(c.bc[k])) return fail(nullptr, HWENO_ERR_ARG, "unknown boundary condition");
+  if ((c.bc[0] == HWENO_BC_PERIODIC) != (c.bc[1] == HWENO_BC_PERIODIC) ||
+      (c.bc[2] == HWENO_BC_PERIODIC) != (c.bc[3] == HWENO_BC_PERIODIC))
+    return fail(nullptr, HWENO_ERR_ARG, "periodic boundaries must be set on both sides");
+  if (!(c.eps_pp > 0.0) || !(c.eps_weno > 0.0)) return fail(nullptr, HWENO_ERR_ARG, "eps_pp, eps_weno must be > 0");
+  if (c.precision != HWENO_FP64 && c.precision != HWENO_MIXED)
+    return fail(nullptr, HWENO_ERR_ARG, "precision must be HWENO_FP64 or HWENO_MIXED");
+  if (c.scheme != 0 || c.reserved != 0) return fail(nullptr, HWENO_ERR_ARG, "scheme must be 0 (HWENO-GR)");
+  return HWENO_OK;
+}
+
+extern "C" int hweno_residual_noalloc(const hweno_config* cfg, const double* q, double* rhs, double* vhat,
+                                      void* stream) {
+  if (!cfg || !q || !rhs) return fail(nullptr, HWENO_ERR_ARG, "hweno_residual_noalloc: NULL argument");
+  int rc = noalloc_check_config(*cfg);
+  if (rc) return rc;
+  const hweno_config& c = *cfg;
+  Grid g;
+  g.nx = c.nx;
+  g.ny = c.ny;
+  g.pitch = ((c.nx + 2 * NG + 15) / 16) * 16;
+  g.ps = (long long)(c.ny + 2 * NG) * g.pitch;
+  if (g.ps > NOALLOC_MAX_PLANE) {
+    char buf[256];
+    snprintf(buf, sizeof(buf),
+             "hweno_residual_noalloc: grid %d x %d needs %lld padded cells per plane, the static "
+             "scratch holds %lld ((ny + 8) * round_up(nx + 8, 16) must be <= %lld)",
+             c.nx, c.ny, g.ps, NOALLOC_MAX_PLANE, NOALLOC_MAX_PLANE);
+    return fail(nullptr, HWENO_ERR_ARG, buf);
+  }
+  g.dx = (c.x1 - c.x0) / c.nx;
+  g.dy = (c.y1 - c.y0) / c.ny;
+  g.gamma = c.gamma; g.Pr = c.Pr; g.Re = c.Re;
+  g.eps_pp = c.eps_pp; g.eps_weno = c.eps_weno;
+  for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
+
+  double* base = nullptr;
+  if ((rc = noalloc_scratch_address(&base))) return rc;
+  // the same spatial operator as hweno_residual, on a stack handle whose planes all
+  // point into the static array (no profiling, so the handle allocates nothing)
+  hweno_handle tmp;
+  tmp.cfg = c;
+  tmp.st = (cudaStream_t)stream;
+  tmp.g = g;
+  double* p = base;
+  auto take = [&](long long n) { double* r = p; p += n * g.ps; return r; };
+  double* Q = take(12);
+  double* R = take(12);
+  double* M = take(8);
+  tmp.w.face = take(48); tmp.w.vol = take(36); tmp.w.wbar = take(3); tmp.w.wx = take(6); tmp.w.wy = take(6);
+  tmp.w.rm = take(18); tmp.w.gr = take(126); tmp.w.fx = take(12); tmp.w.fy = take(12); tmp.w.theta = take(2);
+  tmp.d_diag = reinterpret_cast<Diag*>(p);
+  tmp.prof = false;
+  // the reductions accumulate into the Diag words: they start from zero on every call;
+  // every other plane is written before it is read within the call
+  cudaError_t e = cudaMemsetAsync(tmp.d_diag, 0, sizeof(Diag), tmp.st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "hweno_residual_noalloc: clearing the reductions");
+  k_scatter<<<256, 256, 0, tmp.st>>>(g, 12, q, Q);
+  rc = residual_eval(&tmp, Q, R, M);
+  if (rc) return fail(nullptr, rc, tmp.err);
+  k_gather<<<256, 256, 0, tmp.st>>>(g, 12, R, rhs);
+  if (vhat) k_gather<<<256, 256, 0, tmp.st>>>(g, 8, M, vhat);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "hweno_residual_noalloc: launch");
+  return HWENO_OK;
+}

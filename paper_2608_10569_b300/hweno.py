@@ -78,6 +78,8 @@ SIGNATURES = [
     ("hweno_profile_read", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D]),
     ("hweno_launch_count", ctypes.c_longlong, [_H]),
     ("hweno_measure_peak", ctypes.c_int, [_H, ctypes.c_int, _D]),
+    ("hweno_residual_noalloc", ctypes.c_int, [ctypes.POINTER(hweno_config), ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 ]
 
 
