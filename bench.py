@@ -39,12 +39,14 @@ sys.path.insert(0, ROOT)
 METRIC = "Gcell-RK-stage/s"
 WORKLOAD = "viscous shock tube 1024x512, no-slip walls + symmetry, Re 1000, Pr 0.73, SSP-RK3 under the CFL/viscous step rule"
 
-# Algorithmic FP64 flops per interior cell of one launch of each spatial-operator
-# kernel (an FMA counts 2, a division or square root counts 1), counted from the
-# kernels' arithmetic; the halo ring the launch also processes is not counted.
+# FP64 flops per cell of one launch of the two reconstruction kernels: executed
+# DADD + DMUL + 2 DFMA counted by ncu on the 256x128 shock tube, divided by the
+# cells the launch processes (profiles/fp64_op_counts_shock_tube_256x128.md).
+# `achieved` multiplies them by the INTERIOR cells only, so the halo ring each launch
+# also reconstructs (interior grown by 3, resp. 1) is not credited.
 FLOPS_PER_CELL_FP64 = {
-    "cons_recon": None,   # filled from the op count, see profiles/
-    "grad_recon": None,
+    "cons_recon": 5904.0,
+    "grad_recon": 3928.0,
 }
 
 
