@@ -45,8 +45,8 @@ WORKLOAD = "viscous shock tube 1024x512, no-slip walls + symmetry, Re 1000, Pr 0
 # `achieved` multiplies them by the INTERIOR cells only, so the halo ring each launch
 # also reconstructs (interior grown by 3, resp. 1) is not credited.
 FLOPS_PER_CELL_FP64 = {
-    "cons_recon": 5904.0,
-    "grad_recon": 3928.0,
+    "cons_recon": 5011.0,
+    "grad_recon": 3108.0,
 }
 
 
@@ -279,11 +279,14 @@ def main():
         peak32 = m.measure_peak(1)
         m.set_state(qd)
         torch.cuda.synchronize()
+        m.profile(True)
         ev0.record(stream)
         for _ in range(args.steps):
             m.step()
         ev1.record(stream)
         torch.cuda.synchronize()
+        mprof = m.profile_read()
+        m.profile(False)
         mms = max_over_ranks(ws, ev0.elapsed_time(ev1))
         qm = m.get_state().cpu().numpy()
         # L1 error against the FP64 path after the same number of steps from the same state
@@ -298,7 +301,8 @@ def main():
         linf = float(np.abs(qm[0] - q64[0]).max() / np.abs(q64[0]).max())
         mixed = {"value": ws * cells * stages / (mms * 1e-3) / 1e9, "unit": METRIC,
                  "ms_per_step": mms / args.steps, "fp32_peak_tflops": peak32,
-                 "rel_l1_rho_vs_fp64": l1, "rel_linf_rho_vs_fp64": linf}
+                 "rel_l1_rho_vs_fp64": l1, "rel_linf_rho_vs_fp64": linf,
+                 "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in mprof.items()}}
         m.close()
 
     # ---- CPU baseline: the oracle on the host cores --------------------------------

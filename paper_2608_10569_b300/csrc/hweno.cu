@@ -30,42 +30,42 @@ __global__ void __launch_bounds__(BX * BY) k_cons(Grid g, const double* __restri
   unsigned long long pp = 0;
   unsigned int flags = 0;
   if (i < g.nx + 3 && j < g.ny + 3) {
+    constexpr bool OFF = sizeof(T) == 4;  // FP32: reconstruct offsets from the average
     const long long c = cidx(g, i, j);
     double ub[4];
-    T cc[4][15], sl[4][4];
+    T cc[4][15], sl[4][4], ctr[4];
 #pragma unroll
     for (int v = 0; v < 4; v++) {
       double d[17];
-      gather17(g, q, v, i, j, d);
+      gather17<OFF>(g, q, v, i, j, d);
       ub[v] = q[(long long)v * g.ps + c];
       T dt[17];
 #pragma unroll
       for (int k = 0; k < 17; k++) dt[k] = (T)d[k];
       hw_p0_coeffs<T>(dt, cc[v]);
-      sl[v][0] = -dt[3];
-      sl[v][1] = dt[5];
-      sl[v][2] = -dt[1];
-      sl[v][3] = dt[7];
+      sl[v][0] = (T)(d[4] - d[3]);
+      sl[v][1] = (T)(d[5] - d[4]);
+      sl[v][2] = (T)(d[4] - d[1]);
+      sl[v][3] = (T)(d[7] - d[4]);
+      ctr[v] = OFF ? T(0) : (T)ub[v];
     }
     const T ut[4] = {(T)ub[0], (T)ub[1], (T)ub[2], (T)ub[3]};
     const T eps = (T)g.eps_weno;
     double face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
-    {
-      Eigen<T> e;
-      euler_eigen<T>(ut, (T)g.gamma, 0, e);
-      recon_dir<T, 0>(cc, sl, e, eps, face, volx, mx);
-    }
-    {
-      Eigen<T> e;
-      euler_eigen<T>(ut, (T)g.gamma, 1, e);
-      recon_dir<T, 1>(cc, sl, e, eps, face + 6, vol, my);
-    }
+    CharState<T> cs;
+    char_state<T>(ut, (T)g.gamma, cs);
+    recon_dir<T, 0>(cc, sl, ctr, cs, eps, face, volx, mx);
+    recon_dir<T, 1>(cc, sl, ctr, cs, eps, face + 6, vol, my);
 #pragma unroll
     for (int v = 0; v < 4; v++) {
 #pragma unroll
-      for (int k = 0; k < 12; k++) face[k][v] += ub[v];
+      for (int k = 0; k < 12; k++)
+        if (OFF) face[k][v] += ub[v];
 #pragma unroll
-      for (int k = 0; k < 9; k++) vol[k][v] = 0.5 * (volx[k][v] + vol[k][v]) + ub[v];
+      for (int k = 0; k < 9; k++) {
+        vol[k][v] = 0.5 * (volx[k][v] + vol[k][v]);
+        if (OFF) vol[k][v] += ub[v];
+      }
     }
     double th[2] = {1.0, 1.0};
     const double pb = pressure(ub, g.gamma);
@@ -198,13 +198,14 @@ __global__ void __launch_bounds__(BX * BY) k_grad(Grid g, Work w) {
     const double* A = w.rm + (long long)(6 * n + 3 * l) * g.ps;
     const double* X = A + g.ps;
     const double* Y = A + 2 * g.ps;
-    const double cen = A[c];
+    constexpr bool OFF = sizeof(T) == 4;  // FP32: reconstruct offsets from the centre value
+    const double cen = OFF ? A[c] : 0.0;
     T d[17];
 #pragma unroll
     for (int b = -1; b <= 1; b++)
 #pragma unroll
       for (int a = -1; a <= 1; a++) d[(b + 1) * 3 + (a + 1)] = (T)(A[cidx(g, i + a, j + b)] - cen);
-    d[4] = T(0);
+    if (OFF) d[4] = T(0);
     d[9] = (T)X[cidx(g, i - 1, j)];
     d[10] = (T)X[cidx(g, i + 1, j)];
     d[11] = (T)Y[cidx(g, i, j - 1)];
@@ -220,12 +221,13 @@ __global__ void __launch_bounds__(BX * BY) k_grad(Grid g, Work w) {
     eval_yfaces<T>(C, vy);
     eval_vol<T>(C, vv);
     double* out = w.gr + (long long)comp * g.ps + c;
+    // FP64: the values themselves; FP32: offsets, restored in FP64
 #pragma unroll
-    for (int k = 0; k < 6; k++) out[(long long)(6 * k) * g.ps] = cen + (double)vx[k];
+    for (int k = 0; k < 6; k++) out[(long long)(6 * k) * g.ps] = OFF ? cen + (double)vx[k] : (double)vx[k];
 #pragma unroll
-    for (int k = 0; k < 6; k++) out[(long long)(6 * (6 + k)) * g.ps] = cen + (double)vy[k];
+    for (int k = 0; k < 6; k++) out[(long long)(6 * (6 + k)) * g.ps] = OFF ? cen + (double)vy[k] : (double)vy[k];
 #pragma unroll
-    for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = cen + (double)vv[k];
+    for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = OFF ? cen + (double)vv[k] : (double)vv[k];
   }
 }
 

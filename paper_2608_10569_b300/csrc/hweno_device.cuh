@@ -31,56 +31,77 @@ template <class T>
 __device__ __forceinline__ T gnode(int g) { return T(g - 1) * T(GN); }
 
 // ---------------------------------------------------------------------------
-// scalar unified-stencil HWENO on offset data.
-// d[0..8]: averages minus the centre average (so d[4] == 0), d[9..16]: the eight
-// first moments in the order of hweno_stencil.h.  Returns the coefficients C of the
-// nonlinear combination w0 (p0/g0 - sum gm/g0 pm) + sum wm pm of Eq. (3.4), also
-// relative to the centre average.
-// c0: the quartic's coefficients; s = (dxm, dxp, dym, dyp): the one-sided
-// differences of the averages, centre minus left, right minus centre, centre minus
-// bottom, top minus centre.  The four linear candidates share the centre average and
-// take their slopes from S1={2,4,5}: (dxm, dym), S2={2,5,6}: (dxp, dym),
-// S3={4,5,8}: (dxm, dyp), S4={5,6,8}: (dxp, dyp).
+// scalar unified-stencil HWENO (Appendix A.2).
+// c0: the quartic's 15 coefficients; s = (dxm, dxp, dym, dyp): the one-sided
+// differences of the averages (centre minus left, right minus centre, centre minus
+// bottom, top minus centre); ctr: the centre average in the same representation as
+// c0 (zero when the data are offsets from it).  The four linear candidates share the
+// centre average and take their slopes from S1={2,4,5}: (dxm, dym), S2={2,5,6}:
+// (dxp, dym), S3={4,5,8}: (dxm, dyp), S4={5,6,8}: (dxp, dyp).  Writes the
+// coefficients C of the nonlinear combination w0 (p0/g0 - sum gm/g0 pm) + sum wm pm
+// of Eq. (3.4) with the weights of Eq. (A.6).
 template <class T>
-__device__ __forceinline__ void hweno_combine_coeffs(const T* c0, const T* s, T eps, T* C) {
+__device__ __forceinline__ void hweno_combine_coeffs(const T* c0, const T* s, T ctr, T eps, T* C) {
   const T dxm = s[0], dxp = s[1], dym = s[2], dyp = s[3];
   const T sxm = dxm * dxm, sxp = dxp * dxp, sym = dym * dym, syp = dyp * dyp;
-  T b[5];
-  b[0] = hw_beta_quartic<T>(c0);
-  b[1] = sxm + sym;
-  b[2] = sxp + sym;
-  b[3] = sxm + syp;
-  b[4] = sxp + syp;
-  T ts = fabs(b[0] - b[1]) + fabs(b[0] - b[2]) + fabs(b[0] - b[3]) + fabs(b[0] - b[4]);
-  ts = T(0.25) * ts;
+  const T b0 = hw_beta_quartic<T>(c0);
+  const T b1 = sxm + sym, b2 = sxp + sym, b3 = sxm + syp, b4 = sxp + syp;
+  const T e1 = b0 - b1, e2 = b0 - b2, e3 = b0 - b3, e4 = b0 - b4;
+  const T ts = T(0.25) * (fabs(e1) + fabs(e2) + fabs(e3) + fabs(e4));
   const T tau = ts * ts;
-  // t_m = tau/(beta_m + eps); omega_m = gamma_m (1 + t_m) / S.  The combination
-  // coefficients of Eq. (3.4) are then a0 = omega0/gamma0 = (1 + t0)/S and
-  // a_m = omega_m - a0 gamma_m = gamma_m (t_m - t0)/S for the linear candidates.
-  T t[5];
-#pragma unroll
-  for (int m = 0; m < 5; m++) t[m] = tau / (b[m] + eps);
-  const T wsum = T(GAM0) * (T(1) + t[0]) + T(GAML) * ((T(1) + t[1]) + (T(1) + t[2]) + (T(1) + t[3]) + (T(1) + t[4]));
-  const T rs = T(1) / wsum;
-  const T a0 = (T(1) + t[0]) * rs;
-  const T gl = T(GAML) * rs;
-  T a[4];
-#pragma unroll
-  for (int m = 0; m < 4; m++) a[m] = gl * (t[m + 1] - t[0]);
+  // omega_m = gamma_m (1 + tau/D_m) / S with D_m = beta_m + eps.  The combination
+  // coefficients of Eq. (3.4) are a0 = omega0/gamma0 and a_m = omega_m - a0 gamma_m.
+  T a0, a[4];
+  if constexpr (sizeof(T) == 8) {
+    // FP64: one reciprocal.  With P = prod D_k, Q_m = P/D_m and R_m = P/(D_0 D_m):
+    //   omega_m ~ gamma_m (P + tau Q_m),  a0 = (P + tau Q_0)/S',
+    //   a_m = gamma_m tau (Q_m - Q_0)/S' = gamma_m tau R_m (beta_0 - beta_m)/S',
+    //   S' = sum_m gamma_m (P + tau Q_m) = P + tau (gamma0 Q_0 + gammaL D_0 sum R_m).
+    // D_m >= eps = 1e-8, so P >= 1e-40 stays a normal double.
+    const T D0 = b0 + eps, D1 = b1 + eps, D2 = b2 + eps, D3 = b3 + eps, D4 = b4 + eps;
+    const T D12 = D1 * D2, D34 = D3 * D4;
+    const T R1 = D2 * D34, R2 = D1 * D34, R3 = D12 * D4, R4 = D12 * D3;
+    const T Q0 = D12 * D34;
+    const T P = D0 * Q0;
+    const T Sp = P + tau * (T(GAM0) * Q0 + T(GAML) * D0 * ((R1 + R2) + (R3 + R4)));
+    const T rs = T(1) / Sp;
+    a0 = (P + tau * Q0) * rs;
+    const T g = T(GAML) * tau * rs;
+    a[0] = g * R1 * e1;
+    a[1] = g * R2 * e2;
+    a[2] = g * R3 * e3;
+    a[3] = g * R4 * e4;
+  } else {
+    // FP32: the products above leave the float range for smooth data (eps^5 = 1e-40),
+    // so divide once per candidate: t_m = tau/D_m, a0 = (1 + t0)/S,
+    // a_m = gamma_m (t_m - t0)/S with S = gamma0 (1 + t0) + gammaL sum (1 + t_m).
+    const T t0 = tau / (b0 + eps), t1 = tau / (b1 + eps), t2 = tau / (b2 + eps);
+    const T t3 = tau / (b3 + eps), t4 = tau / (b4 + eps);
+    const T wsum = T(GAM0) * (T(1) + t0) + T(GAML) * ((T(4) + t1) + (t2 + t3) + t4);
+    const T rs = T(1) / wsum;
+    a0 = (T(1) + t0) * rs;
+    const T gl = T(GAML) * rs;
+    a[0] = gl * (t1 - t0);
+    a[1] = gl * (t2 - t0);
+    a[2] = gl * (t3 - t0);
+    a[3] = gl * (t4 - t0);
+  }
 #pragma unroll
   for (int k = 0; k < 15; k++) C[k] = a0 * c0[k];
-  // sum_m a_m = 1 - a0 multiplies the (zero) centre offset: nothing to add to C[0]
+  // the linear candidates' constant terms are the centre average; their weights sum
+  // to 1 - a0
+  C[0] += (T(1) - a0) * ctr;
   C[1] += (a[0] + a[2]) * dxm + (a[1] + a[3]) * dxp;
   C[2] += (a[0] + a[1]) * dym + (a[2] + a[3]) * dyp;
 }
 
-// scalar reconstruction from the 17 offset data (d[4] == 0)
+// scalar reconstruction from the 17 data in the order of hweno_stencil.h
 template <class T>
 __device__ __forceinline__ void hweno_combine(const T* d, T eps, T* C) {
   T c0[15];
   hw_p0_coeffs<T>(d, c0);
-  const T s[4] = {-d[3], d[5], -d[1], d[7]};
-  hweno_combine_coeffs<T>(c0, s, eps, C);
+  const T s[4] = {d[4] - d[3], d[5] - d[4], d[4] - d[1], d[7] - d[4]};
+  hweno_combine_coeffs<T>(c0, s, d[4], eps, C);
 }
 
 // ---------------------------------------------------------------------------
@@ -171,41 +192,62 @@ __device__ __forceinline__ void eval_vol(const T* c, T* out) {
 }
 
 // ---------------------------------------------------------------------------
-// eigenvectors of the Euler flux Jacobian at a state (direction dir = 0: x, 1: y).
-// Columns of R: waves u_n - c, u_n (entropy), shear, u_n + c; L = R^{-1}.
+// local characteristic fields of the Euler flux Jacobian at a state (Sec. 3.1).
+// Right eigenvectors in direction n (normal velocity un, tangential ut), columns in
+// the order u_n - c, u_n (entropy), shear, u_n + c:
+//   r1 = (1, un - c, ut, H - un c), r2 = (1, un, ut, q^2/2), r3 = (0, 0, 1, ut),
+//   r4 = (1, un + c, ut, H + un c)        (components ordered rho, m_n, m_t, E)
+// and L = R^{-1}.  Both maps are applied in factored form: with
+//   A = b2 x0 + b1 (x3 - un x_n - ut x_t),  B = (un x0 - x_n)/c,  b1 = (g-1)/c^2,
+//   b2 = b1 q^2/2:   y0 = (A + B)/2, y1 = x0 - A, y2 = x_t - ut x0, y3 = (A - B)/2,
+// and back  x0 = y0 + y1 + y3, x_n = un x0 + c (y3 - y0), x_t = ut x0 + y2,
+//           x3 = H (y0 + y3) + un c (y3 - y0) + q^2/2 y1 + ut y2.
 template <class T>
-struct Eigen {
-  T L[4][4];
-  T R[4][4];
+struct CharState {
+  T u, v, c, H, hq2;      // velocity, sound speed, total enthalpy, q^2/2
+  T hb1, hb2, hrc;        // b1/2, b2/2, 1/(2c)
 };
 
 template <class T>
-__device__ __forceinline__ void euler_eigen(const T* ub, T gamma, int dir, Eigen<T>& e) {
+__device__ __forceinline__ void char_state(const T* ub, T gamma, CharState<T>& s) {
   const T rr = T(1) / ub[0];
-  const T u = ub[1] * rr, v = ub[2] * rr;
-  const T q2 = u * u + v * v;
-  const T p = (gamma - T(1)) * (ub[3] - T(0.5) * ub[0] * q2);
+  s.u = ub[1] * rr;
+  s.v = ub[2] * rr;
+  s.hq2 = T(0.5) * (s.u * s.u + s.v * s.v);
+  const T p = (gamma - T(1)) * (ub[3] - ub[0] * s.hq2);
   const T c2 = gamma * p * rr;
-  const T c = sqrt(c2);
-  const T rc = T(1) / c;
-  const T H = (ub[3] + p) * rr;
-  const T b1 = (gamma - T(1)) / c2, b2 = T(0.5) * b1 * q2;
-  const T un = dir == 0 ? u : v, ut = dir == 0 ? v : u;
-  const int in = dir == 0 ? 1 : 2, it = dir == 0 ? 2 : 1;
-#pragma unroll
-  for (int a = 0; a < 4; a++)
-#pragma unroll
-    for (int b = 0; b < 4; b++) { e.L[a][b] = T(0); e.R[a][b] = T(0); }
-  e.R[0][0] = T(1); e.R[in][0] = un - c; e.R[it][0] = ut; e.R[3][0] = H - un * c;
-  e.R[0][1] = T(1); e.R[in][1] = un;     e.R[it][1] = ut; e.R[3][1] = T(0.5) * q2;
-  e.R[it][2] = T(1); e.R[3][2] = ut;
-  e.R[0][3] = T(1); e.R[in][3] = un + c; e.R[it][3] = ut; e.R[3][3] = H + un * c;
-  e.L[0][0] = T(0.5) * (b2 + un * rc); e.L[0][in] = T(-0.5) * (b1 * un + rc);
-  e.L[0][it] = T(-0.5) * b1 * ut;      e.L[0][3] = T(0.5) * b1;
-  e.L[1][0] = T(1) - b2; e.L[1][in] = b1 * un; e.L[1][it] = b1 * ut; e.L[1][3] = -b1;
-  e.L[2][0] = -ut; e.L[2][it] = T(1);
-  e.L[3][0] = T(0.5) * (b2 - un * rc); e.L[3][in] = T(0.5) * (rc - b1 * un);
-  e.L[3][it] = T(-0.5) * b1 * ut;      e.L[3][3] = T(0.5) * b1;
+  s.c = sqrt(c2);
+  s.H = (ub[3] + p) * rr;
+  const T b1 = (gamma - T(1)) / c2;
+  s.hb1 = T(0.5) * b1;
+  s.hb2 = s.hb1 * s.hq2;
+  s.hrc = T(0.5) / s.c;
+}
+
+// x (rho, m, n, E) -> characteristic y for direction DIR (0: x, 1: y)
+template <class T, int DIR>
+__device__ __forceinline__ void to_char(const CharState<T>& s, const T* x, T* y) {
+  const T un = DIR == 0 ? s.u : s.v, ut = DIR == 0 ? s.v : s.u;
+  const T xn = DIR == 0 ? x[1] : x[2], xt = DIR == 0 ? x[2] : x[1];
+  const T Ah = s.hb2 * x[0] + s.hb1 * (x[3] - un * xn - ut * xt);  // A/2
+  const T Bh = s.hrc * (un * x[0] - xn);                             // B/2
+  y[0] = Ah + Bh;
+  y[1] = x[0] - T(2) * Ah;
+  y[2] = xt - ut * x[0];
+  y[3] = Ah - Bh;
+}
+
+template <class T, int DIR>
+__device__ __forceinline__ void from_char(const CharState<T>& s, const T* y, T* x) {
+  const T un = DIR == 0 ? s.u : s.v, ut = DIR == 0 ? s.v : s.u;
+  const T x0 = y[0] + y[1] + y[3];
+  const T dd = y[3] - y[0];
+  const T xn = un * x0 + s.c * dd;
+  const T xt = ut * x0 + y[2];
+  x[0] = x0;
+  x[DIR == 0 ? 1 : 2] = xn;
+  x[DIR == 0 ? 2 : 1] = xt;
+  x[3] = s.H * (y[0] + y[3]) + (un * s.c) * dd + s.hq2 * y[1] + ut * y[2];
 }
 
 // ---------------------------------------------------------------------------

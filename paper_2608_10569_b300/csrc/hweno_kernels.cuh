@@ -138,19 +138,21 @@ __global__ void k_ghost_y(Grid g, double* q) {
 }
 
 // ---------------------------------------------------------------------------
-// gather the 17 data of one conserved variable (plane offset v) around (i, j)
-// in the order of hweno_stencil.h, as offsets from the centre average
+// gather the 17 data of one conserved variable (plane offset v) around (i, j) in the
+// order of hweno_stencil.h; with OFF the averages are taken relative to the centre
+// average (so d[4] == 0), which keeps the FP32 reconstruction accurate
+template <bool OFF>
 __device__ __forceinline__ void gather17(const Grid& g, const double* q, int v, int i, int j,
                                          double* d) {
   const double* A = q + (long long)v * g.ps;
   const double* X = q + (long long)(4 + v) * g.ps;
   const double* Y = q + (long long)(8 + v) * g.ps;
-  const double c = A[cidx(g, i, j)];
+  const double c = OFF ? A[cidx(g, i, j)] : 0.0;
 #pragma unroll
   for (int b = -1; b <= 1; b++)
 #pragma unroll
     for (int a = -1; a <= 1; a++) d[(b + 1) * 3 + (a + 1)] = A[cidx(g, i + a, j + b)] - c;
-  d[4] = 0.0;
+  if (OFF) d[4] = 0.0;
   d[9] = X[cidx(g, i - 1, j)];
   d[10] = X[cidx(g, i + 1, j)];
   d[11] = Y[cidx(g, i, j - 1)];
@@ -161,43 +163,63 @@ __device__ __forceinline__ void gather17(const Grid& g, const double* q, int v, 
   d[16] = Y[cidx(g, i + 1, j)];
 }
 
-// characteristic reconstruction of one direction: per field, project the
-// conserved p0 coefficients and slopes, form the nonlinear combination, evaluate
-// at this direction's 6 face points, the 9 volume points and the moment, and
-// transform back.  Outputs are offsets from the centre average (moments absolute).
+// characteristic reconstruction of one direction: per field, project the conserved
+// p0 coefficients, slopes and centre average (p0 is linear in the data, so these are
+// the coefficients of the projected data), form the nonlinear combination, evaluate
+// it at this direction's 6 face points, the 9 volume points and the moment, and
+// transform back.  cc, sl, ctr hold absolute values (FP64) or offsets from the centre
+// average (FP32, ctr = 0); the outputs are in the same representation (moments are
+// unaffected by the offset).
 template <class T, int DIR>
-__device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], const Eigen<T>& e,
-                                          T eps, double (*face)[4], double (*vol)[4], double* mom) {
+__device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], const T* ctr,
+                                          const CharState<T>& cs, T eps, double (*face)[4],
+                                          double (*vol)[4], double* mom) {
   T chf[4][6], chv[4][9], chm[4];
+  T pc[15][4], ps[4][4], pz[4];
+#pragma unroll
+  for (int k = 0; k < 15; k++) {
+    const T x[4] = {cc[0][k], cc[1][k], cc[2][k], cc[3][k]};
+    to_char<T, DIR>(cs, x, pc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const T x[4] = {sl[0][k], sl[1][k], sl[2][k], sl[3][k]};
+    to_char<T, DIR>(cs, x, ps[k]);
+  }
+  to_char<T, DIR>(cs, ctr, pz);
 #pragma unroll
   for (int f = 0; f < 4; f++) {
-    // the projected coefficients are those of the projected data: p0 is linear
-    T c0[15];
+    T c0[15], s[4], C[15];
 #pragma unroll
-    for (int k = 0; k < 15; k++)
-      c0[k] = e.L[f][0] * cc[0][k] + e.L[f][1] * cc[1][k] + e.L[f][2] * cc[2][k] + e.L[f][3] * cc[3][k];
-    // projected one-sided differences (dxm, dxp, dym, dyp)
-    T s[4];
+    for (int k = 0; k < 15; k++) c0[k] = pc[k][f];
 #pragma unroll
-    for (int k = 0; k < 4; k++)
-      s[k] = e.L[f][0] * sl[0][k] + e.L[f][1] * sl[1][k] + e.L[f][2] * sl[2][k] + e.L[f][3] * sl[3][k];
-    T C[15];
-    hweno_combine_coeffs<T>(c0, s, eps, C);
+    for (int k = 0; k < 4; k++) s[k] = ps[k][f];
+    hweno_combine_coeffs<T>(c0, s, pz[f], eps, C);
     if (DIR == 0) eval_xfaces<T>(C, chf[f]); else eval_yfaces<T>(C, chf[f]);
     eval_vol<T>(C, chv[f]);
     chm[f] = DIR == 0 ? hw_moment_xi<T>(C) : hw_moment_eta<T>(C);
   }
 #pragma unroll
-  for (int v = 0; v < 4; v++) {
+  for (int k = 0; k < 6; k++) {
+    const T y[4] = {chf[0][k], chf[1][k], chf[2][k], chf[3][k]};
+    T x[4];
+    from_char<T, DIR>(cs, y, x);
 #pragma unroll
-    for (int k = 0; k < 6; k++)
-      face[k][v] = (double)(e.R[v][0] * chf[0][k] + e.R[v][1] * chf[1][k] + e.R[v][2] * chf[2][k] +
-                            e.R[v][3] * chf[3][k]);
+    for (int v = 0; v < 4; v++) face[k][v] = (double)x[v];
+  }
 #pragma unroll
-    for (int k = 0; k < 9; k++)
-      vol[k][v] = (double)(e.R[v][0] * chv[0][k] + e.R[v][1] * chv[1][k] + e.R[v][2] * chv[2][k] +
-                           e.R[v][3] * chv[3][k]);
-    mom[v] = (double)(e.R[v][0] * chm[0] + e.R[v][1] * chm[1] + e.R[v][2] * chm[2] + e.R[v][3] * chm[3]);
+  for (int k = 0; k < 9; k++) {
+    const T y[4] = {chv[0][k], chv[1][k], chv[2][k], chv[3][k]};
+    T x[4];
+    from_char<T, DIR>(cs, y, x);
+#pragma unroll
+    for (int v = 0; v < 4; v++) vol[k][v] = (double)x[v];
+  }
+  {
+    T x[4];
+    from_char<T, DIR>(cs, chm, x);
+#pragma unroll
+    for (int v = 0; v < 4; v++) mom[v] = (double)x[v];
   }
 }
 
