@@ -14,6 +14,7 @@
 
 #include "hweno.h"
 #include "hweno_kernels.cuh"
+#include "hweno_mixed.cuh"
 
 namespace hw {
 
@@ -54,8 +55,8 @@ __global__ void __launch_bounds__(BX * BY) k_cons(Grid g, const double* __restri
     double face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
     CharState<T> cs;
     char_state<T>(ut, (T)g.gamma, cs);
-    recon_dir<T, 0>(cc, sl, ctr, cs, eps, face, volx, mx);
-    recon_dir<T, 1>(cc, sl, ctr, cs, eps, face + 6, vol, my);
+    recon_dir<T, 0, double>(cc, sl, ctr, cs, eps, face, volx, mx);
+    recon_dir<T, 1, double>(cc, sl, ctr, cs, eps, face + 6, vol, my);
 #pragma unroll
     for (int v = 0; v < 4; v++) {
 #pragma unroll
@@ -267,7 +268,10 @@ __global__ void __launch_bounds__(BX * BY) k_flux(Grid g, Work w, Diag* diag) {
         amax = fmax(amax, (double)fmax(fabs(st[s][gp][1]) + cs, fabs(st[s][gp][2]) + cs));
       }
     bmax = (double)beta;
-    double* out = (dir == 0 ? w.fx : w.fy) + cl;
+    // the moment balances use each face's fluxes only through the Gauss sums
+    // S0 = sum_g w_g fhat_g and S1 = sum_g w_g t_g fhat_g (t_g: the transverse Gauss
+    // offset): both cells read the same stored sums, so the telescoping is exact
+    T S0[4] = {T(0), T(0), T(0), T(0)}, S1[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
     for (int gp = 0; gp < 3; gp++) {
       T fl[4], fr[4], ul[4], ur[4];
@@ -282,9 +286,19 @@ __global__ void __launch_bounds__(BX * BY) k_flux(Grid g, Work w, Diag* diag) {
         u[2] = p[0] * p[2];
         u[3] = p[0] * (p[3] + T(0.5) * (p[1] * p[1] + p[2] * p[2]));
       }
+      const T wg = gweight<T>(gp), wt = gweight<T>(gp) * gnode<T>(gp);
 #pragma unroll
-      for (int v = 0; v < 4; v++)
-        out[(long long)(4 * gp + v) * g.ps] = (double)(T(0.5) * (fl[v] + fr[v] - beta * (ur[v] - ul[v])));
+      for (int v = 0; v < 4; v++) {
+        const T fh = T(0.5) * (fl[v] + fr[v] - beta * (ur[v] - ul[v]));
+        S0[v] += wg * fh;
+        if (gp != 1) S1[v] += wt * fh;
+      }
+    }
+    double* out = (dir == 0 ? w.fx : w.fy) + cl;
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      out[(long long)v * g.ps] = (double)S0[v];
+      out[(long long)(4 + v) * g.ps] = (double)S1[v];
     }
   }
   amax = warp_max(amax);
@@ -329,24 +343,14 @@ __global__ void __launch_bounds__(BX * BY) k_assemble(Grid g, Work w, double* __
     const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
 #pragma unroll
     for (int v = 0; v < 4; v++) {
-      double a = 0, b = 0, s1 = 0, s2 = 0, t1 = 0, t2 = 0;
-#pragma unroll
-      for (int gp = 0; gp < 3; gp++) {
-        const double wg = gweight<double>(gp), xg = gnode<double>(gp);
-        const double fR = w.fx[(long long)(4 * gp + v) * g.ps + c];
-        const double fL = w.fx[(long long)(4 * gp + v) * g.ps + cl];
-        const double gT = w.fy[(long long)(4 * gp + v) * g.ps + c];
-        const double gB = w.fy[(long long)(4 * gp + v) * g.ps + cb];
-        a += wg * (fR - fL);
-        b += wg * (gT - gB);
-        s1 += wg * (fL + fR);
-        s2 += wg * xg * (gT - gB);
-        t1 += wg * xg * (fR - fL);
-        t2 += wg * (gB + gT);
-      }
-      const double r0 = -a * rdx - b * rdy;
-      const double r1 = -s1 * (0.5 * rdx) - s2 * rdy + vf[v] * rdx;
-      const double r2 = -t1 * rdx - t2 * (0.5 * rdy) + vg[v] * rdy;
+      // face Gauss sums: S0 = sum w_g fhat_g, S1 = sum w_g t_g fhat_g (see k_flux)
+      const double fR0 = w.fx[(long long)v * g.ps + c], fL0 = w.fx[(long long)v * g.ps + cl];
+      const double fR1 = w.fx[(long long)(4 + v) * g.ps + c], fL1 = w.fx[(long long)(4 + v) * g.ps + cl];
+      const double gT0 = w.fy[(long long)v * g.ps + c], gB0 = w.fy[(long long)v * g.ps + cb];
+      const double gT1 = w.fy[(long long)(4 + v) * g.ps + c], gB1 = w.fy[(long long)(4 + v) * g.ps + cb];
+      const double r0 = -(fR0 - fL0) * rdx - (gT0 - gB0) * rdy;
+      const double r1 = -(fL0 + fR0) * (0.5 * rdx) - (gT1 - gB1) * rdy + vf[v] * rdx;
+      const double r2 = -(fR1 - fL1) * rdx - (gB0 + gT0) * (0.5 * rdy) + vg[v] * rdy;
       rhs[(long long)v * g.ps + c] = r0;
       rhs[(long long)(4 + v) * g.ps + c] = r1;
       rhs[(long long)(8 + v) * g.ps + c] = r2;
@@ -382,13 +386,14 @@ __global__ void k_rk(Grid g, int stage, const double* __restrict__ qin, const do
       } else if (stage == 2) {
         out[k] = 0.75 * base[(long long)k * g.ps + c] + 0.25 * (cur + dt * f);
       } else {
-        out[k] = base[(long long)k * g.ps + c] / 3.0 + 2.0 / 3.0 * (cur + dt * f);
+        out[k] = base[(long long)k * g.ps + c] * (1.0 / 3.0) + (2.0 / 3.0) * (cur + dt * f);
       }
       qout[(long long)k * g.ps + c] = out[k];
       if (!isfinite(out[k])) bad = FLAG_INADMISSIBLE;
     }
-    const double p = (g.gamma - 1.0) * (out[3] - 0.5 * (out[1] * out[1] + out[2] * out[2]) / out[0]);
-    if (!(out[0] > 0.0) || !(p > 0.0)) bad = FLAG_INADMISSIBLE;
+    // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
+    const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
+    if (!(out[0] > 0.0) || !(rp > 0.0)) bad = FLAG_INADMISSIBLE;
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0 && bad) atomicOr(&diag->flags, bad);
@@ -600,39 +605,61 @@ static void launch_ghost(hweno_handle* h, double* q) {
 // modified moments mom (8 planes)
 static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
   const Grid& g = h->g;
-  const bool mixed = h->cfg.precision == HWENO_MIXED;
   launch_ghost(h, q);
-  {
-    Prof p(h, K_CONS);
-    dim3 gr = grid2(g.nx + 6, g.ny + 6);
-    if (mixed) k_cons<float><<<gr, dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
-    else k_cons<double><<<gr, dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
-  }
-  {
-    Prof p(h, K_FACEMOM);
-    k_face_moments<<<grid2(g.nx + 5, g.ny + 5, 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
-  }
-  {
-    Prof p(h, K_WEAK);
-    k_weak_moments<<<grid2(g.nx + 4, g.ny + 4), dim3(BX, BY), 0, h->st>>>(g, h->w);
-  }
-  {
-    Prof p(h, K_GRAD);
-    dim3 gr = grid2(g.nx + 2, g.ny + 2);
-    if (mixed) k_grad<float><<<gr, dim3(BX, BY), 0, h->st>>>(g, h->w);
-    else k_grad<double><<<gr, dim3(BX, BY), 0, h->st>>>(g, h->w);
-  }
-  {
-    Prof p(h, K_FLUX);
-    dim3 gr = grid2(g.nx + 1, g.ny + 1, 2);
-    if (mixed) k_flux<float><<<gr, dim3(BX, BY), 0, h->st>>>(g, h->w, h->d_diag);
-    else k_flux<double><<<gr, dim3(BX, BY), 0, h->st>>>(g, h->w, h->d_diag);
-  }
-  {
-    Prof p(h, K_ASSEMBLE);
-    dim3 gr = grid2(g.nx, g.ny);
-    if (mixed) k_assemble<float><<<gr, dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
-    else k_assemble<double><<<gr, dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
+  if (h->cfg.precision == HWENO_MIXED) {
+    {
+      Prof p(h, K_GHOST);
+      k_split<<<4 * 148, 256, 0, h->st>>>(g, q, mixed_planes(h->w, g.ps).hilo);
+    }
+    {
+      Prof p(h, K_CONS);
+      k_cons_mixed<<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
+    }
+    {
+      Prof p(h, K_FACEMOM);
+      k_face_moments_mixed<<<grid2(g.nx + 5, g.ny + 5, 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+    }
+    {
+      Prof p(h, K_WEAK);
+      k_weak_moments_mixed<<<grid2(g.nx + 4, g.ny + 4), dim3(BX, BY), 0, h->st>>>(g, h->w);
+    }
+    {
+      Prof p(h, K_GRAD);
+      k_grad_mixed<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+    }
+    {
+      Prof p(h, K_FLUX);
+      k_flux_mixed<<<grid2(g.nx + 1, g.ny + 1, 2), dim3(BX, BY), 0, h->st>>>(g, h->w, h->d_diag);
+    }
+    {
+      Prof p(h, K_ASSEMBLE);
+      k_assemble_mixed<<<grid2(g.nx, g.ny), dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
+    }
+  } else {
+    {
+      Prof p(h, K_CONS);
+      k_cons<double><<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
+    }
+    {
+      Prof p(h, K_FACEMOM);
+      k_face_moments<<<grid2(g.nx + 5, g.ny + 5, 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+    }
+    {
+      Prof p(h, K_WEAK);
+      k_weak_moments<<<grid2(g.nx + 4, g.ny + 4), dim3(BX, BY), 0, h->st>>>(g, h->w);
+    }
+    {
+      Prof p(h, K_GRAD);
+      k_grad<double><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+    }
+    {
+      Prof p(h, K_FLUX);
+      k_flux<double><<<grid2(g.nx + 1, g.ny + 1, 2), dim3(BX, BY), 0, h->st>>>(g, h->w, h->d_diag);
+    }
+    {
+      Prof p(h, K_ASSEMBLE);
+      k_assemble<double><<<grid2(g.nx, g.ny), dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "spatial operator launch");
@@ -973,15 +1000,35 @@ int hweno_debug_fields(hweno_handle* h, int which, double* out, int on_device) {
   if (!h->have_residual) return fail(h, HWENO_ERR_STATE, "hweno_debug_fields before hweno_residual");
   const Grid& g = h->g;
   const long long N = (long long)g.nx * g.ny;
-  if (which <= 1) {
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (h->cfg.precision == HWENO_MIXED && which <= 3) {
+    // FP32 intermediates of the mixed path, widened to FP64
+    const WorkF f = mixed_planes(h->w, g.ps);
+    if (which <= 1) {
+      const int npts = which == 0 ? 12 : 9;
+      const float* src = which == 0 ? f.face : f.vol;
+      for (int k = 0; k < npts; k++) {
+        k_gather_cons_f<<<256, 256, 0, h->st>>>(g, src + (long long)4 * k * g.ps, h->STAGE);
+        h->launches++;
+        CK(cudaMemcpyAsync(out + 4 * k * N, h->STAGE, 4 * N * sizeof(double), kind, h->st), "debug copy");
+      }
+    } else {
+      const int n = which == 2 ? 18 : 126;
+      const float* src = which == 2 ? f.rm : f.gr;
+      for (int k = 0; k < n; k += 4) {
+        const int m = n - k < 4 ? n - k : 4;
+        k_gather_f<<<256, 256, 0, h->st>>>(g, m, src + (long long)k * g.ps, h->STAGE);
+        h->launches++;
+        CK(cudaMemcpyAsync(out + (long long)k * N, h->STAGE, m * N * sizeof(double), kind, h->st), "debug copy");
+      }
+    }
+  } else if (which <= 1) {
     const int npts = which == 0 ? 12 : 9;
     const double* src = which == 0 ? h->w.face : h->w.vol;
     for (int k = 0; k < npts; k++) {
       k_gather_cons<<<256, 256, 0, h->st>>>(g, 1, src + (long long)4 * k * g.ps, h->STAGE);
       h->launches++;
-      CK(cudaMemcpyAsync(out + 4 * k * N, h->STAGE, 4 * N * sizeof(double),
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st),
-         "debug copy");
+      CK(cudaMemcpyAsync(out + 4 * k * N, h->STAGE, 4 * N * sizeof(double), kind, h->st), "debug copy");
     }
   } else {
     const int n = which == 2 ? 18 : (which == 3 ? 126 : 2);

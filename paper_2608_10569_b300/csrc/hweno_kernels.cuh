@@ -46,8 +46,9 @@ struct Work {
   double* wy;     // 6 planes at the y-face above a cell
   double* rm;     // 18 planes: 6*w + (x0, x_xi, x_eta, y0, y_xi, y_eta)
   double* gr;     // 126 planes: point k (0..20) x (u_x, u_y, v_x, v_y, e_x, e_y)
-  double* fx;     // 12 planes: x-face right of a cell, Gauss point g x variable v
-  double* fy;     // 12 planes: y-face above a cell
+  double* fx;     // x-face right of a cell: planes 0-3 S0 = sum_g w_g fhat_g, 4-7
+                  // S1 = sum_g w_g eta_g fhat_g, per conserved variable (12 allocated)
+  double* fy;     // y-face above a cell: the same with xi_g
   double* theta;  // 2 planes: limiter factors
 };
 
@@ -170,10 +171,10 @@ __device__ __forceinline__ void gather17(const Grid& g, const double* q, int v, 
 // transform back.  cc, sl, ctr hold absolute values (FP64) or offsets from the centre
 // average (FP32, ctr = 0); the outputs are in the same representation (moments are
 // unaffected by the offset).
-template <class T, int DIR>
+template <class T, int DIR, class O>
 __device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], const T* ctr,
-                                          const CharState<T>& cs, T eps, double (*face)[4],
-                                          double (*vol)[4], double* mom) {
+                                          const CharState<T>& cs, T eps, O (*face)[4], O (*vol)[4],
+                                          O* mom) {
   T chf[4][6], chv[4][9], chm[4];
   T pc[15][4], ps[4][4], pz[4];
 #pragma unroll
@@ -205,7 +206,7 @@ __device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], c
     T x[4];
     from_char<T, DIR>(cs, y, x);
 #pragma unroll
-    for (int v = 0; v < 4; v++) face[k][v] = (double)x[v];
+    for (int v = 0; v < 4; v++) face[k][v] = (O)x[v];
   }
 #pragma unroll
   for (int k = 0; k < 9; k++) {
@@ -213,13 +214,13 @@ __device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], c
     T x[4];
     from_char<T, DIR>(cs, y, x);
 #pragma unroll
-    for (int v = 0; v < 4; v++) vol[k][v] = (double)x[v];
+    for (int v = 0; v < 4; v++) vol[k][v] = (O)x[v];
   }
   {
     T x[4];
     from_char<T, DIR>(cs, chm, x);
 #pragma unroll
-    for (int v = 0; v < 4; v++) mom[v] = (double)x[v];
+    for (int v = 0; v < 4; v++) mom[v] = (O)x[v];
   }
 }
 

@@ -1,0 +1,510 @@
+// Mixed-precision spatial operator: reconstruction, weights, gradients and fluxes
+// in FP32; the stored state, the positivity limiter's checks and theta solve where
+// they can bind, the face-flux differences of the moment balances and the RK update
+// in FP64.
+//
+// FP32 intermediates share the handle's scratch planes: a float plane k of a group
+// starts at (float*)group + k * ps, so a group of n double planes holds 2n float
+// planes.  The state is split once per evaluation into float planes hi = fl(q) and
+// lo = fl(q - hi) (stored after the 48 float face planes, in the face group's unused
+// half), so offsets from a cell's own average, (hi_k - hi_c) + (lo_k - lo_c), are
+// exact to FP32 rounding of the offset itself rather than of the average.
+#pragma once
+#include "hweno_kernels.cuh"
+
+namespace hw {
+
+struct WorkF {
+  float* face;   // 48: point k x (rho, u, v, e), limited
+  float* vol;    // 36: point k x (rho, u, v, e)
+  float* wbar;   // 3
+  float* wx;     // 6
+  float* wy;     // 6
+  float* rm;     // 18
+  float* gr;     // 126
+  float* hilo;   // 24: hi of the 12 state planes, then lo
+};
+
+__host__ __device__ inline WorkF mixed_planes(const Work& w, long long ps) {
+  WorkF f;
+  f.face = (float*)w.face;
+  f.hilo = (float*)w.face + 48 * ps;
+  f.vol = (float*)w.vol;
+  f.wbar = (float*)w.wbar;
+  f.wx = (float*)w.wx;
+  f.wy = (float*)w.wy;
+  f.rm = (float*)w.rm;
+  f.gr = (float*)w.gr;
+  return f;
+}
+
+// hi/lo split of the 12 ghost-filled state planes (whole padded planes), with integer
+// operations only: hi keeps the sign, the exponent and the leading 23 mantissa bits of
+// x (truncation), lo is the float nearest below the exact remainder x - hi (the trailing
+// 29 mantissa bits, normalised).  Zero gives (0, 0); magnitudes below 2^-74 or beyond
+// the float range take hi = fl(x), lo = 0.
+__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7ff);
+  const int fe = E - 1023 + 127;
+  if (E == 0) {  // zero (or a double denormal, below any float): signed zero
+    hi = __int_as_float((int)sign);
+    lo = 0.0f;
+    return;
+  }
+  // the remainder's float exponent field is fe - 52 + top >= fe - 52: keep it >= 1
+  if (fe < 53 || fe > 254) {  // |x| < 2^-74, beyond the float range, inf or nan
+    hi = (float)x;
+    lo = 0.0f;
+    return;
+  }
+  const unsigned long long m = b & 0xfffffffffffffull;
+  hi = __int_as_float((int)(sign | ((unsigned int)fe << 23) | (unsigned int)(m >> 29)));
+  const unsigned int r = (unsigned int)(m & 0x1fffffffull);  // remainder: r * 2^(E - 1075)
+  if (r == 0u) {
+    lo = 0.0f;
+    return;
+  }
+  const int top = 31 - __clz((int)r);          // highest set bit, 0..28
+  const int le = fe - 52 + top;                 // float exponent field of the remainder
+  const unsigned int mant = top >= 23 ? (r >> (top - 23)) : (r << (23 - top));
+  lo = __int_as_float((int)(sign | ((unsigned int)le << 23) | (mant & 0x7fffffu)));
+}
+
+__global__ void k_split(Grid g, const double* __restrict__ q, float* __restrict__ hilo) {
+  const long long n = 12 * g.ps;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    float hi, lo;
+    split_hilo(q[t], hi, lo);
+    hilo[t] = hi;
+    hilo[n + t] = lo;
+  }
+}
+
+__device__ __forceinline__ void to_prim(const double* s, float* w) {
+  const double rr = 1.0 / s[0];
+  const double u = s[1] * rr, v = s[2] * rr;
+  w[0] = (float)s[0];
+  w[1] = (float)u;
+  w[2] = (float)v;
+  w[3] = (float)(s[3] * rr - 0.5 * (u * u + v * v));
+}
+
+__device__ __forceinline__ void to_prim_f(const float* s, float* w) {
+  const float rr = 1.0f / s[0];
+  w[0] = s[0];
+  w[1] = s[1] * rr;
+  w[2] = s[2] * rr;
+  w[3] = s[3] * rr - 0.5f * (w[1] * w[1] + w[2] * w[2]);
+}
+
+// FP32 admissibility filter: true only if the FP64 limiter check would certainly pass
+// (rho and the internal energy clear of zero by a margin far above FP32 rounding) and
+// the internal energy is at least 1 % of E, so that FP32 primitives keep about 6
+// significant digits of e.  Otherwise the cell takes the FP64 route.
+__device__ __forceinline__ bool clearly_fine(const float* s, float rho_ref) {
+  const float ke = 0.5f * (s[1] * s[1] + s[2] * s[2]);
+  const float ie = s[3] * s[0] - ke;  // rho * (rho e)
+  return s[0] > 1e-4f * rho_ref && ie > 1e-2f * (fabsf(s[3] * s[0]) + ke);
+}
+
+__global__ void __launch_bounds__(128) k_cons_mixed(Grid g, const double* __restrict__ q, Work w,
+                                                    double* __restrict__ mom, Diag* diag) {
+  const int i = blockIdx.x * 32 + threadIdx.x - 3;
+  const int j = blockIdx.y * 4 + threadIdx.y - 3;
+  unsigned long long pp = 0;
+  unsigned int flags = 0;
+  const WorkF f = mixed_planes(w, g.ps);
+  if (i < g.nx + 3 && j < g.ny + 3) {
+    const long long c = cidx(g, i, j);
+    const long long n12 = 12 * g.ps;
+    float cc[4][15], sl[4][4], hc[4], lc[4];
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const float* H = f.hilo + (long long)v * g.ps;
+      const float* L = H + n12;
+      const float* X = f.hilo + (long long)(4 + v) * g.ps;
+      const float* Y = f.hilo + (long long)(8 + v) * g.ps;
+      hc[v] = H[c];
+      lc[v] = L[c];
+      float d[17];
+#pragma unroll
+      for (int b = -1; b <= 1; b++)
+#pragma unroll
+        for (int a = -1; a <= 1; a++) {
+          const long long k = cidx(g, i + a, j + b);
+          d[(b + 1) * 3 + (a + 1)] = (H[k] - hc[v]) + (L[k] - lc[v]);
+        }
+      d[4] = 0.0f;
+      d[9] = X[cidx(g, i - 1, j)];
+      d[10] = X[cidx(g, i + 1, j)];
+      d[11] = Y[cidx(g, i, j - 1)];
+      d[12] = Y[cidx(g, i, j + 1)];
+      d[13] = X[cidx(g, i, j - 1)];
+      d[14] = X[cidx(g, i, j + 1)];
+      d[15] = Y[cidx(g, i - 1, j)];
+      d[16] = Y[cidx(g, i + 1, j)];
+      hw_p0_coeffs<float>(d, cc[v]);
+      sl[v][0] = -d[3];
+      sl[v][1] = d[5];
+      sl[v][2] = -d[1];
+      sl[v][3] = d[7];
+    }
+    const float ubf[4] = {hc[0] + lc[0], hc[1] + lc[1], hc[2] + lc[2], hc[3] + lc[3]};
+    const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+    float face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
+    CharState<float> cs;
+    char_state<float>(ubf, (float)g.gamma, cs);
+    recon_dir<float, 0>(cc, sl, zero, cs, (float)g.eps_weno, face, volx, mx);
+    recon_dir<float, 1>(cc, sl, zero, cs, (float)g.eps_weno, face + 6, vol, my);
+#pragma unroll
+    for (int k = 0; k < 9; k++)
+#pragma unroll
+      for (int v = 0; v < 4; v++) vol[k][v] = 0.5f * (volx[k][v] + vol[k][v]);
+    // face[][] and vol[][] hold offsets from the cell average
+    bool fine = true;
+#pragma unroll
+    for (int k = 0; k < 21; k++) {
+      float s[4];
+#pragma unroll
+      for (int v = 0; v < 4; v++) s[v] = (k < 12 ? face[k][v] : vol[k - 12][v]) + ubf[v];
+      fine = fine && clearly_fine(s, ubf[0]);
+    }
+    const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+    double th[2] = {1.0, 1.0};
+    float wb[3] = {0.f, 0.f, 0.f};
+    if (fine) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        float s[4], p[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) s[v] = face[k][v] + ubf[v];
+        to_prim_f(s, p);
+#pragma unroll
+        for (int v = 0; v < 4; v++) f.face[(long long)(4 * k + v) * g.ps + c] = p[v];
+      }
+#pragma unroll
+      for (int G = 0; G < 3; G++)
+#pragma unroll
+        for (int Hh = 0; Hh < 3; Hh++) {
+          const int k = 3 * G + Hh;
+          float s[4], p[4];
+#pragma unroll
+          for (int v = 0; v < 4; v++) s[v] = vol[k][v] + ubf[v];
+          to_prim_f(s, p);
+#pragma unroll
+          for (int v = 0; v < 4; v++) f.vol[(long long)(4 * k + v) * g.ps + c] = p[v];
+          const float wgt = gweight<float>(G) * gweight<float>(Hh);
+          wb[0] += wgt * p[1];
+          wb[1] += wgt * p[2];
+          wb[2] += wgt * p[3];
+        }
+    } else {
+      // FP64 route: the limiter of Sec. 3.1 on ub + offset, exactly as in the FP64 path
+      double ub[4], fd[12][4], vd[9][4];
+#pragma unroll
+      for (int v = 0; v < 4; v++) ub[v] = q[(long long)v * g.ps + c];
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+#pragma unroll
+        for (int k = 0; k < 12; k++) fd[k][v] = ub[v] + (double)face[k][v];
+#pragma unroll
+        for (int k = 0; k < 9; k++) vd[k][v] = ub[v] + (double)vol[k][v];
+      }
+      const double pb = pressure(ub, g.gamma);
+      if (!(ub[0] > 0.0) || !(pb > 0.0)) flags |= FLAG_BADAVG;
+      else if (pp_limit(ub, fd, vd, g.gamma, g.eps_pp, th) && interior) pp = 1;
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        float p[4];
+        to_prim(fd[k], p);
+#pragma unroll
+        for (int v = 0; v < 4; v++) f.face[(long long)(4 * k + v) * g.ps + c] = p[v];
+      }
+#pragma unroll
+      for (int G = 0; G < 3; G++)
+#pragma unroll
+        for (int Hh = 0; Hh < 3; Hh++) {
+          const int k = 3 * G + Hh;
+          float p[4];
+          to_prim(vd[k], p);
+#pragma unroll
+          for (int v = 0; v < 4; v++) f.vol[(long long)(4 * k + v) * g.ps + c] = p[v];
+          const float wgt = gweight<float>(G) * gweight<float>(Hh);
+          wb[0] += wgt * p[1];
+          wb[1] += wgt * p[2];
+          wb[2] += wgt * p[3];
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < 3; n++) f.wbar[(long long)n * g.ps + c] = wb[n];
+    w.theta[c] = th[0];
+    w.theta[g.ps + c] = th[1];
+    if (interior) {
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        mom[(long long)v * g.ps + c] = (double)mx[v];
+        mom[(long long)(4 + v) * g.ps + c] = (double)my[v];
+      }
+    }
+  }
+  pp = warp_sum_u64(pp);
+  flags = __reduce_or_sync(0xffffffffu, flags);
+  if ((threadIdx.x & 31) == 0) {
+    if (pp) atomicAdd(&diag->pp_count, pp);
+    if (flags) atomicOr(&diag->flags, flags);
+  }
+}
+
+// Eq. (3.6) in FP32 on the float traces
+__global__ void k_face_moments_mixed(Grid g, Work w) {
+  const int dir = blockIdx.z;
+  const int i = blockIdx.x * 32 + threadIdx.x - (dir == 0 ? 3 : 2);
+  const int j = blockIdx.y * 4 + threadIdx.y - (dir == 0 ? 2 : 3);
+  if (i >= g.nx + 2 || j >= g.ny + 2) return;
+  const WorkF f = mixed_planes(w, g.ps);
+  const long long cl = cidx(g, i, j);
+  const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
+  const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
+  float W0[3] = {0.f, 0.f, 0.f}, W1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int gp = 0; gp < 3; gp++) {
+    const float wg = gweight<float>(gp), xg = gnode<float>(gp);
+#pragma unroll
+    for (int n = 0; n < 3; n++) {
+      const float a = f.face[(long long)(4 * (kl + gp) + 1 + n) * g.ps + cl];
+      const float b = f.face[(long long)(4 * (kr + gp) + 1 + n) * g.ps + cr];
+      const float h = 0.5f * (a + b);
+      W0[n] += wg * h;
+      W1[n] += wg * h * xg;
+    }
+  }
+  float* out = dir == 0 ? f.wx : f.wy;
+#pragma unroll
+  for (int n = 0; n < 3; n++) {
+    out[(long long)n * g.ps + cl] = W0[n];
+    out[(long long)(3 + n) * g.ps + cl] = W1[n];
+  }
+}
+
+// Eqs. (3.7)-(3.8) in FP32
+__global__ void k_weak_moments_mixed(Grid g, Work w) {
+  const int i = blockIdx.x * 32 + threadIdx.x - 2;
+  const int j = blockIdx.y * 4 + threadIdx.y - 2;
+  if (i >= g.nx + 2 || j >= g.ny + 2) return;
+  const WorkF f = mixed_planes(w, g.ps);
+  const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
+  const float rdx = (float)(1.0 / g.dx), rdy = (float)(1.0 / g.dy);
+#pragma unroll
+  for (int n = 0; n < 3; n++) {
+    const float xr0 = f.wx[(long long)n * g.ps + c], xl0 = f.wx[(long long)n * g.ps + cl];
+    const float xr1 = f.wx[(long long)(3 + n) * g.ps + c], xl1 = f.wx[(long long)(3 + n) * g.ps + cl];
+    const float yt0 = f.wy[(long long)n * g.ps + c], yb0 = f.wy[(long long)n * g.ps + cb];
+    const float yt1 = f.wy[(long long)(3 + n) * g.ps + c], yb1 = f.wy[(long long)(3 + n) * g.ps + cb];
+    const float wb = f.wbar[(long long)n * g.ps + c];
+    float* r = f.rm + (long long)(6 * n) * g.ps + c;
+    r[0] = (xr0 - xl0) * rdx;
+    r[g.ps] = (0.5f * (xr0 + xl0) - wb) * rdx;
+    r[2 * g.ps] = (xr1 - xl1) * rdx;
+    r[3 * g.ps] = (yt0 - yb0) * rdy;
+    r[4 * g.ps] = (yt1 - yb1) * rdy;
+    r[5 * g.ps] = (0.5f * (yt0 + yb0) - wb) * rdy;
+  }
+}
+
+// Eq. (3.9) in FP32 on offsets from the centre value
+__global__ void __launch_bounds__(128) k_grad_mixed(Grid g, Work w) {
+  const int i = blockIdx.x * 32 + threadIdx.x - 1;
+  const int j = blockIdx.y * 4 + threadIdx.y - 1;
+  if (i >= g.nx + 1 || j >= g.ny + 1) return;
+  const WorkF f = mixed_planes(w, g.ps);
+  const long long c = cidx(g, i, j);
+  const float eps = (float)g.eps_weno;
+#pragma unroll 1
+  for (int comp = 0; comp < 6; comp++) {
+    const int n = comp >> 1, l = comp & 1;
+    const float* A = f.rm + (long long)(6 * n + 3 * l) * g.ps;
+    const float* X = A + g.ps;
+    const float* Y = A + 2 * g.ps;
+    const float cen = A[c];
+    float d[17];
+#pragma unroll
+    for (int b = -1; b <= 1; b++)
+#pragma unroll
+      for (int a = -1; a <= 1; a++) d[(b + 1) * 3 + (a + 1)] = A[cidx(g, i + a, j + b)] - cen;
+    d[4] = 0.0f;
+    d[9] = X[cidx(g, i - 1, j)];
+    d[10] = X[cidx(g, i + 1, j)];
+    d[11] = Y[cidx(g, i, j - 1)];
+    d[12] = Y[cidx(g, i, j + 1)];
+    d[13] = X[cidx(g, i, j - 1)];
+    d[14] = X[cidx(g, i, j + 1)];
+    d[15] = Y[cidx(g, i - 1, j)];
+    d[16] = Y[cidx(g, i + 1, j)];
+    float C[15];
+    hweno_combine<float>(d, eps, C);
+    float vx[6], vy[6], vv[9];
+    eval_xfaces<float>(C, vx);
+    eval_yfaces<float>(C, vy);
+    eval_vol<float>(C, vv);
+    float* out = f.gr + (long long)comp * g.ps + c;
+#pragma unroll
+    for (int k = 0; k < 6; k++) out[(long long)(6 * k) * g.ps] = cen + vx[k];
+#pragma unroll
+    for (int k = 0; k < 6; k++) out[(long long)(6 * (6 + k)) * g.ps] = cen + vy[k];
+#pragma unroll
+    for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = cen + vv[k];
+  }
+}
+
+// Eq. (3.3) in FP32; the face fluxes are stored in FP64 so that the moment balances
+// difference them exactly
+__global__ void __launch_bounds__(128) k_flux_mixed(Grid g, Work w, Diag* diag) {
+  const int dir = blockIdx.z;
+  const int i = blockIdx.x * 32 + threadIdx.x - (dir == 0 ? 1 : 0);
+  const int j = blockIdx.y * 4 + threadIdx.y - (dir == 0 ? 0 : 1);
+  float amax = 0.f, bmax = 0.f;
+  const WorkF f = mixed_planes(w, g.ps);
+  if (i < g.nx && j < g.ny) {
+    const long long cl = cidx(g, i, j);
+    const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
+    const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
+    const float gam = (float)g.gamma, rPr = (float)(1.0 / g.Pr), rRe = (float)(1.0 / g.Re);
+    float st[2][3][4], gs[2][3][6];
+#pragma unroll
+    for (int gp = 0; gp < 3; gp++)
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        const long long cc = s == 0 ? cl : cr;
+        const int k = (s == 0 ? kl : kr) + gp;
+#pragma unroll
+        for (int v = 0; v < 4; v++) st[s][gp][v] = f.face[(long long)(4 * k + v) * g.ps + cc];
+#pragma unroll
+        for (int n = 0; n < 6; n++) gs[s][gp][n] = f.gr[(long long)(6 * k + n) * g.ps + cc];
+      }
+    float beta = 0.f;
+#pragma unroll
+    for (int gp = 0; gp < 3; gp++)
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        beta = fmaxf(beta, wave_bound<float>(dir, st[s][gp], gs[s][gp], gam, rPr, rRe));
+        const float cs = sqrtf(gam * (gam - 1.f) * st[s][gp][3]);
+        amax = fmaxf(amax, fmaxf(fabsf(st[s][gp][1]) + cs, fabsf(st[s][gp][2]) + cs));
+      }
+    bmax = beta;
+    float S0[4] = {0.f, 0.f, 0.f, 0.f}, S1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int gp = 0; gp < 3; gp++) {
+      float fl[4], fr[4], ul[4], ur[4];
+      phys_flux<float>(dir, st[0][gp], gs[0][gp], gam, rPr, rRe, fl);
+      phys_flux<float>(dir, st[1][gp], gs[1][gp], gam, rPr, rRe, fr);
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        float* u = s == 0 ? ul : ur;
+        const float* p = st[s][gp];
+        u[0] = p[0];
+        u[1] = p[0] * p[1];
+        u[2] = p[0] * p[2];
+        u[3] = p[0] * (p[3] + 0.5f * (p[1] * p[1] + p[2] * p[2]));
+      }
+      const float wg = gweight<float>(gp), wt = gweight<float>(gp) * gnode<float>(gp);
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        const float fh = 0.5f * (fl[v] + fr[v] - beta * (ur[v] - ul[v]));
+        S0[v] += wg * fh;
+        if (gp != 1) S1[v] += wt * fh;
+      }
+    }
+    // stored in FP64 so that the balances difference them exactly
+    double* out = (dir == 0 ? w.fx : w.fy) + cl;
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      out[(long long)v * g.ps] = (double)S0[v];
+      out[(long long)(4 + v) * g.ps] = (double)S1[v];
+    }
+  }
+  amax = warp_max(amax);
+  bmax = warp_max(bmax);
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_pos(&diag->alpha_bits, (double)amax);
+    atomic_max_pos(&diag->beta_bits, (double)bmax);
+  }
+}
+
+// Eq. (3.2): volume fluxes in FP32, face-flux sums and the balances in FP64
+__global__ void __launch_bounds__(128) k_assemble_mixed(Grid g, Work w, double* __restrict__ rhs,
+                                                        Diag* diag) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 4 + threadIdx.y;
+  unsigned int bad = 0;
+  const WorkF f = mixed_planes(w, g.ps);
+  if (i < g.nx && j < g.ny) {
+    const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
+    const float gam = (float)g.gamma, rPr = (float)(1.0 / g.Pr), rRe = (float)(1.0 / g.Re);
+    float vf[4] = {0.f, 0.f, 0.f, 0.f}, vg[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int G = 0; G < 3; G++)
+#pragma unroll
+      for (int H = 0; H < 3; H++) {
+        const int k = 3 * G + H;
+        float st[4], gs[6], fx[4], gy[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) st[v] = f.vol[(long long)(4 * k + v) * g.ps + c];
+#pragma unroll
+        for (int n = 0; n < 6; n++) gs[n] = f.gr[(long long)(6 * (12 + k) + n) * g.ps + c];
+        phys_flux<float>(0, st, gs, gam, rPr, rRe, fx);
+        phys_flux<float>(1, st, gs, gam, rPr, rRe, gy);
+        const float wgt = gweight<float>(G) * gweight<float>(H);
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+          vf[v] += wgt * fx[v];
+          vg[v] += wgt * gy[v];
+        }
+      }
+    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const double fR0 = w.fx[(long long)v * g.ps + c], fL0 = w.fx[(long long)v * g.ps + cl];
+      const double fR1 = w.fx[(long long)(4 + v) * g.ps + c], fL1 = w.fx[(long long)(4 + v) * g.ps + cl];
+      const double gT0 = w.fy[(long long)v * g.ps + c], gB0 = w.fy[(long long)v * g.ps + cb];
+      const double gT1 = w.fy[(long long)(4 + v) * g.ps + c], gB1 = w.fy[(long long)(4 + v) * g.ps + cb];
+      const double r0 = -(fR0 - fL0) * rdx - (gT0 - gB0) * rdy;
+      const double r1 = -(fL0 + fR0) * (0.5 * rdx) - (gT1 - gB1) * rdy + (double)vf[v] * rdx;
+      const double r2 = -(fR1 - fL1) * rdx - (gB0 + gT0) * (0.5 * rdy) + (double)vg[v] * rdy;
+      rhs[(long long)v * g.ps + c] = r0;
+      rhs[(long long)(4 + v) * g.ps + c] = r1;
+      rhs[(long long)(8 + v) * g.ps + c] = r2;
+      if (!isfinite(r0) || !isfinite(r1) || !isfinite(r2)) bad = FLAG_NONFINITE;
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&diag->flags, bad);
+}
+
+// float planes back to a contiguous double array (debug output of the mixed path)
+__global__ void k_gather_f(Grid g, int n, const float* __restrict__ src, double* __restrict__ dst) {
+  const long long N = (long long)g.nx * g.ny;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * N;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long p = t / N, r = t % N;
+    const int jj = (int)(r / g.nx), ii = (int)(r % g.nx);
+    dst[t] = (double)src[p * g.ps + cidx(g, ii, jj)];
+  }
+}
+__global__ void k_gather_cons_f(Grid g, const float* __restrict__ src, double* __restrict__ dst) {
+  const long long N = (long long)g.nx * g.ny;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int jj = (int)(r / g.nx), ii = (int)(r % g.nx);
+    const long long c = cidx(g, ii, jj);
+    const double rho = src[c], u = src[g.ps + c], v = src[2 * g.ps + c], e = src[3 * g.ps + c];
+    dst[r] = rho;
+    dst[N + r] = rho * u;
+    dst[2 * N + r] = rho * v;
+    dst[3 * N + r] = rho * (e + 0.5 * (u * u + v * v));
+  }
+}
+
+}  // namespace hw

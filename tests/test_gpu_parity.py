@@ -24,16 +24,21 @@ RES_TOL = 1e-12
 
 
 def flux_scale(case, q):
-    """per conserved variable: max over cells of (|F_v| + |G_v|)/h of the cell averages'
-    inviscid fluxes, the magnitude of the terms whose differences form a residual plane"""
+    """per conserved variable: max over cells of (|F_v| + |G_v| + (|u| + |v| + 2c)|U_v|)/h,
+    with the inviscid fluxes F, G of the cell averages and the Lax-Friedrichs
+    dissipation scale: the magnitude of the face-flux terms whose differences form a
+    residual plane (nonzero even for a fluid at rest)"""
     g = case.gamma
     rho, m, n, E = q[0], q[1], q[2], q[3]
     u, v = m / rho, n / rho
     p = (g - 1) * (E - 0.5 * rho * (u * u + v * v))
+    c = np.sqrt(np.maximum(g * p / rho, 0.0))
     F = [m, m * u + p, m * v, (E + p) * u]
     G = [n, n * u, n * v + p, (E + p) * v]
+    U = [rho, m, n, E]
+    lam = np.abs(u) + np.abs(v) + 2 * c
     h = min(case.dx, case.dy)
-    return np.array([np.abs(F[k]).max() + np.abs(G[k]).max() for k in range(4)]) / h
+    return np.array([(np.abs(F[k]) + np.abs(G[k]) + lam * np.abs(U[k])).max() for k in range(4)]) / h
 
 
 def rel_linf(a, b, scale=None, mask=None):
@@ -312,3 +317,31 @@ def test_mixed_precision_residual_error(name):
     o = O.residual(ocfg(case), q)
     assert rel_linf(g["rhs"], o["rhs"], flux_scale(case, q)) <= 1e-5
     assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= 1e-6
+
+
+def test_mixed_precision_conserves_to_fp64_roundoff():
+    """The mixed path stores the face fluxes in FP64 and differences them in FP64, so the
+    periodic cell-average residual still telescopes to FP64 round-off."""
+    case, q = I.random_rough(40, 36, seed=12)
+    g = gpu_residual(case, q, precision="mixed")
+    for v in range(4):
+        assert abs(g["rhs"][v].sum()) <= 1e-13 * np.abs(g["rhs"][v]).sum()
+
+
+def test_mixed_precision_limiter_route_and_intermediates():
+    """Cells the FP32 filter cannot clear take the FP64 limiter: on a low-pressure rough
+    state the limited cells and theta match the FP64 path, the limited face states stay
+    positive, and the FP32 intermediates stay within FP32 accuracy of the FP64 ones."""
+    case, q = I.random_rough(40, 36, seed=2, low=0.01)
+    gm = gpu_residual(case, q, precision="mixed", dumps=(0, 1, 2, 3, 4))
+    gd = gpu_residual(case, q, precision="fp64", dumps=(0, 1, 2, 3, 4))
+    lim_m = (gm[4][0] < 1) | (gm[4][1] < 1)
+    lim_d = (gd[4][0] < 1) | (gd[4][1] < 1)
+    assert lim_d.any() and np.array_equal(lim_m, lim_d)
+    far = _far_from(lim_d, 4)
+    assert rel_linf(gm[0], gd[0], state_scale(q), far) <= 1e-5
+    assert rel_linf(gm[1], gd[1], state_scale(q), far) <= 1e-5
+    assert rel_linf(gm["rhs"], gd["rhs"], flux_scale(case, q), far) <= 1e-5
+    face = gm[0].reshape(12, 4, 36, 40)
+    p = (case.gamma - 1) * (face[:, 3] - 0.5 * (face[:, 1] ** 2 + face[:, 2] ** 2) / face[:, 0])
+    assert face[:, 0].min() > 0 and p.min() > 0
