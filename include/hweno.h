@@ -180,6 +180,44 @@ int hweno_measure_peak(hweno_handle* h, int which, double* tflops);
  * (the count bench tools report as gpu_launches). */
 long long hweno_launch_count(const hweno_handle* h);
 
+/* ---- Batched ensembles ---------------------------------------------------------
+ * Many independent problems (own grid, physics, boundaries; one common precision)
+ * advanced together.  Each kernel of the spatial operator runs as one launch for all
+ * cases: persistent blocks (a multiple of the SM count) walk a work list of
+ * (case, tile) items; one SSP-RK3 step of the whole ensemble is a CUDA graph, captured
+ * at init and replayed per step.  Each case keeps its own time step (the rule of
+ * Sec. 5) and its own restarts: after a replay the flags of all cases are read back
+ * (one synchronisation per step) and only the rejected cases are replayed with half
+ * their step.  The method is the one of hweno_step; the paper solves one problem at a
+ * time and has no counterpart of the batching itself. */
+typedef struct hweno_batch hweno_batch;
+
+/* Create ncases solvers (cfgs[0..ncases-1], as for hweno_init, all with the same
+ * precision) sharing one stream; NULL stream: the batch creates its own non-blocking
+ * stream (graph capture needs one).  Allocates everything.  Errors as hweno_init. */
+int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_batch** out);
+void hweno_batch_destroy(hweno_batch* b);
+const char* hweno_batch_last_error(const hweno_batch* b);
+
+/* The solver of case k, for hweno_set_state / hweno_get_state / hweno_get_diag (and,
+ * if wanted, hweno_step on that case alone).  Owned by the batch. */
+int hweno_batch_case(hweno_batch* b, int k, hweno_handle** h);
+
+/* nsteps SSP-RK3 steps of every case, each with its own dt = min(CFL h/alpha*, b Re h^2).
+ * *rejections (may be NULL): restarted case-steps.  Errors: HWENO_ERR_STATE if a case
+ * has no state, HWENO_ERR_INADMISSIBLE after max_halvings restarts of a case. */
+int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections);
+
+/* Autotuner: times every batched kernel of the spatial operator for the block shapes
+ * 32x4, 16x8, 64x2 and 128x1 on the current states (their tile lists differ), keeps
+ * the fastest per kernel and re-captures the step graph.  chosen (6 ints, may be
+ * NULL): the index of the kept shape for cons, face moments, weak moments, gradients,
+ * fluxes and assembly/RK.  Does not change the states. */
+int hweno_batch_autotune(hweno_batch* b, int* chosen);
+
+/* Kernel launches issued by the batch (graph replays count their nodes). */
+long long hweno_batch_launch_count(const hweno_batch* b);
+
 /* The spatial operator of hweno_residual for callers that cannot allocate device
  * memory while they run: programs whose device memory belongs to another allocator
  * under a fixed budget (a framework's caching pool, a reserved arena), where an extra

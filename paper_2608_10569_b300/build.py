@@ -16,7 +16,6 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libhweno.so")
 SOURCES = ["hweno.cu"]
-DEPS = SOURCES + ["hweno_device.cuh", "hweno_kernels.cuh", "hweno_stencil.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +30,8 @@ def stale():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, d) for d in DEPS] + [os.path.join(ROOT, "include", "hweno.h")]
+    deps = [os.path.join(CSRC, d) for d in os.listdir(CSRC) if d.endswith((".cu", ".cuh", ".h"))]
+    deps.append(os.path.join(ROOT, "include", "hweno.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -13,390 +13,43 @@
 #include <vector>
 
 #include "hweno.h"
-#include "hweno_kernels.cuh"
+#include "hweno_ops.cuh"
 #include "hweno_mixed.cuh"
+#include "hweno_batch.cuh"
 
 namespace hw {
 
 constexpr int BX = 32, BY = 4;
 
-// ---------------------------------------------------------------------------
-// conservative characteristic reconstruction, modified moments and PP limiter of
-// every cell of the interior grown by 3 (Sec. 3.1, Eq. (3.4), Appendix A.2)
+// single-grid kernels: one thread per position of the launch region
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_cons(Grid g, const double* __restrict__ q, Work w,
                                                   double* __restrict__ mom, Diag* diag) {
-  const int i = blockIdx.x * BX + threadIdx.x - 3;
-  const int j = blockIdx.y * BY + threadIdx.y - 3;
-  unsigned long long pp = 0;
-  unsigned int flags = 0;
-  if (i < g.nx + 3 && j < g.ny + 3) {
-    constexpr bool OFF = sizeof(T) == 4;  // FP32: reconstruct offsets from the average
-    const long long c = cidx(g, i, j);
-    double ub[4];
-    T cc[4][15], sl[4][4], ctr[4];
-#pragma unroll
-    for (int v = 0; v < 4; v++) {
-      double d[17];
-      gather17<OFF>(g, q, v, i, j, d);
-      ub[v] = q[(long long)v * g.ps + c];
-      T dt[17];
-#pragma unroll
-      for (int k = 0; k < 17; k++) dt[k] = (T)d[k];
-      hw_p0_coeffs<T>(dt, cc[v]);
-      sl[v][0] = (T)(d[4] - d[3]);
-      sl[v][1] = (T)(d[5] - d[4]);
-      sl[v][2] = (T)(d[4] - d[1]);
-      sl[v][3] = (T)(d[7] - d[4]);
-      ctr[v] = OFF ? T(0) : (T)ub[v];
-    }
-    const T ut[4] = {(T)ub[0], (T)ub[1], (T)ub[2], (T)ub[3]};
-    const T eps = (T)g.eps_weno;
-    double face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
-    CharState<T> cs;
-    char_state<T>(ut, (T)g.gamma, cs);
-    recon_dir<T, 0, double>(cc, sl, ctr, cs, eps, face, volx, mx);
-    recon_dir<T, 1, double>(cc, sl, ctr, cs, eps, face + 6, vol, my);
-#pragma unroll
-    for (int v = 0; v < 4; v++) {
-#pragma unroll
-      for (int k = 0; k < 12; k++)
-        if (OFF) face[k][v] += ub[v];
-#pragma unroll
-      for (int k = 0; k < 9; k++) {
-        vol[k][v] = 0.5 * (volx[k][v] + vol[k][v]);
-        if (OFF) vol[k][v] += ub[v];
-      }
-    }
-    double th[2] = {1.0, 1.0};
-    const double pb = pressure(ub, g.gamma);
-    const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
-    if (!(ub[0] > 0.0) || !(pb > 0.0)) {
-      flags |= FLAG_BADAVG;
-    } else if (pp_limit(ub, face, vol, g.gamma, g.eps_pp, th) && interior) {
-      pp = 1;
-    }
-    // primitive (rho, u, v, e) at the 12 limited face points and the 9 volume points
-#pragma unroll
-    for (int k = 0; k < 12; k++) {
-      const double rr = 1.0 / face[k][0];
-      const double u = face[k][1] * rr, v = face[k][2] * rr;
-      const double e = face[k][3] * rr - 0.5 * (u * u + v * v);
-      w.face[(long long)(4 * k + 0) * g.ps + c] = face[k][0];
-      w.face[(long long)(4 * k + 1) * g.ps + c] = u;
-      w.face[(long long)(4 * k + 2) * g.ps + c] = v;
-      w.face[(long long)(4 * k + 3) * g.ps + c] = e;
-    }
-    double wb[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int G = 0; G < 3; G++)
-#pragma unroll
-      for (int H = 0; H < 3; H++) {
-        const int k = 3 * G + H;
-        const double rr = 1.0 / vol[k][0];
-        const double u = vol[k][1] * rr, v = vol[k][2] * rr;
-        const double e = vol[k][3] * rr - 0.5 * (u * u + v * v);
-        w.vol[(long long)(4 * k + 0) * g.ps + c] = vol[k][0];
-        w.vol[(long long)(4 * k + 1) * g.ps + c] = u;
-        w.vol[(long long)(4 * k + 2) * g.ps + c] = v;
-        w.vol[(long long)(4 * k + 3) * g.ps + c] = e;
-        const double wgt = gweight<double>(G) * gweight<double>(H);
-        wb[0] += wgt * u;
-        wb[1] += wgt * v;
-        wb[2] += wgt * e;
-      }
-#pragma unroll
-    for (int n = 0; n < 3; n++) w.wbar[(long long)n * g.ps + c] = wb[n];
-    w.theta[c] = th[0];
-    w.theta[g.ps + c] = th[1];
-    if (interior) {
-#pragma unroll
-      for (int v = 0; v < 4; v++) {
-        mom[(long long)v * g.ps + c] = mx[v];
-        mom[(long long)(4 + v) * g.ps + c] = my[v];
-      }
-    }
-  }
-  // block reduction of the activation count and flags: one atomic per warp
-  pp = warp_sum_u64(pp);
-  flags = __reduce_or_sync(0xffffffffu, flags);
-  if ((threadIdx.x & 31) == 0) {
-    if (pp) atomicAdd(&diag->pp_count, pp);
-    if (flags) atomicOr(&diag->flags, flags);
-  }
+  cons_body<T>(g, q, w, mom, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
-
-// face moments W^{x,0}, W^{x,1} (blockIdx.z = 0) of the x-faces right of cells
-// i in [-3, nx+2), j in [-2, ny+2), and W^{y,0}, W^{y,1} (z = 1) of the y-faces
-// above cells i in [-2, nx+2), j in [-3, ny+2)  (Eq. (3.6) with the interface
-// average of the two traces)
 __global__ void k_face_moments(Grid g, Work w) {
-  const int dir = blockIdx.z;
-  const int i = blockIdx.x * BX + threadIdx.x - (dir == 0 ? 3 : 2);
-  const int j = blockIdx.y * BY + threadIdx.y - (dir == 0 ? 2 : 3);
-  if (i >= g.nx + 2 || j >= g.ny + 2) return;
-  const long long cl = cidx(g, i, j);
-  const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
-  const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
-  double W0[3] = {0.0, 0.0, 0.0}, W1[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-  for (int gp = 0; gp < 3; gp++) {
-    const double wg = gweight<double>(gp), xg = gnode<double>(gp);
-#pragma unroll
-    for (int n = 0; n < 3; n++) {
-      const double a = w.face[(long long)(4 * (kl + gp) + 1 + n) * g.ps + cl];
-      const double b = w.face[(long long)(4 * (kr + gp) + 1 + n) * g.ps + cr];
-      const double h = 0.5 * (a + b);
-      W0[n] += wg * h;
-      W1[n] += wg * h * xg;
-    }
-  }
-  double* out = dir == 0 ? w.wx : w.wy;
-#pragma unroll
-  for (int n = 0; n < 3; n++) {
-    out[(long long)n * g.ps + cl] = W0[n];
-    out[(long long)(3 + n) * g.ps + cl] = W1[n];
-  }
+  face_moments_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
 }
-
-// weak-derivative moments (Eqs. (3.7)-(3.8)) of cells in the interior grown by 2
 __global__ void k_weak_moments(Grid g, Work w) {
-  const int i = blockIdx.x * BX + threadIdx.x - 2;
-  const int j = blockIdx.y * BY + threadIdx.y - 2;
-  if (i >= g.nx + 2 || j >= g.ny + 2) return;
-  const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
-  const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
-#pragma unroll
-  for (int n = 0; n < 3; n++) {
-    const double xr0 = w.wx[(long long)n * g.ps + c], xl0 = w.wx[(long long)n * g.ps + cl];
-    const double xr1 = w.wx[(long long)(3 + n) * g.ps + c], xl1 = w.wx[(long long)(3 + n) * g.ps + cl];
-    const double yt0 = w.wy[(long long)n * g.ps + c], yb0 = w.wy[(long long)n * g.ps + cb];
-    const double yt1 = w.wy[(long long)(3 + n) * g.ps + c], yb1 = w.wy[(long long)(3 + n) * g.ps + cb];
-    const double wb = w.wbar[(long long)n * g.ps + c];
-    double* r = w.rm + (long long)(6 * n) * g.ps + c;
-    r[0] = (xr0 - xl0) * rdx;
-    r[g.ps] = (0.5 * (xr0 + xl0) - wb) * rdx;
-    r[2 * g.ps] = (xr1 - xl1) * rdx;
-    r[3 * g.ps] = (yt0 - yb0) * rdy;
-    r[4 * g.ps] = (yt1 - yb1) * rdy;
-    r[5 * g.ps] = (0.5 * (yt0 + yb0) - wb) * rdy;
-  }
+  weak_moments_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
-
-// gradient reconstruction (Eq. (3.9)): the scalar HWENO of Appendix A.2 applied to
-// the weak-derivative moments of each of u, v, e in each direction, on cells of the
-// interior grown by 1; values at the 12 face and 9 volume points
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_grad(Grid g, Work w) {
-  const int i = blockIdx.x * BX + threadIdx.x - 1;
-  const int j = blockIdx.y * BY + threadIdx.y - 1;
-  if (i >= g.nx + 1 || j >= g.ny + 1) return;
-  const long long c = cidx(g, i, j);
-  const T eps = (T)g.eps_weno;
-#pragma unroll 1
-  for (int comp = 0; comp < 6; comp++) {
-    const int n = comp >> 1, l = comp & 1;
-    const double* A = w.rm + (long long)(6 * n + 3 * l) * g.ps;
-    const double* X = A + g.ps;
-    const double* Y = A + 2 * g.ps;
-    constexpr bool OFF = sizeof(T) == 4;  // FP32: reconstruct offsets from the centre value
-    const double cen = OFF ? A[c] : 0.0;
-    T d[17];
-#pragma unroll
-    for (int b = -1; b <= 1; b++)
-#pragma unroll
-      for (int a = -1; a <= 1; a++) d[(b + 1) * 3 + (a + 1)] = (T)(A[cidx(g, i + a, j + b)] - cen);
-    if (OFF) d[4] = T(0);
-    d[9] = (T)X[cidx(g, i - 1, j)];
-    d[10] = (T)X[cidx(g, i + 1, j)];
-    d[11] = (T)Y[cidx(g, i, j - 1)];
-    d[12] = (T)Y[cidx(g, i, j + 1)];
-    d[13] = (T)X[cidx(g, i, j - 1)];
-    d[14] = (T)X[cidx(g, i, j + 1)];
-    d[15] = (T)Y[cidx(g, i - 1, j)];
-    d[16] = (T)Y[cidx(g, i + 1, j)];
-    T C[15];
-    hweno_combine<T>(d, eps, C);
-    T vx[6], vy[6], vv[9];
-    eval_xfaces<T>(C, vx);
-    eval_yfaces<T>(C, vy);
-    eval_vol<T>(C, vv);
-    double* out = w.gr + (long long)comp * g.ps + c;
-    // FP64: the values themselves; FP32: offsets, restored in FP64
-#pragma unroll
-    for (int k = 0; k < 6; k++) out[(long long)(6 * k) * g.ps] = OFF ? cen + (double)vx[k] : (double)vx[k];
-#pragma unroll
-    for (int k = 0; k < 6; k++) out[(long long)(6 * (6 + k)) * g.ps] = OFF ? cen + (double)vy[k] : (double)vy[k];
-#pragma unroll
-    for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = OFF ? cen + (double)vv[k] : (double)vv[k];
-  }
+  grad_body<T>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
-
-// PP local Lax-Friedrichs fluxes (Eq. (3.3)) of the interior faces: x-faces right
-// of cells i in [-1, nx), j in [0, ny) (blockIdx.z = 0); y-faces above cells
-// i in [0, nx), j in [-1, ny) (z = 1).  Also the face maxima alpha* and beta.
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_flux(Grid g, Work w, Diag* diag) {
-  const int dir = blockIdx.z;
-  const int i = blockIdx.x * BX + threadIdx.x - (dir == 0 ? 1 : 0);
-  const int j = blockIdx.y * BY + threadIdx.y - (dir == 0 ? 0 : 1);
-  double amax = 0.0, bmax = 0.0;
-  if (i < g.nx && j < g.ny) {
-    const long long cl = cidx(g, i, j);
-    const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
-    const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
-    const T gam = (T)g.gamma, rPr = (T)(1.0 / g.Pr), rRe = (T)(1.0 / g.Re);
-    T st[2][3][4], gs[2][3][6];
-#pragma unroll
-    for (int gp = 0; gp < 3; gp++)
-#pragma unroll
-      for (int s = 0; s < 2; s++) {
-        const long long cc = s == 0 ? cl : cr;
-        const int k = (s == 0 ? kl : kr) + gp;
-#pragma unroll
-        for (int v = 0; v < 4; v++) st[s][gp][v] = (T)w.face[(long long)(4 * k + v) * g.ps + cc];
-#pragma unroll
-        for (int n = 0; n < 6; n++) gs[s][gp][n] = (T)w.gr[(long long)(6 * k + n) * g.ps + cc];
-      }
-    T beta = T(0);
-#pragma unroll
-    for (int gp = 0; gp < 3; gp++)
-#pragma unroll
-      for (int s = 0; s < 2; s++) {
-        beta = fmax(beta, wave_bound<T>(dir, st[s][gp], gs[s][gp], gam, rPr, rRe));
-        const T cs = sqrt(gam * (gam - T(1)) * st[s][gp][3]);
-        amax = fmax(amax, (double)fmax(fabs(st[s][gp][1]) + cs, fabs(st[s][gp][2]) + cs));
-      }
-    bmax = (double)beta;
-    // the moment balances use each face's fluxes only through the Gauss sums
-    // S0 = sum_g w_g fhat_g and S1 = sum_g w_g t_g fhat_g (t_g: the transverse Gauss
-    // offset): both cells read the same stored sums, so the telescoping is exact
-    T S0[4] = {T(0), T(0), T(0), T(0)}, S1[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-    for (int gp = 0; gp < 3; gp++) {
-      T fl[4], fr[4], ul[4], ur[4];
-      phys_flux<T>(dir, st[0][gp], gs[0][gp], gam, rPr, rRe, fl);
-      phys_flux<T>(dir, st[1][gp], gs[1][gp], gam, rPr, rRe, fr);
-#pragma unroll
-      for (int s = 0; s < 2; s++) {
-        T* u = s == 0 ? ul : ur;
-        const T* p = st[s][gp];
-        u[0] = p[0];
-        u[1] = p[0] * p[1];
-        u[2] = p[0] * p[2];
-        u[3] = p[0] * (p[3] + T(0.5) * (p[1] * p[1] + p[2] * p[2]));
-      }
-      const T wg = gweight<T>(gp), wt = gweight<T>(gp) * gnode<T>(gp);
-#pragma unroll
-      for (int v = 0; v < 4; v++) {
-        const T fh = T(0.5) * (fl[v] + fr[v] - beta * (ur[v] - ul[v]));
-        S0[v] += wg * fh;
-        if (gp != 1) S1[v] += wt * fh;
-      }
-    }
-    double* out = (dir == 0 ? w.fx : w.fy) + cl;
-#pragma unroll
-    for (int v = 0; v < 4; v++) {
-      out[(long long)v * g.ps] = (double)S0[v];
-      out[(long long)(4 + v) * g.ps] = (double)S1[v];
-    }
-  }
-  amax = warp_max(amax);
-  bmax = warp_max(bmax);
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_pos(&diag->alpha_bits, amax);
-    atomic_max_pos(&diag->beta_bits, bmax);
-  }
+  flux_body<T>(g, w, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
 }
-
-// moment balances Eq. (3.2) of the interior cells
 template <class T>
-__global__ void __launch_bounds__(BX * BY) k_assemble(Grid g, Work w, double* __restrict__ rhs,
-                                                      Diag* diag) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  unsigned int bad = 0;
-  if (i < g.nx && j < g.ny) {
-    const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
-    const T gam = (T)g.gamma, rPr = (T)(1.0 / g.Pr), rRe = (T)(1.0 / g.Re);
-    // volume quadrature of f and g at the tensor Gauss points
-    double vf[4] = {0, 0, 0, 0}, vg[4] = {0, 0, 0, 0};
-#pragma unroll 1
-    for (int G = 0; G < 3; G++)
-#pragma unroll
-      for (int H = 0; H < 3; H++) {
-        const int k = 3 * G + H;
-        T st[4], gs[6], f[4], h[4];
-#pragma unroll
-        for (int v = 0; v < 4; v++) st[v] = (T)w.vol[(long long)(4 * k + v) * g.ps + c];
-#pragma unroll
-        for (int n = 0; n < 6; n++) gs[n] = (T)w.gr[(long long)(6 * (12 + k) + n) * g.ps + c];
-        phys_flux<T>(0, st, gs, gam, rPr, rRe, f);
-        phys_flux<T>(1, st, gs, gam, rPr, rRe, h);
-        const double wgt = gweight<double>(G) * gweight<double>(H);
-#pragma unroll
-        for (int v = 0; v < 4; v++) {
-          vf[v] += wgt * (double)f[v];
-          vg[v] += wgt * (double)h[v];
-        }
-      }
-    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
-#pragma unroll
-    for (int v = 0; v < 4; v++) {
-      // face Gauss sums: S0 = sum w_g fhat_g, S1 = sum w_g t_g fhat_g (see k_flux)
-      const double fR0 = w.fx[(long long)v * g.ps + c], fL0 = w.fx[(long long)v * g.ps + cl];
-      const double fR1 = w.fx[(long long)(4 + v) * g.ps + c], fL1 = w.fx[(long long)(4 + v) * g.ps + cl];
-      const double gT0 = w.fy[(long long)v * g.ps + c], gB0 = w.fy[(long long)v * g.ps + cb];
-      const double gT1 = w.fy[(long long)(4 + v) * g.ps + c], gB1 = w.fy[(long long)(4 + v) * g.ps + cb];
-      const double r0 = -(fR0 - fL0) * rdx - (gT0 - gB0) * rdy;
-      const double r1 = -(fL0 + fR0) * (0.5 * rdx) - (gT1 - gB1) * rdy + vf[v] * rdx;
-      const double r2 = -(fR1 - fL1) * rdx - (gB0 + gT0) * (0.5 * rdy) + vg[v] * rdy;
-      rhs[(long long)v * g.ps + c] = r0;
-      rhs[(long long)(4 + v) * g.ps + c] = r1;
-      rhs[(long long)(8 + v) * g.ps + c] = r2;
-      if (!isfinite(r0) || !isfinite(r1) || !isfinite(r2)) bad = FLAG_NONFINITE;
-    }
-  }
-  bad = __reduce_or_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&diag->flags, bad);
+__global__ void __launch_bounds__(BX * BY) k_assemble(Grid g, Work w, double* __restrict__ rhs, Diag* diag) {
+  assemble_body<T>(g, w, rhs, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
-
-// SSP-RK3 stage with modified moments (Eq. (2.10), 2D analogue) on interior cells:
-//   stage 1: out = [u^n; vhat^n] + dt F,                        base = [u^n; vhat^n]
-//   stage 2: out = 3/4 base + 1/4 ([u^(1); vhat^(1)] + dt F)
-//   stage 3: out = 1/3 base + 2/3 ([u^(2); vhat^(2)] + dt F)
-// plus the admissibility test of the output averages (Sec. 5).
 __global__ void k_rk(Grid g, int stage, const double* __restrict__ qin, const double* __restrict__ mom,
                      const double* __restrict__ rhs, double* __restrict__ base, double* __restrict__ qout,
                      Diag* diag) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  unsigned int bad = 0;
-  if (i < g.nx && j < g.ny) {
-    const long long c = cidx(g, i, j);
-    const double dt = diag->dt;
-    double out[12];
-#pragma unroll
-    for (int k = 0; k < 12; k++) {
-      const double cur = k < 4 ? qin[(long long)k * g.ps + c] : mom[(long long)(k - 4) * g.ps + c];
-      const double f = rhs[(long long)k * g.ps + c];
-      if (stage == 1) {
-        base[(long long)k * g.ps + c] = cur;
-        out[k] = cur + dt * f;
-      } else if (stage == 2) {
-        out[k] = 0.75 * base[(long long)k * g.ps + c] + 0.25 * (cur + dt * f);
-      } else {
-        out[k] = base[(long long)k * g.ps + c] * (1.0 / 3.0) + (2.0 / 3.0) * (cur + dt * f);
-      }
-      qout[(long long)k * g.ps + c] = out[k];
-      if (!isfinite(out[k])) bad = FLAG_INADMISSIBLE;
-    }
-    // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
-    const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
-    if (!(out[0] > 0.0) || !(rp > 0.0)) bad = FLAG_INADMISSIBLE;
-  }
-  bad = __reduce_or_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&diag->flags, bad);
+  rk_body(g, stage, qin, mom, rhs, base, qout, diag, blockIdx.x * blockDim.x + threadIdx.x,
+          blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 // time step of Sec. 5: dt = min(CFL h / alpha*, b Re h^2), or a forced trial
@@ -1091,6 +744,429 @@ int hweno_measure_peak(hweno_handle* h, int which, double* tflops) {
   cudaEventDestroy(b);
   *tflops = best;
   return HWENO_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched ensembles: many independent problems advanced together, one launch of each
+// kernel for all cases, one CUDA graph per SSP-RK3 step of the whole ensemble.
+
+namespace {
+enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_N };
+const char* const BR_NAME[BR_N] = {"cons", "face_moments", "weak_moments", "grad", "flux", "assemble_rk",
+                                   "ghost_x", "ghost_y", "split"};
+
+struct BatchList {
+  int bx = 32, by = 4;  // block shape of the kernels that use this list
+  int total = 0;        // work items
+  int grid = 0;         // persistent blocks
+  int* d = nullptr;     // device: start[n+1], tx[n], ty[n]
+  TileList tl() const { return TileList{d, d + (n + 1), d + (2 * n + 1)}; }
+  int n = 0;
+};
+}  // namespace
+
+struct hweno_batch {
+  int n = 0;
+  int mixed = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<hweno_handle*> h;
+  CaseDev* d_cases = nullptr;
+  CaseDev* h_cases = nullptr;  // pinned mirror
+  Diag* d_diag = nullptr;
+  Diag* h_diag = nullptr;      // pinned
+  BatchList L[BR_N];
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+  int sms = 148;
+  char err[512];
+};
+
+static int bfail(hweno_batch* b, int code, const char* msg) {
+  if (b) snprintf(b->err, sizeof(b->err), "%s", msg);
+  snprintf(g_init_err, sizeof(g_init_err), "%s", msg);
+  return code;
+}
+
+#define BCK(call, where)                                                        \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      char m_[400];                                                             \
+      snprintf(m_, sizeof(m_), "%s: %s", where, cudaGetErrorString(e_));        \
+      return bfail(b, HWENO_ERR_CUDA, m_);                                      \
+    }                                                                           \
+  } while (0)
+
+// launch-region extents (x, y, z) of list kind k for a grid
+static void region_of(int k, const Grid& g, int& wx, int& wy, int& wz) {
+  wz = 1;
+  switch (k) {
+    case BR_CONS: wx = g.nx + 6; wy = g.ny + 6; break;
+    case BR_FACE: wx = g.nx + 5; wy = g.ny + 5; wz = 2; break;
+    case BR_WEAK: wx = g.nx + 4; wy = g.ny + 4; break;
+    case BR_GRAD: wx = g.nx + 2; wy = g.ny + 2; break;
+    case BR_FLUX: wx = g.nx + 1; wy = g.ny + 1; wz = 2; break;
+    case BR_INT: wx = g.nx; wy = g.ny; break;
+    case BR_GX: wx = 8 * g.ny; wy = 1; break;
+    case BR_GY: wx = 8 * (g.nx + 2 * NG); wy = 1; break;
+    default: wx = (int)(12 * g.ps); wy = 1; break;  // BR_SPLIT
+  }
+}
+
+static int build_list(hweno_batch* b, int k, int bx, int by) {
+  BatchList& L = b->L[k];
+  std::vector<int> host(3 * b->n + 1);
+  int total = 0;
+  for (int c = 0; c < b->n; c++) {
+    int wx, wy, wz;
+    region_of(k, b->h[c]->g, wx, wy, wz);
+    const int tx = (wx + bx - 1) / bx, ty = (wy + by - 1) / by;
+    host[c] = total;
+    host[b->n + 1 + c] = tx;
+    host[2 * b->n + 1 + c] = ty;
+    total += tx * ty * wz;
+  }
+  host[b->n] = total;
+  L.n = b->n;
+  L.bx = bx;
+  L.by = by;
+  L.total = total;
+  if (!L.d) BCK(cudaMalloc(&L.d, host.size() * sizeof(int)), "batch work list");
+  BCK(cudaMemcpyAsync(L.d, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice, b->st), "batch list");
+  BCK(cudaStreamSynchronize(b->st), "batch list");
+  return HWENO_OK;
+}
+
+// persistent grid: blocks resident on all SMs at once, never more than the items
+template <class K>
+static int persistent_grid(hweno_batch* b, K kernel, int items) {
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int g = b->sms * per_sm;
+  return items < g ? (items > 0 ? items : 1) : g;
+}
+
+// enqueue one SSP-RK3 step of every active case (no host synchronisation: capturable)
+static void batch_enqueue_step(hweno_batch* b) {
+  const int n = b->n;
+  const dim3 blk1(128, 1);
+  auto dims = [&](int k) { return dim3(b->L[k].bx, b->L[k].by); };
+  auto grid = [&](int k) { return b->L[k].grid; };
+  kb_reset<<<(n + 127) / 128, 128, 0, b->st>>>(b->d_cases, n);
+  b->launches++;
+  for (int stage = 1; stage <= 3; stage++) {
+    const int which = stage == 1 ? 0 : 1;
+    kb_ghost<<<grid(BR_GX), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GX].tl(), n, which, 0);
+    kb_ghost<<<grid(BR_GY), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GY].tl(), n, which, 1);
+    b->launches += 2;
+    if (b->mixed) {
+      kb_split<<<grid(BR_SPLIT), blk1, 0, b->st>>>(b->d_cases, b->L[BR_SPLIT].tl(), n, which);
+      kb_cons<1><<<grid(BR_CONS), dims(BR_CONS), 0, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n, which);
+      kb_face_moments<1><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
+      kb_weak_moments<1><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
+      kb_grad<1><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+      kb_flux<1><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
+      kb_assemble<1><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
+      b->launches += 7;
+    } else {
+      kb_cons<0><<<grid(BR_CONS), dims(BR_CONS), 0, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n, which);
+      kb_face_moments<0><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
+      kb_weak_moments<0><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
+      kb_grad<0><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+      kb_flux<0><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
+      kb_assemble<0><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
+      b->launches += 6;
+    }
+    if (stage == 1) {
+      kb_dt<<<(n + 127) / 128, 128, 0, b->st>>>(b->d_cases, n);
+      b->launches++;
+    }
+    kb_rk<<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, stage);
+    b->launches++;
+  }
+}
+
+static int batch_grids(hweno_batch* b) {
+  b->L[BR_GX].grid = persistent_grid(b, kb_ghost, b->L[BR_GX].total);
+  b->L[BR_GY].grid = persistent_grid(b, kb_ghost, b->L[BR_GY].total);
+  b->L[BR_SPLIT].grid = persistent_grid(b, kb_split, b->L[BR_SPLIT].total);
+  if (b->mixed) {
+    b->L[BR_CONS].grid = persistent_grid(b, kb_cons<1>, b->L[BR_CONS].total);
+    b->L[BR_FACE].grid = persistent_grid(b, kb_face_moments<1>, b->L[BR_FACE].total);
+    b->L[BR_WEAK].grid = persistent_grid(b, kb_weak_moments<1>, b->L[BR_WEAK].total);
+    b->L[BR_GRAD].grid = persistent_grid(b, kb_grad<1>, b->L[BR_GRAD].total);
+    b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<1>, b->L[BR_FLUX].total);
+    b->L[BR_INT].grid = persistent_grid(b, kb_assemble<1>, b->L[BR_INT].total);
+  } else {
+    b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0>, b->L[BR_CONS].total);
+    b->L[BR_FACE].grid = persistent_grid(b, kb_face_moments<0>, b->L[BR_FACE].total);
+    b->L[BR_WEAK].grid = persistent_grid(b, kb_weak_moments<0>, b->L[BR_WEAK].total);
+    b->L[BR_GRAD].grid = persistent_grid(b, kb_grad<0>, b->L[BR_GRAD].total);
+    b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<0>, b->L[BR_FLUX].total);
+    b->L[BR_INT].grid = persistent_grid(b, kb_assemble<0>, b->L[BR_INT].total);
+  }
+  return HWENO_OK;
+}
+
+static int batch_capture(hweno_batch* b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+  const long long l0 = b->launches;
+  batch_enqueue_step(b);
+  b->launches = l0;  // captured launches run (and are counted) at each replay
+  BCK(cudaStreamEndCapture(b->st, &graph), "graph capture end");
+  cudaError_t e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  BCK(e, "graph instantiate");
+  return HWENO_OK;
+}
+
+static int batch_upload(hweno_batch* b) {
+  BCK(cudaMemcpyAsync(b->d_cases, b->h_cases, b->n * sizeof(CaseDev), cudaMemcpyHostToDevice, b->st),
+      "batch case upload");
+  return HWENO_OK;
+}
+
+static void batch_refresh_case(hweno_batch* b, int c) {
+  hweno_handle* h = b->h[c];
+  CaseDev& cd = b->h_cases[c];
+  cd.g = h->g;
+  cd.w = h->w;
+  cd.Q = h->Q; cd.QS = h->QS; cd.BASE = h->BASE; cd.RHS0 = h->RHS0; cd.RHS = h->RHS;
+  cd.MOM0 = h->MOM0; cd.MOM = h->MOM;
+  cd.diag = b->d_diag + c;
+  cd.cfl = h->cfg.cfl;
+  cd.hmin = h_min(h);
+  cd.visc_cap = h->cfg.b_visc * h->cfg.Re * cd.hmin * cd.hmin;
+  cd.dt_scale = 1.0;
+  cd.active = 1;
+  cd.pad = 0;
+}
+
+extern "C" {
+
+int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_batch** out) {
+  if (!out) return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: out is NULL");
+  *out = nullptr;
+  if (!cfgs || ncases < 1) return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: need at least one case");
+  for (int c = 1; c < ncases; c++)
+    if (cfgs[c].precision != cfgs[0].precision)
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same precision");
+  hweno_batch* b = new (std::nothrow) hweno_batch();
+  if (!b) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
+  snprintf(b->err, sizeof(b->err), "no error");
+  b->n = ncases;
+  b->mixed = cfgs[0].precision == HWENO_MIXED;
+  b->st = (cudaStream_t)stream;
+  if (!b->st) {  // graphs cannot be captured on the legacy default stream
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return fail(nullptr, HWENO_ERR_CUDA, "hweno_batch_init: stream creation failed");
+    }
+    b->own_stream = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  int rc = HWENO_OK;
+  for (int c = 0; c < ncases && !rc; c++) {
+    hweno_handle* h = nullptr;
+    rc = hweno_init(&cfgs[c], b->st, &h);
+    if (!rc) b->h.push_back(h);
+  }
+  if (!rc) {
+    cudaError_t e = cudaMalloc(&b->d_cases, ncases * sizeof(CaseDev));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_cases, ncases * sizeof(CaseDev));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_diag, ncases * sizeof(Diag));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_diag, ncases * sizeof(Diag));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_diag, 0, ncases * sizeof(Diag), b->st);
+    if (e != cudaSuccess) rc = bfail(b, HWENO_ERR_CUDA, "hweno_batch_init: allocation failed");
+  }
+  for (int k = 0; k < BR_N && !rc; k++) rc = build_list(b, k, k <= BR_INT ? 32 : 128, k <= BR_INT ? 4 : 1);
+  if (!rc) rc = batch_grids(b);
+  if (!rc) {
+    for (int c = 0; c < ncases; c++) batch_refresh_case(b, c);
+    rc = batch_upload(b);
+  }
+  if (!rc) rc = batch_capture(b);
+  if (rc) {
+    hweno_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return HWENO_OK;
+}
+
+void hweno_batch_destroy(hweno_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto* h : b->h) hweno_destroy(h);
+  for (int k = 0; k < BR_N; k++)
+    if (b->L[k].d) cudaFree(b->L[k].d);
+  if (b->d_cases) cudaFree(b->d_cases);
+  if (b->h_cases) cudaFreeHost(b->h_cases);
+  if (b->d_diag) cudaFree(b->d_diag);
+  if (b->h_diag) cudaFreeHost(b->h_diag);
+  if (b->own_stream) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+const char* hweno_batch_last_error(const hweno_batch* b) { return b ? b->err : g_init_err; }
+
+int hweno_batch_case(hweno_batch* b, int k, hweno_handle** h) {
+  if (!b || !h || k < 0 || k >= b->n) return bfail(b, HWENO_ERR_ARG, "hweno_batch_case: bad index");
+  *h = b->h[k];
+  return HWENO_OK;
+}
+
+long long hweno_batch_launch_count(const hweno_batch* b) { return b ? b->launches : 0; }
+
+// one replay of the step graph for the active cases, then the flags
+static int batch_attempt(hweno_batch* b) {
+  int rc = batch_upload(b);
+  if (rc) return rc;
+  BCK(cudaGraphLaunch(b->exec, b->st), "graph launch");
+  b->launches += 1 + 3 * ((b->mixed ? 7 : 6) + 3) + 1;  // reset, 3 stages, dt
+  BCK(cudaMemcpyAsync(b->h_diag, b->d_diag, b->n * sizeof(Diag), cudaMemcpyDeviceToHost, b->st), "diag read");
+  BCK(cudaStreamSynchronize(b->st), "stream synchronize");
+  return HWENO_OK;
+}
+
+int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections) {
+  if (!b || nsteps < 0) return bfail(b, HWENO_ERR_ARG, "hweno_batch_step: bad argument");
+  for (int c = 0; c < b->n; c++)
+    if (!b->h[c]->have_state) return bfail(b, HWENO_ERR_STATE, "hweno_batch_step: a case has no state");
+  int rej_total = 0;
+  std::vector<int> pending(b->n);
+  for (int s = 0; s < nsteps; s++) {
+    for (int c = 0; c < b->n; c++) {
+      batch_refresh_case(b, c);
+      pending[c] = 1;
+    }
+    for (int round = 0;; round++) {
+      int rc = batch_attempt(b);
+      if (rc) return rc;
+      int left = 0;
+      for (int c = 0; c < b->n; c++) {
+        if (!pending[c]) continue;
+        const Diag& d = b->h_diag[c];
+        hweno_handle* h = b->h[c];
+        if (!(d.flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE))) {
+          double* tmp = h->Q;
+          h->Q = h->QS;
+          h->QS = tmp;
+          h->t += d.dt;
+          h->dt_last = d.dt;
+          h->steps++;
+          h->rejected += round;
+          h->pp_total += (double)d.pp_count;
+          h->cell_stages += 3.0 * h->g.nx * (double)h->g.ny;
+          h->alpha = bits_to_double(d.alpha_bits);
+          h->beta = bits_to_double(d.beta_bits);
+          h->have_residual = false;
+          pending[c] = 0;
+          b->h_cases[c].active = 0;
+        } else {
+          left++;
+          b->h_cases[c].dt_scale *= 0.5;
+          b->h_cases[c].active = 1;
+        }
+      }
+      if (!left) break;
+      rej_total += left;
+      if (round + 1 > b->h[0]->cfg.max_halvings) {
+        if (rejections) *rejections = rej_total;
+        return bfail(b, HWENO_ERR_INADMISSIBLE, "hweno_batch_step: a case stayed inadmissible after max_halvings restarts");
+      }
+    }
+  }
+  if (rejections) *rejections = rej_total;
+  return HWENO_OK;
+}
+
+// Time each batched kernel of the spatial operator for the candidate block shapes on the
+// current states (one step is computed and discarded, so the states do not change), keep
+// the fastest shape per kernel, and re-capture the step graph.
+int hweno_batch_autotune(hweno_batch* b, int* chosen) {
+  if (!b) return bfail(b, HWENO_ERR_ARG, "hweno_batch_autotune: NULL batch");
+  for (int c = 0; c < b->n; c++)
+    if (!b->h[c]->have_state) return bfail(b, HWENO_ERR_STATE, "hweno_batch_autotune: a case has no state");
+  static const int shapes[4][2] = {{32, 4}, {16, 8}, {64, 2}, {128, 1}};
+  for (int c = 0; c < b->n; c++) batch_refresh_case(b, c);
+  int rc = batch_upload(b);
+  if (rc) return rc;
+  batch_enqueue_step(b);  // fills every scratch plane; QS is overwritten next step anyway
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0), "event");
+  BCK(cudaEventCreate(&e1), "event");
+  const int n = b->n;
+  for (int k = BR_CONS; k <= BR_INT; k++) {
+    float best = 1e30f;
+    int bi = 0;
+    for (int si = 0; si < 4; si++) {
+      if ((rc = build_list(b, k, shapes[si][0], shapes[si][1]))) return rc;
+      batch_grids(b);
+      const dim3 blk(shapes[si][0], shapes[si][1]);
+      const int gr = b->L[k].grid;
+      const TileList tl = b->L[k].tl();
+      float ms_sum = 0.f;
+      for (int rep = 0; rep < 3; rep++) {
+        BCK(cudaEventRecord(e0, b->st), "event");
+        switch (k) {
+          case BR_CONS:
+            if (b->mixed) kb_cons<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
+            else kb_cons<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
+            break;
+          case BR_FACE:
+            if (b->mixed) kb_face_moments<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            else kb_face_moments<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            break;
+          case BR_WEAK:
+            if (b->mixed) kb_weak_moments<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            else kb_weak_moments<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            break;
+          case BR_GRAD:
+            if (b->mixed) kb_grad<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            else kb_grad<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            break;
+          case BR_FLUX:
+            if (b->mixed) kb_flux<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            else kb_flux<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            break;
+          default:
+            if (b->mixed) kb_assemble<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
+            else kb_assemble<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
+            break;
+        }
+        b->launches++;
+        BCK(cudaEventRecord(e1, b->st), "event");
+        BCK(cudaEventSynchronize(e1), "event");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_sum += ms;  // the first launch warms the caches
+      }
+      if (ms_sum < best) {
+        best = ms_sum;
+        bi = si;
+      }
+    }
+    if ((rc = build_list(b, k, shapes[bi][0], shapes[bi][1]))) return rc;
+    if (chosen) chosen[k] = bi;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  batch_grids(b);
+  BCK(cudaStreamSynchronize(b->st), "stream synchronize");
+  return batch_capture(b);
 }
 
 }  // extern "C"

@@ -1,0 +1,166 @@
+// Batched kernels: one launch of each spatial-operator kernel advances every case of an
+// ensemble of independent problems with their own grids.  Blocks are persistent: a grid
+// sized to the SMs loops over a work list of (case, tile) items, where a case's tiles
+// cover that kernel's launch region.  The per-cell work is the single-grid bodies.
+#pragma once
+#include "hweno_mixed.cuh"
+
+namespace hw {
+
+// device description of one case of a batch
+struct CaseDev {
+  Grid g;
+  Work w;
+  double *Q, *QS, *BASE, *RHS0, *RHS, *MOM0, *MOM;
+  Diag* diag;
+  double cfl, hmin, visc_cap;  // time-step rule of Sec. 5
+  double dt_scale;             // 1, or 2^-k after k restarts of this step
+  int active;                  // 0: the case does no work in this launch
+  int pad;
+};
+
+// work list of one kernel: case c owns items [start[c], start[c+1]); its tiles are
+// tx[c] x ty[c] per z-slice of the launch region
+struct TileList {
+  const int* start;
+  const int* tx;
+  const int* ty;
+};
+
+__device__ __forceinline__ int find_case(const int* start, int ncase, int t) {
+  int lo = 0, hi = ncase - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// position of this thread in case c's launch region for work item t
+__device__ __forceinline__ void tile_pos(const TileList& L, int c, int t, int& gx, int& gy, int& gz) {
+  int l = t - L.start[c];
+  const int per = L.tx[c] * L.ty[c];
+  gz = l / per;
+  l -= gz * per;
+  const int by = l / L.tx[c], bx = l - by * L.tx[c];
+  gx = bx * blockDim.x + threadIdx.x;
+  gy = by * blockDim.y + threadIdx.y;
+}
+
+#define HW_BATCH_LOOP(L, ncase)                                   \
+  const int total_ = (L).start[ncase];                             \
+  for (int t_ = blockIdx.x; t_ < total_; t_ += gridDim.x) {        \
+    const int c_ = find_case((L).start, ncase, t_);                \
+    const CaseDev& cd = cases[c_];                                 \
+    if (!cd.active) continue;                                      \
+    int gx, gy, gz;                                                \
+    tile_pos(L, c_, t_, gx, gy, gz);                               \
+    (void)gz;
+
+#define HW_BATCH_END }
+
+// which = 0: stage 1 (state Q, residual into RHS0/MOM0); 1: stages 2, 3 (QS -> RHS/MOM)
+template <int MIXED>
+__global__ void __launch_bounds__(128) kb_cons(const CaseDev* __restrict__ cases, TileList L, int ncase, int which) {
+  HW_BATCH_LOOP(L, ncase)
+  const double* q = which == 0 ? cd.Q : cd.QS;
+  double* mom = which == 0 ? cd.MOM0 : cd.MOM;
+  if (MIXED) cons_mixed_body(cd.g, q, cd.w, mom, cd.diag, gx, gy);
+  else cons_body<double>(cd.g, q, cd.w, mom, cd.diag, gx, gy);
+  HW_BATCH_END
+}
+
+template <int MIXED>
+__global__ void kb_face_moments(const CaseDev* __restrict__ cases, TileList L, int ncase) {
+  HW_BATCH_LOOP(L, ncase)
+  if (MIXED) face_moments_mixed_body(cd.g, cd.w, gx, gy, gz);
+  else face_moments_body(cd.g, cd.w, gx, gy, gz);
+  HW_BATCH_END
+}
+
+template <int MIXED>
+__global__ void kb_weak_moments(const CaseDev* __restrict__ cases, TileList L, int ncase) {
+  HW_BATCH_LOOP(L, ncase)
+  if (MIXED) weak_moments_mixed_body(cd.g, cd.w, gx, gy);
+  else weak_moments_body(cd.g, cd.w, gx, gy);
+  HW_BATCH_END
+}
+
+template <int MIXED>
+__global__ void __launch_bounds__(128) kb_grad(const CaseDev* __restrict__ cases, TileList L, int ncase) {
+  HW_BATCH_LOOP(L, ncase)
+  if (MIXED) grad_mixed_body(cd.g, cd.w, gx, gy);
+  else grad_body<double>(cd.g, cd.w, gx, gy);
+  HW_BATCH_END
+}
+
+template <int MIXED>
+__global__ void __launch_bounds__(128) kb_flux(const CaseDev* __restrict__ cases, TileList L, int ncase) {
+  HW_BATCH_LOOP(L, ncase)
+  if (MIXED) flux_mixed_body(cd.g, cd.w, cd.diag, gx, gy, gz);
+  else flux_body<double>(cd.g, cd.w, cd.diag, gx, gy, gz);
+  HW_BATCH_END
+}
+
+template <int MIXED>
+__global__ void __launch_bounds__(128) kb_assemble(const CaseDev* __restrict__ cases, TileList L, int ncase,
+                                                   int which) {
+  HW_BATCH_LOOP(L, ncase)
+  double* rhs = which == 0 ? cd.RHS0 : cd.RHS;
+  if (MIXED) assemble_mixed_body(cd.g, cd.w, rhs, cd.diag, gx, gy);
+  else assemble_body<double>(cd.g, cd.w, rhs, cd.diag, gx, gy);
+  HW_BATCH_END
+}
+
+__global__ void __launch_bounds__(128) kb_rk(const CaseDev* __restrict__ cases, TileList L, int ncase, int stage) {
+  HW_BATCH_LOOP(L, ncase)
+  if (stage == 1) rk_body(cd.g, 1, cd.Q, cd.MOM0, cd.RHS0, cd.BASE, cd.QS, cd.diag, gx, gy);
+  else rk_body(cd.g, stage, cd.QS, cd.MOM, cd.RHS, cd.BASE, cd.QS, cd.diag, gx, gy);
+  HW_BATCH_END
+}
+
+// ghost fill: 1D items, gx = element index (x pass: 8 ny, y pass: 8 (nx + 8))
+__global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int pass) {
+  HW_BATCH_LOOP(L, ncase)
+  double* q = which == 0 ? cd.Q : cd.QS;
+  if (pass == 0) ghost_x_body(cd.g, q, gx);
+  else ghost_y_body(cd.g, q, gx);
+  HW_BATCH_END
+}
+
+// hi/lo split of the mixed path: 1D items over the 12 whole padded planes
+__global__ void kb_split(const CaseDev* __restrict__ cases, TileList L, int ncase, int which) {
+  HW_BATCH_LOOP(L, ncase)
+  const double* q = which == 0 ? cd.Q : cd.QS;
+  const long long n = 12 * cd.g.ps;
+  if (gx < n) {
+    float* hilo = mixed_planes(cd.w, cd.g.ps).hilo;
+    float hi, lo;
+    split_hilo(q[gx], hi, lo);
+    hilo[gx] = hi;
+    hilo[n + gx] = lo;
+  }
+  HW_BATCH_END
+}
+
+// per-case reductions: reset before a step, time step after the stage-1 residual
+__global__ void kb_reset(const CaseDev* __restrict__ cases, int ncase) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncase || !cases[c].active) return;
+  Diag* d = cases[c].diag;
+  d->alpha_bits = 0ull;
+  d->beta_bits = 0ull;
+  d->pp_count = 0ull;
+  d->flags = 0u;
+}
+
+__global__ void kb_dt(const CaseDev* __restrict__ cases, int ncase) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncase || !cases[c].active) return;
+  const CaseDev& cd = cases[c];
+  const double a = __longlong_as_double((long long)cd.diag->alpha_bits);
+  cd.diag->dt = fmin(cd.cfl * cd.hmin / a, cd.visc_cap) * cd.dt_scale;
+}
+
+}  // namespace hw

@@ -95,8 +95,8 @@ __device__ __forceinline__ double bc_sign(int bc, int normal_dir, int v) {
   return (v == 1 + normal_dir) ? -1.0 : 1.0;  // symmetry/slip: normal momentum odd
 }
 
-__global__ void k_ghost_x(Grid g, double* q) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // over 8 ghost columns x ny rows
+__device__ __forceinline__ void ghost_x_body(const Grid& g, double* q, int t) {
+  // t over 8 ghost columns x ny rows
   if (t >= 8 * g.ny) return;
   const int j = t / 8, c = t % 8;
   const int side = c / 4, k = c % 4;  // side 0: i = -1-k, side 1: i = nx+k
@@ -116,9 +116,9 @@ __global__ void k_ghost_x(Grid g, double* q) {
     }
 }
 
-__global__ void k_ghost_y(Grid g, double* q) {
+__device__ __forceinline__ void ghost_y_body(const Grid& g, double* q, int t) {
+  // t over 8 ghost rows x padded width
   const int W = g.nx + 2 * NG;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // over 8 ghost rows x padded width
   if (t >= 8 * W) return;
   const int r = t / W, i = t % W - NG;
   const int side = r / 4, k = r % 4;
@@ -137,6 +137,9 @@ __global__ void k_ghost_y(Grid g, double* q) {
       q[(4 * m + v) * g.ps + d] = sg * q[(4 * m + v) * g.ps + s];
     }
 }
+
+__global__ void k_ghost_x(Grid g, double* q) { ghost_x_body(g, q, blockIdx.x * blockDim.x + threadIdx.x); }
+__global__ void k_ghost_y(Grid g, double* q) { ghost_y_body(g, q, blockIdx.x * blockDim.x + threadIdx.x); }
 
 // ---------------------------------------------------------------------------
 // gather the 17 data of one conserved variable (plane offset v) around (i, j) in the

@@ -10,7 +10,7 @@
 // half), so offsets from a cell's own average, (hi_k - hi_c) + (lo_k - lo_c), are
 // exact to FP32 rounding of the offset itself rather than of the average.
 #pragma once
-#include "hweno_kernels.cuh"
+#include "hweno_ops.cuh"
 
 namespace hw {
 
@@ -110,10 +110,10 @@ __device__ __forceinline__ bool clearly_fine(const float* s, float rho_ref) {
   return s[0] > 1e-4f * rho_ref && ie > 1e-2f * (fabsf(s[3] * s[0]) + ke);
 }
 
-__global__ void __launch_bounds__(128) k_cons_mixed(Grid g, const double* __restrict__ q, Work w,
-                                                    double* __restrict__ mom, Diag* diag) {
-  const int i = blockIdx.x * 32 + threadIdx.x - 3;
-  const int j = blockIdx.y * 4 + threadIdx.y - 3;
+__device__ __forceinline__ void cons_mixed_body(const Grid& g, const double* __restrict__ q, const Work& w,
+                                                double* __restrict__ mom, Diag* diag, int gx, int gy) {
+  const int i = gx - 3;
+  const int j = gy - 3;
   unsigned long long pp = 0;
   unsigned int flags = 0;
   const WorkF f = mixed_planes(w, g.ps);
@@ -252,17 +252,17 @@ __global__ void __launch_bounds__(128) k_cons_mixed(Grid g, const double* __rest
   }
   pp = warp_sum_u64(pp);
   flags = __reduce_or_sync(0xffffffffu, flags);
-  if ((threadIdx.x & 31) == 0) {
+  if (lane_id() == 0) {
     if (pp) atomicAdd(&diag->pp_count, pp);
     if (flags) atomicOr(&diag->flags, flags);
   }
 }
 
 // Eq. (3.6) in FP32 on the float traces
-__global__ void k_face_moments_mixed(Grid g, Work w) {
-  const int dir = blockIdx.z;
-  const int i = blockIdx.x * 32 + threadIdx.x - (dir == 0 ? 3 : 2);
-  const int j = blockIdx.y * 4 + threadIdx.y - (dir == 0 ? 2 : 3);
+__device__ __forceinline__ void face_moments_mixed_body(const Grid& g, const Work& w, int gx, int gy, int gz) {
+  const int dir = gz;
+  const int i = gx - (dir == 0 ? 3 : 2);
+  const int j = gy - (dir == 0 ? 2 : 3);
   if (i >= g.nx + 2 || j >= g.ny + 2) return;
   const WorkF f = mixed_planes(w, g.ps);
   const long long cl = cidx(g, i, j);
@@ -290,9 +290,9 @@ __global__ void k_face_moments_mixed(Grid g, Work w) {
 }
 
 // Eqs. (3.7)-(3.8) in FP32
-__global__ void k_weak_moments_mixed(Grid g, Work w) {
-  const int i = blockIdx.x * 32 + threadIdx.x - 2;
-  const int j = blockIdx.y * 4 + threadIdx.y - 2;
+__device__ __forceinline__ void weak_moments_mixed_body(const Grid& g, const Work& w, int gx, int gy) {
+  const int i = gx - 2;
+  const int j = gy - 2;
   if (i >= g.nx + 2 || j >= g.ny + 2) return;
   const WorkF f = mixed_planes(w, g.ps);
   const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
@@ -315,9 +315,9 @@ __global__ void k_weak_moments_mixed(Grid g, Work w) {
 }
 
 // Eq. (3.9) in FP32 on offsets from the centre value
-__global__ void __launch_bounds__(128) k_grad_mixed(Grid g, Work w) {
-  const int i = blockIdx.x * 32 + threadIdx.x - 1;
-  const int j = blockIdx.y * 4 + threadIdx.y - 1;
+__device__ __forceinline__ void grad_mixed_body(const Grid& g, const Work& w, int gx, int gy) {
+  const int i = gx - 1;
+  const int j = gy - 1;
   if (i >= g.nx + 1 || j >= g.ny + 1) return;
   const WorkF f = mixed_planes(w, g.ps);
   const long long c = cidx(g, i, j);
@@ -361,10 +361,10 @@ __global__ void __launch_bounds__(128) k_grad_mixed(Grid g, Work w) {
 
 // Eq. (3.3) in FP32; the face fluxes are stored in FP64 so that the moment balances
 // difference them exactly
-__global__ void __launch_bounds__(128) k_flux_mixed(Grid g, Work w, Diag* diag) {
-  const int dir = blockIdx.z;
-  const int i = blockIdx.x * 32 + threadIdx.x - (dir == 0 ? 1 : 0);
-  const int j = blockIdx.y * 4 + threadIdx.y - (dir == 0 ? 0 : 1);
+__device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Diag* diag, int gx, int gy, int gz) {
+  const int dir = gz;
+  const int i = gx - (dir == 0 ? 1 : 0);
+  const int j = gy - (dir == 0 ? 0 : 1);
   float amax = 0.f, bmax = 0.f;
   const WorkF f = mixed_planes(w, g.ps);
   if (i < g.nx && j < g.ny) {
@@ -427,17 +427,17 @@ __global__ void __launch_bounds__(128) k_flux_mixed(Grid g, Work w, Diag* diag) 
   }
   amax = warp_max(amax);
   bmax = warp_max(bmax);
-  if ((threadIdx.x & 31) == 0) {
+  if (lane_id() == 0) {
     atomic_max_pos(&diag->alpha_bits, (double)amax);
     atomic_max_pos(&diag->beta_bits, (double)bmax);
   }
 }
 
 // Eq. (3.2): volume fluxes in FP32, face-flux sums and the balances in FP64
-__global__ void __launch_bounds__(128) k_assemble_mixed(Grid g, Work w, double* __restrict__ rhs,
-                                                        Diag* diag) {
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 4 + threadIdx.y;
+__device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w, double* __restrict__ rhs,
+                                                    Diag* diag, int gx, int gy) {
+  const int i = gx;
+  const int j = gy;
   unsigned int bad = 0;
   const WorkF f = mixed_planes(w, g.ps);
   if (i < g.nx && j < g.ny) {
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(128) k_assemble_mixed(Grid g, Work w, double* 
     }
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&diag->flags, bad);
+  if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
 }
 
 // float planes back to a contiguous double array (debug output of the mixed path)
@@ -505,6 +505,29 @@ __global__ void k_gather_cons_f(Grid g, const float* __restrict__ src, double* _
     dst[2 * N + r] = rho * v;
     dst[3 * N + r] = rho * (e + 0.5 * (u * u + v * v));
   }
+}
+
+// single-grid kernels of the mixed path
+__global__ void __launch_bounds__(128) k_cons_mixed(Grid g, const double* __restrict__ q, Work w,
+                                                    double* __restrict__ mom, Diag* diag) {
+  cons_mixed_body(g, q, w, mom, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
+__global__ void k_face_moments_mixed(Grid g, Work w) {
+  face_moments_mixed_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
+                          blockIdx.z);
+}
+__global__ void k_weak_moments_mixed(Grid g, Work w) {
+  weak_moments_mixed_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
+__global__ void __launch_bounds__(128) k_grad_mixed(Grid g, Work w) {
+  grad_mixed_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
+__global__ void __launch_bounds__(128) k_flux_mixed(Grid g, Work w, Diag* diag) {
+  flux_mixed_body(g, w, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
+                  blockIdx.z);
+}
+__global__ void __launch_bounds__(128) k_assemble_mixed(Grid g, Work w, double* __restrict__ rhs, Diag* diag) {
+  assemble_mixed_body(g, w, rhs, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 }  // namespace hw

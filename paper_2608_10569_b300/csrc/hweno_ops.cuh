@@ -1,0 +1,401 @@
+// Per-cell bodies of the spatial-operator kernels and the SSP-RK3 stage, as device
+// functions of the position (gx, gy[, gz]) in the launch region of each kernel.  The
+// single-grid kernels (hweno.cu) call them with gx = blockIdx.x*blockDim.x +
+// threadIdx.x; the batched kernels map persistent blocks over a (case, tile) list.
+// Each kernel's launch region and its offset to cell indices (i, j):
+//   cons          (nx+6) x (ny+6)        i = gx - 3, j = gy - 3
+//   face moments  (nx+5) x (ny+5) x 2    z = 0: i = gx - 3, j = gy - 2; z = 1: i = gx - 2, j = gy - 3
+//   weak moments  (nx+4) x (ny+4)        i = gx - 2, j = gy - 2
+//   grad          (nx+2) x (ny+2)        i = gx - 1, j = gy - 1
+//   flux          (nx+1) x (ny+1) x 2    z = 0: i = gx - 1, j = gy; z = 1: i = gx, j = gy - 1
+//   assemble, rk  nx x ny                i = gx, j = gy
+#pragma once
+#include "hweno_kernels.cuh"
+
+namespace hw {
+
+// lane of the calling thread in its warp, for any block shape
+__device__ __forceinline__ int lane_id() { return (threadIdx.x + threadIdx.y * blockDim.x) & 31; }
+
+
+// ---------------------------------------------------------------------------
+// conservative characteristic reconstruction, modified moments and PP limiter of
+// every cell of the interior grown by 3 (Sec. 3.1, Eq. (3.4), Appendix A.2)
+template <class T>
+__device__ __forceinline__ void cons_body(const Grid& g, const double* __restrict__ q, const Work& w,
+                                          double* __restrict__ mom, Diag* diag, int gx, int gy) {
+  const int i = gx - 3;
+  const int j = gy - 3;
+  unsigned long long pp = 0;
+  unsigned int flags = 0;
+  if (i < g.nx + 3 && j < g.ny + 3) {
+    constexpr bool OFF = sizeof(T) == 4;  // FP32: reconstruct offsets from the average
+    const long long c = cidx(g, i, j);
+    double ub[4];
+    T cc[4][15], sl[4][4], ctr[4];
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      double d[17];
+      gather17<OFF>(g, q, v, i, j, d);
+      ub[v] = q[(long long)v * g.ps + c];
+      T dt[17];
+#pragma unroll
+      for (int k = 0; k < 17; k++) dt[k] = (T)d[k];
+      hw_p0_coeffs<T>(dt, cc[v]);
+      sl[v][0] = (T)(d[4] - d[3]);
+      sl[v][1] = (T)(d[5] - d[4]);
+      sl[v][2] = (T)(d[4] - d[1]);
+      sl[v][3] = (T)(d[7] - d[4]);
+      ctr[v] = OFF ? T(0) : (T)ub[v];
+    }
+    const T ut[4] = {(T)ub[0], (T)ub[1], (T)ub[2], (T)ub[3]};
+    const T eps = (T)g.eps_weno;
+    double face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
+    CharState<T> cs;
+    char_state<T>(ut, (T)g.gamma, cs);
+    recon_dir<T, 0, double>(cc, sl, ctr, cs, eps, face, volx, mx);
+    recon_dir<T, 1, double>(cc, sl, ctr, cs, eps, face + 6, vol, my);
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        if (OFF) face[k][v] += ub[v];
+#pragma unroll
+      for (int k = 0; k < 9; k++) {
+        vol[k][v] = 0.5 * (volx[k][v] + vol[k][v]);
+        if (OFF) vol[k][v] += ub[v];
+      }
+    }
+    double th[2] = {1.0, 1.0};
+    const double pb = pressure(ub, g.gamma);
+    const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+    if (!(ub[0] > 0.0) || !(pb > 0.0)) {
+      flags |= FLAG_BADAVG;
+    } else if (pp_limit(ub, face, vol, g.gamma, g.eps_pp, th) && interior) {
+      pp = 1;
+    }
+    // primitive (rho, u, v, e) at the 12 limited face points and the 9 volume points
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const double rr = 1.0 / face[k][0];
+      const double u = face[k][1] * rr, v = face[k][2] * rr;
+      const double e = face[k][3] * rr - 0.5 * (u * u + v * v);
+      w.face[(long long)(4 * k + 0) * g.ps + c] = face[k][0];
+      w.face[(long long)(4 * k + 1) * g.ps + c] = u;
+      w.face[(long long)(4 * k + 2) * g.ps + c] = v;
+      w.face[(long long)(4 * k + 3) * g.ps + c] = e;
+    }
+    double wb[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int G = 0; G < 3; G++)
+#pragma unroll
+      for (int H = 0; H < 3; H++) {
+        const int k = 3 * G + H;
+        const double rr = 1.0 / vol[k][0];
+        const double u = vol[k][1] * rr, v = vol[k][2] * rr;
+        const double e = vol[k][3] * rr - 0.5 * (u * u + v * v);
+        w.vol[(long long)(4 * k + 0) * g.ps + c] = vol[k][0];
+        w.vol[(long long)(4 * k + 1) * g.ps + c] = u;
+        w.vol[(long long)(4 * k + 2) * g.ps + c] = v;
+        w.vol[(long long)(4 * k + 3) * g.ps + c] = e;
+        const double wgt = gweight<double>(G) * gweight<double>(H);
+        wb[0] += wgt * u;
+        wb[1] += wgt * v;
+        wb[2] += wgt * e;
+      }
+#pragma unroll
+    for (int n = 0; n < 3; n++) w.wbar[(long long)n * g.ps + c] = wb[n];
+    w.theta[c] = th[0];
+    w.theta[g.ps + c] = th[1];
+    if (interior) {
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        mom[(long long)v * g.ps + c] = mx[v];
+        mom[(long long)(4 + v) * g.ps + c] = my[v];
+      }
+    }
+  }
+  // block reduction of the activation count and flags: one atomic per warp
+  pp = warp_sum_u64(pp);
+  flags = __reduce_or_sync(0xffffffffu, flags);
+  if (lane_id() == 0) {
+    if (pp) atomicAdd(&diag->pp_count, pp);
+    if (flags) atomicOr(&diag->flags, flags);
+  }
+}
+
+// face moments W^{x,0}, W^{x,1} (blockIdx.z = 0) of the x-faces right of cells
+// i in [-3, nx+2), j in [-2, ny+2), and W^{y,0}, W^{y,1} (z = 1) of the y-faces
+// above cells i in [-2, nx+2), j in [-3, ny+2)  (Eq. (3.6) with the interface
+// average of the two traces)
+__device__ __forceinline__ void face_moments_body(const Grid& g, const Work& w, int gx, int gy, int gz) {
+  const int dir = gz;
+  const int i = gx - (dir == 0 ? 3 : 2);
+  const int j = gy - (dir == 0 ? 2 : 3);
+  if (i >= g.nx + 2 || j >= g.ny + 2) return;
+  const long long cl = cidx(g, i, j);
+  const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
+  const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
+  double W0[3] = {0.0, 0.0, 0.0}, W1[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int gp = 0; gp < 3; gp++) {
+    const double wg = gweight<double>(gp), xg = gnode<double>(gp);
+#pragma unroll
+    for (int n = 0; n < 3; n++) {
+      const double a = w.face[(long long)(4 * (kl + gp) + 1 + n) * g.ps + cl];
+      const double b = w.face[(long long)(4 * (kr + gp) + 1 + n) * g.ps + cr];
+      const double h = 0.5 * (a + b);
+      W0[n] += wg * h;
+      W1[n] += wg * h * xg;
+    }
+  }
+  double* out = dir == 0 ? w.wx : w.wy;
+#pragma unroll
+  for (int n = 0; n < 3; n++) {
+    out[(long long)n * g.ps + cl] = W0[n];
+    out[(long long)(3 + n) * g.ps + cl] = W1[n];
+  }
+}
+
+// weak-derivative moments (Eqs. (3.7)-(3.8)) of cells in the interior grown by 2
+__device__ __forceinline__ void weak_moments_body(const Grid& g, const Work& w, int gx, int gy) {
+  const int i = gx - 2;
+  const int j = gy - 2;
+  if (i >= g.nx + 2 || j >= g.ny + 2) return;
+  const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
+  const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+#pragma unroll
+  for (int n = 0; n < 3; n++) {
+    const double xr0 = w.wx[(long long)n * g.ps + c], xl0 = w.wx[(long long)n * g.ps + cl];
+    const double xr1 = w.wx[(long long)(3 + n) * g.ps + c], xl1 = w.wx[(long long)(3 + n) * g.ps + cl];
+    const double yt0 = w.wy[(long long)n * g.ps + c], yb0 = w.wy[(long long)n * g.ps + cb];
+    const double yt1 = w.wy[(long long)(3 + n) * g.ps + c], yb1 = w.wy[(long long)(3 + n) * g.ps + cb];
+    const double wb = w.wbar[(long long)n * g.ps + c];
+    double* r = w.rm + (long long)(6 * n) * g.ps + c;
+    r[0] = (xr0 - xl0) * rdx;
+    r[g.ps] = (0.5 * (xr0 + xl0) - wb) * rdx;
+    r[2 * g.ps] = (xr1 - xl1) * rdx;
+    r[3 * g.ps] = (yt0 - yb0) * rdy;
+    r[4 * g.ps] = (yt1 - yb1) * rdy;
+    r[5 * g.ps] = (0.5 * (yt0 + yb0) - wb) * rdy;
+  }
+}
+
+// gradient reconstruction (Eq. (3.9)): the scalar HWENO of Appendix A.2 applied to
+// the weak-derivative moments of each of u, v, e in each direction, on cells of the
+// interior grown by 1; values at the 12 face and 9 volume points
+template <class T>
+__device__ __forceinline__ void grad_body(const Grid& g, const Work& w, int gx, int gy) {
+  const int i = gx - 1;
+  const int j = gy - 1;
+  if (i >= g.nx + 1 || j >= g.ny + 1) return;
+  const long long c = cidx(g, i, j);
+  const T eps = (T)g.eps_weno;
+#pragma unroll 1
+  for (int comp = 0; comp < 6; comp++) {
+    const int n = comp >> 1, l = comp & 1;
+    const double* A = w.rm + (long long)(6 * n + 3 * l) * g.ps;
+    const double* X = A + g.ps;
+    const double* Y = A + 2 * g.ps;
+    constexpr bool OFF = sizeof(T) == 4;  // FP32: reconstruct offsets from the centre value
+    const double cen = OFF ? A[c] : 0.0;
+    T d[17];
+#pragma unroll
+    for (int b = -1; b <= 1; b++)
+#pragma unroll
+      for (int a = -1; a <= 1; a++) d[(b + 1) * 3 + (a + 1)] = (T)(A[cidx(g, i + a, j + b)] - cen);
+    if (OFF) d[4] = T(0);
+    d[9] = (T)X[cidx(g, i - 1, j)];
+    d[10] = (T)X[cidx(g, i + 1, j)];
+    d[11] = (T)Y[cidx(g, i, j - 1)];
+    d[12] = (T)Y[cidx(g, i, j + 1)];
+    d[13] = (T)X[cidx(g, i, j - 1)];
+    d[14] = (T)X[cidx(g, i, j + 1)];
+    d[15] = (T)Y[cidx(g, i - 1, j)];
+    d[16] = (T)Y[cidx(g, i + 1, j)];
+    T C[15];
+    hweno_combine<T>(d, eps, C);
+    T vx[6], vy[6], vv[9];
+    eval_xfaces<T>(C, vx);
+    eval_yfaces<T>(C, vy);
+    eval_vol<T>(C, vv);
+    double* out = w.gr + (long long)comp * g.ps + c;
+    // FP64: the values themselves; FP32: offsets, restored in FP64
+#pragma unroll
+    for (int k = 0; k < 6; k++) out[(long long)(6 * k) * g.ps] = OFF ? cen + (double)vx[k] : (double)vx[k];
+#pragma unroll
+    for (int k = 0; k < 6; k++) out[(long long)(6 * (6 + k)) * g.ps] = OFF ? cen + (double)vy[k] : (double)vy[k];
+#pragma unroll
+    for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = OFF ? cen + (double)vv[k] : (double)vv[k];
+  }
+}
+
+// PP local Lax-Friedrichs fluxes (Eq. (3.3)) of the interior faces: x-faces right
+// of cells i in [-1, nx), j in [0, ny) (blockIdx.z = 0); y-faces above cells
+// i in [0, nx), j in [-1, ny) (z = 1).  Also the face maxima alpha* and beta.
+template <class T>
+__device__ __forceinline__ void flux_body(const Grid& g, const Work& w, Diag* diag, int gx, int gy, int gz) {
+  const int dir = gz;
+  const int i = gx - (dir == 0 ? 1 : 0);
+  const int j = gy - (dir == 0 ? 0 : 1);
+  double amax = 0.0, bmax = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const long long cl = cidx(g, i, j);
+    const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
+    const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
+    const T gam = (T)g.gamma, rPr = (T)(1.0 / g.Pr), rRe = (T)(1.0 / g.Re);
+    T st[2][3][4], gs[2][3][6];
+#pragma unroll
+    for (int gp = 0; gp < 3; gp++)
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        const long long cc = s == 0 ? cl : cr;
+        const int k = (s == 0 ? kl : kr) + gp;
+#pragma unroll
+        for (int v = 0; v < 4; v++) st[s][gp][v] = (T)w.face[(long long)(4 * k + v) * g.ps + cc];
+#pragma unroll
+        for (int n = 0; n < 6; n++) gs[s][gp][n] = (T)w.gr[(long long)(6 * k + n) * g.ps + cc];
+      }
+    T beta = T(0);
+#pragma unroll
+    for (int gp = 0; gp < 3; gp++)
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        beta = fmax(beta, wave_bound<T>(dir, st[s][gp], gs[s][gp], gam, rPr, rRe));
+        const T cs = sqrt(gam * (gam - T(1)) * st[s][gp][3]);
+        amax = fmax(amax, (double)fmax(fabs(st[s][gp][1]) + cs, fabs(st[s][gp][2]) + cs));
+      }
+    bmax = (double)beta;
+    // the moment balances use each face's fluxes only through the Gauss sums
+    // S0 = sum_g w_g fhat_g and S1 = sum_g w_g t_g fhat_g (t_g: the transverse Gauss
+    // offset): both cells read the same stored sums, so the telescoping is exact
+    T S0[4] = {T(0), T(0), T(0), T(0)}, S1[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int gp = 0; gp < 3; gp++) {
+      T fl[4], fr[4], ul[4], ur[4];
+      phys_flux<T>(dir, st[0][gp], gs[0][gp], gam, rPr, rRe, fl);
+      phys_flux<T>(dir, st[1][gp], gs[1][gp], gam, rPr, rRe, fr);
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        T* u = s == 0 ? ul : ur;
+        const T* p = st[s][gp];
+        u[0] = p[0];
+        u[1] = p[0] * p[1];
+        u[2] = p[0] * p[2];
+        u[3] = p[0] * (p[3] + T(0.5) * (p[1] * p[1] + p[2] * p[2]));
+      }
+      const T wg = gweight<T>(gp), wt = gweight<T>(gp) * gnode<T>(gp);
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        const T fh = T(0.5) * (fl[v] + fr[v] - beta * (ur[v] - ul[v]));
+        S0[v] += wg * fh;
+        if (gp != 1) S1[v] += wt * fh;
+      }
+    }
+    double* out = (dir == 0 ? w.fx : w.fy) + cl;
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      out[(long long)v * g.ps] = (double)S0[v];
+      out[(long long)(4 + v) * g.ps] = (double)S1[v];
+    }
+  }
+  amax = warp_max(amax);
+  bmax = warp_max(bmax);
+  if (lane_id() == 0) {
+    atomic_max_pos(&diag->alpha_bits, amax);
+    atomic_max_pos(&diag->beta_bits, bmax);
+  }
+}
+
+// moment balances Eq. (3.2) of the interior cells
+template <class T>
+__device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, double* __restrict__ rhs,
+                                              Diag* diag, int gx, int gy) {
+  const int i = gx;
+  const int j = gy;
+  unsigned int bad = 0;
+  if (i < g.nx && j < g.ny) {
+    const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
+    const T gam = (T)g.gamma, rPr = (T)(1.0 / g.Pr), rRe = (T)(1.0 / g.Re);
+    // volume quadrature of f and g at the tensor Gauss points
+    double vf[4] = {0, 0, 0, 0}, vg[4] = {0, 0, 0, 0};
+#pragma unroll 1
+    for (int G = 0; G < 3; G++)
+#pragma unroll
+      for (int H = 0; H < 3; H++) {
+        const int k = 3 * G + H;
+        T st[4], gs[6], f[4], h[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) st[v] = (T)w.vol[(long long)(4 * k + v) * g.ps + c];
+#pragma unroll
+        for (int n = 0; n < 6; n++) gs[n] = (T)w.gr[(long long)(6 * (12 + k) + n) * g.ps + c];
+        phys_flux<T>(0, st, gs, gam, rPr, rRe, f);
+        phys_flux<T>(1, st, gs, gam, rPr, rRe, h);
+        const double wgt = gweight<double>(G) * gweight<double>(H);
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+          vf[v] += wgt * (double)f[v];
+          vg[v] += wgt * (double)h[v];
+        }
+      }
+    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      // face Gauss sums: S0 = sum w_g fhat_g, S1 = sum w_g t_g fhat_g (see k_flux)
+      const double fR0 = w.fx[(long long)v * g.ps + c], fL0 = w.fx[(long long)v * g.ps + cl];
+      const double fR1 = w.fx[(long long)(4 + v) * g.ps + c], fL1 = w.fx[(long long)(4 + v) * g.ps + cl];
+      const double gT0 = w.fy[(long long)v * g.ps + c], gB0 = w.fy[(long long)v * g.ps + cb];
+      const double gT1 = w.fy[(long long)(4 + v) * g.ps + c], gB1 = w.fy[(long long)(4 + v) * g.ps + cb];
+      const double r0 = -(fR0 - fL0) * rdx - (gT0 - gB0) * rdy;
+      const double r1 = -(fL0 + fR0) * (0.5 * rdx) - (gT1 - gB1) * rdy + vf[v] * rdx;
+      const double r2 = -(fR1 - fL1) * rdx - (gB0 + gT0) * (0.5 * rdy) + vg[v] * rdy;
+      rhs[(long long)v * g.ps + c] = r0;
+      rhs[(long long)(4 + v) * g.ps + c] = r1;
+      rhs[(long long)(8 + v) * g.ps + c] = r2;
+      if (!isfinite(r0) || !isfinite(r1) || !isfinite(r2)) bad = FLAG_NONFINITE;
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
+}
+
+// SSP-RK3 stage with modified moments (Eq. (2.10), 2D analogue) on interior cells:
+//   stage 1: out = [u^n; vhat^n] + dt F,                        base = [u^n; vhat^n]
+//   stage 2: out = 3/4 base + 1/4 ([u^(1); vhat^(1)] + dt F)
+//   stage 3: out = 1/3 base + 2/3 ([u^(2); vhat^(2)] + dt F)
+// plus the admissibility test of the output averages (Sec. 5).
+__device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* __restrict__ qin,
+                                        const double* __restrict__ mom, const double* __restrict__ rhs,
+                                        double* __restrict__ base, double* __restrict__ qout, Diag* diag,
+                                        int gx, int gy) {
+  const int i = gx;
+  const int j = gy;
+  unsigned int bad = 0;
+  if (i < g.nx && j < g.ny) {
+    const long long c = cidx(g, i, j);
+    const double dt = diag->dt;
+    double out[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const double cur = k < 4 ? qin[(long long)k * g.ps + c] : mom[(long long)(k - 4) * g.ps + c];
+      const double f = rhs[(long long)k * g.ps + c];
+      if (stage == 1) {
+        base[(long long)k * g.ps + c] = cur;
+        out[k] = cur + dt * f;
+      } else if (stage == 2) {
+        out[k] = 0.75 * base[(long long)k * g.ps + c] + 0.25 * (cur + dt * f);
+      } else {
+        out[k] = base[(long long)k * g.ps + c] * (1.0 / 3.0) + (2.0 / 3.0) * (cur + dt * f);
+      }
+      qout[(long long)k * g.ps + c] = out[k];
+      if (!isfinite(out[k])) bad = FLAG_INADMISSIBLE;
+    }
+    // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
+    const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
+    if (!(out[0] > 0.0) || !(rp > 0.0)) bad = FLAG_INADMISSIBLE;
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
+}
+
+}  // namespace hw

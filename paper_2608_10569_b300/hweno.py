@@ -80,6 +80,14 @@ SIGNATURES = [
     ("hweno_measure_peak", ctypes.c_int, [_H, ctypes.c_int, _D]),
     ("hweno_residual_noalloc", ctypes.c_int, [ctypes.POINTER(hweno_config), ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("hweno_batch_init", ctypes.c_int, [ctypes.POINTER(hweno_config), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    ("hweno_batch_destroy", None, [ctypes.c_void_p]),
+    ("hweno_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("hweno_batch_case", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_H)]),
+    ("hweno_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("hweno_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("hweno_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
 ]
 
 
@@ -249,3 +257,71 @@ class Solver:
         tf = ctypes.c_double(0.0)
         _check(self.h, self.lib.hweno_measure_peak(self.h, int(which), ctypes.byref(tf)))
         return tf.value
+
+
+class _CaseView(Solver):
+    """A case of a Batch: the Solver interface on a handle the batch owns."""
+
+    def __init__(self, lib, h, cfg):
+        self.lib = lib
+        self.h = h
+        self.cfg = cfg
+        self.nx, self.ny = cfg.nx, cfg.ny
+
+    def close(self):
+        self.h = None  # owned by the batch
+
+
+class Batch:
+    """An ensemble of independent problems advanced together (hweno_batch_*)."""
+
+    def __init__(self, case_params_list, precision="mixed", stream=None):
+        self.lib = load()
+        n = len(case_params_list)
+        cfgs = (hweno_config * n)()
+        for k, p in enumerate(case_params_list):
+            p = dict(p)
+            p["precision"] = precision
+            cfgs[k] = make_config(**p)
+        self.cfgs = cfgs
+        b = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        rc = self.lib.hweno_batch_init(cfgs, n, s, ctypes.byref(b))
+        if rc != HWENO_OK:
+            raise HwenoError(rc, self.lib.hweno_last_error(None).decode())
+        self.b = b
+        self.cases = []
+        for k in range(n):
+            h = _H()
+            self._check(self.lib.hweno_batch_case(self.b, k, ctypes.byref(h)))
+            self.cases.append(_CaseView(self.lib, h, cfgs[k]))
+
+    def _check(self, rc):
+        if rc != HWENO_OK:
+            raise HwenoError(rc, self.lib.hweno_batch_last_error(self.b).decode())
+
+    def step(self, nsteps=1):
+        rej = ctypes.c_int(0)
+        self._check(self.lib.hweno_batch_step(self.b, int(nsteps), ctypes.byref(rej)))
+        return rej.value
+
+    def autotune(self):
+        chosen = (ctypes.c_int * 6)()
+        self._check(self.lib.hweno_batch_autotune(self.b, chosen))
+        return list(chosen)
+
+    def launch_count(self):
+        return self.lib.hweno_batch_launch_count(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for c in self.cases:
+                c.close()
+            self.lib.hweno_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,97 @@
+"""Batched ensembles (hweno_batch_*): every case of a batch must follow exactly the
+steps its own single-grid solver takes (same kernels, same per-case time step), in
+FP64 and in the mixed path, also after the autotuner changed the tile shapes, and with
+per-case restarts."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2608_10569_b300 import hweno, inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return [I.random_smooth(16, 16, seed=1),
+            I.random_rough(37, 21, seed=2, bc=("noslip", "noslip", "noslip", "symmetry")),
+            I.taylor_green(32, 0.3, 500.0, 1 / 1.4, rho_pert=1e-2, seed=7),
+            I.random_smooth(24, 40, seed=3, bc=("slip", "symmetry", "periodic", "periodic")),
+            I.shock_tube(48, 24)]
+
+
+def _single(case, q, precision, nsteps):
+    s = hweno.Solver(case.params(), precision=precision)
+    s.set_state(torch.from_numpy(q).cuda())
+    dts = [s.step()[0] for _ in range(nsteps)]
+    out = s.get_state().cpu().numpy(), dts, s.diag()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_matches_single_solvers(precision, tune):
+    cases = _cases()
+    stream = torch.cuda.Stream()
+    b = hweno.Batch([c.params() for c, _ in cases], precision=precision, stream=stream)
+    with torch.cuda.stream(stream):
+        for view, (case, q) in zip(b.cases, cases):
+            view.set_state(torch.from_numpy(q).cuda())
+    stream.synchronize()
+    if tune:
+        chosen = b.autotune()
+        assert len(chosen) == 6 and all(0 <= c < 4 for c in chosen)
+    n0 = b.launch_count()
+    assert b.step(3) == 0
+    assert b.launch_count() > n0
+    for view, (case, q) in zip(b.cases, cases):
+        ref, dts, d1 = _single(case, q, precision, 3)
+        with torch.cuda.stream(stream):
+            got = view.get_state()
+        stream.synchronize()
+        d = view.diag()
+        assert d["steps"] == 3 and d["dt_last"] == dts[-1]
+        assert abs(d["t"] - sum(dts)) <= 1e-15 * sum(dts)
+        assert np.array_equal(got.cpu().numpy(), ref)
+    b.close()
+
+
+def test_batch_fp64_matches_the_oracle():
+    case, q = I.random_rough(37, 21, seed=2, bc=("noslip", "noslip", "noslip", "symmetry"))
+    b = hweno.Batch([case.params(), I.random_smooth(16, 16, seed=1)[0].params()], precision="fp64",
+                    stream=torch.cuda.Stream())
+    b.cases[0].set_state(q.copy())
+    b.cases[1].set_state(I.random_smooth(16, 16, seed=1)[1])
+    b.step(1)
+    qo, st = O.step(O.make_cfg(**case.params()), q)
+    got = b.cases[0].get_state(np.zeros_like(q))
+    scale = np.abs(q[:4]).reshape(4, -1).max(1)
+    err = max(np.abs(got[k] - qo[k]).max() / max(np.abs(qo[k]).max(), scale[k % 4]) for k in range(12))
+    assert err <= 1e-12
+    b.close()
+
+
+def test_batch_restarts_only_the_rejected_case():
+    """A shock tube whose CFL number is far above the stable one is rejected and
+    repeated with half its step (Sec. 5) while the other case advances once; both end
+    where their single-grid solvers end."""
+    fast, qf = I.shock_tube(48, 24)
+    fast.cfl = 8.0
+    fast.b_visc = 10.0
+    calm, qc = I.random_smooth(20, 20, seed=4)
+    b = hweno.Batch([fast.params(), calm.params()], precision="fp64", stream=torch.cuda.Stream())
+    b.cases[0].set_state(qf.copy())
+    b.cases[1].set_state(qc.copy())
+    rej = b.step(1)
+    assert rej > 0
+    for view, (case, q) in zip(b.cases, [(fast, qf), (calm, qc)]):
+        s = hweno.Solver(case.params())
+        s.set_state(q.copy())
+        s.step()
+        ref = s.get_state(np.zeros_like(q))
+        s.close()
+        assert np.array_equal(view.get_state(np.zeros_like(q)), ref)
+    assert b.cases[0].diag()["rejected"] == rej and b.cases[1].diag()["rejected"] == 0
+    b.close()
