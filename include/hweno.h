@@ -180,6 +180,37 @@ int hweno_measure_peak(hweno_handle* h, int which, double* tflops);
  * (the count bench tools report as gpu_launches). */
 long long hweno_launch_count(const hweno_handle* h);
 
+/* ---- Discrete adjoint (FP64) -----------------------------------------------------
+ * Hand-written vector-Jacobian products of the SSP-RK3 step of Eq. (2.10) (2D
+ * analogue) with the spatial operator of Eq. (3.2): the characteristic HWENO with its
+ * nonlinear weights and the derivatives of the eigenvectors with respect to the cell
+ * average, the weak-derivative gradient reconstruction, the PP-LLF fluxes (the
+ * Lax-Friedrichs coefficient is differentiated through the state that attains it),
+ * the ghost cells, and the modified moments that re-enter every stage.  The time step
+ * is frozen (a given dt), as a checkpointed rollout records it.  The positivity limiter
+ * is differentiated only where it is inactive (theta = 1); a step in which it acts is
+ * rejected with HWENO_ERR_ARG.  The paper has no adjoint; the derivatives are those of
+ * its discrete scheme. */
+
+/* Allocate the adjoint buffers (about 3.8 KB per padded cell); FP64 handles only. */
+int hweno_adjoint_init(hweno_handle* h);
+
+/* xbar = (dR/dx)^T rbar + (dM/dx)^T mbar and *mubar = d<rbar, R>/dmu + d<mbar, M>/dmu
+ * at the state x, for the residual R [3][4][ny][nx] and the modified moments M
+ * [2][4][ny][nx] of hweno_residual; rbar or mbar may be NULL (zero).  Replaces the
+ * handle's state with x. */
+int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar, const double* mbar, double* xbar,
+                           double* mubar, int on_device);
+
+/* lam = (d q^{n+1} / d q^n)^T lam_next for the step q^n -> q^{n+1} taken with dt, and
+ * *mubar = (d q^{n+1} / d mu)^T lam_next with mu = 1/Re (the viscosity).  q: the state
+ * q^n, lam_next and lam: adjoint states, all [3][4][ny][nx]; on_device as elsewhere.
+ * The step's stage states are recomputed from q^n.  Replaces the handle's state with
+ * q^n.  Errors: HWENO_ERR_STATE before hweno_adjoint_init, HWENO_ERR_ARG if the limiter
+ * acts, HWENO_ERR_INADMISSIBLE if a stage of the forward step is inadmissible. */
+int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double* lam_next, double* lam,
+                       double* mubar, int on_device);
+
 /* ---- Batched ensembles ---------------------------------------------------------
  * Many independent problems (own grid, physics, boundaries; one common precision)
  * advanced together.  Each kernel of the spatial operator runs as one launch for all

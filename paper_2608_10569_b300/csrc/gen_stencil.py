@@ -145,6 +145,26 @@ def emit():
         out.append("template <class T> __device__ __forceinline__ T %s(const T* c) {\n" % name)
         terms = ["%s * c[%d]" % (_lit(v), k) for k, v in enumerate(m) if abs(v) > 1e-15]
         out.append("  return %s;\n}\n" % " + ".join(terms))
+    # transposes for the discrete adjoint
+    out.append("\n// adjoint of hw_p0_coeffs: dbar[n] += sum_k M[k][n] cbar[k]\n")
+    out.append("template <class T> __device__ __forceinline__ void hw_p0_coeffs_T(const T* cbar, T* dbar) {\n")
+    for n in range(17):
+        terms = [(M[k, n], k) for k in range(15) if M[k, n] != 0.0]
+        if terms:
+            out.append("  dbar[%d] += %s;\n" % (n, " + ".join("%s * cbar[%d]" % (_lit(v), k) for v, k in terms)))
+    out.append("}\n\n// gradient of the smoothness indicator: g = 2 B c\n")
+    out.append("template <class T> __device__ __forceinline__ void hw_beta_quartic_grad(const T* c, T* g) {\n")
+    out.append("  g[0] = T(0);\n")
+    for i in range(1, 15):
+        terms = ["%s * c[%d]" % (_lit(2.0 * B[i, j]), j) for j in range(1, 15) if B[i, j] != 0.0]
+        out.append("  g[%d] = %s;\n" % (i, " + ".join(terms) if terms else "T(0)"))
+    out.append("}\n")
+    for name, m in (("hw_moment_xi_T", mx), ("hw_moment_eta_T", my)):
+        out.append("template <class T> __device__ __forceinline__ void %s(T mbar, T* cbar) {\n" % name)
+        for k, v in enumerate(m):
+            if abs(v) > 1e-15:
+                out.append("  cbar[%d] += %s * mbar;\n" % (k, _lit(v)))
+        out.append("}\n")
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "hweno_stencil.h")
     with open(path, "w") as f:
         f.write("".join(out))

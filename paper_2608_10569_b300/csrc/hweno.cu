@@ -16,6 +16,7 @@
 #include "hweno_ops.cuh"
 #include "hweno_mixed.cuh"
 #include "hweno_batch.cuh"
+#include "hweno_adjoint.cuh"
 
 namespace hw {
 
@@ -186,6 +187,10 @@ struct hweno_handle {
   double pp_total = 0.0, cell_stages = 0.0;
   long long steps = 0, rejected = 0, launches = 0;
   double alpha = 0.0, beta = 0.0, dt_last = 0.0;
+  // adjoint buffers (hweno_adjoint_init)
+  double* apool = nullptr;
+  Adj adj{};
+  double *AST1 = nullptr, *ALAM = nullptr, *ABB = nullptr, *ATMP = nullptr;
   // profiling
   bool prof = false;
   std::vector<EventPair> ev;
@@ -433,6 +438,7 @@ void hweno_destroy(hweno_handle* h) {
   cudaStreamSynchronize(h->st);
   for (auto& ep : h->ev) { cudaEventDestroy(ep.a); cudaEventDestroy(ep.b); }
   if (h->pool) cudaFree(h->pool);
+  if (h->apool) cudaFree(h->apool);
   if (h->d_diag) cudaFree(h->d_diag);
   if (h->h_diag) cudaFreeHost(h->h_diag);
   if (h->h_red) cudaFreeHost(h->h_red);
@@ -743,6 +749,147 @@ int hweno_measure_peak(hweno_handle* h, int which, double* tflops) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   *tflops = best;
+  return HWENO_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Discrete adjoint of one SSP-RK3 step (FP64 path)
+
+// (dR/dx)^T R + (dM/dx)^T M at the state x whose forward intermediates are in h->w
+static int adjoint_operator(hweno_handle* h, const double* x) {
+  const Grid& g = h->g;
+  Adj& a = h->adj;
+  const size_t P = (size_t)g.ps * sizeof(double);
+  CK(cudaMemsetAsync(a.face, 0, 48 * P, h->st), "adjoint clear");
+  CK(cudaMemsetAsync(a.vol, 0, 36 * P, h->st), "adjoint clear");
+  CK(cudaMemsetAsync(a.gr, 0, 126 * P, h->st), "adjoint clear");
+  const dim3 blk(BX, BY);
+  ka_assemble<<<grid2(g.nx, g.ny), blk, 0, h->st>>>(g, h->w, a);
+  ka_flux<<<grid2(g.nx + 1, g.ny + 1, 2), blk, 0, h->st>>>(g, h->w, a);
+  ka_grad<<<grid2(g.nx + 2, g.ny + 2), blk, 0, h->st>>>(g, h->w, a);
+  ka_gather_rm<<<grid2(g.nx + 4, g.ny + 4), blk, 0, h->st>>>(g, a);
+  ka_face_moments<<<grid2(g.nx + 5, g.ny + 5, 2), blk, 0, h->st>>>(g, a);
+  ka_cons<<<grid2(g.nx + 6, g.ny + 6), blk, 0, h->st>>>(g, x, h->w, a);
+  ka_gather_q<<<grid2(g.nx + 8, g.ny + 8), blk, 0, h->st>>>(g, a);
+  ka_ghost_y<<<(8 * (g.nx + 2 * NG) + 127) / 128, 128, 0, h->st>>>(g, a);
+  ka_ghost_x<<<(8 * g.ny + 127) / 128, 128, 0, h->st>>>(g, a);
+  h->launches += 9;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint launch");
+  return HWENO_OK;
+}
+
+extern "C" {
+
+int hweno_adjoint_init(hweno_handle* h) {
+  if (!h) return HWENO_ERR_ARG;
+  if (h->cfg.precision != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_FP64");
+  if (h->apool) return HWENO_OK;
+  const Grid& g = h->g;
+  // R 12, M 8, face 48, vol 36, gr 126, rm 18, cg 102, cc 68, q 12, stage-1 state 12,
+  // lambda 12, base adjoint 12, temporary 12
+  const long long nplanes = 12 + 8 + 48 + 36 + 126 + 18 + 102 + 68 + 12 + 12 * 4;
+  const long long total = nplanes * g.ps + 8;
+  CK(cudaMalloc(&h->apool, (size_t)total * sizeof(double)), "adjoint allocation");
+  CK(cudaMemsetAsync(h->apool, 0, (size_t)total * sizeof(double), h->st), "adjoint clear");
+  double* p = h->apool;
+  auto take = [&](long long n) { double* r = p; p += n * g.ps; return r; };
+  Adj& a = h->adj;
+  a.R = take(12); a.M = take(8); a.face = take(48); a.vol = take(36); a.gr = take(126); a.rm = take(18);
+  a.cg = take(102); a.cc = take(68); a.q = take(12);
+  h->AST1 = take(12); h->ALAM = take(12); h->ABB = take(12); h->ATMP = take(12);
+  a.mu = p;
+  a.flags = reinterpret_cast<unsigned int*>(p + 1);
+  CK(cudaStreamSynchronize(h->st), "stream synchronize");
+  return HWENO_OK;
+}
+
+int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar, const double* mbar, double* xbar,
+                           double* mubar, int on_device) {
+  if (!h || !x || !xbar) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_residual: bad argument");
+  if (!h->apool) return fail(h, HWENO_ERR_STATE, "hweno_adjoint_residual before hweno_adjoint_init");
+  const Grid& g = h->g;
+  Adj& a = h->adj;
+  int rc;
+  if ((rc = copy_planes_in(h, x, 12, h->Q, on_device))) return rc;
+  h->have_state = true;
+  const size_t P = (size_t)g.ps * sizeof(double);
+  CK(cudaMemsetAsync(a.R, 0, 12 * P, h->st), "adjoint clear");
+  CK(cudaMemsetAsync(a.M, 0, 8 * P, h->st), "adjoint clear");
+  if (rbar && (rc = copy_planes_in(h, rbar, 12, a.R, on_device))) return rc;
+  if (mbar && (rc = copy_planes_in(h, mbar, 8, a.M, on_device))) return rc;
+  CK(cudaMemsetAsync(a.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
+  if ((rc = reset_diag(h))) return rc;
+  if ((rc = residual_eval(h, h->Q, h->RHS, h->MOM))) return rc;
+  h->have_residual = true;
+  if ((rc = adjoint_operator(h, h->Q))) return rc;
+  if ((rc = copy_planes_out(h, a.q, 12, xbar, on_device))) return rc;
+  double hm[2];
+  CK(cudaMemcpyAsync(h->h_red, a.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
+  CK(cudaStreamSynchronize(h->st), "stream synchronize");
+  memcpy(hm, h->h_red, sizeof(hm));
+  unsigned int fl;
+  memcpy(&fl, &hm[1], sizeof(fl));
+  if (fl & FLAG_ADJ_LIMITER) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_residual: limiter active");
+  if (mubar) *mubar = hm[0];
+  return HWENO_OK;
+}
+
+int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double* lam_next, double* lam,
+                       double* mubar, int on_device) {
+  if (!h || !q || !lam_next || !lam || !(dt > 0.0)) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_step: bad argument");
+  if (!h->apool) return fail(h, HWENO_ERR_STATE, "hweno_adjoint_step before hweno_adjoint_init");
+  const Grid& g = h->g;
+  Adj& a = h->adj;
+  int rc;
+  if ((rc = copy_planes_in(h, q, 12, h->Q, on_device))) return rc;
+  if ((rc = copy_planes_in(h, lam_next, 12, h->ALAM, on_device))) return rc;
+  h->have_state = true;
+  h->have_residual = false;
+  // forward stage states q1 (kept in AST1) and q2 (in QS), dt forced
+  if ((rc = reset_diag(h))) return rc;
+  if ((rc = residual_eval(h, h->Q, h->RHS0, h->MOM0))) return rc;
+  k_dt<<<1, 1, 0, h->st>>>(h->d_diag, h->cfg.cfl, h_min(h), 1.0, dt, INFINITY);
+  if ((rc = launch_rk(h, 1, h->Q, h->MOM0, h->RHS0, h->QS))) return rc;
+  CK(cudaMemcpyAsync(h->AST1, h->QS, 12 * (size_t)g.ps * sizeof(double), cudaMemcpyDeviceToDevice, h->st), "stage copy");
+  if ((rc = residual_eval(h, h->QS, h->RHS, h->MOM))) return rc;
+  if ((rc = launch_rk(h, 2, h->QS, h->MOM, h->RHS, h->QS))) return rc;
+  if ((rc = read_diag(h))) return rc;
+  if (h->h_diag->pp_count) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_step: the positivity limiter is active in this step (its adjoint is not implemented)");
+  if (h->h_diag->flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE)) return fail(h, HWENO_ERR_INADMISSIBLE, "hweno_adjoint_step: the forward step is inadmissible at this dt");
+  CK(cudaMemsetAsync(a.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
+  const dim3 gi = grid2(g.nx, g.ny), blk(BX, BY);
+  // stage 3: q3 = B/3 + 2/3 G(q2):  Bbar = lam/3, G's seed 2/3 lam
+  ka_axpby<<<gi, blk, 0, h->st>>>(g, h->ABB, 0.0, h->ALAM, 1.0 / 3.0);
+  if ((rc = residual_eval(h, h->QS, h->RHS, h->MOM))) return rc;
+  ka_seed<<<gi, blk, 0, h->st>>>(g, h->ALAM, dt * (2.0 / 3.0), 2.0 / 3.0, nullptr, 0.0, a);
+  if ((rc = adjoint_operator(h, h->QS))) return rc;
+  ka_finish<<<gi, blk, 0, h->st>>>(g, a, h->ALAM, 2.0 / 3.0, nullptr, 0.0, h->ATMP);
+  std::swap(h->ALAM, h->ATMP);  // lam = q2bar
+  // stage 2: q2 = 3/4 B + 1/4 G(q1)
+  ka_axpby<<<gi, blk, 0, h->st>>>(g, h->ABB, 1.0, h->ALAM, 0.75);
+  if ((rc = residual_eval(h, h->AST1, h->RHS, h->MOM))) return rc;
+  ka_seed<<<gi, blk, 0, h->st>>>(g, h->ALAM, dt * 0.25, 0.25, nullptr, 0.0, a);
+  if ((rc = adjoint_operator(h, h->AST1))) return rc;
+  ka_finish<<<gi, blk, 0, h->st>>>(g, a, h->ALAM, 0.25, nullptr, 0.0, h->ATMP);
+  std::swap(h->ALAM, h->ATMP);  // lam = q1bar
+  // stage 1: q1 = G(q), B = [q_avg; M(q)]
+  if ((rc = residual_eval(h, h->Q, h->RHS, h->MOM))) return rc;
+  ka_seed<<<gi, blk, 0, h->st>>>(g, h->ALAM, dt, 1.0, h->ABB, 1.0, a);
+  if ((rc = adjoint_operator(h, h->Q))) return rc;
+  ka_finish<<<gi, blk, 0, h->st>>>(g, a, h->ALAM, 1.0, h->ABB, 1.0, h->ATMP);
+  h->launches += 9;
+  if ((rc = copy_planes_out(h, h->ATMP, 12, lam, on_device))) return rc;
+  double hm[2];
+  CK(cudaMemcpyAsync(h->h_red, a.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
+  CK(cudaStreamSynchronize(h->st), "stream synchronize");
+  memcpy(hm, h->h_red, sizeof(hm));
+  unsigned int fl;
+  memcpy(&fl, &hm[1], sizeof(fl));
+  if (fl & FLAG_ADJ_LIMITER) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_step: limiter active in a stage");
+  if (mubar) *mubar = hm[0];
   return HWENO_OK;
 }
 

@@ -80,6 +80,11 @@ SIGNATURES = [
     ("hweno_measure_peak", ctypes.c_int, [_H, ctypes.c_int, _D]),
     ("hweno_residual_noalloc", ctypes.c_int, [ctypes.POINTER(hweno_config), ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("hweno_adjoint_init", ctypes.c_int, [_H]),
+    ("hweno_adjoint_residual", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, _D, ctypes.c_int]),
+    ("hweno_adjoint_step", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                          ctypes.c_void_p, _D, ctypes.c_int]),
     ("hweno_batch_init", ctypes.c_int, [ctypes.POINTER(hweno_config), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_void_p)]),
     ("hweno_batch_destroy", None, [ctypes.c_void_p]),
@@ -252,6 +257,35 @@ class Solver:
     def launch_count(self):
         return self.lib.hweno_launch_count(self.h)
 
+    def adjoint_init(self):
+        _check(self.h, self.lib.hweno_adjoint_init(self.h))
+
+    def adjoint_residual(self, x, rbar=None, mbar=None, xbar=None):
+        """(xbar, mubar): VJP of (residual, modified moments) at the state x."""
+        if xbar is None:
+            xbar = np.zeros_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+        px, dx = _ptr_of(x)
+        po, _ = _ptr_of(xbar)
+        pr = _ptr_of(rbar)[0] if rbar is not None else None
+        pm = _ptr_of(mbar)[0] if mbar is not None else None
+        mub = ctypes.c_double(0.0)
+        _check(self.h, self.lib.hweno_adjoint_residual(self.h, px, pr, pm, po, ctypes.byref(mub), dx))
+        return xbar, mub.value
+
+    def adjoint_step(self, q, dt, lam_next, lam=None):
+        """(lam, mubar): the VJP of the SSP-RK3 step q -> q' taken with dt (mu = 1/Re)."""
+        import torch
+        if lam is None:
+            lam = torch.empty_like(lam_next)
+        pq, dq = _ptr_of(q)
+        pl, dl = _ptr_of(lam_next)
+        po, do = _ptr_of(lam)
+        if not (dq == dl == do):
+            raise ValueError("q, lam_next and lam must all be host or all be device buffers")
+        mub = ctypes.c_double(0.0)
+        _check(self.h, self.lib.hweno_adjoint_step(self.h, pq, float(dt), pl, po, ctypes.byref(mub), dq))
+        return lam, mub.value
+
     def measure_peak(self, which):
         """FP64 (which=0) or FP32 (which=1) FMA throughput in TFLOP/s."""
         tf = ctypes.c_double(0.0)
@@ -325,3 +359,71 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _rollout_autograd():
+    import torch
+
+    class Rollout(torch.autograd.Function):
+        """q_T = Phi^n(q_0) for n SSP-RK3 steps of the FP64 solver, differentiable with
+        respect to the initial state q_0 and the viscosity mu = 1/Re.
+
+        Forward: the steps under the time-step rule of Sec. 5; the step sizes are
+        recorded and the state is checkpointed every `ckpt` steps.  Backward: for each
+        segment, last to first, the states inside it are recomputed from its checkpoint
+        with the recorded step sizes, then the adjoint runs backwards through the
+        segment's steps (hweno_adjoint_step); the step sizes are held fixed."""
+
+        @staticmethod
+        def forward(ctx, q0, mu, case_params, nsteps, ckpt):
+            p = dict(case_params)
+            p["Re"] = 1.0 / float(mu)
+            s = Solver(p, precision="fp64")
+            s.set_state(q0.detach().contiguous())
+            dts, ckpts = [], {0: q0.detach().clone()}
+            for n in range(nsteps):
+                dt, _ = s.step()
+                dts.append(dt)
+                if (n + 1) % ckpt == 0 and n + 1 < nsteps:
+                    ckpts[n + 1] = s.get_state().clone()
+            qT = s.get_state().clone()
+            ctx.solver = s
+            ctx.dts = dts
+            ctx.ckpts = ckpts
+            ctx.ckpt = ckpt
+            return qT
+
+        @staticmethod
+        def backward(ctx, qbar):
+            s = ctx.solver
+            s.adjoint_init()
+            dts, ckpts, K = ctx.dts, ctx.ckpts, ctx.ckpt
+            n = len(dts)
+            lam = qbar.detach().contiguous().clone()
+            mubar = 0.0
+            starts = sorted(ckpts)
+            for a in reversed(starts):
+                b = min(a + K, n)
+                states = [ckpts[a]]
+                s.set_state(ckpts[a])
+                for k in range(a, b - 1):
+                    s.step(dts[k])
+                    states.append(s.get_state().clone())
+                for k in range(b - 1, a - 1, -1):
+                    lam, mb = s.adjoint_step(states[k - a], dts[k], lam)
+                    mubar += mb
+            s.close()
+            return lam, qbar.new_tensor(mubar), None, None, None
+
+    return Rollout
+
+
+def rollout(q0, mu, case_params, nsteps, ckpt=20):
+    """Differentiable n-step FP64 rollout; see the Rollout autograd function."""
+    import torch
+    global _ROLLOUT
+    if "_ROLLOUT" not in globals():
+        _ROLLOUT = _rollout_autograd()
+    if not torch.is_tensor(mu):
+        mu = torch.tensor(float(mu), dtype=torch.float64, device=q0.device)
+    return _ROLLOUT.apply(q0, mu, case_params, int(nsteps), int(ckpt))

@@ -1,0 +1,163 @@
+"""Discrete adjoint of the FP64 SSP-RK3 step: vector-Jacobian products against central
+finite differences of the forward step (the GPU's and the oracle's), the derivative
+with respect to mu = 1/Re, and a checkpointed multi-step rollout through
+torch.autograd.
+
+The nonlinear weights make the step strongly curved (epsilon_WENO = 1e-8 sets the scale
+of their second derivatives), so plain central differences carry an O(h^2) error with a
+large constant.  The checks use Richardson-extrapolated central differences,
+(4 D(h/2) - D(h)) / 3, which cancel that term."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2608_10569_b300 import hweno, inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def richardson(f, h):
+    """(4 D(h/2) - D(h)) / 3 with D(h) = (f(h) - f(-h)) / (2h)"""
+    d1 = (f(h) - f(-h)) / (2 * h)
+    d2 = (f(h / 2) - f(-h / 2)) / h
+    return (4 * d2 - d1) / 3
+
+
+def _step(case, q, dt, Re=None):
+    p = case.params()
+    if Re is not None:
+        p["Re"] = Re
+    s = hweno.Solver(p)
+    s.set_state(q.copy())
+    s.step(dt)
+    out = s.get_state(np.zeros_like(q))
+    s.close()
+    return out
+
+
+CASES = {
+    "periodic_smooth": lambda: I.random_smooth(20, 18, seed=31),
+    "walls_smooth": lambda: I.random_smooth(19, 17, seed=32, bc=("noslip", "slip", "symmetry", "noslip")),
+    "taylor_green": lambda: I.taylor_green(24, 0.5, 300.0, 1 / (1.4 * 0.09), rho_pert=1e-3),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_step_vjp_matches_central_differences(name):
+    case, q = CASES[name]()
+    rng = np.random.default_rng(5)
+    dt = 2e-3
+    lam_next = rng.normal(size=q.shape)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    s = hweno.Solver(case.params())
+    s.adjoint_init()
+    lam, _ = s.adjoint_step(q.copy(), dt, lam_next, np.zeros_like(q))
+    s.close()
+    fd = richardson(lambda e: (_step(case, q + e * v, dt) * lam_next).sum(), 2e-6)
+    ad = (lam * v).sum()
+    assert abs(ad - fd) <= 1e-6 * abs(fd), (ad, fd)
+
+
+def test_residual_vjp_on_a_discontinuous_state():
+    """On data with jumps the weights switch between candidates and the Lax-Friedrichs
+    coefficient changes hands between states, so central differences converge to the
+    adjoint only as the step shrinks; the adjoint is the limit they approach."""
+    case, q = I.random_rough(22, 20, seed=33)
+    rng = np.random.default_rng(1)
+    rb = rng.normal(size=q.shape)
+    s = hweno.Solver(case.params())
+    s.adjoint_init()
+    xb, _ = s.adjoint_residual(q.copy(), rb, None)
+    v = np.zeros_like(q)
+    v[0] = rng.normal(size=q[0].shape) * np.abs(q[0]).max()
+    ad = (xb * v).sum()
+
+    def R(e):
+        r = np.zeros_like(q)
+        s.set_state(q + e * v)
+        s.residual(r, np.zeros((8,) + q.shape[1:]))
+        return (r * rb).sum()
+
+    errs = [abs((R(h) - R(-h)) / (2 * h) - ad) / abs(ad) for h in (1e-6, 1e-7, 1e-8)]
+    s.close()
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 2e-3, errs
+
+
+def test_viscosity_derivative_matches_central_differences():
+    case, q = I.random_smooth(20, 18, seed=34, Re=200.0)
+    rng = np.random.default_rng(6)
+    dt = 2e-3
+    lam_next = rng.normal(size=q.shape)
+    s = hweno.Solver(case.params())
+    s.adjoint_init()
+    _, mub = s.adjoint_step(q.copy(), dt, lam_next, np.zeros_like(q))
+    s.close()
+    mu = 1.0 / case.Re
+    fd = richardson(lambda e: (_step(case, q, dt, 1.0 / (mu + e)) * lam_next).sum(), 2e-8)
+    assert abs(mub - fd) <= 1e-6 * abs(fd), (mub, fd)
+
+
+def test_step_vjp_against_the_oracle_step():
+    """dot-product test with the independent CPU implementation: <lam, J v> by central
+    differences of the oracle's step equals <J^T lam, v> from the GPU adjoint"""
+    case, q = I.random_smooth(16, 16, seed=35, bc=("noslip", "noslip", "noslip", "symmetry"))
+    rng = np.random.default_rng(7)
+    dt = 1e-3
+    lam_next = rng.normal(size=q.shape)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    s = hweno.Solver(case.params())
+    s.adjoint_init()
+    lam, _ = s.adjoint_step(q.copy(), dt, lam_next, np.zeros_like(q))
+    s.close()
+    cfg = O.make_cfg(**case.params())
+    fd = richardson(lambda e: (O.step(cfg, q + e * v, dt_fixed=dt)[0] * lam_next).sum(), 2e-6)
+    assert abs((lam * v).sum() - fd) <= 1e-6 * abs(fd)
+
+
+def test_checkpointed_rollout_gradient():
+    """J = 1/2 sum (rho(T) - rho*)^2 dx dy over 12 steps with checkpoints every 5 steps:
+    dJ/dq0 and dJ/dmu through torch.autograd against central differences on random
+    directions (the step sizes recorded in the forward are reused)."""
+    case, q = I.taylor_green(24, 0.5, 400.0, 1 / (1.4 * 0.09), rho_pert=1e-3, seed=8)
+    params = case.params()
+    q0 = torch.from_numpy(q).cuda().requires_grad_(True)
+    mu = torch.tensor(1.0 / case.Re, dtype=torch.float64, device="cuda", requires_grad=True)
+    rng = np.random.default_rng(9)
+    target = torch.from_numpy(q[0] + 1e-2 * rng.normal(size=q[0].shape)).cuda()
+    area = case.dx * case.dy
+
+    def J(qT):
+        return 0.5 * ((qT[0] - target) ** 2).sum() * area
+
+    qT = hweno.rollout(q0, mu, params, nsteps=12, ckpt=5)
+    loss = J(qT)
+    loss.backward()
+    g0 = q0.grad.cpu().numpy()
+    gmu = float(mu.grad)
+    # replay with the same step sizes for the differences
+    s = hweno.Solver(params)
+    s.set_state(q.copy())
+    dts = [s.step()[0] for _ in range(12)]
+    s.close()
+
+    def run(qi, Re):
+        p = dict(params)
+        p["Re"] = Re
+        s = hweno.Solver(p)
+        s.set_state(qi.copy())
+        for dt in dts:
+            s.step(dt)
+        out = s.get_state(np.zeros_like(qi))
+        s.close()
+        return float(J(torch.from_numpy(out).cuda()))
+
+    scale = np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    for k in range(3):
+        v = rng.normal(size=q.shape) * scale
+        fd = richardson(lambda e: run(q + e * v, case.Re), 1e-7)
+        assert abs((g0 * v).sum() - fd) <= 1e-6 * abs(fd), ((g0 * v).sum(), fd)
+    mu0 = 1.0 / case.Re
+    fdmu = richardson(lambda e: run(q, 1.0 / (mu0 + e)), 2e-6)
+    assert abs(gmu - fdmu) <= 1e-6 * abs(fdmu), (gmu, fdmu)
