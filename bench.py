@@ -57,11 +57,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hweno", choices=["hweno", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fd-directions", type=int, default=4)
+    ap.add_argument("--adj-n", type=int, default=512)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--workload", default="shock_tube",
-                    choices=["shock_tube", "ensemble", "smooth_periodic", "colliding_streams", "taylor_green"],
+                    choices=["shock_tube", "ensemble", "smooth_periodic", "colliding_streams", "taylor_green",
+                             "adjoint"],
                     help="shock_tube is the headline line; the others print their own line")
     return ap.parse_args()
 
@@ -229,6 +232,79 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Gradient of J = 1/2 sum (rho(T) - rho*)^2 dx dy after --steps SSP-RK3 steps of the
+    Taylor-Green flow (512^2, Re 1600, Mach 0.3), checkpoints every 20 steps, with
+    respect to the initial state and mu = 1/Re; time of the backward pass over the
+    forward pass, and central-difference checks on seeded directions (the step sizes of
+    the forward run are reused)."""
+    import torch
+    from paper_2608_10569_b300 import hweno, inputs as I
+    steps = args.steps
+    case, q = I.adjoint_taylor_green(args.adj_n)
+    params = case.params()
+    target = torch.from_numpy(I.adjoint_target(case)).cuda()
+    area = case.dx * case.dy
+
+    def J(qT):
+        return 0.5 * ((qT[0] - target) ** 2).sum() * area
+
+    # warm-up: library load, allocation paths and caches on a short rollout
+    qw = torch.from_numpy(q).cuda().requires_grad_(True)
+    muw = torch.tensor(1.0 / case.Re, dtype=torch.float64, device="cuda", requires_grad=True)
+    J(hweno.rollout(qw, muw, params, nsteps=max(args.warmup, 2), ckpt=20)).backward()
+    q0 = torch.from_numpy(q).cuda().requires_grad_(True)
+    mu = torch.tensor(1.0 / case.Re, dtype=torch.float64, device="cuda", requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qT = hweno.rollout(q0, mu, params, nsteps=steps, ckpt=20)
+    loss = J(qT)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g0 = q0.grad.cpu().numpy()
+    gmu = float(mu.grad)
+    s = hweno.Solver(params)
+    s.set_state(q.copy())
+    dts = [s.step()[0] for _ in range(steps)]
+    s.close()
+
+    def run(qi, Re):
+        p = dict(params)
+        p["Re"] = Re
+        sv = hweno.Solver(p)
+        sv.set_state(torch.from_numpy(qi).cuda())
+        for dt in dts:
+            sv.step(dt)
+        out = sv.get_state()
+        sv.close()
+        return float(J(out))
+
+    def rich(f, h):
+        d1 = (f(h) - f(-h)) / (2 * h)
+        d2 = (f(h / 2) - f(-h / 2)) / h
+        return (4 * d2 - d1) / 3
+
+    rng = np.random.default_rng(16)
+    scale = np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    errs = []
+    for _ in range(args.fd_directions):
+        v = rng.normal(size=q.shape) * scale
+        fd = rich(lambda e: run(q + e * v, case.Re), 1e-7)
+        errs.append(abs((g0 * v).sum() - fd) / abs(fd))
+    mu0 = 1.0 / case.Re
+    fdmu = rich(lambda e: run(q, 1.0 / (mu0 + e)), 0.02 * mu0)
+    line = {"metric": "adjoint/forward time ratio", "workload": "adjoint Taylor-Green %d^2, Re 1600, Mach 0.3, "
+            "%d SSP-RK3 steps, checkpoints every 20" % (args.adj_n, steps),
+            "forward_s": t1 - t0, "backward_s": t2 - t1, "value": (t2 - t1) / (t1 - t0), "unit": "ratio",
+            "higher_is_better": False, "dtype": "f64", "J": float(loss),
+            "fd_directions": args.fd_directions, "fd_max_rel_err": max(errs) if errs else None,
+            "dJ_dmu": gmu, "mu_fd_rel_err": abs(gmu - fdmu) / abs(fdmu)}
+    print(json.dumps(line), flush=True)
+
+
 def run_single(args):
     """configs 1, 3 and 5 on one solver: FP64 and mixed step rates (config 3, whose
     limited states make the step rule restart ~20 times per step, reports residual
@@ -294,6 +370,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     if args.workload != "shock_tube":
         return run_single(args)
     import torch

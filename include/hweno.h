@@ -202,6 +202,23 @@ int hweno_adjoint_init(hweno_handle* h);
 int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar, const double* mbar, double* xbar,
                            double* mubar, int on_device);
 
+/* Storage for hweno_adjoint_segment: the three stage states of up to max_steps steps
+ * and, with keep_intermediates, the forward intermediates of every stage (about 2 KB
+ * per padded cell and stage), so that the reverse recomputes nothing.  When those do
+ * not fit in 80 % of the free device memory only the states are kept and every stage is
+ * re-evaluated during the reverse.  Returns 1 if intermediates are kept, 0 if not. */
+int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_intermediates);
+
+/* The adjoint through a checkpoint segment: recompute the nsteps steps from q_start with
+ * the step sizes dts[0..nsteps-1] (host array), keeping their stage states, then
+ * lam_start = (d q^{end} / d q_start)^T lam_end and *mubar = the mu = 1/Re derivative of
+ * <lam_end, q^{end}>.  Buffers [3][4][ny][nx] as elsewhere.  Errors: HWENO_ERR_STATE
+ * without enough reserved storage, HWENO_ERR_ARG if the limiter acts,
+ * HWENO_ERR_INADMISSIBLE if a stage is inadmissible at the given steps.  Leaves the
+ * handle without a state (call hweno_set_state before stepping again). */
+int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int nsteps, const double* dts,
+                          const double* lam_end, double* lam_start, double* mubar, int on_device);
+
 /* lam = (d q^{n+1} / d q^n)^T lam_next for the step q^n -> q^{n+1} taken with dt, and
  * *mubar = (d q^{n+1} / d mu)^T lam_next with mu = 1/Re (the viscosity).  q: the state
  * q^n, lam_next and lam: adjoint states, all [3][4][ny][nx]; on_device as elsewhere.

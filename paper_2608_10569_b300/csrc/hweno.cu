@@ -191,6 +191,11 @@ struct hweno_handle {
   double* apool = nullptr;
   Adj adj{};
   double *AST1 = nullptr, *ALAM = nullptr, *ABB = nullptr, *ATMP = nullptr;
+  // segment storage (hweno_adjoint_reserve): 3 stage states per step, and optionally the
+  // forward intermediates of every stage
+  double* spool = nullptr;
+  int seg_max = 0;
+  int seg_keep = 0;
   // profiling
   bool prof = false;
   std::vector<EventPair> ev;
@@ -439,6 +444,7 @@ void hweno_destroy(hweno_handle* h) {
   for (auto& ep : h->ev) { cudaEventDestroy(ep.a); cudaEventDestroy(ep.b); }
   if (h->pool) cudaFree(h->pool);
   if (h->apool) cudaFree(h->apool);
+  if (h->spool) cudaFree(h->spool);
   if (h->d_diag) cudaFree(h->d_diag);
   if (h->h_diag) cudaFreeHost(h->h_diag);
   if (h->h_red) cudaFreeHost(h->h_red);
@@ -803,6 +809,127 @@ int hweno_adjoint_init(hweno_handle* h) {
   a.mu = p;
   a.flags = reinterpret_cast<unsigned int*>(p + 1);
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
+  return HWENO_OK;
+}
+
+// planes of the forward intermediates the reverse kernels read
+static const long long SEG_WORK_PLANES = 48 + 36 + 3 + 6 + 6 + 18 + 126 + 12 + 12 + 2;
+
+static Work seg_work(hweno_handle* h, int n, int stage) {
+  const long long ps = h->g.ps;
+  double* p = h->spool + (long long)h->seg_max * 36 * ps + ((long long)n * 3 + stage) * SEG_WORK_PLANES * ps;
+  Work w;
+  w.face = p; p += 48 * ps;
+  w.vol = p; p += 36 * ps;
+  w.wbar = p; p += 3 * ps;
+  w.wx = p; p += 6 * ps;
+  w.wy = p; p += 6 * ps;
+  w.rm = p; p += 18 * ps;
+  w.gr = p; p += 126 * ps;
+  w.fx = p; p += 12 * ps;
+  w.fy = p; p += 12 * ps;
+  w.theta = p;
+  return w;
+}
+
+static double* seg_state(hweno_handle* h, int n, int k) {  // k = 0: q^n, 1: q1, 2: q2
+  return h->spool + ((long long)n * 3 + k) * 12 * h->g.ps;
+}
+
+extern "C" int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_intermediates) {
+  if (!h || max_steps < 1) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_reserve: bad argument");
+  if (!h->apool) return fail(h, HWENO_ERR_STATE, "hweno_adjoint_reserve before hweno_adjoint_init");
+  if (h->spool && h->seg_max >= max_steps && (h->seg_keep || !keep_intermediates)) return HWENO_OK;
+  if (h->spool) {
+    CK(cudaStreamSynchronize(h->st), "stream synchronize");
+    cudaFree(h->spool);
+    h->spool = nullptr;
+  }
+  const long long ps = h->g.ps;
+  long long planes = (long long)max_steps * 36;
+  int keep = keep_intermediates ? 1 : 0;
+  if (keep) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const long long with = planes + (long long)max_steps * 3 * SEG_WORK_PLANES;
+    if ((double)with * ps * sizeof(double) > 0.8 * (double)fr) keep = 0;  // fall back to recomputation
+    else planes = with;
+  }
+  CK(cudaMalloc(&h->spool, (size_t)planes * ps * sizeof(double)), "adjoint segment allocation");
+  h->seg_max = max_steps;
+  h->seg_keep = keep;
+  return keep ? 1 : HWENO_OK;
+}
+
+extern "C" int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int nsteps, const double* dts,
+                                     const double* lam_end, double* lam_start, double* mubar, int on_device) {
+  if (!h || !q_start || !dts || !lam_end || !lam_start || nsteps < 1)
+    return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: bad argument");
+  if (!h->spool || nsteps > h->seg_max)
+    return fail(h, HWENO_ERR_STATE, "hweno_adjoint_segment: reserve storage for this many steps first");
+  const Grid& g = h->g;
+  Adj& a = h->adj;
+  const Work base = h->w;
+  const bool keep = h->seg_keep != 0;
+  int rc;
+  if ((rc = copy_planes_in(h, q_start, 12, seg_state(h, 0, 0), on_device))) return rc;
+  if ((rc = copy_planes_in(h, lam_end, 12, h->ALAM, on_device))) return rc;
+  if ((rc = reset_diag(h))) return rc;
+  // forward recomputation of the segment, keeping the stage states (and intermediates)
+  for (int n = 0; n < nsteps; n++) {
+    double* q0 = seg_state(h, n, 0);
+    double* q1 = seg_state(h, n, 1);
+    double* q2 = seg_state(h, n, 2);
+    double* out = n + 1 < nsteps ? seg_state(h, n + 1, 0) : h->QS;
+    if (keep) h->w = seg_work(h, n, 0);
+    if ((rc = residual_eval(h, q0, h->RHS0, h->MOM0))) break;
+    k_dt<<<1, 1, 0, h->st>>>(h->d_diag, h->cfg.cfl, h_min(h), 1.0, dts[n], INFINITY);
+    if ((rc = launch_rk(h, 1, q0, h->MOM0, h->RHS0, q1))) break;
+    if (keep) h->w = seg_work(h, n, 1);
+    if ((rc = residual_eval(h, q1, h->RHS, h->MOM))) break;
+    if ((rc = launch_rk(h, 2, q1, h->MOM, h->RHS, q2))) break;
+    if (keep) h->w = seg_work(h, n, 2);
+    if ((rc = residual_eval(h, q2, h->RHS, h->MOM))) break;
+    if ((rc = launch_rk(h, 3, q2, h->MOM, h->RHS, out))) break;
+  }
+  h->w = base;
+  if (rc) return rc;
+  if ((rc = read_diag(h))) return rc;
+  if (h->h_diag->pp_count)
+    return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: the positivity limiter is active in this segment (its adjoint is not implemented)");
+  if (h->h_diag->flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE))
+    return fail(h, HWENO_ERR_INADMISSIBLE, "hweno_adjoint_segment: a forward stage is inadmissible at the given steps");
+  CK(cudaMemsetAsync(a.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
+  const dim3 gi = grid2(g.nx, g.ny), blk(BX, BY);
+  for (int n = nsteps - 1; n >= 0 && !rc; n--) {
+    const double dt = dts[n];
+    double* st[3] = {seg_state(h, n, 0), seg_state(h, n, 1), seg_state(h, n, 2)};
+    // stage 3 at q2, stage 2 at q1, stage 1 at q^n (see hweno_adjoint_step)
+    const double sr[3] = {dt, 0.25 * dt, (2.0 / 3.0) * dt}, sm[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int stage = 2; stage >= 0 && !rc; stage--) {
+      if (stage == 2) ka_axpby<<<gi, blk, 0, h->st>>>(g, h->ABB, 0.0, h->ALAM, 1.0 / 3.0);
+      if (stage == 1) ka_axpby<<<gi, blk, 0, h->st>>>(g, h->ABB, 1.0, h->ALAM, 0.75);
+      if (keep) h->w = seg_work(h, n, stage);
+      else if ((rc = residual_eval(h, st[stage], h->RHS, h->MOM))) break;
+      ka_seed<<<gi, blk, 0, h->st>>>(g, h->ALAM, sr[stage], sm[stage], stage == 0 ? h->ABB : nullptr, 1.0, a);
+      if ((rc = adjoint_operator(h, st[stage]))) break;
+      ka_finish<<<gi, blk, 0, h->st>>>(g, a, h->ALAM, sm[stage], stage == 0 ? h->ABB : nullptr, 1.0, h->ATMP);
+      h->launches += 3;
+      std::swap(h->ALAM, h->ATMP);
+    }
+  }
+  h->w = base;
+  if (rc) return rc;
+  if ((rc = copy_planes_out(h, h->ALAM, 12, lam_start, on_device))) return rc;
+  double hm[2];
+  CK(cudaMemcpyAsync(h->h_red, a.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
+  CK(cudaStreamSynchronize(h->st), "stream synchronize");
+  memcpy(hm, h->h_red, sizeof(hm));
+  unsigned int fl;
+  memcpy(&fl, &hm[1], sizeof(fl));
+  if (fl & FLAG_ADJ_LIMITER) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: limiter active in a stage");
+  if (mubar) *mubar = hm[0];
+  h->have_state = false;  // the handle's state buffers hold segment data now
   return HWENO_OK;
 }
 

@@ -83,6 +83,9 @@ SIGNATURES = [
     ("hweno_adjoint_init", ctypes.c_int, [_H]),
     ("hweno_adjoint_residual", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, _D, ctypes.c_int]),
+    ("hweno_adjoint_reserve", ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    ("hweno_adjoint_segment", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_void_p,
+                                             ctypes.c_void_p, _D, ctypes.c_int]),
     ("hweno_adjoint_step", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                                           ctypes.c_void_p, _D, ctypes.c_int]),
     ("hweno_batch_init", ctypes.c_int, [ctypes.POINTER(hweno_config), ctypes.c_int, ctypes.c_void_p,
@@ -272,6 +275,27 @@ class Solver:
         _check(self.h, self.lib.hweno_adjoint_residual(self.h, px, pr, pm, po, ctypes.byref(mub), dx))
         return xbar, mub.value
 
+    def adjoint_reserve(self, max_steps, keep_intermediates=True):
+        rc = self.lib.hweno_adjoint_reserve(self.h, int(max_steps), 1 if keep_intermediates else 0)
+        if rc < 0:
+            _check(self.h, rc)
+        return rc == 1
+
+    def adjoint_segment(self, q_start, dts, lam_end, lam_start=None):
+        """(lam_start, mubar) through the steps with sizes dts from q_start."""
+        import torch
+        if lam_start is None:
+            lam_start = torch.empty_like(lam_end)
+        pq, dq = _ptr_of(q_start)
+        pl, dl = _ptr_of(lam_end)
+        po, do = _ptr_of(lam_start)
+        if not (dq == dl == do):
+            raise ValueError("q_start, lam_end and lam_start must all be host or all be device buffers")
+        arr = (ctypes.c_double * len(dts))(*[float(x) for x in dts])
+        mub = ctypes.c_double(0.0)
+        _check(self.h, self.lib.hweno_adjoint_segment(self.h, pq, len(dts), arr, pl, po, ctypes.byref(mub), dq))
+        return lam_start, mub.value
+
     def adjoint_step(self, q, dt, lam_next, lam=None):
         """(lam, mubar): the VJP of the SSP-RK3 step q -> q' taken with dt (mu = 1/Re)."""
         import torch
@@ -399,19 +423,13 @@ def _rollout_autograd():
             s.adjoint_init()
             dts, ckpts, K = ctx.dts, ctx.ckpts, ctx.ckpt
             n = len(dts)
+            s.adjoint_reserve(min(K, n), keep_intermediates=True)
             lam = qbar.detach().contiguous().clone()
             mubar = 0.0
-            starts = sorted(ckpts)
-            for a in reversed(starts):
+            for a in reversed(sorted(ckpts)):
                 b = min(a + K, n)
-                states = [ckpts[a]]
-                s.set_state(ckpts[a])
-                for k in range(a, b - 1):
-                    s.step(dts[k])
-                    states.append(s.get_state().clone())
-                for k in range(b - 1, a - 1, -1):
-                    lam, mb = s.adjoint_step(states[k - a], dts[k], lam)
-                    mubar += mb
+                lam, mb = s.adjoint_segment(ckpts[a], dts[a:b], lam)
+                mubar += mb
             s.close()
             return lam, qbar.new_tensor(mubar), None, None, None
 

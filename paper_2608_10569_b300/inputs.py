@@ -216,6 +216,25 @@ def adjoint_taylor_green(n=512, M=0.3):
     return case, q
 
 
+def adjoint_target(case, seed=5, modes=8, amp=0.01):
+    """Seeded density target of the adjoint workload: 1 + amp times a sum of `modes`
+    Fourier modes with wavenumbers |k| <= 4, sampled at the cell centres."""
+    rng = _rng(seed)
+    L = case.x1 - case.x0
+    xc = case.x0 + (np.arange(case.nx) + 0.5) * case.dx
+    yc = case.y0 + (np.arange(case.ny) + 0.5) * case.dy
+    X, Y = np.meshgrid(xc, yc)
+    f = np.zeros_like(X)
+    for _ in range(modes):
+        while True:
+            kx, ky = rng.integers(-4, 5, size=2)
+            if 0 < kx * kx + ky * ky <= 16:
+                break
+        ph = rng.uniform(0, 2 * np.pi)
+        f += np.cos(2 * np.pi * (kx * X + ky * Y) / L + ph)
+    return 1.0 + amp * f / modes
+
+
 # ---------------------------------------------------------------------------
 # generic seeded states for parity tests
 

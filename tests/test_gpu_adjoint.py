@@ -161,3 +161,29 @@ def test_checkpointed_rollout_gradient():
     mu0 = 1.0 / case.Re
     fdmu = richardson(lambda e: run(q, 1.0 / (mu0 + e)), 2e-6)
     assert abs(gmu - fdmu) <= 1e-6 * abs(fdmu), (gmu, fdmu)
+
+
+@pytest.mark.parametrize("keep", [True, False])
+def test_segment_adjoint_equals_chained_steps(keep):
+    """hweno_adjoint_segment (one forward recomputation, stored stage states, with or
+    without stored intermediates) equals the chain of single-step adjoints."""
+    case, q = I.taylor_green(20, 0.4, 300.0, 1 / (1.4 * 0.09), rho_pert=1e-3, seed=10)
+    rng = np.random.default_rng(11)
+    lam_end = rng.normal(size=q.shape)
+    s = hweno.Solver(case.params())
+    s.set_state(q.copy())
+    states, dts = [q.copy()], []
+    for _ in range(4):
+        dts.append(s.step()[0])
+        states.append(s.get_state(np.zeros_like(q)))
+    s.adjoint_init()
+    lam, mub = lam_end.copy(), 0.0
+    for k in range(3, -1, -1):
+        lam, mb = s.adjoint_step(states[k].copy(), dts[k], lam, np.zeros_like(q))
+        mub += mb
+    kept = s.adjoint_reserve(4, keep_intermediates=keep)
+    assert kept == keep
+    lam2, mub2 = s.adjoint_segment(q.copy(), dts, lam_end.copy(), np.zeros_like(q))
+    s.close()
+    assert np.abs(lam2 - lam).max() <= 1e-12 * np.abs(lam).max()
+    assert abs(mub2 - mub) <= 1e-12 * abs(mub)
