@@ -209,13 +209,28 @@ int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar,
  * re-evaluated during the reverse.  Returns 1 if intermediates are kept, 0 if not. */
 int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_intermediates);
 
+/* Recording for the adjoint.  With on != 0 (after hweno_adjoint_reserve), each step
+ * hweno_step or hweno_advance accepts from now on is recorded into the next slot of the
+ * reserved storage: its stage states, its intermediates if they are kept, and its step
+ * size; more steps than reserved fail with HWENO_ERR_STATE.  on = 0 stops recording and
+ * keeps what was recorded.  The recording costs one state copy per step. */
+int hweno_adjoint_record(hweno_handle* h, int on);
+
+/* The adjoint through the recorded steps, last to first, with their step sizes held
+ * fixed: lam_start = (d q^{end} / d q^{first})^T lam_end, *mubar (may be NULL) = the
+ * mu = 1/Re derivative of <lam_end, q^{end}>.  Buffers [3][4][ny][nx], host or device per
+ * on_device.  Errors: HWENO_ERR_STATE with nothing recorded, HWENO_ERR_ARG if the
+ * positivity limiter acts in a recorded stage.  Ends recording; the handle's state is
+ * unchanged. */
+int hweno_adjoint_replay(hweno_handle* h, const double* lam_end, double* lam_start, double* mubar, int on_device);
+
 /* The adjoint through a checkpoint segment: recompute the nsteps steps from q_start with
- * the step sizes dts[0..nsteps-1] (host array), keeping their stage states, then
- * lam_start = (d q^{end} / d q_start)^T lam_end and *mubar = the mu = 1/Re derivative of
- * <lam_end, q^{end}>.  Buffers [3][4][ny][nx] as elsewhere.  Errors: HWENO_ERR_STATE
- * without enough reserved storage, HWENO_ERR_ARG if the limiter acts,
- * HWENO_ERR_INADMISSIBLE if a stage is inadmissible at the given steps.  Leaves the
- * handle without a state (call hweno_set_state before stepping again). */
+ * the step sizes dts[0..nsteps-1] (host array), keeping their stage states (and
+ * intermediates), then the reverse sweep of hweno_adjoint_replay over them.  Errors:
+ * HWENO_ERR_STATE without enough reserved storage, HWENO_ERR_ARG if the limiter acts,
+ * HWENO_ERR_INADMISSIBLE if a stage is inadmissible at the given steps.  Replaces any
+ * recording and leaves the handle without a state (call hweno_set_state before stepping
+ * again). */
 int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int nsteps, const double* dts,
                           const double* lam_end, double* lam_start, double* mubar, int on_device);
 

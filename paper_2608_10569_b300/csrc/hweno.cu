@@ -28,6 +28,12 @@ __global__ void __launch_bounds__(BX * BY) k_cons(Grid g, const double* __restri
                                                   double* __restrict__ mom, Diag* diag) {
   cons_body<T>(g, q, w, mom, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
+// the FP64 traces of a step recorded for the adjoint (Work::yrec set)
+__global__ void __launch_bounds__(BX * BY) k_cons_rec(Grid g, const double* __restrict__ q, Work w,
+                                                      double* __restrict__ mom, Diag* diag) {
+  cons_body<double, true>(g, q, w, mom, diag, blockIdx.x * blockDim.x + threadIdx.x,
+                          blockIdx.y * blockDim.y + threadIdx.y);
+}
 __global__ void k_face_moments(Grid g, Work w) {
   face_moments_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
 }
@@ -191,11 +197,15 @@ struct hweno_handle {
   double* apool = nullptr;
   Adj adj{};
   double *AST1 = nullptr, *ALAM = nullptr, *ABB = nullptr, *ATMP = nullptr;
+  double* AYREC = nullptr;  // reconstruction record of a stage re-evaluated for the reverse
   // segment storage (hweno_adjoint_reserve): 3 stage states per step, and optionally the
   // forward intermediates of every stage
   double* spool = nullptr;
   int seg_max = 0;
   int seg_keep = 0;
+  bool recording = false;        // do_step records each accepted step into the next slot
+  int rec_count = 0;             // recorded steps
+  std::vector<double> rec_dts;   // their step sizes
   // profiling
   bool prof = false;
   std::vector<EventPair> ev;
@@ -301,7 +311,10 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
   } else {
     {
       Prof p(h, K_CONS);
-      k_cons<double><<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
+      if (h->w.yrec)
+        k_cons_rec<<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
+      else
+        k_cons<double><<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
     }
     {
       Prof p(h, K_FACEMOM);
@@ -549,11 +562,55 @@ int hweno_residual(hweno_handle* h, double* rhs, double* vhat, int on_device) {
 }
 
 // one SSP-RK3 step from h->Q; on success the new state is in h->Q
+// planes of the forward intermediates the reverse kernels read
+// planes of the forward intermediates the reverse kernels read, kept per stage: the
+// limited face and volume point values, the limiter factors, the weak moments, the
+// gradients and the characteristic reconstruction data; the other scratch is shared
+static const long long SEG_WORK_PLANES = 48 + 36 + 2 + 18 + 126 + 144;
+
+static Work seg_work(hweno_handle* h, int n, int stage) {
+  const long long ps = h->g.ps;
+  double* p = h->spool + (long long)h->seg_max * 36 * ps + ((long long)n * 3 + stage) * SEG_WORK_PLANES * ps;
+  Work w = h->w;  // the shared planes are the same in every scratch set
+  w.face = p; p += 48 * ps;
+  w.vol = p; p += 36 * ps;
+  w.theta = p; p += 2 * ps;
+  w.rm = p; p += 18 * ps;
+  w.gr = p; p += 126 * ps;
+  w.yrec = p;
+  return w;
+}
+
+static double* seg_state(hweno_handle* h, int n, int k) {  // k = 0: q^n, 1: q1, 2: q2
+  return h->spool + ((long long)n * 3 + k) * 12 * h->g.ps;
+}
+
+
+// restores the handle's scratch set on every exit of a scope that points it elsewhere
+struct WorkGuard {
+  hweno_handle* h;
+  Work w;
+  explicit WorkGuard(hweno_handle* hh) : h(hh), w(hh->w) {}
+  ~WorkGuard() { h->w = w; }
+};
+
 static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_used, int* rejections) {
   const Grid& g = h->g;
+  // recording for the adjoint: stage states (and intermediates) go to the next slot
+  const int rec = h->recording ? h->rec_count : -1;
+  if (rec >= h->seg_max && h->recording)
+    return fail(h, HWENO_ERR_STATE, "recording more steps than hweno_adjoint_reserve allowed");
+  const bool keep = rec >= 0 && h->seg_keep;
+  WorkGuard wg(h);
+  double* q1 = rec >= 0 ? seg_state(h, rec, 1) : h->QS;
+  double* q2 = rec >= 0 ? seg_state(h, rec, 2) : h->QS;
+  if (keep) h->w = seg_work(h, rec, 0);
   int rc = reset_diag(h);
   if (!rc) rc = residual_eval(h, h->Q, h->RHS0, h->MOM0);
   if (rc) return rc;
+  if (rec >= 0)  // q^n with its ghost cells, as the reverse reads it
+    CK(cudaMemcpyAsync(seg_state(h, rec, 0), h->Q, (size_t)12 * g.ps * sizeof(double), cudaMemcpyDeviceToDevice,
+                       h->st), "record copy");
   {
     Prof p(h, K_RK);
     k_dt<<<1, 1, 0, h->st>>>(h->d_diag, h->cfg.cfl, h_min(h), h->cfg.b_visc * h->cfg.Re * h_min(h) * h_min(h),
@@ -569,11 +626,13 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
     // stage flags and counters of this attempt; keep dt and the stage-1 maxima
     CK(cudaMemsetAsync(&h->d_diag->pp_count, 0, sizeof(unsigned long long), h->st), "diag");
     CK(cudaMemsetAsync(&h->d_diag->flags, 0, sizeof(unsigned int), h->st), "diag");
-    if ((rc = launch_rk(h, 1, h->Q, h->MOM0, h->RHS0, h->QS))) return rc;
-    if ((rc = residual_eval(h, h->QS, h->RHS, h->MOM))) return rc;
-    if ((rc = launch_rk(h, 2, h->QS, h->MOM, h->RHS, h->QS))) return rc;
-    if ((rc = residual_eval(h, h->QS, h->RHS, h->MOM))) return rc;
-    if ((rc = launch_rk(h, 3, h->QS, h->MOM, h->RHS, h->QS))) return rc;
+    if ((rc = launch_rk(h, 1, h->Q, h->MOM0, h->RHS0, q1))) return rc;
+    if (keep) h->w = seg_work(h, rec, 1);
+    if ((rc = residual_eval(h, q1, h->RHS, h->MOM))) return rc;
+    if ((rc = launch_rk(h, 2, q1, h->MOM, h->RHS, q2))) return rc;
+    if (keep) h->w = seg_work(h, rec, 2);
+    if ((rc = residual_eval(h, q2, h->RHS, h->MOM))) return rc;
+    if ((rc = launch_rk(h, 3, q2, h->MOM, h->RHS, h->QS))) return rc;
     if ((rc = read_diag(h))) return rc;
     const Diag& d = *h->h_diag;
     if (!(d.flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE))) {
@@ -588,6 +647,10 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
       h->dt_last = dt;
       h->steps++;
       h->rejected += rej;
+      if (rec >= 0) {
+        h->rec_dts.push_back(dt);
+        h->rec_count++;
+      }
       if (dt_used) *dt_used = dt;
       if (rejections) *rejections = rej;
       return HWENO_OK;
@@ -767,6 +830,7 @@ int hweno_measure_peak(hweno_handle* h, int which, double* tflops) {
 static int adjoint_operator(hweno_handle* h, const double* x) {
   const Grid& g = h->g;
   Adj& a = h->adj;
+  if (!h->w.yrec) return fail(h, HWENO_ERR_STATE, "adjoint sweep without the forward's reconstruction record");
   const size_t P = (size_t)g.ps * sizeof(double);
   CK(cudaMemsetAsync(a.face, 0, 48 * P, h->st), "adjoint clear");
   CK(cudaMemsetAsync(a.vol, 0, 36 * P, h->st), "adjoint clear");
@@ -795,8 +859,8 @@ int hweno_adjoint_init(hweno_handle* h) {
   if (h->apool) return HWENO_OK;
   const Grid& g = h->g;
   // R 12, M 8, face 48, vol 36, gr 126, rm 18, cg 102, cc 68, q 12, stage-1 state 12,
-  // lambda 12, base adjoint 12, temporary 12
-  const long long nplanes = 12 + 8 + 48 + 36 + 126 + 18 + 102 + 68 + 12 + 12 * 4;
+  // lambda 12, base adjoint 12, temporary 12, reconstruction record 144
+  const long long nplanes = 12 + 8 + 48 + 36 + 126 + 18 + 102 + 68 + 12 + 12 * 4 + 144;
   const long long total = nplanes * g.ps + 8;
   CK(cudaMalloc(&h->apool, (size_t)total * sizeof(double)), "adjoint allocation");
   CK(cudaMemsetAsync(h->apool, 0, (size_t)total * sizeof(double), h->st), "adjoint clear");
@@ -806,34 +870,11 @@ int hweno_adjoint_init(hweno_handle* h) {
   a.R = take(12); a.M = take(8); a.face = take(48); a.vol = take(36); a.gr = take(126); a.rm = take(18);
   a.cg = take(102); a.cc = take(68); a.q = take(12);
   h->AST1 = take(12); h->ALAM = take(12); h->ABB = take(12); h->ATMP = take(12);
+  h->AYREC = take(144);
   a.mu = p;
   a.flags = reinterpret_cast<unsigned int*>(p + 1);
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   return HWENO_OK;
-}
-
-// planes of the forward intermediates the reverse kernels read
-static const long long SEG_WORK_PLANES = 48 + 36 + 3 + 6 + 6 + 18 + 126 + 12 + 12 + 2;
-
-static Work seg_work(hweno_handle* h, int n, int stage) {
-  const long long ps = h->g.ps;
-  double* p = h->spool + (long long)h->seg_max * 36 * ps + ((long long)n * 3 + stage) * SEG_WORK_PLANES * ps;
-  Work w;
-  w.face = p; p += 48 * ps;
-  w.vol = p; p += 36 * ps;
-  w.wbar = p; p += 3 * ps;
-  w.wx = p; p += 6 * ps;
-  w.wy = p; p += 6 * ps;
-  w.rm = p; p += 18 * ps;
-  w.gr = p; p += 126 * ps;
-  w.fx = p; p += 12 * ps;
-  w.fy = p; p += 12 * ps;
-  w.theta = p;
-  return w;
-}
-
-static double* seg_state(hweno_handle* h, int n, int k) {  // k = 0: q^n, 1: q1, 2: q2
-  return h->spool + ((long long)n * 3 + k) * 12 * h->g.ps;
 }
 
 extern "C" int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_intermediates) {
@@ -856,55 +897,27 @@ extern "C" int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_in
     else planes = with;
   }
   CK(cudaMalloc(&h->spool, (size_t)planes * ps * sizeof(double)), "adjoint segment allocation");
+  h->rec_count = 0;
+  h->rec_dts.clear();
   h->seg_max = max_steps;
   h->seg_keep = keep;
   return keep ? 1 : HWENO_OK;
 }
 
-extern "C" int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int nsteps, const double* dts,
-                                     const double* lam_end, double* lam_start, double* mubar, int on_device) {
-  if (!h || !q_start || !dts || !lam_end || !lam_start || nsteps < 1)
-    return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: bad argument");
-  if (!h->spool || nsteps > h->seg_max)
-    return fail(h, HWENO_ERR_STATE, "hweno_adjoint_segment: reserve storage for this many steps first");
+// the reverse sweep over the recorded steps rec_count-1 .. 0: lam (in h->ALAM) becomes
+// the adjoint at the first recorded state; mu-bar accumulates in a.mu
+static int adjoint_reverse(hweno_handle* h, const char* who) {
   const Grid& g = h->g;
   Adj& a = h->adj;
-  const Work base = h->w;
   const bool keep = h->seg_keep != 0;
-  int rc;
-  if ((rc = copy_planes_in(h, q_start, 12, seg_state(h, 0, 0), on_device))) return rc;
-  if ((rc = copy_planes_in(h, lam_end, 12, h->ALAM, on_device))) return rc;
-  if ((rc = reset_diag(h))) return rc;
-  // forward recomputation of the segment, keeping the stage states (and intermediates)
-  for (int n = 0; n < nsteps; n++) {
-    double* q0 = seg_state(h, n, 0);
-    double* q1 = seg_state(h, n, 1);
-    double* q2 = seg_state(h, n, 2);
-    double* out = n + 1 < nsteps ? seg_state(h, n + 1, 0) : h->QS;
-    if (keep) h->w = seg_work(h, n, 0);
-    if ((rc = residual_eval(h, q0, h->RHS0, h->MOM0))) break;
-    k_dt<<<1, 1, 0, h->st>>>(h->d_diag, h->cfg.cfl, h_min(h), 1.0, dts[n], INFINITY);
-    if ((rc = launch_rk(h, 1, q0, h->MOM0, h->RHS0, q1))) break;
-    if (keep) h->w = seg_work(h, n, 1);
-    if ((rc = residual_eval(h, q1, h->RHS, h->MOM))) break;
-    if ((rc = launch_rk(h, 2, q1, h->MOM, h->RHS, q2))) break;
-    if (keep) h->w = seg_work(h, n, 2);
-    if ((rc = residual_eval(h, q2, h->RHS, h->MOM))) break;
-    if ((rc = launch_rk(h, 3, q2, h->MOM, h->RHS, out))) break;
-  }
-  h->w = base;
-  if (rc) return rc;
-  if ((rc = read_diag(h))) return rc;
-  if (h->h_diag->pp_count)
-    return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: the positivity limiter is active in this segment (its adjoint is not implemented)");
-  if (h->h_diag->flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE))
-    return fail(h, HWENO_ERR_INADMISSIBLE, "hweno_adjoint_segment: a forward stage is inadmissible at the given steps");
-  CK(cudaMemsetAsync(a.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
+  WorkGuard wg(h);
+  h->w.yrec = h->AYREC;  // for stages re-evaluated here
+  int rc = HWENO_OK;
   const dim3 gi = grid2(g.nx, g.ny), blk(BX, BY);
-  for (int n = nsteps - 1; n >= 0 && !rc; n--) {
-    const double dt = dts[n];
+  for (int n = h->rec_count - 1; n >= 0 && !rc; n--) {
+    const double dt = h->rec_dts[n];
     double* st[3] = {seg_state(h, n, 0), seg_state(h, n, 1), seg_state(h, n, 2)};
-    // stage 3 at q2, stage 2 at q1, stage 1 at q^n (see hweno_adjoint_step)
+    // stage 3 at q2, stage 2 at q1, stage 1 at q^n (the Shu-Osher weights of each stage)
     const double sr[3] = {dt, 0.25 * dt, (2.0 / 3.0) * dt}, sm[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int stage = 2; stage >= 0 && !rc; stage--) {
       if (stage == 2) ka_axpby<<<gi, blk, 0, h->st>>>(g, h->ABB, 0.0, h->ALAM, 1.0 / 3.0);
@@ -918,19 +931,100 @@ extern "C" int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int
       std::swap(h->ALAM, h->ATMP);
     }
   }
-  h->w = base;
   if (rc) return rc;
+  CK(cudaGetLastError(), "adjoint launch");
+  (void)who;
+  return HWENO_OK;
+}
+
+// lam_start and mu-bar from h->ALAM and a.mu after a reverse sweep
+static int adjoint_finish(hweno_handle* h, double* lam_start, double* mubar, int on_device, const char* who) {
+  int rc;
   if ((rc = copy_planes_out(h, h->ALAM, 12, lam_start, on_device))) return rc;
   double hm[2];
-  CK(cudaMemcpyAsync(h->h_red, a.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
+  CK(cudaMemcpyAsync(h->h_red, h->adj.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   memcpy(hm, h->h_red, sizeof(hm));
   unsigned int fl;
   memcpy(&fl, &hm[1], sizeof(fl));
-  if (fl & FLAG_ADJ_LIMITER) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: limiter active in a stage");
+  if (fl & FLAG_ADJ_LIMITER) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "%s: the positivity limiter acts in a stage (its adjoint is not implemented)", who);
+    return fail(h, HWENO_ERR_ARG, msg);
+  }
   if (mubar) *mubar = hm[0];
-  h->have_state = false;  // the handle's state buffers hold segment data now
   return HWENO_OK;
+}
+
+extern "C" int hweno_adjoint_record(hweno_handle* h, int on) {
+  if (!h) return HWENO_ERR_ARG;
+  if (on && !h->spool) return fail(h, HWENO_ERR_STATE, "hweno_adjoint_record before hweno_adjoint_reserve");
+  h->recording = on != 0;
+  if (on) {
+    h->rec_count = 0;
+    h->rec_dts.clear();
+  }
+  return HWENO_OK;
+}
+
+extern "C" int hweno_adjoint_replay(hweno_handle* h, const double* lam_end, double* lam_start, double* mubar,
+                                    int on_device) {
+  if (!h || !lam_end || !lam_start) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_replay: bad argument");
+  if (!h->spool || h->rec_count < 1) return fail(h, HWENO_ERR_STATE, "hweno_adjoint_replay: no recorded steps");
+  h->recording = false;
+  int rc;
+  if ((rc = copy_planes_in(h, lam_end, 12, h->ALAM, on_device))) return rc;
+  CK(cudaMemsetAsync(h->adj.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
+  if ((rc = adjoint_reverse(h, "hweno_adjoint_replay"))) return rc;
+  return adjoint_finish(h, lam_start, mubar, on_device, "hweno_adjoint_replay");
+}
+
+extern "C" int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int nsteps, const double* dts,
+                                     const double* lam_end, double* lam_start, double* mubar, int on_device) {
+  if (!h || !q_start || !dts || !lam_end || !lam_start || nsteps < 1)
+    return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: bad argument");
+  if (!h->spool || nsteps > h->seg_max)
+    return fail(h, HWENO_ERR_STATE, "hweno_adjoint_segment: reserve storage for this many steps first");
+  const bool keep = h->seg_keep != 0;
+  h->recording = false;
+  int rc;
+  if ((rc = copy_planes_in(h, q_start, 12, seg_state(h, 0, 0), on_device))) return rc;
+  if ((rc = copy_planes_in(h, lam_end, 12, h->ALAM, on_device))) return rc;
+  if ((rc = reset_diag(h))) return rc;
+  // forward recomputation of the segment with the given step sizes, keeping the stage
+  // states (and intermediates)
+  {
+    WorkGuard wg(h);
+    for (int n = 0; n < nsteps && !rc; n++) {
+      double* q0 = seg_state(h, n, 0);
+      double* q1 = seg_state(h, n, 1);
+      double* q2 = seg_state(h, n, 2);
+      double* out = n + 1 < nsteps ? seg_state(h, n + 1, 0) : h->QS;
+      if (keep) h->w = seg_work(h, n, 0);
+      if ((rc = residual_eval(h, q0, h->RHS0, h->MOM0))) break;
+      k_dt<<<1, 1, 0, h->st>>>(h->d_diag, h->cfg.cfl, h_min(h), 1.0, dts[n], INFINITY);
+      if ((rc = launch_rk(h, 1, q0, h->MOM0, h->RHS0, q1))) break;
+      if (keep) h->w = seg_work(h, n, 1);
+      if ((rc = residual_eval(h, q1, h->RHS, h->MOM))) break;
+      if ((rc = launch_rk(h, 2, q1, h->MOM, h->RHS, q2))) break;
+      if (keep) h->w = seg_work(h, n, 2);
+      if ((rc = residual_eval(h, q2, h->RHS, h->MOM))) break;
+      if ((rc = launch_rk(h, 3, q2, h->MOM, h->RHS, out))) break;
+    }
+  }
+  if (rc) return rc;
+  if ((rc = read_diag(h))) return rc;
+  if (h->h_diag->pp_count)
+    return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: the positivity limiter is active in this segment (its adjoint is not implemented)");
+  if (h->h_diag->flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE))
+    return fail(h, HWENO_ERR_INADMISSIBLE, "hweno_adjoint_segment: a forward stage is inadmissible at the given steps");
+  h->rec_count = nsteps;
+  h->rec_dts.assign(dts, dts + nsteps);
+  CK(cudaMemsetAsync(h->adj.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
+  if ((rc = adjoint_reverse(h, "hweno_adjoint_segment"))) return rc;
+  h->rec_count = 0;
+  h->have_state = false;  // the handle's state buffers hold segment data now
+  return adjoint_finish(h, lam_start, mubar, on_device, "hweno_adjoint_segment");
 }
 
 int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar, const double* mbar, double* xbar,
@@ -939,6 +1033,8 @@ int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar,
   if (!h->apool) return fail(h, HWENO_ERR_STATE, "hweno_adjoint_residual before hweno_adjoint_init");
   const Grid& g = h->g;
   Adj& a = h->adj;
+  WorkGuard wg(h);
+  h->w.yrec = h->AYREC;
   int rc;
   if ((rc = copy_planes_in(h, x, 12, h->Q, on_device))) return rc;
   h->have_state = true;
@@ -970,6 +1066,8 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
   if (!h->apool) return fail(h, HWENO_ERR_STATE, "hweno_adjoint_step before hweno_adjoint_init");
   const Grid& g = h->g;
   Adj& a = h->adj;
+  WorkGuard wg(h);
+  h->w.yrec = h->AYREC;
   int rc;
   if ((rc = copy_planes_in(h, q, 12, h->Q, on_device))) return rc;
   if ((rc = copy_planes_in(h, lam_next, 12, h->ALAM, on_device))) return rc;

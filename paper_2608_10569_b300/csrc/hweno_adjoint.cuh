@@ -42,11 +42,11 @@ struct Adj {
 // ---------------------------------------------------------------------------
 // adjoints of the pointwise helpers
 
-// cons (rho, m, n, E) -> prim (rho, u, v, e):  given wbar, accumulate Ubar
-__device__ __forceinline__ void prim_T(const double* U, const double* wb, double* Ub) {
-  const double rr = 1.0 / U[0];
-  const double u = U[1] * rr, v = U[2] * rr;
-  const double e = U[3] * rr - 0.5 * (u * u + v * v);
+// cons -> prim (rho, u, v, e) VJP: given wbar at U, accumulate Ubar; takes the primitive
+// values W = (rho, u, v, e) of U
+__device__ __forceinline__ void prim_T_w(const double* W, const double* wb, double* Ub) {
+  const double rr = 1.0 / W[0];
+  const double u = W[1], v = W[2], e = W[3];
   Ub[1] += (wb[1] - wb[3] * u) * rr;
   Ub[2] += (wb[2] - wb[3] * v) * rr;
   Ub[3] += wb[3] * rr;
@@ -239,12 +239,14 @@ __device__ __forceinline__ void eval_vol_T(const double* ob, double* cb) {
 }
 
 // ---------------------------------------------------------------------------
-// adjoint of hweno_combine_coeffs<double> (the product form of the weights).
-// Recomputes the forward from (c0, s, ctr); given Cbar accumulates c0b, sb, ctrb.
+// adjoint of hweno_combine_coeffs<double> (the product form of the weights).  Takes the
+// forward's beta_0, the gradient gr = d beta_0 / d c0 and, if rs0 > 0, the forward's
+// reciprocal 1/S' (else it is recomputed); recomputes the rest of the weights from
+// (c0, s, ctr); given Cbar accumulates c0b, sb, ctrb.
 __device__ __forceinline__ void hweno_combine_T(const double* c0, const double* s, double ctr, double eps,
-                                                const double* Cb, double* c0b, double* sb, double& ctrb) {
+                                                double b0, double rs0, const double* gr, const double* Cb,
+                                                double* c0b, double* sb, double& ctrb) {
   const double dxm = s[0], dxp = s[1], dym = s[2], dyp = s[3];
-  const double b0 = hw_beta_quartic<double>(c0);
   const double b[5] = {b0, dxm * dxm + dym * dym, dxp * dxp + dym * dym, dxm * dxm + dyp * dyp, dxp * dxp + dyp * dyp};
   double e[5];
   for (int m = 1; m < 5; m++) e[m] = b0 - b[m];
@@ -256,8 +258,7 @@ __device__ __forceinline__ void hweno_combine_T(const double* c0, const double* 
   const double R[5] = {0.0, D[2] * D34, D[1] * D34, D12 * D[4], D12 * D[3]};
   const double Q0 = D12 * D34, P = D[0] * Q0;
   const double SR = (R[1] + R[2]) + (R[3] + R[4]);
-  const double Sp = P + tau * (GAM0 * Q0 + GAML * D[0] * SR);
-  const double rs = 1.0 / Sp;
+  const double rs = rs0 > 0.0 ? rs0 : 1.0 / (P + tau * (GAM0 * Q0 + GAML * D[0] * SR));
   const double a0 = (P + tau * Q0) * rs;
   const double g = GAML * tau * rs;
   double a[5];
@@ -315,8 +316,6 @@ __device__ __forceinline__ void hweno_combine_T(const double* c0, const double* 
   sb[1] += sbl[1] + 2.0 * dxp * sxpb;
   sb[2] += sbl[2] + 2.0 * dym * symb;
   sb[3] += sbl[3] + 2.0 * dyp * sypb;
-  double gr[15];
-  hw_beta_quartic_grad<double>(c0, gr);
   for (int k = 0; k < 15; k++) c0b[k] += bb[0] * gr[k];
 }
 
@@ -326,67 +325,73 @@ struct CharBar {
   double u, v, c, H, hq2, hb1, hb2, hrc;
 };
 
+// The state-parameter parts of the map adjoints are bilinear in (vector, adjoint): each
+// call adds to a few sums, and char_sums_finish turns the sums of one direction into
+// CharBar once.
+struct CharSums {
+  // to_char: sum Bh x0, Bh xn, Ah x0, Ah x3, Ah xn, Ah xt, yb2 x0  (Ah = A/2 adjoint, Bh = B/2)
+  double B0, Bn, A0, A3, An, At, Y20;
+  // from_char: sum x3b (y0 + y3), x3b dd, xnb dd, x3b y1, xnb x0, x3b y2, xtb x0
+  double H, X3d, Xnd, X31, Xn0, X32, Xt0;
+};
+
 template <int DIR>
 __device__ __forceinline__ void to_char_T(const CharState<double>& s, const double* x, const double* yb, double* xb,
-                                          CharBar& sb) {
+                                          CharSums& m) {
   const double un = DIR == 0 ? s.u : s.v, ut = DIR == 0 ? s.v : s.u;
   const double xn = DIR == 0 ? x[1] : x[2], xt = DIR == 0 ? x[2] : x[1];
   const double Ahb = yb[0] - 2.0 * yb[1] + yb[3];
   const double Bhb = yb[0] - yb[3];
-  double x0b = yb[1] - yb[2] * ut, xnb = 0.0, xtb = yb[2], x3b = 0.0, unb = 0.0, utb = -yb[2] * x[0];
-  sb.hrc += Bhb * (un * x[0] - xn);
-  unb += Bhb * s.hrc * x[0];
-  x0b += Bhb * s.hrc * un;
-  xnb += -Bhb * s.hrc;
-  sb.hb2 += Ahb * x[0];
-  x0b += Ahb * s.hb2;
-  sb.hb1 += Ahb * (x[3] - un * xn - ut * xt);
-  x3b += Ahb * s.hb1;
-  xnb += -Ahb * s.hb1 * un;
-  unb += -Ahb * s.hb1 * xn;
-  xtb += -Ahb * s.hb1 * ut;
-  utb += -Ahb * s.hb1 * xt;
-  xb[0] += x0b;
-  xb[DIR == 0 ? 1 : 2] += xnb;
-  xb[DIR == 0 ? 2 : 1] += xtb;
-  xb[3] += x3b;
-  if (DIR == 0) { sb.u += unb; sb.v += utb; }
-  else { sb.v += unb; sb.u += utb; }
+  const double bh = Bhb * s.hrc, ah = Ahb * s.hb1;
+  xb[0] += (yb[1] - yb[2] * ut) + bh * un + Ahb * s.hb2;
+  xb[DIR == 0 ? 1 : 2] += -bh - ah * un;
+  xb[DIR == 0 ? 2 : 1] += yb[2] - ah * ut;
+  xb[3] += ah;
+  m.B0 += Bhb * x[0];
+  m.Bn += Bhb * xn;
+  m.A0 += Ahb * x[0];
+  m.A3 += Ahb * x[3];
+  m.An += Ahb * xn;
+  m.At += Ahb * xt;
+  m.Y20 += yb[2] * x[0];
 }
 
 template <int DIR>
 __device__ __forceinline__ void from_char_T(const CharState<double>& s, const double* y, const double* xbar,
-                                            double* yb, CharBar& sb) {
+                                            double* yb, CharSums& m) {
   const double un = DIR == 0 ? s.u : s.v, ut = DIR == 0 ? s.v : s.u;
   const double x0 = y[0] + y[1] + y[3];
   const double dd = y[3] - y[0];
-  const double x0b_in = xbar[0], xnb = xbar[DIR == 0 ? 1 : 2], xtb = xbar[DIR == 0 ? 2 : 1], x3b = xbar[3];
-  double unb = 0.0, utb = 0.0, ddb = 0.0;
+  const double x3b = xbar[3], xnb = xbar[DIR == 0 ? 1 : 2], xtb = xbar[DIR == 0 ? 2 : 1];
+  // x0 = y0 + y1 + y3, xn = un x0 + c dd, xt = ut x0 + y2,
   // x3 = H (y0 + y3) + un c dd + hq2 y1 + ut y2
-  sb.H += x3b * (y[0] + y[3]);
-  yb[0] += x3b * s.H;
-  yb[3] += x3b * s.H;
-  ddb += x3b * un * s.c;
-  unb += x3b * s.c * dd;
-  sb.c += x3b * un * dd;
-  sb.hq2 += x3b * y[1];
-  yb[1] += x3b * s.hq2;
-  utb += x3b * y[2];
-  yb[2] += x3b * ut;
-  // xt = ut x0 + y2
-  utb += xtb * x0;
-  double x0b = x0b_in + xtb * ut;
-  yb[2] += xtb;
-  // xn = un x0 + c dd
-  unb += xnb * x0;
-  x0b += xnb * un;
-  sb.c += xnb * dd;
-  ddb += xnb * s.c;
-  yb[3] += ddb;
-  yb[0] -= ddb;
-  yb[0] += x0b;
-  yb[1] += x0b;
-  yb[3] += x0b;
+  const double ddb = s.c * (x3b * un + xnb);
+  const double x0b = xbar[0] + xtb * ut + xnb * un;
+  const double hb = x3b * s.H;
+  yb[0] += hb - ddb + x0b;
+  yb[3] += hb + ddb + x0b;
+  yb[1] += x3b * s.hq2 + x0b;
+  yb[2] += x3b * ut + xtb;
+  m.H += x3b * (y[0] + y[3]);
+  m.X3d += x3b * dd;
+  m.Xnd += xnb * dd;
+  m.X31 += x3b * y[1];
+  m.Xn0 += xnb * x0;
+  m.X32 += x3b * y[2];
+  m.Xt0 += xtb * x0;
+}
+
+template <int DIR>
+__device__ __forceinline__ void char_sums_finish(const CharState<double>& s, const CharSums& m, CharBar& sb) {
+  const double un = DIR == 0 ? s.u : s.v, ut = DIR == 0 ? s.v : s.u;
+  sb.hrc += un * m.B0 - m.Bn;
+  sb.hb2 += m.A0;
+  sb.hb1 += m.A3 - un * m.An - ut * m.At;
+  sb.H += m.H;
+  sb.c += un * m.X3d + m.Xnd;
+  sb.hq2 += m.X31;
+  const double unb = s.hrc * m.B0 - s.hb1 * m.An + s.c * m.X3d + m.Xn0;
+  const double utb = -m.Y20 - s.hb1 * m.At + m.X32 + m.Xt0;
   if (DIR == 0) { sb.u += unb; sb.v += utb; }
   else { sb.v += unb; sb.u += utb; }
 }
@@ -577,8 +582,13 @@ __global__ void __launch_bounds__(128) ka_grad(Grid g, Work w, Adj a) {
     double c0[15];
     hw_p0_coeffs<double>(d, c0);
     const double s[4] = {d[4] - d[3], d[5] - d[4], d[4] - d[1], d[7] - d[4]};
+    // beta_0 = c0 . B c0 from its gradient 2 B c0, which the reverse needs anyway
+    double gr[15], b0 = 0.0;
+    hw_beta_quartic_grad<double>(c0, gr);
+    for (int k = 0; k < 15; k++) b0 += c0[k] * gr[k];
+    b0 *= 0.5;
     double c0b[15] = {0}, sb[4] = {0, 0, 0, 0}, ctrb = 0.0;
-    hweno_combine_T(c0, s, d[4], g.eps_weno, Cb, c0b, sb, ctrb);
+    hweno_combine_T(c0, s, d[4], g.eps_weno, b0, 0.0, gr, Cb, c0b, sb, ctrb);
     double db[17] = {0};
     hw_p0_coeffs_T<double>(c0b, db);
     db[4] += ctrb + sb[0] - sb[1] + sb[2] - sb[3];
@@ -700,27 +710,19 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
     CharState<double> cs;
     char_state<double>(ub, g.gamma, cs);
     const double eps = g.eps_weno;
-    // forward values (recomputed) and adjoints of the conserved point values
-    double face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
-    recon_dir<double, 0, double>(cc, sl, ctr, cs, eps, face, volx, mx);
-    recon_dir<double, 1, double>(cc, sl, ctr, cs, eps, face + 6, vol, my);
-    for (int k = 0; k < 9; k++)
-      for (int v = 0; v < 4; v++) vol[k][v] = 0.5 * (volx[k][v] + vol[k][v]);
-    {
-      double th[2];
-      double ftmp[12][4];
-      for (int k = 0; k < 12; k++)
-        for (int v = 0; v < 4; v++) ftmp[k][v] = face[k][v];
-      if (pp_limit(ub, ftmp, vol, g.gamma, g.eps_pp, th)) flags |= FLAG_ADJ_LIMITER;
-    }
+    // adjoints of the conserved point values, from the stored primitive point values
+    // (the limiter is inactive wherever the adjoint is defined: theta = 1 leaves the
+    // traces unchanged)
+    if (w.theta[c] < 1.0 || w.theta[g.ps + c] < 1.0) flags |= FLAG_ADJ_LIMITER;
     double fb[12][4], vb[9][4];
     for (int k = 0; k < 12; k++) {
-      double wbp[4];
+      double wbp[4], wp[4];
       for (int v = 0; v < 4; v++) {
         wbp[v] = a.face[(long long)(4 * k + v) * g.ps + c];
+        wp[v] = w.face[(long long)(4 * k + v) * g.ps + c];
         fb[k][v] = 0.0;
       }
-      prim_T(face[k], wbp, fb[k]);
+      prim_T_w(wp, wbp, fb[k]);
     }
     // cell mean of u, v, e from the volume values feeds both weak moments
     const bool in2 = i >= -2 && j >= -2 && i < g.nx + 2 && j < g.ny + 2;
@@ -738,7 +740,9 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
         }
         const double wgt = gweight<double>(G) * gweight<double>(H);
         for (int n = 0; n < 3; n++) wbp[1 + n] += wgt * wbarb[n];
-        prim_T(vol[k], wbp, vb[k]);
+        double wp[4];
+        for (int v = 0; v < 4; v++) wp[v] = w.vol[(long long)(4 * k + v) * g.ps + c];
+        prim_T_w(wp, wbp, vb[k]);
       }
     const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
     double mb[2][4];
@@ -765,18 +769,20 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
         if (dir == 0) to_char<double, 0>(cs, x, ps[k]); else to_char<double, 1>(cs, x, ps[k]);
       }
       if (dir == 0) to_char<double, 0>(cs, ctr, pz); else to_char<double, 1>(cs, ctr, pz);
-      // forward per field: combined coefficients and point values in char space
-      double C[4][15], chf[4][6], chv[4][9], chm[4];
+      // this direction's characteristic point values and weight factors per field, as
+      // the forward wrote them
+      const double* yr = w.yrec + (long long)(72 * dir) * g.ps + c;
+      double chf[4][6], chv[4][9], chm[4], wrec[4][2];
       for (int f = 0; f < 4; f++) {
-        double c0[15], s[4];
-        for (int k = 0; k < 15; k++) c0[k] = pc[k][f];
-        for (int k = 0; k < 4; k++) s[k] = ps[k][f];
-        hweno_combine_coeffs<double>(c0, s, pz[f], eps, C[f]);
-        if (dir == 0) eval_xfaces<double>(C[f], chf[f]); else eval_yfaces<double>(C[f], chf[f]);
-        eval_vol<double>(C[f], chv[f]);
-        chm[f] = dir == 0 ? hw_moment_xi<double>(C[f]) : hw_moment_eta<double>(C[f]);
+        const double* y = yr + (long long)(18 * f) * g.ps;
+        for (int k = 0; k < 6; k++) chf[f][k] = y[k * g.ps];
+        for (int k = 0; k < 9; k++) chv[f][k] = y[(6 + k) * g.ps];
+        chm[f] = y[15 * g.ps];
+        wrec[f][0] = y[16 * g.ps];
+        wrec[f][1] = y[17 * g.ps];
       }
       // back-projection adjoints -> char value adjoints
+      CharSums ms = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
       double chfb[4][6], chvb[4][9], chmb[4] = {0, 0, 0, 0};
       for (int f = 0; f < 4; f++) {
         for (int k = 0; k < 6; k++) chfb[f][k] = 0.0;
@@ -785,19 +791,19 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
       for (int k = 0; k < 6; k++) {
         const double y[4] = {chf[0][k], chf[1][k], chf[2][k], chf[3][k]};
         double yb[4] = {0, 0, 0, 0};
-        if (dir == 0) from_char_T<0>(cs, y, fb[k], yb, sb); else from_char_T<1>(cs, y, fb[6 + k], yb, sb);
+        if (dir == 0) from_char_T<0>(cs, y, fb[k], yb, ms); else from_char_T<1>(cs, y, fb[6 + k], yb, ms);
         for (int f = 0; f < 4; f++) chfb[f][k] = yb[f];
       }
       for (int k = 0; k < 9; k++) {
         const double y[4] = {chv[0][k], chv[1][k], chv[2][k], chv[3][k]};
         const double xb[4] = {0.5 * vb[k][0], 0.5 * vb[k][1], 0.5 * vb[k][2], 0.5 * vb[k][3]};
         double yb[4] = {0, 0, 0, 0};
-        if (dir == 0) from_char_T<0>(cs, y, xb, yb, sb); else from_char_T<1>(cs, y, xb, yb, sb);
+        if (dir == 0) from_char_T<0>(cs, y, xb, yb, ms); else from_char_T<1>(cs, y, xb, yb, ms);
         for (int f = 0; f < 4; f++) chvb[f][k] = yb[f];
       }
       {
         double yb[4] = {0, 0, 0, 0};
-        if (dir == 0) from_char_T<0>(cs, chm, mb[0], yb, sb); else from_char_T<1>(cs, chm, mb[1], yb, sb);
+        if (dir == 0) from_char_T<0>(cs, chm, mb[0], yb, ms); else from_char_T<1>(cs, chm, mb[1], yb, ms);
         for (int f = 0; f < 4; f++) chmb[f] = yb[f];
       }
       // per field: point evaluations and the combination
@@ -810,7 +816,9 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
         double c0[15], s[4], c0b[15] = {0}, sbb[4] = {0, 0, 0, 0}, zb = 0.0;
         for (int k = 0; k < 15; k++) c0[k] = pc[k][f];
         for (int k = 0; k < 4; k++) s[k] = ps[k][f];
-        hweno_combine_T(c0, s, pz[f], eps, Cb, c0b, sbb, zb);
+        double gr[15];
+        hw_beta_quartic_grad<double>(c0, gr);
+        hweno_combine_T(c0, s, pz[f], eps, wrec[f][0], wrec[f][1], gr, Cb, c0b, sbb, zb);
         for (int k = 0; k < 15; k++) pcb[k][f] = c0b[k];
         for (int k = 0; k < 4; k++) psb[k][f] = sbb[k];
         pzb[f] = zb;
@@ -819,20 +827,21 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
       for (int k = 0; k < 15; k++) {
         const double x[4] = {cc[0][k], cc[1][k], cc[2][k], cc[3][k]};
         double xb[4] = {0, 0, 0, 0};
-        if (dir == 0) to_char_T<0>(cs, x, pcb[k], xb, sb); else to_char_T<1>(cs, x, pcb[k], xb, sb);
+        if (dir == 0) to_char_T<0>(cs, x, pcb[k], xb, ms); else to_char_T<1>(cs, x, pcb[k], xb, ms);
         for (int v = 0; v < 4; v++) ccb[v][k] += xb[v];
       }
       for (int k = 0; k < 4; k++) {
         const double x[4] = {sl[0][k], sl[1][k], sl[2][k], sl[3][k]};
         double xb[4] = {0, 0, 0, 0};
-        if (dir == 0) to_char_T<0>(cs, x, psb[k], xb, sb); else to_char_T<1>(cs, x, psb[k], xb, sb);
+        if (dir == 0) to_char_T<0>(cs, x, psb[k], xb, ms); else to_char_T<1>(cs, x, psb[k], xb, ms);
         for (int v = 0; v < 4; v++) slb[v][k] += xb[v];
       }
       {
         double xb[4] = {0, 0, 0, 0};
-        if (dir == 0) to_char_T<0>(cs, ctr, pzb, xb, sb); else to_char_T<1>(cs, ctr, pzb, xb, sb);
+        if (dir == 0) to_char_T<0>(cs, ctr, pzb, xb, ms); else to_char_T<1>(cs, ctr, pzb, xb, ms);
         for (int v = 0; v < 4; v++) ctrb[v] += xb[v];
       }
+      if (dir == 0) char_sums_finish<0>(cs, ms, sb); else char_sums_finish<1>(cs, ms, sb);
     }
     char_state_T(ub, g.gamma, sb, ubb);
     for (int v = 0; v < 4; v++) {

@@ -40,8 +40,11 @@ __device__ __forceinline__ T gnode(int g) { return T(g - 1) * T(GN); }
 // (dxp, dym), S3={4,5,8}: (dxm, dyp), S4={5,6,8}: (dxp, dyp).  Writes the
 // coefficients C of the nonlinear combination w0 (p0/g0 - sum gm/g0 pm) + sum wm pm
 // of Eq. (3.4) with the weights of Eq. (A.6).
-template <class T>
-__device__ __forceinline__ void hweno_combine_coeffs(const T* c0, const T* s, T ctr, T eps, T* C) {
+// REC (FP64 only): also return beta_0 and the reciprocal 1/S' in rec[0], rec[1] for a
+// reverse sweep.
+template <class T, bool REC = false>
+__device__ __forceinline__ void hweno_combine_coeffs(const T* c0, const T* s, T ctr, T eps, T* C,
+                                                     T* rec = nullptr) {
   const T dxm = s[0], dxp = s[1], dym = s[2], dyp = s[3];
   const T sxm = dxm * dxm, sxp = dxp * dxp, sym = dym * dym, syp = dyp * dyp;
   const T b0 = hw_beta_quartic<T>(c0);
@@ -65,6 +68,10 @@ __device__ __forceinline__ void hweno_combine_coeffs(const T* c0, const T* s, T 
     const T P = D0 * Q0;
     const T Sp = P + tau * (T(GAM0) * Q0 + T(GAML) * D0 * ((R1 + R2) + (R3 + R4)));
     const T rs = T(1) / Sp;
+    if constexpr (REC) {
+      rec[0] = b0;
+      rec[1] = rs;
+    }
     a0 = (P + tau * Q0) * rs;
     const T g = T(GAML) * tau * rs;
     a[0] = g * R1 * e1;

@@ -50,6 +50,11 @@ struct Work {
                   // S1 = sum_g w_g eta_g fhat_g, per conserved variable (12 allocated)
   double* fy;     // y-face above a cell: the same with xi_g
   double* theta;  // 2 planes: limiter factors
+  // 144 planes, only while a step is recorded for the adjoint (else null): per direction
+  // d and field f of the characteristic reconstruction, plane 72 d + 18 f + slot with
+  // slots 0-5 the face values, 6-14 the volume values, 15 the moment (characteristic
+  // variables), 16 beta_0 and 17 1/S' of the nonlinear weights
+  double* yrec = nullptr;
 };
 
 // device-side reductions and flags of one evaluation / step
@@ -180,10 +185,12 @@ __device__ __forceinline__ void gather17(const Grid& g, const double* q, int v, 
 // transform back.  cc, sl, ctr hold absolute values (FP64) or offsets from the centre
 // average (FP32, ctr = 0); the outputs are in the same representation (moments are
 // unaffected by the offset).
-template <class T, int DIR, class O>
+// REC (FP64): also store this direction's characteristic point values and weight
+// factors of every field at yr[(18 f + slot) * yps] (the Work::yrec layout).
+template <class T, int DIR, class O, bool REC = false>
 __device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], const T* ctr,
                                           const CharState<T>& cs, T eps, O (*face)[4], O (*vol)[4],
-                                          O* mom) {
+                                          O* mom, double* yr = nullptr, long long yps = 0) {
   T chf[4][6], chv[4][9], chm[4];
   T pc[15][4], ps[4][4], pz[4];
 #pragma unroll
@@ -204,10 +211,21 @@ __device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], c
     for (int k = 0; k < 15; k++) c0[k] = pc[k][f];
 #pragma unroll
     for (int k = 0; k < 4; k++) s[k] = ps[k][f];
-    hweno_combine_coeffs<T>(c0, s, pz[f], eps, C);
+    T wr[2];
+    hweno_combine_coeffs<T, REC>(c0, s, pz[f], eps, C, wr);
     if (DIR == 0) eval_xfaces<T>(C, chf[f]); else eval_yfaces<T>(C, chf[f]);
     eval_vol<T>(C, chv[f]);
     chm[f] = DIR == 0 ? hw_moment_xi<T>(C) : hw_moment_eta<T>(C);
+    if constexpr (REC) {
+      double* y = yr + (long long)(18 * f) * yps;
+#pragma unroll
+      for (int k = 0; k < 6; k++) y[k * yps] = chf[f][k];
+#pragma unroll
+      for (int k = 0; k < 9; k++) y[(6 + k) * yps] = chv[f][k];
+      y[15 * yps] = chm[f];
+      y[16 * yps] = wr[0];
+      y[17 * yps] = wr[1];
+    }
   }
 #pragma unroll
   for (int k = 0; k < 6; k++) {

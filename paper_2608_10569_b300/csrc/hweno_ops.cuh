@@ -21,7 +21,8 @@ __device__ __forceinline__ int lane_id() { return (threadIdx.x + threadIdx.y * b
 // ---------------------------------------------------------------------------
 // conservative characteristic reconstruction, modified moments and PP limiter of
 // every cell of the interior grown by 3 (Sec. 3.1, Eq. (3.4), Appendix A.2)
-template <class T>
+// REC (FP64 only): also write the reconstruction data a reverse sweep reads (Work::yrec)
+template <class T, bool REC = false>
 __device__ __forceinline__ void cons_body(const Grid& g, const double* __restrict__ q, const Work& w,
                                           double* __restrict__ mom, Diag* diag, int gx, int gy) {
   const int i = gx - 3;
@@ -53,8 +54,9 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
     double face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
     CharState<T> cs;
     char_state<T>(ut, (T)g.gamma, cs);
-    recon_dir<T, 0, double>(cc, sl, ctr, cs, eps, face, volx, mx);
-    recon_dir<T, 1, double>(cc, sl, ctr, cs, eps, face + 6, vol, my);
+    recon_dir<T, 0, double, REC>(cc, sl, ctr, cs, eps, face, volx, mx, REC ? w.yrec + c : nullptr, g.ps);
+    recon_dir<T, 1, double, REC>(cc, sl, ctr, cs, eps, face + 6, vol, my, REC ? w.yrec + 72 * g.ps + c : nullptr,
+                                 g.ps);
 #pragma unroll
     for (int v = 0; v < 4; v++) {
 #pragma unroll

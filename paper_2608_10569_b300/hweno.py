@@ -84,6 +84,8 @@ SIGNATURES = [
     ("hweno_adjoint_residual", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, _D, ctypes.c_int]),
     ("hweno_adjoint_reserve", ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    ("hweno_adjoint_record", ctypes.c_int, [_H, ctypes.c_int]),
+    ("hweno_adjoint_replay", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, _D, ctypes.c_int]),
     ("hweno_adjoint_segment", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_void_p,
                                              ctypes.c_void_p, _D, ctypes.c_int]),
     ("hweno_adjoint_step", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -281,6 +283,22 @@ class Solver:
             _check(self.h, rc)
         return rc == 1
 
+    def adjoint_record(self, on=True):
+        _check(self.h, self.lib.hweno_adjoint_record(self.h, 1 if on else 0))
+
+    def adjoint_replay(self, lam_end, lam_start=None):
+        """(lam_start, mubar) through the recorded steps."""
+        import torch
+        if lam_start is None:
+            lam_start = torch.empty_like(lam_end) if torch.is_tensor(lam_end) else np.empty_like(lam_end)
+        pl, dl = _ptr_of(lam_end)
+        po, do = _ptr_of(lam_start)
+        if dl != do:
+            raise ValueError("lam_end and lam_start must both be host or both be device buffers")
+        mub = ctypes.c_double(0.0)
+        _check(self.h, self.lib.hweno_adjoint_replay(self.h, pl, po, ctypes.byref(mub), dl))
+        return lam_start, mub.value
+
     def adjoint_segment(self, q_start, dts, lam_end, lam_start=None):
         """(lam_start, mubar) through the steps with sizes dts from q_start."""
         import torch
@@ -392,29 +410,41 @@ def _rollout_autograd():
         """q_T = Phi^n(q_0) for n SSP-RK3 steps of the FP64 solver, differentiable with
         respect to the initial state q_0 and the viscosity mu = 1/Re.
 
-        Forward: the steps under the time-step rule of Sec. 5; the step sizes are
-        recorded and the state is checkpointed every `ckpt` steps.  Backward: for each
-        segment, last to first, the states inside it are recomputed from its checkpoint
-        with the recorded step sizes, then the adjoint runs backwards through the
-        segment's steps (hweno_adjoint_step); the step sizes are held fixed."""
+        Forward: the steps under the time-step rule of Sec. 5; the step sizes are kept,
+        the state is checkpointed every `ckpt` steps, and (when a gradient will be taken)
+        the final segment is recorded with its stage states and intermediates
+        (hweno_adjoint_record).  Backward: the adjoint of the final segment from the
+        recording (hweno_adjoint_replay), then for each earlier segment, last to first,
+        one recomputation from its checkpoint with the kept step sizes followed by the
+        reverse sweep (hweno_adjoint_segment).  The step sizes are held fixed."""
 
         @staticmethod
-        def forward(ctx, q0, mu, case_params, nsteps, ckpt):
+        def forward(ctx, q0, mu, case_params, nsteps, ckpt, record):
             p = dict(case_params)
             p["Re"] = 1.0 / float(mu)
             s = Solver(p, precision="fp64")
             s.set_state(q0.detach().contiguous())
             dts, ckpts = [], {0: q0.detach().clone()}
+            last = ((nsteps - 1) // ckpt) * ckpt if nsteps > 0 else 0  # first step of the final segment
+            recorded = False
             for n in range(nsteps):
+                if record and n == last:
+                    s.adjoint_init()
+                    s.adjoint_reserve(min(ckpt, nsteps), keep_intermediates=True)
+                    s.adjoint_record(True)
+                    recorded = True
                 dt, _ = s.step()
                 dts.append(dt)
                 if (n + 1) % ckpt == 0 and n + 1 < nsteps:
                     ckpts[n + 1] = s.get_state().clone()
+            if recorded:
+                s.adjoint_record(False)
             qT = s.get_state().clone()
             ctx.solver = s
             ctx.dts = dts
             ctx.ckpts = ckpts
             ctx.ckpt = ckpt
+            ctx.recorded = last if recorded else None
             return qT
 
         @staticmethod
@@ -428,10 +458,13 @@ def _rollout_autograd():
             mubar = 0.0
             for a in reversed(sorted(ckpts)):
                 b = min(a + K, n)
-                lam, mb = s.adjoint_segment(ckpts[a], dts[a:b], lam)
+                if a == ctx.recorded:
+                    lam, mb = s.adjoint_replay(lam)
+                else:
+                    lam, mb = s.adjoint_segment(ckpts[a], dts[a:b], lam)
                 mubar += mb
             s.close()
-            return lam, qbar.new_tensor(mubar), None, None, None
+            return lam, qbar.new_tensor(mubar), None, None, None, None
 
     return Rollout
 
@@ -444,4 +477,5 @@ def rollout(q0, mu, case_params, nsteps, ckpt=20):
         _ROLLOUT = _rollout_autograd()
     if not torch.is_tensor(mu):
         mu = torch.tensor(float(mu), dtype=torch.float64, device=q0.device)
-    return _ROLLOUT.apply(q0, mu, case_params, int(nsteps), int(ckpt))
+    record = torch.is_grad_enabled() and (q0.requires_grad or mu.requires_grad)
+    return _ROLLOUT.apply(q0, mu, case_params, int(nsteps), int(ckpt), bool(record))

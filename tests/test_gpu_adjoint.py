@@ -187,3 +187,43 @@ def test_segment_adjoint_equals_chained_steps(keep):
     s.close()
     assert np.abs(lam2 - lam).max() <= 1e-12 * np.abs(lam).max()
     assert abs(mub2 - mub) <= 1e-12 * abs(mub)
+
+
+@pytest.mark.parametrize("keep", [True, False])
+def test_recorded_steps_replay_equals_chained_steps(keep):
+    """Steps recorded while hweno_step runs (hweno_adjoint_record), reversed by
+    hweno_adjoint_replay, give the chain of single-step adjoints at the recorded step
+    sizes; the replay leaves the solver's state alone, and recording more steps than
+    reserved is an error."""
+    case, q = I.taylor_green(20, 0.4, 300.0, 1 / (1.4 * 0.09), rho_pert=1e-3, seed=12)
+    rng = np.random.default_rng(13)
+    lam_end = rng.normal(size=q.shape)
+    s = hweno.Solver(case.params())
+    s.set_state(q.copy())
+    s.adjoint_init()
+    assert s.adjoint_reserve(3, keep_intermediates=keep) == keep
+    s.step()  # not recorded
+    states = [s.get_state(np.zeros_like(q))]
+    s.adjoint_record(True)
+    dts = []
+    for _ in range(3):
+        dts.append(s.step()[0])
+        states.append(s.get_state(np.zeros_like(q)))
+    s.adjoint_record(False)
+    s.step()  # not recorded either
+    q_after = s.get_state(np.zeros_like(q))
+    lam, mub = s.adjoint_replay(lam_end.copy(), np.zeros_like(q))
+    assert np.array_equal(s.get_state(np.zeros_like(q)), q_after)
+    lam2, mub2 = lam_end.copy(), 0.0
+    for k in range(2, -1, -1):
+        lam2, mb = s.adjoint_step(states[k].copy(), dts[k], lam2, np.zeros_like(q))
+        mub2 += mb
+    assert np.abs(lam - lam2).max() <= 1e-12 * np.abs(lam2).max()
+    assert abs(mub - mub2) <= 1e-12 * abs(mub2)
+    s.set_state(q.copy())
+    s.adjoint_record(True)
+    for _ in range(3):
+        s.step()
+    with pytest.raises(hweno.HwenoError, match="reserve"):
+        s.step()
+    s.close()
