@@ -2,7 +2,9 @@
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this module.  It compiles ``hweno_oracle.c`` with gcc
-(no FMA contraction, OpenMP over cells) into ``liboracle.so`` beside it.
+(no FMA contraction, OpenMP over cells) into ``liboracle.so`` beside it, and the same
+source over dual numbers (``hweno_oracle_jvp.cpp``, g++) into ``liboracle_jvp.so``:
+the forward-mode tangents ``residual_jvp`` and ``step_jvp``.
 
 States are numpy float64 arrays of shape (12, ny, nx): plane 4*m + v holds
 moment m (0 = cell average, 1 = scaled xi-moment, 2 = scaled eta-moment) of
@@ -19,8 +21,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hweno_oracle.c")
 _HDR = os.path.join(_HERE, "oracle_tables.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_JVP_SRC = os.path.join(_HERE, "hweno_oracle_jvp.cpp")
+_JVP_LIB = os.path.join(_HERE, "liboracle_jvp.so")
 _lock = threading.Lock()
 _lib = None
+_jvp = None
 
 BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3}
 
@@ -46,6 +51,16 @@ def build(force=False):
                "-std=c11", "-o", _LIB + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
+    stale = (not os.path.exists(_JVP_LIB) or
+             os.path.getmtime(_JVP_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR),
+                                               os.path.getmtime(_JVP_SRC)))
+    if force or stale:
+        # -fpermissive -w: the C source assigns malloc/calloc results without casts,
+        # the only construct C++ rejects; nothing else is diagnosed
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+               "-std=c++17", "-fpermissive", "-w", "-o", _JVP_LIB + ".tmp", _JVP_SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_JVP_LIB + ".tmp", _JVP_LIB)
     return _LIB
 
 
@@ -197,3 +212,45 @@ def eigen(ub, gamma, direction):
     L, R = np.zeros((4, 4)), np.zeros((4, 4))
     lib.or_eigen_export(_ptr(ub), float(gamma), int(direction), _ptr(L), _ptr(R))
     return L, R
+
+
+def _load_jvp():
+    global _jvp
+    _load()
+    with _lock:
+        if _jvp is None:
+            lib = ctypes.CDLL(_JVP_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.or_jvp_residual.argtypes = [ctypes.POINTER(_Cfg), dp, dp, ctypes.c_double, dp, dp, dp, dp]
+            lib.or_jvp_step.argtypes = [ctypes.POINTER(_Cfg), dp, dp, ctypes.c_double, ctypes.c_double, dp]
+            _jvp = lib
+    return _jvp
+
+
+def residual_jvp(cfg, q, qdot=None, dmu=0.0):
+    """The residual and its tangent along (qdot, dmu) by the dual-number build:
+    dict(rhs, rhs_dot (12,ny,nx), vhat, vhat_dot (8,ny,nx)).  dmu is the tangent of
+    mu = 1/Re."""
+    lib = _load_jvp()
+    q = _state(cfg, q)
+    qd = None if qdot is None else _state(cfg, qdot)
+    ny, nx = cfg.ny, cfg.nx
+    o = {"rhs": np.zeros((12, ny, nx)), "rhs_dot": np.zeros((12, ny, nx)),
+         "vhat": np.zeros((8, ny, nx)), "vhat_dot": np.zeros((8, ny, nx))}
+    rc = lib.or_jvp_residual(ctypes.byref(cfg), _ptr(q), _ptr(qd), float(dmu), _ptr(o["rhs"]),
+                             _ptr(o["rhs_dot"]), _ptr(o["vhat"]), _ptr(o["vhat_dot"]))
+    if rc:
+        raise MemoryError("oracle residual_jvp failed")
+    return o
+
+
+def step_jvp(cfg, q, qdot, dt, dmu=0.0):
+    """One SSP-RK3 step of size dt and its tangent along (qdot, dmu), by the
+    dual-number build: returns (q_new, qdot_new, stats dict)."""
+    lib = _load_jvp()
+    q = _state(cfg, q).copy()
+    qd = _state(cfg, qdot).copy()
+    st = np.zeros(6)
+    lib.or_jvp_step(ctypes.byref(cfg), _ptr(q), _ptr(qd), float(dmu), float(dt), _ptr(st))
+    return q, qd, {"dt": st[0], "rejections": int(st[1]), "alpha": st[2], "beta_max": st[3],
+                   "pp_active": st[4], "status": int(st[5])}

@@ -34,6 +34,9 @@ __global__ void __launch_bounds__(BX * BY) k_cons_rec(Grid g, const double* __re
   cons_body<double, true>(g, q, w, mom, diag, blockIdx.x * blockDim.x + threadIdx.x,
                           blockIdx.y * blockDim.y + threadIdx.y);
 }
+__global__ void __launch_bounds__(BX * BY) k_grad_rec(Grid g, Work w) {
+  grad_body<double, true>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
 __global__ void k_face_moments(Grid g, Work w) {
   face_moments_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
 }
@@ -326,7 +329,10 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
     }
     {
       Prof p(h, K_GRAD);
-      k_grad<double><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+      if (h->w.yrec)
+        k_grad_rec<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+      else
+        k_grad<double><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
     }
     {
       Prof p(h, K_FLUX);
@@ -566,7 +572,7 @@ int hweno_residual(hweno_handle* h, double* rhs, double* vhat, int on_device) {
 // planes of the forward intermediates the reverse kernels read, kept per stage: the
 // limited face and volume point values, the limiter factors, the weak moments, the
 // gradients and the characteristic reconstruction data; the other scratch is shared
-static const long long SEG_WORK_PLANES = 48 + 36 + 2 + 18 + 126 + 144;
+static const long long SEG_WORK_PLANES = 48 + 36 + 2 + 18 + 126 + YREC_PLANES;
 
 static Work seg_work(hweno_handle* h, int n, int stage) {
   const long long ps = h->g.ps;
@@ -859,8 +865,8 @@ int hweno_adjoint_init(hweno_handle* h) {
   if (h->apool) return HWENO_OK;
   const Grid& g = h->g;
   // R 12, M 8, face 48, vol 36, gr 126, rm 18, cg 102, cc 68, q 12, stage-1 state 12,
-  // lambda 12, base adjoint 12, temporary 12, reconstruction record 144
-  const long long nplanes = 12 + 8 + 48 + 36 + 126 + 18 + 102 + 68 + 12 + 12 * 4 + 144;
+  // lambda 12, base adjoint 12, temporary 12, reconstruction record
+  const long long nplanes = 12 + 8 + 48 + 36 + 126 + 18 + 102 + 68 + 12 + 12 * 4 + YREC_PLANES;
   const long long total = nplanes * g.ps + 8;
   CK(cudaMalloc(&h->apool, (size_t)total * sizeof(double)), "adjoint allocation");
   CK(cudaMemsetAsync(h->apool, 0, (size_t)total * sizeof(double), h->st), "adjoint clear");
@@ -870,7 +876,7 @@ int hweno_adjoint_init(hweno_handle* h) {
   a.R = take(12); a.M = take(8); a.face = take(48); a.vol = take(36); a.gr = take(126); a.rm = take(18);
   a.cg = take(102); a.cc = take(68); a.q = take(12);
   h->AST1 = take(12); h->ALAM = take(12); h->ABB = take(12); h->ATMP = take(12);
-  h->AYREC = take(144);
+  h->AYREC = take(YREC_PLANES);
   a.mu = p;
   a.flags = reinterpret_cast<unsigned int*>(p + 1);
   CK(cudaStreamSynchronize(h->st), "stream synchronize");

@@ -560,35 +560,29 @@ __global__ void __launch_bounds__(128) ka_grad(Grid g, Work w, Adj a) {
   for (int comp = 0; comp < 6; comp++) {
     const int n = comp >> 1, l = comp & 1;
     const double* A = w.rm + (long long)(6 * n + 3 * l) * g.ps;
-    const double* X = A + g.ps;
-    const double* Y = A + 2 * g.ps;
+    // the 5-point stencil of the averages for the slopes; p0 coefficients and weight
+    // factors as the forward wrote them
     double d[17];
-    for (int b = -1; b <= 1; b++)
-      for (int aa = -1; aa <= 1; aa++) d[(b + 1) * 3 + (aa + 1)] = A[cidx(g, i + aa, j + b)];
-    d[9] = X[cidx(g, i - 1, j)];
-    d[10] = X[cidx(g, i + 1, j)];
-    d[11] = Y[cidx(g, i, j - 1)];
-    d[12] = Y[cidx(g, i, j + 1)];
-    d[13] = X[cidx(g, i, j - 1)];
-    d[14] = X[cidx(g, i, j + 1)];
-    d[15] = Y[cidx(g, i - 1, j)];
-    d[16] = Y[cidx(g, i + 1, j)];
+    d[1] = A[cidx(g, i, j - 1)];
+    d[3] = A[cidx(g, i - 1, j)];
+    d[4] = A[c];
+    d[5] = A[cidx(g, i + 1, j)];
+    d[7] = A[cidx(g, i, j + 1)];
+    const double* y = w.yrec + (long long)(YREC_GR + 17 * comp) * g.ps + c;
+    double c0[15];
+    for (int k = 0; k < 15; k++) c0[k] = y[(long long)k * g.ps];
+    const double b0 = y[(long long)15 * g.ps], rs = y[(long long)16 * g.ps];
     double ob[21];
     for (int k = 0; k < 21; k++) ob[k] = a.gr[(long long)(6 * k + comp) * g.ps + c];
     double Cb[15] = {0};
     eval_xfaces_T(ob, Cb);
     eval_yfaces_T(ob + 6, Cb);
     eval_vol_T(ob + 12, Cb);
-    double c0[15];
-    hw_p0_coeffs<double>(d, c0);
     const double s[4] = {d[4] - d[3], d[5] - d[4], d[4] - d[1], d[7] - d[4]};
-    // beta_0 = c0 . B c0 from its gradient 2 B c0, which the reverse needs anyway
-    double gr[15], b0 = 0.0;
+    double gr[15];
     hw_beta_quartic_grad<double>(c0, gr);
-    for (int k = 0; k < 15; k++) b0 += c0[k] * gr[k];
-    b0 *= 0.5;
     double c0b[15] = {0}, sb[4] = {0, 0, 0, 0}, ctrb = 0.0;
-    hweno_combine_T(c0, s, d[4], g.eps_weno, b0, 0.0, gr, Cb, c0b, sb, ctrb);
+    hweno_combine_T(c0, s, d[4], g.eps_weno, b0, rs, gr, Cb, c0b, sb, ctrb);
     double db[17] = {0};
     hw_p0_coeffs_T<double>(c0b, db);
     db[4] += ctrb + sb[0] - sb[1] + sb[2] - sb[3];
@@ -695,17 +689,19 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
   unsigned int flags = 0;
   if (i < g.nx + 3 && j < g.ny + 3) {
     const long long c = cidx(g, i, j);
+    // p0 coefficients as the forward wrote them; the slopes from the 5-point stencil
     double ub[4], cc[4][15], sl[4][4], ctr[4];
     for (int v = 0; v < 4; v++) {
-      double d[17];
-      gather17<false>(g, q, v, i, j, d);
-      ub[v] = q[(long long)v * g.ps + c];
-      hw_p0_coeffs<double>(d, cc[v]);
-      sl[v][0] = d[4] - d[3];
-      sl[v][1] = d[5] - d[4];
-      sl[v][2] = d[4] - d[1];
-      sl[v][3] = d[7] - d[4];
-      ctr[v] = ub[v];
+      const double* Q = q + (long long)v * g.ps;
+      const double dc = Q[c], dw = Q[cidx(g, i - 1, j)], de = Q[cidx(g, i + 1, j)];
+      const double ds = Q[cidx(g, i, j - 1)], dn = Q[cidx(g, i, j + 1)];
+      ub[v] = dc;
+      for (int k = 0; k < 15; k++) cc[v][k] = w.yrec[(long long)(YREC_CC + 15 * v + k) * g.ps + c];
+      sl[v][0] = dc - dw;
+      sl[v][1] = de - dc;
+      sl[v][2] = dc - ds;
+      sl[v][3] = dn - dc;
+      ctr[v] = dc;
     }
     CharState<double> cs;
     char_state<double>(ub, g.gamma, cs);

@@ -37,6 +37,8 @@ __device__ __forceinline__ long long cidx(const Grid& g, int i, int j) {
   return (long long)(j + NG) * g.pitch + (i + NG);
 }
 
+constexpr int YREC_CC = 144, YREC_GR = 204, YREC_PLANES = 306;
+
 // scratch planes of one spatial-operator evaluation
 struct Work {
   double* face;   // 48 planes: point k (0..11) x (rho, u, v, e), limited
@@ -50,10 +52,13 @@ struct Work {
                   // S1 = sum_g w_g eta_g fhat_g, per conserved variable (12 allocated)
   double* fy;     // y-face above a cell: the same with xi_g
   double* theta;  // 2 planes: limiter factors
-  // 144 planes, only while a step is recorded for the adjoint (else null): per direction
-  // d and field f of the characteristic reconstruction, plane 72 d + 18 f + slot with
-  // slots 0-5 the face values, 6-14 the volume values, 15 the moment (characteristic
-  // variables), 16 beta_0 and 17 1/S' of the nonlinear weights
+  // YREC_PLANES planes, only while a step is recorded for the adjoint (else null):
+  //   72 d + 18 f + slot  per direction d and field f of the characteristic
+  //       reconstruction: slots 0-5 the face values, 6-14 the volume values, 15 the
+  //       moment (characteristic variables), 16 beta_0 and 17 1/S' of the weights;
+  //   YREC_CC + 15 v + k  the p0 coefficients of conserved variable v;
+  //   YREC_GR + 17 m + k  gradient component m: k < 15 its p0 coefficients, 15 beta_0,
+  //       16 1/S'
   double* yrec = nullptr;
 };
 

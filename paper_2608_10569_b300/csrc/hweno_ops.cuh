@@ -43,6 +43,10 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
 #pragma unroll
       for (int k = 0; k < 17; k++) dt[k] = (T)d[k];
       hw_p0_coeffs<T>(dt, cc[v]);
+      if constexpr (REC) {
+#pragma unroll
+        for (int k = 0; k < 15; k++) w.yrec[(long long)(YREC_CC + 15 * v + k) * g.ps + c] = cc[v][k];
+      }
       sl[v][0] = (T)(d[4] - d[3]);
       sl[v][1] = (T)(d[5] - d[4]);
       sl[v][2] = (T)(d[4] - d[1]);
@@ -186,7 +190,9 @@ __device__ __forceinline__ void weak_moments_body(const Grid& g, const Work& w, 
 // gradient reconstruction (Eq. (3.9)): the scalar HWENO of Appendix A.2 applied to
 // the weak-derivative moments of each of u, v, e in each direction, on cells of the
 // interior grown by 1; values at the 12 face and 9 volume points
-template <class T>
+// REC (FP64 only): also write each component's p0 coefficients and weight factors
+// (Work::yrec)
+template <class T, bool REC = false>
 __device__ __forceinline__ void grad_body(const Grid& g, const Work& w, int gx, int gy) {
   const int i = gx - 1;
   const int j = gy - 1;
@@ -216,7 +222,19 @@ __device__ __forceinline__ void grad_body(const Grid& g, const Work& w, int gx, 
     d[15] = (T)Y[cidx(g, i - 1, j)];
     d[16] = (T)Y[cidx(g, i + 1, j)];
     T C[15];
-    hweno_combine<T>(d, eps, C);
+    if constexpr (REC) {
+      T c0[15], wr[2];
+      hw_p0_coeffs<T>(d, c0);
+      const T s[4] = {d[4] - d[3], d[5] - d[4], d[4] - d[1], d[7] - d[4]};
+      hweno_combine_coeffs<T, true>(c0, s, d[4], eps, C, wr);
+      double* y = w.yrec + (long long)(YREC_GR + 17 * comp) * g.ps + c;
+#pragma unroll
+      for (int k = 0; k < 15; k++) y[(long long)k * g.ps] = c0[k];
+      y[(long long)15 * g.ps] = wr[0];
+      y[(long long)16 * g.ps] = wr[1];
+    } else {
+      hweno_combine<T>(d, eps, C);
+    }
     T vx[6], vy[6], vv[9];
     eval_xfaces<T>(C, vx);
     eval_yfaces<T>(C, vy);

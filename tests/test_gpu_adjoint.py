@@ -1,7 +1,7 @@
-"""Discrete adjoint of the FP64 SSP-RK3 step: vector-Jacobian products against central
-finite differences of the forward step (the GPU's and the oracle's), the derivative
-with respect to mu = 1/Re, and a checkpointed multi-step rollout through
-torch.autograd.
+"""Discrete adjoint of the FP64 SSP-RK3 step: vector-Jacobian products against the
+oracle's forward-mode (dual-number) tangents by dot products, against central finite
+differences of the GPU forward step, the derivative with respect to mu = 1/Re, and
+checkpointed or recorded multi-step rollouts (torch.autograd, record/replay).
 
 The nonlinear weights make the step strongly curved (epsilon_WENO = 1e-8 sets the scale
 of their second derivatives), so plain central differences carry an O(h^2) error with a
@@ -99,21 +99,82 @@ def test_viscosity_derivative_matches_central_differences():
     assert abs(mub - fd) <= 1e-6 * abs(fd), (mub, fd)
 
 
-def test_step_vjp_against_the_oracle_step():
-    """dot-product test with the independent CPU implementation: <lam, J v> by central
-    differences of the oracle's step equals <J^T lam, v> from the GPU adjoint"""
-    case, q = I.random_smooth(16, 16, seed=35, bc=("noslip", "noslip", "noslip", "symmetry"))
-    rng = np.random.default_rng(7)
+ORACLE_CASES = {
+    "walls": lambda: I.random_smooth(16, 16, seed=35, bc=("noslip", "noslip", "noslip", "symmetry")),
+    "periodic_tg": lambda: I.taylor_green(16, 0.5, 300.0, 1 / (1.4 * 0.09), rho_pert=1e-3, seed=36),
+}
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(a), abs(b))
+
+
+@pytest.mark.parametrize("name", sorted(ORACLE_CASES))
+def test_residual_vjp_dot_product_with_the_dual_oracle(name):
+    """<(rbar, mbar), J (v, dmu)> from the oracle's forward-mode tangent equals
+    <xbar, v> + mubar dmu from the GPU adjoint of the residual, to 1e-10"""
+    case, q = ORACLE_CASES[name]()
+    rng = np.random.default_rng(71)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    rbar = rng.normal(size=q.shape)
+    mbar = rng.normal(size=(8,) + q.shape[1:])
+    s = hweno.Solver(case.params())
+    s.adjoint_init()
+    xbar, mub = s.adjoint_residual(q.copy(), rbar, mbar)
+    s.close()
+    cfg = O.make_cfg(**case.params())
+    t = O.residual_jvp(cfg, q, v)
+    tm = O.residual_jvp(cfg, q, None, dmu=1.0)
+    lhs = (rbar * t["rhs_dot"]).sum() + (mbar * t["vhat_dot"]).sum()
+    assert _rel(lhs, (xbar * v).sum()) <= 1e-10
+    lhs_mu = (rbar * tm["rhs_dot"]).sum() + (mbar * tm["vhat_dot"]).sum()
+    assert _rel(lhs_mu, mub) <= 1e-10
+
+
+@pytest.mark.parametrize("name", sorted(ORACLE_CASES))
+def test_step_vjp_dot_product_with_the_dual_oracle(name):
+    """one SSP-RK3 step at fixed dt: <lam', J v> and <lam', dq/dmu> from the oracle's
+    forward-mode tangent against <J^T lam', v> and mubar from the GPU, to 1e-10"""
+    case, q = ORACLE_CASES[name]()
+    rng = np.random.default_rng(72)
     dt = 1e-3
     lam_next = rng.normal(size=q.shape)
     v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
     s = hweno.Solver(case.params())
     s.adjoint_init()
-    lam, _ = s.adjoint_step(q.copy(), dt, lam_next, np.zeros_like(q))
+    lam, mub = s.adjoint_step(q.copy(), dt, lam_next, np.zeros_like(q))
     s.close()
     cfg = O.make_cfg(**case.params())
-    fd = richardson(lambda e: (O.step(cfg, q + e * v, dt_fixed=dt)[0] * lam_next).sum(), 2e-6)
-    assert abs((lam * v).sum() - fd) <= 1e-6 * abs(fd)
+    _, t, st = O.step_jvp(cfg, q, v, dt)
+    assert st["status"] == 0 and st["rejections"] == 0
+    assert _rel((lam_next * t).sum(), (lam * v).sum()) <= 1e-10
+    _, tm, _ = O.step_jvp(cfg, q, np.zeros_like(q), dt, dmu=1.0)
+    assert _rel((lam_next * tm).sum(), mub) <= 1e-10
+
+
+def test_recorded_rollout_dot_product_with_the_dual_oracle():
+    """five recorded steps under the step rule, reversed by hweno_adjoint_replay, against
+    the oracle's tangent through the same five steps (the GPU's step sizes), to 1e-10"""
+    case, q = ORACLE_CASES["walls"]()
+    rng = np.random.default_rng(73)
+    lam_T = rng.normal(size=q.shape)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    s = hweno.Solver(case.params())
+    s.set_state(q.copy())
+    s.adjoint_init()
+    s.adjoint_reserve(5)
+    s.adjoint_record(True)
+    dts = [s.step()[0] for _ in range(5)]
+    s.adjoint_record(False)
+    lam0, mub = s.adjoint_replay(lam_T.copy(), np.zeros_like(q))
+    s.close()
+    cfg = O.make_cfg(**case.params())
+    qa, ta, qb, tb = q.copy(), v.copy(), q.copy(), np.zeros_like(q)
+    for dt in dts:
+        qa, ta, _ = O.step_jvp(cfg, qa, ta, dt)
+        qb, tb, _ = O.step_jvp(cfg, qb, tb, dt, dmu=1.0)
+    assert _rel((lam_T * ta).sum(), (lam0 * v).sum()) <= 1e-10
+    assert _rel((lam_T * tb).sum(), mub) <= 1e-10
 
 
 def test_checkpointed_rollout_gradient():
