@@ -195,6 +195,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def mixed_error(params, q, nsteps=10):
+    """Relative L1 and L-infinity error of the mixed path's density against the FP64
+    path after nsteps steps from q, both at the FP64 path's step sizes."""
+    import torch
+    from paper_2608_10569_b300 import hweno
+    s64 = hweno.Solver(params, precision="fp64")
+    s32 = hweno.Solver(params, precision="mixed")
+    s64.set_state(torch.from_numpy(q).cuda())
+    s32.set_state(torch.from_numpy(q).cuda())
+    try:
+        for _ in range(nsteps):
+            dt, _ = s64.step()
+            s32.step(dt)
+        r64, r32 = s64.get_state()[0], s32.get_state()[0]
+        d = (r32 - r64).abs()
+        return {"rel_l1_rho_vs_fp64": float(d.sum() / r64.abs().sum()),
+                "rel_linf_rho_vs_fp64": float(d.max() / r64.abs().max()), "steps": nsteps}
+    except hweno.HwenoError as e:
+        return {"error": str(e)}
+    finally:
+        s64.close()
+        s32.close()
+
+
 def run_ensemble(args):
     """64 periodic Taylor-Green cases (sides 128..1024, Re 1e2..1e4), mixed precision,
     advanced together by the batched solver: one graph replay per SSP-RK3 step."""
@@ -219,16 +243,29 @@ def run_ensemble(args):
     stream.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    launches = b.launch_count() - n0
     pp = sum(v.diag()["pp_active"] for v in b.cases)
+    b.close()
+    # the batched mixed path equals single mixed solvers bit for bit (tested), so one
+    # case of each side states the ensemble's error against FP64
+    acc, seen = [], set()
+    for case, q in ens:
+        if case.nx not in seen:
+            seen.add(case.nx)
+            acc.append(dict(mixed_error(case.params(), q), side=case.nx))
+    errs = [a for a in acc if "error" not in a]
     line = {"metric": METRIC, "value": cells * 3.0 * args.steps / (ms * 1e-3) / 1e9, "unit": METRIC,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": {"workload": "ensemble of 64 periodic Taylor-Green cases, sides 128-1024, "
                                    "Re 1e2-1e4, batched (one graph per step)", "cells": cells,
                        "autotuned_shapes": chosen, "rejected_case_steps": rej},
-            "gpu_launches": b.launch_count() - n0, "clocks": clk,
-            "pp_active_cell_stages": pp}
-    b.close()
+            "gpu_launches": launches, "clocks": clk,
+            "pp_active_cell_stages": pp,
+            "accuracy": {"rel_l1_rho_vs_fp64": max(a["rel_l1_rho_vs_fp64"] for a in errs) if errs else None,
+                         "rel_linf_rho_vs_fp64": max(a["rel_linf_rho_vs_fp64"] for a in errs) if errs else None,
+                         "sample": "one case of each side, mixed vs FP64 over 10 steps at the FP64 step sizes",
+                         "cases": acc}}
     print(json.dumps(line), flush=True)
 
 
@@ -332,6 +369,8 @@ def run_single(args):
         except hweno.HwenoError as e:
             out[prec] = {"error": str(e)}
         s.close()
+    if "error" not in out.get("mixed", {}) and args.workload != "colliding_streams":
+        out["mixed"]["accuracy"] = mixed_error(case.params(), q)
     line = {"metric": METRIC, "unit": METRIC, "workload": args.workload, "cells": cells,
             "steps": args.steps, "warmup": args.warmup, "results": out}
     print(json.dumps(line), flush=True)

@@ -188,11 +188,13 @@ long long hweno_launch_count(const hweno_handle* h);
  * Lax-Friedrichs coefficient is differentiated through the state that attains it),
  * the ghost cells, and the modified moments that re-enter every stage.  The time step
  * is frozen (a given dt), as a checkpointed rollout records it.  The positivity limiter
- * is differentiated only where it is inactive (theta = 1); a step in which it acts is
- * rejected with HWENO_ERR_ARG.  The paper has no adjoint; the derivatives are those of
- * its discrete scheme. */
+ * is differentiated on the branch it took: its density factor through the point of
+ * minimum density, its pressure factor through the smallest root of the pressure
+ * quadratic (implicit-function theorem), and eps = min(eps_PP, rho_bar, p_bar) through
+ * the term that set it.  The paper has no adjoint; the derivatives are those of its
+ * discrete scheme. */
 
-/* Allocate the adjoint buffers (about 3.8 KB per padded cell); FP64 handles only. */
+/* Allocate the adjoint buffers (about 6.3 KB per padded cell); FP64 handles only. */
 int hweno_adjoint_init(hweno_handle* h);
 
 /* xbar = (dR/dx)^T rbar + (dM/dx)^T mbar and *mubar = d<rbar, R>/dmu + d<mbar, M>/dmu
@@ -202,9 +204,9 @@ int hweno_adjoint_init(hweno_handle* h);
 int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar, const double* mbar, double* xbar,
                            double* mubar, int on_device);
 
-/* Storage for hweno_adjoint_segment: the three stage states of up to max_steps steps
- * and, with keep_intermediates, the forward intermediates of every stage (about 2 KB
- * per padded cell and stage), so that the reverse recomputes nothing.  When those do
+/* Storage for hweno_adjoint_segment and recording: the three stage states of up to
+ * max_steps steps and, with keep_intermediates, the forward intermediates the reverse
+ * reads (about 4.3 KB per padded cell and stage), so that the reverse recomputes nothing.  When those do
  * not fit in 80 % of the free device memory only the states are kept and every stage is
  * re-evaluated during the reverse.  Returns 1 if intermediates are kept, 0 if not. */
 int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_intermediates);
@@ -219,16 +221,15 @@ int hweno_adjoint_record(hweno_handle* h, int on);
 /* The adjoint through the recorded steps, last to first, with their step sizes held
  * fixed: lam_start = (d q^{end} / d q^{first})^T lam_end, *mubar (may be NULL) = the
  * mu = 1/Re derivative of <lam_end, q^{end}>.  Buffers [3][4][ny][nx], host or device per
- * on_device.  Errors: HWENO_ERR_STATE with nothing recorded, HWENO_ERR_ARG if the
- * positivity limiter acts in a recorded stage.  Ends recording; the handle's state is
- * unchanged. */
+ * on_device.  Errors: HWENO_ERR_STATE with nothing recorded.  Ends recording; the
+ * handle's state is unchanged. */
 int hweno_adjoint_replay(hweno_handle* h, const double* lam_end, double* lam_start, double* mubar, int on_device);
 
 /* The adjoint through a checkpoint segment: recompute the nsteps steps from q_start with
  * the step sizes dts[0..nsteps-1] (host array), keeping their stage states (and
  * intermediates), then the reverse sweep of hweno_adjoint_replay over them.  Errors:
- * HWENO_ERR_STATE without enough reserved storage, HWENO_ERR_ARG if the limiter acts,
- * HWENO_ERR_INADMISSIBLE if a stage is inadmissible at the given steps.  Replaces any
+ * HWENO_ERR_STATE without enough reserved storage, HWENO_ERR_INADMISSIBLE if a stage is
+ * inadmissible at the given steps.  Replaces any
  * recording and leaves the handle without a state (call hweno_set_state before stepping
  * again). */
 int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int nsteps, const double* dts,
@@ -238,8 +239,8 @@ int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int nsteps, co
  * *mubar = (d q^{n+1} / d mu)^T lam_next with mu = 1/Re (the viscosity).  q: the state
  * q^n, lam_next and lam: adjoint states, all [3][4][ny][nx]; on_device as elsewhere.
  * The step's stage states are recomputed from q^n.  Replaces the handle's state with
- * q^n.  Errors: HWENO_ERR_STATE before hweno_adjoint_init, HWENO_ERR_ARG if the limiter
- * acts, HWENO_ERR_INADMISSIBLE if a stage of the forward step is inadmissible. */
+ * q^n.  Errors: HWENO_ERR_STATE before hweno_adjoint_init, HWENO_ERR_INADMISSIBLE if a
+ * stage of the forward step is inadmissible. */
 int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double* lam_next, double* lam,
                        double* mubar, int on_device);
 

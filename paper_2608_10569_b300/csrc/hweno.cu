@@ -951,13 +951,7 @@ static int adjoint_finish(hweno_handle* h, double* lam_start, double* mubar, int
   CK(cudaMemcpyAsync(h->h_red, h->adj.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   memcpy(hm, h->h_red, sizeof(hm));
-  unsigned int fl;
-  memcpy(&fl, &hm[1], sizeof(fl));
-  if (fl & FLAG_ADJ_LIMITER) {
-    char msg[160];
-    snprintf(msg, sizeof(msg), "%s: the positivity limiter acts in a stage (its adjoint is not implemented)", who);
-    return fail(h, HWENO_ERR_ARG, msg);
-  }
+  (void)who;
   if (mubar) *mubar = hm[0];
   return HWENO_OK;
 }
@@ -1020,8 +1014,6 @@ extern "C" int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int
   }
   if (rc) return rc;
   if ((rc = read_diag(h))) return rc;
-  if (h->h_diag->pp_count)
-    return fail(h, HWENO_ERR_ARG, "hweno_adjoint_segment: the positivity limiter is active in this segment (its adjoint is not implemented)");
   if (h->h_diag->flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE))
     return fail(h, HWENO_ERR_INADMISSIBLE, "hweno_adjoint_segment: a forward stage is inadmissible at the given steps");
   h->rec_count = nsteps;
@@ -1059,9 +1051,6 @@ int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar,
   CK(cudaMemcpyAsync(h->h_red, a.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   memcpy(hm, h->h_red, sizeof(hm));
-  unsigned int fl;
-  memcpy(&fl, &hm[1], sizeof(fl));
-  if (fl & FLAG_ADJ_LIMITER) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_residual: limiter active");
   if (mubar) *mubar = hm[0];
   return HWENO_OK;
 }
@@ -1088,7 +1077,6 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
   if ((rc = residual_eval(h, h->QS, h->RHS, h->MOM))) return rc;
   if ((rc = launch_rk(h, 2, h->QS, h->MOM, h->RHS, h->QS))) return rc;
   if ((rc = read_diag(h))) return rc;
-  if (h->h_diag->pp_count) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_step: the positivity limiter is active in this step (its adjoint is not implemented)");
   if (h->h_diag->flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE)) return fail(h, HWENO_ERR_INADMISSIBLE, "hweno_adjoint_step: the forward step is inadmissible at this dt");
   CK(cudaMemsetAsync(a.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
   const dim3 gi = grid2(g.nx, g.ny), blk(BX, BY);
@@ -1117,9 +1105,6 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
   CK(cudaMemcpyAsync(h->h_red, a.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   memcpy(hm, h->h_red, sizeof(hm));
-  unsigned int fl;
-  memcpy(&fl, &hm[1], sizeof(fl));
-  if (fl & FLAG_ADJ_LIMITER) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_step: limiter active in a stage");
   if (mubar) *mubar = hm[0];
   return HWENO_OK;
 }

@@ -13,14 +13,14 @@
 // per stencil slot and a gather kernel sums them in a fixed order (deterministic, no
 // atomics).  Branches are differentiated on the side the forward took: |x| by sign(x),
 // max() by its argument (the Lax-Friedrichs coefficient goes to the state that set it).
-// The positivity limiter is differentiated on its inactive branch (theta = 1); a cell
-// whose limiter is active sets FLAG_ADJ_LIMITER and the host reports an error.
+// The positivity limiter is differentiated on the branch the forward took: through its
+// density factor, the argmin point of its minimum density, the argmin point of its
+// smallest pressure root (implicit-function theorem on the pressure quadratic) and the
+// term that set eps.
 #pragma once
 #include "hweno_ops.cuh"
 
 namespace hw {
-
-enum { FLAG_ADJ_LIMITER = 8u };
 
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
@@ -396,6 +396,105 @@ __device__ __forceinline__ void char_sums_finish(const CharState<double>& s, con
   else { sb.v += unb; sb.u += utb; }
 }
 
+// adjoint of pp_limit in a cell where it acted (thr < 1 or thp < 1).  ub: the cell
+// average; fu, vu: the unlimited face and volume values (conserved); thr, thp: the
+// forward's factors.  Given Fb, the adjoint of the limited face values, writes fb, the
+// adjoint of the unlimited face values, and accumulates vb (volume values) and ubb
+// (average).  Ties go to the first point, as in the forward's strict comparisons.
+__device__ void pp_limit_T(const double* ub, const double (*fu)[4], const double (*vu)[4], double gamma,
+                           double eps_pp, double thr, double thp, const double (*Fb)[4], double (*fb)[4],
+                           double (*vb)[4], double* ubb) {
+  const double gm1 = gamma - 1.0;
+  const double pb = pressure(ub, gamma);
+  // eps = min(eps_pp, rho_bar, p_bar) and the term that set it
+  double eps = eps_pp;
+  int esrc = 0;
+  if (ub[0] < eps) { eps = ub[0]; esrc = 1; }
+  if (pb < eps) { eps = pb; esrc = 2; }
+  // the face map: f~0 = ub0 + thp thr (f0 - ub0), f~v = ubv + thp (fv - ubv)
+  const double A = thp * thr;
+  double thpb = 0.0, thrb = 0.0, epsb = 0.0;
+  for (int k = 0; k < 12; k++) {
+    const double d0 = fu[k][0] - ub[0];
+    fb[k][0] = A * Fb[k][0];
+    ubb[0] += (1.0 - A) * Fb[k][0];
+    thpb += thr * d0 * Fb[k][0];
+    thrb += thp * d0 * Fb[k][0];
+    for (int v = 1; v < 4; v++) {
+      fb[k][v] = thp * Fb[k][v];
+      ubb[v] += (1.0 - thp) * Fb[k][v];
+      thpb += (fu[k][v] - ub[v]) * Fb[k][v];
+    }
+  }
+  // pressure factor: the smallest root t* over the points below eps, with the density
+  // already rescaled; P(t) = U3 U0 - |U12|^2/2 - e1 U0 at U = ub + t (w - ub)
+  if (thp < 1.0) {
+    int ks = -1;
+    double tmin = 1.0;
+    for (int k = 0; k < 21; k++) {
+      const double* sp = k < 12 ? fu[k] : vu[k - 12];
+      const double wv[4] = {ub[0] + thr * (sp[0] - ub[0]), sp[1], sp[2], sp[3]};
+      const double lhs = gm1 * (wv[3] * wv[0] - 0.5 * (wv[1] * wv[1] + wv[2] * wv[2]));
+      if (lhs < eps * wv[0]) {
+        const double t = theta_root(ub, wv, eps, gamma);
+        if (t < tmin) { tmin = t; ks = k; }
+      }
+    }
+    if (ks >= 0 && tmin > 0.0 && tmin < 1.0) {
+      const double* sp = ks < 12 ? fu[ks] : vu[ks - 12];
+      const double wv[4] = {ub[0] + thr * (sp[0] - ub[0]), sp[1], sp[2], sp[3]};
+      const double e1 = eps / gm1;
+      double U[4], dP[4], dPdt = 0.0;
+      for (int v = 0; v < 4; v++) U[v] = ub[v] + tmin * (wv[v] - ub[v]);
+      dP[0] = U[3] - e1;
+      dP[1] = -U[1];
+      dP[2] = -U[2];
+      dP[3] = U[0];
+      for (int v = 0; v < 4; v++) dPdt += dP[v] * (wv[v] - ub[v]);
+      const double G = -thpb / dPdt;
+      double wb[4];
+      for (int v = 0; v < 4; v++) {
+        ubb[v] += G * (1.0 - tmin) * dP[v];
+        wb[v] = G * tmin * dP[v];
+      }
+      epsb += -G * U[0] / gm1;
+      // w0 = ub0 + thr (s0 - ub0)
+      ubb[0] += (1.0 - thr) * wb[0];
+      thrb += (sp[0] - ub[0]) * wb[0];
+      double* sb = ks < 12 ? fb[ks] : vb[ks - 12];
+      sb[0] += thr * wb[0];
+      for (int v = 1; v < 4; v++) sb[v] += wb[v];
+    }
+  }
+  // density factor thr = (ub0 - eps) / (ub0 - rmin) at the point of minimum density
+  if (thr < 1.0) {
+    int km = -1;
+    double rmin = ub[0];
+    for (int k = 0; k < 12; k++)
+      if (fu[k][0] < rmin) { rmin = fu[k][0]; km = k; }
+    for (int k = 0; k < 9; k++)
+      if (vu[k][0] < rmin) { rmin = vu[k][0]; km = 12 + k; }
+    if (km >= 0) {
+      const double D = ub[0] - rmin;
+      ubb[0] += thrb * (eps - rmin) / (D * D);
+      epsb += -thrb / D;
+      const double rb = thrb * (ub[0] - eps) / (D * D);
+      if (km < 12) fb[km][0] += rb;
+      else vb[km - 12][0] += rb;
+    }
+  }
+  // eps = min(eps_pp, rho_bar, p_bar)
+  if (esrc == 1) {
+    ubb[0] += epsb;
+  } else if (esrc == 2) {
+    const double u = ub[1] / ub[0], v = ub[2] / ub[0];
+    ubb[0] += epsb * gm1 * 0.5 * (u * u + v * v);
+    ubb[1] -= epsb * gm1 * u;
+    ubb[2] -= epsb * gm1 * v;
+    ubb[3] += epsb * gm1;
+  }
+}
+
 // adjoint of char_state: accumulate ubar
 __device__ __forceinline__ void char_state_T(const double* ub, double gamma, const CharBar& sb, double* ubb) {
   const double rr = 1.0 / ub[0];
@@ -686,7 +785,6 @@ __global__ void ka_face_moments(Grid g, Adj a) {
 __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict__ q, Work w, Adj a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x - 3;
   const int j = blockIdx.y * blockDim.y + threadIdx.y - 3;
-  unsigned int flags = 0;
   if (i < g.nx + 3 && j < g.ny + 3) {
     const long long c = cidx(g, i, j);
     // p0 coefficients as the forward wrote them; the slopes from the 5-point stencil
@@ -707,9 +805,7 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
     char_state<double>(ub, g.gamma, cs);
     const double eps = g.eps_weno;
     // adjoints of the conserved point values, from the stored primitive point values
-    // (the limiter is inactive wherever the adjoint is defined: theta = 1 leaves the
-    // traces unchanged)
-    if (w.theta[c] < 1.0 || w.theta[g.ps + c] < 1.0) flags |= FLAG_ADJ_LIMITER;
+    // (the face values are the limited ones)
     double fb[12][4], vb[9][4];
     for (int k = 0; k < 12; k++) {
       double wbp[4], wp[4];
@@ -740,6 +836,31 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
         for (int v = 0; v < 4; v++) wp[v] = w.vol[(long long)(4 * k + v) * g.ps + c];
         prim_T_w(wp, wbp, vb[k]);
       }
+    // where the limiter acted: from the limited to the unlimited face values, whose
+    // conserved form is R y of the recorded characteristic values (as the forward
+    // formed them); the volume values are unlimited
+    double ubl[4] = {0, 0, 0, 0};
+    const double thr = w.theta[c], thp = w.theta[g.ps + c];
+    if (thr < 1.0 || thp < 1.0) {
+      double fu[12][4], vu[9][4], Fb[12][4];
+      for (int dir = 0; dir < 2; dir++)
+        for (int k = 0; k < 6; k++) {
+          double y[4];
+          for (int f = 0; f < 4; f++) y[f] = w.yrec[(long long)(72 * dir + 18 * f + k) * g.ps + c];
+          if (dir == 0) from_char<double, 0>(cs, y, fu[k]); else from_char<double, 1>(cs, y, fu[6 + k]);
+        }
+      for (int k = 0; k < 9; k++) {
+        const double r = w.vol[(long long)(4 * k) * g.ps + c], u = w.vol[(long long)(4 * k + 1) * g.ps + c];
+        const double v = w.vol[(long long)(4 * k + 2) * g.ps + c], e = w.vol[(long long)(4 * k + 3) * g.ps + c];
+        vu[k][0] = r;
+        vu[k][1] = r * u;
+        vu[k][2] = r * v;
+        vu[k][3] = r * (e + 0.5 * (u * u + v * v));
+      }
+      for (int k = 0; k < 12; k++)
+        for (int v = 0; v < 4; v++) Fb[k][v] = fb[k][v];
+      pp_limit_T(ub, fu, vu, g.gamma, g.eps_pp, thr, thp, Fb, fb, vb, ubl);
+    }
     const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
     double mb[2][4];
     for (int v = 0; v < 4; v++) {
@@ -843,7 +964,7 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
     for (int v = 0; v < 4; v++) {
       double db[17] = {0};
       hw_p0_coeffs_T<double>(ccb[v], db);
-      db[4] += ctrb[v] + ubb[v] + slb[v][0] - slb[v][1] + slb[v][2] - slb[v][3];
+      db[4] += ctrb[v] + ubb[v] + ubl[v] + slb[v][0] - slb[v][1] + slb[v][2] - slb[v][3];
       db[3] -= slb[v][0];
       db[5] += slb[v][1];
       db[1] -= slb[v][2];
@@ -851,8 +972,6 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
       for (int k = 0; k < 17; k++) a.cc[(long long)(17 * v + k) * g.ps + c] = db[k];
     }
   }
-  flags = __reduce_or_sync(0xffffffffu, flags);
-  if (lane_id() == 0 && flags) atomicOr(a.flags, flags);
 }
 
 // state adjoint of every padded cell from ka_cons's contributions

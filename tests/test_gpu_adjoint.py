@@ -152,6 +152,48 @@ def test_step_vjp_dot_product_with_the_dual_oracle(name):
     assert _rel((lam_next * tm).sum(), mub) <= 1e-10
 
 
+LIMITED = {
+    # smooth data with eps_PP raised so that the positivity limiter acts in many cells
+    # while the state stays well conditioned (at the default eps_PP = 1e-12 it acts only
+    # next to vacuum, where two correct implementations agree to few digits)
+    "density_factor": (37, 0.85, 0),
+    "pressure_factor": (35, 0.9, 1),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LIMITED))
+def test_limiter_vjp_dot_products_with_the_dual_oracle(name):
+    """residual and step adjoints where the limiter acts, against the oracle's
+    forward-mode tangents, to 1e-10"""
+    seed, eps_pp, which = LIMITED[name]
+    case, q = I.random_smooth(16, 16, seed=seed, bc=("noslip", "noslip", "noslip", "symmetry"))
+    p = case.params()
+    p["eps_pp"] = eps_pp
+    cfg = O.make_cfg(**p)
+    th = O.residual(cfg, q, dumps=True)["theta"]
+    assert (th[which] < 1).sum() >= 5
+    rng = np.random.default_rng(74)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    rbar = rng.normal(size=q.shape)
+    mbar = rng.normal(size=(8,) + q.shape[1:])
+    s = hweno.Solver(p)
+    s.adjoint_init()
+    xbar, mub = s.adjoint_residual(q.copy(), rbar, mbar)
+    t = O.residual_jvp(cfg, q, v)
+    tm = O.residual_jvp(cfg, q, None, dmu=1.0)
+    assert _rel((rbar * t["rhs_dot"]).sum() + (mbar * t["vhat_dot"]).sum(), (xbar * v).sum()) <= 1e-10
+    assert _rel((rbar * tm["rhs_dot"]).sum() + (mbar * tm["vhat_dot"]).sum(), mub) <= 1e-10
+    dt = 0.25 * O.step(cfg, q)[1]["dt"]
+    lam_next = rng.normal(size=q.shape)
+    lam, mub = s.adjoint_step(q.copy(), dt, lam_next, np.zeros_like(q))
+    s.close()
+    _, ts, st = O.step_jvp(cfg, q, v, dt)
+    assert st["status"] == 0 and st["rejections"] == 0 and st["pp_active"] > 0
+    assert _rel((lam_next * ts).sum(), (lam * v).sum()) <= 1e-10
+    _, tms, _ = O.step_jvp(cfg, q, np.zeros_like(q), dt, dmu=1.0)
+    assert _rel((lam_next * tms).sum(), mub) <= 1e-10
+
+
 def test_recorded_rollout_dot_product_with_the_dual_oracle():
     """five recorded steps under the step rule, reversed by hweno_adjoint_replay, against
     the oracle's tangent through the same five steps (the GPU's step sizes), to 1e-10"""
