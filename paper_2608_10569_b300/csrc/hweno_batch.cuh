@@ -54,6 +54,8 @@ __device__ __forceinline__ void tile_pos(const TileList& L, int c, int t, int& g
     const int c_ = find_case((L).start, ncase, t_);                \
     const CaseDev& cd = cases[c_];                                 \
     if (!cd.active) continue;                                      \
+    const Grid cg = cd.g; /* local copies: the bodies' stores to */ \
+    const Work cw = cd.w; /* the planes cannot alias them */       \
     int gx, gy, gz;                                                \
     tile_pos(L, c_, t_, gx, gy, gz);                               \
     (void)gz;
@@ -66,40 +68,40 @@ __global__ void __launch_bounds__(128) kb_cons(const CaseDev* __restrict__ cases
   HW_BATCH_LOOP(L, ncase)
   const double* q = which == 0 ? cd.Q : cd.QS;
   double* mom = which == 0 ? cd.MOM0 : cd.MOM;
-  if (MIXED) cons_mixed_body(cd.g, q, cd.w, mom, cd.diag, gx, gy);
-  else cons_body<double>(cd.g, q, cd.w, mom, cd.diag, gx, gy);
+  if (MIXED) cons_mixed_body(cg, q, cw, mom, cd.diag, gx, gy);
+  else cons_body<double>(cg, q, cw, mom, cd.diag, gx, gy);
   HW_BATCH_END
 }
 
 template <int MIXED>
 __global__ void kb_face_moments(const CaseDev* __restrict__ cases, TileList L, int ncase) {
   HW_BATCH_LOOP(L, ncase)
-  if (MIXED) face_moments_mixed_body(cd.g, cd.w, gx, gy, gz);
-  else face_moments_body(cd.g, cd.w, gx, gy, gz);
+  if (MIXED) face_moments_mixed_body(cg, cw, gx, gy, gz);
+  else face_moments_body(cg, cw, gx, gy, gz);
   HW_BATCH_END
 }
 
 template <int MIXED>
 __global__ void kb_weak_moments(const CaseDev* __restrict__ cases, TileList L, int ncase) {
   HW_BATCH_LOOP(L, ncase)
-  if (MIXED) weak_moments_mixed_body(cd.g, cd.w, gx, gy);
-  else weak_moments_body(cd.g, cd.w, gx, gy);
+  if (MIXED) weak_moments_mixed_body(cg, cw, gx, gy);
+  else weak_moments_body(cg, cw, gx, gy);
   HW_BATCH_END
 }
 
 template <int MIXED>
 __global__ void __launch_bounds__(128) kb_grad(const CaseDev* __restrict__ cases, TileList L, int ncase) {
   HW_BATCH_LOOP(L, ncase)
-  if (MIXED) grad_mixed_body(cd.g, cd.w, gx, gy);
-  else grad_body<double>(cd.g, cd.w, gx, gy);
+  if (MIXED) grad_mixed_body(cg, cw, gx, gy);
+  else grad_body<double>(cg, cw, gx, gy);
   HW_BATCH_END
 }
 
 template <int MIXED>
 __global__ void __launch_bounds__(128) kb_flux(const CaseDev* __restrict__ cases, TileList L, int ncase) {
   HW_BATCH_LOOP(L, ncase)
-  if (MIXED) flux_mixed_body(cd.g, cd.w, cd.diag, gx, gy, gz);
-  else flux_body<double>(cd.g, cd.w, cd.diag, gx, gy, gz);
+  if (MIXED) flux_mixed_body(cg, cw, cd.diag, gx, gy, gz);
+  else flux_body<double>(cg, cw, cd.diag, gx, gy, gz);
   HW_BATCH_END
 }
 
@@ -108,15 +110,15 @@ __global__ void __launch_bounds__(128) kb_assemble(const CaseDev* __restrict__ c
                                                    int which) {
   HW_BATCH_LOOP(L, ncase)
   double* rhs = which == 0 ? cd.RHS0 : cd.RHS;
-  if (MIXED) assemble_mixed_body(cd.g, cd.w, rhs, cd.diag, gx, gy);
-  else assemble_body<double>(cd.g, cd.w, rhs, cd.diag, gx, gy);
+  if (MIXED) assemble_mixed_body(cg, cw, rhs, cd.diag, gx, gy);
+  else assemble_body<double>(cg, cw, rhs, cd.diag, gx, gy);
   HW_BATCH_END
 }
 
 __global__ void __launch_bounds__(128) kb_rk(const CaseDev* __restrict__ cases, TileList L, int ncase, int stage) {
   HW_BATCH_LOOP(L, ncase)
-  if (stage == 1) rk_body(cd.g, 1, cd.Q, cd.MOM0, cd.RHS0, cd.BASE, cd.QS, cd.diag, gx, gy);
-  else rk_body(cd.g, stage, cd.QS, cd.MOM, cd.RHS, cd.BASE, cd.QS, cd.diag, gx, gy);
+  if (stage == 1) rk_body(cg, 1, cd.Q, cd.MOM0, cd.RHS0, cd.BASE, cd.QS, cd.diag, gx, gy);
+  else rk_body(cg, stage, cd.QS, cd.MOM, cd.RHS, cd.BASE, cd.QS, cd.diag, gx, gy);
   HW_BATCH_END
 }
 
@@ -124,8 +126,8 @@ __global__ void __launch_bounds__(128) kb_rk(const CaseDev* __restrict__ cases, 
 __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int pass) {
   HW_BATCH_LOOP(L, ncase)
   double* q = which == 0 ? cd.Q : cd.QS;
-  if (pass == 0) ghost_x_body(cd.g, q, gx);
-  else ghost_y_body(cd.g, q, gx);
+  if (pass == 0) ghost_x_body(cg, q, gx);
+  else ghost_y_body(cg, q, gx);
   HW_BATCH_END
 }
 
@@ -133,9 +135,9 @@ __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncas
 __global__ void kb_split(const CaseDev* __restrict__ cases, TileList L, int ncase, int which) {
   HW_BATCH_LOOP(L, ncase)
   const double* q = which == 0 ? cd.Q : cd.QS;
-  const long long n = 12 * cd.g.ps;
+  const long long n = 12 * cg.ps;
   if (gx < n) {
-    float* hilo = mixed_planes(cd.w, cd.g.ps).hilo;
+    float* hilo = mixed_planes(cw, cg.ps).hilo;
     float hi, lo;
     split_hilo(q[gx], hi, lo);
     hilo[gx] = hi;
