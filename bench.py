@@ -33,6 +33,8 @@ import time
 
 import numpy as np
 
+HERE = os.path.dirname(os.path.abspath(__file__))
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -150,16 +152,54 @@ def max_over_ranks(ws, x):
 
 
 def oracle_step_rate(case, q, steps=1):
-    """FP64 CPU oracle: cell-stages per second over `steps` SSP-RK3 steps."""
+    """FP64 CPU oracle: cell-stages per second over `steps` SSP-RK3 steps, the elapsed
+    time, the final state and the step sizes taken."""
     from oracle import oracle as O
     cfg = O.make_cfg(**case.params())
     O.build()
     t0 = time.perf_counter()
-    qq = q
+    qq, dts = q, []
     for _ in range(steps):
         qq, st = O.step(cfg, qq)
+        dts.append(st["dt"])
     el = time.perf_counter() - t0
-    return case.nx * case.ny * 3.0 * steps / el, el
+    return case.nx * case.ny * 3.0 * steps / el, el, qq, dts
+
+
+def oracle_single_thread(nx=256, ny=128):
+    """The oracle on one host thread (a child process with OMP_NUM_THREADS=1): one
+    SSP-RK3 step of the shock tube at nx x ny, in Gcell-RK-stage/s."""
+    code = ("import json, sys; sys.path.insert(0, %r)\n"
+            "from paper_2608_10569_b300 import inputs as I\n"
+            "import bench\n"
+            "case, q = I.shock_tube(%d, %d)\n"
+            "rate, el, _, _ = bench.oracle_step_rate(case, q)\n"
+            "print(json.dumps({'value': rate / 1e9, 'seconds': el}))\n" % (HERE, nx, ny))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal: the baseline is context
+        return {"error": str(e)[:200]}
+    return {"value": r["value"], "unit": METRIC, "cores": 1,
+            "sample": "one SSP-RK3 step of the %dx%d shock tube, %.1f s" % (nx, ny, r["seconds"])}
+
+
+def state_errors(q, ref, gamma):
+    """Errors of q against ref: relative L1 and L-infinity of the density average plane,
+    and the worst plane, every plane (average and moments) of a conserved variable
+    measured against that variable's scale in ref (max rho; max(|rho u|, |rho v|,
+    rho c) for both momenta; max E), L1 as the mean absolute error over that scale"""
+    q, ref = np.asarray(q), np.asarray(ref)
+    rho, m, n, E = ref[0], ref[1], ref[2], ref[3]
+    p = (gamma - 1.0) * (E - 0.5 * (m * m + n * n) / rho)
+    mom = max(np.abs(m).max(), np.abs(n).max(), (rho * np.sqrt(np.maximum(gamma * p / rho, 0.0))).max())
+    scale = [np.abs(rho).max(), mom, mom, np.abs(E).max()]
+    d = np.abs(q - ref).reshape(12, -1)
+    l1 = [d[k].mean() / scale[k % 4] for k in range(12)]
+    linf = [d[k].max() / scale[k % 4] for k in range(12)]
+    return {"rel_l1_rho": float(d[0].sum() / np.abs(rho).sum()), "rel_linf_rho": float(d[0].max() / np.abs(rho).max()),
+            "max_plane_l1": float(max(l1)), "max_plane_linf": float(max(linf))}
 
 
 def cpu_threads():
@@ -530,10 +570,20 @@ def main():
 
     # ---- CPU baseline: the oracle on the host cores --------------------------------
     cpu = None
+    parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, el = oracle_step_rate(case, q, steps=1)
+        rate, el, q_or, dts_or = oracle_step_rate(case, q, steps=1)
         cpu = {"value": rate / 1e9, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
-               "sample": "one SSP-RK3 step (3 stages) of the full 1024x512 workload, %.1f s" % el}
+               "sample": "one SSP-RK3 step (3 stages) of the full 1024x512 workload, %.1f s" % el,
+               "single_thread": oracle_single_thread()}
+        # the same step on the GPU, FP64 and mixed, against the oracle's result
+        parity = {"sample": "one SSP-RK3 step of the full 1024x512 workload at the oracle's step size"}
+        for prec in ("fp64", "mixed"):
+            sv = hweno.Solver(case.params(), precision=prec, stream=stream)
+            sv.set_state(qd)
+            sv.step(dts_or[0])
+            parity[prec] = state_errors(sv.get_state().cpu().numpy(), q_or, case.gamma)
+            sv.close()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
@@ -543,7 +593,7 @@ def main():
                            "stages_per_step": 3, "l2": "inputs larger than L2 (~1.5 GB state and scratch per step)",
                            "parallelism": "replicas" if ws > 1 else "single GPU",
                            "t_reached": t_reached, "rejected_steps": rejected},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
+                "roofline": roof, "cpu_baseline": cpu, "parity_vs_oracle": parity, "e2e": e2e, "mixed": mixed,
                 "clocks": clk, "gpu_launches": launches, "kernel_ms": kernel_ms}
         print(json.dumps(line), flush=True)
     if ws > 1:

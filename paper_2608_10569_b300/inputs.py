@@ -100,10 +100,11 @@ def _rng(k):
 # the five benchmark workloads
 
 
-def smooth_periodic(n=64, seed=1):
+def smooth_periodic(n=64, seed=1, noise=1e-3):
     """2D NS on a periodic [0,2]^2 grid: rho = 1 + 0.2 sin(pi (x+y)) plus a seeded
-    uniform cell perturbation of amplitude 1e-3, u = 0.7, v = 0.3, p = 1,
-    gamma 1.4, Pr 0.72, mu = 1e-3 (Re = 1000), CFL 0.5, t_end 0.1."""
+    uniform cell perturbation of amplitude `noise` (1e-3; 0 for the smooth field of
+    convergence studies), u = 0.7, v = 0.3, p = 1, gamma 1.4, Pr 0.72, mu = 1e-3
+    (Re = 1000), CFL 0.5, t_end 0.1."""
     case = Case("smooth_periodic_%d" % n, n, n, 0.0, 2.0, 0.0, 2.0, 1.4, 0.72, 1000.0,
                 cfl=0.5, t_end=0.1)
 
@@ -111,7 +112,7 @@ def smooth_periodic(n=64, seed=1):
         return 1.0 + 0.2 * np.sin(np.pi * (x + y)), 0.7 + 0 * x, 0.3 + 0 * x, 1.0 + 0 * x
 
     q = cell_moments(case, prim)
-    d = _rng(seed).uniform(-1e-3, 1e-3, size=(n, n))
+    d = _rng(seed).uniform(-noise, noise, size=(n, n))
     # add d to the density average keeping u, v, p of the cell fixed
     q[0] += d
     q[1] += 0.7 * d

@@ -194,6 +194,45 @@ def test_limiter_vjp_dot_products_with_the_dual_oracle(name):
     assert _rel((lam_next * tms).sum(), mub) <= 1e-10
 
 
+def test_config5_replica_dot_product_with_the_dual_oracle():
+    """the adjoint Taylor-Green flow (Re 1600, Mach 0.3) on a 64^2 replica: three
+    recorded steps under the step rule against the oracle's forward-mode tangent, for
+    the initial state and for mu, to 1e-10 or ten times the products' own sensitivity
+    to rounding-level changes of the state, whichever is larger"""
+    case, q = I.adjoint_taylor_green(64)
+    rng = np.random.default_rng(75)
+    lam_T = rng.normal(size=q.shape)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    s = hweno.Solver(case.params())
+    s.set_state(q.copy())
+    s.adjoint_init()
+    s.adjoint_reserve(3)
+    s.adjoint_record(True)
+    dts = [s.step()[0] for _ in range(3)]
+    lam0, mub = s.adjoint_replay(lam_T.copy(), np.zeros_like(q))
+    s.close()
+    cfg = O.make_cfg(**case.params())
+
+    def tangents(q0):
+        qa, ta, qb, tb = q0.copy(), v.copy(), q0.copy(), np.zeros_like(q0)
+        for dt in dts:
+            qa, ta, _ = O.step_jvp(cfg, qa, ta, dt)
+            qb, tb, _ = O.step_jvp(cfg, qb, tb, dt, dmu=1.0)
+        return (lam_T * ta).sum(), (lam_T * tb).sum()
+
+    ref_q, ref_mu = tangents(q)
+    # conditioning: how far the oracle's own products move when the state moves by
+    # rounding (2e-16 relative), as the GPU's forward states differ from the oracle's.
+    # The replica's density starts uniform, so smoothness indicators sit near eps_WENO
+    # and the weights' second derivatives amplify rounding to about 1e-9.
+    sens_q, sens_mu = 0.0, 0.0
+    for k in range(2):
+        pq, pmu = tangents(q * (1.0 + 2e-16 * np.random.default_rng(200 + k).normal(size=q.shape)))
+        sens_q, sens_mu = max(sens_q, _rel(pq, ref_q)), max(sens_mu, _rel(pmu, ref_mu))
+    assert _rel(ref_q, (lam0 * v).sum()) <= max(1e-10, 10 * sens_q)
+    assert _rel(ref_mu, mub) <= max(1e-10, 10 * sens_mu)
+
+
 def test_recorded_rollout_dot_product_with_the_dual_oracle():
     """five recorded steps under the step rule, reversed by hweno_adjoint_replay, against
     the oracle's tangent through the same five steps (the GPU's step sizes), to 1e-10"""

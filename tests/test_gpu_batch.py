@@ -95,3 +95,31 @@ def test_batch_restarts_only_the_rejected_case():
         assert np.array_equal(view.get_state(np.zeros_like(q)), ref)
     assert b.cases[0].diag()["rejected"] == rej and b.cases[1].diag()["rejected"] == 0
     b.close()
+
+
+def test_ensemble_case_against_the_oracle_at_full_length():
+    """The 64-case ensemble's first 128^2 case, stepped by the batch for its 100 steps
+    in FP64 and in mixed precision, against the FP64 oracle run at the batch's step
+    sizes: FP64 to 1e-9 relative L1 (the full-run bar), mixed to 1e-6."""
+    case, q = next((c, q) for c, q in I.ensemble(64) if c.nx == 128)
+    out, dts = {}, None
+    for prec in ("fp64", "mixed"):
+        b = hweno.Batch([case.params()], precision=prec, stream=torch.cuda.Stream())
+        b.cases[0].set_state(q)
+        steps = []
+        for _ in range(100):
+            b.step(1)
+            steps.append(b.cases[0].diag()["dt_last"])
+        out[prec] = b.cases[0].get_state(np.zeros_like(q))
+        b.close()
+        if prec == "fp64":
+            dts = steps
+    cfg = O.make_cfg(**case.params())
+    ref = q
+    for dt in dts:
+        ref, st = O.step(cfg, ref, dt_fixed=dt)
+        assert st["status"] == 0 and st["rejections"] == 0
+    for prec, bound in (("fp64", 1e-9), ("mixed", 1e-6)):
+        for k in range(12):
+            err = np.abs(out[prec][k] - ref[k]).sum() / max(np.abs(ref[k]).sum(), np.abs(ref[:4]).sum(axis=(1, 2)).max())
+            assert err <= bound, (prec, k, err)

@@ -345,3 +345,40 @@ def test_mixed_precision_limiter_route_and_intermediates():
     face = gm[0].reshape(12, 4, 36, 40)
     p = (case.gamma - 1) * (face[:, 3] - 0.5 * (face[:, 1] ** 2 + face[:, 2] ** 2) / face[:, 0])
     assert face[:, 0].min() > 0 and p.min() > 0
+
+
+CONVERGENCE = {
+    # a random smooth periodic field (several Fourier modes in every variable): the
+    # rate is fifth order; config 1's flow without its cell noise, a single density
+    # wave at constant velocity and pressure, converges faster still (the leading
+    # error terms cancel for it), so only at least fifth order is asked there
+    "random_smooth": (lambda n: I.random_smooth(n, n, seed=31), 0.02, 4.6, 5.8),
+    "config1_smooth": (lambda n: I.smooth_periodic(n, noise=0.0), 0.05, 4.6, None),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CONVERGENCE))
+def test_self_convergence_is_fifth_order(name):
+    """Advance to t_end on 64^2, 128^2 and 256^2 (the viscous cap of Sec. 5 binds, so
+    dt ~ h^2 and the RK3 error is O(h^6)): the differences between successive grids,
+    fine solutions restricted by averaging 2x2 cells (exact for cell averages), shrink
+    at the fifth-order rate in density, momentum and energy."""
+    gen, t_end, lo, hi = CONVERGENCE[name]
+    sols = {}
+    for n in (64, 128, 256):
+        case, q = gen(n)
+        s = hweno.Solver(case.params())
+        s.set_state(q)
+        t, _ = s.advance(t_end)
+        assert abs(t - t_end) < 1e-12
+        sols[n] = s.get_state(np.zeros_like(q))
+        s.close()
+
+    def restrict(f):
+        return 0.25 * (f[0::2, 0::2] + f[1::2, 0::2] + f[0::2, 1::2] + f[1::2, 1::2])
+
+    for p in (0, 1, 3):
+        e1 = np.abs(sols[64][p] - restrict(sols[128][p])).mean()
+        e2 = np.abs(sols[128][p] - restrict(sols[256][p])).mean()
+        rate = np.log2(e1 / e2)
+        assert rate >= lo and (hi is None or rate <= hi), (p, e1, e2, rate)
