@@ -73,6 +73,10 @@ __global__ void k_dt(Diag* diag, double cfl, double h, double visc_cap, double f
 
 __global__ void k_scale_dt(Diag* diag, double f) { diag->dt *= f; }
 
+// keep the stage-1 maxima, flags and dt of a step in the second slot, so that one
+// read at the end of the step's attempt brings both back
+__global__ void k_stash(Diag* diag) { diag[1] = diag[0]; }
+
 // scatter a contiguous [n][ny][nx] array into padded planes, and back
 __global__ void k_scatter(Grid g, int n, const double* __restrict__ src, double* __restrict__ dst) {
   const long long N = (long long)g.nx * g.ny;
@@ -268,12 +272,12 @@ static void launch_ghost(hweno_handle* h, double* q) {
   {
     Prof p(h, K_GHOST);
     const int n = 8 * g.ny;
-    k_ghost_x<<<(n + 127) / 128, 128, 0, h->st>>>(g, q);
+    k_ghost_x<<<dim3((n + 127) / 128, 12), 128, 0, h->st>>>(g, q);
   }
   {
     Prof p(h, K_GHOST);
     const int n = 8 * (g.nx + 2 * NG);
-    k_ghost_y<<<(n + 127) / 128, 128, 0, h->st>>>(g, q);
+    k_ghost_y<<<dim3((n + 127) / 128, 12), 128, 0, h->st>>>(g, q);
   }
 }
 
@@ -420,6 +424,7 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   g.gamma = c.gamma; g.Pr = c.Pr; g.Re = c.Re;
   g.eps_pp = c.eps_pp; g.eps_weno = c.eps_weno;
   for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
+  g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
 
   const long long N = (long long)c.nx * c.ny;
   // planes: Q 12, QS 12, BASE 12, RHS0 12, RHS 12, MOM0 8, MOM 8, face 48, vol 36,
@@ -443,9 +448,9 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   h->PART = p; p += 6LL * c.ny;
   h->d_red = p;
   e = cudaMemsetAsync(h->pool, 0, (size_t)total * sizeof(double), h->st);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, sizeof(Diag));
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_diag, 0, sizeof(Diag), h->st);
-  if (e == cudaSuccess) e = cudaMallocHost(&h->h_diag, sizeof(Diag));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, 2 * sizeof(Diag));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_diag, 0, 2 * sizeof(Diag), h->st);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_diag, 2 * sizeof(Diag));
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_red, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) {
@@ -507,7 +512,7 @@ static int reset_diag(hweno_handle* h) {
 }
 
 static int read_diag(hweno_handle* h) {
-  CK(cudaMemcpyAsync(h->h_diag, h->d_diag, sizeof(Diag), cudaMemcpyDeviceToHost, h->st), "diag read");
+  CK(cudaMemcpyAsync(h->h_diag, h->d_diag, 2 * sizeof(Diag), cudaMemcpyDeviceToHost, h->st), "diag read");
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   return HWENO_OK;
 }
@@ -621,12 +626,11 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
     Prof p(h, K_RK);
     k_dt<<<1, 1, 0, h->st>>>(h->d_diag, h->cfg.cfl, h_min(h), h->cfg.b_visc * h->cfg.Re * h_min(h) * h_min(h),
                              dt_forced, t_cap);
+    k_stash<<<1, 1, 0, h->st>>>(h->d_diag);
+    h->launches++;
   }
-  if ((rc = read_diag(h))) return rc;
-  const Diag first = *h->h_diag;
-  if (first.flags & FLAG_NONFINITE) return fail(h, HWENO_ERR_NONFINITE, "non-finite residual at t^n");
-  double dt = first.dt;
-  if (!(dt > 0.0) || !isfinite(dt)) return fail(h, HWENO_ERR_NONFINITE, "time step is not positive and finite");
+  // no host round trip until the attempt's stages are queued: the stages read dt on
+  // the device, and the stage-1 flags wait in the second slot
   int rej = 0;
   for (;;) {
     // stage flags and counters of this attempt; keep dt and the stage-1 maxima
@@ -640,7 +644,11 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
     if ((rc = residual_eval(h, q2, h->RHS, h->MOM))) return rc;
     if ((rc = launch_rk(h, 3, q2, h->MOM, h->RHS, h->QS))) return rc;
     if ((rc = read_diag(h))) return rc;
-    const Diag& d = *h->h_diag;
+    const Diag first = h->h_diag[1];
+    const Diag& d = h->h_diag[0];
+    if (first.flags & FLAG_NONFINITE) return fail(h, HWENO_ERR_NONFINITE, "non-finite residual at t^n");
+    const double dt = d.dt;
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(h, HWENO_ERR_NONFINITE, "time step is not positive and finite");
     if (!(d.flags & (FLAG_INADMISSIBLE | FLAG_NONFINITE))) {
       double* tmp = h->Q;
       h->Q = h->QS;
@@ -667,7 +675,6 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
       return fail(h, HWENO_ERR_INADMISSIBLE, "stage inadmissible after max_halvings restarts");
     }
     rej++;
-    dt *= 0.5;
     k_scale_dt<<<1, 1, 0, h->st>>>(h->d_diag, 0.5);
     h->launches++;
   }
@@ -1620,6 +1627,7 @@ extern "C" int hweno_residual_noalloc(const hweno_config* cfg, const double* q, 
   g.gamma = c.gamma; g.Pr = c.Pr; g.Re = c.Re;
   g.eps_pp = c.eps_pp; g.eps_weno = c.eps_weno;
   for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
+  g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
 
   double* base = nullptr;
   if ((rc = noalloc_scratch_address(&base))) return rc;

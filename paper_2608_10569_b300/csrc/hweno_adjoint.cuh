@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(128) ka_assemble(Grid g, Work w, Adj a) {
   double mub = 0.0;
   if (i < g.nx && j < g.ny) {
     const long long c = cidx(g, i, j);
-    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy, rPr = 1.0 / g.Pr, rRe = 1.0 / g.Re;
+    const double rdx = g.rdx, rdy = g.rdy, rPr = g.rPr, rRe = g.rRe;
     double Rb1[4], Rb2[4];
     for (int v = 0; v < 4; v++) {
       Rb1[v] = a.R[(long long)(4 + v) * g.ps + c];
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(128) ka_flux(Grid g, Work w, Adj a) {
     const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
     const bool inL = i >= 0 && j >= 0;
     const bool inR = dir == 0 ? (i + 1 < g.nx) : (j + 1 < g.ny);
-    const double r = dir == 0 ? 1.0 / g.dx : 1.0 / g.dy;
+    const double r = dir == 0 ? g.rdx : g.rdy;
     // S0/S1 seeds: x-face: r0 (-r, +r), r1 (-r/2 both), r2 via S1 (-r, +r);
     //              y-face: r0 (-r, +r), r2 (-r/2 both), r1 via S1 (-r, +r)
     const int kh = dir == 0 ? 1 : 2, ks = dir == 0 ? 2 : 1;
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(128) ka_flux(Grid g, Work w, Adj a) {
       S1b[v] = s1;
     }
     const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
-    const double gam = g.gamma, rPr = 1.0 / g.Pr, rRe = 1.0 / g.Re;
+    const double gam = g.gamma, rPr = g.rPr, rRe = g.rRe;
     double st[2][3][4], gs[2][3][6];
     for (int gp = 0; gp < 3; gp++)
       for (int s = 0; s < 2; s++) {
@@ -755,7 +755,7 @@ __global__ void ka_face_moments(Grid g, Adj a) {
   // weak moments exist for cells of the interior grown by 2
   const bool inL = i >= -2 && j >= -2;
   const bool inR = dir == 0 ? (i + 1 < g.nx + 2) : (j + 1 < g.ny + 2);
-  const double r = dir == 0 ? 1.0 / g.dx : 1.0 / g.dy;
+  const double r = dir == 0 ? g.rdx : g.rdy;
   // x: r0 = (W0+ - W0-) r, r_xi = (W0+ + W0-)/2 r - wbar r, r_eta = (W1+ - W1-) r
   // y: r0 = (W0+ - W0-) r, r_xi = (W1+ - W1-) r, r_eta = (W0+ + W0-)/2 r - wbar r
   const int o0 = dir == 0 ? 0 : 3, oh = dir == 0 ? 1 : 5, o1 = dir == 0 ? 2 : 4;
@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(128) ka_cons(Grid g, const double* __restrict_
     double wbarb[3] = {0.0, 0.0, 0.0};
     if (in2)
       for (int n = 0; n < 3; n++)
-        wbarb[n] = -a.rm[(long long)(6 * n + 1) * g.ps + c] / g.dx - a.rm[(long long)(6 * n + 5) * g.ps + c] / g.dy;
+        wbarb[n] = -a.rm[(long long)(6 * n + 1) * g.ps + c] * g.rdx - a.rm[(long long)(6 * n + 5) * g.ps + c] * g.rdy;
     for (int G = 0; G < 3; G++)
       for (int H = 0; H < 3; H++) {
         const int k = 3 * G + H;

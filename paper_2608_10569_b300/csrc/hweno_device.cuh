@@ -19,6 +19,15 @@ namespace hw {
 
 // three-point Gauss rule on the scaled cell [-1/2, 1/2]
 constexpr double GN = 0.3872983346207416885;   // sqrt(15)/10
+
+// precision-preserving math for the templated bodies: the float forms are the FP32
+// instructions, the double forms the FP64 ones (no promotion of FP32 work to FP64)
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tfabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double tfabs(double x) { return fabs(x); }
+__device__ __forceinline__ float tfmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tfmax(double a, double b) { return fmax(a, b); }
 constexpr double GW_OUT = 5.0 / 18.0;
 constexpr double GW_MID = 4.0 / 9.0;
 // linear weights of Appendix A.2
@@ -50,7 +59,7 @@ __device__ __forceinline__ void hweno_combine_coeffs(const T* c0, const T* s, T 
   const T b0 = hw_beta_quartic<T>(c0);
   const T b1 = sxm + sym, b2 = sxp + sym, b3 = sxm + syp, b4 = sxp + syp;
   const T e1 = b0 - b1, e2 = b0 - b2, e3 = b0 - b3, e4 = b0 - b4;
-  const T ts = T(0.25) * (fabs(e1) + fabs(e2) + fabs(e3) + fabs(e4));
+  const T ts = T(0.25) * (tfabs(e1) + tfabs(e2) + tfabs(e3) + tfabs(e4));
   const T tau = ts * ts;
   // omega_m = gamma_m (1 + tau/D_m) / S with D_m = beta_m + eps.  The combination
   // coefficients of Eq. (3.4) are a0 = omega0/gamma0 and a_m = omega_m - a0 gamma_m.
@@ -223,7 +232,7 @@ __device__ __forceinline__ void char_state(const T* ub, T gamma, CharState<T>& s
   s.hq2 = T(0.5) * (s.u * s.u + s.v * s.v);
   const T p = (gamma - T(1)) * (ub[3] - ub[0] * s.hq2);
   const T c2 = gamma * p * rr;
-  s.c = sqrt(c2);
+  s.c = tsqrt(c2);
   s.H = (ub[3] + p) * rr;
   const T b1 = (gamma - T(1)) / c2;
   s.hb1 = T(0.5) * b1;
@@ -363,7 +372,7 @@ template <class T>
 __device__ __forceinline__ T wave_bound(int dir, const T* w, const T* s, T gamma, T rPr, T rRe) {
   const T rho = w[0], e = w[3];
   const T p = (gamma - T(1)) * rho * e;
-  const T cs = sqrt(gamma * (gamma - T(1)) * e);
+  const T cs = tsqrt(gamma * (gamma - T(1)) * e);
   const T txx = T(4.0 / 3.0) * s[0] - T(2.0 / 3.0) * s[3];
   const T txy = s[1] + s[2];
   const T tyy = T(4.0 / 3.0) * s[3] - T(2.0 / 3.0) * s[0];
@@ -374,9 +383,9 @@ __device__ __forceinline__ T wave_bound(int dir, const T* w, const T* s, T gamma
     un = w[2]; q = gamma * s[5] * rPr * rRe; s1 = txy * rRe; s2 = tyy * rRe - p;
   }
   const T r2e = rho * rho * e;
-  const T pp = fabs(un) + (sqrt(rho * rho * q * q + T(2) * r2e * (s1 * s1 + s2 * s2)) + rho * fabs(q)) /
+  const T pp = tfabs(un) + (tsqrt(rho * rho * q * q + T(2) * r2e * (s1 * s1 + s2 * s2)) + rho * tfabs(q)) /
                               (T(2) * r2e);
-  return fmax(fabs(un) + cs, pp);
+  return tfmax(tfabs(un) + cs, pp);
 }
 
 }  // namespace hw

@@ -31,7 +31,13 @@ struct Grid {
   double gamma, Pr, Re;
   double eps_pp, eps_weno;
   int bc[4];
+  double rdx, rdy, rPr, rRe;  // 1/dx, 1/dy, 1/Pr, 1/Re (correctly rounded, on the host)
 };
+
+// x is neither infinite nor NaN: an exponent-field test in the integer pipe
+__device__ __forceinline__ bool finite_d(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
 
 __device__ __forceinline__ long long cidx(const Grid& g, int i, int j) {
   return (long long)(j + NG) * g.pitch + (i + NG);
@@ -111,7 +117,8 @@ __device__ __forceinline__ double bc_sign(int bc, int normal_dir, int v) {
   return (v == 1 + normal_dir) ? -1.0 : 1.0;  // symmetry/slip: normal momentum odd
 }
 
-__device__ __forceinline__ void ghost_x_body(const Grid& g, double* q, int t) {
+// planes [p0, p1) of the state (plane 4 m + v: moment m of variable v)
+__device__ __forceinline__ void ghost_x_body(const Grid& g, double* q, int t, int p0 = 0, int p1 = 12) {
   // t over 8 ghost columns x ny rows
   if (t >= 8 * g.ny) return;
   const int j = t / 8, c = t % 8;
@@ -122,17 +129,15 @@ __device__ __forceinline__ void ghost_x_body(const Grid& g, double* q, int t) {
   if (bc == 0) src = side == 0 ? ((i % g.nx) + g.nx) % g.nx : i % g.nx;
   else src = side == 0 ? -1 - i : 2 * g.nx - 1 - i;
   const long long d = cidx(g, i, j), s = cidx(g, src, j);
-#pragma unroll
-  for (int m = 0; m < 3; m++)
-#pragma unroll
-    for (int v = 0; v < 4; v++) {
-      double sg = 1.0;
-      if (bc != 0) sg = bc_sign(bc, 0, v) * (m == 1 ? -1.0 : 1.0);
-      q[(4 * m + v) * g.ps + d] = sg * q[(4 * m + v) * g.ps + s];
-    }
+  for (int p = p0; p < p1; p++) {
+    const int m = p >> 2, v = p & 3;
+    double sg = 1.0;
+    if (bc != 0) sg = bc_sign(bc, 0, v) * (m == 1 ? -1.0 : 1.0);
+    q[p * g.ps + d] = sg * q[p * g.ps + s];
+  }
 }
 
-__device__ __forceinline__ void ghost_y_body(const Grid& g, double* q, int t) {
+__device__ __forceinline__ void ghost_y_body(const Grid& g, double* q, int t, int p0 = 0, int p1 = 12) {
   // t over 8 ghost rows x padded width
   const int W = g.nx + 2 * NG;
   if (t >= 8 * W) return;
@@ -144,18 +149,21 @@ __device__ __forceinline__ void ghost_y_body(const Grid& g, double* q, int t) {
   if (bc == 0) src = side == 0 ? ((j % g.ny) + g.ny) % g.ny : j % g.ny;
   else src = side == 0 ? -1 - j : 2 * g.ny - 1 - j;
   const long long d = cidx(g, i, j), s = cidx(g, i, src);
-#pragma unroll
-  for (int m = 0; m < 3; m++)
-#pragma unroll
-    for (int v = 0; v < 4; v++) {
-      double sg = 1.0;
-      if (bc != 0) sg = bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0);
-      q[(4 * m + v) * g.ps + d] = sg * q[(4 * m + v) * g.ps + s];
-    }
+  for (int p = p0; p < p1; p++) {
+    const int m = p >> 2, v = p & 3;
+    double sg = 1.0;
+    if (bc != 0) sg = bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0);
+    q[p * g.ps + d] = sg * q[p * g.ps + s];
+  }
 }
 
-__global__ void k_ghost_x(Grid g, double* q) { ghost_x_body(g, q, blockIdx.x * blockDim.x + threadIdx.x); }
-__global__ void k_ghost_y(Grid g, double* q) { ghost_y_body(g, q, blockIdx.x * blockDim.x + threadIdx.x); }
+// one plane per blockIdx.y: 12 x the threads of a cell-wise loop over the planes
+__global__ void k_ghost_x(Grid g, double* q) {
+  ghost_x_body(g, q, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.y + 1);
+}
+__global__ void k_ghost_y(Grid g, double* q) {
+  ghost_y_body(g, q, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.y + 1);
+}
 
 // ---------------------------------------------------------------------------
 // gather the 17 data of one conserved variable (plane offset v) around (i, j) in the

@@ -296,7 +296,7 @@ __device__ __forceinline__ void weak_moments_mixed_body(const Grid& g, const Wor
   if (i >= g.nx + 2 || j >= g.ny + 2) return;
   const WorkF f = mixed_planes(w, g.ps);
   const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
-  const float rdx = (float)(1.0 / g.dx), rdy = (float)(1.0 / g.dy);
+  const float rdx = (float)g.rdx, rdy = (float)g.rdy;
 #pragma unroll
   for (int n = 0; n < 3; n++) {
     const float xr0 = f.wx[(long long)n * g.ps + c], xl0 = f.wx[(long long)n * g.ps + cl];
@@ -371,7 +371,7 @@ __device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Di
     const long long cl = cidx(g, i, j);
     const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
     const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
-    const float gam = (float)g.gamma, rPr = (float)(1.0 / g.Pr), rRe = (float)(1.0 / g.Re);
+    const float gam = (float)g.gamma, rPr = (float)g.rPr, rRe = (float)g.rRe;
     float st[2][3][4], gs[2][3][6];
 #pragma unroll
     for (int gp = 0; gp < 3; gp++)
@@ -442,7 +442,7 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
   const WorkF f = mixed_planes(w, g.ps);
   if (i < g.nx && j < g.ny) {
     const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
-    const float gam = (float)g.gamma, rPr = (float)(1.0 / g.Pr), rRe = (float)(1.0 / g.Re);
+    const float gam = (float)g.gamma, rPr = (float)g.rPr, rRe = (float)g.rRe;
     float vf[4] = {0.f, 0.f, 0.f, 0.f}, vg[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
     for (int G = 0; G < 3; G++)
@@ -463,7 +463,7 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
           vg[v] += wgt * gy[v];
         }
       }
-    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+    const double rdx = g.rdx, rdy = g.rdy;
 #pragma unroll
     for (int v = 0; v < 4; v++) {
       const double fR0 = w.fx[(long long)v * g.ps + c], fL0 = w.fx[(long long)v * g.ps + cl];
@@ -476,7 +476,7 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
       rhs[(long long)v * g.ps + c] = r0;
       rhs[(long long)(4 + v) * g.ps + c] = r1;
       rhs[(long long)(8 + v) * g.ps + c] = r2;
-      if (!isfinite(r0) || !isfinite(r1) || !isfinite(r2)) bad = FLAG_NONFINITE;
+      if (!finite_d(r0) || !finite_d(r1) || !finite_d(r2)) bad = FLAG_NONFINITE;
     }
   }
   bad = __reduce_or_sync(0xffffffffu, bad);

@@ -169,7 +169,7 @@ __device__ __forceinline__ void weak_moments_body(const Grid& g, const Work& w, 
   const int j = gy - 2;
   if (i >= g.nx + 2 || j >= g.ny + 2) return;
   const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
-  const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+  const double rdx = g.rdx, rdy = g.rdy;
 #pragma unroll
   for (int n = 0; n < 3; n++) {
     const double xr0 = w.wx[(long long)n * g.ps + c], xl0 = w.wx[(long long)n * g.ps + cl];
@@ -263,7 +263,7 @@ __device__ __forceinline__ void flux_body(const Grid& g, const Work& w, Diag* di
     const long long cl = cidx(g, i, j);
     const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
     const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
-    const T gam = (T)g.gamma, rPr = (T)(1.0 / g.Pr), rRe = (T)(1.0 / g.Re);
+    const T gam = (T)g.gamma, rPr = (T)g.rPr, rRe = (T)g.rRe;
     T st[2][3][4], gs[2][3][6];
 #pragma unroll
     for (int gp = 0; gp < 3; gp++)
@@ -281,9 +281,9 @@ __device__ __forceinline__ void flux_body(const Grid& g, const Work& w, Diag* di
     for (int gp = 0; gp < 3; gp++)
 #pragma unroll
       for (int s = 0; s < 2; s++) {
-        beta = fmax(beta, wave_bound<T>(dir, st[s][gp], gs[s][gp], gam, rPr, rRe));
-        const T cs = sqrt(gam * (gam - T(1)) * st[s][gp][3]);
-        amax = fmax(amax, (double)fmax(fabs(st[s][gp][1]) + cs, fabs(st[s][gp][2]) + cs));
+        beta = tfmax(beta, wave_bound<T>(dir, st[s][gp], gs[s][gp], gam, rPr, rRe));
+        const T cs = tsqrt(gam * (gam - T(1)) * st[s][gp][3]);
+        amax = fmax(amax, (double)tfmax(tfabs(st[s][gp][1]) + cs, tfabs(st[s][gp][2]) + cs));
       }
     bmax = (double)beta;
     // the moment balances use each face's fluxes only through the Gauss sums
@@ -336,7 +336,7 @@ __device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, doub
   unsigned int bad = 0;
   if (i < g.nx && j < g.ny) {
     const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
-    const T gam = (T)g.gamma, rPr = (T)(1.0 / g.Pr), rRe = (T)(1.0 / g.Re);
+    const T gam = (T)g.gamma, rPr = (T)g.rPr, rRe = (T)g.rRe;
     // volume quadrature of f and g at the tensor Gauss points
     double vf[4] = {0, 0, 0, 0}, vg[4] = {0, 0, 0, 0};
 #pragma unroll 1
@@ -358,7 +358,7 @@ __device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, doub
           vg[v] += wgt * (double)h[v];
         }
       }
-    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+    const double rdx = g.rdx, rdy = g.rdy;
 #pragma unroll
     for (int v = 0; v < 4; v++) {
       // face Gauss sums: S0 = sum w_g fhat_g, S1 = sum w_g t_g fhat_g (see k_flux)
@@ -372,7 +372,7 @@ __device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, doub
       rhs[(long long)v * g.ps + c] = r0;
       rhs[(long long)(4 + v) * g.ps + c] = r1;
       rhs[(long long)(8 + v) * g.ps + c] = r2;
-      if (!isfinite(r0) || !isfinite(r1) || !isfinite(r2)) bad = FLAG_NONFINITE;
+      if (!finite_d(r0) || !finite_d(r1) || !finite_d(r2)) bad = FLAG_NONFINITE;
     }
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
@@ -408,7 +408,7 @@ __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* 
         out[k] = base[(long long)k * g.ps + c] * (1.0 / 3.0) + (2.0 / 3.0) * (cur + dt * f);
       }
       qout[(long long)k * g.ps + c] = out[k];
-      if (!isfinite(out[k])) bad = FLAG_INADMISSIBLE;
+      if (!finite_d(out[k])) bad = FLAG_INADMISSIBLE;
     }
     // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
     const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
