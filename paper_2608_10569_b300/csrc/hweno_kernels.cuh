@@ -38,6 +38,7 @@ struct Grid {
 __device__ __forceinline__ bool finite_d(double x) {
   return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
 }
+__device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
 
 __device__ __forceinline__ long long cidx(const Grid& g, int i, int j) {
   return (long long)(j + NG) * g.pitch + (i + NG);

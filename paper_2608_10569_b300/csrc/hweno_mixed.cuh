@@ -25,6 +25,13 @@ struct WorkF {
   float* hilo;   // 24: hi of the 12 state planes, then lo
 };
 
+// FP32 face sums of the mixed path: S0 (planes 0-3) and S1 (4-7) of each conserved
+// variable, in the face-flux group's double planes 8-11, which it does not use otherwise
+__host__ __device__ inline float* mixed_face_sums(double* f, long long ps) { return (float*)(f + 8 * ps); }
+__host__ __device__ inline const float* mixed_face_sums(const double* f, long long ps) {
+  return (const float*)(f + 8 * ps);
+}
+
 __host__ __device__ inline WorkF mixed_planes(const Work& w, long long ps) {
   WorkF f;
   f.face = (float*)w.face;
@@ -417,12 +424,16 @@ __device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Di
         if (gp != 1) S1[v] += wt * fh;
       }
     }
-    // stored in FP64 so that the balances difference them exactly
+    // S0 in FP64 planes 0-3: the average balances difference it in FP64, so their sum
+    // over a periodic grid telescopes to FP64 rounding; S0 and S1 again as FP32 planes
+    // (in double planes 8-11) for the moment balances, which run in FP32
     double* out = (dir == 0 ? w.fx : w.fy) + cl;
+    float* outf = mixed_face_sums(dir == 0 ? w.fx : w.fy, g.ps) + cl;
 #pragma unroll
     for (int v = 0; v < 4; v++) {
       out[(long long)v * g.ps] = (double)S0[v];
-      out[(long long)(4 + v) * g.ps] = (double)S1[v];
+      outf[(long long)v * g.ps] = S0[v];
+      outf[(long long)(4 + v) * g.ps] = S1[v];
     }
   }
   amax = warp_max(amax);
@@ -464,19 +475,26 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
         }
       }
     const double rdx = g.rdx, rdy = g.rdy;
+    const float rdxf = (float)g.rdx, rdyf = (float)g.rdy;
+    const float* fxf = mixed_face_sums(w.fx, g.ps);
+    const float* fyf = mixed_face_sums(w.fy, g.ps);
 #pragma unroll
     for (int v = 0; v < 4; v++) {
+      // average balance in FP64 from the FP64 face sums
       const double fR0 = w.fx[(long long)v * g.ps + c], fL0 = w.fx[(long long)v * g.ps + cl];
-      const double fR1 = w.fx[(long long)(4 + v) * g.ps + c], fL1 = w.fx[(long long)(4 + v) * g.ps + cl];
       const double gT0 = w.fy[(long long)v * g.ps + c], gB0 = w.fy[(long long)v * g.ps + cb];
-      const double gT1 = w.fy[(long long)(4 + v) * g.ps + c], gB1 = w.fy[(long long)(4 + v) * g.ps + cb];
       const double r0 = -(fR0 - fL0) * rdx - (gT0 - gB0) * rdy;
-      const double r1 = -(fL0 + fR0) * (0.5 * rdx) - (gT1 - gB1) * rdy + (double)vf[v] * rdx;
-      const double r2 = -(fR1 - fL1) * rdx - (gB0 + gT0) * (0.5 * rdy) + (double)vg[v] * rdy;
+      // moment balances in FP32, like the volume fluxes they combine with
+      const float sR0 = fxf[(long long)v * g.ps + c], sL0 = fxf[(long long)v * g.ps + cl];
+      const float sR1 = fxf[(long long)(4 + v) * g.ps + c], sL1 = fxf[(long long)(4 + v) * g.ps + cl];
+      const float tT0 = fyf[(long long)v * g.ps + c], tB0 = fyf[(long long)v * g.ps + cb];
+      const float tT1 = fyf[(long long)(4 + v) * g.ps + c], tB1 = fyf[(long long)(4 + v) * g.ps + cb];
+      const float r1 = -(sL0 + sR0) * (0.5f * rdxf) - (tT1 - tB1) * rdyf + vf[v] * rdxf;
+      const float r2 = -(sR1 - sL1) * rdxf - (tB0 + tT0) * (0.5f * rdyf) + vg[v] * rdyf;
       rhs[(long long)v * g.ps + c] = r0;
-      rhs[(long long)(4 + v) * g.ps + c] = r1;
-      rhs[(long long)(8 + v) * g.ps + c] = r2;
-      if (!finite_d(r0) || !finite_d(r1) || !finite_d(r2)) bad = FLAG_NONFINITE;
+      rhs[(long long)(4 + v) * g.ps + c] = (double)r1;
+      rhs[(long long)(8 + v) * g.ps + c] = (double)r2;
+      if (!finite_d(r0) || !finite_f(r1) || !finite_f(r2)) bad = FLAG_NONFINITE;
     }
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
