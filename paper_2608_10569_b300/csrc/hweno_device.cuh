@@ -28,6 +28,11 @@ __device__ __forceinline__ float tfabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double tfabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tfmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double tfmax(double a, double b) { return fmax(a, b); }
+// a / b: IEEE division in FP64; in FP32 the reciprocal-multiply form (at most 2 ulp, for
+// divisors between 2^-126 and 2^126, which the mixed path's weights, densities and sound
+// speeds are)
+__device__ __forceinline__ float tdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double tdiv(double a, double b) { return a / b; }
 constexpr double GW_OUT = 5.0 / 18.0;
 constexpr double GW_MID = 4.0 / 9.0;
 // linear weights of Appendix A.2
@@ -91,10 +96,10 @@ __device__ __forceinline__ void hweno_combine_coeffs(const T* c0, const T* s, T 
     // FP32: the products above leave the float range for smooth data (eps^5 = 1e-40),
     // so divide once per candidate: t_m = tau/D_m, a0 = (1 + t0)/S,
     // a_m = gamma_m (t_m - t0)/S with S = gamma0 (1 + t0) + gammaL sum (1 + t_m).
-    const T t0 = tau / (b0 + eps), t1 = tau / (b1 + eps), t2 = tau / (b2 + eps);
-    const T t3 = tau / (b3 + eps), t4 = tau / (b4 + eps);
+    const T t0 = tdiv(tau, b0 + eps), t1 = tdiv(tau, b1 + eps), t2 = tdiv(tau, b2 + eps);
+    const T t3 = tdiv(tau, b3 + eps), t4 = tdiv(tau, b4 + eps);
     const T wsum = T(GAM0) * (T(1) + t0) + T(GAML) * ((T(4) + t1) + (t2 + t3) + t4);
-    const T rs = T(1) / wsum;
+    const T rs = tdiv(T(1), wsum);
     a0 = (T(1) + t0) * rs;
     const T gl = T(GAML) * rs;
     a[0] = gl * (t1 - t0);
@@ -226,7 +231,7 @@ struct CharState {
 
 template <class T>
 __device__ __forceinline__ void char_state(const T* ub, T gamma, CharState<T>& s) {
-  const T rr = T(1) / ub[0];
+  const T rr = tdiv(T(1), ub[0]);
   s.u = ub[1] * rr;
   s.v = ub[2] * rr;
   s.hq2 = T(0.5) * (s.u * s.u + s.v * s.v);
@@ -234,10 +239,10 @@ __device__ __forceinline__ void char_state(const T* ub, T gamma, CharState<T>& s
   const T c2 = gamma * p * rr;
   s.c = tsqrt(c2);
   s.H = (ub[3] + p) * rr;
-  const T b1 = (gamma - T(1)) / c2;
+  const T b1 = tdiv(gamma - T(1), c2);
   s.hb1 = T(0.5) * b1;
   s.hb2 = s.hb1 * s.hq2;
-  s.hrc = T(0.5) / s.c;
+  s.hrc = tdiv(T(0.5), s.c);
 }
 
 // x (rho, m, n, E) -> characteristic y for direction DIR (0: x, 1: y)
@@ -383,8 +388,8 @@ __device__ __forceinline__ T wave_bound(int dir, const T* w, const T* s, T gamma
     un = w[2]; q = gamma * s[5] * rPr * rRe; s1 = txy * rRe; s2 = tyy * rRe - p;
   }
   const T r2e = rho * rho * e;
-  const T pp = tfabs(un) + (tsqrt(rho * rho * q * q + T(2) * r2e * (s1 * s1 + s2 * s2)) + rho * tfabs(q)) /
-                              (T(2) * r2e);
+  const T pp = tfabs(un) + tdiv(tsqrt(rho * rho * q * q + T(2) * r2e * (s1 * s1 + s2 * s2)) + rho * tfabs(q),
+                                T(2) * r2e);
   return tfmax(tfabs(un) + cs, pp);
 }
 

@@ -100,7 +100,7 @@ __device__ __forceinline__ void to_prim(const double* s, float* w) {
 }
 
 __device__ __forceinline__ void to_prim_f(const float* s, float* w) {
-  const float rr = 1.0f / s[0];
+  const float rr = tdiv(1.0f, s[0]);
   w[0] = s[0];
   w[1] = s[1] * rr;
   w[2] = s[2] * rr;
