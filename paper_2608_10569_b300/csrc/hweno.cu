@@ -61,6 +61,13 @@ __global__ void k_rk(Grid g, int stage, const double* __restrict__ qin, const do
   rk_body(g, stage, qin, mom, rhs, base, qout, diag, blockIdx.x * blockDim.x + threadIdx.x,
           blockIdx.y * blockDim.y + threadIdx.y);
 }
+// the mixed path's stage update: also the hi/lo split of the new state
+__global__ void k_rk_split(Grid g, int stage, const double* __restrict__ qin, const double* __restrict__ mom,
+                           const double* __restrict__ rhs, double* __restrict__ base, double* __restrict__ qout,
+                           Diag* diag, float* __restrict__ hilo) {
+  rk_body<true>(g, stage, qin, mom, rhs, base, qout, diag, blockIdx.x * blockDim.x + threadIdx.x,
+                blockIdx.y * blockDim.y + threadIdx.y, hilo);
+}
 
 // time step of Sec. 5: dt = min(CFL h / alpha*, b Re h^2), or a forced trial
 // value, capped by the remaining time
@@ -195,6 +202,7 @@ struct hweno_handle {
   double* h_red = nullptr; // pinned [6]
   double* d_red = nullptr;
   bool have_state = false, have_residual = false;
+  const double* split_of = nullptr;  // mixed path: the state whose hi/lo split is current
   double t = 0.0;
   // counters
   double pp_total = 0.0, cell_stages = 0.0;
@@ -267,17 +275,19 @@ static dim3 grid2(int wx, int wy, int z = 1) {
 }
 
 // ghost fill of a 12-plane state set
-static void launch_ghost(hweno_handle* h, double* q) {
+// ghost fill of q's 12 planes and, with hilo, of the 24 planes of its hi/lo split
+static void launch_ghost(hweno_handle* h, double* q, float* hilo = nullptr) {
   const Grid& g = h->g;
+  const int planes = hilo ? 36 : 12;
   {
     Prof p(h, K_GHOST);
     const int n = 8 * g.ny;
-    k_ghost_x<<<dim3((n + 127) / 128, 12), 128, 0, h->st>>>(g, q);
+    k_ghost_x<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, q, hilo);
   }
   {
     Prof p(h, K_GHOST);
     const int n = 8 * (g.nx + 2 * NG);
-    k_ghost_y<<<dim3((n + 127) / 128, 12), 128, 0, h->st>>>(g, q);
+    k_ghost_y<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, q, hilo);
   }
 }
 
@@ -285,11 +295,16 @@ static void launch_ghost(hweno_handle* h, double* q) {
 // modified moments mom (8 planes)
 static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
   const Grid& g = h->g;
-  launch_ghost(h, q);
   if (h->cfg.precision == HWENO_MIXED) {
-    {
+    float* hilo = mixed_planes(h->w, g.ps).hilo;
+    if (h->split_of == q) {
+      // the stage update that wrote q also wrote the interior of its split
+      launch_ghost(h, q, hilo);
+    } else {
+      launch_ghost(h, q);
       Prof p(h, K_GHOST);
-      k_split<<<4 * 148, 256, 0, h->st>>>(g, q, mixed_planes(h->w, g.ps).hilo);
+      k_split<<<4 * 148, 256, 0, h->st>>>(g, q, hilo);
+      h->split_of = q;
     }
     {
       Prof p(h, K_CONS);
@@ -316,6 +331,7 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
       k_assemble_mixed<<<grid2(g.nx, g.ny), dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
     }
   } else {
+    launch_ghost(h, q);
     {
       Prof p(h, K_CONS);
       if (h->w.yrec)
@@ -355,8 +371,14 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
 static int launch_rk(hweno_handle* h, int stage, const double* qin, const double* mom,
                      const double* rhs, double* qout) {
   Prof p(h, K_RK);
-  k_rk<<<grid2(h->g.nx, h->g.ny), dim3(BX, BY), 0, h->st>>>(h->g, stage, qin, mom, rhs, h->BASE, qout,
-                                                            h->d_diag);
+  if (h->cfg.precision == HWENO_MIXED) {
+    k_rk_split<<<grid2(h->g.nx, h->g.ny), dim3(BX, BY), 0, h->st>>>(h->g, stage, qin, mom, rhs, h->BASE, qout,
+                                                                  h->d_diag, mixed_planes(h->w, h->g.ps).hilo);
+    h->split_of = qout;
+  } else {
+    k_rk<<<grid2(h->g.nx, h->g.ny), dim3(BX, BY), 0, h->st>>>(h->g, stage, qin, mom, rhs, h->BASE, qout,
+                                                              h->d_diag);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "rk launch");
   return HWENO_OK;
@@ -527,6 +549,7 @@ extern "C" {
 
 int hweno_set_state(hweno_handle* h, const double* q, int on_device) {
   if (!h || !q) return fail(h, HWENO_ERR_ARG, "hweno_set_state: NULL argument");
+  h->split_of = nullptr;
   int rc = copy_planes_in(h, q, 12, h->Q, on_device);
   if (rc) return rc;
   h->have_state = true;
@@ -1041,6 +1064,7 @@ int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar,
   WorkGuard wg(h);
   h->w.yrec = h->AYREC;
   int rc;
+  h->split_of = nullptr;
   if ((rc = copy_planes_in(h, x, 12, h->Q, on_device))) return rc;
   h->have_state = true;
   const size_t P = (size_t)g.ps * sizeof(double);
@@ -1071,6 +1095,7 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
   WorkGuard wg(h);
   h->w.yrec = h->AYREC;
   int rc;
+  h->split_of = nullptr;
   if ((rc = copy_planes_in(h, q, 12, h->Q, on_device))) return rc;
   if ((rc = copy_planes_in(h, lam_next, 12, h->ALAM, on_device))) return rc;
   h->have_state = true;
@@ -1434,6 +1459,7 @@ int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections) {
           double* tmp = h->Q;
           h->Q = h->QS;
           h->QS = tmp;
+          h->split_of = nullptr;  // the batched stage update does not write the split
           h->t += d.dt;
           h->dt_last = d.dt;
           h->steps++;

@@ -40,6 +40,40 @@ __device__ __forceinline__ bool finite_d(double x) {
 }
 __device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
 
+// hi/lo split of the 12 ghost-filled state planes (whole padded planes), with integer
+// operations only: hi keeps the sign, the exponent and the leading 23 mantissa bits of
+// x (truncation), lo is the float nearest below the exact remainder x - hi (the trailing
+// 29 mantissa bits, normalised).  Zero gives (0, 0); magnitudes below 2^-74 or beyond
+// the float range take hi = fl(x), lo = 0.
+__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7ff);
+  const int fe = E - 1023 + 127;
+  if (E == 0) {  // zero (or a double denormal, below any float): signed zero
+    hi = __int_as_float((int)sign);
+    lo = 0.0f;
+    return;
+  }
+  // the remainder's float exponent field is fe - 52 + top >= fe - 52: keep it >= 1
+  if (fe < 53 || fe > 254) {  // |x| < 2^-74, beyond the float range, inf or nan
+    hi = (float)x;
+    lo = 0.0f;
+    return;
+  }
+  const unsigned long long m = b & 0xfffffffffffffull;
+  hi = __int_as_float((int)(sign | ((unsigned int)fe << 23) | (unsigned int)(m >> 29)));
+  const unsigned int r = (unsigned int)(m & 0x1fffffffull);  // remainder: r * 2^(E - 1075)
+  if (r == 0u) {
+    lo = 0.0f;
+    return;
+  }
+  const int top = 31 - __clz((int)r);          // highest set bit, 0..28
+  const int le = fe - 52 + top;                 // float exponent field of the remainder
+  const unsigned int mant = top >= 23 ? (r >> (top - 23)) : (r << (23 - top));
+  lo = __int_as_float((int)(sign | ((unsigned int)le << 23) | (mant & 0x7fffffu)));
+}
+
 __device__ __forceinline__ long long cidx(const Grid& g, int i, int j) {
   return (long long)(j + NG) * g.pitch + (i + NG);
 }
@@ -118,8 +152,10 @@ __device__ __forceinline__ double bc_sign(int bc, int normal_dir, int v) {
   return (v == 1 + normal_dir) ? -1.0 : 1.0;  // symmetry/slip: normal momentum odd
 }
 
-// planes [p0, p1) of the state (plane 4 m + v: moment m of variable v)
-__device__ __forceinline__ void ghost_x_body(const Grid& g, double* q, int t, int p0 = 0, int p1 = 12) {
+// planes [p0, p1) of the state (plane 4 m + v: moment m of variable v), or of its
+// hi/lo split (24 float planes: plane p holds state plane p mod 12)
+template <class E>
+__device__ __forceinline__ void ghost_x_body(const Grid& g, E* q, int t, int p0 = 0, int p1 = 12) {
   // t over 8 ghost columns x ny rows
   if (t >= 8 * g.ny) return;
   const int j = t / 8, c = t % 8;
@@ -131,14 +167,15 @@ __device__ __forceinline__ void ghost_x_body(const Grid& g, double* q, int t, in
   else src = side == 0 ? -1 - i : 2 * g.nx - 1 - i;
   const long long d = cidx(g, i, j), s = cidx(g, src, j);
   for (int p = p0; p < p1; p++) {
-    const int m = p >> 2, v = p & 3;
-    double sg = 1.0;
-    if (bc != 0) sg = bc_sign(bc, 0, v) * (m == 1 ? -1.0 : 1.0);
+    const int m = (p % 12) >> 2, v = p & 3;
+    E sg = E(1);
+    if (bc != 0) sg = E(bc_sign(bc, 0, v) * (m == 1 ? -1.0 : 1.0));
     q[p * g.ps + d] = sg * q[p * g.ps + s];
   }
 }
 
-__device__ __forceinline__ void ghost_y_body(const Grid& g, double* q, int t, int p0 = 0, int p1 = 12) {
+template <class E>
+__device__ __forceinline__ void ghost_y_body(const Grid& g, E* q, int t, int p0 = 0, int p1 = 12) {
   // t over 8 ghost rows x padded width
   const int W = g.nx + 2 * NG;
   if (t >= 8 * W) return;
@@ -151,19 +188,24 @@ __device__ __forceinline__ void ghost_y_body(const Grid& g, double* q, int t, in
   else src = side == 0 ? -1 - j : 2 * g.ny - 1 - j;
   const long long d = cidx(g, i, j), s = cidx(g, i, src);
   for (int p = p0; p < p1; p++) {
-    const int m = p >> 2, v = p & 3;
-    double sg = 1.0;
-    if (bc != 0) sg = bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0);
+    const int m = (p % 12) >> 2, v = p & 3;
+    E sg = E(1);
+    if (bc != 0) sg = E(bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0));
     q[p * g.ps + d] = sg * q[p * g.ps + s];
   }
 }
 
-// one plane per blockIdx.y: 12 x the threads of a cell-wise loop over the planes
-__global__ void k_ghost_x(Grid g, double* q) {
-  ghost_x_body(g, q, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.y + 1);
+// one plane per blockIdx.y: 12 x the threads of a cell-wise loop over the planes;
+// with hilo, blockIdx.y = 12..35 fills the 24 planes of the state's hi/lo split too
+__global__ void k_ghost_x(Grid g, double* q, float* hilo) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+  if (p < 12) ghost_x_body(g, q, t, p, p + 1);
+  else ghost_x_body(g, hilo, t, p - 12, p - 11);
 }
-__global__ void k_ghost_y(Grid g, double* q) {
-  ghost_y_body(g, q, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.y + 1);
+__global__ void k_ghost_y(Grid g, double* q, float* hilo) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+  if (p < 12) ghost_y_body(g, q, t, p, p + 1);
+  else ghost_y_body(g, hilo, t, p - 12, p - 11);
 }
 
 // ---------------------------------------------------------------------------

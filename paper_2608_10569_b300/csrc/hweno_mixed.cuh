@@ -1,14 +1,16 @@
-// Mixed-precision spatial operator: reconstruction, weights, gradients and fluxes
-// in FP32; the stored state, the positivity limiter's checks and theta solve where
-// they can bind, the face-flux differences of the moment balances and the RK update
-// in FP64.
+// Mixed-precision spatial operator: reconstruction, weights, gradients, fluxes and the
+// moment balances in FP32; the stored state, the positivity limiter's checks and theta
+// solve where they can bind, the face-flux differences of the average balances (exact
+// conservation) and the RK update in FP64.
 //
 // FP32 intermediates share the handle's scratch planes: a float plane k of a group
 // starts at (float*)group + k * ps, so a group of n double planes holds 2n float
-// planes.  The state is split once per evaluation into float planes hi = fl(q) and
-// lo = fl(q - hi) (stored after the 48 float face planes, in the face group's unused
-// half), so offsets from a cell's own average, (hi_k - hi_c) + (lo_k - lo_c), are
-// exact to FP32 rounding of the offset itself rather than of the average.
+// planes.  The state is kept split into float planes hi (the double truncated to 24
+// significant bits) and lo (the remainder), stored after the 48 float face planes in the
+// face group's unused half; the RK update writes the split with the state, a separate
+// pass splits a state set from outside.  Offsets from a cell's own average,
+// (hi_k - hi_c) + (lo_k - lo_c), are then exact to FP32 rounding of the offset itself
+// rather than of the average.
 #pragma once
 #include "hweno_ops.cuh"
 
@@ -43,40 +45,6 @@ __host__ __device__ inline WorkF mixed_planes(const Work& w, long long ps) {
   f.rm = (float*)w.rm;
   f.gr = (float*)w.gr;
   return f;
-}
-
-// hi/lo split of the 12 ghost-filled state planes (whole padded planes), with integer
-// operations only: hi keeps the sign, the exponent and the leading 23 mantissa bits of
-// x (truncation), lo is the float nearest below the exact remainder x - hi (the trailing
-// 29 mantissa bits, normalised).  Zero gives (0, 0); magnitudes below 2^-74 or beyond
-// the float range take hi = fl(x), lo = 0.
-__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-  const int E = (int)((b >> 52) & 0x7ff);
-  const int fe = E - 1023 + 127;
-  if (E == 0) {  // zero (or a double denormal, below any float): signed zero
-    hi = __int_as_float((int)sign);
-    lo = 0.0f;
-    return;
-  }
-  // the remainder's float exponent field is fe - 52 + top >= fe - 52: keep it >= 1
-  if (fe < 53 || fe > 254) {  // |x| < 2^-74, beyond the float range, inf or nan
-    hi = (float)x;
-    lo = 0.0f;
-    return;
-  }
-  const unsigned long long m = b & 0xfffffffffffffull;
-  hi = __int_as_float((int)(sign | ((unsigned int)fe << 23) | (unsigned int)(m >> 29)));
-  const unsigned int r = (unsigned int)(m & 0x1fffffffull);  // remainder: r * 2^(E - 1075)
-  if (r == 0u) {
-    lo = 0.0f;
-    return;
-  }
-  const int top = 31 - __clz((int)r);          // highest set bit, 0..28
-  const int le = fe - 52 + top;                 // float exponent field of the remainder
-  const unsigned int mant = top >= 23 ? (r >> (top - 23)) : (r << (23 - top));
-  lo = __int_as_float((int)(sign | ((unsigned int)le << 23) | (mant & 0x7fffffu)));
 }
 
 __global__ void k_split(Grid g, const double* __restrict__ q, float* __restrict__ hilo) {

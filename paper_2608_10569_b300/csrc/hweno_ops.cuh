@@ -384,10 +384,13 @@ __device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, doub
 //   stage 2: out = 3/4 base + 1/4 ([u^(1); vhat^(1)] + dt F)
 //   stage 3: out = 1/3 base + 2/3 ([u^(2); vhat^(2)] + dt F)
 // plus the admissibility test of the output averages (Sec. 5).
+// SPLIT (mixed path): also write the hi/lo split of the new state (24 float planes at
+// hilo), so that the next evaluation needs no separate split pass
+template <bool SPLIT = false>
 __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* __restrict__ qin,
                                         const double* __restrict__ mom, const double* __restrict__ rhs,
                                         double* __restrict__ base, double* __restrict__ qout, Diag* diag,
-                                        int gx, int gy) {
+                                        int gx, int gy, float* __restrict__ hilo = nullptr) {
   const int i = gx;
   const int j = gy;
   unsigned int bad = 0;
@@ -408,6 +411,12 @@ __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* 
         out[k] = base[(long long)k * g.ps + c] * (1.0 / 3.0) + (2.0 / 3.0) * (cur + dt * f);
       }
       qout[(long long)k * g.ps + c] = out[k];
+      if constexpr (SPLIT) {
+        float hi, lo;
+        split_hilo(out[k], hi, lo);
+        hilo[(long long)k * g.ps + c] = hi;
+        hilo[(long long)(12 + k) * g.ps + c] = lo;
+      }
       if (!finite_d(out[k])) bad = FLAG_INADMISSIBLE;
     }
     // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
