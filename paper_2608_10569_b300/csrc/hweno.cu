@@ -1255,18 +1255,24 @@ static void batch_enqueue_step(hweno_batch* b) {
   b->launches++;
   for (int stage = 1; stage <= 3; stage++) {
     const int which = stage == 1 ? 0 : 1;
-    kb_ghost<<<grid(BR_GX), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GX].tl(), n, which, 0);
-    kb_ghost<<<grid(BR_GY), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GY].tl(), n, which, 1);
+    // mixed: stages 2 and 3 read the split their stage update wrote; stage 1 splits its
+    // state (a case may be repeated after a rejected attempt, or set from outside)
+    const int split = b->mixed && stage > 1;
+    kb_ghost<<<grid(BR_GX), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GX].tl(), n, which, 0, split);
+    kb_ghost<<<grid(BR_GY), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GY].tl(), n, which, 1, split);
     b->launches += 2;
     if (b->mixed) {
-      kb_split<<<grid(BR_SPLIT), blk1, 0, b->st>>>(b->d_cases, b->L[BR_SPLIT].tl(), n, which);
+      if (stage == 1) {
+        kb_split<<<grid(BR_SPLIT), blk1, 0, b->st>>>(b->d_cases, b->L[BR_SPLIT].tl(), n, which);
+        b->launches++;
+      }
       kb_cons<1><<<grid(BR_CONS), dims(BR_CONS), 0, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n, which);
       kb_face_moments<1><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
       kb_weak_moments<1><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
       kb_grad<1><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
       kb_flux<1><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
       kb_assemble<1><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
-      b->launches += 7;
+      b->launches += 6;
     } else {
       kb_cons<0><<<grid(BR_CONS), dims(BR_CONS), 0, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n, which);
       kb_face_moments<0><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
@@ -1280,7 +1286,8 @@ static void batch_enqueue_step(hweno_batch* b) {
       kb_dt<<<(n + 127) / 128, 128, 0, b->st>>>(b->d_cases, n);
       b->launches++;
     }
-    kb_rk<<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, stage);
+    if (b->mixed) kb_rk<1><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, stage);
+    else kb_rk<0><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, stage);
     b->launches++;
   }
 }
@@ -1430,7 +1437,7 @@ static int batch_attempt(hweno_batch* b) {
   int rc = batch_upload(b);
   if (rc) return rc;
   BCK(cudaGraphLaunch(b->exec, b->st), "graph launch");
-  b->launches += 1 + 3 * ((b->mixed ? 7 : 6) + 3) + 1;  // reset, 3 stages, dt
+  b->launches += 1 + 3 * (6 + 3) + 1 + (b->mixed ? 1 : 0);  // reset, 3 stages, dt, stage-1 split
   BCK(cudaMemcpyAsync(b->h_diag, b->d_diag, b->n * sizeof(Diag), cudaMemcpyDeviceToHost, b->st), "diag read");
   BCK(cudaStreamSynchronize(b->st), "stream synchronize");
   return HWENO_OK;

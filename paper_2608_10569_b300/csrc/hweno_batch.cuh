@@ -115,19 +115,30 @@ __global__ void __launch_bounds__(128) kb_assemble(const CaseDev* __restrict__ c
   HW_BATCH_END
 }
 
+// MIXED: also the hi/lo split of the new state (the next stage's evaluation then needs
+// no split pass)
+template <int MIXED>
 __global__ void __launch_bounds__(128) kb_rk(const CaseDev* __restrict__ cases, TileList L, int ncase, int stage) {
   HW_BATCH_LOOP(L, ncase)
-  if (stage == 1) rk_body(cg, 1, cd.Q, cd.MOM0, cd.RHS0, cd.BASE, cd.QS, cd.diag, gx, gy);
-  else rk_body(cg, stage, cd.QS, cd.MOM, cd.RHS, cd.BASE, cd.QS, cd.diag, gx, gy);
+  float* hilo = MIXED ? mixed_planes(cw, cg.ps).hilo : nullptr;
+  if (stage == 1) rk_body<MIXED != 0>(cg, 1, cd.Q, cd.MOM0, cd.RHS0, cd.BASE, cd.QS, cd.diag, gx, gy, hilo);
+  else rk_body<MIXED != 0>(cg, stage, cd.QS, cd.MOM, cd.RHS, cd.BASE, cd.QS, cd.diag, gx, gy, hilo);
   HW_BATCH_END
 }
 
-// ghost fill: 1D items, gx = element index (x pass: 8 ny, y pass: 8 (nx + 8))
-__global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int pass) {
+// ghost fill: 1D items, gx = element index (x pass: 8 ny, y pass: 8 (nx + 8)); with
+// split, also the 24 planes of the state's hi/lo split
+__global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int pass,
+                         int split) {
   HW_BATCH_LOOP(L, ncase)
   double* q = which == 0 ? cd.Q : cd.QS;
   if (pass == 0) ghost_x_body(cg, q, gx);
   else ghost_y_body(cg, q, gx);
+  if (split) {
+    float* hilo = mixed_planes(cw, cg.ps).hilo;
+    if (pass == 0) ghost_x_body(cg, hilo, gx, 0, 24);
+    else ghost_y_body(cg, hilo, gx, 0, 24);
+  }
   HW_BATCH_END
 }
 
