@@ -58,7 +58,23 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
     double face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
     CharState<T> cs;
     char_state<T>(ut, (T)g.gamma, cs);
+    const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
     recon_dir<T, 0, double, REC>(cc, sl, ctr, cs, eps, face, volx, mx, REC ? w.yrec + c : nullptr, g.ps);
+    if (interior) {
+#pragma unroll
+      for (int v = 0; v < 4; v++) mom[(long long)v * g.ps + c] = mx[v];
+    }
+    // FP64: the x-system's volume values wait in this thread's shared-memory slot while
+    // the y-system is reconstructed (36 doubles fewer live registers: less spilling)
+    // [blocks of 128 threads]
+    __shared__ double park[36][128];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if constexpr (!OFF) {
+#pragma unroll
+      for (int k = 0; k < 9; k++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) park[4 * k + v][tid] = volx[k][v];
+    }
     recon_dir<T, 1, double, REC>(cc, sl, ctr, cs, eps, face + 6, vol, my, REC ? w.yrec + 72 * g.ps + c : nullptr,
                                  g.ps);
 #pragma unroll
@@ -68,13 +84,13 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
         if (OFF) face[k][v] += ub[v];
 #pragma unroll
       for (int k = 0; k < 9; k++) {
-        vol[k][v] = 0.5 * (volx[k][v] + vol[k][v]);
+        const double vx = OFF ? volx[k][v] : park[4 * k + v][tid];
+        vol[k][v] = 0.5 * (vx + vol[k][v]);
         if (OFF) vol[k][v] += ub[v];
       }
     }
     double th[2] = {1.0, 1.0};
     const double pb = pressure(ub, g.gamma);
-    const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
     if (!(ub[0] > 0.0) || !(pb > 0.0)) {
       flags |= FLAG_BADAVG;
     } else if (pp_limit(ub, face, vol, g.gamma, g.eps_pp, th) && interior) {
@@ -115,10 +131,7 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
     w.theta[g.ps + c] = th[1];
     if (interior) {
 #pragma unroll
-      for (int v = 0; v < 4; v++) {
-        mom[(long long)v * g.ps + c] = mx[v];
-        mom[(long long)(4 + v) * g.ps + c] = my[v];
-      }
+      for (int v = 0; v < 4; v++) mom[(long long)(4 + v) * g.ps + c] = my[v];
     }
   }
   // block reduction of the activation count and flags: one atomic per warp
