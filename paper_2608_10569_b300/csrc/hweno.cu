@@ -291,6 +291,23 @@ static void launch_ghost(hweno_handle* h, double* q, float* hilo = nullptr) {
   }
 }
 
+// the FP64 cell-trace kernels take CONS_SMEM_BYTES of dynamic shared memory (above the
+// 48 KB default): allowed once per device
+static cudaError_t cons_smem_allow() {
+  static unsigned int done = 0;  // bit per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 32 && (done >> dev) & 1u) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_cons<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cons_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_cons<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
+  if (e == cudaSuccess && dev < 32) done |= 1u << dev;
+  return e;
+}
+
 // one spatial-operator evaluation of state q (12 planes): rhs (12 planes) and the
 // modified moments mom (8 planes)
 static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
@@ -335,9 +352,11 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
     {
       Prof p(h, K_CONS);
       if (h->w.yrec)
-        k_cons_rec<<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
+        k_cons_rec<<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), CONS_SMEM_BYTES, h->st>>>(g, q, h->w, mom,
+                                                                                     h->d_diag);
       else
-        k_cons<double><<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
+        k_cons<double><<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), CONS_SMEM_BYTES, h->st>>>(g, q, h->w, mom,
+                                                                                         h->d_diag);
     }
     {
       Prof p(h, K_FACEMOM);
@@ -453,7 +472,8 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   // wbar 3, wx 6, wy 6, rm 18, gr 126, fx 12, fy 12, theta 2
   const long long nplanes = 12 * 5 + 16 + 48 + 36 + 3 + 12 + 18 + 126 + 24 + 2;
   const long long total = nplanes * g.ps + 4 * N + 6LL * c.ny + 16;
-  cudaError_t e = cudaMalloc(&h->pool, (size_t)total * sizeof(double));
+  cudaError_t e = cons_smem_allow();
+  if (e == cudaSuccess) e = cudaMalloc(&h->pool, (size_t)total * sizeof(double));
   if (e != cudaSuccess) {
     snprintf(g_init_err, sizeof(g_init_err), "device allocation of %.2f GB failed: %s",
              total * 8.0 / 1e9, cudaGetErrorString(e));
@@ -1237,9 +1257,9 @@ static int build_list(hweno_batch* b, int k, int bx, int by) {
 
 // persistent grid: blocks resident on all SMs at once, never more than the items
 template <class K>
-static int persistent_grid(hweno_batch* b, K kernel, int items) {
+static int persistent_grid(hweno_batch* b, K kernel, int items, size_t smem = 0) {
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, smem);
   if (per_sm < 1) per_sm = 1;
   const int g = b->sms * per_sm;
   return items < g ? (items > 0 ? items : 1) : g;
@@ -1274,7 +1294,8 @@ static void batch_enqueue_step(hweno_batch* b) {
       kb_assemble<1><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
       b->launches += 6;
     } else {
-      kb_cons<0><<<grid(BR_CONS), dims(BR_CONS), 0, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n, which);
+      kb_cons<0><<<grid(BR_CONS), dims(BR_CONS), CONS_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n,
+                                                                           which);
       kb_face_moments<0><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
       kb_weak_moments<0><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
       kb_grad<0><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
@@ -1304,7 +1325,7 @@ static int batch_grids(hweno_batch* b) {
     b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<1>, b->L[BR_FLUX].total);
     b->L[BR_INT].grid = persistent_grid(b, kb_assemble<1>, b->L[BR_INT].total);
   } else {
-    b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0>, b->L[BR_CONS].total);
+    b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0>, b->L[BR_CONS].total, CONS_SMEM_BYTES);
     b->L[BR_FACE].grid = persistent_grid(b, kb_face_moments<0>, b->L[BR_FACE].total);
     b->L[BR_WEAK].grid = persistent_grid(b, kb_weak_moments<0>, b->L[BR_WEAK].total);
     b->L[BR_GRAD].grid = persistent_grid(b, kb_grad<0>, b->L[BR_GRAD].total);
@@ -1527,7 +1548,7 @@ int hweno_batch_autotune(hweno_batch* b, int* chosen) {
         switch (k) {
           case BR_CONS:
             if (b->mixed) kb_cons<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
-            else kb_cons<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
+            else kb_cons<0><<<gr, blk, CONS_SMEM_BYTES, b->st>>>(b->d_cases, tl, n, 1);
             break;
           case BR_FACE:
             if (b->mixed) kb_face_moments<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
@@ -1681,7 +1702,8 @@ extern "C" int hweno_residual_noalloc(const hweno_config* cfg, const double* q, 
   tmp.prof = false;
   // the reductions accumulate into the Diag words: they start from zero on every call;
   // every other plane is written before it is read within the call
-  cudaError_t e = cudaMemsetAsync(tmp.d_diag, 0, sizeof(Diag), tmp.st);
+  cudaError_t e = cons_smem_allow();
+  if (e == cudaSuccess) e = cudaMemsetAsync(tmp.d_diag, 0, sizeof(Diag), tmp.st);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "hweno_residual_noalloc: clearing the reductions");
   k_scatter<<<256, 256, 0, tmp.st>>>(g, 12, q, Q);
   rc = residual_eval(&tmp, Q, R, M);

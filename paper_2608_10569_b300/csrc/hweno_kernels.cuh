@@ -241,17 +241,29 @@ __device__ __forceinline__ void gather17(const Grid& g, const double* q, int v, 
 // transform back.  cc, sl, ctr hold absolute values (FP64) or offsets from the centre
 // average (FP32, ctr = 0); the outputs are in the same representation (moments are
 // unaffected by the offset).
+// the p0 coefficients of the 4 conserved variables, cc(v, k): held in registers, or in
+// this thread's slot of a shared-memory array [60][128] (blocks of 128 threads)
+template <class T>
+struct CoefRegs {
+  const T (*c)[15];
+  __device__ __forceinline__ T operator()(int v, int k) const { return c[v][k]; }
+};
+struct CoefShared {
+  const double* p;  // &smem[0][thread]
+  __device__ __forceinline__ double operator()(int v, int k) const { return p[(15 * v + k) * 128]; }
+};
+
 // REC (FP64): also store this direction's characteristic point values and weight
 // factors of every field at yr[(18 f + slot) * yps] (the Work::yrec layout).
-template <class T, int DIR, class O, bool REC = false>
-__device__ __forceinline__ void recon_dir(const T (*cc)[15], const T (*sl)[4], const T* ctr,
+template <class T, int DIR, class O, bool REC = false, class CC>
+__device__ __forceinline__ void recon_dir(const CC& cc, const T (*sl)[4], const T* ctr,
                                           const CharState<T>& cs, T eps, O (*face)[4], O (*vol)[4],
                                           O* mom, double* yr = nullptr, long long yps = 0) {
   T chf[4][6], chv[4][9], chm[4];
   T pc[15][4], ps[4][4], pz[4];
 #pragma unroll
   for (int k = 0; k < 15; k++) {
-    const T x[4] = {cc[0][k], cc[1][k], cc[2][k], cc[3][k]};
+    const T x[4] = {cc(0, k), cc(1, k), cc(2, k), cc(3, k)};
     to_char<T, DIR>(cs, x, pc[k]);
   }
 #pragma unroll

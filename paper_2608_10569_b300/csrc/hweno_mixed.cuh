@@ -132,8 +132,9 @@ __device__ __forceinline__ void cons_mixed_body(const Grid& g, const double* __r
     float face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
     CharState<float> cs;
     char_state<float>(ubf, (float)g.gamma, cs);
-    recon_dir<float, 0>(cc, sl, zero, cs, (float)g.eps_weno, face, volx, mx);
-    recon_dir<float, 1>(cc, sl, zero, cs, (float)g.eps_weno, face + 6, vol, my);
+    const CoefRegs<float> ccr{cc};
+    recon_dir<float, 0>(ccr, sl, zero, cs, (float)g.eps_weno, face, volx, mx);
+    recon_dir<float, 1>(ccr, sl, zero, cs, (float)g.eps_weno, face + 6, vol, my);
 #pragma unroll
     for (int k = 0; k < 9; k++)
 #pragma unroll

@@ -21,6 +21,12 @@ __device__ __forceinline__ int lane_id() { return (threadIdx.x + threadIdx.y * b
 // ---------------------------------------------------------------------------
 // conservative characteristic reconstruction, modified moments and PP limiter of
 // every cell of the interior grown by 3 (Sec. 3.1, Eq. (3.4), Appendix A.2)
+// FP64: per-thread scratch of cons_body in dynamic shared memory, [96][128] doubles:
+// the p0 coefficients (60) and the x-system's volume values (36), so that they do not
+// occupy registers while the other reconstruction steps run (launch with
+// CONS_SMEM_BYTES of dynamic shared memory, blocks of 128 threads)
+constexpr int CONS_SMEM_BYTES = 96 * 128 * 8;
+
 // REC (FP64 only): also write the reconstruction data a reverse sweep reads (Work::yrec)
 template <class T, bool REC = false>
 __device__ __forceinline__ void cons_body(const Grid& g, const double* __restrict__ q, const Work& w,
@@ -32,6 +38,10 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
   if (i < g.nx + 3 && j < g.ny + 3) {
     constexpr bool OFF = sizeof(T) == 4;  // FP32: reconstruct offsets from the average
     const long long c = cidx(g, i, j);
+    extern __shared__ double cons_smem[];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    double* ccs = cons_smem + tid;             // [60][128]: p0 coefficients
+    double* park = cons_smem + 60 * 128 + tid;  // [36][128]: x-system volume values
     double ub[4];
     T cc[4][15], sl[4][4], ctr[4];
 #pragma unroll
@@ -47,36 +57,46 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
 #pragma unroll
         for (int k = 0; k < 15; k++) w.yrec[(long long)(YREC_CC + 15 * v + k) * g.ps + c] = cc[v][k];
       }
+      if constexpr (!OFF) {
+#pragma unroll
+        for (int k = 0; k < 15; k++) ccs[(15 * v + k) * 128] = cc[v][k];
+      }
       sl[v][0] = (T)(d[4] - d[3]);
       sl[v][1] = (T)(d[5] - d[4]);
       sl[v][2] = (T)(d[4] - d[1]);
       sl[v][3] = (T)(d[7] - d[4]);
       ctr[v] = OFF ? T(0) : (T)ub[v];
     }
+    // a compiler barrier: the reconstructions below load the coefficients from the
+    // shared slot instead of keeping the stored registers alive
+    if constexpr (!OFF) asm volatile("" ::: "memory");
     const T ut[4] = {(T)ub[0], (T)ub[1], (T)ub[2], (T)ub[3]};
     const T eps = (T)g.eps_weno;
     double face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
     CharState<T> cs;
     char_state<T>(ut, (T)g.gamma, cs);
     const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
-    recon_dir<T, 0, double, REC>(cc, sl, ctr, cs, eps, face, volx, mx, REC ? w.yrec + c : nullptr, g.ps);
+    // FP64: the coefficients are read from the shared slot, and the x-system's volume
+    // values wait there while the y-system is reconstructed (fewer live registers)
+    const CoefRegs<T> ccr{cc};
+    const CoefShared ccsh{ccs};
+    if constexpr (OFF) recon_dir<T, 0, double, REC>(ccr, sl, ctr, cs, eps, face, volx, mx, nullptr, g.ps);
+    else recon_dir<T, 0, double, REC>(ccsh, sl, ctr, cs, eps, face, volx, mx, REC ? w.yrec + c : nullptr, g.ps);
     if (interior) {
 #pragma unroll
       for (int v = 0; v < 4; v++) mom[(long long)v * g.ps + c] = mx[v];
     }
-    // FP64: the x-system's volume values wait in this thread's shared-memory slot while
-    // the y-system is reconstructed (36 doubles fewer live registers: less spilling)
-    // [blocks of 128 threads]
-    __shared__ double park[36][128];
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if constexpr (!OFF) {
 #pragma unroll
       for (int k = 0; k < 9; k++)
 #pragma unroll
-        for (int v = 0; v < 4; v++) park[4 * k + v][tid] = volx[k][v];
+        for (int v = 0; v < 4; v++) park[(4 * k + v) * 128] = volx[k][v];
+      asm volatile("" ::: "memory");
     }
-    recon_dir<T, 1, double, REC>(cc, sl, ctr, cs, eps, face + 6, vol, my, REC ? w.yrec + 72 * g.ps + c : nullptr,
-                                 g.ps);
+    if constexpr (OFF) recon_dir<T, 1, double, REC>(ccr, sl, ctr, cs, eps, face + 6, vol, my, nullptr, g.ps);
+    else
+      recon_dir<T, 1, double, REC>(ccsh, sl, ctr, cs, eps, face + 6, vol, my,
+                                   REC ? w.yrec + 72 * g.ps + c : nullptr, g.ps);
 #pragma unroll
     for (int v = 0; v < 4; v++) {
 #pragma unroll
@@ -84,7 +104,7 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
         if (OFF) face[k][v] += ub[v];
 #pragma unroll
       for (int k = 0; k < 9; k++) {
-        const double vx = OFF ? volx[k][v] : park[4 * k + v][tid];
+        const double vx = OFF ? volx[k][v] : park[(4 * k + v) * 128];
         vol[k][v] = 0.5 * (vx + vol[k][v]);
         if (OFF) vol[k][v] += ub[v];
       }
