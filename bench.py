@@ -51,6 +51,19 @@ FLOPS_PER_CELL_FP64 = {
     "grad_recon": 3108.0,
 }
 
+# DRAM bytes of one cons_recon (k_cons<double>) launch on the 1024x512 shock tube,
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this build
+# (profiles/k_cons_traffic_shock_tube_1024x512.md); valid for that grid only
+K_CONS_TRAFFIC = {(1024, 512): 56465152 + 534104832}
+
+
+def k_cons_algorithmic_bytes(nx, ny):
+    """what one cons_recon launch must move: the 12 state planes read once (96 B) and
+    89 output planes (traces, volume values, cell means, limiter factors: 712 B) per
+    processed cell of the interior grown by 3, plus the 8 modified-moment planes (64 B)
+    per interior cell"""
+    return 808 * (nx + 6) * (ny + 6) + 64 * nx * ny
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -505,7 +518,9 @@ def main():
     roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak64,
             "peak_source": "measured FP64 FMA peak (hweno_measure_peak, this run)",
             "launches": n_l, "mean_launch_ms": tot_ms / max(n_l, 1),
-            "share_of_step": tot_ms / ms if ms > 0 else None, "traffic": None}
+            "share_of_step": tot_ms / ms if ms > 0 else None,
+            "traffic": K_CONS_TRAFFIC.get((case.nx, case.ny)) if dom == "cons_recon" else None,
+            "algorithmic_bytes": k_cons_algorithmic_bytes(case.nx, case.ny) if dom == "cons_recon" else None}
     if fpc:
         achieved = fpc * cells / (tot_ms / n_l * 1e-3) / 1e12
         roof.update({"achieved": achieved, "frac": achieved / peak64, "flops_per_cell": fpc})
