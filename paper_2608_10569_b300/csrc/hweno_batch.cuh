@@ -64,7 +64,7 @@ __device__ __forceinline__ void tile_pos(const TileList& L, int c, int t, int& g
 
 // which = 0: stage 1 (state Q, residual into RHS0/MOM0); 1: stages 2, 3 (QS -> RHS/MOM)
 template <int MIXED>
-__global__ void __launch_bounds__(128) kb_cons(const CaseDev* __restrict__ cases, TileList L, int ncase, int which) {
+__global__ void __launch_bounds__(128, MIXED ? 3 : 1) kb_cons(const CaseDev* __restrict__ cases, TileList L, int ncase, int which) {
   HW_BATCH_LOOP(L, ncase)
   const double* q = which == 0 ? cd.Q : cd.QS;
   double* mom = which == 0 ? cd.MOM0 : cd.MOM;

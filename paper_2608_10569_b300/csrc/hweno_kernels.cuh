@@ -248,9 +248,10 @@ struct CoefRegs {
   const T (*c)[15];
   __device__ __forceinline__ T operator()(int v, int k) const { return c[v][k]; }
 };
+template <class T>
 struct CoefShared {
-  const double* p;  // &smem[0][thread]
-  __device__ __forceinline__ double operator()(int v, int k) const { return p[(15 * v + k) * 128]; }
+  const T* p;  // &smem[0][thread]
+  __device__ __forceinline__ T operator()(int v, int k) const { return p[(15 * v + k) * 128]; }
 };
 
 // REC (FP64): also store this direction's characteristic point values and weight

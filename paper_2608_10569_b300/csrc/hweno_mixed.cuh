@@ -95,6 +95,13 @@ __device__ __forceinline__ void cons_mixed_body(const Grid& g, const double* __r
   if (i < g.nx + 3 && j < g.ny + 3) {
     const long long c = cidx(g, i, j);
     const long long n12 = 12 * g.ps;
+    // the p0 coefficients (60) and the x-system's volume values (36) wait in this
+    // thread's slot of shared memory, [96][128] floats (blocks of 128 threads), so that
+    // they do not occupy registers while the reconstructions run
+    __shared__ float mixed_smem[96 * 128];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    float* ccs = mixed_smem + tid;
+    float* park = mixed_smem + 60 * 128 + tid;
     float cc[4][15], sl[4][4], hc[4], lc[4];
 #pragma unroll
     for (int v = 0; v < 4; v++) {
@@ -122,6 +129,8 @@ __device__ __forceinline__ void cons_mixed_body(const Grid& g, const double* __r
       d[15] = Y[cidx(g, i - 1, j)];
       d[16] = Y[cidx(g, i + 1, j)];
       hw_p0_coeffs<float>(d, cc[v]);
+#pragma unroll
+      for (int k = 0; k < 15; k++) ccs[(15 * v + k) * 128] = cc[v][k];
       sl[v][0] = -d[3];
       sl[v][1] = d[5];
       sl[v][2] = -d[1];
@@ -132,13 +141,19 @@ __device__ __forceinline__ void cons_mixed_body(const Grid& g, const double* __r
     float face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
     CharState<float> cs;
     char_state<float>(ubf, (float)g.gamma, cs);
-    const CoefRegs<float> ccr{cc};
-    recon_dir<float, 0>(ccr, sl, zero, cs, (float)g.eps_weno, face, volx, mx);
-    recon_dir<float, 1>(ccr, sl, zero, cs, (float)g.eps_weno, face + 6, vol, my);
+    asm volatile("" ::: "memory");  // the reconstructions load the coefficients from shared memory
+    const CoefShared<float> ccsh{ccs};
+    recon_dir<float, 0>(ccsh, sl, zero, cs, (float)g.eps_weno, face, volx, mx);
 #pragma unroll
     for (int k = 0; k < 9; k++)
 #pragma unroll
-      for (int v = 0; v < 4; v++) vol[k][v] = 0.5f * (volx[k][v] + vol[k][v]);
+      for (int v = 0; v < 4; v++) park[(4 * k + v) * 128] = volx[k][v];
+    asm volatile("" ::: "memory");
+    recon_dir<float, 1>(ccsh, sl, zero, cs, (float)g.eps_weno, face + 6, vol, my);
+#pragma unroll
+    for (int k = 0; k < 9; k++)
+#pragma unroll
+      for (int v = 0; v < 4; v++) vol[k][v] = 0.5f * (park[(4 * k + v) * 128] + vol[k][v]);
     // face[][] and vol[][] hold offsets from the cell average
     bool fine = true;
 #pragma unroll
@@ -495,7 +510,9 @@ __global__ void k_gather_cons_f(Grid g, const float* __restrict__ src, double* _
 }
 
 // single-grid kernels of the mixed path
-__global__ void __launch_bounds__(128) k_cons_mixed(Grid g, const double* __restrict__ q, Work w,
+// 3 blocks of 128 per SM (168 registers): with the coefficients in shared memory the
+// extra resident warps hide more latency than the few remaining spills cost
+__global__ void __launch_bounds__(128, 3) k_cons_mixed(Grid g, const double* __restrict__ q, Work w,
                                                     double* __restrict__ mom, Diag* diag) {
   cons_mixed_body(g, q, w, mom, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }

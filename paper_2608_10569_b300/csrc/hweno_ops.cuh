@@ -79,7 +79,7 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
     // FP64: the coefficients are read from the shared slot, and the x-system's volume
     // values wait there while the y-system is reconstructed (fewer live registers)
     const CoefRegs<T> ccr{cc};
-    const CoefShared ccsh{ccs};
+    const CoefShared<double> ccsh{ccs};
     if constexpr (OFF) recon_dir<T, 0, double, REC>(ccr, sl, ctr, cs, eps, face, volx, mx, nullptr, g.ps);
     else recon_dir<T, 0, double, REC>(ccsh, sl, ctr, cs, eps, face, volx, mx, REC ? w.yrec + c : nullptr, g.ps);
     if (interior) {
