@@ -928,7 +928,6 @@ int hweno_adjoint_init(hweno_handle* h) {
   h->AST1 = take(12); h->ALAM = take(12); h->ABB = take(12); h->ATMP = take(12);
   h->AYREC = take(YREC_PLANES);
   a.mu = p;
-  a.flags = reinterpret_cast<unsigned int*>(p + 1);
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   return HWENO_OK;
 }
@@ -962,7 +961,7 @@ extern "C" int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_in
 
 // the reverse sweep over the recorded steps rec_count-1 .. 0: lam (in h->ALAM) becomes
 // the adjoint at the first recorded state; mu-bar accumulates in a.mu
-static int adjoint_reverse(hweno_handle* h, const char* who) {
+static int adjoint_reverse(hweno_handle* h) {
   const Grid& g = h->g;
   Adj& a = h->adj;
   const bool keep = h->seg_keep != 0;
@@ -989,19 +988,17 @@ static int adjoint_reverse(hweno_handle* h, const char* who) {
   }
   if (rc) return rc;
   CK(cudaGetLastError(), "adjoint launch");
-  (void)who;
   return HWENO_OK;
 }
 
 // lam_start and mu-bar from h->ALAM and a.mu after a reverse sweep
-static int adjoint_finish(hweno_handle* h, double* lam_start, double* mubar, int on_device, const char* who) {
+static int adjoint_finish(hweno_handle* h, double* lam_start, double* mubar, int on_device) {
   int rc;
   if ((rc = copy_planes_out(h, h->ALAM, 12, lam_start, on_device))) return rc;
   double hm[2];
   CK(cudaMemcpyAsync(h->h_red, h->adj.mu, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "adjoint read");
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   memcpy(hm, h->h_red, sizeof(hm));
-  (void)who;
   if (mubar) *mubar = hm[0];
   return HWENO_OK;
 }
@@ -1025,8 +1022,8 @@ extern "C" int hweno_adjoint_replay(hweno_handle* h, const double* lam_end, doub
   int rc;
   if ((rc = copy_planes_in(h, lam_end, 12, h->ALAM, on_device))) return rc;
   CK(cudaMemsetAsync(h->adj.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
-  if ((rc = adjoint_reverse(h, "hweno_adjoint_replay"))) return rc;
-  return adjoint_finish(h, lam_start, mubar, on_device, "hweno_adjoint_replay");
+  if ((rc = adjoint_reverse(h))) return rc;
+  return adjoint_finish(h, lam_start, mubar, on_device);
 }
 
 extern "C" int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int nsteps, const double* dts,
@@ -1069,10 +1066,10 @@ extern "C" int hweno_adjoint_segment(hweno_handle* h, const double* q_start, int
   h->rec_count = nsteps;
   h->rec_dts.assign(dts, dts + nsteps);
   CK(cudaMemsetAsync(h->adj.mu, 0, 2 * sizeof(double), h->st), "adjoint clear");
-  if ((rc = adjoint_reverse(h, "hweno_adjoint_segment"))) return rc;
+  if ((rc = adjoint_reverse(h))) return rc;
   h->rec_count = 0;
   h->have_state = false;  // the handle's state buffers hold segment data now
-  return adjoint_finish(h, lam_start, mubar, on_device, "hweno_adjoint_segment");
+  return adjoint_finish(h, lam_start, mubar, on_device);
 }
 
 int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar, const double* mbar, double* xbar,

@@ -36,7 +36,6 @@ struct Adj {
   double* cc;     // 68: per-cell contributions of k_cons's reverse to its 17 stencil data x 4
   double* q;      // 12: adjoint of the padded state (ghost layers included)
   double* mu;     // 1 double: d/d(1/Re), accumulated
-  unsigned int* flags;
 };
 
 // ---------------------------------------------------------------------------
@@ -240,11 +239,11 @@ __device__ __forceinline__ void eval_vol_T(const double* ob, double* cb) {
 
 // ---------------------------------------------------------------------------
 // adjoint of hweno_combine_coeffs<double> (the product form of the weights).  Takes the
-// forward's beta_0, the gradient gr = d beta_0 / d c0 and, if rs0 > 0, the forward's
-// reciprocal 1/S' (else it is recomputed); recomputes the rest of the weights from
-// (c0, s, ctr); given Cbar accumulates c0b, sb, ctrb.
+// forward's beta_0 and reciprocal rs = 1/S' (as the forward recorded them) and the
+// gradient gr = d beta_0 / d c0; recomputes the rest of the weights from (c0, s, ctr);
+// given Cbar accumulates c0b, sb, ctrb.
 __device__ __forceinline__ void hweno_combine_T(const double* c0, const double* s, double ctr, double eps,
-                                                double b0, double rs0, const double* gr, const double* Cb,
+                                                double b0, double rs, const double* gr, const double* Cb,
                                                 double* c0b, double* sb, double& ctrb) {
   const double dxm = s[0], dxp = s[1], dym = s[2], dyp = s[3];
   const double b[5] = {b0, dxm * dxm + dym * dym, dxp * dxp + dym * dym, dxm * dxm + dyp * dyp, dxp * dxp + dyp * dyp};
@@ -258,7 +257,6 @@ __device__ __forceinline__ void hweno_combine_T(const double* c0, const double* 
   const double R[5] = {0.0, D[2] * D34, D[1] * D34, D12 * D[4], D12 * D[3]};
   const double Q0 = D12 * D34, P = D[0] * Q0;
   const double SR = (R[1] + R[2]) + (R[3] + R[4]);
-  const double rs = rs0 > 0.0 ? rs0 : 1.0 / (P + tau * (GAM0 * Q0 + GAML * D[0] * SR));
   const double a0 = (P + tau * Q0) * rs;
   const double g = GAML * tau * rs;
   double a[5];
