@@ -1166,8 +1166,6 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 
 namespace {
 enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_N };
-const char* const BR_NAME[BR_N] = {"cons", "face_moments", "weak_moments", "grad", "flux", "assemble_rk",
-                                   "ghost_x", "ghost_y", "split"};
 
 struct BatchList {
   int bx = 32, by = 4;  // block shape of the kernels that use this list
