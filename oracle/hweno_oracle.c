@@ -21,6 +21,8 @@
  *                                           only face values modified), Sec. 5 (eps_PP)
  *   face moments, weak-derivative moments . Eqs. (3.6)-(3.8)
  *   gradient reconstruction ............... Eq. (3.9), Remark 3.1
+ *   HWENO-DR comparison gradients ......... Sec. 3.1 (differentiated candidates, the
+ *                                           convective weights reused)
  *   HWENO candidates, weights ............. Appendix A.2, Eqs. (A.4)-(A.6)
  *   SSP-RK3 with modified moments ......... Eq. (2.10) and its 2D analogue (Sec. 3.1)
  *   time step, restart .................... Sec. 5 (CFL, b*Re*h^2, halving), Sec. 4
@@ -36,6 +38,10 @@
  *                         then the pressure root of the quadratic in t
  *   gradient inputs       face averages from limited traces, cell mean from the
  *                         unlimited volume values
+ *   DR gradients          each system differentiates at its own face points; volume
+ *                         points take the mean of the two systems' conservative
+ *                         derivatives (as for the volume values); u, v, e follow by the
+ *                         chain rule from the unlimited reconstructed state
  *   LF coefficient        per face, max over 3 points x 2 sides of max(|u_n|+c, PP bound)
  *   ghost moments         mirror: normal moment takes -parity, tangential +parity
  *   parity unpinned:      the smoothness-indicator normalisation and the characteristic
@@ -59,7 +65,7 @@ typedef struct {
     int max_halvings;
     int linear_weights; /* 1: omega_m = gamma_m (used only by exactness pins) */
     int limiter;        /* 1: PP limiter active */
-    int pad_;
+    int scheme;         /* viscous gradients: 0 HWENO-GR (Sec. 3.2), 1 HWENO-DR (Sec. 3.1) */
 } or_cfg;
 
 /* linear weights of Appendix A.2 */
@@ -269,6 +275,53 @@ static double or_hweno_moment(const or_hweno* h, const double mom[15]) {
     return h->omega[0] * inner + outer;
 }
 
+/* derivative of a quartic in the scaled coordinate xi (axis 0) or eta (axis 1),
+ * monomial by monomial: d/dxi xi^p eta^q = p xi^(p-1) eta^q */
+static double or_poly_d(const double c[15], int axis, double xi, double eta) {
+    double s = 0.0;
+    for (int k = 0; k < 15; k++) {
+        int p = OR_MONO_P[k], q = OR_MONO_Q[k];
+        int e = axis == 0 ? p : q;
+        if (e == 0) continue;
+        if (axis == 0) p -= 1; else q -= 1;
+        double t = e;
+        for (int a = 0; a < p; a++) t *= xi;
+        for (int b = 0; b < q; b++) t *= eta;
+        s += c[k] * t;
+    }
+    return s;
+}
+
+/* HWENO-DR (Sec. 3.1): the candidates' derivatives in the combination of Eq. (3.4),
+ * with the nonlinear weights of the value reconstruction (constant over the cell):
+ * w0 (p0'/g0 - sum gm/g0 pm') + sum wm pm', derivative in scaled units */
+static double or_hweno_eval_d(const or_hweno* h, int axis, double xi, double eta) {
+    double d0 = or_poly_d(h->c0, axis, xi, eta);
+    double inner = d0 / OR_GAMMA[0], outer = 0.0;
+    for (int m = 0; m < 4; m++) {
+        double dm = or_poly_d(h->cl[m], axis, xi, eta);
+        inner -= OR_GAMMA[m + 1] / OR_GAMMA[0] * dm;
+        outer += h->omega[m + 1] * dm;
+    }
+    return h->omega[0] * inner + outer;
+}
+
+/* gradients (u_x, u_y, v_x, v_y, e_x, e_y) of the dissipative variables from a
+ * conservative state s and its physical derivatives sx, sy, by the chain rule of
+ * u = m/rho, v = n/rho, e = E/rho - (u^2 + v^2)/2 */
+static void or_dissip_grad(const double s[4], const double sx[4], const double sy[4], double g[6]) {
+    double rho = s[0], u = s[1] / rho, v = s[2] / rho, en = s[3] / rho;
+    for (int l = 0; l < 2; l++) {
+        const double* D = l == 0 ? sx : sy;
+        double ud = (D[1] - u * D[0]) / rho;
+        double vd = (D[2] - v * D[0]) / rho;
+        double end = (D[3] - en * D[0]) / rho;
+        g[0 + l] = ud;
+        g[2 + l] = vd;
+        g[4 + l] = end - (u * ud + v * vd);
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* padded working grid                                                  */
 typedef struct {
@@ -324,10 +377,17 @@ static void or_cons_cell(or_work* W, int i, int j) {
     double* face = W->face + 48 * id;
     double* vol = W->vol + 36 * id;
     double volx[9][4], voly[9][4];
+    /* HWENO-DR: conservative x- and y-derivatives at this system's face points and
+     * at the volume points (summed over the two systems) */
+    const int dr = c->scheme == 1;
+    const double hx = (c->x1 - c->x0) / c->nx, hy = (c->y1 - c->y0) / c->ny;
+    double dface[12][2][4], dvol[9][2][4];
+    memset(dvol, 0, sizeof(dvol));
     for (int dir = 0; dir < 2; dir++) {
         double L[4][4], R[4][4];
         or_eigen(ub, c->gamma, dir, L, R);
         double chf[6][4], chv[9][4], chm[4];
+        double dchf[6][2][4], dchv[9][2][4];
         for (int k = 0; k < 4; k++) {
             double d17[17];
             for (int n = 0; n < 17; n++) {
@@ -348,7 +408,35 @@ static void or_cons_cell(or_work* W, int i, int j) {
                 chv[v][k] = or_hweno_eval(&h, xi, eta);
             }
             chm[k] = or_hweno_moment(&h, dir == 0 ? OR_MOM_XI : OR_MOM_ETA);
+            if (dr)
+                for (int l = 0; l < 2; l++) {
+                    double hl = l == 0 ? hx : hy;
+                    for (int f = 0; f < 6; f++) {
+                        double xi, eta;
+                        or_face_point(6 * dir + f, &xi, &eta);
+                        dchf[f][l][k] = or_hweno_eval_d(&h, l, xi, eta) / hl;
+                    }
+                    for (int v = 0; v < 9; v++) {
+                        double xi, eta;
+                        or_vol_point(v, &xi, &eta);
+                        dchv[v][l][k] = or_hweno_eval_d(&h, l, xi, eta) / hl;
+                    }
+                }
         }
+        if (dr)
+            for (int v = 0; v < 4; v++)
+                for (int l = 0; l < 2; l++) {
+                    for (int f = 0; f < 6; f++) {
+                        double s = 0.0;
+                        for (int k = 0; k < 4; k++) s += R[v][k] * dchf[f][l][k];
+                        dface[6 * dir + f][l][v] = s;
+                    }
+                    for (int p = 0; p < 9; p++) {
+                        double s = 0.0;
+                        for (int k = 0; k < 4; k++) s += R[v][k] * dchv[p][l][k];
+                        dvol[p][l][v] += 0.5 * s;
+                    }
+                }
         /* transform back to conservative variables */
         for (int v = 0; v < 4; v++) {
             for (int f = 0; f < 6; f++) {
@@ -368,6 +456,12 @@ static void or_cons_cell(or_work* W, int i, int j) {
     }
     for (int p = 0; p < 9; p++)
         for (int v = 0; v < 4; v++) vol[4 * p + v] = 0.5 * (volx[p][v] + voly[p][v]);
+    if (dr) {
+        /* the unlimited traces and volume values: the limiter leaves gradients alone */
+        double* gr = W->grad + 126 * id;
+        for (int k = 0; k < 12; k++) or_dissip_grad(face + 4 * k, dface[k][0], dface[k][1], gr + 6 * k);
+        for (int p = 0; p < 9; p++) or_dissip_grad(vol + 4 * p, dvol[p][0], dvol[p][1], gr + 6 * (12 + p));
+    }
 }
 
 /* smallest t in [0,1] with p(ub + t (uq - ub)) = eps, p(uq) < eps <= p(ub).
@@ -688,12 +782,14 @@ static int or_region(const or_cfg* c, const double* q, int ox, int oy, int wx, i
 #pragma omp parallel for schedule(dynamic, 1)
     for (int j = -3; j < wy + 3; j++)
         for (int i = -3; i < wx + 3; i++) { or_cons_cell(&W, i, j); or_limit_cell(&W, i, j); }
+    if (c->scheme != 1) { /* HWENO-GR; DR wrote its gradients with the traces */
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int j = -2; j < wy + 2; j++)
-        for (int i = -2; i < wx + 2; i++) or_rmom_cell(&W, i, j, dx, dy);
+        for (int j = -2; j < wy + 2; j++)
+            for (int i = -2; i < wx + 2; i++) or_rmom_cell(&W, i, j, dx, dy);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int j = -1; j < wy + 1; j++)
-        for (int i = -1; i < wx + 1; i++) or_grad_cell(&W, i, j);
+        for (int j = -1; j < wy + 1; j++)
+            for (int i = -1; i < wx + 1; i++) or_grad_cell(&W, i, j);
+    }
 #pragma omp parallel for schedule(dynamic, 1)
     for (int j = 0; j < wy; j++)
         for (int i = -1; i < wx; i++) or_face_flux(&W, 0, i, j);
@@ -939,6 +1035,20 @@ int or_hweno_scalar(const double* d17, double eps, int linear, double* pts21, do
     mom2[1] = or_hweno_moment(&h, OR_MOM_ETA);
     for (int m = 0; m < 5; m++) { beta5[m] = h.beta[m]; omega5[m] = h.omega[m]; }
     for (int k = 0; k < 15; k++) c0[k] = h.c0[k];
+    return 0;
+}
+
+/* the HWENO-DR derivatives of one scalar reconstruction (unit pins): d17 ->
+ * d/dxi and d/deta (scaled units) at the 12 face and 9 volume points */
+int or_hweno_scalar_dr(const double* d17, double eps, int linear, double* dxi21, double* deta21) {
+    or_hweno h;
+    or_hweno_build(d17, eps, linear, &h);
+    for (int k = 0; k < 21; k++) {
+        double xi, eta;
+        if (k < 12) or_face_point(k, &xi, &eta); else or_vol_point(k - 12, &xi, &eta);
+        dxi21[k] = or_hweno_eval_d(&h, 0, xi, eta);
+        deta21[k] = or_hweno_eval_d(&h, 1, xi, eta);
+    }
     return 0;
 }
 

@@ -71,7 +71,7 @@ typedef struct {
     double gamma, Pr, Re;
     int bc[4];
     double cfl, b_visc, eps_pp, eps_weno;
-    int max_halvings, linear_weights, limiter, pad_;
+    int max_halvings, linear_weights, limiter, scheme;
 } or_cfg_plain;
 
 /* the dual configuration: mu = 1/Re moves with tangent dmu, so dRe = -Re^2 dmu */
@@ -87,7 +87,7 @@ static void or_cfg_dual(const or_cfg_plain* a, double dmu, or_cfg* b) {
     b->max_halvings = a->max_halvings;
     b->linear_weights = a->linear_weights;
     b->limiter = a->limiter;
-    b->pad_ = 0;
+    b->scheme = a->scheme;
 }
 
 extern "C" {

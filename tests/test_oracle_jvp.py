@@ -47,10 +47,11 @@ def test_values_are_the_plain_oracle_bit_for_bit(name):
     assert st["status"] == 0 and st2["status"] == 0
 
 
+@pytest.mark.parametrize("scheme", ["gr", "dr"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_residual_tangent_matches_differences(name):
+def test_residual_tangent_matches_differences(name, scheme):
     case, q = CASES[name]()
-    cfg = O.make_cfg(**case.params())
+    cfg = O.make_cfg(**case.params(), scheme=scheme)
     v = _direction(q, 2)
     t = O.residual_jvp(cfg, q, v)["rhs_dot"]
     fd = richardson(lambda e: O.residual(cfg, q + e * v)["rhs"], 1e-6)
@@ -62,7 +63,7 @@ def test_residual_tangent_matches_differences(name):
     def at(e):
         p = dict(case.params())
         p["Re"] = 1.0 / (mu0 + e)
-        return O.residual(O.make_cfg(**p), q)["rhs"]
+        return O.residual(O.make_cfg(**p, scheme=scheme), q)["rhs"]
 
     fdm = richardson(at, 1e-2 * mu0)
     assert np.abs(tm - fdm).max() <= 1e-9 * np.abs(tm).max()
