@@ -41,7 +41,9 @@
  *   DR gradients          each system differentiates at its own face points; volume
  *                         points take the mean of the two systems' conservative
  *                         derivatives (as for the volume values); u, v, e follow by the
- *                         chain rule from the unlimited reconstructed state
+ *                         chain rule with the state the scheme holds at the point (the
+ *                         limited face traces, the volume values), while the derivatives
+ *                         stay those of the unlimited reconstruction
  *   LF coefficient        per face, max over 3 points x 2 sides of max(|u_n|+c, PP bound)
  *   ghost moments         mirror: normal moment takes -parity, tangential +parity
  *   parity unpinned:      the smoothness-indicator normalisation and the characteristic
@@ -336,6 +338,7 @@ typedef struct {
     int* bad;          /* [bx*by] inadmissible cell average met */
     double* rm;        /* [bx*by][18] weak-derivative moments, 6*w + {x0,xxi,xeta,y0,yxi,yeta} */
     double* grad;      /* [bx*by][21][6] (u_x,u_y,v_x,v_y,e_x,e_y) at 12 face + 9 volume points */
+    double* dcons;     /* HWENO-DR: [bx*by][21][2][4] conservative x/y derivatives there */
     double* fx;        /* [bx*by][3][4] flux at the x-face on the right of the cell */
     double* fy;        /* [bx*by][3][4] flux at the y-face on top of the cell */
     double* bfx;       /* [bx*by] LF coefficient of that x-face */
@@ -457,10 +460,14 @@ static void or_cons_cell(or_work* W, int i, int j) {
     for (int p = 0; p < 9; p++)
         for (int v = 0; v < 4; v++) vol[4 * p + v] = 0.5 * (volx[p][v] + voly[p][v]);
     if (dr) {
-        /* the unlimited traces and volume values: the limiter leaves gradients alone */
-        double* gr = W->grad + 126 * id;
-        for (int k = 0; k < 12; k++) or_dissip_grad(face + 4 * k, dface[k][0], dface[k][1], gr + 6 * k);
-        for (int p = 0; p < 9; p++) or_dissip_grad(vol + 4 * p, dvol[p][0], dvol[p][1], gr + 6 * (12 + p));
+        /* the derivatives of the unlimited reconstruction: the limiter leaves them alone */
+        double* dc = W->dcons + 168 * id;
+        for (int k = 0; k < 12; k++)
+            for (int l = 0; l < 2; l++)
+                for (int v = 0; v < 4; v++) dc[8 * k + 4 * l + v] = dface[k][l][v];
+        for (int p = 0; p < 9; p++)
+            for (int l = 0; l < 2; l++)
+                for (int v = 0; v < 4; v++) dc[8 * (12 + p) + 4 * l + v] = dvol[p][l][v];
     }
 }
 
@@ -619,6 +626,17 @@ static void or_grad_cell(or_work* W, int i, int j) {
         }
 }
 
+/* HWENO-DR gradients of one cell (Sec. 3.1): the chain rule at each point, with the
+ * limited face traces and the volume values the fluxes use */
+static void or_dr_grad_cell(or_work* W, int i, int j) {
+    size_t id = IDX(W, i, j);
+    const double* dc = W->dcons + 168 * id;
+    double* gr = W->grad + 126 * id;
+    for (int k = 0; k < 12; k++) or_dissip_grad(W->face + 48 * id + 4 * k, dc + 8 * k, dc + 8 * k + 4, gr + 6 * k);
+    for (int p = 0; p < 9; p++)
+        or_dissip_grad(W->vol + 36 * id + 4 * p, dc + 8 * (12 + p), dc + 8 * (12 + p) + 4, gr + 6 * (12 + p));
+}
+
 /* physical fluxes f (dir 0) and g (dir 1) of Sec. 3.1 */
 static void or_phys_flux(const or_cfg* c, int dir, const double s[4], const double gr[6], double f[4]) {
     double g = c->gamma, Re = c->Re, Pr = c->Pr;
@@ -747,17 +765,18 @@ static int or_work_alloc(or_work* W, const or_cfg* c, int bx, int by) {
     W->bad = calloc(n, sizeof(int));
     W->rm = calloc(18 * n, sizeof(double));
     W->grad = calloc(126 * n, sizeof(double));
+    W->dcons = c->scheme == 1 ? calloc(168 * n, sizeof(double)) : NULL;
     W->fx = calloc(12 * n, sizeof(double));
     W->fy = calloc(12 * n, sizeof(double));
     W->bfx = calloc(n, sizeof(double));
     W->bfy = calloc(n, sizeof(double));
     return (W->Q && W->face && W->vol && W->mom && W->theta && W->active && W->bad && W->rm &&
-            W->grad && W->fx && W->fy && W->bfx && W->bfy) ? 0 : -1;
+            W->grad && (W->dcons || c->scheme != 1) && W->fx && W->fy && W->bfx && W->bfy) ? 0 : -1;
 }
 
 static void or_work_free(or_work* W) {
     free(W->Q); free(W->face); free(W->vol); free(W->mom); free(W->theta); free(W->active);
-    free(W->bad); free(W->rm); free(W->grad); free(W->fx); free(W->fy); free(W->bfx); free(W->bfy);
+    free(W->bad); free(W->rm); free(W->grad); free(W->dcons); free(W->fx); free(W->fy); free(W->bfx); free(W->bfy);
 }
 
 /* diagnostics written by or_residual: [0] alpha*, [1] beta_max, [2] limiter
@@ -782,7 +801,11 @@ static int or_region(const or_cfg* c, const double* q, int ox, int oy, int wx, i
 #pragma omp parallel for schedule(dynamic, 1)
     for (int j = -3; j < wy + 3; j++)
         for (int i = -3; i < wx + 3; i++) { or_cons_cell(&W, i, j); or_limit_cell(&W, i, j); }
-    if (c->scheme != 1) { /* HWENO-GR; DR wrote its gradients with the traces */
+    if (c->scheme == 1) { /* HWENO-DR: the derivatives came with the traces */
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int j = -1; j < wy + 1; j++)
+            for (int i = -1; i < wx + 1; i++) or_dr_grad_cell(&W, i, j);
+    } else {
 #pragma omp parallel for schedule(dynamic, 1)
         for (int j = -2; j < wy + 2; j++)
             for (int i = -2; i < wx + 2; i++) or_rmom_cell(&W, i, j, dx, dy);
