@@ -12,6 +12,8 @@ The metric is Gcell-RK-stage/s = cells x stages / seconds, summed over ranks.
             the state from pinned host memory and reads the new state back
   mixed     the FP32-reconstruction path on the same steps, with its L1 error
             against the FP64 path after the K steps
+  dr        the paper's comparison scheme HWENO-DR (differentiated candidates for
+            the viscous gradients) on the same workload and steps, FP64
   roofline  the dominant kernel's algorithmic FP64 flops per launch / its mean
             event-timed duration, against the FP64 FMA peak measured live
   cpu_baseline  the FP64 CPU oracle on the host cores, one SSP-RK3 step of the
@@ -51,6 +53,10 @@ FLOPS_PER_CELL_FP64 = {
     "grad_recon": 3108.0,
 }
 
+# the same for HWENO-DR's gradient kernel k_dr (profiled under the "grad_recon" slot);
+# empty until counted
+FLOPS_PER_CELL_FP64_DR = {}
+
 # DRAM bytes of one cons_recon (k_cons<double>) launch on the 1024x512 shock tube,
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this build
 # (profiles/k_cons_traffic_shock_tube_1024x512.md); valid for that grid only
@@ -75,6 +81,7 @@ def parse():
     ap.add_argument("--fd-directions", type=int, default=4)
     ap.add_argument("--adj-n", type=int, default=512)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-dr", action="store_true")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--workload", default="shock_tube",
@@ -595,6 +602,40 @@ def main():
                  "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in mprof.items()}}
         m.close()
 
+    # ---- HWENO-DR, the paper's comparison scheme, on the same workload ---------------
+    dr = None
+    if not args.no_dr:
+        d = hweno.Solver(dict(case.params(), scheme="dr"), precision="fp64", stream=stream)
+        d.set_state(qd)
+        for _ in range(args.warmup):
+            d.step()
+        torch.cuda.synchronize()
+        d.profile(True)
+        n0 = d.launch_count()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            d.step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        dlaunch = d.launch_count() - n0
+        dprof = d.profile_read()
+        d.profile(False)
+        dms = max_over_ranks(ws, ev0.elapsed_time(ev1))
+        qdr = d.get_state().cpu().numpy()
+        # both schemes took warm-up + K steps of their own step rule from the same state
+        dr = {"value": replica_value(ws, cells, stages, dms), "unit": METRIC, "ms_per_step": dms / args.steps,
+              "gpu_launches": dlaunch, "t_reached": d.diag()["t"], "t_reached_gr": t_reached,
+              "rel_l1_rho_vs_gr": float(np.abs(qdr[0] - q_fp64[0]).sum() / np.abs(q_fp64[0]).sum()),
+              "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in dprof.items()}}
+        fpc = FLOPS_PER_CELL_FP64_DR.get("grad_recon")
+        n_l, tot_ms = dprof["grad_recon"]
+        if fpc and n_l:
+            achieved = fpc * cells / (tot_ms / n_l * 1e-3) / 1e12
+            dr["k_dr_roofline"] = {"bound": "alu", "kernel": "k_dr", "unit": "TFLOP/s", "peak": peak64,
+                                   "achieved": achieved, "frac": achieved / peak64, "flops_per_cell": fpc,
+                                   "mean_launch_ms": tot_ms / n_l}
+        d.close()
+
     # ---- CPU baseline: the oracle on the host cores --------------------------------
     cpu = None
     parity = None
@@ -621,6 +662,7 @@ def main():
                            "parallelism": "replicas" if ws > 1 else "single GPU",
                            "t_reached": t_reached, "rejected_steps": rejected},
                 "roofline": roof, "cpu_baseline": cpu, "parity_vs_oracle": parity, "e2e": e2e, "mixed": mixed,
+                "dr": dr,
                 "clocks": clk, "gpu_launches": launches, "kernel_ms": kernel_ms}
         print(json.dumps(line), flush=True)
     if ws > 1:

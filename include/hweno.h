@@ -11,7 +11,10 @@
  * viscous gradients from weak-derivative moments reconstructed by the same scalar
  * HWENO routine (Eqs. (3.6)-(3.9)).  Time stepping is SSP-RK3 with modified
  * moments (Eq. (2.10) and its 2D analogue) under the time-step and restart rules of
- * Sec. 5; boundary ghost cells follow Remark 4.1.
+ * Sec. 5; boundary ghost cells follow Remark 4.1.  The paper's comparison scheme,
+ * HWENO-DR, is selected per handle (hweno_config.scheme): its viscous gradients are the
+ * derivatives of the characteristic candidates, combined with the nonlinear weights of
+ * the convective reconstruction (Sec. 3.1); everything else is shared.
  *
  * Conventions shared by every entry point
  *   - Every function returns int: HWENO_OK (0) or a negative HWENO_ERR_* code; the
@@ -59,6 +62,11 @@ extern "C" {
                          the RK update, the positivity limiter's checks and theta
                          solve, and all reductions in FP64 */
 
+/* viscous gradients */
+#define HWENO_SCHEME_GR 0 /* weak-derivative moments through the scalar HWENO (Eqs. (3.6)-(3.9)) */
+#define HWENO_SCHEME_DR 1 /* differentiated characteristic candidates with the convective
+                             weights (Sec. 3.1); fourth order; HWENO_FP64 only */
+
 typedef struct hweno_handle hweno_handle;
 
 /* Problem statement (Sec. 3.1, Sec. 5).  Uniform cells dx = (x1-x0)/nx,
@@ -75,7 +83,8 @@ typedef struct {
     double eps_weno;          /* epsilon of the nonlinear weights (Appendix A: 1e-8) */
     int max_halvings;         /* restarts with dt/2 before HWENO_ERR_INADMISSIBLE */
     int precision;            /* HWENO_FP64 or HWENO_MIXED */
-    int scheme;               /* 0: HWENO-GR (the only value accepted) */
+    int scheme;               /* HWENO_SCHEME_GR or HWENO_SCHEME_DR (handles only: the
+                                 adjoint, the batch and hweno_residual_noalloc take GR) */
     int reserved;             /* must be 0 */
 } hweno_config;
 
@@ -194,7 +203,8 @@ long long hweno_launch_count(const hweno_handle* h);
  * the term that set it.  The paper has no adjoint; the derivatives are those of its
  * discrete scheme. */
 
-/* Allocate the adjoint buffers (about 6.3 KB per padded cell); FP64 handles only. */
+/* Allocate the adjoint buffers (about 6.3 KB per padded cell); FP64 HWENO-GR handles
+ * only (HWENO_ERR_ARG otherwise). */
 int hweno_adjoint_init(hweno_handle* h);
 
 /* xbar = (dR/dx)^T rbar + (dM/dx)^T mbar and *mubar = d<rbar, R>/dmu + d<mbar, M>/dmu
@@ -257,8 +267,9 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 typedef struct hweno_batch hweno_batch;
 
 /* Create ncases solvers (cfgs[0..ncases-1], as for hweno_init, all with the same
- * precision) sharing one stream; NULL stream: the batch creates its own non-blocking
- * stream (graph capture needs one).  Allocates everything.  Errors as hweno_init. */
+ * precision and HWENO_SCHEME_GR) sharing one stream; NULL stream: the batch creates its
+ * own non-blocking stream (graph capture needs one).  Allocates everything.  Errors as
+ * hweno_init. */
 int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_batch** out);
 void hweno_batch_destroy(hweno_batch* b);
 const char* hweno_batch_last_error(const hweno_batch* b);
@@ -289,7 +300,8 @@ long long hweno_batch_launch_count(const hweno_batch* b);
  * take cudaMalloc's implicit device-wide synchronisation.  The paper has no
  * counterpart: this is a deployment variant of the same evaluation.
  *
- * No handle: cfg describes the problem as for hweno_init.  q [3][4][ny][nx] (the
+ * No handle: cfg describes the problem as for hweno_init (HWENO_SCHEME_GR only).
+ * q [3][4][ny][nx] (the
  * state layout above), rhs [3][4][ny][nx] and vhat [2][4][ny][nx] (or NULL) are
  * caller-owned DEVICE buffers on the current device.  All intermediate fields live
  * in one library-static device array of about 9.9 MB that every GPU loading the

@@ -34,6 +34,16 @@ __global__ void __launch_bounds__(BX * BY) k_cons_rec(Grid g, const double* __re
   cons_body<double, true>(g, q, w, mom, diag, blockIdx.x * blockDim.x + threadIdx.x,
                           blockIdx.y * blockDim.y + threadIdx.y);
 }
+// HWENO-DR: the FP64 traces also store the characteristic combinations (Work::dr)
+__global__ void __launch_bounds__(BX * BY) k_cons_dr(Grid g, const double* __restrict__ q, Work w,
+                                                     double* __restrict__ mom, Diag* diag) {
+  cons_body<double, false, true>(g, q, w, mom, diag, blockIdx.x * blockDim.x + threadIdx.x,
+                                 blockIdx.y * blockDim.y + threadIdx.y);
+}
+// HWENO-DR gradients from those combinations, in place of the gradient reconstruction
+__global__ void __launch_bounds__(DR_THREADS) k_dr(Grid g, const double* __restrict__ q, Work w) {
+  dr_body(g, q, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
 __global__ void __launch_bounds__(BX * BY) k_grad_rec(Grid g, Work w) {
   grad_body<double, true>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
@@ -304,6 +314,9 @@ static cudaError_t cons_smem_allow() {
     e = cudaFuncSetAttribute(k_cons_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kb_cons<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cons_dr, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dr, cudaFuncAttributeMaxDynamicSharedMemorySize, DR_SMEM_BYTES);
   if (e == cudaSuccess && dev < 32) done |= 1u << dev;
   return e;
 }
@@ -346,6 +359,25 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
     {
       Prof p(h, K_ASSEMBLE);
       k_assemble_mixed<<<grid2(g.nx, g.ny), dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
+    }
+  } else if (h->cfg.scheme == HWENO_SCHEME_DR) {
+    launch_ghost(h, q);
+    {
+      Prof p(h, K_CONS);
+      k_cons_dr<<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), CONS_SMEM_BYTES, h->st>>>(g, q, h->w, mom, h->d_diag);
+    }
+    {
+      Prof p(h, K_GRAD);
+      const dim3 blk(32, DR_THREADS / 32);
+      k_dr<<<dim3((g.nx + 2 + 31) / 32, (g.ny + 2 + blk.y - 1) / blk.y), blk, DR_SMEM_BYTES, h->st>>>(g, q, h->w);
+    }
+    {
+      Prof p(h, K_FLUX);
+      k_flux<double><<<grid2(g.nx + 1, g.ny + 1, 2), dim3(BX, BY), 0, h->st>>>(g, h->w, h->d_diag);
+    }
+    {
+      Prof p(h, K_ASSEMBLE);
+      k_assemble<double><<<grid2(g.nx, g.ny), dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
     }
   } else {
     launch_ghost(h, q);
@@ -447,7 +479,11 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
     return fail(nullptr, HWENO_ERR_ARG, "cfl, b_visc, eps_pp, eps_weno must be > 0");
   if (c.precision != HWENO_FP64 && c.precision != HWENO_MIXED)
     return fail(nullptr, HWENO_ERR_ARG, "precision must be HWENO_FP64 or HWENO_MIXED");
-  if (c.scheme != 0 || c.reserved != 0) return fail(nullptr, HWENO_ERR_ARG, "scheme must be 0 (HWENO-GR)");
+  if (c.scheme != HWENO_SCHEME_GR && c.scheme != HWENO_SCHEME_DR)
+    return fail(nullptr, HWENO_ERR_ARG, "scheme must be HWENO_SCHEME_GR or HWENO_SCHEME_DR");
+  if (c.scheme == HWENO_SCHEME_DR && c.precision != HWENO_FP64)
+    return fail(nullptr, HWENO_ERR_ARG, "HWENO_SCHEME_DR runs in HWENO_FP64");
+  if (c.reserved != 0) return fail(nullptr, HWENO_ERR_ARG, "reserved must be 0");
 
   h = new (std::nothrow) hweno_handle();
   if (!h) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
@@ -469,8 +505,9 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
 
   const long long N = (long long)c.nx * c.ny;
   // planes: Q 12, QS 12, BASE 12, RHS0 12, RHS 12, MOM0 8, MOM 8, face 48, vol 36,
-  // wbar 3, wx 6, wy 6, rm 18, gr 126, fx 12, fy 12, theta 2
-  const long long nplanes = 12 * 5 + 16 + 48 + 36 + 3 + 12 + 18 + 126 + 24 + 2;
+  // wbar 3, wx 6, wy 6, rm 18, gr 126, fx 12, fy 12, theta 2; HWENO-DR: dr 120
+  const long long ndr = c.scheme == HWENO_SCHEME_DR ? 120 : 0;
+  const long long nplanes = 12 * 5 + 16 + 48 + 36 + 3 + 12 + 18 + 126 + 24 + 2 + ndr;
   const long long total = nplanes * g.ps + 4 * N + 6LL * c.ny + 16;
   cudaError_t e = cons_smem_allow();
   if (e == cudaSuccess) e = cudaMalloc(&h->pool, (size_t)total * sizeof(double));
@@ -486,6 +523,7 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   h->MOM0 = take(8); h->MOM = take(8);
   h->w.face = take(48); h->w.vol = take(36); h->w.wbar = take(3); h->w.wx = take(6); h->w.wy = take(6);
   h->w.rm = take(18); h->w.gr = take(126); h->w.fx = take(12); h->w.fy = take(12); h->w.theta = take(2);
+  if (ndr) h->w.dr = take(ndr);
   h->STAGE = p; p += 4 * N;
   h->PART = p; p += 6LL * c.ny;
   h->d_red = p;
@@ -912,6 +950,8 @@ extern "C" {
 int hweno_adjoint_init(hweno_handle* h) {
   if (!h) return HWENO_ERR_ARG;
   if (h->cfg.precision != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_FP64");
+  if (h->cfg.scheme != HWENO_SCHEME_GR)
+    return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_SCHEME_GR");
   if (h->apool) return HWENO_OK;
   const Grid& g = h->g;
   // R 12, M 8, face 48, vol 36, gr 126, rm 18, cg 102, cc 68, q 12, stage-1 state 12,
@@ -1378,6 +1418,9 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   for (int c = 1; c < ncases; c++)
     if (cfgs[c].precision != cfgs[0].precision)
       return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same precision");
+  for (int c = 0; c < ncases; c++)
+    if (cfgs[c].scheme != HWENO_SCHEME_GR)
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels run HWENO_SCHEME_GR");
   hweno_batch* b = new (std::nothrow) hweno_batch();
   if (!b) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
   snprintf(b->err, sizeof(b->err), "no error");
@@ -1648,7 +1691,8 @@ static int noalloc_check_config(const hweno_config& c) {
   if (!(c.eps_pp > 0.0) || !(c.eps_weno > 0.0)) return fail(nullptr, HWENO_ERR_ARG, "eps_pp, eps_weno must be > 0");
   if (c.precision != HWENO_FP64 && c.precision != HWENO_MIXED)
     return fail(nullptr, HWENO_ERR_ARG, "precision must be HWENO_FP64 or HWENO_MIXED");
-  if (c.scheme != 0 || c.reserved != 0) return fail(nullptr, HWENO_ERR_ARG, "scheme must be 0 (HWENO-GR)");
+  if (c.scheme != HWENO_SCHEME_GR || c.reserved != 0)
+    return fail(nullptr, HWENO_ERR_ARG, "hweno_residual_noalloc runs HWENO_SCHEME_GR (reserved must be 0)");
   return HWENO_OK;
 }
 

@@ -12,6 +12,8 @@
 //   k_face_moments      face moments W^{x,0}, W^{x,1}, W^{y,0}, W^{y,1} (Eq. (3.6))
 //   k_weak_moments      weak-derivative moments r (Eqs. (3.7)-(3.8)) on interior + 2
 //   k_grad              gradient HWENO (Eq. (3.9)) on interior + 1
+//   (HWENO-DR instead: k_cons_dr also stores the characteristic combinations, and
+//    k_dr differentiates them on interior + 1 in place of the three kernels above)
 //   k_flux              PP-LLF face fluxes (Eq. (3.3)) of the interior faces
 //   k_assemble          moment balances Eq. (3.2) on the interior
 #pragma once
@@ -101,6 +103,10 @@ struct Work {
   //   YREC_GR + 17 m + k  gradient component m: k < 15 its p0 coefficients, 15 beta_0,
   //       16 1/S'
   double* yrec = nullptr;
+  // 120 planes, HWENO-DR only (else null): 60 d + 15 f + k, coefficient k of the
+  // nonlinear combination of characteristic field f of direction d's reconstruction
+  // (absolute values), for cells of the interior grown by 1
+  double* dr = nullptr;
 };
 
 // device-side reductions and flags of one evaluation / step
@@ -256,10 +262,13 @@ struct CoefShared {
 
 // REC (FP64): also store this direction's characteristic point values and weight
 // factors of every field at yr[(18 f + slot) * yps] (the Work::yrec layout).
+// dw (HWENO-DR, FP64): also store each field's combination coefficients at
+// dw[(15 f + k) * yps] (the Work::dr layout).
 template <class T, int DIR, class O, bool REC = false, class CC>
 __device__ __forceinline__ void recon_dir(const CC& cc, const T (*sl)[4], const T* ctr,
                                           const CharState<T>& cs, T eps, O (*face)[4], O (*vol)[4],
-                                          O* mom, double* yr = nullptr, long long yps = 0) {
+                                          O* mom, double* yr = nullptr, long long yps = 0,
+                                          double* dw = nullptr) {
   T chf[4][6], chv[4][9], chm[4];
   T pc[15][4], ps[4][4], pz[4];
 #pragma unroll
@@ -282,6 +291,10 @@ __device__ __forceinline__ void recon_dir(const CC& cc, const T (*sl)[4], const 
     for (int k = 0; k < 4; k++) s[k] = ps[k][f];
     T wr[2];
     hweno_combine_coeffs<T, REC>(c0, s, pz[f], eps, C, wr);
+    if (dw) {
+#pragma unroll
+      for (int k = 0; k < 15; k++) dw[(long long)(15 * f + k) * yps] = (double)C[k];
+    }
     if (DIR == 0) eval_xfaces<T>(C, chf[f]); else eval_yfaces<T>(C, chf[f]);
     eval_vol<T>(C, chv[f]);
     chm[f] = DIR == 0 ? hw_moment_xi<T>(C) : hw_moment_eta<T>(C);

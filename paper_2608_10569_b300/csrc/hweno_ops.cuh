@@ -6,7 +6,7 @@
 //   cons          (nx+6) x (ny+6)        i = gx - 3, j = gy - 3
 //   face moments  (nx+5) x (ny+5) x 2    z = 0: i = gx - 3, j = gy - 2; z = 1: i = gx - 2, j = gy - 3
 //   weak moments  (nx+4) x (ny+4)        i = gx - 2, j = gy - 2
-//   grad          (nx+2) x (ny+2)        i = gx - 1, j = gy - 1
+//   grad, dr      (nx+2) x (ny+2)        i = gx - 1, j = gy - 1
 //   flux          (nx+1) x (ny+1) x 2    z = 0: i = gx - 1, j = gy; z = 1: i = gx, j = gy - 1
 //   assemble, rk  nx x ny                i = gx, j = gy
 #pragma once
@@ -28,7 +28,9 @@ __device__ __forceinline__ int lane_id() { return (threadIdx.x + threadIdx.y * b
 constexpr int CONS_SMEM_BYTES = 96 * 128 * 8;
 
 // REC (FP64 only): also write the reconstruction data a reverse sweep reads (Work::yrec)
-template <class T, bool REC = false>
+// DR (FP64 only): also write the combination coefficients HWENO-DR differentiates
+// (Work::dr) for the cells of the interior grown by 1
+template <class T, bool REC = false, bool DR = false>
 __device__ __forceinline__ void cons_body(const Grid& g, const double* __restrict__ q, const Work& w,
                                           double* __restrict__ mom, Diag* diag, int gx, int gy) {
   const int i = gx - 3;
@@ -80,8 +82,14 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
     // values wait there while the y-system is reconstructed (fewer live registers)
     const CoefRegs<T> ccr{cc};
     const CoefShared<double> ccsh{ccs};
+    double* dw = nullptr;
+    if constexpr (DR) {
+      if (i >= -1 && i <= g.nx && j >= -1 && j <= g.ny) dw = w.dr + c;
+    }
     if constexpr (OFF) recon_dir<T, 0, double, REC>(ccr, sl, ctr, cs, eps, face, volx, mx, nullptr, g.ps);
-    else recon_dir<T, 0, double, REC>(ccsh, sl, ctr, cs, eps, face, volx, mx, REC ? w.yrec + c : nullptr, g.ps);
+    else
+      recon_dir<T, 0, double, REC>(ccsh, sl, ctr, cs, eps, face, volx, mx, REC ? w.yrec + c : nullptr, g.ps,
+                                   DR ? dw : nullptr);
     if (interior) {
 #pragma unroll
       for (int v = 0; v < 4; v++) mom[(long long)v * g.ps + c] = mx[v];
@@ -96,7 +104,8 @@ __device__ __forceinline__ void cons_body(const Grid& g, const double* __restric
     if constexpr (OFF) recon_dir<T, 1, double, REC>(ccr, sl, ctr, cs, eps, face + 6, vol, my, nullptr, g.ps);
     else
       recon_dir<T, 1, double, REC>(ccsh, sl, ctr, cs, eps, face + 6, vol, my,
-                                   REC ? w.yrec + 72 * g.ps + c : nullptr, g.ps);
+                                   REC ? w.yrec + 72 * g.ps + c : nullptr, g.ps,
+                                   DR && dw ? dw + 60 * g.ps : nullptr);
 #pragma unroll
     for (int v = 0; v < 4; v++) {
 #pragma unroll
@@ -281,6 +290,122 @@ __device__ __forceinline__ void grad_body(const Grid& g, const Work& w, int gx, 
 #pragma unroll
     for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = OFF ? cen + (double)vv[k] : (double)vv[k];
   }
+}
+
+// ---------------------------------------------------------------------------
+// HWENO-DR viscous gradients (Sec. 3.1) of cells of the interior grown by 1.  The
+// nonlinear weights are constant over the cell, so the combination of the candidates'
+// derivatives is the derivative of the combined polynomial that cons_body stored per
+// characteristic field and direction (Work::dr).  The back-transform to conserved
+// variables is linear, so it is applied to the coefficients: P_d = R_d C_d, one
+// conservative quartic per variable and direction.  Each direction's polynomials give
+// the xi/eta derivatives at its own face points; the volume points use the mean of the
+// two directions' polynomials, as the volume values do.  The chain rule of u = m/rho,
+// v = n/rho, e = E/rho - (u^2+v^2)/2 takes the state the fluxes use at the point (the
+// limited face traces, the volume values; primitive in Work::face and Work::vol) and
+// gives the gradients at the 21 points in the layout k_grad writes (Work::gr).
+// Per-thread scratch in dynamic shared memory, [120][DR_THREADS] doubles: this
+// direction's polynomials and the running mean (blocks of DR_THREADS threads).
+constexpr int DR_THREADS = 64;
+constexpr int DR_SMEM_BYTES = 120 * DR_THREADS * 8;
+
+// (u_x, u_y, v_x, v_y, e_x, e_y) from the primitive state w = (rho, u, v, e) and the
+// conserved variables' derivatives Ux, Uy
+__device__ __forceinline__ void dissip_grad(const double* w, const double* Ux, const double* Uy, double* gr) {
+  const double rr = 1.0 / w[0];
+  const double u = w[1], v = w[2], en = w[3] + 0.5 * (u * u + v * v);
+  const double ux = (Ux[1] - u * Ux[0]) * rr, vx = (Ux[2] - v * Ux[0]) * rr;
+  const double uy = (Uy[1] - u * Uy[0]) * rr, vy = (Uy[2] - v * Uy[0]) * rr;
+  gr[0] = ux;
+  gr[1] = uy;
+  gr[2] = vx;
+  gr[3] = vy;
+  gr[4] = (Ux[3] - en * Ux[0]) * rr - (u * ux + v * vx);
+  gr[5] = (Uy[3] - en * Uy[0]) * rr - (u * uy + v * vy);
+}
+
+// three points (one face of direction DIR, side S; or, with DIR = 2, volume row S) of
+// the polynomials at P ([60][DR_THREADS]), point indices k0 .. k0+2: derivatives,
+// then the gradients with the primitive state at prim (the point sets of Work::face or
+// Work::vol, point k0 - kp first)
+template <int DIR, int S>
+__device__ __forceinline__ void dr_points(const Grid& g, const Work& w, long long c, const double* P, int k0,
+                                          const double* prim, int kp) {
+  double dx[4][3], dy[4][3];
+#pragma unroll
+  for (int v = 0; v < 4; v++) {
+    double cv[15], d[15];
+#pragma unroll
+    for (int k = 0; k < 15; k++) cv[k] = P[(15 * v + k) * DR_THREADS];
+    poly_dxi<double>(cv, d);
+    if (DIR == 0) eval_xface<double, S>(d, dx[v]);
+    else if (DIR == 1) eval_yface<double, S>(d, dx[v]);
+    else eval_vrow<double, S>(d, dx[v]);
+    poly_deta<double>(cv, d);
+    if (DIR == 0) eval_xface<double, S>(d, dy[v]);
+    else if (DIR == 1) eval_yface<double, S>(d, dy[v]);
+    else eval_vrow<double, S>(d, dy[v]);
+    // one variable's coefficients live at a time: the next variable's loads wait here
+    asm volatile("" ::: "memory");
+  }
+#pragma unroll
+  for (int p = 0; p < 3; p++) {
+    const int kk = k0 - kp + p;
+    const double st[4] = {prim[(long long)(4 * kk) * g.ps + c], prim[(long long)(4 * kk + 1) * g.ps + c],
+                          prim[(long long)(4 * kk + 2) * g.ps + c], prim[(long long)(4 * kk + 3) * g.ps + c]};
+    const double Ux[4] = {dx[0][p] * g.rdx, dx[1][p] * g.rdx, dx[2][p] * g.rdx, dx[3][p] * g.rdx};
+    const double Uy[4] = {dy[0][p] * g.rdy, dy[1][p] * g.rdy, dy[2][p] * g.rdy, dy[3][p] * g.rdy};
+    double gr[6];
+    dissip_grad(st, Ux, Uy, gr);
+#pragma unroll
+    for (int n = 0; n < 6; n++) w.gr[(long long)(6 * (k0 + p) + n) * g.ps + c] = gr[n];
+  }
+}
+
+// direction DIR: its conservative polynomials into P, half of them into the mean Pv,
+// then the gradients at its six face points
+template <int DIR>
+__device__ __forceinline__ void dr_direction(const Grid& g, const Work& w, long long c, const CharState<double>& cs,
+                                             double* P, double* Pv) {
+  const double* C = w.dr + (long long)(60 * DIR) * g.ps + c;
+#pragma unroll
+  for (int k = 0; k < 15; k++) {
+    const double y[4] = {C[(long long)k * g.ps], C[(long long)(15 + k) * g.ps], C[(long long)(30 + k) * g.ps],
+                         C[(long long)(45 + k) * g.ps]};
+    double x[4];
+    from_char<double, DIR>(cs, y, x);
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      P[(15 * v + k) * DR_THREADS] = x[v];
+      double* m = Pv + (15 * v + k) * DR_THREADS;
+      *m = DIR == 0 ? 0.5 * x[v] : *m + 0.5 * x[v];
+    }
+  }
+  // a compiler barrier: the evaluations below reload the coefficients from the slot
+  asm volatile("" ::: "memory");
+  dr_points<DIR, 0>(g, w, c, P, 6 * DIR, w.face, 0);
+  dr_points<DIR, 1>(g, w, c, P, 6 * DIR + 3, w.face, 0);
+  asm volatile("" ::: "memory");
+}
+
+__device__ __forceinline__ void dr_body(const Grid& g, const double* __restrict__ q, const Work& w, int gx,
+                                        int gy) {
+  const int i = gx - 1;
+  const int j = gy - 1;
+  if (i >= g.nx + 1 || j >= g.ny + 1) return;
+  extern __shared__ double dr_smem[];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  double* P = dr_smem + tid;
+  double* Pv = dr_smem + 60 * DR_THREADS + tid;
+  const long long c = cidx(g, i, j);
+  const double ub[4] = {q[c], q[g.ps + c], q[2 * g.ps + c], q[3 * g.ps + c]};
+  CharState<double> cs;
+  char_state<double>(ub, g.gamma, cs);
+  dr_direction<0>(g, w, c, cs, P, Pv);
+  dr_direction<1>(g, w, c, cs, P, Pv);
+  dr_points<2, 0>(g, w, c, Pv, 12, w.vol, 12);
+  dr_points<2, 1>(g, w, c, Pv, 15, w.vol, 12);
+  dr_points<2, 2>(g, w, c, Pv, 18, w.vol, 12);
 }
 
 // PP local Lax-Friedrichs fluxes (Eq. (3.3)) of the interior faces: x-faces right

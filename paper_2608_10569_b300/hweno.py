@@ -22,7 +22,11 @@ HWENO_ERR_TIMEOUT = -5
 HWENO_ERR_STATE = -6
 HWENO_FP64 = 0
 HWENO_MIXED = 1
+HWENO_SCHEME_GR = 0
+HWENO_SCHEME_DR = 1
 BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3}
+SCHEME = {"gr": HWENO_SCHEME_GR, "dr": HWENO_SCHEME_DR, HWENO_SCHEME_GR: HWENO_SCHEME_GR,
+          HWENO_SCHEME_DR: HWENO_SCHEME_DR}
 
 # kernel indices of hweno_profile_read
 KERNELS = ["ghost", "cons_recon", "face_moments", "weak_moments", "grad_recon", "flux", "assemble",
@@ -133,7 +137,7 @@ def _check(h, rc):
 
 def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
                 bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
-                max_halvings=20, precision="fp64", **_ignored):
+                max_halvings=20, precision="fp64", scheme="gr", **_ignored):
     c = hweno_config()
     load().hweno_config_default(ctypes.byref(c))
     c.nx, c.ny = int(nx), int(ny)
@@ -144,6 +148,7 @@ def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1
     c.cfl, c.b_visc, c.eps_pp, c.eps_weno = float(cfl), float(b_visc), float(eps_pp), float(eps_weno)
     c.max_halvings = int(max_halvings)
     c.precision = HWENO_MIXED if precision in ("mixed", HWENO_MIXED) else HWENO_FP64
+    c.scheme = SCHEME[scheme]
     return c
 
 

@@ -92,3 +92,26 @@ def test_gpu_and_oracle_tables_agree():
             else:
                 B[i_, j_] = B[j_, i_] = float(v) / 2
     assert np.abs(B - Bx).max() <= 1e-13 * np.abs(Bx).max()
+
+
+def test_scheme_is_validated_before_any_device_call(lib):
+    """HWENO_SCHEME_DR is accepted for FP64 handles only; an unknown scheme, DR with
+    the mixed precision, a DR case in a batch and DR in hweno_residual_noalloc are
+    refused on the host"""
+    from paper_2608_10569_b300 import hweno
+    h = ctypes.c_void_p()
+    for kw in (dict(scheme="dr", precision="mixed"),):
+        c = hweno.make_config(8, 8, **kw)
+        assert lib.hweno_init(ctypes.byref(c), None, ctypes.byref(h)) == hweno.HWENO_ERR_ARG
+        assert b"FP64" in lib.hweno_last_error(None)
+    c = hweno.make_config(8, 8)
+    c.scheme = 2
+    assert lib.hweno_init(ctypes.byref(c), None, ctypes.byref(h)) == hweno.HWENO_ERR_ARG
+    cfgs = (hweno.hweno_config * 2)(hweno.make_config(8, 8), hweno.make_config(8, 8, scheme="dr"))
+    b = ctypes.c_void_p()
+    assert lib.hweno_batch_init(cfgs, 2, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
+    assert b.value is None
+    buf = (ctypes.c_double * 12)()
+    c = hweno.make_config(8, 8, scheme="dr")
+    assert lib.hweno_residual_noalloc(ctypes.byref(c), buf, buf, None, None) == hweno.HWENO_ERR_ARG
+    assert b"GR" in lib.hweno_last_error(None)
