@@ -53,9 +53,9 @@ FLOPS_PER_CELL_FP64 = {
     "grad_recon": 3108.0,
 }
 
-# the same for HWENO-DR's gradient kernel k_dr (profiled under the "grad_recon" slot);
-# empty until counted
-FLOPS_PER_CELL_FP64_DR = {}
+# the same for HWENO-DR's gradient kernel k_dr, profiled under the "grad_recon" slot
+# (profiles/dr_kernels_shock_tube_256x128.md)
+FLOPS_PER_CELL_FP64_DR = {"grad_recon": 3204.0}
 
 # DRAM bytes of one cons_recon (k_cons<double>) launch on the 1024x512 shock tube,
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this build
