@@ -55,7 +55,7 @@ FLOPS_PER_CELL_FP64 = {
 
 # the same for HWENO-DR's gradient kernel k_dr, profiled under the "grad_recon" slot
 # (profiles/dr_kernels_shock_tube_256x128.md)
-FLOPS_PER_CELL_FP64_DR = {"grad_recon": 3204.0}
+FLOPS_PER_CELL_FP64_DR = {"grad_recon": 2782.0}
 
 # DRAM bytes of one cons_recon (k_cons<double>) launch on the 1024x512 shock tube,
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this build

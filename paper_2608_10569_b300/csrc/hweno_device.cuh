@@ -212,56 +212,22 @@ __device__ __forceinline__ void eval_vol(const T* c, T* out) {
   out[6] = v[0]; out[7] = v[1]; out[8] = v[2];
 }
 
-// partial derivatives of a quartic in the scaled coordinates, as quartics in the same
-// monomial order (the five quartic slots zero): d/dxi xi^p eta^q = p xi^(p-1) eta^q
+// physical partial derivatives of a quartic in the scaled coordinates, as quartics in
+// the same monomial order (the five quartic slots zero): with f = (r, 2r, 3r, 4r) and
+// r = 1/dx (resp. 1/dy), d/dx xi^p eta^q = p r xi^(p-1) eta^q
 template <class T>
-__device__ __forceinline__ void poly_dxi(const T* c, T* d) {
-  d[0] = c[1]; d[1] = T(2) * c[3]; d[2] = c[4];
-  d[3] = T(3) * c[6]; d[4] = T(2) * c[7]; d[5] = c[8];
-  d[6] = T(4) * c[10]; d[7] = T(3) * c[11]; d[8] = T(2) * c[12]; d[9] = c[13];
+__device__ __forceinline__ void poly_dx(const T* c, const T* f, T* d) {
+  d[0] = f[0] * c[1]; d[1] = f[1] * c[3]; d[2] = f[0] * c[4];
+  d[3] = f[2] * c[6]; d[4] = f[1] * c[7]; d[5] = f[0] * c[8];
+  d[6] = f[3] * c[10]; d[7] = f[2] * c[11]; d[8] = f[1] * c[12]; d[9] = f[0] * c[13];
   d[10] = d[11] = d[12] = d[13] = d[14] = T(0);
 }
 template <class T>
-__device__ __forceinline__ void poly_deta(const T* c, T* d) {
-  d[0] = c[2]; d[1] = c[4]; d[2] = T(2) * c[5];
-  d[3] = c[7]; d[4] = T(2) * c[8]; d[5] = T(3) * c[9];
-  d[6] = c[11]; d[7] = T(2) * c[12]; d[8] = T(3) * c[13]; d[9] = T(4) * c[14];
+__device__ __forceinline__ void poly_dy(const T* c, const T* f, T* d) {
+  d[0] = f[0] * c[2]; d[1] = f[0] * c[4]; d[2] = f[1] * c[5];
+  d[3] = f[0] * c[7]; d[4] = f[1] * c[8]; d[5] = f[2] * c[9];
+  d[6] = f[0] * c[11]; d[7] = f[1] * c[12]; d[8] = f[2] * c[13]; d[9] = f[3] * c[14];
   d[10] = d[11] = d[12] = d[13] = d[14] = T(0);
-}
-// one face or one row of volume points at a time (the pieces of eval_xfaces,
-// eval_yfaces and eval_vol): S = 0 the left (bottom) face, S = 1 the right (top) face;
-// G the volume row xi = xi_G, whose points are 3G + H
-template <class T, int S>
-__device__ __forceinline__ void eval_xface(const T* c, T* out) {
-  T E[5], O[4], a[5];
-  collapse_x<T>(c, T(0.5), E, O);
-#pragma unroll
-  for (int q = 0; q < 4; q++) a[q] = S ? E[q] + O[q] : E[q] - O[q];
-  a[4] = E[4];
-  line3<T>(a, out);
-}
-template <class T, int S>
-__device__ __forceinline__ void eval_yface(const T* c, T* out) {
-  T E[5], O[4], a[5];
-  collapse_y<T>(c, T(0.5), E, O);
-#pragma unroll
-  for (int q = 0; q < 4; q++) a[q] = S ? E[q] + O[q] : E[q] - O[q];
-  a[4] = E[4];
-  line3<T>(a, out);
-}
-template <class T, int G>
-__device__ __forceinline__ void eval_vrow(const T* c, T* out) {
-  T a[5];
-  if (G == 1) {
-    a[0] = c[0]; a[1] = c[2]; a[2] = c[5]; a[3] = c[9]; a[4] = c[14];
-  } else {
-    T E[5], O[4];
-    collapse_x<T>(c, T(GN), E, O);
-#pragma unroll
-    for (int q = 0; q < 4; q++) a[q] = G == 2 ? E[q] + O[q] : E[q] - O[q];
-    a[4] = E[4];
-  }
-  line3<T>(a, out);
 }
 
 // ---------------------------------------------------------------------------

@@ -324,37 +324,18 @@ __device__ __forceinline__ void dissip_grad(const double* w, const double* Ux, c
   gr[5] = (Uy[3] - en * Uy[0]) * rr - (u * uy + v * vy);
 }
 
-// three points (one face of direction DIR, side S; or, with DIR = 2, volume row S) of
-// the polynomials at P ([60][DR_THREADS]), point indices k0 .. k0+2: derivatives,
-// then the gradients with the primitive state at prim (the point sets of Work::face or
-// Work::vol, point k0 - kp first)
-template <int DIR, int S>
-__device__ __forceinline__ void dr_points(const Grid& g, const Work& w, long long c, const double* P, int k0,
-                                          const double* prim, int kp) {
-  double dx[4][3], dy[4][3];
+// the gradients at NP points k0 .. k0+NP-1 from the conserved variables' derivatives
+// dx, dy there and the primitive state of the point sets at prim (point k0 - kp first)
+template <int NP>
+__device__ __forceinline__ void dr_store(const Grid& g, const Work& w, long long c, const double (*dx)[NP],
+                                         const double (*dy)[NP], int k0, const double* prim, int kp) {
 #pragma unroll
-  for (int v = 0; v < 4; v++) {
-    double cv[15], d[15];
-#pragma unroll
-    for (int k = 0; k < 15; k++) cv[k] = P[(15 * v + k) * DR_THREADS];
-    poly_dxi<double>(cv, d);
-    if (DIR == 0) eval_xface<double, S>(d, dx[v]);
-    else if (DIR == 1) eval_yface<double, S>(d, dx[v]);
-    else eval_vrow<double, S>(d, dx[v]);
-    poly_deta<double>(cv, d);
-    if (DIR == 0) eval_xface<double, S>(d, dy[v]);
-    else if (DIR == 1) eval_yface<double, S>(d, dy[v]);
-    else eval_vrow<double, S>(d, dy[v]);
-    // one variable's coefficients live at a time: the next variable's loads wait here
-    asm volatile("" ::: "memory");
-  }
-#pragma unroll
-  for (int p = 0; p < 3; p++) {
+  for (int p = 0; p < NP; p++) {
     const int kk = k0 - kp + p;
     const double st[4] = {prim[(long long)(4 * kk) * g.ps + c], prim[(long long)(4 * kk + 1) * g.ps + c],
                           prim[(long long)(4 * kk + 2) * g.ps + c], prim[(long long)(4 * kk + 3) * g.ps + c]};
-    const double Ux[4] = {dx[0][p] * g.rdx, dx[1][p] * g.rdx, dx[2][p] * g.rdx, dx[3][p] * g.rdx};
-    const double Uy[4] = {dy[0][p] * g.rdy, dy[1][p] * g.rdy, dy[2][p] * g.rdy, dy[3][p] * g.rdy};
+    const double Ux[4] = {dx[0][p], dx[1][p], dx[2][p], dx[3][p]};
+    const double Uy[4] = {dy[0][p], dy[1][p], dy[2][p], dy[3][p]};
     double gr[6];
     dissip_grad(st, Ux, Uy, gr);
 #pragma unroll
@@ -363,10 +344,11 @@ __device__ __forceinline__ void dr_points(const Grid& g, const Work& w, long lon
 }
 
 // direction DIR: its conservative polynomials into P, half of them into the mean Pv,
-// then the gradients at its six face points
+// then the gradients at its six face points (both faces from one collapse per
+// derivative polynomial)
 template <int DIR>
 __device__ __forceinline__ void dr_direction(const Grid& g, const Work& w, long long c, const CharState<double>& cs,
-                                             double* P, double* Pv) {
+                                             const double* fx, const double* fy, double* P, double* Pv) {
   const double* C = w.dr + (long long)(60 * DIR) * g.ps + c;
 #pragma unroll
   for (int k = 0; k < 15; k++) {
@@ -383,9 +365,39 @@ __device__ __forceinline__ void dr_direction(const Grid& g, const Work& w, long 
   }
   // a compiler barrier: the evaluations below reload the coefficients from the slot
   asm volatile("" ::: "memory");
-  dr_points<DIR, 0>(g, w, c, P, 6 * DIR, w.face, 0);
-  dr_points<DIR, 1>(g, w, c, P, 6 * DIR + 3, w.face, 0);
+  double dx[4][6], dy[4][6];
+#pragma unroll
+  for (int v = 0; v < 4; v++) {
+    double cv[15], d[15];
+#pragma unroll
+    for (int k = 0; k < 15; k++) cv[k] = P[(15 * v + k) * DR_THREADS];
+    poly_dx<double>(cv, fx, d);
+    if (DIR == 0) eval_xfaces<double>(d, dx[v]); else eval_yfaces<double>(d, dx[v]);
+    poly_dy<double>(cv, fy, d);
+    if (DIR == 0) eval_xfaces<double>(d, dy[v]); else eval_yfaces<double>(d, dy[v]);
+    // one variable's coefficients live at a time: the next variable's loads wait here
+    asm volatile("" ::: "memory");
+  }
+  dr_store<6>(g, w, c, dx, dy, 6 * DIR, w.face, 0);
   asm volatile("" ::: "memory");
+}
+
+// the volume points from the mean of the two directions' polynomials
+__device__ __forceinline__ void dr_volume(const Grid& g, const Work& w, long long c, const double* fx,
+                                          const double* fy, const double* Pv) {
+  double dx[4][9], dy[4][9];
+#pragma unroll
+  for (int v = 0; v < 4; v++) {
+    double cv[15], d[15];
+#pragma unroll
+    for (int k = 0; k < 15; k++) cv[k] = Pv[(15 * v + k) * DR_THREADS];
+    poly_dx<double>(cv, fx, d);
+    eval_vol<double>(d, dx[v]);
+    poly_dy<double>(cv, fy, d);
+    eval_vol<double>(d, dy[v]);
+    asm volatile("" ::: "memory");
+  }
+  dr_store<9>(g, w, c, dx, dy, 12, w.vol, 12);
 }
 
 __device__ __forceinline__ void dr_body(const Grid& g, const double* __restrict__ q, const Work& w, int gx,
@@ -401,11 +413,12 @@ __device__ __forceinline__ void dr_body(const Grid& g, const double* __restrict_
   const double ub[4] = {q[c], q[g.ps + c], q[2 * g.ps + c], q[3 * g.ps + c]};
   CharState<double> cs;
   char_state<double>(ub, g.gamma, cs);
-  dr_direction<0>(g, w, c, cs, P, Pv);
-  dr_direction<1>(g, w, c, cs, P, Pv);
-  dr_points<2, 0>(g, w, c, Pv, 12, w.vol, 12);
-  dr_points<2, 1>(g, w, c, Pv, 15, w.vol, 12);
-  dr_points<2, 2>(g, w, c, Pv, 18, w.vol, 12);
+  // the derivative factors p/dx, p/dy of the monomials' exponents p = 1..4
+  const double fx[4] = {g.rdx, 2.0 * g.rdx, 3.0 * g.rdx, 4.0 * g.rdx};
+  const double fy[4] = {g.rdy, 2.0 * g.rdy, 3.0 * g.rdy, 4.0 * g.rdy};
+  dr_direction<0>(g, w, c, cs, fx, fy, P, Pv);
+  dr_direction<1>(g, w, c, cs, fx, fy, P, Pv);
+  dr_volume(g, w, c, fx, fy, Pv);
 }
 
 // PP local Lax-Friedrichs fluxes (Eq. (3.3)) of the interior faces: x-faces right
