@@ -27,6 +27,7 @@
  *   SSP-RK3 with modified moments ......... Eq. (2.10) and its 2D analogue (Sec. 3.1)
  *   time step, restart .................... Sec. 5 (CFL, b*Re*h^2, halving), Sec. 4
  *   ghost cells ........................... Remark 4.1
+ *   manufactured source ................... Example 5.2 (fields, S = U_t + F_x + G_y)
  *
  * Readings where the paper is silent (also listed in the design notes):
  *   smoothness indicator  classical integral form in scaled coordinates (gen_tables.py)
@@ -68,6 +69,9 @@ typedef struct {
     int linear_weights; /* 1: omega_m = gamma_m (used only by exactness pins) */
     int limiter;        /* 1: PP limiter active */
     int scheme;         /* viscous gradients: 0 HWENO-GR (Sec. 3.2), 1 HWENO-DR (Sec. 3.1) */
+    int source;         /* 1: Example 5.2's manufactured source added to every residual */
+    int pad2_;
+    double time;        /* time of a residual evaluation (the source's t) */
 } or_cfg;
 
 /* linear weights of Appendix A.2 */
@@ -750,6 +754,88 @@ static void or_assemble_cell(or_work* W, int i, int j, double dx, double dy, dou
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Example 5.2: manufactured solution and its source term              */
+/* one manufactured field  base + 0.1 e^{-t} (sin(2 pi (a1 x + b1 y)) + cos(2 pi (a2 x + b2 y)))
+ * with its t-, first and second space derivatives; w = 0 rho, 1 u, 2 v, 3 e */
+typedef struct { double f, ft, fx, fy, fxx, fxy, fyy; } or_mfield;
+
+static void or_mms_field(int w, double x, double y, double t, or_mfield* F) {
+    static const double base[4] = {2.0, 1.0, 2.0, 2.0};
+    static const double ab[4][4] = {{2, -1, -1, 2}, {-1, 1, 1, 1}, {1, 1, 1, -1}, {1, -1, 1, 1}};
+    const double tp = 6.283185307179586476925286766559;
+    double a1 = ab[w][0], b1 = ab[w][1], a2 = ab[w][2], b2 = ab[w][3];
+    double amp = 0.1 * exp(-t);
+    double p1 = tp * (a1 * x + b1 * y), p2 = tp * (a2 * x + b2 * y);
+    double s1 = sin(p1), c1 = cos(p1), s2 = sin(p2), c2 = cos(p2);
+    F->f = base[w] + amp * (s1 + c2);
+    F->ft = -amp * (s1 + c2);
+    F->fx = amp * tp * (a1 * c1 - a2 * s2);
+    F->fy = amp * tp * (b1 * c1 - b2 * s2);
+    F->fxx = -amp * tp * tp * (a1 * a1 * s1 + a2 * a2 * c2);
+    F->fxy = -amp * tp * tp * (a1 * b1 * s1 + a2 * b2 * c2);
+    F->fyy = -amp * tp * tp * (b1 * b1 * s1 + b2 * b2 * c2);
+}
+
+/* S = U_t + F_x + G_y at (x, y, t) for the manufactured fields: the equations of
+ * Example 5.2 (the fluxes of Sec. 3.1), differentiated by the product and chain rules */
+static void or_mms_source(const or_cfg* c, double x, double y, double t, double S[4]) {
+    or_mfield R, U, V, Q;
+    or_mms_field(0, x, y, t, &R);
+    or_mms_field(1, x, y, t, &U);
+    or_mms_field(2, x, y, t, &V);
+    or_mms_field(3, x, y, t, &Q);
+    double g = c->gamma, Re = c->Re, Pr = c->Pr;
+    double rho = R.f, u = U.f, v = V.f, e = Q.f;
+    /* momenta m = rho u, n = rho v */
+    double m = rho * u, m_t = R.ft * u + rho * U.ft, m_x = R.fx * u + rho * U.fx, m_y = R.fy * u + rho * U.fy;
+    double n = rho * v, n_t = R.ft * v + rho * V.ft, n_x = R.fx * v + rho * V.fx, n_y = R.fy * v + rho * V.fy;
+    /* total energy E = rho (e + k), k = (u^2 + v^2)/2; pressure p = (g - 1) rho e */
+    double k = 0.5 * (u * u + v * v);
+    double k_t = u * U.ft + v * V.ft, k_x = u * U.fx + v * V.fx, k_y = u * U.fy + v * V.fy;
+    double E = rho * (e + k);
+    double E_t = R.ft * (e + k) + rho * (Q.ft + k_t);
+    double E_x = R.fx * (e + k) + rho * (Q.fx + k_x);
+    double E_y = R.fy * (e + k) + rho * (Q.fy + k_y);
+    double p = (g - 1.0) * rho * e;
+    double p_x = (g - 1.0) * (R.fx * e + rho * Q.fx), p_y = (g - 1.0) * (R.fy * e + rho * Q.fy);
+    /* viscous stresses and their derivatives */
+    double txx = (4.0 * U.fx - 2.0 * V.fy) / 3.0, txy = U.fy + V.fx, tyy = (4.0 * V.fy - 2.0 * U.fx) / 3.0;
+    double txx_x = (4.0 * U.fxx - 2.0 * V.fxy) / 3.0, tyy_y = (4.0 * V.fyy - 2.0 * U.fxy) / 3.0;
+    double txy_x = U.fxy + V.fxx, txy_y = U.fyy + V.fxy;
+    /* x- and y-derivatives of the viscous energy fluxes txx u + txy v + g/Pr e_x and
+     * txy u + tyy v + g/Pr e_y */
+    double hx_x = txx_x * u + txx * U.fx + txy_x * v + txy * V.fx + g / Pr * Q.fxx;
+    double hy_y = txy_y * u + txy * U.fy + tyy_y * v + tyy * V.fy + g / Pr * Q.fyy;
+    S[0] = R.ft + m_x + n_y;
+    S[1] = m_t + (m_x * u + m * U.fx) + p_x + (m_y * v + m * V.fy) - (txx_x + txy_y) / Re;
+    S[2] = n_t + (n_x * u + n * U.fx) + (n_y * v + n * V.fy) + p_y - (txy_x + tyy_y) / Re;
+    S[3] = E_t + (E_x + p_x) * u + (E + p) * U.fx + (E_y + p_y) * v + (E + p) * V.fy - (hx_x + hy_y) / Re;
+}
+
+/* cell average and scaled first moments of S over cell (i, j) at time t: 4-point
+ * Gauss-Legendre per direction (nodes +-sqrt(3/7 -+ 2/7 sqrt(6/5)), weights
+ * (18 +- sqrt(30))/36 on [-1, 1], halved onto the scaled cell [-1/2, 1/2]) */
+static void or_mms_moments(const or_cfg* c, int i, int j, double t, double out[12]) {
+    double dx = (c->x1 - c->x0) / c->nx, dy = (c->y1 - c->y0) / c->ny;
+    double xc = c->x0 + (i + 0.5) * dx, yc = c->y0 + (j + 0.5) * dy;
+    double ri = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0)), ro = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+    double wi = (18.0 + sqrt(30.0)) / 36.0, wo = (18.0 - sqrt(30.0)) / 36.0;
+    double nd[4] = {-0.5 * ro, -0.5 * ri, 0.5 * ri, 0.5 * ro}, wt[4] = {0.5 * wo, 0.5 * wi, 0.5 * wi, 0.5 * wo};
+    for (int k = 0; k < 12; k++) out[k] = 0.0;
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) {
+            double S[4];
+            or_mms_source(c, xc + nd[a] * dx, yc + nd[b] * dy, t, S);
+            double w = wt[a] * wt[b];
+            for (int v = 0; v < 4; v++) {
+                out[v] += w * S[v];
+                out[4 + v] += w * nd[a] * S[v];
+                out[8 + v] += w * nd[b] * S[v];
+            }
+        }
+}
+
 static int or_work_alloc(or_work* W, const or_cfg* c, int bx, int by) {
     memset(W, 0, sizeof(*W));
     W->c = c;
@@ -825,6 +911,11 @@ static int or_region(const or_cfg* c, const double* q, int ox, int oy, int wx, i
         for (int i = 0; i < wx; i++) {
             double r[12];
             or_assemble_cell(&W, i, j, dx, dy, r);
+            if (c->source == 1) { /* Example 5.2: dU/dt = R(U) + S */
+                double sm[12];
+                or_mms_moments(c, ox + i, oy + j, c->time, sm);
+                for (int k = 0; k < 12; k++) r[k] += sm[k];
+            }
             size_t at = (size_t)j * wx + i;
             for (int k = 0; k < 12; k++) {
                 if (rhs) rhs[k * n + at] = r[k];
@@ -938,7 +1029,10 @@ int or_step(const or_cfg* c, double* q, double t, double t_end, double dt_fixed,
     double diag[OR_NDIAG];
     int status = 0;
     for (int k = 0; k < 6; k++) stats[k] = 0.0;
-    or_residual(c, q, r0, m0, diag, NULL, NULL, NULL, NULL, NULL);
+    /* stage times of the SSP-RK3 step (a source term's t): t, t + dt, t + dt/2 */
+    or_cfg cs = *c;
+    cs.time = t;
+    or_residual(&cs, q, r0, m0, diag, NULL, NULL, NULL, NULL, NULL);
     double bmax = diag[1], act = diag[2];
     stats[2] = diag[0];
     double h = (c->x1 - c->x0) / c->nx;
@@ -965,7 +1059,8 @@ int or_step(const or_cfg* c, double* q, double t, double t_end, double dt_fixed,
             }
         ok = or_admissible(c, q1);
         if (ok) {
-            or_residual(c, q1, r, m, diag, NULL, NULL, NULL, NULL, NULL);
+            cs.time = t + dt;
+            or_residual(&cs, q1, r, m, diag, NULL, NULL, NULL, NULL, NULL);
             if (diag[1] > sb) sb = diag[1];
             sa += diag[2];
             for (size_t k = 0; k < n; k++)
@@ -977,7 +1072,8 @@ int or_step(const or_cfg* c, double* q, double t, double t_end, double dt_fixed,
             ok = or_admissible(c, q2);
         }
         if (ok) {
-            or_residual(c, q2, r, m, diag, NULL, NULL, NULL, NULL, NULL);
+            cs.time = t + 0.5 * dt;
+            or_residual(&cs, q2, r, m, diag, NULL, NULL, NULL, NULL, NULL);
             if (diag[1] > sb) sb = diag[1];
             sa += diag[2];
             for (size_t k = 0; k < n; k++)
@@ -1072,6 +1168,12 @@ int or_hweno_scalar_dr(const double* d17, double eps, int linear, double* dxi21,
         dxi21[k] = or_hweno_eval_d(&h, 0, xi, eta);
         deta21[k] = or_hweno_eval_d(&h, 1, xi, eta);
     }
+    return 0;
+}
+
+/* Example 5.2's source at a point (unit pins): S[4] */
+int or_mms_source_export(const or_cfg* c, double x, double y, double t, double* S) {
+    or_mms_source(c, x, y, t, S);
     return 0;
 }
 

@@ -12,7 +12,8 @@
  *
  * Derivative rules at the non-smooth points the oracle passes through: |x| and the
  * comparisons act on the value part, d|x| = sign(x) dx with sign(0) = 0, and
- * d sqrt(x) = dx / (2 sqrt(x)).  The step size of a step is an input (dt_fixed), so
+ * d sqrt(x) = dx / (2 sqrt(x)); d sin = cos dx, d cos = -sin dx, d exp = exp dx (the
+ * manufactured source, which depends on mu).  The step size of a step is an input (dt_fixed), so
  * it carries no tangent: the tangent is the one of the map q -> q^{n+1} at fixed dt.
  */
 #include <cmath>
@@ -58,6 +59,12 @@ static inline or_dual fabs(const or_dual& a) {
     return or_dual(std::fabs(a.v), sg * a.d);
 }
 static inline bool isfinite(const or_dual& a) { return std::isfinite(a.v) && std::isfinite(a.d); }
+static inline or_dual sin(const or_dual& a) { return or_dual(std::sin(a.v), std::cos(a.v) * a.d); }
+static inline or_dual cos(const or_dual& a) { return or_dual(std::cos(a.v), -std::sin(a.v) * a.d); }
+static inline or_dual exp(const or_dual& a) {
+    const double e = std::exp(a.v);
+    return or_dual(e, e * a.d);
+}
 
 /* the oracle, with every double a dual number */
 #define double or_dual
@@ -72,6 +79,8 @@ typedef struct {
     int bc[4];
     double cfl, b_visc, eps_pp, eps_weno;
     int max_halvings, linear_weights, limiter, scheme;
+    int source, pad2_;
+    double time;
 } or_cfg_plain;
 
 /* the dual configuration: mu = 1/Re moves with tangent dmu, so dRe = -Re^2 dmu */
@@ -88,6 +97,9 @@ static void or_cfg_dual(const or_cfg_plain* a, double dmu, or_cfg* b) {
     b->linear_weights = a->linear_weights;
     b->limiter = a->limiter;
     b->scheme = a->scheme;
+    b->source = a->source;
+    b->pad2_ = 0;
+    b->time = a->time;
 }
 
 extern "C" {

@@ -31,6 +31,8 @@ BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3}
 # viscous gradients: HWENO-GR (weak-derivative moments) or HWENO-DR (differentiated
 # convective candidates, the comparison scheme)
 SCHEME = {"gr": 0, "dr": 1, 0: 0, 1: 1}
+# source terms: none, or Example 5.2's manufactured source
+SOURCE = {None: 0, "none": 0, "mms52": 1, 0: 0, 1: 1}
 
 
 class _Cfg(ctypes.Structure):
@@ -42,7 +44,8 @@ class _Cfg(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("b_visc", ctypes.c_double),
                 ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("linear_weights", ctypes.c_int),
-                ("limiter", ctypes.c_int), ("scheme", ctypes.c_int)]
+                ("limiter", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("source", ctypes.c_int), ("pad2_", ctypes.c_int), ("time", ctypes.c_double)]
 
 
 def build(force=False):
@@ -84,6 +87,8 @@ def _load():
                                        ctypes.c_int, dp]
             lib.or_fill_ghosts.argtypes = [ctypes.POINTER(_Cfg), dp, dp]
             lib.or_hweno_scalar.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp]
+            lib.or_mms_source_export.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, dp]
             lib.or_hweno_scalar_dr.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp, dp]
             lib.or_theta_root_export.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double]
             lib.or_theta_root_export.restype = ctypes.c_double
@@ -100,7 +105,8 @@ def _ptr(a):
 
 def make_cfg(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
              bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
-             max_halvings=20, linear_weights=False, limiter=True, scheme="gr", **_ignored):
+             max_halvings=20, linear_weights=False, limiter=True, scheme="gr", source=0, time=0.0,
+             **_ignored):
     c = _Cfg()
     c.nx, c.ny = int(nx), int(ny)
     c.x0, c.x1, c.y0, c.y1 = float(x0), float(x1), float(y0), float(y1)
@@ -112,6 +118,8 @@ def make_cfg(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000
     c.linear_weights = 1 if linear_weights else 0
     c.limiter = 1 if limiter else 0
     c.scheme = SCHEME[scheme]
+    c.source = SOURCE[source]
+    c.time = float(time)
     mirror = any(c.bc[k] != 0 for k in range(4))
     if mirror and (c.nx < 4 or c.ny < 4):
         raise ValueError("mirror boundaries need at least 4 cells per direction")
@@ -213,6 +221,14 @@ def hweno_scalar_dr(d17, eps=1e-8, linear=False):
     dxi, deta = np.zeros(21), np.zeros(21)
     lib.or_hweno_scalar_dr(_ptr(d17), float(eps), 1 if linear else 0, _ptr(dxi), _ptr(deta))
     return dxi, deta
+
+
+def mms_source(cfg, x, y, t):
+    """Example 5.2's source S(x, y, t) (4,) at one point."""
+    lib = _load()
+    S = np.zeros(4)
+    lib.or_mms_source_export(ctypes.byref(cfg), float(x), float(y), float(t), _ptr(S))
+    return S
 
 
 def theta_root(ub, uq, eps, gamma):

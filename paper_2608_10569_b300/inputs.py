@@ -38,6 +38,7 @@ class Case:
     eps_pp: float = 1e-12
     eps_weno: float = 1e-8
     max_halvings: int = 20
+    source: int = 0          # 1: Example 5.2's manufactured source term
     t_end: float = 0.0
     extra: dict = field(default_factory=dict)
 
@@ -238,6 +239,26 @@ def adjoint_target(case, seed=5, modes=8, amp=0.01):
 
 # ---------------------------------------------------------------------------
 # generic seeded states for parity tests
+
+
+def manufactured_prim(x, y, t, gamma=1.4):
+    """Example 5.2's manufactured solution at time t as primitive fields (rho, u, v, p),
+    with p = (gamma - 1) rho e."""
+    a = 0.1 * np.exp(-t)
+    tp = 2 * np.pi
+    rho = 2 + a * (np.sin(tp * (2 * x - y)) + np.cos(tp * (-x + 2 * y)))
+    u = 1 + a * (np.sin(tp * (-x + y)) + np.cos(tp * (x + y)))
+    v = 2 + a * (np.sin(tp * (x + y)) + np.cos(tp * (x - y)))
+    e = 2 + a * (np.sin(tp * (x - y)) + np.cos(tp * (x + y)))
+    return rho, u, v, (gamma - 1) * rho * e
+
+
+def manufactured(n, t=0.0, Re=100.0):
+    """Example 5.2: [0,1]^2 periodic, gamma 1.4, Pr 0.72, Re 100, the manufactured source
+    switched on, T = 0.1; the cell moments of the exact solution at time t (t = 0 the
+    initial state, t = T the reference of the error table)."""
+    case = Case("manufactured_%d" % n, n, n, 0.0, 1.0, 0.0, 1.0, 1.4, 0.72, Re, source=1, t_end=0.1)
+    return case, cell_moments(case, lambda x, y: manufactured_prim(x, y, t, case.gamma))
 
 
 def random_smooth(nx, ny, seed=0, bc=("periodic",) * 4, gamma=1.4, Re=500.0, Pr=0.72,
