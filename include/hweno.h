@@ -67,6 +67,14 @@ extern "C" {
 #define HWENO_SCHEME_DR 1 /* differentiated characteristic candidates with the convective
                              weights (Sec. 3.1); fourth order; HWENO_FP64 only */
 
+/* source terms added to the spatial operator (dU/dt = R(U) + S(t)) */
+#define HWENO_SOURCE_NONE 0
+#define HWENO_SOURCE_MMS52 1 /* Example 5.2's manufactured source: S = U_t + F_x + G_y of
+                                its manufactured fields, for any domain, gamma, Pr and Re;
+                                cell average and scaled moments by 4x4 Gauss quadrature,
+                                at the handle's time (hweno_set_time) in hweno_residual and
+                                at t^n, t^n + dt, t^n + dt/2 in the stages of a step */
+
 typedef struct hweno_handle hweno_handle;
 
 /* Problem statement (Sec. 3.1, Sec. 5).  Uniform cells dx = (x1-x0)/nx,
@@ -85,7 +93,7 @@ typedef struct {
     int precision;            /* HWENO_FP64 or HWENO_MIXED */
     int scheme;               /* HWENO_SCHEME_GR or HWENO_SCHEME_DR (handles only: the
                                  adjoint, the batch and hweno_residual_noalloc take GR) */
-    int reserved;             /* must be 0 */
+    int source;               /* HWENO_SOURCE_NONE or HWENO_SOURCE_MMS52 (handles only) */
 } hweno_config;
 
 /* Diagnostics of the run so far (Sec. 5: PP-limiter percentage; Remark 3.1:
@@ -171,8 +179,9 @@ int hweno_debug_fields(hweno_handle* h, int which, double* out, int on_device);
 /* Kernel timing of the residual's dominant kernel: enable = 1 records CUDA events
  * around every launch of each kernel of the spatial operator; hweno_profile_read
  * returns, for kernel index k (0 ghost, 1 conservative reconstruction, 2 face
- * moments, 3 weak moments, 4 gradient reconstruction, 5 face fluxes, 6 assembly,
- * 7 RK update), the launches and the summed device milliseconds since enabling.
+ * moments, 3 weak moments, 4 gradient reconstruction (k_dr under HWENO_SCHEME_DR),
+ * 5 face fluxes, 6 assembly, 7 RK update, 8 source term), the launches and the summed
+ * device milliseconds since enabling.
  * Reading synchronises the stream. */
 int hweno_profile(hweno_handle* h, int enable);
 int hweno_profile_read(hweno_handle* h, int kernel, long long* launches, double* total_ms);
@@ -204,7 +213,7 @@ long long hweno_launch_count(const hweno_handle* h);
  * discrete scheme. */
 
 /* Allocate the adjoint buffers (about 6.3 KB per padded cell); FP64 HWENO-GR handles
- * only (HWENO_ERR_ARG otherwise). */
+ * without a source term only (HWENO_ERR_ARG otherwise). */
 int hweno_adjoint_init(hweno_handle* h);
 
 /* xbar = (dR/dx)^T rbar + (dM/dx)^T mbar and *mubar = d<rbar, R>/dmu + d<mbar, M>/dmu
@@ -267,7 +276,7 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 typedef struct hweno_batch hweno_batch;
 
 /* Create ncases solvers (cfgs[0..ncases-1], as for hweno_init, all with the same
- * precision and HWENO_SCHEME_GR) sharing one stream; NULL stream: the batch creates its
+ * precision, HWENO_SCHEME_GR and no source term) sharing one stream; NULL stream: the batch creates its
  * own non-blocking stream (graph capture needs one).  Allocates everything.  Errors as
  * hweno_init. */
 int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_batch** out);
@@ -300,7 +309,7 @@ long long hweno_batch_launch_count(const hweno_batch* b);
  * take cudaMalloc's implicit device-wide synchronisation.  The paper has no
  * counterpart: this is a deployment variant of the same evaluation.
  *
- * No handle: cfg describes the problem as for hweno_init (HWENO_SCHEME_GR only).
+ * No handle: cfg describes the problem as for hweno_init (HWENO_SCHEME_GR, no source).
  * q [3][4][ny][nx] (the
  * state layout above), rhs [3][4][ny][nx] and vhat [2][4][ny][nx] (or NULL) are
  * caller-owned DEVICE buffers on the current device.  All intermediate fields live

@@ -17,6 +17,7 @@
 #include "hweno_mixed.cuh"
 #include "hweno_batch.cuh"
 #include "hweno_adjoint.cuh"
+#include "hweno_source.cuh"
 
 namespace hw {
 
@@ -43,6 +44,11 @@ __global__ void __launch_bounds__(BX * BY) k_cons_dr(Grid g, const double* __res
 // HWENO-DR gradients from those combinations, in place of the gradient reconstruction
 __global__ void __launch_bounds__(DR_THREADS) k_dr(Grid g, const double* __restrict__ q, Work w) {
   dr_body(g, q, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
+// Example 5.2's manufactured source, added to the residual at t0 + cst * dt
+__global__ void __launch_bounds__(BX * BY) k_source(Grid g, Quad4 qd, double t0, double cst, const Diag* diag,
+                                                    double* __restrict__ rhs) {
+  source_body(g, qd, t0, cst, diag, rhs, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 __global__ void __launch_bounds__(BX * BY) k_grad_rec(Grid g, Work w) {
   grad_body<double, true>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
@@ -191,7 +197,7 @@ using namespace hw;
 
 namespace {
 
-enum { K_GHOST = 0, K_CONS, K_FACEMOM, K_WEAK, K_GRAD, K_FLUX, K_ASSEMBLE, K_RK, K_NKIND };
+enum { K_GHOST = 0, K_CONS, K_FACEMOM, K_WEAK, K_GRAD, K_FLUX, K_ASSEMBLE, K_RK, K_SOURCE, K_NKIND };
 
 struct EventPair {
   cudaEvent_t a, b;
@@ -234,6 +240,7 @@ struct hweno_handle {
   // profiling
   bool prof = false;
   std::vector<EventPair> ev;
+  Quad4 quad{};  // the source term's 4-point Gauss rule
   long long prof_n[K_NKIND];
   double prof_ms[K_NKIND];
   char err[512];
@@ -322,8 +329,9 @@ static cudaError_t cons_smem_allow() {
 }
 
 // one spatial-operator evaluation of state q (12 planes): rhs (12 planes) and the
-// modified moments mom (8 planes)
-static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
+// modified moments mom (8 planes); a source term is taken at t + cst * dt (t the
+// handle's time, dt the device-side step of the current attempt)
+static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, double cst = 0.0) {
   const Grid& g = h->g;
   if (h->cfg.precision == HWENO_MIXED) {
     float* hilo = mixed_planes(h->w, g.ps).hilo;
@@ -414,6 +422,10 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom) {
       k_assemble<double><<<grid2(g.nx, g.ny), dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
     }
   }
+  if (h->cfg.source == HWENO_SOURCE_MMS52) {
+    Prof p(h, K_SOURCE);
+    k_source<<<grid2(g.nx, g.ny), dim3(BX, BY), 0, h->st>>>(g, h->quad, h->t, cst, h->d_diag, rhs);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "spatial operator launch");
   return HWENO_OK;
@@ -483,7 +495,8 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
     return fail(nullptr, HWENO_ERR_ARG, "scheme must be HWENO_SCHEME_GR or HWENO_SCHEME_DR");
   if (c.scheme == HWENO_SCHEME_DR && c.precision != HWENO_FP64)
     return fail(nullptr, HWENO_ERR_ARG, "HWENO_SCHEME_DR runs in HWENO_FP64");
-  if (c.reserved != 0) return fail(nullptr, HWENO_ERR_ARG, "reserved must be 0");
+  if (c.source != HWENO_SOURCE_NONE && c.source != HWENO_SOURCE_MMS52)
+    return fail(nullptr, HWENO_ERR_ARG, "source must be HWENO_SOURCE_NONE or HWENO_SOURCE_MMS52");
 
   h = new (std::nothrow) hweno_handle();
   if (!h) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
@@ -502,6 +515,13 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   g.eps_pp = c.eps_pp; g.eps_weno = c.eps_weno;
   for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
   g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
+  g.x0 = c.x0; g.y0 = c.y0;
+  {  // 4-point Gauss-Legendre on [-1/2, 1/2]: nodes sqrt(3/7 -+ 2/7 sqrt(6/5)) / 2,
+     // weights (18 +- sqrt(30)) / 72
+    const double ri = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0)), ro = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+    const double wi = (18.0 + sqrt(30.0)) / 72.0, wo = (18.0 - sqrt(30.0)) / 72.0;
+    h->quad = Quad4{{-0.5 * ro, -0.5 * ri, 0.5 * ri, 0.5 * ro}, {wo, wi, wi, wo}};
+  }
 
   const long long N = (long long)c.nx * c.ny;
   // planes: Q 12, QS 12, BASE 12, RHS0 12, RHS 12, MOM0 8, MOM 8, face 48, vol 36,
@@ -719,10 +739,11 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
     CK(cudaMemsetAsync(&h->d_diag->flags, 0, sizeof(unsigned int), h->st), "diag");
     if ((rc = launch_rk(h, 1, h->Q, h->MOM0, h->RHS0, q1))) return rc;
     if (keep) h->w = seg_work(h, rec, 1);
-    if ((rc = residual_eval(h, q1, h->RHS, h->MOM))) return rc;
+    // stage times of SSP-RK3 (a source term's t): t^n, t^n + dt, t^n + dt/2
+    if ((rc = residual_eval(h, q1, h->RHS, h->MOM, 1.0))) return rc;
     if ((rc = launch_rk(h, 2, q1, h->MOM, h->RHS, q2))) return rc;
     if (keep) h->w = seg_work(h, rec, 2);
-    if ((rc = residual_eval(h, q2, h->RHS, h->MOM))) return rc;
+    if ((rc = residual_eval(h, q2, h->RHS, h->MOM, 0.5))) return rc;
     if ((rc = launch_rk(h, 3, q2, h->MOM, h->RHS, h->QS))) return rc;
     if ((rc = read_diag(h))) return rc;
     const Diag first = h->h_diag[1];
@@ -950,8 +971,8 @@ extern "C" {
 int hweno_adjoint_init(hweno_handle* h) {
   if (!h) return HWENO_ERR_ARG;
   if (h->cfg.precision != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_FP64");
-  if (h->cfg.scheme != HWENO_SCHEME_GR)
-    return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_SCHEME_GR");
+  if (h->cfg.scheme != HWENO_SCHEME_GR || h->cfg.source != HWENO_SOURCE_NONE)
+    return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_SCHEME_GR without a source term");
   if (h->apool) return HWENO_OK;
   const Grid& g = h->g;
   // R 12, M 8, face 48, vol 36, gr 126, rm 18, cg 102, cc 68, q 12, stage-1 state 12,
@@ -1419,8 +1440,9 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
     if (cfgs[c].precision != cfgs[0].precision)
       return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same precision");
   for (int c = 0; c < ncases; c++)
-    if (cfgs[c].scheme != HWENO_SCHEME_GR)
-      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels run HWENO_SCHEME_GR");
+    if (cfgs[c].scheme != HWENO_SCHEME_GR || cfgs[c].source != HWENO_SOURCE_NONE)
+      return fail(nullptr, HWENO_ERR_ARG,
+                  "hweno_batch_init: the batched kernels run HWENO_SCHEME_GR without a source term");
   hweno_batch* b = new (std::nothrow) hweno_batch();
   if (!b) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
   snprintf(b->err, sizeof(b->err), "no error");
@@ -1691,8 +1713,8 @@ static int noalloc_check_config(const hweno_config& c) {
   if (!(c.eps_pp > 0.0) || !(c.eps_weno > 0.0)) return fail(nullptr, HWENO_ERR_ARG, "eps_pp, eps_weno must be > 0");
   if (c.precision != HWENO_FP64 && c.precision != HWENO_MIXED)
     return fail(nullptr, HWENO_ERR_ARG, "precision must be HWENO_FP64 or HWENO_MIXED");
-  if (c.scheme != HWENO_SCHEME_GR || c.reserved != 0)
-    return fail(nullptr, HWENO_ERR_ARG, "hweno_residual_noalloc runs HWENO_SCHEME_GR (reserved must be 0)");
+  if (c.scheme != HWENO_SCHEME_GR || c.source != HWENO_SOURCE_NONE)
+    return fail(nullptr, HWENO_ERR_ARG, "hweno_residual_noalloc runs HWENO_SCHEME_GR without a source term");
   return HWENO_OK;
 }
 
@@ -1721,6 +1743,7 @@ extern "C" int hweno_residual_noalloc(const hweno_config* cfg, const double* q, 
   g.eps_pp = c.eps_pp; g.eps_weno = c.eps_weno;
   for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
   g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
+  g.x0 = c.x0; g.y0 = c.y0;
 
   double* base = nullptr;
   if ((rc = noalloc_scratch_address(&base))) return rc;

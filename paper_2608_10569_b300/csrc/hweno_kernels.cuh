@@ -34,6 +34,7 @@ struct Grid {
   double eps_pp, eps_weno;
   int bc[4];
   double rdx, rdy, rPr, rRe;  // 1/dx, 1/dy, 1/Pr, 1/Re (correctly rounded, on the host)
+  double x0, y0;              // domain origin (coordinates of a source term)
 };
 
 // x is neither infinite nor NaN: an exponent-field test in the integer pipe

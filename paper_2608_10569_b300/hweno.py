@@ -24,13 +24,17 @@ HWENO_FP64 = 0
 HWENO_MIXED = 1
 HWENO_SCHEME_GR = 0
 HWENO_SCHEME_DR = 1
+HWENO_SOURCE_NONE = 0
+HWENO_SOURCE_MMS52 = 1
 BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3}
 SCHEME = {"gr": HWENO_SCHEME_GR, "dr": HWENO_SCHEME_DR, HWENO_SCHEME_GR: HWENO_SCHEME_GR,
           HWENO_SCHEME_DR: HWENO_SCHEME_DR}
+SOURCE = {None: HWENO_SOURCE_NONE, "none": HWENO_SOURCE_NONE, "mms52": HWENO_SOURCE_MMS52,
+          HWENO_SOURCE_NONE: HWENO_SOURCE_NONE, HWENO_SOURCE_MMS52: HWENO_SOURCE_MMS52}
 
 # kernel indices of hweno_profile_read
 KERNELS = ["ghost", "cons_recon", "face_moments", "weak_moments", "grad_recon", "flux", "assemble",
-           "rk_update"]
+           "rk_update", "source"]
 
 
 class HwenoError(RuntimeError):
@@ -48,7 +52,7 @@ class hweno_config(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("b_visc", ctypes.c_double),
                 ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("precision", ctypes.c_int),
-                ("scheme", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("source", ctypes.c_int)]
 
 
 class hweno_diag(ctypes.Structure):
@@ -137,7 +141,7 @@ def _check(h, rc):
 
 def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
                 bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
-                max_halvings=20, precision="fp64", scheme="gr", **_ignored):
+                max_halvings=20, precision="fp64", scheme="gr", source=0, **_ignored):
     c = hweno_config()
     load().hweno_config_default(ctypes.byref(c))
     c.nx, c.ny = int(nx), int(ny)
@@ -149,6 +153,7 @@ def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1
     c.max_halvings = int(max_halvings)
     c.precision = HWENO_MIXED if precision in ("mixed", HWENO_MIXED) else HWENO_FP64
     c.scheme = SCHEME[scheme]
+    c.source = SOURCE[source]
     return c
 
 

@@ -115,3 +115,20 @@ def test_scheme_is_validated_before_any_device_call(lib):
     c = hweno.make_config(8, 8, scheme="dr")
     assert lib.hweno_residual_noalloc(ctypes.byref(c), buf, buf, None, None) == hweno.HWENO_ERR_ARG
     assert b"GR" in lib.hweno_last_error(None)
+
+
+def test_source_is_validated_before_any_device_call(lib):
+    """an unknown source term, a source in a batch and a source in
+    hweno_residual_noalloc are refused on the host"""
+    from paper_2608_10569_b300 import hweno
+    h = ctypes.c_void_p()
+    c = hweno.make_config(8, 8)
+    c.source = 2
+    assert lib.hweno_init(ctypes.byref(c), None, ctypes.byref(h)) == hweno.HWENO_ERR_ARG
+    cfgs = (hweno.hweno_config * 1)(hweno.make_config(8, 8, source="mms52"))
+    b = ctypes.c_void_p()
+    assert lib.hweno_batch_init(cfgs, 1, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
+    buf = (ctypes.c_double * 12)()
+    c = hweno.make_config(8, 8, source="mms52")
+    assert lib.hweno_residual_noalloc(ctypes.byref(c), buf, buf, None, None) == hweno.HWENO_ERR_ARG
+    assert b"source" in lib.hweno_last_error(None)
