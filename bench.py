@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dr", action="store_true")
     ap.add_argument("--mms-meshes", default="40,80,120,160")
+    ap.add_argument("--mms-schemes", default="gr,dr")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--workload", default="shock_tube",
@@ -430,7 +431,7 @@ def run_mms(args):
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
-    for scheme in ("gr", "dr"):
+    for scheme in args.mms_schemes.split(","):
         rows = []
         for n in meshes:
             case, q = I.manufactured(n, 0.0)
