@@ -10,7 +10,7 @@
  * (Eq. (3.4), Appendix A.2), the PP limiter on the conservative face states, and
  * viscous gradients from weak-derivative moments reconstructed by the same scalar
  * HWENO routine (Eqs. (3.6)-(3.9)).  Time stepping is SSP-RK3 with modified
- * moments (Eq. (2.10) and its 2D analogue) under the time-step and restart rules of
+ * moments (Eq. (2.12) and its 2D analogue) under the time-step and restart rules of
  * Sec. 5; boundary ghost cells follow Remark 4.1.  The paper's comparison scheme,
  * HWENO-DR, is selected per handle (hweno_config.scheme): its viscous gradients are the
  * derivatives of the characteristic candidates, combined with the nonlinear weights of
@@ -148,7 +148,7 @@ int hweno_get_state(hweno_handle* h, double* q, int on_device);
  * not finite (outputs are still written). */
 int hweno_residual(hweno_handle* h, double* rhs, double* vhat, int on_device);
 
-/* One SSP-RK3 step with modified moments (Eq. (2.10), 2D analogue).
+/* One SSP-RK3 step with modified moments (Eq. (2.12), 2D analogue).
  *   dt > 0: trial step; dt <= 0: dt = min(CFL h / alpha*, b Re h^2) (Sec. 5).
  * A stage whose cell averages are not all of positive density and pressure
  * rejects the step and repeats it from t^n with dt/2 (Sec. 5), at most
@@ -199,7 +199,7 @@ int hweno_measure_peak(hweno_handle* h, int which, double* tflops);
 long long hweno_launch_count(const hweno_handle* h);
 
 /* ---- Discrete adjoint (FP64) -----------------------------------------------------
- * Hand-written vector-Jacobian products of the SSP-RK3 step of Eq. (2.10) (2D
+ * Hand-written vector-Jacobian products of the SSP-RK3 step of Eq. (2.12) (2D
  * analogue) with the spatial operator of Eq. (3.2): the characteristic HWENO with its
  * nonlinear weights and the derivatives of the eigenvectors with respect to the cell
  * average, the weak-derivative gradient reconstruction, the PP-LLF fluxes (the

@@ -24,7 +24,7 @@
  *   HWENO-DR comparison gradients ......... Sec. 3.1 (differentiated candidates, the
  *                                           convective weights reused)
  *   HWENO candidates, weights ............. Appendix A.2, Eqs. (A.4)-(A.6)
- *   SSP-RK3 with modified moments ......... Eq. (2.10) and its 2D analogue (Sec. 3.1)
+ *   SSP-RK3 with modified moments ......... Eq. (2.12) and its 2D analogue (Sec. 3.1)
  *   time step, restart .................... Sec. 5 (CFL, b*Re*h^2, halving), Sec. 4
  *   ghost cells ........................... Remark 4.1
  *   manufactured source ................... Example 5.2 (fields, S = U_t + F_x + G_y)
@@ -1014,7 +1014,7 @@ static int or_admissible(const or_cfg* c, const double* q) {
     return 1;
 }
 
-/* one SSP-RK3 step with modified moments (Eq. (2.10), 2D analogue) and the
+/* one SSP-RK3 step with modified moments (Eq. (2.12), 2D analogue) and the
  * restart rule of Sec. 5.  q [12][ny][nx] is updated in place.  dt_fixed > 0
  * forces the trial step; otherwise dt = min(CFL h / alpha*, b Re h^2, t_end - t).
  * stats: [0] dt used, [1] rejections, [2] alpha*, [3] beta_max (stage max),

@@ -7,7 +7,7 @@
  * derivative along a chosen direction, so one evaluation gives F(q) and the exact
  * Jacobian-vector product J v = dF/dq v (plus the derivative with respect to
  * mu = 1/Re) with no difference quotient: the discrete tangent of the residual of
- * Eq. (3.2) and of the SSP-RK3 step of Eq. (2.10), to rounding.  The value parts are
+ * Eq. (3.2) and of the SSP-RK3 step of Eq. (2.12), to rounding.  The value parts are
  * the oracle's own results bit for bit (the same operations in the same order).
  *
  * Derivative rules at the non-smooth points the oracle passes through: |x| and the

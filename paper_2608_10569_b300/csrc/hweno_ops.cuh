@@ -550,7 +550,7 @@ __device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, doub
   if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
 }
 
-// SSP-RK3 stage with modified moments (Eq. (2.10), 2D analogue) on interior cells:
+// SSP-RK3 stage with modified moments (Eq. (2.12), 2D analogue) on interior cells:
 //   stage 1: out = [u^n; vhat^n] + dt F,                        base = [u^n; vhat^n]
 //   stage 2: out = 3/4 base + 1/4 ([u^(1); vhat^(1)] + dt F)
 //   stage 3: out = 1/3 base + 2/3 ([u^(2); vhat^(2)] + dt F)

@@ -103,8 +103,8 @@ def test_semi_discrete_system_is_consistent():
 def test_step_matches_butcher_form_with_stage_times():
     """A non-autonomous right-hand side dU/dt = R(U) + S(t) is sampled by SSP-RK3 at the
     nodes of its Butcher tableau, c = A 1 = (0, 1, 1/2) for a21 = 1, a31 = a32 = 1/4.
-    The oracle's Shu-Osher step (Eq. (2.10)) with the source equals the Butcher form
-    evaluated at t0 + c dt, with each stage's first moments taken as Eq. (2.10) states
+    The oracle's Shu-Osher step (Eq. (2.12)) with the source equals the Butcher form
+    evaluated at t0 + c dt, with each stage's first moments taken as Eq. (2.12) states
     (modified moment of the stage plus dt times the moment residual)."""
     case, q = I.manufactured(16, 0.02)
     t0, dt = 0.02, 4e-3

@@ -501,9 +501,9 @@ def test_spatial_operator_is_fifth_order():
 
 
 def test_rk3_step_matches_butcher_form():
-    """P13: SSP-RK3 in Shu-Osher form (Eq. (2.10)) equals the Butcher form
+    """P13: SSP-RK3 in Shu-Osher form (Eq. (2.12)) equals the Butcher form
     k1 = F(y), k2 = F(y + dt k1), k3 = F(y + dt (k1 + k2)/4), y' = y + dt (k1 + k2 + 4 k3)/6
-    on the cell averages, with each stage's first moments taken as Eq. (2.10) states
+    on the cell averages, with each stage's first moments taken as Eq. (2.12) states
     (modified moment of the stage plus dt times the moment residual)."""
     case, q = I.random_smooth(16, 16, seed=9, Re=200.0)
     cfg = _cfg(case)
