@@ -14,7 +14,7 @@
  * Sec. 5; boundary ghost cells follow Remark 4.1.  The paper's comparison scheme,
  * HWENO-DR, is selected per handle (hweno_config.scheme): its viscous gradients are the
  * derivatives of the characteristic candidates, combined with the nonlinear weights of
- * the convective reconstruction (Sec. 3.1); everything else is shared.
+ * the convective reconstruction (Eq. (3.5)); everything else is shared.
  *
  * Conventions shared by every entry point
  *   - Every function returns int: HWENO_OK (0) or a negative HWENO_ERR_* code; the
@@ -65,7 +65,7 @@ extern "C" {
 /* viscous gradients */
 #define HWENO_SCHEME_GR 0 /* weak-derivative moments through the scalar HWENO (Eqs. (3.6)-(3.9)) */
 #define HWENO_SCHEME_DR 1 /* differentiated characteristic candidates with the convective
-                             weights (Sec. 3.1); fourth order; HWENO_FP64 only */
+                             weights (Eq. (3.5)); fourth order; HWENO_FP64 only */
 
 /* source terms added to the spatial operator (dU/dt = R(U) + S(t)) */
 #define HWENO_SOURCE_NONE 0

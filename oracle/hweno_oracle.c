@@ -21,7 +21,7 @@
  *                                           only face values modified), Sec. 5 (eps_PP)
  *   face moments, weak-derivative moments . Eqs. (3.6)-(3.8)
  *   gradient reconstruction ............... Eq. (3.9), Remark 3.1
- *   HWENO-DR comparison gradients ......... Sec. 3.1 (differentiated candidates, the
+ *   HWENO-DR comparison gradients ......... Eq. (3.5) (differentiated candidates, the
  *                                           convective weights reused)
  *   HWENO candidates, weights ............. Appendix A.2, Eqs. (A.4)-(A.6)
  *   SSP-RK3 with modified moments ......... Eq. (2.12) and its 2D analogue (Sec. 3.1)
@@ -68,7 +68,7 @@ typedef struct {
     int max_halvings;
     int linear_weights; /* 1: omega_m = gamma_m (used only by exactness pins) */
     int limiter;        /* 1: PP limiter active */
-    int scheme;         /* viscous gradients: 0 HWENO-GR (Sec. 3.2), 1 HWENO-DR (Sec. 3.1) */
+    int scheme;         /* viscous gradients: 0 HWENO-GR (Sec. 3.2), 1 HWENO-DR (Eq. (3.5)) */
     int source;         /* 1: Example 5.2's manufactured source added to every residual */
     int pad2_;
     double time;        /* time of a residual evaluation (the source's t) */
@@ -298,7 +298,7 @@ static double or_poly_d(const double c[15], int axis, double xi, double eta) {
     return s;
 }
 
-/* HWENO-DR (Sec. 3.1): the candidates' derivatives in the combination of Eq. (3.4),
+/* HWENO-DR (Eq. (3.5)): the candidates' derivatives in the combination of Eq. (3.4),
  * with the nonlinear weights of the value reconstruction (constant over the cell):
  * w0 (p0'/g0 - sum gm/g0 pm') + sum wm pm', derivative in scaled units */
 static double or_hweno_eval_d(const or_hweno* h, int axis, double xi, double eta) {
@@ -630,7 +630,7 @@ static void or_grad_cell(or_work* W, int i, int j) {
         }
 }
 
-/* HWENO-DR gradients of one cell (Sec. 3.1): the chain rule at each point, with the
+/* HWENO-DR gradients of one cell (Eq. (3.5)): the chain rule at each point, with the
  * limited face traces and the volume values the fluxes use */
 static void or_dr_grad_cell(or_work* W, int i, int j) {
     size_t id = IDX(W, i, j);

@@ -293,7 +293,7 @@ __device__ __forceinline__ void grad_body(const Grid& g, const Work& w, int gx, 
 }
 
 // ---------------------------------------------------------------------------
-// HWENO-DR viscous gradients (Sec. 3.1) of cells of the interior grown by 1.  The
+// HWENO-DR viscous gradients (Eq. (3.5)) of cells of the interior grown by 1.  The
 // nonlinear weights are constant over the cell, so the combination of the candidates'
 // derivatives is the derivative of the combined polynomial that cons_body stored per
 // characteristic field and direction (Work::dr).  The back-transform to conserved

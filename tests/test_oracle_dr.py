@@ -1,4 +1,4 @@
-"""Pins of the oracle's HWENO-DR gradients (the paper's comparison scheme, Sec. 3.1):
+"""Pins of the oracle's HWENO-DR gradients (the paper's comparison scheme, Eq. (3.5)):
 the derivatives of the characteristic candidate polynomials, combined with the nonlinear
 weights of the convective reconstruction, replace the weak-derivative reconstruction of
 Eq. (3.9).
