@@ -1,4 +1,4 @@
-"""ctypes front-end of the FP64 CPU oracle (test infrastructure only).
+"""ctypes front-end of the FP64 CPU oracles (test infrastructure only).
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this module.  It compiles ``hweno_oracle.c`` with gcc
@@ -9,6 +9,10 @@ the forward-mode tangents ``residual_jvp`` and ``step_jvp``.
 States are numpy float64 arrays of shape (12, ny, nx): plane 4*m + v holds
 moment m (0 = cell average, 1 = scaled xi-moment, 2 = scaled eta-moment) of
 conserved variable v (rho, rho*u, rho*v, E).
+
+The one-dimensional oracle (``hweno1d_oracle.c``, the scheme of Sec. 2) is in the same
+library, behind the ``*1d`` functions: its states are arrays of shape (6, n), plane
+3*m + v holding moment m (0 average, 1 scaled moment) of v (rho, rho*u, E).
 """
 import ctypes
 import os
@@ -19,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hweno_oracle.c")
+_SRC1 = os.path.join(_HERE, "hweno1d_oracle.c")
 _HDR = os.path.join(_HERE, "oracle_tables.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _JVP_SRC = os.path.join(_HERE, "hweno_oracle_jvp.cpp")
@@ -51,10 +56,11 @@ class _Cfg(ctypes.Structure):
 def build(force=False):
     """Compile the oracle shared library if it is missing or stale."""
     stale = (not os.path.exists(_LIB) or
-             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR),
+                                          os.path.getmtime(_SRC1)))
     if force or stale:
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
-               "-std=c11", "-o", _LIB + ".tmp", _SRC, "-lm"]
+               "-std=c11", "-o", _LIB + ".tmp", _SRC, _SRC1, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
     stale = (not os.path.exists(_JVP_LIB) or
@@ -286,3 +292,129 @@ def step_jvp(cfg, q, qdot, dt, dmu=0.0):
     lib.or_jvp_step(ctypes.byref(cfg), _ptr(q), _ptr(qd), float(dmu), float(dt), _ptr(st))
     return q, qd, {"dt": st[0], "rejections": int(st[1]), "alpha": st[2], "beta_max": st[3],
                    "pp_active": st[4], "status": int(st[5])}
+
+
+# ---------------------------------------------------------------------------
+# one-dimensional scheme (Sec. 2)
+
+BC1 = {"periodic": 0, "reflective": 1, "inflow": 2, "outflow": 3}
+
+
+class _Cfg1(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("bc", ctypes.c_int * 2), ("pad0_", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("b_visc", ctypes.c_double),
+                ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
+                ("max_halvings", ctypes.c_int), ("linear_weights", ctypes.c_int),
+                ("limiter", ctypes.c_int), ("scheme", ctypes.c_int), ("source", ctypes.c_int),
+                ("pad1_", ctypes.c_int), ("time", ctypes.c_double),
+                ("inflow", (ctypes.c_double * 3) * 2)]
+
+
+_lib1_ready = False
+
+
+def _load1():
+    global _lib1_ready
+    lib = _load()
+    with _lock:
+        if not _lib1_ready:
+            dp = ctypes.POINTER(ctypes.c_double)
+            P = ctypes.POINTER(_Cfg1)
+            lib.or1_residual.argtypes = [P, dp, dp, dp, dp, dp, dp, dp]
+            lib.or1_step.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            lib.or1_advance.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
+            lib.or1_hweno_scalar.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+            lib.or1_mms_source_export.argtypes = [P, ctypes.c_double, ctypes.c_double, dp]
+            _lib1_ready = True
+    return lib
+
+
+def make_cfg1d(n, x0=0.0, x1=1.0, gamma=1.4, Pr=0.72, Re=1000.0, bc=("periodic", "periodic"), cfl=0.6,
+               b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8, max_halvings=20, linear_weights=False, limiter=True,
+               scheme="gr", source=0, time=0.0, inflow=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), **_ignored):
+    c = _Cfg1()
+    c.n = int(n)
+    for k in range(2):
+        c.bc[k] = BC1[bc[k]] if isinstance(bc[k], str) else int(bc[k])
+    if (c.bc[0] == 0) != (c.bc[1] == 0):
+        raise ValueError("periodic boundaries must be set on both sides")
+    c.x0, c.x1 = float(x0), float(x1)
+    c.gamma, c.Pr, c.Re = float(gamma), float(Pr), float(Re)
+    c.cfl, c.b_visc, c.eps_pp, c.eps_weno = float(cfl), float(b_visc), float(eps_pp), float(eps_weno)
+    c.max_halvings = int(max_halvings)
+    c.linear_weights = 1 if linear_weights else 0
+    c.limiter = 1 if limiter else 0
+    c.scheme = SCHEME[scheme]
+    c.source = {None: 0, "none": 0, "mms51": 1, 0: 0, 1: 1}[source]
+    c.time = float(time)
+    for k in range(2):
+        for v in range(3):
+            c.inflow[k][v] = float(inflow[k][v])
+    return c
+
+
+def _state1(cfg, q):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    if q.shape != (6, cfg.n):
+        raise ValueError(f"state shape {q.shape} != (6, {cfg.n})")
+    return q
+
+
+def residual1d(cfg, q, dumps=False):
+    """Sec. 2's spatial operator: dict(rhs (6,n), vhat (3,n), diag) and, with dumps,
+    pts (12,n) (Lobatto point 3*g + v, limited), grad (8,n) (2*g + (u_x, e_x)),
+    theta (2,n)."""
+    lib = _load1()
+    q = _state1(cfg, q)
+    n = cfg.n
+    out = {"rhs": np.zeros((6, n)), "vhat": np.zeros((3, n)), "diag": np.zeros(8)}
+    d = {}
+    if dumps:
+        d = {"pts": np.zeros((12, n)), "grad": np.zeros((8, n)), "theta": np.zeros((2, n))}
+    rc = lib.or1_residual(ctypes.byref(cfg), _ptr(q), _ptr(out["rhs"]), _ptr(out["vhat"]), _ptr(out["diag"]),
+                          _ptr(d.get("pts")), _ptr(d.get("grad")), _ptr(d.get("theta")))
+    if rc:
+        raise MemoryError("oracle 1D residual failed")
+    out.update(d)
+    return out
+
+
+def step1d(cfg, q, t=0.0, t_end=np.inf, dt_fixed=0.0):
+    lib = _load1()
+    q = _state1(cfg, q).copy()
+    st = np.zeros(6)
+    lib.or1_step(ctypes.byref(cfg), _ptr(q), float(t), float(t_end), float(dt_fixed), _ptr(st))
+    return q, {"dt": st[0], "rejections": int(st[1]), "alpha": st[2], "beta_max": st[3],
+               "pp_active": st[4], "status": int(st[5])}
+
+
+def advance1d(cfg, q, t0, t_end, max_steps=10 ** 9):
+    lib = _load1()
+    q = _state1(cfg, q).copy()
+    st = np.zeros(10)
+    lib.or1_advance(ctypes.byref(cfg), _ptr(q), float(t0), float(t_end), int(max_steps), _ptr(st))
+    return q, {"dt": st[0], "pp_active": st[4], "status": int(st[5]), "t": st[6], "steps": int(st[7]),
+               "rejections": int(st[8])}
+
+
+def hweno_scalar1d(d5, eps=1e-8, linear=False):
+    """One 1D scalar reconstruction (Appendix A.1): dict(pts (4,), dpts (4,), mom, beta (3,),
+    omega (3,), c0 (5,)) at the four Lobatto points, derivatives in scaled units."""
+    lib = _load1()
+    d5 = np.ascontiguousarray(d5, dtype=np.float64)
+    assert d5.shape == (5,)
+    o = {"pts": np.zeros(4), "dpts": np.zeros(4), "mom": np.zeros(1), "beta": np.zeros(3),
+         "omega": np.zeros(3), "c0": np.zeros(5)}
+    lib.or1_hweno_scalar(_ptr(d5), float(eps), 1 if linear else 0, _ptr(o["pts"]), _ptr(o["dpts"]),
+                         _ptr(o["mom"]), _ptr(o["beta"]), _ptr(o["omega"]), _ptr(o["c0"]))
+    o["mom"] = float(o["mom"][0])
+    return o
+
+
+def mms_source1d(cfg, x, t):
+    lib = _load1()
+    S = np.zeros(3)
+    lib.or1_mms_source_export(ctypes.byref(cfg), float(x), float(t), _ptr(S))
+    return S

@@ -306,3 +306,75 @@ def random_rough(nx, ny, seed=0, bc=("periodic",) * 4, gamma=1.4, Re=200.0, Pr=0
         return rho, u, v, p
 
     return case, cell_moments(case, prim)
+
+
+# ---------------------------------------------------------------------------
+# one-dimensional workloads (Sec. 2): states of shape (6, n), plane 3*m + v holding
+# moment m (0 average, 1 scaled first moment) of v (rho, rho*u, E)
+
+def cell_moments_1d(x0, x1, n, prim, gamma, nq=5):
+    """cell averages and scaled first moments of a primitive point field
+    prim(x) -> (rho, u, p) with an nq-point Gauss rule"""
+    gn, gw = np.polynomial.legendre.leggauss(nq)
+    gn, gw = 0.5 * gn, 0.5 * gw
+    dx = (x1 - x0) / n
+    xc = x0 + (np.arange(n) + 0.5) * dx
+    q = np.zeros((6, n))
+    for a in range(nq):
+        rho, u, p = prim(xc + gn[a] * dx)
+        U = (rho, rho * u, p / (gamma - 1.0) + 0.5 * rho * u * u)
+        for v in range(3):
+            q[v] += gw[a] * U[v]
+            q[3 + v] += gw[a] * gn[a] * U[v]
+    return q
+
+
+def manufactured_prim_1d(x, t, gamma=1.4):
+    """Example 5.1's manufactured solution (rho, u, p) at time t, p = (gamma - 1) rho e"""
+    a = 0.2 * np.exp(-t)
+    s, c = np.sin(2 * np.pi * x), np.cos(2 * np.pi * x)
+    rho, u, e = 2 + a * s, 1 + a * c, 1 + a * s
+    return rho, u, (gamma - 1) * rho * e
+
+
+def manufactured_1d(n, t=0.0, Re=100.0):
+    """Example 5.1: [0,1] periodic, gamma 1.4, Pr 0.72, Re 100, the manufactured source on,
+    T = 0.1; the exact solution's cell moments at time t"""
+    params = dict(n=n, x0=0.0, x1=1.0, gamma=1.4, Pr=0.72, Re=Re, bc=("periodic", "periodic"), source=1)
+    return params, cell_moments_1d(0.0, 1.0, n, lambda x: manufactured_prim_1d(x, t), 1.4)
+
+
+def double_rarefaction(n=200, Re=1000.0):
+    """Example 5.4: [-1, 1], (rho, u, p) = (7, -1, 0.2) left of 0 and (7, 1, 0.2) right,
+    gamma 1.4, Re 1000, T = 0.6, inflow (the left state) at x = -1 and outflow at x = 1;
+    cell x = 0 is an interface for even n"""
+    g = 1.4
+    left = (7.0, -1.0 * 7.0, 0.2 / (g - 1.0) + 0.5 * 7.0)
+    params = dict(n=n, x0=-1.0, x1=1.0, gamma=g, Pr=0.72, Re=Re, bc=("inflow", "outflow"),
+                  inflow=(left, (0.0, 0.0, 0.0)))
+
+    def prim(x):
+        return 7.0 + 0 * x, np.where(x < 0.0, -1.0, 1.0), 0.2 + 0 * x
+
+    return params, cell_moments_1d(-1.0, 1.0, n, prim, g)
+
+
+def random_smooth_1d(n, seed=0, bc=("periodic", "periodic"), Re=300.0, amp=0.2, modes=3):
+    """a few seeded Fourier modes on rho, u, p over [0, 1]"""
+    rng = np.random.default_rng(SEED_BASE + 300 + seed)
+    coef = rng.uniform(-1, 1, size=(3, modes, 2))
+    k = rng.integers(1, 4, size=(3, modes))
+    base = np.array([1.0, 0.3, 1.0])
+
+    def prim(x):
+        out = []
+        for f in range(3):
+            s = base[f] + 0 * x
+            for m in range(modes):
+                ph = 2 * np.pi * k[f, m] * x
+                s = s + amp / modes * (coef[f, m, 0] * np.sin(ph) + coef[f, m, 1] * np.cos(ph))
+            out.append(s)
+        return tuple(out)
+
+    params = dict(n=n, x0=0.0, x1=1.0, gamma=1.4, Pr=0.72, Re=Re, bc=tuple(bc))
+    return params, cell_moments_1d(0.0, 1.0, n, prim, 1.4)

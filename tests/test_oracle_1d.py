@@ -1,0 +1,254 @@
+"""Pins of the one-dimensional oracle (the scheme of Sec. 2, Appendix A.1), the
+survey's NEXT-3 row: printed constants and error tables of the paper, exact polynomial
+results, integration identities, symmetries and convergence orders.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import sympy as sp
+from numpy.polynomial import polynomial as npoly
+
+from oracle import oracle as O
+from paper_2608_10569_b300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LOB = np.array([-0.5, -math.sqrt(5.0) / 10.0, math.sqrt(5.0) / 10.0, 0.5])
+LOBW = np.array([1.0, 5.0, 5.0, 1.0]) / 12.0
+
+
+def golden_constants():
+    out = {}
+    with open(os.path.join(HERE, "golden", "paper_constants.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, val = line.split()[:2]
+            out[name] = float(val)
+    return out
+
+
+def table_5_1():
+    rows = {}
+    with open(os.path.join(HERE, "golden", "table_5_1.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            sc, n, linf, l1 = line.split()
+            rows[(sc, int(n))] = (float(linf), float(l1))
+    return rows
+
+
+def _data5(P):
+    """the five data of the 1D stencil for a point function P(xi) in the centre cell's
+    scaled coordinate: averages over cells -1, 0, 1 and first moments of cells -1, 1
+    (8-point Gauss, exact for the polynomials used)"""
+    gn, gw = np.polynomial.legendre.leggauss(8)
+    gn, gw = 0.5 * gn, 0.5 * gw
+
+    def m(j, w=False):
+        return sum(gw[k] * P(j + gn[k]) * (gn[k] if w else 1.0) for k in range(8))
+
+    return np.array([m(-1), m(0), m(1), m(-1, True), m(1, True)])
+
+
+# ---------------------------------------------------------------------------
+# the scalar reconstruction (Appendix A.1)
+
+def test_trace_error_constant():
+    """Sec. 2.2: p0's left and right traces at x_{i+1/2} err by -+ (241/95760) dx^5 w^(5).
+    For w = xi^5 (dx = 1, w^(5) = 120) there are no higher terms, so the error at the
+    cell's right face is exactly -120 * 241/95760 and at its left face +120 * 241/95760."""
+    c = golden_constants()["trace_error_1d"]
+    o = O.hweno_scalar1d(_data5(lambda x: x ** 5), linear=True)
+    assert abs((o["pts"][3] - 0.5 ** 5) - (-120 * c)) < 1e-13
+    assert abs((o["pts"][0] + 0.5 ** 5) - (120 * c)) < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_quartic_recovered_with_linear_weights(seed):
+    """p0 satisfies the five conditions of Appendix A.1 exactly for a quartic, so it is
+    that quartic; with omega = gamma the combination of Eq. (2.4) returns it at the
+    Lobatto points, its modified moment is the quartic's first moment, and its DR
+    derivative (Eq. (2.5)) the quartic's derivative"""
+    c = np.random.default_rng(60 + seed).normal(size=5)
+    P = lambda x: npoly.polyval(x, c)
+    o = O.hweno_scalar1d(_data5(P), linear=True)
+    assert np.abs(o["c0"] - c).max() < 1e-12
+    assert np.abs(o["pts"] - P(LOB)).max() < 1e-12
+    gn, gw = np.polynomial.legendre.leggauss(6)
+    assert abs(o["mom"] - sum(0.5 * gw * 0.5 * gn * P(0.5 * gn))) < 1e-13
+    assert np.abs(o["dpts"] - npoly.polyval(LOB, npoly.polyder(c))).max() < 1e-11
+
+
+def test_weights_and_average():
+    """the printed linear weights for data whose candidates coincide, weights summing
+    to one, and the Lobatto mean of the four point values equal to the centre average
+    for any data (the 4-point Lobatto rule is exact for the quartic combination)"""
+    g = golden_constants()
+    o = O.hweno_scalar1d(_data5(lambda x: 0.3 + 1.7 * x))
+    assert np.allclose(o["omega"], [g["gamma0_1d"], g["gamma12_1d"], g["gamma12_1d"]], rtol=0, atol=1e-15)
+    assert abs(g["lobatto_node"] - LOB[2]) < 1e-16
+    assert abs(g["lobatto_w_end"] - LOBW[0]) < 1e-16 and abs(g["lobatto_w_inner"] - LOBW[1]) < 1e-16
+    rng = np.random.default_rng(61)
+    for _ in range(6):
+        d = rng.normal(size=5) * rng.uniform(0.2, 5.0)
+        o = O.hweno_scalar1d(d)
+        assert abs(o["omega"].sum() - 1.0) < 1e-14
+        assert abs(LOBW @ o["pts"] - d[1]) < 1e-13 * max(1.0, np.abs(d).max())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dr_derivatives_integrate_to_the_values(seed):
+    """Eq. (2.5) with the weights constant over the cell is the derivative of the value
+    combination u; the 4-point Lobatto rule is exact for u' and xi u' (degrees 3, 4):
+    sum w_G u'(xi_G) = u(1/2) - u(-1/2) and sum w_G xi_G u'(xi_G) = (u(1/2) + u(-1/2))/2
+    - u_bar, for random data with nonlinear weights"""
+    rng = np.random.default_rng(70 + seed)
+    d = rng.normal(size=5) * rng.uniform(0.5, 5.0)
+    o = O.hweno_scalar1d(d)
+    assert np.abs(o["omega"] - np.array([0.995, 0.0025, 0.0025])).max() > 1e-3
+    tol = 1e-12 * max(1.0, np.abs(d).max())
+    assert abs(LOBW @ o["dpts"] - (o["pts"][3] - o["pts"][0])) < tol
+    assert abs(LOBW @ (LOB * o["dpts"]) - (0.5 * (o["pts"][3] + o["pts"][0]) - d[1])) < tol
+
+
+# ---------------------------------------------------------------------------
+# the spatial operator
+
+def test_free_stream_and_conservation():
+    """a constant state has zero residual; on a periodic line the averages' residual
+    sums to zero (every interface flux enters two cells with opposite signs)"""
+    p, q = I.random_smooth_1d(24, seed=1)
+    qc = np.zeros_like(q)
+    qc[0], qc[1], qc[2] = 1.3, 0.5, 2.0
+    for scheme in ("gr", "dr"):
+        r = O.residual1d(O.make_cfg1d(**p, scheme=scheme), qc)
+        assert np.abs(r["rhs"]).max() < 1e-13
+        r = O.residual1d(O.make_cfg1d(**p, scheme=scheme), q)["rhs"]
+        for v in range(3):
+            assert abs(r[v].sum()) < 1e-13 * max(np.abs(r[v]).sum(), 1.0)
+
+
+@pytest.mark.parametrize("scheme", ["gr", "dr"])
+def test_mirror_equivariance(scheme):
+    """x -> -x (m and the moment of rho and E change sign, the moment of m does not)
+    commutes with the residual between reflective walls (Remark 4.1)"""
+    p, q = I.random_smooth_1d(21, seed=3, bc=("reflective", "reflective"))
+    cfg = O.make_cfg1d(**p, scheme=scheme)
+    sgn = np.array([1, -1, 1, -1, 1, -1], dtype=float)[:, None]
+    r1 = O.residual1d(cfg, q)["rhs"]
+    r2 = O.residual1d(cfg, sgn * q[:, ::-1])["rhs"]
+    assert np.abs(sgn * r1[:, ::-1] - r2).max() <= 1e-12 * np.abs(r2).max()
+
+
+def test_euler_limit_dr_equals_gr():
+    p, q = I.random_smooth_1d(20, seed=4)
+    a = O.residual1d(O.make_cfg1d(**dict(p, Re=math.inf)), q)
+    b = O.residual1d(O.make_cfg1d(**dict(p, Re=math.inf), scheme="dr"), q)
+    assert np.array_equal(a["rhs"], b["rhs"]) and np.array_equal(a["vhat"], b["vhat"])
+    assert not np.array_equal(O.residual1d(O.make_cfg1d(**p), q)["rhs"],
+                              O.residual1d(O.make_cfg1d(**p, scheme="dr"), q)["rhs"])
+
+
+@pytest.mark.parametrize("linear", [True, False], ids=["linear_weights", "nonlinear_weights"])
+def test_gradient_orders(linear):
+    """Sec. 2.2: the weak-derivative gradients are fifth order, the differentiated ones
+    (DR) fourth; errors of (u_x, e_x) at the Lobatto points on Example 5.1's fields"""
+    t = 0.05
+
+    def err(n, scheme):
+        p, q = I.manufactured_1d(n, t)
+        r = O.residual1d(O.make_cfg1d(**p, scheme=scheme, linear_weights=linear, time=t), q, dumps=True)
+        xc = (np.arange(n) + 0.5) / n
+        a = 0.2 * math.exp(-t)
+        e = 0.0
+        for g, xi in enumerate(LOB):
+            x = xc + xi / n
+            ux = -a * 2 * np.pi * np.sin(2 * np.pi * x)
+            ex = a * 2 * np.pi * np.cos(2 * np.pi * x)
+            e = max(e, np.abs(r["grad"][2 * g] - ux).max(), np.abs(r["grad"][2 * g + 1] - ex).max())
+        return e
+
+    ns = (40, 80) if linear else (80, 160)
+    gr = [err(n, "gr") for n in ns]
+    dr = [err(n, "dr") for n in ns]
+    assert math.log2(gr[0] / gr[1]) > 4.8, gr
+    assert 3.8 < math.log2(dr[0] / dr[1]) < 4.2, dr
+
+
+@pytest.mark.parametrize("Re", [100.0, 9.0])
+def test_source_matches_symbolic_differentiation(Re):
+    x, t = sp.symbols("x t")
+    a = sp.Rational(1, 5) * sp.exp(-t)
+    rho = 2 + a * sp.sin(2 * sp.pi * x)
+    u = 1 + a * sp.cos(2 * sp.pi * x)
+    e = 1 + a * sp.sin(2 * sp.pi * x)
+    g, Pr = 1.4, 0.72
+    p = (g - 1) * rho * e
+    E = rho * (e + u * u / 2)
+    tau = sp.Rational(4, 3) * sp.diff(u, x) / Re
+    q = -g * sp.diff(e, x) / (Pr * Re)
+    U = [rho, rho * u, E]
+    F = [rho * u, rho * u * u + p - tau, u * (E + p) - (u * tau - q)]
+    f = sp.lambdify((x, t), [sp.diff(U[k], t) + sp.diff(F[k], x) for k in range(3)], "numpy")
+    cfg = O.make_cfg1d(8, Re=Re, source=1)
+    rng = np.random.default_rng(51)
+    for _ in range(20):
+        xx, tt = rng.uniform(0, 1), rng.choice([0.0, 0.07, 0.4])
+        ex = np.array(f(xx, tt), dtype=float)
+        assert np.abs(O.mms_source1d(cfg, xx, tt) - ex).max() <= 1e-12 * np.abs(ex).max()
+
+
+def test_example_5_1_against_table_5_1():
+    """Example 5.1 to T = 0.1 under the Sec. 5 step rule: the density errors of both
+    schemes at 80 and 120 cells lie within 25 % of Table 5.1's (where the nonlinear
+    weights are close to the linear ones, so the unprinted smoothness indicator matters
+    little), and GR's error falls faster than DR's"""
+    tab = table_5_1()
+    errs = {}
+    for scheme in ("gr", "dr"):
+        for n in (80, 120):
+            p, q = I.manufactured_1d(n, 0.0)
+            qT, st = O.advance1d(O.make_cfg1d(**p, scheme=scheme), q, 0.0, 0.1)
+            assert st["status"] == 0 and abs(st["t"] - 0.1) < 1e-15
+            _, qe = I.manufactured_1d(n, 0.1)
+            e = np.abs(qT[0] - qe[0])
+            errs[(scheme, n)] = (e.max(), e.mean())
+            for k in range(2):
+                ratio = errs[(scheme, n)][k] / tab[(scheme, n)][k]
+                assert 0.75 < ratio < 1.25, (scheme, n, k, errs[(scheme, n)], tab[(scheme, n)])
+    gain = lambda s: errs[(s, 80)][1] / errs[(s, 120)][1]
+    assert gain("gr") > gain("dr")
+
+
+def test_limiter_keeps_the_average_on_the_double_rarefaction():
+    """Example 5.4's vacuum-forming double rarefaction (100 cells): by the time the
+    limiter acts, every limited Lobatto value has rho, p >= eps_PP, the Lobatto mean of
+    the limited values is still the cell average (the rescaling is about it), the averages
+    stay positive, and the run is mirror-symmetric (rho, E even, m odd)"""
+    p, q = I.double_rarefaction(100)
+    cfg = O.make_cfg1d(**p)
+    t = 0.0
+    for _ in range(60):
+        r = O.residual1d(cfg, q, dumps=True)
+        if (r["theta"] < 1).any():
+            break
+        q, st = O.step1d(cfg, q, t=t)
+        assert st["status"] == 0
+        t += st["dt"]
+    lim = (r["theta"] < 1).any(axis=0)
+    assert lim.any() and t > 0.01
+    pts = r["pts"].reshape(4, 3, -1)
+    pr = 0.4 * (pts[:, 2] - 0.5 * pts[:, 1] ** 2 / pts[:, 0])
+    # p = (g - 1)(E - m^2/(2 rho)) at a clipped point cancels down from |E| ~ 1: its
+    # rounding is relative to |E|, not to eps_PP
+    assert pts[:, 0, lim].min() >= 1e-12 * (1 - 1e-9)
+    assert pr[:, lim].min() >= 1e-12 - 1e-14 * np.abs(pts[:, 2]).max()
+    mean = np.einsum("g,gvn->vn", LOBW, pts)
+    assert np.abs(mean - q[:3]).max() <= 1e-13 * np.abs(q[:3]).max()
+    rho, m, E = q[0], q[1], q[2]
+    assert rho.min() > 0 and (0.4 * (E - 0.5 * m * m / rho)).min() > 0
+    assert np.abs(rho - rho[::-1]).max() <= 1e-12 * rho.max()
+    assert np.abs(m + m[::-1]).max() <= 1e-12 * np.abs(m).max()
