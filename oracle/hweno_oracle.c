@@ -47,6 +47,10 @@
  *                         stay those of the unlimited reconstruction
  *   LF coefficient        per face, max over 3 points x 2 sides of max(|u_n|+c, PP bound)
  *   ghost moments         mirror: normal moment takes -parity, tangential +parity
+ *   inflow / outflow      inflow: the prescribed state with zero moments; outflow: the
+ *                         adjacent interior cell's average and moments; corners as the x
+ *                         pass then the y pass over the full padded width (a y-face
+ *                         inflow fills its whole ghost row)
  *   parity unpinned:      the smoothness-indicator normalisation and the characteristic
  *                         state are not fixed by the paper; the pins hold for any choice.
  */
@@ -57,7 +61,8 @@
 
 #define OR_G 4 /* ghost layers: residual of cell i depends on states i-4..i+4 */
 
-enum { OR_BC_PERIODIC = 0, OR_BC_NOSLIP = 1, OR_BC_SYMMETRY = 2, OR_BC_SLIP = 3 };
+enum { OR_BC_PERIODIC = 0, OR_BC_NOSLIP = 1, OR_BC_SYMMETRY = 2, OR_BC_SLIP = 3, OR_BC_INFLOW = 4,
+       OR_BC_OUTFLOW = 5 };
 
 typedef struct {
     int nx, ny;
@@ -72,6 +77,13 @@ typedef struct {
     int source;         /* 1: Example 5.2's manufactured source added to every residual */
     int pad2_;
     double time;        /* time of a residual evaluation (the source's t) */
+    /* inflow faces (Remark 4.1): per side xlo, xhi, ylo, yhi the conserved state A inside
+     * the band |t - band[s][0]| < band[s][1] of the face coordinate t (y on x-faces, x on
+     * y-faces; the ghost cell's centre) and B elsewhere */
+    double inflow[4][2][4];
+    double band[4][2];
+    int linear_grad;    /* 1: linear weights in the gradient reconstruction only (ablation) */
+    int pad3_;
 } or_cfg;
 
 /* linear weights of Appendix A.2 */
@@ -112,30 +124,64 @@ static void or_parity(int bc, int normal_dir, double s[4]) {
     }
 }
 
+/* the prescribed inflow state of side s for a ghost cell whose face coordinate is t */
+static void or_inflow_state(const or_cfg* c, int s, double t, double out[12]) {
+    int in = fabs(t - c->band[s][0]) < c->band[s][1];
+    for (int v = 0; v < 4; v++) {
+        out[v] = c->inflow[s][in ? 0 : 1][v];
+        out[4 + v] = 0.0;
+        out[8 + v] = 0.0;
+    }
+}
+
 static void or_fetch(const or_cfg* c, const double* q, int i, int j, double out[12]) {
     int nx = c->nx, ny = c->ny;
     double sa[4] = {1, 1, 1, 1}, sx[4] = {1, 1, 1, 1}, sy[4] = {1, 1, 1, 1};
     int ii = i, jj = j;
-    if (ii < 0 || ii >= nx) {
-        int bc = ii < 0 ? c->bc[0] : c->bc[1];
-        if (bc == OR_BC_PERIODIC) {
-            ii = ((ii % nx) + nx) % nx;
-        } else {
-            double s[4];
-            or_parity(bc, 0, s);
-            ii = ii < 0 ? -1 - ii : 2 * nx - 1 - ii;
-            for (int v = 0; v < 4; v++) { sa[v] *= s[v]; sx[v] *= -s[v]; sy[v] *= s[v]; }
+    double dx = (c->x1 - c->x0) / nx, dy = (c->y1 - c->y0) / ny;
+    /* a y-face inflow fills its whole ghost row, corners included */
+    if (jj < 0 || jj >= ny) {
+        int s = jj < 0 ? 2 : 3;
+        if (c->bc[s] == OR_BC_INFLOW) {
+            or_inflow_state(c, s, c->x0 + (i + 0.5) * dx, out);
+            return;
         }
     }
+    /* the row the y rule maps j to, with its parities */
     if (jj < 0 || jj >= ny) {
         int bc = jj < 0 ? c->bc[2] : c->bc[3];
         if (bc == OR_BC_PERIODIC) {
             jj = ((jj % ny) + ny) % ny;
+        } else if (bc == OR_BC_OUTFLOW) {
+            jj = jj < 0 ? 0 : ny - 1;
         } else {
             double s[4];
             or_parity(bc, 1, s);
             jj = jj < 0 ? -1 - jj : 2 * ny - 1 - jj;
             for (int v = 0; v < 4; v++) { sa[v] *= s[v]; sx[v] *= s[v]; sy[v] *= -s[v]; }
+        }
+    }
+    if (ii < 0 || ii >= nx) {
+        int bc = ii < 0 ? c->bc[0] : c->bc[1];
+        if (bc == OR_BC_INFLOW) {
+            double st[12];
+            or_inflow_state(c, ii < 0 ? 0 : 1, c->y0 + (jj + 0.5) * dy, st);
+            for (int v = 0; v < 4; v++) {
+                out[v] = sa[v] * st[v];
+                out[4 + v] = 0.0;
+                out[8 + v] = 0.0;
+            }
+            return;
+        }
+        if (bc == OR_BC_PERIODIC) {
+            ii = ((ii % nx) + nx) % nx;
+        } else if (bc == OR_BC_OUTFLOW) {
+            ii = ii < 0 ? 0 : nx - 1;
+        } else {
+            double s[4];
+            or_parity(bc, 0, s);
+            ii = ii < 0 ? -1 - ii : 2 * nx - 1 - ii;
+            for (int v = 0; v < 4; v++) { sa[v] *= s[v]; sx[v] *= -s[v]; sy[v] *= s[v]; }
         }
     }
     size_t n = (size_t)nx * ny, at = (size_t)jj * nx + ii;
@@ -621,7 +667,7 @@ static void or_grad_cell(or_work* W, int i, int j) {
                 d17[15 + t] = W->rm[18 * IDX(W, i + a, j + b) + o + 2];
             }
             or_hweno h;
-            or_hweno_build(d17, c->eps_weno, c->linear_weights, &h);
+            or_hweno_build(d17, c->eps_weno, c->linear_weights || c->linear_grad, &h);
             for (int k = 0; k < 21; k++) {
                 double xi, eta;
                 if (k < 12) or_face_point(k, &xi, &eta); else or_vol_point(k - 12, &xi, &eta);

@@ -81,6 +81,9 @@ typedef struct {
     int max_halvings, linear_weights, limiter, scheme;
     int source, pad2_;
     double time;
+    double inflow[4][2][4];
+    double band[4][2];
+    int linear_grad, pad3_;
 } or_cfg_plain;
 
 /* the dual configuration: mu = 1/Re moves with tangent dmu, so dRe = -Re^2 dmu */
@@ -100,6 +103,14 @@ static void or_cfg_dual(const or_cfg_plain* a, double dmu, or_cfg* b) {
     b->source = a->source;
     b->pad2_ = 0;
     b->time = a->time;
+    for (int s = 0; s < 4; s++) {
+        for (int k = 0; k < 2; k++)
+            for (int v = 0; v < 4; v++) b->inflow[s][k][v] = a->inflow[s][k][v];
+        b->band[s][0] = a->band[s][0];
+        b->band[s][1] = a->band[s][1];
+    }
+    b->linear_grad = a->linear_grad;
+    b->pad3_ = 0;
 }
 
 extern "C" {

@@ -32,7 +32,7 @@ _lock = threading.Lock()
 _lib = None
 _jvp = None
 
-BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3}
+BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3, "inflow": 4, "outflow": 5}
 # viscous gradients: HWENO-GR (weak-derivative moments) or HWENO-DR (differentiated
 # convective candidates, the comparison scheme)
 SCHEME = {"gr": 0, "dr": 1, 0: 0, 1: 1}
@@ -50,7 +50,9 @@ class _Cfg(ctypes.Structure):
                 ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("linear_weights", ctypes.c_int),
                 ("limiter", ctypes.c_int), ("scheme", ctypes.c_int),
-                ("source", ctypes.c_int), ("pad2_", ctypes.c_int), ("time", ctypes.c_double)]
+                ("source", ctypes.c_int), ("pad2_", ctypes.c_int), ("time", ctypes.c_double),
+                ("inflow", ((ctypes.c_double * 4) * 2) * 4), ("band", (ctypes.c_double * 2) * 4),
+                ("linear_grad", ctypes.c_int), ("pad3_", ctypes.c_int)]
 
 
 def build(force=False):
@@ -112,7 +114,9 @@ def _ptr(a):
 def make_cfg(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
              bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
              max_halvings=20, linear_weights=False, limiter=True, scheme="gr", source=0, time=0.0,
-             **_ignored):
+             inflow=None, band=None, linear_grad=False, **_ignored):
+    """inflow: per side (xlo, xhi, ylo, yhi) None or a pair of conserved states (A, B);
+    band: per side (centre, half-width) of the face coordinate where A applies"""
     c = _Cfg()
     c.nx, c.ny = int(nx), int(ny)
     c.x0, c.x1, c.y0, c.y1 = float(x0), float(x1), float(y0), float(y1)
@@ -126,6 +130,17 @@ def make_cfg(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000
     c.scheme = SCHEME[scheme]
     c.source = SOURCE[source]
     c.time = float(time)
+    c.linear_grad = 1 if linear_grad else 0
+    for k in range(4):
+        st = inflow[k] if inflow and inflow[k] is not None else None
+        if c.bc[k] == 4 and st is None:
+            raise ValueError("an inflow side needs its states")
+        if st is not None:
+            for a in range(2):
+                for v in range(4):
+                    c.inflow[k][a][v] = float(st[a][v])
+        if band and band[k] is not None:
+            c.band[k][0], c.band[k][1] = float(band[k][0]), float(band[k][1])
     mirror = any(c.bc[k] != 0 for k in range(4))
     if mirror and (c.nx < 4 or c.ny < 4):
         raise ValueError("mirror boundaries need at least 4 cells per direction")

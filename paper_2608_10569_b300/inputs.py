@@ -39,6 +39,8 @@ class Case:
     eps_weno: float = 1e-8
     max_halvings: int = 20
     source: int = 0          # 1: Example 5.2's manufactured source term
+    inflow: tuple = None     # per side None or conserved states (A, B) of an inflow face
+    band: tuple = None       # per side (centre, half-width) of the face coordinate where A applies
     t_end: float = 0.0
     extra: dict = field(default_factory=dict)
 
@@ -259,6 +261,35 @@ def manufactured(n, t=0.0, Re=100.0):
     initial state, t = T the reference of the error table)."""
     case = Case("manufactured_%d" % n, n, n, 0.0, 1.0, 0.0, 1.0, 1.4, 0.72, Re, source=1, t_end=0.1)
     return case, cell_moments(case, lambda x, y: manufactured_prim(x, y, t, case.gamma))
+
+
+def sedov_2d(n, Re=1000.0):
+    """Example 5.7's 2D Sedov blast: [0, 1.1]^2, rho = 1, u = v = 0, E = 0.244816/(dx dy) in
+    the corner cell and 1e-12 elsewhere (gamma 1.4), reflective (symmetry) faces at x = 0
+    and y = 0, outflow at x = 1.1 and y = 1.1, Re 1000, T = 1"""
+    case = Case("sedov_2d_%d" % n, n, n, 0.0, 1.1, 0.0, 1.1, 1.4, 0.72, Re,
+                bc=("symmetry", "outflow", "symmetry", "outflow"), t_end=1.0)
+    q = np.zeros((12, n, n))
+    q[0] = 1.0
+    q[3] = 1e-12
+    q[3, 0, 0] = 0.244816 / (case.dx * case.dy)
+    return case, q
+
+
+def mach2000(nx=640, ny=320, Re=1000.0):
+    """Example 5.8's Mach-2000 jet: [0, 1] x [-0.25, 0.25], ambient (rho, u, v, p) =
+    (0.5, 0, 0, 0.4127), gamma 5/3; inflow at x = 0 of (5, 800, 0, 0.4127) for |y| < 0.05
+    and (5, 0, 0, 0.4127) elsewhere; outflow on the other sides; Re 1000, T = 0.001"""
+    g = 5.0 / 3.0
+    jet = conserved(5.0, 800.0, 0.0, 0.4127, g)
+    still = conserved(5.0, 0.0, 0.0, 0.4127, g)
+    case = Case("mach2000_%dx%d" % (nx, ny), nx, ny, 0.0, 1.0, -0.25, 0.25, g, 0.72, Re,
+                bc=("inflow", "outflow", "outflow", "outflow"), t_end=0.001,
+                inflow=((tuple(jet), tuple(still)), None, None, None), band=((0.0, 0.05), None, None, None))
+    q = np.zeros((12, ny, nx))
+    for v, val in enumerate(conserved(0.5, 0.0, 0.0, 0.4127, g)):
+        q[v] = val
+    return case, q
 
 
 def random_smooth(nx, ny, seed=0, bc=("periodic",) * 4, gamma=1.4, Re=500.0, Pr=0.72,
