@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libhweno.so")
-SOURCES = ["hweno.cu"]
+SOURCES = ["hweno.cu", "hweno1d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,6 +32,7 @@ def stale():
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, d) for d in os.listdir(CSRC) if d.endswith((".cu", ".cuh", ".h"))]
     deps.append(os.path.join(ROOT, "include", "hweno.h"))
+    deps.append(os.path.join(ROOT, "include", "hweno1d.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -64,6 +64,20 @@ class hweno_diag(ctypes.Structure):
                 ("steps", ctypes.c_longlong), ("rejected", ctypes.c_longlong)]
 
 
+class hweno1d_config(ctypes.Structure):
+    """include/hweno1d.h: one problem of the one-dimensional solver (Sec. 2)"""
+    _fields_ = [("n", ctypes.c_int), ("bc", ctypes.c_int * 2), ("scheme", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("b_visc", ctypes.c_double),
+                ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
+                ("max_halvings", ctypes.c_int), ("source", ctypes.c_int),
+                ("inflow", (ctypes.c_double * 3) * 2)]
+
+
+BC1D = {"periodic": 0, "reflective": 1, "inflow": 2, "outflow": 3}
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported entry point
@@ -106,6 +120,15 @@ SIGNATURES = [
     ("hweno_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("hweno_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("hweno_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("hweno1d_config_default", ctypes.c_int, [ctypes.POINTER(hweno1d_config)]),
+    ("hweno1d_advance", ctypes.c_int, [ctypes.POINTER(hweno1d_config), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, _D, ctypes.c_void_p]),
+    ("hweno1d_step", ctypes.c_int, [ctypes.POINTER(hweno1d_config), ctypes.c_void_p, ctypes.c_double,
+                                    ctypes.c_double, _D, ctypes.c_void_p]),
+    ("hweno1d_residual", ctypes.c_int, [ctypes.POINTER(hweno1d_config), ctypes.c_void_p, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("hweno1d_last_error", ctypes.c_char_p, []),
 ]
 
 
@@ -489,3 +512,78 @@ def rollout(q0, mu, case_params, nsteps, ckpt=20):
         mu = torch.tensor(float(mu), dtype=torch.float64, device=q0.device)
     record = torch.is_grad_enabled() and (q0.requires_grad or mu.requires_grad)
     return _ROLLOUT.apply(q0, mu, case_params, int(nsteps), int(ckpt), bool(record))
+
+
+# ---------------------------------------------------------------------------
+# one-dimensional solver (include/hweno1d.h)
+
+def make_config1d(n, x0=0.0, x1=1.0, gamma=1.4, Pr=0.72, Re=1000.0, bc=("periodic", "periodic"), cfl=0.6,
+                  b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8, max_halvings=20, scheme="gr", source=0,
+                  inflow=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), **_ignored):
+    c = hweno1d_config()
+    load().hweno1d_config_default(ctypes.byref(c))
+    c.n = int(n)
+    for k in range(2):
+        c.bc[k] = BC1D[bc[k]] if isinstance(bc[k], str) else int(bc[k])
+    c.x0, c.x1 = float(x0), float(x1)
+    c.gamma, c.Pr, c.Re = float(gamma), float(Pr), float(Re)
+    c.cfl, c.b_visc, c.eps_pp, c.eps_weno = float(cfl), float(b_visc), float(eps_pp), float(eps_weno)
+    c.max_halvings = int(max_halvings)
+    c.scheme = SCHEME[scheme]
+    c.source = {None: 0, "none": 0, "mms51": 1, 0: 0, 1: 1}[source]
+    for k in range(2):
+        for v in range(3):
+            c.inflow[k][v] = float(inflow[k][v])
+    return c
+
+
+def _dev1d(a):
+    """device pointer of a CUDA float64 tensor (the 1D ABI takes device buffers only)"""
+    ptr, dev = _ptr_of(a)
+    if not dev:
+        raise ValueError("the 1D solver takes CUDA tensors")
+    return ptr
+
+
+def _check1d(rc):
+    if rc != HWENO_OK:
+        raise HwenoError(rc, load().hweno1d_last_error().decode())
+
+
+def advance1d(params_list, states, t0, t_end, max_steps=2 ** 31 - 1, stream=None):
+    """Advance several 1D problems together (one thread block each) from t0 to t_end.
+    states: CUDA float64 tensors of shape (6, n_k), updated in place.  Returns one
+    dict per problem: t, steps, rejections, status."""
+    lib = load()
+    n = len(params_list)
+    cfgs = (hweno1d_config * n)(*[make_config1d(**p) for p in params_list])
+    ptrs = (ctypes.c_void_p * n)(*[_dev1d(q).value for q in states])
+    out = np.zeros(4 * n)
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check1d(lib.hweno1d_advance(cfgs, n, ptrs, float(t0), float(t_end), int(max_steps),
+                                 out.ctypes.data_as(_D), s))
+    return [{"t": out[4 * k], "steps": int(out[4 * k + 1]), "rejections": int(out[4 * k + 2]),
+             "status": int(out[4 * k + 3])} for k in range(n)]
+
+
+def step1d(params, state, t, dt=0.0, stream=None):
+    """One SSP-RK3 step of a 1D problem (state a CUDA (6, n) tensor, in place)."""
+    lib = load()
+    c = make_config1d(**params)
+    out = np.zeros(3)
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check1d(lib.hweno1d_step(ctypes.byref(c), _dev1d(state), float(t), float(dt),
+                              out.ctypes.data_as(_D), s))
+    return {"dt": out[0], "rejections": int(out[1]), "status": int(out[2])}
+
+
+def residual1d(params, state, t=0.0, stream=None):
+    """Eq. (2.2) at state (CUDA (6, n) tensor) and time t: (rhs (6, n), vhat (3, n))."""
+    import torch
+    lib = load()
+    c = make_config1d(**params)
+    rhs = torch.empty((6, c.n), dtype=torch.float64, device="cuda")
+    vhat = torch.empty((3, c.n), dtype=torch.float64, device="cuda")
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check1d(lib.hweno1d_residual(ctypes.byref(c), _dev1d(state), float(t), _dev1d(rhs), _dev1d(vhat), s))
+    return rhs, vhat

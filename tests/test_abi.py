@@ -10,9 +10,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    txt = open(os.path.join(ROOT, "include", "hweno.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(hweno_[a-z_0-9]+)\s*\(", txt)))
+    names = set()
+    for h in ("hweno.h", "hweno1d.h"):
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(hweno1?d?_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -132,3 +135,27 @@ def test_source_is_validated_before_any_device_call(lib):
     c = hweno.make_config(8, 8, source="mms52")
     assert lib.hweno_residual_noalloc(ctypes.byref(c), buf, buf, None, None) == hweno.HWENO_ERR_ARG
     assert b"source" in lib.hweno_last_error(None)
+
+
+def test_1d_configurations_are_validated_before_any_device_call(lib):
+    """the 1D entry points check every problem's configuration on the host: cell count,
+    boundary codes and periodic pairing, scheme, source and the physical constants"""
+    from paper_2608_10569_b300 import hweno
+    c = hweno.make_config1d(40)
+    assert (c.cfl, c.b_visc, c.eps_pp, c.eps_weno, c.gamma, c.Pr) == (0.6, 1e-3, 1e-12, 1e-8, 1.4, 0.72)
+    bad = [dict(n=3), dict(n=40, bc=("periodic", "outflow")), dict(n=40, scheme=2), dict(n=40, Re=0.0),
+           dict(n=40, source=3), dict(n=hweno_max_cells() + 1)]
+    ptr = (ctypes.c_void_p * 1)(ctypes.c_void_p(8).value)
+    for kw in bad:
+        kw = dict(kw)
+        scheme, source = kw.pop("scheme", "gr"), kw.pop("source", 0)
+        c = hweno.make_config1d(**kw)
+        c.scheme, c.source = scheme if isinstance(scheme, int) else 0, source
+        rc = lib.hweno1d_advance(ctypes.byref(c), 1, ptr, 0.0, 1.0, 1, None, None)
+        assert rc == hweno.HWENO_ERR_ARG, kw
+        assert lib.hweno1d_last_error()
+
+
+def hweno_max_cells():
+    txt = open(os.path.join(ROOT, "include", "hweno1d.h")).read()
+    return int(re.search(r"#define HWENO1D_MAX_CELLS (\d+)", txt).group(1))
