@@ -56,14 +56,14 @@ def emit():
            "// One-dimensional unified-stencil HWENO constants of Appendix A.1 as straight-line code.",
            "#pragma once", "",
            "// p0 coefficients (xi^0..xi^4) from the five stencil data",
-           "template <class T> __device__ __forceinline__ void hw1_p0_coeffs(const T* d, T* c) {"]
+           "template <class T> __host__ __device__ __forceinline__ void hw1_p0_coeffs(const T* d, T* c) {"]
     for k in range(5):
         terms = [f"{lit(M[k, m])} * d[{m}]" for m in range(5) if M[k, m] != 0]
         out.append(f"  c[{k}] = " + " + ".join(terms) + ";")
     out += ["}", "",
             "// smoothness indicator of a quartic: sum over orders 1..4 of the cell integral of the",
             "// squared derivative (a quadratic form in its coefficients)",
-            "template <class T> __device__ __forceinline__ T hw1_beta_quartic(const T* c) {",
+            "template <class T> __host__ __device__ __forceinline__ T hw1_beta_quartic(const T* c) {",
             "  T s = T(0);"]
     for a in range(5):
         for b in range(a, 5):
@@ -72,7 +72,7 @@ def emit():
                 out.append(f"  s += {lit(v)} * c[{a}] * c[{b}];")
     out += ["  return s;", "}", "",
             "// modified moment int xi p(xi) over the centre cell of a quartic",
-            "template <class T> __device__ __forceinline__ T hw1_moment(const T* c) {",
+            "template <class T> __host__ __device__ __forceinline__ T hw1_moment(const T* c) {",
             "  return " + " + ".join(f"{lit(mom[k])} * c[{k}]" for k in range(5) if mom[k] != 0) + ";",
             "}", ""]
     return "\n".join(out)

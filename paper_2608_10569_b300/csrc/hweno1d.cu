@@ -1,6 +1,7 @@
 // B300 (sm_103a) one-dimensional HWENO-GR / HWENO-DR solver (Sec. 2 of Guo, Fan, Zhao,
 // arXiv 2608.10569) and the C ABI declared in include/hweno1d.h.
 //
+// The per-cell functions are __host__ __device__: they hold no thread-level state.
 // One thread block owns one problem: its threads stride over the cells in each phase
 // of the spatial operator (ghost fill, characteristic reconstruction and limiter,
 // gradients, interface fluxes, moment balances), with __syncthreads between phases;
@@ -49,7 +50,7 @@ struct Ptrs {
   double *r0, *r, *m0, *m, *q1, *q2, *q3;                // [k][n]
 };
 
-__device__ __forceinline__ Ptrs layout(const Prob& p) {
+__host__ __device__ __forceinline__ Ptrs layout(const Prob& p) {
   const long long P = p.n + 2 * G;
   double* a = p.w;
   Ptrs s;
@@ -71,16 +72,16 @@ __device__ __forceinline__ Ptrs layout(const Prob& p) {
   return s;
 }
 
-__device__ __forceinline__ double lnode(int g) { return g == 0 ? -0.5 : (g == 1 ? -SQ5_10 : (g == 2 ? SQ5_10 : 0.5)); }
-__device__ __forceinline__ double lweight(int g) { return (g == 0 || g == 3) ? 1.0 / 12.0 : 5.0 / 12.0; }
+__host__ __device__ __forceinline__ double lnode(int g) { return g == 0 ? -0.5 : (g == 1 ? -SQ5_10 : (g == 2 ? SQ5_10 : 0.5)); }
+__host__ __device__ __forceinline__ double lweight(int g) { return (g == 0 || g == 3) ? 1.0 / 12.0 : 5.0 / 12.0; }
 
-__device__ __forceinline__ double pressure(const double* u, double g) {
+__host__ __device__ __forceinline__ double pressure(const double* u, double g) {
   return (g - 1.0) * (u[2] - 0.5 * u[1] * u[1] / u[0]);
 }
 
 // ---------------------------------------------------------------------------
 // ghost fill of the padded state (Remark 4.1); k = padded index, cell i = k - G
-__device__ void fetch(const Prob& p, const double* q, int i, double* out) {
+__host__ __device__ void fetch(const Prob& p, const double* q, int i, double* out) {
   const int n = p.n;
   if (i >= 0 && i < n) {
 #pragma unroll
@@ -114,7 +115,7 @@ __device__ void fetch(const Prob& p, const double* q, int i, double* out) {
 // scalar HWENO (Appendix A.1) as the coefficients of the combined polynomial: the
 // weights are constant over the cell, so Eq. (2.4)'s combination of the candidates is
 // one quartic C; its values, derivatives (Eq. (2.5)) and moment follow from C
-__device__ void hweno1(const double* d, double eps, double* C) {
+__host__ __device__ void hweno1(const double* d, double eps, double* C) {
   double c0[5];
   hw1_p0_coeffs<double>(d, c0);
   const double sm = d[1] - d[0], sp = d[2] - d[1];
@@ -133,15 +134,15 @@ __device__ void hweno1(const double* d, double eps, double* C) {
   C[1] += a1 * sm + a2 * sp;
 }
 
-__device__ __forceinline__ double poly5(const double* C, double x) {
+__host__ __device__ __forceinline__ double poly5(const double* C, double x) {
   return C[0] + x * (C[1] + x * (C[2] + x * (C[3] + x * C[4])));
 }
-__device__ __forceinline__ double dpoly5(const double* C, double x) {
+__host__ __device__ __forceinline__ double dpoly5(const double* C, double x) {
   return C[1] + x * (2.0 * C[2] + x * (3.0 * C[3] + x * 4.0 * C[4]));
 }
 
 // eigenvectors of the Jacobian of f^a at u (fields u - c, u, u + c) and their inverse
-__device__ void eigen(const double* ub, double g, double L[3][3], double R[3][3]) {
+__host__ __device__ void eigen(const double* ub, double g, double L[3][3], double R[3][3]) {
   const double rho = ub[0], u = ub[1] / rho;
   const double p = pressure(ub, g);
   const double c = sqrt(g * p / rho);
@@ -157,7 +158,7 @@ __device__ void eigen(const double* ub, double g, double L[3][3], double R[3][3]
 
 // characteristic reconstruction of padded cell k (Sec. 2.1, Eq. (2.4)): the Lobatto
 // values, their x-derivatives (Eq. (2.5)) and the modified moment, then the limiter
-__device__ void cons_cell(const Prob& p, const Ptrs& s, int k) {
+__host__ __device__ void cons_cell(const Prob& p, const Ptrs& s, int k) {
   const long long P = p.n + 2 * G;
   double ub[3], ql[6], qr[6];
   for (int v = 0; v < 3; v++) ub[v] = s.Q[v * P + k];
@@ -237,17 +238,17 @@ __device__ void cons_cell(const Prob& p, const Ptrs& s, int k) {
     for (int v = 0; v < 3; v++) s.pts[(3 * g + v) * P + k] = pts[g][v];
 }
 
-__device__ __forceinline__ void dissip(const double* st, double* w) {
+__host__ __device__ __forceinline__ void dissip(const double* st, double* w) {
   w[0] = st[1] / st[0];
   w[1] = st[2] / st[0] - 0.5 * w[0] * w[0];
 }
 
-__device__ __forceinline__ void point(const Ptrs& s, long long P, int k, int g, double* st) {
+__host__ __device__ __forceinline__ void point(const Ptrs& s, long long P, int k, int g, double* st) {
   for (int v = 0; v < 3; v++) st[v] = s.pts[(3 * g + v) * P + k];
 }
 
 // Eqs. (2.6), (2.8): interface averages and weak moments of u_x, e_x in padded cell k
-__device__ void weak_cell(const Prob& p, const Ptrs& s, int k) {
+__host__ __device__ void weak_cell(const Prob& p, const Ptrs& s, int k) {
   const long long P = p.n + 2 * G;
   double a[3], b[3], wa[2], wb[2], wl[2], wr[2], wbar[2] = {0.0, 0.0};
   point(s, P, k - 1, 3, a); point(s, P, k, 0, b);
@@ -268,7 +269,7 @@ __device__ void weak_cell(const Prob& p, const Ptrs& s, int k) {
 }
 
 // Eq. (2.9): GR gradients at the Lobatto points of padded cell k
-__device__ void grad_cell(const Prob& p, const Ptrs& s, int k) {
+__host__ __device__ void grad_cell(const Prob& p, const Ptrs& s, int k) {
   const long long P = p.n + 2 * G;
   for (int n = 0; n < 2; n++) {
     const double* A = s.rw + (2 * n) * P;
@@ -281,7 +282,7 @@ __device__ void grad_cell(const Prob& p, const Ptrs& s, int k) {
 }
 
 // Eq. (2.5) then the chain rule with the limited values: DR gradients of cell k
-__device__ void dr_cell(const Prob& p, const Ptrs& s, int k) {
+__host__ __device__ void dr_cell(const Prob& p, const Ptrs& s, int k) {
   const long long P = p.n + 2 * G;
   for (int g = 0; g < 4; g++) {
     double st[3];
@@ -296,7 +297,7 @@ __device__ void dr_cell(const Prob& p, const Ptrs& s, int k) {
 }
 
 // f = f^a - f^d of Eq. (2.1), tau = 4/3 u_x / Re, q = -g e_x / (Pr Re)
-__device__ __forceinline__ void phys_flux(const Prob& p, const double* st, double ux, double ex, double* f) {
+__host__ __device__ __forceinline__ void phys_flux(const Prob& p, const double* st, double ux, double ex, double* f) {
   const double rho = st[0], u = st[1] / rho, pr = pressure(st, p.gamma);
   const double tau = (4.0 / 3.0) * ux * p.rRe, qh = -p.gamma * ex * p.rPr * p.rRe;
   f[0] = rho * u;
@@ -305,7 +306,7 @@ __device__ __forceinline__ void phys_flux(const Prob& p, const double* st, doubl
 }
 
 // max(|u| + c, the PP wave-speed bound of Eq. (2.3))
-__device__ __forceinline__ double wave_bound(const Prob& p, const double* st, double ux, double ex) {
+__host__ __device__ __forceinline__ double wave_bound(const Prob& p, const double* st, double ux, double ex) {
   const double rho = st[0], u = st[1] / rho, pr = pressure(st, p.gamma);
   const double e = pr / ((p.gamma - 1.0) * rho);
   const double tau = (4.0 / 3.0) * ux * p.rRe, qh = -p.gamma * ex * p.rPr * p.rRe;
@@ -315,7 +316,7 @@ __device__ __forceinline__ double wave_bound(const Prob& p, const double* st, do
 }
 
 // Example 5.1's source at (x, t), and its cell average and scaled moment (4-point Gauss)
-__device__ void mms_source(const Prob& p, double x, double t, double* S) {
+__host__ __device__ void mms_source(const Prob& p, double x, double t, double* S) {
   const double a = 0.2 * exp(-t);
   double sn, cs;
   sincos(TWO_PI * x, &sn, &cs);
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(const Prob* probs, int mode, 
       rej++;
       dt *= 0.5;
     }
-    if (!ok) { status = HWENO_ERR_INADMISSIBLE; rej_total += rej; break; }
+    if (!ok) { status = HWENO_ERR_INADMISSIBLE; break; }  // restarts count for accepted steps only
     for (int i = threadIdx.x; i < 6 * n; i += blockDim.x) p.q[i] = s.q3[i];
     __syncthreads();
     t += dt;

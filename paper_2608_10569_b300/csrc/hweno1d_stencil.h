@@ -3,7 +3,7 @@
 #pragma once
 
 // p0 coefficients (xi^0..xi^4) from the five stencil data
-template <class T> __device__ __forceinline__ void hw1_p0_coeffs(const T* d, T* c) {
+template <class T> __host__ __device__ __forceinline__ void hw1_p0_coeffs(const T* d, T* c) {
   c[0] = T(-0.11197916666666667) * d[0] + T(1.2239583333333333) * d[1] + T(-0.11197916666666667) * d[2] + T(-0.421875) * d[3] + T(0.421875) * d[4];
   c[1] = T(-0.8289473684210527) * d[0] + T(0.8289473684210527) * d[2] + T(-3.9473684210526314) * d[3] + T(-3.9473684210526314) * d[4];
   c[2] = T(1.4375) * d[0] + T(-2.875) * d[1] + T(1.4375) * d[2] + T(5.625) * d[3] + T(-5.625) * d[4];
@@ -13,7 +13,7 @@ template <class T> __device__ __forceinline__ void hw1_p0_coeffs(const T* d, T* 
 
 // smoothness indicator of a quartic: sum over orders 1..4 of the cell integral of the
 // squared derivative (a quadratic form in its coefficients)
-template <class T> __device__ __forceinline__ T hw1_beta_quartic(const T* c) {
+template <class T> __host__ __device__ __forceinline__ T hw1_beta_quartic(const T* c) {
   T s = T(0);
   s += T(1.0) * c[1] * c[1];
   s += T(0.5) * c[1] * c[3];
@@ -25,6 +25,6 @@ template <class T> __device__ __forceinline__ T hw1_beta_quartic(const T* c) {
 }
 
 // modified moment int xi p(xi) over the centre cell of a quartic
-template <class T> __device__ __forceinline__ T hw1_moment(const T* c) {
+template <class T> __host__ __device__ __forceinline__ T hw1_moment(const T* c) {
   return T(0.08333333333333333) * c[1] + T(0.0125) * c[3];
 }

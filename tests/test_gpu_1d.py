@@ -1,0 +1,127 @@
+"""GPU parity of the 1D solver (include/hweno1d.h, one thread block per problem)
+against the 1D oracle on the same seeded inputs: residuals at relative 1e-12 (relative
+to the flux terms a residual is computed from, and to the state for the modified
+moments), steps at 1e-12, whole runs at relative L1 1e-9 with the same step counts,
+several problems of different sizes and boundaries in one launch, and the restart
+path of the double rarefaction.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2608_10569_b300 import hweno, inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def flux_scale(p, q):
+    """per conserved variable: max over cells of (|F_v| + (|u| + c)|U_v|)/h with the
+    inviscid flux F of the cell averages"""
+    g = p["gamma"]
+    rho, m, E = q[0], q[1], q[2]
+    u = m / rho
+    pr = (g - 1) * (E - 0.5 * rho * u * u)
+    c = np.sqrt(np.maximum(g * pr / rho, 0.0))
+    F = [m, m * u + pr, (E + pr) * u]
+    U = [rho, m, E]
+    h = (p["x1"] - p["x0"]) / p["n"]
+    return np.array([(np.abs(F[v]) + (np.abs(u) + c) * np.abs(U[v])).max() for v in range(3)]) / h
+
+
+def rel(a, b, scale):
+    return max(np.abs(a[k] - b[k]).max() / max(np.abs(b[k]).max(), scale[k % 3]) for k in range(a.shape[0]))
+
+
+def state_scale(q):
+    return np.abs(q[:3]).max(axis=1)
+
+
+CASES = {
+    "smooth_periodic_53": lambda: I.random_smooth_1d(53, seed=2),
+    "reflective_41": lambda: I.random_smooth_1d(41, seed=3, bc=("reflective", "reflective")),
+    "manufactured_40": lambda: I.manufactured_1d(40, 0.03),
+    "double_rarefaction_64": lambda: I.double_rarefaction(64),
+    "minimum_4": lambda: I.random_smooth_1d(4, seed=5),
+}
+
+
+@pytest.mark.parametrize("scheme", ["gr", "dr"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_residual_parity(name, scheme):
+    p, q = CASES[name]()
+    p = dict(p, scheme=scheme)
+    t = 0.03 if p.get("source") else 0.0
+    rhs, vh = hweno.residual1d(p, torch.from_numpy(q).cuda(), t)
+    o = O.residual1d(O.make_cfg1d(**p, time=t), q)
+    assert rel(rhs.cpu().numpy(), o["rhs"], flux_scale(p, q)) <= TOL
+    assert rel(vh.cpu().numpy(), o["vhat"], state_scale(q)) <= TOL
+
+
+def test_step_parity():
+    """a forced and a rule step"""
+    p, q = I.random_smooth_1d(37, seed=6, bc=("reflective", "outflow"))
+    cfg = O.make_cfg1d(**p)
+    qd = torch.from_numpy(q).cuda()
+    st = hweno.step1d(p, qd, 0.0, 2e-3)
+    assert st["dt"] == 2e-3 and st["rejections"] == 0 and st["status"] == 0
+    qo, _ = O.step1d(cfg, q, dt_fixed=2e-3)
+    assert rel(qd.cpu().numpy(), qo, state_scale(q)) <= TOL
+    st = hweno.step1d(p, qd, 2e-3)
+    qo2, so = O.step1d(cfg, qo, t=2e-3)
+    assert abs(st["dt"] - so["dt"]) <= 1e-13 * so["dt"]
+    assert rel(qd.cpu().numpy(), qo2, state_scale(q)) <= TOL
+
+
+def test_example_5_1_runs_in_one_launch():
+    """Example 5.1 at 40 and 80 cells for both schemes, four problems in one launch, to
+    T = 0.1: the oracle's step counts and relative L1 <= 1e-9"""
+    params, states, refs = [], [], []
+    for scheme in ("gr", "dr"):
+        for n in (40, 80):
+            p, q = I.manufactured_1d(n, 0.0)
+            p = dict(p, scheme=scheme)
+            params.append(p)
+            states.append(torch.from_numpy(q).cuda())
+            refs.append(O.advance1d(O.make_cfg1d(**p), q, 0.0, 0.1))
+    out = hweno.advance1d(params, states, 0.0, 0.1)
+    for st, o, (qo, so) in zip(states, out, refs):
+        assert o["status"] == 0 and o["steps"] == so["steps"] and abs(o["t"] - 0.1) < 1e-15
+        g = st.cpu().numpy()
+        assert max(np.abs(g[k] - qo[k]).sum() / np.abs(qo[k]).sum() for k in range(6)) <= 1e-9
+
+
+def test_mixed_problems_in_one_launch():
+    """problems of different sizes, schemes and boundaries advance independently in the
+    blocks of one launch"""
+    cases = [I.random_smooth_1d(53, seed=7), I.random_smooth_1d(20, seed=8, bc=("reflective", "reflective")),
+             I.double_rarefaction(30)]
+    params = [dict(cases[0][0]), dict(cases[1][0], scheme="dr"), dict(cases[2][0])]
+    states = [torch.from_numpy(q).cuda() for _, q in cases]
+    out = hweno.advance1d(params, states, 0.0, 5e-3, max_steps=8)
+    for p, (_, q), st, o in zip(params, cases, states, out):
+        qo, so = O.advance1d(O.make_cfg1d(**p), q, 0.0, 5e-3, max_steps=8)
+        assert o["status"] == so["status"] and o["steps"] == so["steps"]
+        assert rel(st.cpu().numpy(), qo, state_scale(q)) <= 1e-11
+
+
+def test_restarts_like_the_oracle():
+    """a forced step far above the stable size on the double rarefaction drives a stage
+    inadmissible: the step is repeated from t^n with dt/2 until admissible (Sec. 5), with
+    the oracle's number of restarts and state; run on, the vacuum-forming problem ends in
+    HWENO_ERR_INADMISSIBLE (the design notes' finding) on both sides"""
+    p, q = I.double_rarefaction(64)
+    qd = torch.from_numpy(q).cuda()
+    st = hweno.step1d(p, qd, 0.0, 0.2)
+    qo, so = O.step1d(O.make_cfg1d(**p), q, dt_fixed=0.2)
+    assert so["status"] == 0 and so["rejections"] > 0
+    assert st["status"] == 0 and st["rejections"] == so["rejections"] and st["dt"] == so["dt"]
+    assert rel(qd.cpu().numpy(), qo, state_scale(q)) <= TOL
+    qd = torch.from_numpy(q).cuda()
+    (o,) = hweno.advance1d([p], [qd], 0.0, 0.6, max_steps=400)
+    _, so = O.advance1d(O.make_cfg1d(**p), q, 0.0, 0.6, max_steps=400)
+    assert so["status"] == hweno.HWENO_ERR_INADMISSIBLE == o["status"]
+    assert abs(o["t"] - so["t"]) <= 0.1 * so["t"]
