@@ -3,7 +3,8 @@ against the 1D oracle on the same seeded inputs: residuals at relative 1e-12 (re
 to the flux terms a residual is computed from, and to the state for the modified
 moments), steps at 1e-12, whole runs at relative L1 1e-9 with the same step counts,
 several problems of different sizes and boundaries in one launch, and the restart
-path of the double rarefaction.
+path of the double rarefaction.  The file sorts last so that the suite's earlier files
+run first under -x.
 """
 import numpy as np
 import pytest
