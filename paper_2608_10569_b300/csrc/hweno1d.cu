@@ -33,17 +33,18 @@ struct Prob {
   double x0, dx, rdx, gamma, rPr, rRe, cfl, visc_cap, eps_pp, eps_weno;
   double inflow[2][3];
   double* q;    // [6][n] state (device)
-  double* w;    // workspace (device), laid out by Lay
+  double* w;    // workspace (device), laid out by layout()
 };
 
-// workspace of one problem: padded arrays of P = n + 2G cells, then per-cell arrays
-struct Lay {
-  int P, n;
-  __host__ __device__ static long long doubles(int n) {
-    const long long P = n + 2 * G;
-    return P * (6 + 12 + 12 + 3 + 4 + 8 + 4) + (long long)n * (6 + 6 + 3 + 3 + 6 + 6 + 6);
-  }
-};
+// workspace of one problem: padded planes of P = n + 2G cells (state 6, Lobatto values
+// 12, their derivatives 12, modified moments 3, weak moments 4, gradients 8, fluxes 3,
+// LF coefficients 1), then planes of n cells (residuals 6 + 6, modified moments 3 + 3,
+// stage states 6 + 6 + 6)
+constexpr int PADDED_PLANES = 6 + 12 + 12 + 3 + 4 + 8 + 3 + 1;
+constexpr int CELL_PLANES = 6 + 6 + 3 + 3 + 6 + 6 + 6;
+__host__ __device__ inline long long workspace_doubles(int n) {
+  return (long long)(n + 2 * G) * PADDED_PLANES + (long long)n * CELL_PLANES;
+}
 
 struct Ptrs {
   double *Q, *pts, *dpts, *mom, *rw, *grad, *flux, *bf;  // padded, [k][P]
@@ -598,7 +599,7 @@ static int run(const hweno1d_config* cfgs, int nprob, double* const* q, int mode
     int rc = check_cfg(cfgs[k]);
     if (rc) return rc;
     if (!q[k]) return fail1(HWENO_ERR_ARG, "NULL state");
-    total += hw1::Lay::doubles(cfgs[k].n);
+    total += hw1::workspace_doubles(cfgs[k].n);
   }
   cudaStream_t st = (cudaStream_t)stream;
   double* work = nullptr;
@@ -611,7 +612,7 @@ static int run(const hweno1d_config* cfgs, int nprob, double* const* q, int mode
   long long off = 0;
   for (int k = 0; k < nprob; k++) {
     hp[k] = make_prob(cfgs[k], q[k], work + off);
-    off += hw1::Lay::doubles(cfgs[k].n);
+    off += hw1::workspace_doubles(cfgs[k].n);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, 4 * nprob * sizeof(double), st);
   if (e == cudaSuccess)
@@ -624,7 +625,7 @@ static int run(const hweno1d_config* cfgs, int nprob, double* const* q, int mode
   if (e == cudaSuccess && mode == 2) {
     const int n = cfgs[0].n;
     const long long P = n + 2 * hw1::G;
-    const double* r0 = work + P * (6 + 12 + 12 + 3 + 4 + 8 + 4);
+    const double* r0 = work + P * hw1::PADDED_PLANES;
     const double* m0 = r0 + 12LL * n;
     e = cudaMemcpyAsync(rhs, r0, 6 * (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && vhat)

@@ -97,7 +97,7 @@ int main(int argc, char** argv) {
   const double t0 = dh[15], t_end = dh[16];
   const int max_steps = (int)dh[17];
   const int n = c.n;
-  std::vector<double> q(6 * n), work(Lay::doubles(n));
+  std::vector<double> q(6 * n), work(workspace_doubles(n));
   if (fread(q.data(), sizeof(double), 6 * n, f) != (size_t)(6 * n)) return 3;
   fclose(f);
   Prob p = make_prob(c, q.data(), work.data());
