@@ -111,3 +111,37 @@ def test_gr_only_entry_points_reject_a_source():
     with pytest.raises(hweno.HwenoError) as e:
         hweno.Batch([case.params()], precision="fp64")
     assert e.value.code == hweno.HWENO_ERR_ARG
+
+
+def _table_5_2_gr():
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table_5_2_gr.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            n, linf, l1 = line.split()
+            rows[int(n)] = (float(linf), float(l1))
+    return rows
+
+
+def test_example_5_2_against_table_5_2():
+    """Example 5.2 with HWENO-GR to T = 0.1 at 80^2 and 120^2 under the Sec. 5 step rule:
+    the density errors are of Table 5.2's size (within a factor 1.6 in both norms; the
+    smoothness indicator is not printed) and fall at fifth order between the meshes"""
+    tab = _table_5_2_gr()
+    errs = {}
+    for n in (80, 120):
+        case, q = I.manufactured(n, 0.0)
+        s = hweno.Solver(case.params())
+        s.set_state(torch.from_numpy(q).cuda())
+        t, _ = s.advance(case.t_end)
+        assert t == case.t_end
+        _, qex = I.manufactured(n, case.t_end)
+        e = s.get_state().cpu().numpy()[0] - qex[0]
+        s.close()
+        errs[n] = (np.abs(e).max(), np.abs(e).mean())
+        for k in range(2):
+            assert tab[n][k] / 1.6 < errs[n][k] < 1.6 * tab[n][k], (n, errs[n], tab[n])
+    for k in range(2):
+        assert np.log(errs[80][k] / errs[120][k]) / np.log(1.5) > 4.8, errs
