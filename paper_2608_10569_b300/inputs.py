@@ -277,7 +277,7 @@ def sedov_2d(n, Re=1000.0):
 
 
 def mach2000(nx=640, ny=320, Re=1000.0):
-    """Example 5.8's Mach-2000 jet: [0, 1] x [-0.25, 0.25], ambient (rho, u, v, p) =
+    """Example 5.9's Mach-2000 jet: [0, 1] x [-0.25, 0.25], ambient (rho, u, v, p) =
     (0.5, 0, 0, 0.4127), gamma 5/3; inflow at x = 0 of (5, 800, 0, 0.4127) for |y| < 0.05
     and (5, 0, 0, 0.4127) elsewhere; outflow on the other sides; Re 1000, T = 0.001"""
     g = 5.0 / 3.0

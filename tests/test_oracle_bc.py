@@ -1,5 +1,5 @@
 """Pins of the oracle's inflow and outflow boundaries (Remark 4.1) and of the
-rectangular 2D benchmarks built on them (Examples 5.7 and 5.8, the survey's NEXT-4
+rectangular 2D benchmarks built on them (Examples 5.7 and 5.9, the survey's NEXT-4
 row): the ghost-cell rules as Remark 4.1 states them, free stream through open faces,
 the symmetries of the Sedov and Mach-2000 setups, and the linear-gradient ablation of
 Remark 3.1 acting on the gradients alone.
@@ -81,7 +81,7 @@ def test_sedov_setup_is_transpose_symmetric():
 
 
 def test_mach2000_setup_is_mirror_symmetric():
-    """Example 5.8: the jet band |y| < 0.05 and the outflow faces are symmetric under
+    """Example 5.9: the jet band |y| < 0.05 and the outflow faces are symmetric under
     y -> -y (v and the eta-moment odd), and so is the residual of the initial state"""
     case, q = I.mach2000(32, 16)
     cfg = O.make_cfg(**case.params())
