@@ -55,6 +55,15 @@ extern "C" {
 #define HWENO_BC_NOSLIP 1    /* stationary adiabatic no-slip wall: both momenta odd */
 #define HWENO_BC_SYMMETRY 2  /* reflective parity: normal momentum odd */
 #define HWENO_BC_SLIP 3      /* stationary slip wall: same parity as symmetry */
+#define HWENO_BC_INFLOW 4    /* prescribed state in the ghost cells (averages from
+                                hweno_config.inflow, moments 0) */
+#define HWENO_BC_OUTFLOW 5   /* ghost cells copy the adjacent interior cell (average and
+                                moments) */
+/* Corner ghost cells: a y-face inflow fills its ghost rows across the padded width;
+ * otherwise the y-face rule maps the row into the interior and the x-face rule then
+ * applies to that row (mirror parities multiply; an x-face inflow state takes the
+ * y mirror's parity).  Inflow and outflow faces are taken by solver handles and
+ * hweno_residual_noalloc, not by the batch or the adjoint (HWENO_ERR_ARG). */
 
 /* arithmetic of the spatial operator */
 #define HWENO_FP64 0  /* everything in FP64 */
@@ -94,6 +103,13 @@ typedef struct {
     int scheme;               /* HWENO_SCHEME_GR or HWENO_SCHEME_DR (handles only: the
                                  adjoint, the batch and hweno_residual_noalloc take GR) */
     int source;               /* HWENO_SOURCE_NONE or HWENO_SOURCE_MMS52 (handles only) */
+    double inflow[4][2][4];   /* per face (xlo, xhi, ylo, yhi) with HWENO_BC_INFLOW: the
+                                 conserved state (rho, rho u, rho v, E) of a ghost cell whose
+                                 centre lies inside [0] or outside [1] the face's band;
+                                 rho > 0 and p > 0 required; ignored on other faces */
+    double band[4][2];        /* per inflow face: centre c and half width w >= 0 of the band
+                                 |s - c| < w, s the ghost cell centre's coordinate along the
+                                 face (y on x-faces, x on y-faces; w = 0: state [1] alone) */
 } hweno_config;
 
 /* Diagnostics of the run so far (Sec. 5: PP-limiter percentage; Remark 3.1:

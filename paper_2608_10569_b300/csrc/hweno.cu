@@ -241,6 +241,7 @@ struct hweno_handle {
   bool prof = false;
   std::vector<EventPair> ev;
   Quad4 quad{};  // the source term's 4-point Gauss rule
+  Open open{};   // prescribed states of the inflow faces
   long long prof_n[K_NKIND];
   double prof_ms[K_NKIND];
   char err[512];
@@ -299,12 +300,12 @@ static void launch_ghost(hweno_handle* h, double* q, float* hilo = nullptr) {
   {
     Prof p(h, K_GHOST);
     const int n = 8 * g.ny;
-    k_ghost_x<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, q, hilo);
+    k_ghost_x<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, h->open, q, hilo);
   }
   {
     Prof p(h, K_GHOST);
     const int n = 8 * (g.nx + 2 * NG);
-    k_ghost_y<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, q, hilo);
+    k_ghost_y<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, h->open, q, hilo);
   }
 }
 
@@ -452,7 +453,39 @@ static double h_min(const hweno_handle* h) {
   return dx < dy ? dx : dy;
 }
 
-static int valid_bc(int b) { return b >= HWENO_BC_PERIODIC && b <= HWENO_BC_SLIP; }
+static int valid_bc(int b) { return b >= HWENO_BC_PERIODIC && b <= HWENO_BC_OUTFLOW; }
+
+static bool has_open_face(const hweno_config& c) {
+  for (int k = 0; k < 4; k++)
+    if (c.bc[k] == HWENO_BC_INFLOW || c.bc[k] == HWENO_BC_OUTFLOW) return true;
+  return false;
+}
+
+// the prescribed states of the inflow faces: finite, with rho > 0 and p > 0, and
+// bands of finite centre and half width >= 0
+static int check_inflow(const hweno_config& c) {
+  for (int k = 0; k < 4; k++) {
+    if (c.bc[k] != HWENO_BC_INFLOW) continue;
+    if (!isfinite(c.band[k][0]) || !isfinite(c.band[k][1]) || !(c.band[k][1] >= 0.0))
+      return fail(nullptr, HWENO_ERR_ARG, "an inflow band needs a finite centre and a half width >= 0");
+    for (int a = 0; a < 2; a++) {
+      const double* u = c.inflow[k][a];
+      bool ok = true;
+      for (int v = 0; v < 4; v++) ok = ok && isfinite(u[v]);
+      const double p = ok && u[0] > 0.0 ? (c.gamma - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0]) : -1.0;
+      if (!(u[0] > 0.0) || !(p > 0.0))
+        return fail(nullptr, HWENO_ERR_ARG, "an inflow state needs finite values with rho > 0 and p > 0");
+    }
+  }
+  return HWENO_OK;
+}
+
+static Open make_open(const hweno_config& c) {
+  Open o;
+  memcpy(o.state, c.inflow, sizeof(o.state));
+  memcpy(o.band, c.band, sizeof(o.band));
+  return o;
+}
 
 extern "C" {
 
@@ -497,6 +530,7 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
     return fail(nullptr, HWENO_ERR_ARG, "HWENO_SCHEME_DR runs in HWENO_FP64");
   if (c.source != HWENO_SOURCE_NONE && c.source != HWENO_SOURCE_MMS52)
     return fail(nullptr, HWENO_ERR_ARG, "source must be HWENO_SOURCE_NONE or HWENO_SOURCE_MMS52");
+  if (check_inflow(c)) return HWENO_ERR_ARG;
 
   h = new (std::nothrow) hweno_handle();
   if (!h) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
@@ -516,6 +550,7 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
   g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
   g.x0 = c.x0; g.y0 = c.y0;
+  h->open = make_open(c);
   {  // 4-point Gauss-Legendre on [-1/2, 1/2]: nodes sqrt(3/7 -+ 2/7 sqrt(6/5)) / 2,
      // weights (18 +- sqrt(30)) / 72
     const double ri = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0)), ro = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
@@ -973,6 +1008,8 @@ int hweno_adjoint_init(hweno_handle* h) {
   if (h->cfg.precision != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_FP64");
   if (h->cfg.scheme != HWENO_SCHEME_GR || h->cfg.source != HWENO_SOURCE_NONE)
     return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_SCHEME_GR without a source term");
+  if (has_open_face(h->cfg))
+    return fail(h, HWENO_ERR_ARG, "the adjoint takes periodic and wall faces, not inflow or outflow");
   if (h->apool) return HWENO_OK;
   const Grid& g = h->g;
   // R 12, M 8, face 48, vol 36, gr 126, rm 18, cg 102, cc 68, q 12, stage-1 state 12,
@@ -1443,6 +1480,9 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
     if (cfgs[c].scheme != HWENO_SCHEME_GR || cfgs[c].source != HWENO_SOURCE_NONE)
       return fail(nullptr, HWENO_ERR_ARG,
                   "hweno_batch_init: the batched kernels run HWENO_SCHEME_GR without a source term");
+  for (int c = 0; c < ncases; c++)
+    if (has_open_face(cfgs[c]))
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels take periodic and wall faces");
   hweno_batch* b = new (std::nothrow) hweno_batch();
   if (!b) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
   snprintf(b->err, sizeof(b->err), "no error");
@@ -1715,7 +1755,7 @@ static int noalloc_check_config(const hweno_config& c) {
     return fail(nullptr, HWENO_ERR_ARG, "precision must be HWENO_FP64 or HWENO_MIXED");
   if (c.scheme != HWENO_SCHEME_GR || c.source != HWENO_SOURCE_NONE)
     return fail(nullptr, HWENO_ERR_ARG, "hweno_residual_noalloc runs HWENO_SCHEME_GR without a source term");
-  return HWENO_OK;
+  return check_inflow(c);
 }
 
 extern "C" int hweno_residual_noalloc(const hweno_config* cfg, const double* q, double* rhs, double* vhat,
@@ -1753,6 +1793,7 @@ extern "C" int hweno_residual_noalloc(const hweno_config* cfg, const double* q, 
   tmp.cfg = c;
   tmp.st = (cudaStream_t)stream;
   tmp.g = g;
+  tmp.open = make_open(c);
   double* p = base;
   auto take = [&](long long n) { double* r = p; p += n * g.ps; return r; };
   double* Q = take(12);

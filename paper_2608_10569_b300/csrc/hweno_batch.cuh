@@ -132,12 +132,12 @@ __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncas
                          int split) {
   HW_BATCH_LOOP(L, ncase)
   double* q = which == 0 ? cd.Q : cd.QS;
-  if (pass == 0) ghost_x_body(cg, q, gx);
-  else ghost_y_body(cg, q, gx);
+  if (pass == 0) ghost_x_body(cg, (const Open*)nullptr, q, gx);
+  else ghost_y_body(cg, (const Open*)nullptr, q, gx);
   if (split) {
     float* hilo = mixed_planes(cw, cg.ps).hilo;
-    if (pass == 0) ghost_x_body(cg, hilo, gx, 0, 24);
-    else ghost_y_body(cg, hilo, gx, 0, 24);
+    if (pass == 0) ghost_x_body(cg, (const Open*)nullptr, hilo, gx, 0, 24);
+    else ghost_y_body(cg, (const Open*)nullptr, hilo, gx, 0, 24);
   }
   HW_BATCH_END
 }

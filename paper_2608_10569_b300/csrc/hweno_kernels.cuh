@@ -21,65 +21,15 @@
 #include <stdint.h>
 
 #include "hweno_device.cuh"
+#include "hweno_state.cuh"
 
 namespace hw {
-
-constexpr int NG = 4;  // ghost layers
-
-struct Grid {
-  int nx, ny, pitch;
-  long long ps;  // plane stride in doubles
-  double dx, dy;
-  double gamma, Pr, Re;
-  double eps_pp, eps_weno;
-  int bc[4];
-  double rdx, rdy, rPr, rRe;  // 1/dx, 1/dy, 1/Pr, 1/Re (correctly rounded, on the host)
-  double x0, y0;              // domain origin (coordinates of a source term)
-};
 
 // x is neither infinite nor NaN: an exponent-field test in the integer pipe
 __device__ __forceinline__ bool finite_d(double x) {
   return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
 }
 __device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
-
-// hi/lo split of the 12 ghost-filled state planes (whole padded planes), with integer
-// operations only: hi keeps the sign, the exponent and the leading 23 mantissa bits of
-// x (truncation), lo is the float nearest below the exact remainder x - hi (the trailing
-// 29 mantissa bits, normalised).  Zero gives (0, 0); magnitudes below 2^-74 or beyond
-// the float range take hi = fl(x), lo = 0.
-__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-  const int E = (int)((b >> 52) & 0x7ff);
-  const int fe = E - 1023 + 127;
-  if (E == 0) {  // zero (or a double denormal, below any float): signed zero
-    hi = __int_as_float((int)sign);
-    lo = 0.0f;
-    return;
-  }
-  // the remainder's float exponent field is fe - 52 + top >= fe - 52: keep it >= 1
-  if (fe < 53 || fe > 254) {  // |x| < 2^-74, beyond the float range, inf or nan
-    hi = (float)x;
-    lo = 0.0f;
-    return;
-  }
-  const unsigned long long m = b & 0xfffffffffffffull;
-  hi = __int_as_float((int)(sign | ((unsigned int)fe << 23) | (unsigned int)(m >> 29)));
-  const unsigned int r = (unsigned int)(m & 0x1fffffffull);  // remainder: r * 2^(E - 1075)
-  if (r == 0u) {
-    lo = 0.0f;
-    return;
-  }
-  const int top = 31 - __clz((int)r);          // highest set bit, 0..28
-  const int le = fe - 52 + top;                 // float exponent field of the remainder
-  const unsigned int mant = top >= 23 ? (r >> (top - 23)) : (r << (23 - top));
-  lo = __int_as_float((int)(sign | ((unsigned int)le << 23) | (mant & 0x7fffffu)));
-}
-
-__device__ __forceinline__ long long cidx(const Grid& g, int i, int j) {
-  return (long long)(j + NG) * g.pitch + (i + NG);
-}
 
 constexpr int YREC_CC = 144, YREC_GR = 204, YREC_PLANES = 306;
 
@@ -148,71 +98,17 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
   return v;
 }
 
-// ---------------------------------------------------------------------------
-// ghost cells (Remark 4.1).  x pass over the interior rows, then y pass over the
-// full padded width, so corners take the product of the two parities.
-// Mirror across a face with parity s per variable: ghost average = s * average,
-// moment normal to the face = -s * moment, tangential moment = s * moment.
-__device__ __forceinline__ double bc_sign(int bc, int normal_dir, int v) {
-  if (v == 0 || v == 3) return 1.0;
-  if (bc == 1) return -1.0;                 // no-slip: both momenta odd
-  return (v == 1 + normal_dir) ? -1.0 : 1.0;  // symmetry/slip: normal momentum odd
-}
-
-// planes [p0, p1) of the state (plane 4 m + v: moment m of variable v), or of its
-// hi/lo split (24 float planes: plane p holds state plane p mod 12)
-template <class E>
-__device__ __forceinline__ void ghost_x_body(const Grid& g, E* q, int t, int p0 = 0, int p1 = 12) {
-  // t over 8 ghost columns x ny rows
-  if (t >= 8 * g.ny) return;
-  const int j = t / 8, c = t % 8;
-  const int side = c / 4, k = c % 4;  // side 0: i = -1-k, side 1: i = nx+k
-  const int i = side == 0 ? -1 - k : g.nx + k;
-  const int bc = g.bc[side];
-  int src;
-  if (bc == 0) src = side == 0 ? ((i % g.nx) + g.nx) % g.nx : i % g.nx;
-  else src = side == 0 ? -1 - i : 2 * g.nx - 1 - i;
-  const long long d = cidx(g, i, j), s = cidx(g, src, j);
-  for (int p = p0; p < p1; p++) {
-    const int m = (p % 12) >> 2, v = p & 3;
-    E sg = E(1);
-    if (bc != 0) sg = E(bc_sign(bc, 0, v) * (m == 1 ? -1.0 : 1.0));
-    q[p * g.ps + d] = sg * q[p * g.ps + s];
-  }
-}
-
-template <class E>
-__device__ __forceinline__ void ghost_y_body(const Grid& g, E* q, int t, int p0 = 0, int p1 = 12) {
-  // t over 8 ghost rows x padded width
-  const int W = g.nx + 2 * NG;
-  if (t >= 8 * W) return;
-  const int r = t / W, i = t % W - NG;
-  const int side = r / 4, k = r % 4;
-  const int j = side == 0 ? -1 - k : g.ny + k;
-  const int bc = g.bc[2 + side];
-  int src;
-  if (bc == 0) src = side == 0 ? ((j % g.ny) + g.ny) % g.ny : j % g.ny;
-  else src = side == 0 ? -1 - j : 2 * g.ny - 1 - j;
-  const long long d = cidx(g, i, j), s = cidx(g, i, src);
-  for (int p = p0; p < p1; p++) {
-    const int m = (p % 12) >> 2, v = p & 3;
-    E sg = E(1);
-    if (bc != 0) sg = E(bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0));
-    q[p * g.ps + d] = sg * q[p * g.ps + s];
-  }
-}
-
 // one plane per blockIdx.y: 12 x the threads of a cell-wise loop over the planes;
 // with hilo, blockIdx.y = 12..35 fills the 24 planes of the state's hi/lo split too
-__global__ void k_ghost_x(Grid g, double* q, float* hilo) {
+__global__ void k_ghost_x(Grid g, const __grid_constant__ Open o, double* q, float* hilo) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
-  if (p < 12) ghost_x_body(g, q, t, p, p + 1);
-  else ghost_x_body(g, hilo, t, p - 12, p - 11);
+  if (p < 12) ghost_x_body(g, &o, q, t, p, p + 1);
+  else ghost_x_body(g, &o, hilo, t, p - 12, p - 11);
 }
-__global__ void k_ghost_y(Grid g, double* q, float* hilo) {
+__global__ void k_ghost_y(Grid g, const __grid_constant__ Open o, double* q, float* hilo) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
-  if (p < 12) ghost_y_body(g, q, t, p, p + 1);
-  else ghost_y_body(g, hilo, t, p - 12, p - 11);
+  if (p < 12) ghost_y_body(g, &o, q, t, p, p + 1);
+  else ghost_y_body(g, &o, hilo, t, p - 12, p - 11);
 }
 
 // ---------------------------------------------------------------------------

@@ -26,7 +26,7 @@ HWENO_SCHEME_GR = 0
 HWENO_SCHEME_DR = 1
 HWENO_SOURCE_NONE = 0
 HWENO_SOURCE_MMS52 = 1
-BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3}
+BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3, "inflow": 4, "outflow": 5}
 SCHEME = {"gr": HWENO_SCHEME_GR, "dr": HWENO_SCHEME_DR, HWENO_SCHEME_GR: HWENO_SCHEME_GR,
           HWENO_SCHEME_DR: HWENO_SCHEME_DR}
 SOURCE = {None: HWENO_SOURCE_NONE, "none": HWENO_SOURCE_NONE, "mms52": HWENO_SOURCE_MMS52,
@@ -52,7 +52,8 @@ class hweno_config(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("b_visc", ctypes.c_double),
                 ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("precision", ctypes.c_int),
-                ("scheme", ctypes.c_int), ("source", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("source", ctypes.c_int),
+                ("inflow", ((ctypes.c_double * 4) * 2) * 4), ("band", (ctypes.c_double * 2) * 4)]
 
 
 class hweno_diag(ctypes.Structure):
@@ -164,7 +165,9 @@ def _check(h, rc):
 
 def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
                 bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
-                max_halvings=20, precision="fp64", scheme="gr", source=0, **_ignored):
+                max_halvings=20, precision="fp64", scheme="gr", source=0, inflow=None, band=None, **_ignored):
+    """inflow: per face (xlo, xhi, ylo, yhi) None or the pair of conserved states (inside,
+    outside) the face's band; band: per face None or (centre, half width)"""
     c = hweno_config()
     load().hweno_config_default(ctypes.byref(c))
     c.nx, c.ny = int(nx), int(ny)
@@ -177,6 +180,13 @@ def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1
     c.precision = HWENO_MIXED if precision in ("mixed", HWENO_MIXED) else HWENO_FP64
     c.scheme = SCHEME[scheme]
     c.source = SOURCE[source]
+    for k in range(4):
+        if inflow and inflow[k] is not None:
+            for a in range(2):
+                for v in range(4):
+                    c.inflow[k][a][v] = float(inflow[k][a][v])
+        if band and band[k] is not None:
+            c.band[k][0], c.band[k][1] = float(band[k][0]), float(band[k][1])
     return c
 
 

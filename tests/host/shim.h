@@ -1,8 +1,9 @@
-// CUDA qualifiers and block primitives for running one thread block of the 1D kernel as
-// a single host thread (test infrastructure): barriers are no-ops, a warp shuffle
-// returns the lane's own value (a one-lane warp), and __syncthreads_or returns its
-// argument.  With blockDim.x = 1 every block-strided loop of the kernel visits all its
-// indices in order, so the kernel's own control flow and arithmetic run unchanged.
+// CUDA qualifiers and block primitives for running device code on the host (test
+// infrastructure): one thread block of a kernel becomes a single host thread, barriers
+// are no-ops, a warp shuffle returns the lane's own value (a one-lane warp), and
+// __syncthreads_or returns its argument.  With blockDim.x = 1 every block-strided loop
+// of a kernel visits all its indices in order, so the kernel's own control flow and
+// arithmetic run unchanged.
 #pragma once
 #include <cmath>
 #include <cstring>

@@ -159,3 +159,58 @@ def test_1d_configurations_are_validated_before_any_device_call(lib):
 def hweno_max_cells():
     txt = open(os.path.join(ROOT, "include", "hweno1d.h")).read()
     return int(re.search(r"#define HWENO1D_MAX_CELLS (\d+)", txt).group(1))
+
+
+def test_struct_mirrors_match_the_headers(tmp_path):
+    """the binding's ctypes structures have the C structures' size and field offsets"""
+    import shutil
+    import subprocess
+    from paper_2608_10569_b300 import hweno
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc is needed to compile against the headers")
+    structs = {"hweno_config": hweno.hweno_config, "hweno_diag": hweno.hweno_diag,
+               "hweno1d_config": hweno.hweno1d_config}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hweno.h"', '#include "hweno1d.h"',
+             "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for f in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = str(tmp_path / "layout")
+    subprocess.check_call([cc, "-std=c99", "-I" + os.path.join(ROOT, "include"), "-o", exe, str(src)])
+    seen = {}
+    for line in subprocess.check_output([exe]).decode().split("\n"):
+        if line:
+            s, f, v = line.split()
+            seen[(s, f)] = int(v)
+    for name, cls in structs.items():
+        assert seen[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert seen[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_open_faces_are_validated_before_any_device_call(lib):
+    """inflow states need rho > 0 and p > 0 and a band half width >= 0; the batch takes
+    no inflow or outflow face"""
+    from paper_2608_10569_b300 import hweno
+    h = ctypes.c_void_p()
+    good = (1.0, 0.5, 0.0, 2.5)
+    bad = [dict(inflow=((good, (0.0, 0.0, 0.0, 1.0)), None, None, None), band=((0.5, 0.1), None, None, None)),
+           dict(inflow=((good, (1.0, 2.0, 0.0, 1.0)), None, None, None), band=((0.5, 0.1), None, None, None)),
+           dict(inflow=((good, good), None, None, None), band=((0.5, -0.1), None, None, None)),
+           dict(inflow=((good, (1.0, float("nan"), 0.0, 2.0)), None, None, None), band=((0.5, 0.1), None, None, None))]
+    for kw in bad:
+        c = hweno.make_config(8, 8, bc=("inflow", "outflow", "symmetry", "symmetry"), **kw)
+        assert lib.hweno_init(ctypes.byref(c), None, ctypes.byref(h)) == hweno.HWENO_ERR_ARG, kw
+        assert h.value is None
+    ok = hweno.make_config(8, 8, bc=("inflow", "outflow", "symmetry", "symmetry"),
+                           inflow=((good, good), None, None, None), band=((0.5, 0.1), None, None, None))
+    b = ctypes.c_void_p()
+    cfgs = (hweno.hweno_config * 1)(ok)
+    assert lib.hweno_batch_init(cfgs, 1, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
+    assert b.value is None
+    assert b"periodic and wall" in lib.hweno_last_error(None)

@@ -1,7 +1,7 @@
 """The 1D solver's CUDA kernel run on the host, against the 1D oracle.
 
-`host1d/kernel1d_host.cc` compiles the kernel part of `hweno1d.cu` (everything before
-the launch-based part of its C ABI, extracted here) as plain C++ with `host1d/shim.h`:
+`host/kernel1d_host.cc` compiles the kernel part of `hweno1d.cu` (everything before
+the launch-based part of its C ABI, extracted here) as plain C++ with `host/shim.h`:
 one host thread stands for a thread block, barriers are no-ops and warp or block
 reductions see one lane, so every block-strided loop of `k_solve` visits its indices in
 order and the kernel's own control flow and arithmetic run unchanged.  This checks,
@@ -22,7 +22,7 @@ from paper_2608_10569_b300 import inputs as I
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-DIR = os.path.join(HERE, "host1d")
+DIR = os.path.join(HERE, "host")
 CSRC = os.path.join(ROOT, "paper_2608_10569_b300", "csrc")
 KERNEL = os.path.join(CSRC, "hweno1d.cu")
 MARKER = "// runs mode on nprob problems"

@@ -1,0 +1,195 @@
+"""GPU parity of the inflow and outflow faces (Remark 4.1; HWENO_BC_INFLOW and
+HWENO_BC_OUTFLOW) and of the rectangular benchmarks built on them (Examples 5.7 and
+5.9), against the FP64 oracle, with the tolerances of the other parity tests: relative
+L-infinity 1e-12 of the flux scale per residual plane, 1e-12 per step, relative L1 1e-9
+after a run.  Collected after the other GPU parity tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2608_10569_b300 import hweno, inputs as I  # noqa: E402
+from test_gpu_parity import (RES_TOL, flux_scale, gpu_residual, rel_l1, rel_linf, res_tol,  # noqa: E402
+                             state_scale)
+
+pytestmark = pytest.mark.gpu
+
+
+def open_rough():
+    """rough data entering through a banded inflow face (two states taken from the
+    first column), leaving through outflow faces, a symmetry face below"""
+    case, q = I.random_rough(40, 36, seed=9, bc=("inflow", "outflow", "symmetry", "outflow"), Re=200.0)
+    case.inflow = ((tuple(q[:4, 18, 0]), tuple(q[:4, 5, 0])), None, None, None)
+    case.band = ((0.5, 0.15), None, None, None)
+    return case, q
+
+
+def y_jet():
+    """a jet through a band of the lower face into smooth data, outflow elsewhere"""
+    case, q = I.random_smooth(33, 29, seed=10, bc=("outflow", "outflow", "inflow", "outflow"))
+    a = I.conserved(1.2, 0.1, 0.8, 1.5, case.gamma)
+    b = I.conserved(1.0, 0.0, 0.2, 1.0, case.gamma)
+    case.inflow = (None, None, (a, b), None)
+    case.band = (None, None, (0.5, 0.2), None)
+    return case, q
+
+
+CASES = {
+    "open_rough_40x36": open_rough,
+    "y_jet_33x29": y_jet,
+    "outflow_box_37x29": lambda: I.random_smooth(37, 29, seed=11, bc=("outflow",) * 4),
+    "mach2000_32x16": lambda: I.mach2000(32, 16),
+    "sedov_24": lambda: I.sedov_2d(24),
+}
+
+
+def ocfg(case, **kw):
+    return O.make_cfg(**dict(case.params(), **kw))
+
+
+@pytest.mark.parametrize("scheme", ["gr", "dr"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_residual_parity_open_faces(name, scheme):
+    case, q = CASES[name]()
+    p = dict(case.params(), scheme=scheme)
+    s = hweno.Solver(p)
+    s.set_state(torch.from_numpy(q).cuda())
+    rhs, vhat = s.residual()
+    d = s.diag()
+    s.close()
+    o = O.residual(O.make_cfg(**p), q)
+    tol = res_tol(case, q)
+    assert rel_linf(rhs.cpu().numpy(), o["rhs"], flux_scale(case, q)) <= tol
+    assert rel_linf(vhat.cpu().numpy(), o["vhat"], state_scale(q)) <= tol
+    assert abs(d["alpha_star"] - o["diag"][0]) <= 1e-13 * o["diag"][0]
+    assert abs(d["beta_max"] - o["diag"][1]) <= 1e-12 * o["diag"][1]
+
+
+def test_intermediate_fields_parity_open_faces():
+    """traces, volume values, weak-derivative moments, gradients and limiter factors
+    next to inflow and outflow faces"""
+    case, q = open_rough()
+    g = gpu_residual(case, q, dumps=(0, 1, 2, 3, 4))
+    o = O.residual(ocfg(case), q, dumps=True)
+    assert rel_linf(g[0], o["face"], state_scale(q)) <= RES_TOL
+    assert rel_linf(g[1], o["vol"], state_scale(q)) <= RES_TOL
+    assert rel_linf(g[2], o["rm"]) <= RES_TOL
+    assert rel_linf(g[3], o["grad"]) <= RES_TOL
+    assert np.abs(g[4] - o["theta"]).max() <= 1e-13
+
+
+@pytest.mark.parametrize("name", ["open_rough_40x36", "y_jet_33x29"])
+def test_mixed_precision_open_faces(name):
+    """the mixed path's inflow ghosts hold the hi/lo split of the prescribed state: its
+    residual stays within the mixed path's bound of the FP64 oracle"""
+    case, q = CASES[name]()
+    g = gpu_residual(case, q, precision="mixed")
+    o = O.residual(ocfg(case), q)
+    assert rel_linf(g["rhs"], o["rhs"], flux_scale(case, q)) <= 1e-5
+    assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= 1e-6
+
+
+def test_step_parity_open_faces():
+    """a forced and a rule step; the stages refill the inflow and outflow ghosts"""
+    case, q = open_rough()
+    cfg = ocfg(case)
+    s = hweno.Solver(case.params())
+    s.set_state(torch.from_numpy(q).cuda())
+    dt, rej = s.step(1e-4)
+    assert dt == 1e-4 and rej == 0
+    qo, st = O.step(cfg, q, dt_fixed=1e-4)
+    assert rel_linf(s.get_state().cpu().numpy(), qo, state_scale(q)) <= 1e-12
+    dt2, _ = s.step()
+    qo2, st2 = O.step(cfg, qo)
+    assert abs(dt2 - st2["dt"]) <= 1e-13 * st2["dt"]
+    assert rel_linf(s.get_state().cpu().numpy(), qo2, state_scale(q)) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("name,precision", [("y_jet_33x29", "fp64"), ("open_rough_40x36", "fp64"),
+                                            ("y_jet_33x29", "mixed")])
+def test_run_parity_open_faces(name, precision):
+    """20 steps under the Sec. 5 rule: relative L1 <= 1e-9 against the oracle's run at
+    the same time; on the mixed path, whose wave speeds come from FP32 traces, the time
+    within 1e-6 and the state within 1e-5"""
+    case, q = CASES[name]()
+    s = hweno.Solver(case.params(), precision=precision)
+    s.set_state(torch.from_numpy(q).cuda())
+    qo, st = O.advance(ocfg(case), q, 0.0, 1e9, max_steps=20)
+    assert st["steps"] == 20
+    for _ in range(20):
+        s.step()
+    fp64 = precision == "fp64"
+    assert abs(s.diag()["t"] - st["t"]) <= (1e-13 if fp64 else 1e-6) * st["t"]
+    assert rel_l1(s.get_state().cpu().numpy(), qo) <= (1e-9 if fp64 else 1e-5)
+    s.close()
+
+
+def test_mach2000_steps_and_stall():
+    """Example 5.9 at 32 x 16: six rule steps with the oracle's restarts (2, 6, 7, 15,
+    17, 18) and step sizes, then a step that stays inadmissible after 20 halvings and
+    leaves the state at t^n, as in the oracle"""
+    case, q = I.mach2000(32, 16)
+    cfg = ocfg(case)
+    s = hweno.Solver(case.params())
+    s.set_state(torch.from_numpy(q).cuda())
+    qo = q
+    for _ in range(6):
+        qo, st = O.step(cfg, qo)
+        assert st["status"] == 0
+        dt, rej = s.step()
+        assert rej == st["rejections"] and abs(dt - st["dt"]) <= 1e-13 * st["dt"]
+        assert rel_linf(s.get_state().cpu().numpy(), qo, state_scale(q)) <= 1e-11
+    _, st = O.step(cfg, qo)
+    assert st["status"] == -3
+    with pytest.raises(hweno.HwenoError) as e:
+        s.step()
+    assert e.value.code == hweno.HWENO_ERR_INADMISSIBLE
+    assert rel_linf(s.get_state().cpu().numpy(), qo, state_scale(q)) <= 1e-11
+    s.close()
+
+
+def test_sedov_first_step_stalls_as_in_the_oracle():
+    """Example 5.7 at 24^2 with E = 1e-12 away from the corner cell: the PP wave-speed
+    bound (about 2.5e12) keeps the first step inadmissible through 20 halvings in both"""
+    case, q = I.sedov_2d(24)
+    _, st = O.step(ocfg(case), q)
+    assert st["status"] == -3
+    s = hweno.Solver(case.params())
+    s.set_state(torch.from_numpy(q).cuda())
+    with pytest.raises(hweno.HwenoError) as e:
+        s.step()
+    assert e.value.code == hweno.HWENO_ERR_INADMISSIBLE
+    assert np.array_equal(s.get_state().cpu().numpy(), q)
+    s.close()
+
+
+def test_noalloc_with_open_faces():
+    case, q = y_jet()
+    lib = hweno.load()
+    cfg = hweno.make_config(**case.params())
+    qd = torch.from_numpy(q).cuda()
+    rhs = torch.full((12, case.ny, case.nx), float("nan"), dtype=torch.float64, device="cuda")
+    vhat = torch.full((8, case.ny, case.nx), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rc = lib.hweno_residual_noalloc(ctypes.byref(cfg), ctypes.c_void_p(qd.data_ptr()),
+                                    ctypes.c_void_p(rhs.data_ptr()), ctypes.c_void_p(vhat.data_ptr()),
+                                    ctypes.c_void_p(stream.cuda_stream))
+    assert rc == hweno.HWENO_OK
+    torch.cuda.synchronize()
+    o = O.residual(ocfg(case), q)
+    assert rel_linf(rhs.cpu().numpy(), o["rhs"], flux_scale(case, q)) <= RES_TOL
+    assert rel_linf(vhat.cpu().numpy(), o["vhat"], state_scale(q)) <= RES_TOL
+
+
+def test_adjoint_refuses_open_faces():
+    case, q = y_jet()
+    s = hweno.Solver(case.params())
+    with pytest.raises(hweno.HwenoError) as e:
+        s.adjoint_init()
+    assert e.value.code == hweno.HWENO_ERR_ARG
+    s.close()
