@@ -21,6 +21,9 @@ from oracle import oracle as O
 from paper_2608_10569_b300 import inputs as I
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+# out-of-bounds reads and writes of the kernel's index arithmetic, and undefined
+# behaviour, abort the run where the compiler has the sanitizers
+SANITIZE = ["-fsanitize=address,undefined", "-fno-sanitize-recover=all", "-g"]
 ROOT = os.path.dirname(HERE)
 DIR = os.path.join(HERE, "host")
 CSRC = os.path.join(ROOT, "paper_2608_10569_b300", "csrc")
@@ -40,8 +43,10 @@ def exe(tmp_path_factory):
     with open(build / "kernel1d_extracted.inc", "w") as f:
         f.write(src[:src.index(MARKER)].replace("#include <cuda_runtime.h>\n", ""))
     out = str(build / "kernel1d_host")
-    subprocess.check_call([cxx, "-O2", "-std=c++17", "-I" + DIR, "-I" + str(build), "-I" + os.path.join(ROOT, "include"),
-                           "-I" + CSRC, "-o", out, os.path.join(DIR, "kernel1d_host.cc")])
+    cmd = [cxx, "-O2", "-std=c++17", "-I" + DIR, "-I" + str(build), "-I" + os.path.join(ROOT, "include"),
+           "-I" + CSRC, "-o", out, os.path.join(DIR, "kernel1d_host.cc")]
+    if subprocess.run(cmd + SANITIZE, capture_output=True).returncode != 0:
+        subprocess.check_call(cmd)
     return out
 
 
