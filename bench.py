@@ -82,13 +82,15 @@ def parse():
     ap.add_argument("--adj-n", type=int, default=512)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dr", action="store_true")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the child process that measures the 1D solver and the open faces")
     ap.add_argument("--mms-meshes", default="40,80,120,160")
     ap.add_argument("--mms-schemes", default="gr,dr")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--workload", default="shock_tube",
                     choices=["shock_tube", "ensemble", "smooth_periodic", "colliding_streams", "taylor_green",
-                             "adjoint", "mms"],
+                             "adjoint", "mms", "next"],
                     help="shock_tube is the headline line; the others print their own line")
     return ap.parse_args()
 
@@ -462,6 +464,134 @@ def run_mms(args):
     print(json.dumps(line), flush=True)
 
 
+def _bounded_run(s, t_end, max_steps, wall_s):
+    """rule steps until t_end, max_steps, wall_s seconds or the first failed step"""
+    import torch
+    from paper_2608_10569_b300 import hweno
+    t0 = time.perf_counter()
+    status, beta = 0, []
+    while True:
+        d = s.diag()
+        if d["t"] >= t_end or d["steps"] >= max_steps or time.perf_counter() - t0 > wall_s:
+            break
+        try:
+            s.step()
+        except hweno.HwenoError as e:
+            status = e.code
+            break
+        beta.append(s.diag()["beta_max"])
+    torch.cuda.synchronize()
+    d = s.diag()
+    return {"status": status, "t": d["t"], "steps": d["steps"], "rejected": d["rejected"],
+            "dt_last": d["dt_last"], "beta_max_first": beta[0] if beta else None,
+            "beta_max_last": beta[-1] if beta else None, "wall_s": time.perf_counter() - t0}
+
+
+def run_next(args):
+    """The widened rows on the GPU, one JSON line:
+    - the 1D solver (one thread block per problem): Example 5.1's convergence study,
+      Table 5.1's seven meshes for both schemes in one launch to T = 0.1, with the
+      density errors, orders and step rates; and an ensemble of 4 x 148 periodic
+      problems of 256 cells, 50 steps each, for the throughput of a full GPU;
+    - the inflow and outflow faces: the shock tube's 1024 x 512 box with open faces
+      (FP64 step rate next to the headline's wall-bounded one); Example 5.7 (Sedov 2D,
+      160^2, T = 1) and Example 5.9 (Mach 2000, 640 x 320, T = 0.001) under the Sec. 5
+      rule until T or the first step that stays inadmissible, bounded in steps and
+      wall time, for both schemes."""
+    import torch
+    from paper_2608_10569_b300 import hweno, inputs as I
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        r = fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return r, ev0.elapsed_time(ev1)
+
+    out = {"metric": "widened rows", "dtype": "f64", "data": "synthetic"}
+    # ---- 1D: Example 5.1's study in one launch ------------------------------------
+    meshes = (40, 80, 120, 160, 200, 240, 280)
+    params, states, exact = [], [], []
+    for scheme in ("gr", "dr"):
+        for n in meshes:
+            p, q = I.manufactured_1d(n, 0.0)
+            params.append(dict(p, scheme=scheme))
+            states.append(torch.from_numpy(q).cuda())
+            exact.append(I.manufactured_1d(n, 0.1)[1][0])
+    res, ms = timed(lambda: hweno.advance1d(params, states, 0.0, 0.1, stream=stream))
+    rows = {"gr": [], "dr": []}
+    cell_stages = 0.0
+    for p, st, ex, r in zip(params, states, exact, res):
+        err = st.cpu().numpy()[0] - ex
+        row = {"n": p["n"], "steps": r["steps"], "status": r["status"], "t": r["t"],
+               "linf": float(np.abs(err).max()), "l1": float(np.abs(err).mean())}
+        prev = rows[p["scheme"]]
+        if prev:
+            ratio = row["n"] / prev[-1]["n"]
+            row["order_linf"] = float(np.log(prev[-1]["linf"] / row["linf"]) / np.log(ratio))
+            row["order_l1"] = float(np.log(prev[-1]["l1"] / row["l1"]) / np.log(ratio))
+        prev.append(row)
+        cell_stages += 3.0 * r["steps"] * p["n"]
+    out["example_5_1"] = {"launches": 1, "problems": len(params), "ms": ms, "rows": rows,
+                          "Gcell_stage_per_s": cell_stages / (ms * 1e-3) / 1e9,
+                          "note": "one block per problem; the 280-cell problems (78,400 steps) bound the launch"}
+    print(json.dumps({"example_5_1_ms": ms}), file=sys.stderr, flush=True)
+    # ---- 1D: an ensemble filling the GPU ------------------------------------------
+    for scheme in ("gr", "dr"):
+        nprob, n, steps = 4 * 148, 256, 50
+        params, states = [], []
+        for k in range(nprob):
+            p, q = I.random_smooth_1d(n, seed=1000 + k)
+            params.append(dict(p, scheme=scheme))
+            states.append(torch.from_numpy(q).cuda())
+        res, ms = timed(lambda: hweno.advance1d(params, states, 0.0, 1e9, max_steps=steps, stream=stream))
+        done = sum(r["steps"] for r in res)
+        out["ensemble1d_" + scheme] = {"problems": nprob, "cells": n, "steps": steps, "ms": ms,
+                                       "failed": sum(1 for r in res if r["status"] != 0),
+                                       "Gcell_stage_per_s": 3.0 * n * done / (ms * 1e-3) / 1e9}
+    # ---- open faces: the shock tube's box --------------------------------------------
+    case, q = I.open_shock_tube(args.nx, args.ny)
+    s = hweno.Solver(case.params(), precision="fp64", stream=stream)
+    s.set_state(torch.from_numpy(q).cuda())
+    for _ in range(args.warmup):
+        s.step()
+    s.profile(True)
+    _, ms = timed(lambda: [s.step() for _ in range(args.steps)])
+    prof = s.profile_read()
+    s.profile(False)
+    out["open_shock_tube"] = {"nx": case.nx, "ny": case.ny, "steps": args.steps, "ms_per_step": ms / args.steps,
+                              "Gcell_stage_per_s": case.nx * case.ny * 3.0 * args.steps / (ms * 1e-3) / 1e9,
+                              "rejected": s.diag()["rejected"],
+                              "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    s.close()
+    # ---- open faces: Examples 5.7 and 5.9 ----------------------------------------------
+    for name, make, cap in (("sedov_2d_160", lambda: I.sedov_2d(160), 400),
+                            ("mach2000_640x320", lambda: I.mach2000(640, 320), 1500)):
+        for scheme in ("gr", "dr"):
+            case, q = make()
+            s = hweno.Solver(dict(case.params(), scheme=scheme), precision="fp64", stream=stream)
+            s.set_state(torch.from_numpy(q).cuda())
+            out["%s_%s" % (name, scheme)] = dict(_bounded_run(s, case.t_end, cap, 40.0), T=case.t_end)
+            s.close()
+    print(json.dumps(out), flush=True)
+
+
+def next_rows_child(args):
+    """run_next in a child process (its own CUDA context), bounded in time: a failure
+    there is reported in the line, never taken into the headline measurement"""
+    cmd = [sys.executable, os.path.join(HERE, "bench.py"), "--workload", "next", "--steps", "3", "--warmup", "1"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=480)
+        if r.returncode != 0:
+            return {"error": "exit %d: %s" % (r.returncode, r.stderr.strip()[-300:])}
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:
+        return {"error": str(e)[:300]}
+
+
 def run_single(args):
     """configs 1, 3 and 5 on one solver: FP64 and mixed step rates (config 3, whose
     limited states make the step rule restart ~20 times per step, reports residual
@@ -533,6 +663,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "mms":
         return run_mms(args)
+    if args.workload == "next":
+        return run_next(args)
     if args.workload != "shock_tube":
         return run_single(args)
     import torch
@@ -700,6 +832,11 @@ def main():
             parity[prec] = state_errors(sv.get_state().cpu().numpy(), q_or, case.gamma)
             sv.close()
 
+    # ---- the widened rows (1D solver, open faces), in a child process ------------------
+    next_rows = None
+    if rank == 0 and ws == 1 and not args.no_next:
+        next_rows = next_rows_child(args)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -709,7 +846,7 @@ def main():
                            "parallelism": "replicas" if ws > 1 else "single GPU",
                            "t_reached": t_reached, "rejected_steps": rejected},
                 "roofline": roof, "cpu_baseline": cpu, "parity_vs_oracle": parity, "e2e": e2e, "mixed": mixed,
-                "dr": dr,
+                "dr": dr, "next_rows": next_rows,
                 "clocks": clk, "gpu_launches": launches, "kernel_ms": kernel_ms}
         print(json.dumps(line), flush=True)
     if ws > 1:

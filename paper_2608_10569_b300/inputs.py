@@ -263,6 +263,18 @@ def manufactured(n, t=0.0, Re=100.0):
     return case, cell_moments(case, lambda x, y: manufactured_prim(x, y, t, case.gamma))
 
 
+def open_shock_tube(nx=1024, ny=512, Re=1000.0):
+    """The viscous shock tube's box and initial state with open faces: its left state
+    prescribed at x = 0 (inflow), outflow at x = 1 and y = 0.5, a symmetry plane at y = 0"""
+    case, q = shock_tube(nx, ny, Re)
+    left = tuple(float(v) for v in conserved(120.0, 0.0, 0.0, 120.0 / 1.4, 1.4))
+    case.name = "open_shock_tube_%dx%d" % (nx, ny)
+    case.bc = ("inflow", "outflow", "symmetry", "outflow")
+    case.inflow = ((left, left), None, None, None)
+    case.band = ((0.0, 0.0), None, None, None)
+    return case, q
+
+
 def sedov_2d(n, Re=1000.0):
     """Example 5.7's 2D Sedov blast: [0, 1.1]^2, rho = 1, u = v = 0, E = 0.244816/(dx dy) in
     the corner cell and 1e-12 elsewhere (gamma 1.4), reflective (symmetry) faces at x = 0

@@ -109,3 +109,14 @@ def test_linear_gradient_ablation_changes_only_the_gradients():
     for k in ("face", "vol", "rm", "theta", "vhat"):
         assert np.array_equal(a[k], b[k]), k
     assert np.abs(a["grad"] - b["grad"]).max() > 1e-3 * np.abs(a["grad"]).max()
+
+
+def test_open_shock_tube_inflow_matches_its_left_state():
+    """the open shock tube prescribes its own left state at x = 0: next to that face the
+    flow is uniform and at rest, so the residual vanishes there; it lives at the
+    diaphragm only"""
+    case, q = I.open_shock_tube(32, 16)
+    r = O.residual(O.make_cfg(**case.params()), q)["rhs"]
+    assert np.abs(r[:, :, :10]).max() <= 1e-12 * np.abs(r).max()
+    assert np.abs(r[:, :, 22:]).max() <= 1e-12 * np.abs(r).max()
+    assert np.abs(r[:, :, 14:18]).max() > 0
