@@ -497,7 +497,8 @@ def run_next(args):
       (FP64 step rate next to the headline's wall-bounded one); Example 5.7 (Sedov 2D,
       160^2, T = 1) and Example 5.9 (Mach 2000, 640 x 320, T = 0.001) under the Sec. 5
       rule until T or the first step that stays inadmissible, bounded in steps and
-      wall time, for both schemes."""
+      wall time, for both schemes, and Sedov once more with Remark 3.1's ablation (the
+      linear weights in the gradient reconstruction)."""
     import torch
     from paper_2608_10569_b300 import hweno, inputs as I
     stream = torch.cuda.current_stream()
@@ -576,6 +577,12 @@ def run_next(args):
             s.set_state(torch.from_numpy(q).cuda())
             out["%s_%s" % (name, scheme)] = dict(_bounded_run(s, case.t_end, cap, 40.0), T=case.t_end)
             s.close()
+    # Remark 3.1's ablation: the linear weights in the gradient reconstruction
+    case, q = I.sedov_2d(160)
+    s = hweno.Solver(dict(case.params(), linear_grad=True), precision="fp64", stream=stream)
+    s.set_state(torch.from_numpy(q).cuda())
+    out["sedov_2d_160_gr_linear_grad"] = dict(_bounded_run(s, case.t_end, 400, 40.0), T=case.t_end)
+    s.close()
     print(json.dumps(out), flush=True)
 
 

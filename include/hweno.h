@@ -110,6 +110,10 @@ typedef struct {
     double band[4][2];        /* per inflow face: centre c and half width w >= 0 of the band
                                  |s - c| < w, s the ghost cell centre's coordinate along the
                                  face (y on x-faces, x on y-faces; w = 0: state [1] alone) */
+    int linear_grad;          /* 1: the linear weights in the gradient reconstruction
+                                 (Eq. (3.9)) only, the ablation of Remark 3.1; HWENO_SCHEME_GR
+                                 handles and hweno_residual_noalloc; 0 otherwise */
+    int pad_;                 /* unused, 0 */
 } hweno_config;
 
 /* Diagnostics of the run so far (Sec. 5: PP-limiter percentage; Remark 3.1:

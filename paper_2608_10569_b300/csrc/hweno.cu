@@ -59,9 +59,9 @@ __global__ void k_face_moments(Grid g, Work w) {
 __global__ void k_weak_moments(Grid g, Work w) {
   weak_moments_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
-template <class T>
+template <class T, bool LIN = false>
 __global__ void __launch_bounds__(BX * BY) k_grad(Grid g, Work w) {
-  grad_body<T>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+  grad_body<T, false, LIN>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_flux(Grid g, Work w, Diag* diag) {
@@ -359,7 +359,10 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, d
     }
     {
       Prof p(h, K_GRAD);
-      k_grad_mixed<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+      if (h->cfg.linear_grad)
+        k_grad_mixed<true><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+      else
+        k_grad_mixed<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
     }
     {
       Prof p(h, K_FLUX);
@@ -411,6 +414,8 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, d
       Prof p(h, K_GRAD);
       if (h->w.yrec)
         k_grad_rec<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+      else if (h->cfg.linear_grad)
+        k_grad<double, true><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
       else
         k_grad<double><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
     }
@@ -531,6 +536,9 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   if (c.source != HWENO_SOURCE_NONE && c.source != HWENO_SOURCE_MMS52)
     return fail(nullptr, HWENO_ERR_ARG, "source must be HWENO_SOURCE_NONE or HWENO_SOURCE_MMS52");
   if (check_inflow(c)) return HWENO_ERR_ARG;
+  if (c.linear_grad != 0 && c.linear_grad != 1) return fail(nullptr, HWENO_ERR_ARG, "linear_grad must be 0 or 1");
+  if (c.linear_grad && c.scheme != HWENO_SCHEME_GR)
+    return fail(nullptr, HWENO_ERR_ARG, "linear_grad ablates the gradient reconstruction of HWENO_SCHEME_GR");
 
   h = new (std::nothrow) hweno_handle();
   if (!h) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
@@ -1010,6 +1018,7 @@ int hweno_adjoint_init(hweno_handle* h) {
     return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_SCHEME_GR without a source term");
   if (has_open_face(h->cfg))
     return fail(h, HWENO_ERR_ARG, "the adjoint takes periodic and wall faces, not inflow or outflow");
+  if (h->cfg.linear_grad) return fail(h, HWENO_ERR_ARG, "the adjoint runs the nonlinear gradient reconstruction");
   if (h->apool) return HWENO_OK;
   const Grid& g = h->g;
   // R 12, M 8, face 48, vol 36, gr 126, rm 18, cg 102, cc 68, q 12, stage-1 state 12,
@@ -1483,6 +1492,9 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   for (int c = 0; c < ncases; c++)
     if (has_open_face(cfgs[c]))
       return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels take periodic and wall faces");
+  for (int c = 0; c < ncases; c++)
+    if (cfgs[c].linear_grad)
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels run the nonlinear gradient reconstruction");
   hweno_batch* b = new (std::nothrow) hweno_batch();
   if (!b) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
   snprintf(b->err, sizeof(b->err), "no error");
@@ -1755,6 +1767,7 @@ static int noalloc_check_config(const hweno_config& c) {
     return fail(nullptr, HWENO_ERR_ARG, "precision must be HWENO_FP64 or HWENO_MIXED");
   if (c.scheme != HWENO_SCHEME_GR || c.source != HWENO_SOURCE_NONE)
     return fail(nullptr, HWENO_ERR_ARG, "hweno_residual_noalloc runs HWENO_SCHEME_GR without a source term");
+  if (c.linear_grad != 0 && c.linear_grad != 1) return fail(nullptr, HWENO_ERR_ARG, "linear_grad must be 0 or 1");
   return check_inflow(c);
 }
 

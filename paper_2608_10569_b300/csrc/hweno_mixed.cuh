@@ -305,7 +305,9 @@ __device__ __forceinline__ void weak_moments_mixed_body(const Grid& g, const Wor
   }
 }
 
-// Eq. (3.9) in FP32 on offsets from the centre value
+// Eq. (3.9) in FP32 on offsets from the centre value; LIN: the linear weights, whose
+// combination is p0 itself (the ablation of Remark 3.1)
+template <bool LIN = false>
 __device__ __forceinline__ void grad_mixed_body(const Grid& g, const Work& w, int gx, int gy) {
   const int i = gx - 1;
   const int j = gy - 1;
@@ -335,7 +337,10 @@ __device__ __forceinline__ void grad_mixed_body(const Grid& g, const Work& w, in
     d[15] = Y[cidx(g, i - 1, j)];
     d[16] = Y[cidx(g, i + 1, j)];
     float C[15];
-    hweno_combine<float>(d, eps, C);
+    if constexpr (LIN)
+      hw_p0_coeffs<float>(d, C);
+    else
+      hweno_combine<float>(d, eps, C);
     float vx[6], vy[6], vv[9];
     eval_xfaces<float>(C, vx);
     eval_yfaces<float>(C, vy);
@@ -523,8 +528,9 @@ __global__ void k_face_moments_mixed(Grid g, Work w) {
 __global__ void k_weak_moments_mixed(Grid g, Work w) {
   weak_moments_mixed_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
+template <bool LIN = false>
 __global__ void __launch_bounds__(128) k_grad_mixed(Grid g, Work w) {
-  grad_mixed_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+  grad_mixed_body<LIN>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 __global__ void __launch_bounds__(128) k_flux_mixed(Grid g, Work w, Diag* diag) {
   flux_mixed_body(g, w, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,

@@ -234,7 +234,9 @@ __device__ __forceinline__ void weak_moments_body(const Grid& g, const Work& w, 
 // interior grown by 1; values at the 12 face and 9 volume points
 // REC (FP64 only): also write each component's p0 coefficients and weight factors
 // (Work::yrec)
-template <class T, bool REC = false>
+// LIN: the linear weights (omega_m = gamma_m), which make the combination p0 itself:
+// the ablation of Remark 3.1
+template <class T, bool REC = false, bool LIN = false>
 __device__ __forceinline__ void grad_body(const Grid& g, const Work& w, int gx, int gy) {
   const int i = gx - 1;
   const int j = gy - 1;
@@ -264,7 +266,9 @@ __device__ __forceinline__ void grad_body(const Grid& g, const Work& w, int gx, 
     d[15] = (T)Y[cidx(g, i - 1, j)];
     d[16] = (T)Y[cidx(g, i + 1, j)];
     T C[15];
-    if constexpr (REC) {
+    if constexpr (LIN) {
+      hw_p0_coeffs<T>(d, C);
+    } else if constexpr (REC) {
       T c0[15], wr[2];
       hw_p0_coeffs<T>(d, c0);
       const T s[4] = {d[4] - d[3], d[5] - d[4], d[4] - d[1], d[7] - d[4]};

@@ -53,7 +53,8 @@ class hweno_config(ctypes.Structure):
                 ("eps_pp", ctypes.c_double), ("eps_weno", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("precision", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("source", ctypes.c_int),
-                ("inflow", ((ctypes.c_double * 4) * 2) * 4), ("band", (ctypes.c_double * 2) * 4)]
+                ("inflow", ((ctypes.c_double * 4) * 2) * 4), ("band", (ctypes.c_double * 2) * 4),
+                ("linear_grad", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class hweno_diag(ctypes.Structure):
@@ -165,7 +166,8 @@ def _check(h, rc):
 
 def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
                 bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
-                max_halvings=20, precision="fp64", scheme="gr", source=0, inflow=None, band=None, **_ignored):
+                max_halvings=20, precision="fp64", scheme="gr", source=0, inflow=None, band=None,
+                linear_grad=False, **_ignored):
     """inflow: per face (xlo, xhi, ylo, yhi) None or the pair of conserved states (inside,
     outside) the face's band; band: per face None or (centre, half width)"""
     c = hweno_config()
@@ -187,6 +189,7 @@ def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1
                     c.inflow[k][a][v] = float(inflow[k][a][v])
         if band and band[k] is not None:
             c.band[k][0], c.band[k][1] = float(band[k][0]), float(band[k][1])
+    c.linear_grad = 1 if linear_grad else 0
     return c
 
 

@@ -214,3 +214,19 @@ def test_open_faces_are_validated_before_any_device_call(lib):
     assert lib.hweno_batch_init(cfgs, 1, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
     assert b.value is None
     assert b"periodic and wall" in lib.hweno_last_error(None)
+
+
+def test_linear_gradient_ablation_is_validated_before_any_device_call(lib):
+    """linear_grad is 0 or 1, ablates HWENO-GR only, and is not taken by the batch"""
+    from paper_2608_10569_b300 import hweno
+    h = ctypes.c_void_p()
+    c = hweno.make_config(8, 8, linear_grad=True)
+    c.linear_grad = 2
+    assert lib.hweno_init(ctypes.byref(c), None, ctypes.byref(h)) == hweno.HWENO_ERR_ARG
+    c = hweno.make_config(8, 8, linear_grad=True, scheme="dr")
+    assert lib.hweno_init(ctypes.byref(c), None, ctypes.byref(h)) == hweno.HWENO_ERR_ARG
+    assert h.value is None
+    b = ctypes.c_void_p()
+    cfgs = (hweno.hweno_config * 1)(hweno.make_config(8, 8, linear_grad=True))
+    assert lib.hweno_batch_init(cfgs, 1, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
+    assert b.value is None

@@ -193,3 +193,42 @@ def test_adjoint_refuses_open_faces():
         s.adjoint_init()
     assert e.value.code == hweno.HWENO_ERR_ARG
     s.close()
+
+
+def _residual_with(params, q, precision="fp64", dumps=()):
+    s = hweno.Solver(params, precision=precision)
+    s.set_state(torch.from_numpy(q).cuda())
+    rhs, vhat = s.residual()
+    out = {"rhs": rhs.cpu().numpy(), "vhat": vhat.cpu().numpy(), "diag": s.diag()}
+    for k in dumps:
+        out[k] = s.debug_fields(k).cpu().numpy()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("name", ["open_rough_40x36", "y_jet_33x29", "sedov_24"])
+def test_linear_gradient_ablation_parity(name):
+    """Remark 3.1's ablation (hweno_config.linear_grad): the gradient reconstruction with
+    the linear weights, i.e. p0 itself, against the oracle's; the traces, volume values,
+    weak moments and limiter factors stay those of the nonlinear run, bit for bit"""
+    case, q = CASES[name]()
+    p = dict(case.params(), linear_grad=True)
+    g = _residual_with(p, q, dumps=(0, 1, 2, 3, 4))
+    o = O.residual(O.make_cfg(**p), q)
+    tol = res_tol(case, q)
+    assert rel_linf(g["rhs"], o["rhs"], flux_scale(case, q)) <= tol
+    assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= tol
+    assert abs(g["diag"]["beta_max"] - o["diag"][1]) <= 1e-12 * o["diag"][1]
+    n = _residual_with(case.params(), q, dumps=(0, 1, 2, 3, 4))
+    for k in (0, 1, 2, 4):
+        assert np.array_equal(g[k], n[k]), k
+    assert np.abs(g[3] - n[3]).max() > 1e-6 * np.abs(n[3]).max()
+
+
+def test_linear_gradient_ablation_mixed():
+    case, q = open_rough()
+    p = dict(case.params(), linear_grad=True)
+    g = _residual_with(p, q, precision="mixed")
+    o = O.residual(O.make_cfg(**p), q)
+    assert rel_linf(g["rhs"], o["rhs"], flux_scale(case, q)) <= 1e-5
+    assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= 1e-6
