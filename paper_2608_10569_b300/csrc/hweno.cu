@@ -485,12 +485,6 @@ static int check_inflow(const hweno_config& c) {
   return HWENO_OK;
 }
 
-static Open make_open(const hweno_config& c) {
-  Open o;
-  memcpy(o.state, c.inflow, sizeof(o.state));
-  memcpy(o.band, c.band, sizeof(o.band));
-  return o;
-}
 
 extern "C" {
 
@@ -546,25 +540,10 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   h->st = (cudaStream_t)stream;
   snprintf(h->err, sizeof(h->err), "no error");
   for (int k = 0; k < K_NKIND; k++) { h->prof_n[k] = 0; h->prof_ms[k] = 0.0; }
-  Grid& g = h->g;
-  g.nx = c.nx;
-  g.ny = c.ny;
-  g.pitch = ((c.nx + 2 * NG + 15) / 16) * 16;
-  g.ps = (long long)(c.ny + 2 * NG) * g.pitch;
-  g.dx = (c.x1 - c.x0) / c.nx;
-  g.dy = (c.y1 - c.y0) / c.ny;
-  g.gamma = c.gamma; g.Pr = c.Pr; g.Re = c.Re;
-  g.eps_pp = c.eps_pp; g.eps_weno = c.eps_weno;
-  for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
-  g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
-  g.x0 = c.x0; g.y0 = c.y0;
+  h->g = make_grid(c);
+  const Grid& g = h->g;
   h->open = make_open(c);
-  {  // 4-point Gauss-Legendre on [-1/2, 1/2]: nodes sqrt(3/7 -+ 2/7 sqrt(6/5)) / 2,
-     // weights (18 +- sqrt(30)) / 72
-    const double ri = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0)), ro = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
-    const double wi = (18.0 + sqrt(30.0)) / 72.0, wo = (18.0 - sqrt(30.0)) / 72.0;
-    h->quad = Quad4{{-0.5 * ro, -0.5 * ri, 0.5 * ri, 0.5 * ro}, {wo, wi, wi, wo}};
-  }
+  h->quad = make_quad4();
 
   const long long N = (long long)c.nx * c.ny;
   // planes: Q 12, QS 12, BASE 12, RHS0 12, RHS 12, MOM0 8, MOM 8, face 48, vol 36,
@@ -1777,11 +1756,7 @@ extern "C" int hweno_residual_noalloc(const hweno_config* cfg, const double* q, 
   int rc = noalloc_check_config(*cfg);
   if (rc) return rc;
   const hweno_config& c = *cfg;
-  Grid g;
-  g.nx = c.nx;
-  g.ny = c.ny;
-  g.pitch = ((c.nx + 2 * NG + 15) / 16) * 16;
-  g.ps = (long long)(c.ny + 2 * NG) * g.pitch;
+  const Grid g = make_grid(c);
   if (g.ps > NOALLOC_MAX_PLANE) {
     char buf[256];
     snprintf(buf, sizeof(buf),
@@ -1790,13 +1765,6 @@ extern "C" int hweno_residual_noalloc(const hweno_config* cfg, const double* q, 
              c.nx, c.ny, g.ps, NOALLOC_MAX_PLANE, NOALLOC_MAX_PLANE);
     return fail(nullptr, HWENO_ERR_ARG, buf);
   }
-  g.dx = (c.x1 - c.x0) / c.nx;
-  g.dy = (c.y1 - c.y0) / c.ny;
-  g.gamma = c.gamma; g.Pr = c.Pr; g.Re = c.Re;
-  g.eps_pp = c.eps_pp; g.eps_weno = c.eps_weno;
-  for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
-  g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
-  g.x0 = c.x0; g.y0 = c.y0;
 
   double* base = nullptr;
   if ((rc = noalloc_scratch_address(&base))) return rc;

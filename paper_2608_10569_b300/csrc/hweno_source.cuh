@@ -18,6 +18,14 @@ struct Quad4 {
   double nd[4], wt[4];
 };
 
+// 4-point Gauss-Legendre on [-1/2, 1/2]: nodes sqrt(3/7 -+ 2/7 sqrt(6/5)) / 2, weights
+// (18 +- sqrt(30)) / 72
+inline Quad4 make_quad4() {
+  const double ri = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0)), ro = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+  const double wi = (18.0 + sqrt(30.0)) / 72.0, wo = (18.0 - sqrt(30.0)) / 72.0;
+  return Quad4{{-0.5 * ro, -0.5 * ri, 0.5 * ri, 0.5 * ro}, {wo, wi, wi, wo}};
+}
+
 // one field base + a (sin(2 pi (a1 x + b1 y)) + cos(2 pi (a2 x + b2 y))), given the sine
 // and cosine of both angles: its value and t-, first and second space derivatives
 struct MField {

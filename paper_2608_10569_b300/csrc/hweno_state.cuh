@@ -35,6 +35,32 @@ struct Open {
   double band[4][2];
 };
 
+// the grid of a configuration: padded pitch and plane stride, spacings and their
+// reciprocals (correctly rounded on the host), gas constants, faces and origin
+inline Grid make_grid(const hweno_config& c) {
+  Grid g;
+  g.nx = c.nx;
+  g.ny = c.ny;
+  g.pitch = ((c.nx + 2 * NG + 15) / 16) * 16;
+  g.ps = (long long)(c.ny + 2 * NG) * g.pitch;
+  g.dx = (c.x1 - c.x0) / c.nx;
+  g.dy = (c.y1 - c.y0) / c.ny;
+  g.gamma = c.gamma; g.Pr = c.Pr; g.Re = c.Re;
+  g.eps_pp = c.eps_pp; g.eps_weno = c.eps_weno;
+  for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
+  g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
+  g.x0 = c.x0; g.y0 = c.y0;
+  return g;
+}
+
+// the prescribed states of a configuration's inflow faces
+inline Open make_open(const hweno_config& c) {
+  Open o;
+  memcpy(o.state, c.inflow, sizeof(o.state));
+  memcpy(o.band, c.band, sizeof(o.band));
+  return o;
+}
+
 __host__ __device__ __forceinline__ long long cidx(const Grid& g, int i, int j) {
   return (long long)(j + NG) * g.pitch + (i + NG);
 }
