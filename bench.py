@@ -464,6 +464,12 @@ def run_mms(args):
     print(json.dumps(line), flush=True)
 
 
+def pp_pct(d):
+    """limiter activations as a percentage of the cell-stages evaluated (Table 5.3's
+    PP-limiter column)"""
+    return 100.0 * d["pp_active"] / d["cell_stages"] if d["cell_stages"] > 0 else None
+
+
 def _bounded_run(s, t_end, max_steps, wall_s):
     """rule steps until t_end, max_steps, wall_s seconds or the first failed step"""
     import torch
@@ -482,7 +488,7 @@ def _bounded_run(s, t_end, max_steps, wall_s):
         beta.append(s.diag()["beta_max"])
     torch.cuda.synchronize()
     d = s.diag()
-    return {"status": status, "t": d["t"], "steps": d["steps"], "rejected": d["rejected"],
+    return {"status": status, "t": d["t"], "steps": d["steps"], "rejected": d["rejected"], "pp_percent": pp_pct(d),
             "dt_last": d["dt_last"], "beta_max_first": beta[0] if beta else None,
             "beta_max_last": beta[-1] if beta else None, "wall_s": time.perf_counter() - t0}
 
@@ -565,7 +571,7 @@ def run_next(args):
     s.profile(False)
     out["open_shock_tube"] = {"nx": case.nx, "ny": case.ny, "steps": args.steps, "ms_per_step": ms / args.steps,
                               "Gcell_stage_per_s": case.nx * case.ny * 3.0 * args.steps / (ms * 1e-3) / 1e9,
-                              "rejected": s.diag()["rejected"],
+                              "rejected": s.diag()["rejected"], "pp_percent": pp_pct(s.diag()),
                               "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
     s.close()
     # ---- open faces: Examples 5.7 and 5.9 ----------------------------------------------
@@ -715,6 +721,7 @@ def main():
     value = replica_value(ws, cells, stages, ms_max)
     q_fp64 = s.get_state().cpu().numpy()
     t_reached = s.diag()["t"]
+    pp_percent = pp_pct(s.diag())
 
     # dominant kernel of the operator and its roofline against the FP64 FMA peak
     dom = max((k for k in prof if k != "rk_update"), key=lambda k: prof[k][1])
@@ -809,7 +816,10 @@ def main():
         dms = max_over_ranks(ws, ev0.elapsed_time(ev1))
         qdr = d.get_state().cpu().numpy()
         # both schemes took warm-up + K steps of their own step rule from the same state
+        # Table 5.3 prints the CPU-time ratio T_GR / T_DR of this workload's whole run
+        # (1.09) and the limiter activations of both schemes (0 %)
         dr = {"value": replica_value(ws, cells, stages, dms), "unit": METRIC, "ms_per_step": dms / args.steps,
+              "time_ratio_gr_over_dr": ms_max / dms, "pp_percent": pp_pct(d.diag()),
               "gpu_launches": dlaunch, "t_reached": d.diag()["t"], "t_reached_gr": t_reached,
               "rel_l1_rho_vs_gr": float(np.abs(qdr[0] - q_fp64[0]).sum() / np.abs(q_fp64[0]).sum()),
               "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in dprof.items()}}
@@ -851,7 +861,7 @@ def main():
                 "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny, "cells": cells,
                            "stages_per_step": 3, "l2": "inputs larger than L2 (~1.5 GB state and scratch per step)",
                            "parallelism": "replicas" if ws > 1 else "single GPU",
-                           "t_reached": t_reached, "rejected_steps": rejected},
+                           "t_reached": t_reached, "rejected_steps": rejected, "pp_percent": pp_percent},
                 "roofline": roof, "cpu_baseline": cpu, "parity_vs_oracle": parity, "e2e": e2e, "mixed": mixed,
                 "dr": dr, "next_rows": next_rows,
                 "clocks": clk, "gpu_launches": launches, "kernel_ms": kernel_ms}
