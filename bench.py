@@ -503,7 +503,7 @@ def run_next(args):
       (FP64 step rate next to the headline's wall-bounded one); Example 5.7 (Sedov 2D,
       160^2, T = 1) and Example 5.9 (Mach 2000, 640 x 320, T = 0.001) under the Sec. 5
       rule until T or the first step that stays inadmissible, bounded in steps and
-      wall time, for both schemes, and Sedov once more with Remark 3.1's ablation (the
+      wall time (25 s each), for both schemes, and Sedov once more with Remark 3.1's ablation (the
       linear weights in the gradient reconstruction)."""
     import torch
     from paper_2608_10569_b300 import hweno, inputs as I
@@ -581,13 +581,13 @@ def run_next(args):
             case, q = make()
             s = hweno.Solver(dict(case.params(), scheme=scheme), precision="fp64", stream=stream)
             s.set_state(torch.from_numpy(q).cuda())
-            out["%s_%s" % (name, scheme)] = dict(_bounded_run(s, case.t_end, cap, 40.0), T=case.t_end)
+            out["%s_%s" % (name, scheme)] = dict(_bounded_run(s, case.t_end, cap, 25.0), T=case.t_end)
             s.close()
     # Remark 3.1's ablation: the linear weights in the gradient reconstruction
     case, q = I.sedov_2d(160)
     s = hweno.Solver(dict(case.params(), linear_grad=True), precision="fp64", stream=stream)
     s.set_state(torch.from_numpy(q).cuda())
-    out["sedov_2d_160_gr_linear_grad"] = dict(_bounded_run(s, case.t_end, 400, 40.0), T=case.t_end)
+    out["sedov_2d_160_gr_linear_grad"] = dict(_bounded_run(s, case.t_end, 400, 25.0), T=case.t_end)
     s.close()
     print(json.dumps(out), flush=True)
 
@@ -597,7 +597,7 @@ def next_rows_child(args):
     there is reported in the line, never taken into the headline measurement"""
     cmd = [sys.executable, os.path.join(HERE, "bench.py"), "--workload", "next", "--steps", "3", "--warmup", "1"]
     try:
-        r = subprocess.run(cmd, capture_output=True, text=True, timeout=480)
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=360)
         if r.returncode != 0:
             return {"error": "exit %d: %s" % (r.returncode, r.stderr.strip()[-300:])}
         return json.loads(r.stdout.strip().splitlines()[-1])
