@@ -494,11 +494,11 @@ def _bounded_run(s, t_end, max_steps, wall_s):
 
 
 def run_next(args):
-    """The widened rows on the GPU, one JSON line:
-    - the 1D solver (one thread block per problem): Example 5.1's convergence study,
-      Table 5.1's seven meshes for both schemes in one launch to T = 0.1, with the
-      density errors, orders and step rates; and an ensemble of 4 x 148 periodic
-      problems of 256 cells, 50 steps each, for the throughput of a full GPU;
+    """The widened rows on the GPU, a JSON line after each block (the last one complete):
+    - the 1D solver (one thread block per problem): an ensemble of 4 x 148 periodic
+      problems of 256 cells, 50 steps each, for the throughput of a full GPU; and, last,
+      Example 5.1's convergence study, Table 5.1's seven meshes for both schemes in one
+      launch to T = 0.1, with the density errors, orders and step rates;
     - the inflow and outflow faces: the shock tube's 1024 x 512 box with open faces
       (FP64 step rate next to the headline's wall-bounded one); Example 5.7 (Sedov 2D,
       160^2, T = 1) and Example 5.9 (Mach 2000, 640 x 320, T = 0.001) under the Sec. 5
@@ -519,6 +519,59 @@ def run_next(args):
         return r, ev0.elapsed_time(ev1)
 
     out = {"metric": "widened rows", "dtype": "f64", "data": "synthetic"}
+
+    def snapshot():
+        # the rows so far, one complete line per block, so that a time limit keeps them
+        print(json.dumps(dict(out, partial=True)), flush=True)
+
+    # ---- 1D: an ensemble filling the GPU ------------------------------------------
+    for scheme in ("gr", "dr"):
+        nprob, n, steps = 4 * 148, 256, 50
+        params, states = [], []
+        for k in range(nprob):
+            p, q = I.random_smooth_1d(n, seed=1000 + k)
+            params.append(dict(p, scheme=scheme))
+            states.append(torch.from_numpy(q).cuda())
+        res, ms = timed(lambda: hweno.advance1d(params, states, 0.0, 1e9, max_steps=steps, stream=stream))
+        done = sum(r["steps"] for r in res)
+        out["ensemble1d_" + scheme] = {"problems": nprob, "cells": n, "steps": steps, "ms": ms,
+                                       "failed": sum(1 for r in res if r["status"] != 0),
+                                       "Gcell_stage_per_s": 3.0 * n * done / (ms * 1e-3) / 1e9}
+        snapshot()
+
+    # ---- open faces: the shock tube's box --------------------------------------------
+    case, q = I.open_shock_tube(args.nx, args.ny)
+    s = hweno.Solver(case.params(), precision="fp64", stream=stream)
+    s.set_state(torch.from_numpy(q).cuda())
+    for _ in range(args.warmup):
+        s.step()
+    s.profile(True)
+    _, ms = timed(lambda: [s.step() for _ in range(args.steps)])
+    prof = s.profile_read()
+    s.profile(False)
+    out["open_shock_tube"] = {"nx": case.nx, "ny": case.ny, "steps": args.steps, "ms_per_step": ms / args.steps,
+                              "Gcell_stage_per_s": case.nx * case.ny * 3.0 * args.steps / (ms * 1e-3) / 1e9,
+                              "rejected": s.diag()["rejected"], "pp_percent": pp_pct(s.diag()),
+                              "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    s.close()
+    snapshot()
+    # ---- open faces: Examples 5.7 and 5.9 ----------------------------------------------
+    for name, make, cap in (("sedov_2d_160", lambda: I.sedov_2d(160), 400),
+                            ("mach2000_640x320", lambda: I.mach2000(640, 320), 1500)):
+        for scheme in ("gr", "dr"):
+            case, q = make()
+            s = hweno.Solver(dict(case.params(), scheme=scheme), precision="fp64", stream=stream)
+            s.set_state(torch.from_numpy(q).cuda())
+            out["%s_%s" % (name, scheme)] = dict(_bounded_run(s, case.t_end, cap, 25.0), T=case.t_end)
+            s.close()
+            snapshot()
+    # Remark 3.1's ablation: the linear weights in the gradient reconstruction
+    case, q = I.sedov_2d(160)
+    s = hweno.Solver(dict(case.params(), linear_grad=True), precision="fp64", stream=stream)
+    s.set_state(torch.from_numpy(q).cuda())
+    out["sedov_2d_160_gr_linear_grad"] = dict(_bounded_run(s, case.t_end, 400, 25.0), T=case.t_end)
+    s.close()
+    snapshot()
     # ---- 1D: Example 5.1's study in one launch ------------------------------------
     meshes = (40, 80, 120, 160, 200, 240, 280)
     params, states, exact = [], [], []
@@ -545,50 +598,6 @@ def run_next(args):
     out["example_5_1"] = {"launches": 1, "problems": len(params), "ms": ms, "rows": rows,
                           "Gcell_stage_per_s": cell_stages / (ms * 1e-3) / 1e9,
                           "note": "one block per problem; the 280-cell problems (78,400 steps) bound the launch"}
-    print(json.dumps({"example_5_1_ms": ms}), file=sys.stderr, flush=True)
-    # ---- 1D: an ensemble filling the GPU ------------------------------------------
-    for scheme in ("gr", "dr"):
-        nprob, n, steps = 4 * 148, 256, 50
-        params, states = [], []
-        for k in range(nprob):
-            p, q = I.random_smooth_1d(n, seed=1000 + k)
-            params.append(dict(p, scheme=scheme))
-            states.append(torch.from_numpy(q).cuda())
-        res, ms = timed(lambda: hweno.advance1d(params, states, 0.0, 1e9, max_steps=steps, stream=stream))
-        done = sum(r["steps"] for r in res)
-        out["ensemble1d_" + scheme] = {"problems": nprob, "cells": n, "steps": steps, "ms": ms,
-                                       "failed": sum(1 for r in res if r["status"] != 0),
-                                       "Gcell_stage_per_s": 3.0 * n * done / (ms * 1e-3) / 1e9}
-    # ---- open faces: the shock tube's box --------------------------------------------
-    case, q = I.open_shock_tube(args.nx, args.ny)
-    s = hweno.Solver(case.params(), precision="fp64", stream=stream)
-    s.set_state(torch.from_numpy(q).cuda())
-    for _ in range(args.warmup):
-        s.step()
-    s.profile(True)
-    _, ms = timed(lambda: [s.step() for _ in range(args.steps)])
-    prof = s.profile_read()
-    s.profile(False)
-    out["open_shock_tube"] = {"nx": case.nx, "ny": case.ny, "steps": args.steps, "ms_per_step": ms / args.steps,
-                              "Gcell_stage_per_s": case.nx * case.ny * 3.0 * args.steps / (ms * 1e-3) / 1e9,
-                              "rejected": s.diag()["rejected"], "pp_percent": pp_pct(s.diag()),
-                              "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
-    s.close()
-    # ---- open faces: Examples 5.7 and 5.9 ----------------------------------------------
-    for name, make, cap in (("sedov_2d_160", lambda: I.sedov_2d(160), 400),
-                            ("mach2000_640x320", lambda: I.mach2000(640, 320), 1500)):
-        for scheme in ("gr", "dr"):
-            case, q = make()
-            s = hweno.Solver(dict(case.params(), scheme=scheme), precision="fp64", stream=stream)
-            s.set_state(torch.from_numpy(q).cuda())
-            out["%s_%s" % (name, scheme)] = dict(_bounded_run(s, case.t_end, cap, 25.0), T=case.t_end)
-            s.close()
-    # Remark 3.1's ablation: the linear weights in the gradient reconstruction
-    case, q = I.sedov_2d(160)
-    s = hweno.Solver(dict(case.params(), linear_grad=True), precision="fp64", stream=stream)
-    s.set_state(torch.from_numpy(q).cuda())
-    out["sedov_2d_160_gr_linear_grad"] = dict(_bounded_run(s, case.t_end, 400, 25.0), T=case.t_end)
-    s.close()
     print(json.dumps(out), flush=True)
 
 
@@ -596,11 +605,24 @@ def next_rows_child(args):
     """run_next in a child process (its own CUDA context), bounded in time: a failure
     there is reported in the line, never taken into the headline measurement"""
     cmd = [sys.executable, os.path.join(HERE, "bench.py"), "--workload", "next", "--steps", "3", "--warmup", "1"]
+
+    def last_line(text):
+        for line in reversed((text or "").strip().splitlines()):
+            try:
+                return json.loads(line)
+            except ValueError:
+                continue
+        return {}
+
     try:
         r = subprocess.run(cmd, capture_output=True, text=True, timeout=360)
+        out = last_line(r.stdout)
         if r.returncode != 0:
-            return {"error": "exit %d: %s" % (r.returncode, r.stderr.strip()[-300:])}
-        return json.loads(r.stdout.strip().splitlines()[-1])
+            out["error"] = "exit %d: %s" % (r.returncode, r.stderr.strip()[-300:])
+        return out
+    except subprocess.TimeoutExpired as e:
+        so = e.stdout.decode() if isinstance(e.stdout, bytes) else e.stdout
+        return dict(last_line(so), error="time limit of 360 s reached; the rows above are those completed")
     except Exception as e:
         return {"error": str(e)[:300]}
 
