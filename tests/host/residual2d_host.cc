@@ -1,20 +1,22 @@
 // Runs one evaluation of the 2D spatial operator with the CUDA path's own code compiled
-// for the host (hweno_state.cuh, hweno_ops.cuh, hweno_source.cuh): the grid from
-// make_grid, the ghost passes, then each FP64 kernel's body over the index range of its
-// launch, in the order of the FP64 operator: traces and limiter, face and weak moments,
-// the gradient reconstruction (or the HWENO-DR derivatives), face fluxes, balances and
-// the manufactured source.  Every plane set is an allocation of its own, so that an
-// access past one shows under AddressSanitizer; with a NaN fill, a read of a scratch
-// value that no earlier kernel wrote reaches the output.
+// for the host (hweno_state.cuh, hweno_ops.cuh, hweno_mixed.cuh, hweno_source.cuh): the
+// grid from make_grid, the ghost passes, then each kernel's body over the index range
+// of its launch, in the order of the operator: traces and limiter, face and weak
+// moments, the gradient reconstruction (or the HWENO-DR derivatives), face fluxes,
+// balances and the manufactured source; FP64, or the mixed path (the hi/lo split of the
+// ghost-filled state, then its FP32 bodies).  Every plane set is an allocation of its
+// own, so that an access past one shows under AddressSanitizer; with a NaN fill (NaN as
+// a double and as either float half), a read of a scratch value that no earlier kernel
+// wrote reaches the output.
 //
-// Input: 10 ints (nx, ny, bc[4], scheme, source, linear_grad, nan_fill), 50 doubles
+// Input: 11 ints (nx, ny, bc[4], scheme, source, linear_grad, nan_fill, mixed), 50 doubles
 // (x0, x1, y0, y1, gamma, Pr, Re, eps_pp, eps_weno, t, inflow[4][2][4], band[4][2]), then
 // q[12][ny][nx].  Output (doubles): rhs[12][ny][nx], vhat[8][ny][nx], theta[2][ny][nx],
 // then alpha*, beta_max, limiter activations, flags.
 #include "shim.h"
 #include <cstdio>
 #include <vector>
-#include "hweno_ops.cuh"
+#include "hweno_mixed.cuh"
 #include "hweno_source.cuh"
 
 namespace hw {
@@ -28,9 +30,9 @@ int main(int argc, char** argv) {
   if (argc != 3) return 1;
   FILE* f = fopen(argv[1], "rb");
   if (!f) return 1;
-  int hi[10];
+  int hi[11];
   double hd[50];
-  if (fread(hi, sizeof(int), 10, f) != 10 || fread(hd, sizeof(double), 50, f) != 50) return 2;
+  if (fread(hi, sizeof(int), 11, f) != 11 || fread(hd, sizeof(double), 50, f) != 50) return 2;
   hweno_config c;
   memset(&c, 0, sizeof(c));
   c.nx = hi[0];
@@ -40,6 +42,7 @@ int main(int argc, char** argv) {
   c.source = hi[7];
   c.linear_grad = hi[8];
   const bool nan_fill = hi[9] != 0;
+  const bool mixed = hi[10] != 0;
   c.x0 = hd[0]; c.x1 = hd[1]; c.y0 = hd[2]; c.y1 = hd[3];
   c.gamma = hd[4]; c.Pr = hd[5]; c.Re = hd[6]; c.eps_pp = hd[7]; c.eps_weno = hd[8];
   const double t = hd[9];
@@ -54,7 +57,11 @@ int main(int argc, char** argv) {
   if (fread(in.data(), sizeof(double), in.size(), f) != in.size()) return 3;
   fclose(f);
 
-  const double fill = nan_fill ? NAN : 0.0;
+  double fill = 0.0;
+  if (nan_fill) {
+    const unsigned long long b = 0x7FC000007FC00000ull;
+    memcpy(&fill, &b, sizeof(fill));
+  }
   auto planes = [&](int k) { return std::vector<double>((size_t)k * g.ps, fill); };
   std::vector<double> q = planes(12), rhs = planes(12), mom = planes(8);
   std::vector<double> face = planes(48), vol = planes(36), wbar = planes(3), wx = planes(6), wy = planes(6);
@@ -73,32 +80,57 @@ int main(int argc, char** argv) {
 
   for (int k = 0; k < 8 * ny; k++) ghost_x_body(g, &o, q.data(), k);
   for (int k = 0; k < 8 * (nx + 2 * NG); k++) ghost_y_body(g, &o, q.data(), k);
-  const bool drs = c.scheme == HWENO_SCHEME_DR;
-  for (int gy = 0; gy < ny + 6; gy++)
-    for (int gx = 0; gx < nx + 6; gx++) {
-      if (drs) cons_body<double, false, true>(g, q.data(), w, mom.data(), &diag, gx, gy);
-      else cons_body<double>(g, q.data(), w, mom.data(), &diag, gx, gy);
-    }
-  if (drs) {
-    for (int gy = 0; gy < ny + 2; gy++)
-      for (int gx = 0; gx < nx + 2; gx++) dr_body(g, q.data(), w, gx, gy);
-  } else {
+  if (mixed) {
+    // the split of the ghost-filled state (k_split), then the FP32 bodies
+    float* hilo = mixed_planes(w, g.ps).hilo;
+    const long long np = 12 * g.ps;
+    for (long long k = 0; k < np; k++) split_hilo(q[k], hilo[k], hilo[np + k]);
+    for (int gy = 0; gy < ny + 6; gy++)
+      for (int gx = 0; gx < nx + 6; gx++) cons_mixed_body(g, q.data(), w, mom.data(), &diag, gx, gy);
     for (int gz = 0; gz < 2; gz++)
       for (int gy = 0; gy < ny + 5; gy++)
-        for (int gx = 0; gx < nx + 5; gx++) face_moments_body(g, w, gx, gy, gz);
+        for (int gx = 0; gx < nx + 5; gx++) face_moments_mixed_body(g, w, gx, gy, gz);
     for (int gy = 0; gy < ny + 4; gy++)
-      for (int gx = 0; gx < nx + 4; gx++) weak_moments_body(g, w, gx, gy);
+      for (int gx = 0; gx < nx + 4; gx++) weak_moments_mixed_body(g, w, gx, gy);
     for (int gy = 0; gy < ny + 2; gy++)
       for (int gx = 0; gx < nx + 2; gx++) {
-        if (c.linear_grad) grad_body<double, false, true>(g, w, gx, gy);
-        else grad_body<double>(g, w, gx, gy);
+        if (c.linear_grad) grad_mixed_body<true>(g, w, gx, gy);
+        else grad_mixed_body(g, w, gx, gy);
       }
+    for (int gz = 0; gz < 2; gz++)
+      for (int gy = 0; gy < ny + 1; gy++)
+        for (int gx = 0; gx < nx + 1; gx++) flux_mixed_body(g, w, &diag, gx, gy, gz);
+    for (int gy = 0; gy < ny; gy++)
+      for (int gx = 0; gx < nx; gx++) assemble_mixed_body(g, w, rhs.data(), &diag, gx, gy);
   }
-  for (int gz = 0; gz < 2; gz++)
-    for (int gy = 0; gy < ny + 1; gy++)
-      for (int gx = 0; gx < nx + 1; gx++) flux_body<double>(g, w, &diag, gx, gy, gz);
-  for (int gy = 0; gy < ny; gy++)
-    for (int gx = 0; gx < nx; gx++) assemble_body<double>(g, w, rhs.data(), &diag, gx, gy);
+  if (!mixed) {
+    const bool drs = c.scheme == HWENO_SCHEME_DR;
+    for (int gy = 0; gy < ny + 6; gy++)
+      for (int gx = 0; gx < nx + 6; gx++) {
+        if (drs) cons_body<double, false, true>(g, q.data(), w, mom.data(), &diag, gx, gy);
+        else cons_body<double>(g, q.data(), w, mom.data(), &diag, gx, gy);
+      }
+    if (drs) {
+      for (int gy = 0; gy < ny + 2; gy++)
+        for (int gx = 0; gx < nx + 2; gx++) dr_body(g, q.data(), w, gx, gy);
+    } else {
+      for (int gz = 0; gz < 2; gz++)
+        for (int gy = 0; gy < ny + 5; gy++)
+          for (int gx = 0; gx < nx + 5; gx++) face_moments_body(g, w, gx, gy, gz);
+      for (int gy = 0; gy < ny + 4; gy++)
+        for (int gx = 0; gx < nx + 4; gx++) weak_moments_body(g, w, gx, gy);
+      for (int gy = 0; gy < ny + 2; gy++)
+        for (int gx = 0; gx < nx + 2; gx++) {
+          if (c.linear_grad) grad_body<double, false, true>(g, w, gx, gy);
+          else grad_body<double>(g, w, gx, gy);
+        }
+    }
+    for (int gz = 0; gz < 2; gz++)
+      for (int gy = 0; gy < ny + 1; gy++)
+        for (int gx = 0; gx < nx + 1; gx++) flux_body<double>(g, w, &diag, gx, gy, gz);
+    for (int gy = 0; gy < ny; gy++)
+      for (int gx = 0; gx < nx; gx++) assemble_body<double>(g, w, rhs.data(), &diag, gx, gy);
+  }
   if (c.source == HWENO_SOURCE_MMS52)
     for (int gy = 0; gy < ny; gy++)
       for (int gx = 0; gx < nx; gx++) source_body(g, quad, t, 0.0, &diag, rhs.data(), gx, gy);

@@ -22,7 +22,7 @@
 struct Dim3Shim {
   unsigned x, y, z;
 };
-static Dim3Shim threadIdx = {0, 0, 0}, blockIdx = {0, 0, 0}, blockDim = {1, 1, 1};
+static Dim3Shim threadIdx = {0, 0, 0}, blockIdx = {0, 0, 0}, blockDim = {1, 1, 1}, gridDim = {1, 1, 1};
 
 static inline void __syncthreads() {}
 static inline int __syncthreads_or(int v) { return v != 0; }

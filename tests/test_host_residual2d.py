@@ -1,14 +1,15 @@
 """The 2D spatial operator of the CUDA path run on the host, against the FP64 oracle.
 
 `host/residual2d_host.cc` compiles the kernels' own code (`hweno_state.cuh`,
-`hweno_ops.cuh`, `hweno_source.cuh`) as plain C++ with `host/shim.h` and calls every
-FP64 kernel body over the index range of its launch, in the operator's order, with one
-host thread standing for each thread block.  Every scratch plane starts as NaN, so an
+`hweno_ops.cuh`, `hweno_mixed.cuh`, `hweno_source.cuh`) as plain C++ with `host/shim.h`
+and calls every kernel body of the FP64 operator, or of the mixed FP32/FP64 one, over
+the index range of its launch, in the operator's order, with one host thread standing
+for each thread block.  Every scratch plane starts as NaN, so an
 operator that read a value no earlier kernel wrote would not match; every plane set is
 its own allocation, checked by AddressSanitizer and UBSan where the compiler has them.
 The tolerances are those of the GPU parity tests: relative L-infinity 1e-12 of the flux
 scale per residual plane (the conditioning bound where the characteristic projection
-is ill-conditioned).  What this cannot check, the GPU's own arithmetic and the
+is ill-conditioned), 1e-5 on the mixed path.  What this cannot check, the GPU's own arithmetic and the
 interleaving of threads, the GPU parity tests cover.
 """
 import os
@@ -36,14 +37,15 @@ def exe(tmp_path_factory):
     if cxx is None:
         pytest.skip("g++ is needed to compile the device code for the host")
     out = str(tmp_path_factory.mktemp("residual2d") / "residual2d_host")
-    cmd = [cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I" + os.path.join(HERE, "host"),
+    # the mixed path's float planes live in the double scratch planes
+    cmd = [cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-fno-strict-aliasing", "-I" + os.path.join(HERE, "host"),
            "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-o", out, os.path.join(HERE, "host", "residual2d_host.cc")]
     if subprocess.run(cmd + SANITIZE, capture_output=True).returncode != 0:
         subprocess.check_call(cmd)
     return out
 
 
-def run(exe, tmp_path, p, q, t=0.0):
+def run(exe, tmp_path, p, q, t=0.0, mixed=False):
     """(rhs, vhat, theta, alpha*, beta_max, limiter activations, flags) of the host run"""
     nx, ny = p["nx"], p["ny"]
     inflow = p.get("inflow") or (None,) * 4
@@ -57,8 +59,8 @@ def run(exe, tmp_path, p, q, t=0.0):
         bd += list(band[k]) if band[k] is not None else [0.0, 0.0]
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(fin, "wb") as f:
-        f.write(struct.pack("10i", nx, ny, *[BC[b] for b in p["bc"]], 1 if p.get("scheme") == "dr" else 0,
-                            int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 1))
+        f.write(struct.pack("11i", nx, ny, *[BC[b] for b in p["bc"]], 1 if p.get("scheme") == "dr" else 0,
+                            int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 1, 1 if mixed else 0))
         f.write(struct.pack("50d", p["x0"], p["x1"], p["y0"], p["y1"], p["gamma"], p["Pr"], p["Re"],
                             p.get("eps_pp", 1e-12), p.get("eps_weno", 1e-8), t, *st, *bd))
         f.write(np.ascontiguousarray(q, dtype=np.float64).tobytes())
@@ -160,3 +162,28 @@ def test_limiter_engaged(exe, tmp_path):
     assert rel_linf(vhat, o["vhat"], state_scale(q)) <= tol
     assert np.abs(theta - o["theta"]).max() <= tol
     assert pp == limited.sum()
+
+
+@pytest.mark.parametrize("linear_grad", [False, True])
+@pytest.mark.parametrize("name", ["smooth_periodic_64", "rough_walls_45x21", "shock_tube_64x32", "open_rough_40x36",
+                                  "y_jet_33x29", "thin_grid_5x70"])
+def test_mixed_path(exe, tmp_path, name, linear_grad):
+    """the mixed path's FP32 bodies on the hi/lo split of the ghost-filled state: within
+    the mixed path's bounds of the FP64 oracle (1e-5 of the flux scale, 1e-6 of the state
+    for the modified moments), with inflow ghosts holding the split of their state"""
+    case, q = CASES[name]()
+    p = dict(case.params(), linear_grad=linear_grad)
+    rhs, vhat, theta, alpha, beta, pp, flags = run(exe, tmp_path, p, q, mixed=True)
+    o = O.residual(O.make_cfg(**p), q)
+    assert rel_linf(rhs, o["rhs"], flux_scale(case, q)) <= 1e-5
+    assert rel_linf(vhat, o["vhat"], state_scale(q)) <= 1e-6
+    assert flags == 0
+
+
+def test_mixed_path_conserves_to_fp64_roundoff(exe, tmp_path):
+    """the mixed path differences FP64 face fluxes: a periodic average residual still sums
+    to FP64 round-off"""
+    case, q = I.random_rough(40, 36, seed=12)
+    rhs = run(exe, tmp_path, case.params(), q, mixed=True)[0]
+    for v in range(4):
+        assert abs(rhs[v].sum()) <= 1e-13 * np.abs(rhs[v]).sum()
