@@ -1444,6 +1444,7 @@ static void batch_refresh_case(hweno_batch* b, int c) {
   CaseDev& cd = b->h_cases[c];
   cd.g = h->g;
   cd.w = h->w;
+  cd.open = h->open;
   cd.Q = h->Q; cd.QS = h->QS; cd.BASE = h->BASE; cd.RHS0 = h->RHS0; cd.RHS = h->RHS;
   cd.MOM0 = h->MOM0; cd.MOM = h->MOM;
   cd.diag = b->d_diag + c;
@@ -1469,8 +1470,7 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
       return fail(nullptr, HWENO_ERR_ARG,
                   "hweno_batch_init: the batched kernels run HWENO_SCHEME_GR without a source term");
   for (int c = 0; c < ncases; c++)
-    if (has_open_face(cfgs[c]))
-      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels take periodic and wall faces");
+    if (check_inflow(cfgs[c])) return HWENO_ERR_ARG;
   for (int c = 0; c < ncases; c++)
     if (cfgs[c].linear_grad)
       return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels run the nonlinear gradient reconstruction");

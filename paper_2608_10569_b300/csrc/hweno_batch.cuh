@@ -17,6 +17,7 @@ struct CaseDev {
   double dt_scale;             // 1, or 2^-k after k restarts of this step
   int active;                  // 0: the case does no work in this launch
   int pad;
+  Open open;                   // prescribed states of the case's inflow faces
 };
 
 // work list of one kernel: case c owns items [start[c], start[c+1]); its tiles are
@@ -132,12 +133,12 @@ __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncas
                          int split) {
   HW_BATCH_LOOP(L, ncase)
   double* q = which == 0 ? cd.Q : cd.QS;
-  if (pass == 0) ghost_x_body(cg, (const Open*)nullptr, q, gx);
-  else ghost_y_body(cg, (const Open*)nullptr, q, gx);
+  if (pass == 0) ghost_x_body(cg, &cd.open, q, gx);
+  else ghost_y_body(cg, &cd.open, q, gx);
   if (split) {
     float* hilo = mixed_planes(cw, cg.ps).hilo;
-    if (pass == 0) ghost_x_body(cg, (const Open*)nullptr, hilo, gx, 0, 24);
-    else ghost_y_body(cg, (const Open*)nullptr, hilo, gx, 0, 24);
+    if (pass == 0) ghost_x_body(cg, &cd.open, hilo, gx, 0, 24);
+    else ghost_y_body(cg, &cd.open, hilo, gx, 0, 24);
   }
   HW_BATCH_END
 }

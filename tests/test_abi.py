@@ -194,8 +194,8 @@ def test_struct_mirrors_match_the_headers(tmp_path):
 
 
 def test_open_faces_are_validated_before_any_device_call(lib):
-    """inflow states need rho > 0 and p > 0 and a band half width >= 0; the batch takes
-    no inflow or outflow face"""
+    """inflow states need rho > 0 and p > 0 and a band half width >= 0, in a handle and in
+    every case of a batch"""
     from paper_2608_10569_b300 import hweno
     h = ctypes.c_void_p()
     good = (1.0, 0.5, 0.0, 2.5)
@@ -210,10 +210,11 @@ def test_open_faces_are_validated_before_any_device_call(lib):
     ok = hweno.make_config(8, 8, bc=("inflow", "outflow", "symmetry", "symmetry"),
                            inflow=((good, good), None, None, None), band=((0.5, 0.1), None, None, None))
     b = ctypes.c_void_p()
-    cfgs = (hweno.hweno_config * 1)(ok)
-    assert lib.hweno_batch_init(cfgs, 1, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
+    cfgs = (hweno.hweno_config * 2)(ok, hweno.make_config(8, 8, bc=("inflow", "outflow", "symmetry", "symmetry"),
+                                                          **bad[0]))
+    assert lib.hweno_batch_init(cfgs, 2, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
     assert b.value is None
-    assert b"periodic and wall" in lib.hweno_last_error(None)
+    assert b"inflow state" in lib.hweno_last_error(None)
 
 
 def test_linear_gradient_ablation_is_validated_before_any_device_call(lib):

@@ -236,3 +236,22 @@ def test_linear_gradient_ablation_mixed():
     o = O.residual(O.make_cfg(**p), q)
     assert rel_linf(g["rhs"], o["rhs"], flux_scale(case, q)) <= 1e-5
     assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= 1e-6
+
+
+def test_batch_with_open_faces():
+    """the batch's ghost kernel takes each case's inflow states: one step of two open-face
+    cases against the oracle's step at the batch's step sizes, FP64 to 1e-12 and mixed
+    to 1e-5 (the mixed residual's bound times a CFL fraction)"""
+    cases = [open_rough(), y_jet()]
+    for prec, bound in (("fp64", 1e-12), ("mixed", 1e-5)):
+        b = hweno.Batch([c.params() for c, _ in cases], precision=prec, stream=torch.cuda.Stream())
+        for k, (_, q) in enumerate(cases):
+            b.cases[k].set_state(q.copy())
+        b.step(1)
+        for k, (case, q) in enumerate(cases):
+            dt = b.cases[k].diag()["dt_last"]
+            qo, st = O.step(ocfg(case), q, dt_fixed=dt)
+            assert st["status"] == 0
+            got = b.cases[k].get_state(np.zeros_like(q))
+            assert rel_linf(got, qo, state_scale(q)) <= bound, (prec, k)
+        b.close()
