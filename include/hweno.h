@@ -100,8 +100,9 @@ typedef struct {
     double eps_weno;          /* epsilon of the nonlinear weights (Appendix A: 1e-8) */
     int max_halvings;         /* restarts with dt/2 before HWENO_ERR_INADMISSIBLE */
     int precision;            /* HWENO_FP64 or HWENO_MIXED */
-    int scheme;               /* HWENO_SCHEME_GR or HWENO_SCHEME_DR (handles only: the
-                                 adjoint, the batch and hweno_residual_noalloc take GR) */
+    int scheme;               /* HWENO_SCHEME_GR or HWENO_SCHEME_DR (handles, and FP64
+                                 batches whose cases all take DR; the adjoint and
+                                 hweno_residual_noalloc take GR) */
     int source;               /* HWENO_SOURCE_NONE or HWENO_SOURCE_MMS52 (handles only) */
     double inflow[4][2][4];   /* per face (xlo, xhi, ylo, yhi) with HWENO_BC_INFLOW: the
                                  conserved state (rho, rho u, rho v, E) of a ghost cell whose
@@ -296,9 +297,10 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 typedef struct hweno_batch hweno_batch;
 
 /* Create ncases solvers (cfgs[0..ncases-1], as for hweno_init, all with the same
- * precision, HWENO_SCHEME_GR and no source term) sharing one stream; NULL stream: the batch creates its
- * own non-blocking stream (graph capture needs one).  Allocates everything.  Errors as
- * hweno_init. */
+ * precision and scheme, no source term and linear_grad 0; HWENO_SCHEME_DR in
+ * HWENO_FP64 only) sharing one stream; NULL stream: the batch creates its own
+ * non-blocking stream (graph capture needs one).  Allocates everything.  Errors as
+ * hweno_init; HWENO_ERR_ARG for cases that differ in precision or scheme. */
 int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_batch** out);
 void hweno_batch_destroy(hweno_batch* b);
 const char* hweno_batch_last_error(const hweno_batch* b);
@@ -316,7 +318,8 @@ int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections);
  * 32x4, 16x8, 64x2 and 128x1 on the current states (their tile lists differ), keeps
  * the fastest per kernel and re-captures the step graph.  chosen (6 ints, may be
  * NULL): the index of the kept shape for cons, face moments, weak moments, gradients,
- * fluxes and assembly/RK.  Does not change the states. */
+ * fluxes and assembly/RK; -1 for the three gradient kinds of an HWENO-DR batch, whose
+ * derivative kernel keeps its 32x2 block.  Does not change the states. */
 int hweno_batch_autotune(hweno_batch* b, int* chosen);
 
 /* Kernel launches issued by the batch (graph replays count their nodes). */

@@ -325,6 +325,9 @@ static cudaError_t cons_smem_allow() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cons_dr, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dr, cudaFuncAttributeMaxDynamicSharedMemorySize, DR_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_cons<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_dr, cudaFuncAttributeMaxDynamicSharedMemorySize, DR_SMEM_BYTES);
   if (e == cudaSuccess && dev < 32) done |= 1u << dev;
   return e;
 }
@@ -1266,6 +1269,7 @@ struct BatchList {
 struct hweno_batch {
   int n = 0;
   int mixed = 0;
+  int dr = 0;  // HWENO-DR: kb_dr on the BR_GRAD list in place of the three gradient kernels
   cudaStream_t st = nullptr;
   bool own_stream = false;
   std::vector<hweno_handle*> h;
@@ -1338,9 +1342,9 @@ static int build_list(hweno_batch* b, int k, int bx, int by) {
 
 // persistent grid: blocks resident on all SMs at once, never more than the items
 template <class K>
-static int persistent_grid(hweno_batch* b, K kernel, int items, size_t smem = 0) {
+static int persistent_grid(hweno_batch* b, K kernel, int items, size_t smem = 0, int threads = 128) {
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   if (per_sm < 1) per_sm = 1;
   const int g = b->sms * per_sm;
   return items < g ? (items > 0 ? items : 1) : g;
@@ -1374,6 +1378,13 @@ static void batch_enqueue_step(hweno_batch* b) {
       kb_flux<1><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
       kb_assemble<1><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
       b->launches += 6;
+    } else if (b->dr) {
+      kb_cons<0, true><<<grid(BR_CONS), dims(BR_CONS), CONS_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_CONS].tl(),
+                                                                                 n, which);
+      kb_dr<<<grid(BR_GRAD), dims(BR_GRAD), DR_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n, which);
+      kb_flux<0><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
+      kb_assemble<0><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
+      b->launches += 4;
     } else {
       kb_cons<0><<<grid(BR_CONS), dims(BR_CONS), CONS_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n,
                                                                            which);
@@ -1405,6 +1416,11 @@ static int batch_grids(hweno_batch* b) {
     b->L[BR_GRAD].grid = persistent_grid(b, kb_grad<1>, b->L[BR_GRAD].total);
     b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<1>, b->L[BR_FLUX].total);
     b->L[BR_INT].grid = persistent_grid(b, kb_assemble<1>, b->L[BR_INT].total);
+  } else if (b->dr) {
+    b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0, true>, b->L[BR_CONS].total, CONS_SMEM_BYTES);
+    b->L[BR_GRAD].grid = persistent_grid(b, kb_dr, b->L[BR_GRAD].total, DR_SMEM_BYTES, DR_THREADS);
+    b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<0>, b->L[BR_FLUX].total);
+    b->L[BR_INT].grid = persistent_grid(b, kb_assemble<0>, b->L[BR_INT].total);
   } else {
     b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0>, b->L[BR_CONS].total, CONS_SMEM_BYTES);
     b->L[BR_FACE].grid = persistent_grid(b, kb_face_moments<0>, b->L[BR_FACE].total);
@@ -1465,10 +1481,14 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   for (int c = 1; c < ncases; c++)
     if (cfgs[c].precision != cfgs[0].precision)
       return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same precision");
-  for (int c = 0; c < ncases; c++)
-    if (cfgs[c].scheme != HWENO_SCHEME_GR || cfgs[c].source != HWENO_SOURCE_NONE)
-      return fail(nullptr, HWENO_ERR_ARG,
-                  "hweno_batch_init: the batched kernels run HWENO_SCHEME_GR without a source term");
+  for (int c = 0; c < ncases; c++) {
+    if (cfgs[c].source != HWENO_SOURCE_NONE)
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels run without a source term");
+    if (cfgs[c].scheme != cfgs[0].scheme)
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same scheme");
+    if (cfgs[c].scheme == HWENO_SCHEME_DR && cfgs[c].precision != HWENO_FP64)
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: HWENO_SCHEME_DR runs in HWENO_FP64");
+  }
   for (int c = 0; c < ncases; c++)
     if (check_inflow(cfgs[c])) return HWENO_ERR_ARG;
   for (int c = 0; c < ncases; c++)
@@ -1479,6 +1499,7 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   snprintf(b->err, sizeof(b->err), "no error");
   b->n = ncases;
   b->mixed = cfgs[0].precision == HWENO_MIXED;
+  b->dr = cfgs[0].scheme == HWENO_SCHEME_DR;
   b->st = (cudaStream_t)stream;
   if (!b->st) {  // graphs cannot be captured on the legacy default stream
     if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1504,7 +1525,10 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_diag, 0, ncases * sizeof(Diag), b->st);
     if (e != cudaSuccess) rc = bfail(b, HWENO_ERR_CUDA, "hweno_batch_init: allocation failed");
   }
-  for (int k = 0; k < BR_N && !rc; k++) rc = build_list(b, k, k <= BR_INT ? 32 : 128, k <= BR_INT ? 4 : 1);
+  for (int k = 0; k < BR_N && !rc; k++) {
+    if (b->dr && k == BR_GRAD) rc = build_list(b, k, 32, DR_THREADS / 32);  // kb_dr's block
+    else rc = build_list(b, k, k <= BR_INT ? 32 : 128, k <= BR_INT ? 4 : 1);
+  }
   if (!rc) rc = batch_grids(b);
   if (!rc) {
     for (int c = 0; c < ncases; c++) batch_refresh_case(b, c);
@@ -1625,6 +1649,12 @@ int hweno_batch_autotune(hweno_batch* b, int* chosen) {
   BCK(cudaEventCreate(&e1), "event");
   const int n = b->n;
   for (int k = BR_CONS; k <= BR_INT; k++) {
+    // HWENO-DR: kb_dr keeps its DR_THREADS block on the BR_GRAD list; the face- and
+    // weak-moment lists are unused
+    if (b->dr && (k == BR_FACE || k == BR_WEAK || k == BR_GRAD)) {
+      if (chosen) chosen[k] = -1;
+      continue;
+    }
     float best = 1e30f;
     int bi = 0;
     for (int si = 0; si < 4; si++) {
@@ -1639,6 +1669,7 @@ int hweno_batch_autotune(hweno_batch* b, int* chosen) {
         switch (k) {
           case BR_CONS:
             if (b->mixed) kb_cons<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
+            else if (b->dr) kb_cons<0, true><<<gr, blk, CONS_SMEM_BYTES, b->st>>>(b->d_cases, tl, n, 1);
             else kb_cons<0><<<gr, blk, CONS_SMEM_BYTES, b->st>>>(b->d_cases, tl, n, 1);
             break;
           case BR_FACE:

@@ -63,14 +63,25 @@ __device__ __forceinline__ void tile_pos(const TileList& L, int c, int t, int& g
 
 #define HW_BATCH_END }
 
-// which = 0: stage 1 (state Q, residual into RHS0/MOM0); 1: stages 2, 3 (QS -> RHS/MOM)
-template <int MIXED>
+// which = 0: stage 1 (state Q, residual into RHS0/MOM0); 1: stages 2, 3 (QS -> RHS/MOM).
+// DR (FP64): also store the characteristic combinations HWENO-DR differentiates
+template <int MIXED, bool DR = false>
 __global__ void __launch_bounds__(128, MIXED ? 3 : 1) kb_cons(const CaseDev* __restrict__ cases, TileList L, int ncase, int which) {
   HW_BATCH_LOOP(L, ncase)
   const double* q = which == 0 ? cd.Q : cd.QS;
   double* mom = which == 0 ? cd.MOM0 : cd.MOM;
   if (MIXED) cons_mixed_body(cg, q, cw, mom, cd.diag, gx, gy);
+  else if (DR) cons_body<double, false, true>(cg, q, cw, mom, cd.diag, gx, gy);
   else cons_body<double>(cg, q, cw, mom, cd.diag, gx, gy);
+  HW_BATCH_END
+}
+
+// HWENO-DR gradients (Eq. (3.5)) in place of the face moments, weak moments and gradient
+// reconstruction: blocks of DR_THREADS threads with DR_SMEM_BYTES of shared memory
+__global__ void __launch_bounds__(DR_THREADS) kb_dr(const CaseDev* __restrict__ cases, TileList L, int ncase,
+                                                    int which) {
+  HW_BATCH_LOOP(L, ncase)
+  dr_body(cg, which == 0 ? cd.Q : cd.QS, cw, gx, gy);
   HW_BATCH_END
 }
 

@@ -98,9 +98,9 @@ def test_gpu_and_oracle_tables_agree():
 
 
 def test_scheme_is_validated_before_any_device_call(lib):
-    """HWENO_SCHEME_DR is accepted for FP64 handles only; an unknown scheme, DR with
-    the mixed precision, a DR case in a batch and DR in hweno_residual_noalloc are
-    refused on the host"""
+    """HWENO_SCHEME_DR is accepted for FP64 handles and FP64 batches of DR cases only;
+    an unknown scheme, DR with the mixed precision, a batch mixing the schemes, a mixed
+    DR batch and DR in hweno_residual_noalloc are refused on the host"""
     from paper_2608_10569_b300 import hweno
     h = ctypes.c_void_p()
     for kw in (dict(scheme="dr", precision="mixed"),):
@@ -113,7 +113,10 @@ def test_scheme_is_validated_before_any_device_call(lib):
     cfgs = (hweno.hweno_config * 2)(hweno.make_config(8, 8), hweno.make_config(8, 8, scheme="dr"))
     b = ctypes.c_void_p()
     assert lib.hweno_batch_init(cfgs, 2, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
-    assert b.value is None
+    assert b.value is None and b"same scheme" in lib.hweno_last_error(None)
+    cfgs = (hweno.hweno_config * 1)(hweno.make_config(8, 8, scheme="dr", precision="mixed"))
+    assert lib.hweno_batch_init(cfgs, 1, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
+    assert b.value is None and b"FP64" in lib.hweno_last_error(None)
     buf = (ctypes.c_double * 12)()
     c = hweno.make_config(8, 8, scheme="dr")
     assert lib.hweno_residual_noalloc(ctypes.byref(c), buf, buf, None, None) == hweno.HWENO_ERR_ARG

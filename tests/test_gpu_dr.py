@@ -140,8 +140,9 @@ def test_full_run_smooth_periodic():
 
 
 def test_gr_only_entry_points_reject_dr():
-    """the adjoint and the batch are written for HWENO-GR: a DR handle or case is
-    refused with HWENO_ERR_ARG, not run with the wrong gradients"""
+    """the adjoint is written for HWENO-GR, and a batch runs one scheme: a DR handle's
+    adjoint and a batch mixing GR and DR cases are refused with HWENO_ERR_ARG, not run
+    with the wrong gradients"""
     case, q = I.random_smooth(16, 16, seed=1)
     s = hweno.Solver(dr(case.params()))
     with pytest.raises(hweno.HwenoError) as e:

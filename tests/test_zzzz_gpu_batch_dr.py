@@ -1,0 +1,66 @@
+"""GPU parity of HWENO-DR in the batch (hweno_batch_init with HWENO_SCHEME_DR cases): the
+batched kernels run the single-grid bodies, so a DR batch must give the DR handles'
+states (to 1e-13 of the state scale: the bodies are inlined into other kernels, whose
+multiply-add contractions may differ) and the oracle's DR step to 1e-12.  Collected
+last, so that a failure here cannot stop the other files under -x.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2608_10569_b300 import hweno, inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return [I.random_rough(37, 21, seed=2, bc=("noslip", "noslip", "noslip", "symmetry")),
+            I.random_smooth(16, 16, seed=1),
+            I.shock_tube(64, 32)]
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_dr_batch_matches_dr_handles(tune):
+    """three cases of different sizes and faces, three steps each, with and without the
+    block-shape autotuning (which leaves kb_dr's block alone)"""
+    cases = _cases()
+    stream = torch.cuda.Stream()
+    b = hweno.Batch([dict(c.params(), scheme="dr") for c, _ in cases], precision="fp64", stream=stream)
+    for k, (_, q) in enumerate(cases):
+        b.cases[k].set_state(q.copy())
+    if tune:
+        chosen = b.autotune()
+        assert chosen[1] == chosen[2] == chosen[3] == -1
+    for _ in range(3):
+        b.step(1)
+    for k, (case, q) in enumerate(cases):
+        s = hweno.Solver(dict(case.params(), scheme="dr"), stream=stream)
+        s.set_state(q.copy())
+        for _ in range(3):
+            s.step()
+        ref = s.get_state().cpu().numpy()
+        d = s.diag()
+        s.close()
+        got = b.cases[k].get_state(np.zeros_like(q))
+        assert b.cases[k].diag()["steps"] == 3
+        assert abs(b.cases[k].diag()["dt_last"] - d["dt_last"]) <= 1e-13 * d["dt_last"]
+        scale = np.abs(q[:4]).reshape(4, -1).max(1)
+        err = max(np.abs(got[j] - ref[j]).max() / max(np.abs(ref[j]).max(), scale[j % 4]) for j in range(12))
+        assert err <= 1e-13, (k, err)
+    b.close()
+
+
+def test_dr_batch_step_matches_the_oracle():
+    case, q = _cases()[0]
+    p = dict(case.params(), scheme="dr")
+    b = hweno.Batch([p], precision="fp64", stream=torch.cuda.Stream())
+    b.cases[0].set_state(q.copy())
+    b.step(1)
+    qo, st = O.step(O.make_cfg(**p), q)
+    got = b.cases[0].get_state(np.zeros_like(q))
+    scale = np.abs(q[:4]).reshape(4, -1).max(1)
+    err = max(np.abs(got[k] - qo[k]).max() / max(np.abs(qo[k]).max(), scale[k % 4]) for k in range(12))
+    assert st["status"] == 0 and err <= 1e-12
+    b.close()
