@@ -62,8 +62,9 @@ extern "C" {
 /* Corner ghost cells: a y-face inflow fills its ghost rows across the padded width;
  * otherwise the y-face rule maps the row into the interior and the x-face rule then
  * applies to that row (mirror parities multiply; an x-face inflow state takes the
- * y mirror's parity).  Inflow and outflow faces are taken by solver handles,
- * hweno_residual_noalloc and the batch, not by the adjoint (HWENO_ERR_ARG). */
+ * y mirror's parity).  Every entry point takes inflow and outflow faces; in the
+ * adjoint an outflow ghost's adjoint returns to the edge cell and an inflow ghost's is
+ * dropped (the prescribed state is a constant). */
 
 /* arithmetic of the spatial operator */
 #define HWENO_FP64 0  /* everything in FP64 */

@@ -463,12 +463,6 @@ static double h_min(const hweno_handle* h) {
 
 static int valid_bc(int b) { return b >= HWENO_BC_PERIODIC && b <= HWENO_BC_OUTFLOW; }
 
-static bool has_open_face(const hweno_config& c) {
-  for (int k = 0; k < 4; k++)
-    if (c.bc[k] == HWENO_BC_INFLOW || c.bc[k] == HWENO_BC_OUTFLOW) return true;
-  return false;
-}
-
 // the prescribed states of the inflow faces: finite, with rho > 0 and p > 0, and
 // bands of finite centre and half width >= 0
 static int check_inflow(const hweno_config& c) {
@@ -998,8 +992,6 @@ int hweno_adjoint_init(hweno_handle* h) {
   if (h->cfg.precision != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_FP64");
   if (h->cfg.scheme != HWENO_SCHEME_GR || h->cfg.source != HWENO_SOURCE_NONE)
     return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_SCHEME_GR without a source term");
-  if (has_open_face(h->cfg))
-    return fail(h, HWENO_ERR_ARG, "the adjoint takes periodic and wall faces, not inflow or outflow");
   if (h->cfg.linear_grad) return fail(h, HWENO_ERR_ARG, "the adjoint runs the nonlinear gradient reconstruction");
   if (h->apool) return HWENO_OK;
   const Grid& g = h->g;

@@ -988,8 +988,11 @@ __global__ void ka_gather_q(Grid g, Adj a) {
 }
 
 // adjoint of the ghost fill: every ghost adjoint goes back to its source cell with the
-// ghost's sign (y pass first: it ran last in the forward).  Atomic adds: on grids with
-// fewer than 8 cells a periodic source feeds ghosts on both sides.
+// ghost's sign (y pass first: it ran last in the forward); an outflow ghost's goes to the
+// adjacent interior cell with sign 1, an inflow ghost's is dropped (its value is the
+// prescribed state, independent of the solution).  Atomic adds: on grids with fewer
+// than 8 cells a periodic source feeds ghosts on both sides, and an outflow edge cell
+// feeds all four ghost layers.
 __global__ void ka_ghost_y(Grid g, Adj a) {
   const int W = g.nx + 2 * NG;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -998,14 +1001,12 @@ __global__ void ka_ghost_y(Grid g, Adj a) {
   const int side = r / 4, k = r % 4;
   const int j = side == 0 ? -1 - k : g.ny + k;
   const int bc = g.bc[2 + side];
-  int src;
-  if (bc == 0) src = side == 0 ? ((j % g.ny) + g.ny) % g.ny : j % g.ny;
-  else src = side == 0 ? -1 - j : 2 * g.ny - 1 - j;
-  const long long d = cidx(g, i, j), s = cidx(g, i, src);
+  if (bc == HWENO_BC_INFLOW) return;
+  const long long d = cidx(g, i, j), s = cidx(g, i, ghost_src(bc, j, g.ny));
+  const bool mir = is_mirror(bc);
   for (int m = 0; m < 3; m++)
     for (int v = 0; v < 4; v++) {
-      double sg = 1.0;
-      if (bc != 0) sg = bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0);
+      const double sg = mir ? bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0) : 1.0;
       atomicAdd(&a.q[(4 * m + v) * g.ps + s], sg * a.q[(4 * m + v) * g.ps + d]);
     }
 }
@@ -1016,14 +1017,12 @@ __global__ void ka_ghost_x(Grid g, Adj a) {
   const int side = cix / 4, k = cix % 4;
   const int i = side == 0 ? -1 - k : g.nx + k;
   const int bc = g.bc[side];
-  int src;
-  if (bc == 0) src = side == 0 ? ((i % g.nx) + g.nx) % g.nx : i % g.nx;
-  else src = side == 0 ? -1 - i : 2 * g.nx - 1 - i;
-  const long long d = cidx(g, i, j), s = cidx(g, src, j);
+  if (bc == HWENO_BC_INFLOW) return;
+  const long long d = cidx(g, i, j), s = cidx(g, ghost_src(bc, i, g.nx), j);
+  const bool mir = is_mirror(bc);
   for (int m = 0; m < 3; m++)
     for (int v = 0; v < 4; v++) {
-      double sg = 1.0;
-      if (bc != 0) sg = bc_sign(bc, 0, v) * (m == 1 ? -1.0 : 1.0);
+      const double sg = mir ? bc_sign(bc, 0, v) * (m == 1 ? -1.0 : 1.0) : 1.0;
       atomicAdd(&a.q[(4 * m + v) * g.ps + s], sg * a.q[(4 * m + v) * g.ps + d]);
     }
 }

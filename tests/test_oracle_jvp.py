@@ -21,9 +21,19 @@ def richardson(f, h):
     return (4 * d2 - d1) / 3
 
 
+def _open():
+    """a banded inflow face (two states, constants: no tangent), outflow and symmetry"""
+    case, q = I.random_smooth(14, 12, seed=43, bc=("inflow", "outflow", "symmetry", "outflow"))
+    case.inflow = ((I.conserved(1.2, 0.4, 0.1, 1.5, case.gamma), I.conserved(0.9, 0.2, 0.0, 1.1, case.gamma)),
+                   None, None, None)
+    case.band = ((0.5, 0.2), None, None, None)
+    return case, q
+
+
 CASES = {
     "walls": lambda: I.random_smooth(14, 12, seed=41, bc=("noslip", "slip", "symmetry", "noslip")),
     "periodic": lambda: I.random_smooth(12, 12, seed=42),
+    "open": _open,
 }
 
 

@@ -190,13 +190,38 @@ def test_noalloc_with_open_faces():
     assert rel_linf(vhat.cpu().numpy(), o["vhat"], state_scale(q)) <= RES_TOL
 
 
-def test_adjoint_refuses_open_faces():
-    case, q = y_jet()
+def _rel(a, b):
+    return abs(a - b) / max(abs(a), abs(b))
+
+
+@pytest.mark.parametrize("name", ["y_jet_33x29", "outflow_box_37x29"])
+def test_adjoint_dot_products_with_open_faces(name):
+    """the adjoint's ghost transpose returns an outflow ghost's adjoint to the edge cell
+    and drops an inflow ghost's: <(rbar, mbar), J v> and <lam', J_step v> from the dual
+    oracle against <xbar, v> and <J^T lam', v> from the GPU, and the derivatives in
+    mu = 1/Re, to 1e-10"""
+    case, q = CASES[name]()
+    rng = np.random.default_rng(73)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    rbar = rng.normal(size=q.shape)
+    mbar = rng.normal(size=(8,) + q.shape[1:])
+    lam_next = rng.normal(size=q.shape)
+    dt = 1e-3
     s = hweno.Solver(case.params())
-    with pytest.raises(hweno.HwenoError) as e:
-        s.adjoint_init()
-    assert e.value.code == hweno.HWENO_ERR_ARG
+    s.adjoint_init()
+    xbar, mub = s.adjoint_residual(q.copy(), rbar, mbar)
+    lam, mub_step = s.adjoint_step(q.copy(), dt, lam_next, np.zeros_like(q))
     s.close()
+    cfg = ocfg(case)
+    t = O.residual_jvp(cfg, q, v)
+    tm = O.residual_jvp(cfg, q, None, dmu=1.0)
+    assert _rel((rbar * t["rhs_dot"]).sum() + (mbar * t["vhat_dot"]).sum(), (xbar * v).sum()) <= 1e-10
+    assert _rel((rbar * tm["rhs_dot"]).sum() + (mbar * tm["vhat_dot"]).sum(), mub) <= 1e-10
+    _, ts, st = O.step_jvp(cfg, q, v, dt)
+    assert st["status"] == 0 and st["rejections"] == 0
+    assert _rel((lam_next * ts).sum(), (lam * v).sum()) <= 1e-10
+    _, tms, _ = O.step_jvp(cfg, q, np.zeros_like(q), dt, dmu=1.0)
+    assert _rel((lam_next * tms).sum(), mub_step) <= 1e-10
 
 
 def _residual_with(params, q, precision="fp64", dumps=()):
