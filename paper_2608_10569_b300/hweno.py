@@ -193,18 +193,24 @@ def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1
     return c
 
 
-def _ptr_of(a):
-    """(pointer, on_device) of a torch tensor or numpy array (must be contiguous float64)."""
+def _ptr_of(a, count=None):
+    """(pointer, on_device) of a torch tensor or numpy array: contiguous float64, with
+    exactly count elements when count is given (the library reads or writes that many,
+    so a shorter buffer is refused here rather than overrun)."""
     if isinstance(a, np.ndarray):
         if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
             raise ValueError("need a C-contiguous float64 array")
-        return ctypes.c_void_p(a.ctypes.data), 0
-    import torch
-    if not isinstance(a, torch.Tensor):
-        raise TypeError("need a numpy array or a torch tensor")
-    if a.dtype != torch.float64 or not a.is_contiguous():
-        raise ValueError("need a contiguous float64 tensor")
-    return ctypes.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0)
+        n, out = a.size, (ctypes.c_void_p(a.ctypes.data), 0)
+    else:
+        import torch
+        if not isinstance(a, torch.Tensor):
+            raise TypeError("need a numpy array or a torch tensor")
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("need a contiguous float64 tensor")
+        n, out = a.numel(), (ctypes.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0))
+    if count is not None and n != count:
+        raise ValueError("need %d float64 elements, got %d" % (count, n))
+    return out
 
 
 class Solver:
@@ -238,7 +244,7 @@ class Solver:
             pass
 
     def set_state(self, q):
-        ptr, dev = _ptr_of(q)
+        ptr, dev = _ptr_of(q, 12 * self.nx * self.ny)
         _check(self.h, self.lib.hweno_set_state(self.h, ptr, dev))
 
     def set_time(self, t):
@@ -248,7 +254,7 @@ class Solver:
         import torch
         if out is None:
             out = torch.empty((12, self.ny, self.nx), dtype=torch.float64, device="cuda")
-        ptr, dev = _ptr_of(out)
+        ptr, dev = _ptr_of(out, 12 * self.nx * self.ny)
         _check(self.h, self.lib.hweno_get_state(self.h, ptr, dev))
         return out
 
@@ -258,8 +264,8 @@ class Solver:
             rhs = torch.empty((12, self.ny, self.nx), dtype=torch.float64, device="cuda")
         if vhat is None:
             vhat = torch.empty((8, self.ny, self.nx), dtype=torch.float64, device="cuda")
-        pr, dr = _ptr_of(rhs)
-        pv, dv = _ptr_of(vhat)
+        pr, dr = _ptr_of(rhs, 12 * self.nx * self.ny)
+        pv, dv = _ptr_of(vhat, 8 * self.nx * self.ny)
         if dr != dv:
             raise ValueError("rhs and vhat must both be host or both be device buffers")
         _check(self.h, self.lib.hweno_residual(self.h, pr, pv, dr))
@@ -289,7 +295,7 @@ class Solver:
         import torch
         n = {0: 48, 1: 36, 2: 18, 3: 126, 4: 2}[which]
         out = torch.empty((n, self.ny, self.nx), dtype=torch.float64, device="cuda")
-        ptr, dev = _ptr_of(out)
+        ptr, dev = _ptr_of(out, n * self.nx * self.ny)
         _check(self.h, self.lib.hweno_debug_fields(self.h, int(which), ptr, dev))
         return out
 
@@ -315,10 +321,11 @@ class Solver:
         """(xbar, mubar): VJP of (residual, modified moments) at the state x."""
         if xbar is None:
             xbar = np.zeros_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
-        px, dx = _ptr_of(x)
-        po, _ = _ptr_of(xbar)
-        pr = _ptr_of(rbar)[0] if rbar is not None else None
-        pm = _ptr_of(mbar)[0] if mbar is not None else None
+        n12, n8 = 12 * self.nx * self.ny, 8 * self.nx * self.ny
+        px, dx = _ptr_of(x, n12)
+        po, _ = _ptr_of(xbar, n12)
+        pr = _ptr_of(rbar, n12)[0] if rbar is not None else None
+        pm = _ptr_of(mbar, n8)[0] if mbar is not None else None
         mub = ctypes.c_double(0.0)
         _check(self.h, self.lib.hweno_adjoint_residual(self.h, px, pr, pm, po, ctypes.byref(mub), dx))
         return xbar, mub.value
@@ -337,8 +344,8 @@ class Solver:
         import torch
         if lam_start is None:
             lam_start = torch.empty_like(lam_end) if torch.is_tensor(lam_end) else np.empty_like(lam_end)
-        pl, dl = _ptr_of(lam_end)
-        po, do = _ptr_of(lam_start)
+        pl, dl = _ptr_of(lam_end, 12 * self.nx * self.ny)
+        po, do = _ptr_of(lam_start, 12 * self.nx * self.ny)
         if dl != do:
             raise ValueError("lam_end and lam_start must both be host or both be device buffers")
         mub = ctypes.c_double(0.0)
@@ -350,9 +357,10 @@ class Solver:
         import torch
         if lam_start is None:
             lam_start = torch.empty_like(lam_end)
-        pq, dq = _ptr_of(q_start)
-        pl, dl = _ptr_of(lam_end)
-        po, do = _ptr_of(lam_start)
+        n12 = 12 * self.nx * self.ny
+        pq, dq = _ptr_of(q_start, n12)
+        pl, dl = _ptr_of(lam_end, n12)
+        po, do = _ptr_of(lam_start, n12)
         if not (dq == dl == do):
             raise ValueError("q_start, lam_end and lam_start must all be host or all be device buffers")
         arr = (ctypes.c_double * len(dts))(*[float(x) for x in dts])
@@ -365,9 +373,10 @@ class Solver:
         import torch
         if lam is None:
             lam = torch.empty_like(lam_next)
-        pq, dq = _ptr_of(q)
-        pl, dl = _ptr_of(lam_next)
-        po, do = _ptr_of(lam)
+        n12 = 12 * self.nx * self.ny
+        pq, dq = _ptr_of(q, n12)
+        pl, dl = _ptr_of(lam_next, n12)
+        po, do = _ptr_of(lam, n12)
         if not (dq == dl == do):
             raise ValueError("q, lam_next and lam must all be host or all be device buffers")
         mub = ctypes.c_double(0.0)
@@ -550,9 +559,10 @@ def make_config1d(n, x0=0.0, x1=1.0, gamma=1.4, Pr=0.72, Re=1000.0, bc=("periodi
     return c
 
 
-def _dev1d(a):
-    """device pointer of a CUDA float64 tensor (the 1D ABI takes device buffers only)"""
-    ptr, dev = _ptr_of(a)
+def _dev1d(a, count):
+    """device pointer of a CUDA float64 tensor of count elements (the 1D ABI takes device
+    buffers only)"""
+    ptr, dev = _ptr_of(a, count)
     if not dev:
         raise ValueError("the 1D solver takes CUDA tensors")
     return ptr
@@ -570,7 +580,9 @@ def advance1d(params_list, states, t0, t_end, max_steps=2 ** 31 - 1, stream=None
     lib = load()
     n = len(params_list)
     cfgs = (hweno1d_config * n)(*[make_config1d(**p) for p in params_list])
-    ptrs = (ctypes.c_void_p * n)(*[_dev1d(q).value for q in states])
+    if len(states) != n:
+        raise ValueError("one state per problem: %d problems, %d states" % (n, len(states)))
+    ptrs = (ctypes.c_void_p * n)(*[_dev1d(q, 6 * cfgs[k].n).value for k, q in enumerate(states)])
     out = np.zeros(4 * n)
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check1d(lib.hweno1d_advance(cfgs, n, ptrs, float(t0), float(t_end), int(max_steps),
@@ -585,7 +597,7 @@ def step1d(params, state, t, dt=0.0, stream=None):
     c = make_config1d(**params)
     out = np.zeros(3)
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
-    _check1d(lib.hweno1d_step(ctypes.byref(c), _dev1d(state), float(t), float(dt),
+    _check1d(lib.hweno1d_step(ctypes.byref(c), _dev1d(state, 6 * c.n), float(t), float(dt),
                               out.ctypes.data_as(_D), s))
     return {"dt": out[0], "rejections": int(out[1]), "status": int(out[2])}
 
@@ -598,5 +610,6 @@ def residual1d(params, state, t=0.0, stream=None):
     rhs = torch.empty((6, c.n), dtype=torch.float64, device="cuda")
     vhat = torch.empty((3, c.n), dtype=torch.float64, device="cuda")
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
-    _check1d(lib.hweno1d_residual(ctypes.byref(c), _dev1d(state), float(t), _dev1d(rhs), _dev1d(vhat), s))
+    _check1d(lib.hweno1d_residual(ctypes.byref(c), _dev1d(state, 6 * c.n), float(t), _dev1d(rhs, 6 * c.n),
+                                  _dev1d(vhat, 3 * c.n), s))
     return rhs, vhat

@@ -234,3 +234,26 @@ def test_linear_gradient_ablation_is_validated_before_any_device_call(lib):
     cfgs = (hweno.hweno_config * 1)(hweno.make_config(8, 8, linear_grad=True))
     assert lib.hweno_batch_init(cfgs, 1, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
     assert b.value is None
+
+
+def test_binding_refuses_buffers_of_the_wrong_size():
+    """the library reads or writes exactly the configured number of elements: the binding
+    refuses a state or an output of another size before any call (no GPU needed)"""
+    import numpy as np
+    from paper_2608_10569_b300 import hweno
+    with pytest.raises(ValueError):
+        hweno._ptr_of(np.zeros((12, 5, 7)), 12 * 5 * 8)
+    with pytest.raises(ValueError):
+        hweno._ptr_of(np.zeros((12, 5, 7), dtype=np.float32))
+    ptr, dev = hweno._ptr_of(np.zeros((12, 5, 7)), 12 * 5 * 7)
+    assert ptr.value and dev == 0
+    view = hweno.Solver.__new__(hweno.Solver)
+    view.nx, view.ny, view.h, view.lib = 7, 5, None, None
+    for call in (lambda: view.set_state(np.zeros((12, 5, 6))),
+                 lambda: view.get_state(np.zeros((12, 4, 7))),
+                 lambda: view.residual(np.zeros((12, 5, 7)), np.zeros((12, 5, 7))),
+                 lambda: view.adjoint_step(np.zeros((12, 5, 7)), 1e-3, np.zeros((12, 5, 8)), np.zeros((12, 5, 7)))):
+        with pytest.raises(ValueError):
+            call()
+    with pytest.raises(ValueError):
+        hweno.advance1d([dict(n=8)], [], 0.0, 1.0)
