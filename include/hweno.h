@@ -99,7 +99,9 @@ typedef struct {
     double b_visc;            /* viscous step factor of dt <= b Re h^2 (Sec. 5: 0.001) */
     double eps_pp;            /* positivity-limiter epsilon (Sec. 5: 1e-12) */
     double eps_weno;          /* epsilon of the nonlinear weights (Appendix A: 1e-8) */
-    int max_halvings;         /* restarts with dt/2 before HWENO_ERR_INADMISSIBLE */
+    int max_halvings;         /* restarts with dt/2 before HWENO_ERR_INADMISSIBLE (the
+                                 paper sets no limit; default 60, dt down to 2^-60 of the
+                                 rule's: Sedov 2D's first step needs 37) */
     int precision;            /* HWENO_FP64 or HWENO_MIXED */
     int scheme;               /* HWENO_SCHEME_GR or HWENO_SCHEME_DR (handles, and FP64
                                  batches whose cases all take DR; the adjoint and
@@ -136,7 +138,7 @@ typedef struct {
 
 /* Fill *cfg with the paper's defaults (Sec. 5, Appendix A): periodic boxes on
  * [0,1]^2, gamma 1.4, Pr 0.72, Re 1000, CFL 0.6, b 0.001, eps_PP 1e-12,
- * eps_WENO 1e-8, 20 halvings, FP64.  nx, ny are set to 0 and must be given. */
+ * eps_WENO 1e-8, 60 halvings, FP64.  nx, ny are set to 0 and must be given. */
 int hweno_config_default(hweno_config* cfg);
 
 /* Create a solver on the current CUDA device.  stream: a cudaStream_t passed as

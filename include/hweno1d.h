@@ -53,13 +53,14 @@ typedef struct {
     double b_visc;
     double eps_pp;          /* positivity-limiter epsilon */
     double eps_weno;        /* epsilon of the nonlinear weights */
-    int max_halvings;       /* restarts with dt/2 before HWENO_ERR_INADMISSIBLE */
+    int max_halvings;       /* restarts with dt/2 before HWENO_ERR_INADMISSIBLE (the paper
+                               sets no limit; default 60) */
     int source;             /* HWENO1D_SOURCE_* */
     double inflow[2][3];    /* conserved states of inflow ends (left, right) */
 } hweno1d_config;
 
 /* Paper defaults: gamma 1.4, Pr 0.72, Re 1000, CFL 0.6, b 0.001, eps_PP 1e-12,
- * eps_WENO 1e-8, 20 halvings, periodic ends on [0, 1]; n is left 0. */
+ * eps_WENO 1e-8, 60 halvings, periodic ends on [0, 1]; n is left 0. */
 int hweno1d_config_default(hweno1d_config* c);
 
 /* Advance nprob independent problems from t0 to t_end (at most max_steps steps each)

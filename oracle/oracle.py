@@ -113,7 +113,7 @@ def _ptr(a):
 
 def make_cfg(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
              bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
-             max_halvings=20, linear_weights=False, limiter=True, scheme="gr", source=0, time=0.0,
+             max_halvings=60, linear_weights=False, limiter=True, scheme="gr", source=0, time=0.0,
              inflow=None, band=None, linear_grad=False, **_ignored):
     """inflow: per side (xlo, xhi, ylo, yhi) None or a pair of conserved states (A, B);
     band: per side (centre, half-width) of the face coordinate where A applies"""
@@ -347,7 +347,7 @@ def _load1():
 
 
 def make_cfg1d(n, x0=0.0, x1=1.0, gamma=1.4, Pr=0.72, Re=1000.0, bc=("periodic", "periodic"), cfl=0.6,
-               b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8, max_halvings=20, linear_weights=False, limiter=True,
+               b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8, max_halvings=60, linear_weights=False, limiter=True,
                scheme="gr", source=0, time=0.0, inflow=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), **_ignored):
     c = _Cfg1()
     c.n = int(n)

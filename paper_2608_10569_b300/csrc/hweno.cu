@@ -492,7 +492,7 @@ int hweno_config_default(hweno_config* c) {
   c->gamma = 1.4; c->Pr = 0.72; c->Re = 1000.0;
   for (int k = 0; k < 4; k++) c->bc[k] = HWENO_BC_PERIODIC;
   c->cfl = 0.6; c->b_visc = 1e-3; c->eps_pp = 1e-12; c->eps_weno = 1e-8;
-  c->max_halvings = 20;
+  c->max_halvings = 60;
   c->precision = HWENO_FP64;
   return HWENO_OK;
 }

@@ -650,7 +650,7 @@ int hweno1d_config_default(hweno1d_config* c) {
   c->x0 = 0.0; c->x1 = 1.0;
   c->gamma = 1.4; c->Pr = 0.72; c->Re = 1000.0;
   c->cfl = 0.6; c->b_visc = 1e-3; c->eps_pp = 1e-12; c->eps_weno = 1e-8;
-  c->max_halvings = 20;
+  c->max_halvings = 60;
   return HWENO_OK;
 }
 

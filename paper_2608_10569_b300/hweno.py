@@ -166,7 +166,7 @@ def _check(h, rc):
 
 def make_config(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, Pr=0.72, Re=1000.0,
                 bc=("periodic",) * 4, cfl=0.6, b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8,
-                max_halvings=20, precision="fp64", scheme="gr", source=0, inflow=None, band=None,
+                max_halvings=60, precision="fp64", scheme="gr", source=0, inflow=None, band=None,
                 linear_grad=False, **_ignored):
     """inflow: per face (xlo, xhi, ylo, yhi) None or the pair of conserved states (inside,
     outside) the face's band; band: per face None or (centre, half width)"""
@@ -540,7 +540,7 @@ def rollout(q0, mu, case_params, nsteps, ckpt=20):
 # one-dimensional solver (include/hweno1d.h)
 
 def make_config1d(n, x0=0.0, x1=1.0, gamma=1.4, Pr=0.72, Re=1000.0, bc=("periodic", "periodic"), cfl=0.6,
-                  b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8, max_halvings=20, scheme="gr", source=0,
+                  b_visc=1e-3, eps_pp=1e-12, eps_weno=1e-8, max_halvings=60, scheme="gr", source=0,
                   inflow=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), **_ignored):
     c = hweno1d_config()
     load().hweno1d_config_default(ctypes.byref(c))

@@ -37,7 +37,7 @@ class Case:
     b_visc: float = 1e-3
     eps_pp: float = 1e-12
     eps_weno: float = 1e-8
-    max_halvings: int = 20
+    max_halvings: int = 60
     source: int = 0          # 1: Example 5.2's manufactured source term
     inflow: tuple = None     # per side None or conserved states (A, B) of an inflow face
     band: tuple = None       # per side (centre, half-width) of the face coordinate where A applies

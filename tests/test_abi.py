@@ -43,7 +43,7 @@ def test_config_default_matches_the_paper(lib):
     c = hweno.hweno_config()
     assert lib.hweno_config_default(ctypes.byref(c)) == 0
     assert (c.cfl, c.b_visc, c.eps_pp, c.eps_weno) == (0.6, 1e-3, 1e-12, 1e-8)
-    assert (c.gamma, c.Pr, c.max_halvings) == (1.4, 0.72, 20)
+    assert (c.gamma, c.Pr, c.max_halvings) == (1.4, 0.72, 60)
 
 
 def test_invalid_configurations_are_rejected_before_any_device_call(lib):

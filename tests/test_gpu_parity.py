@@ -200,6 +200,7 @@ def test_inadmissible_after_max_halvings_reports_error():
     bound to ~1e11 cannot be stepped within 20 halvings: the step fails with
     HWENO_ERR_INADMISSIBLE and leaves the state at t^n, as the oracle reports."""
     case, q = I.random_rough(32, 32, seed=2, low=0.01)
+    case.max_halvings = 20
     _, st = O.step(ocfg(case), q, dt_fixed=1e-3)
     assert st["status"] == -3
     s = hweno.Solver(case.params())

@@ -131,13 +131,14 @@ def test_run_parity_open_faces(name, precision):
 
 
 def test_mach2000_steps_and_stall():
-    """Example 5.9 at 32 x 16: six rule steps with the oracle's restarts (2, 6, 7, 15,
-    17, 18) and step sizes, then a step that stays inadmissible after 20 halvings and
-    leaves the state at t^n, as in the oracle.  The states match to 1e-10: the jet's
+    """Example 5.9 at 32 x 16 with the restarts capped at 20: six rule steps with the
+    oracle's restarts (2, 6, 7, 15, 17, 18) and step sizes, then a step that stays
+    inadmissible after 20 halvings and leaves the state at t^n, as in the oracle.  The states match to 1e-10: the jet's
     characteristic projection (|u|/c ~ 2e3 at the band's edges) amplifies rounding
     differences about 5e3-fold in the residual next to the inflow face (1.1e-12 of the
     flux scale between the kernels' code run on the host and the oracle)"""
     case, q = I.mach2000(32, 16)
+    case.max_halvings = 20
     cfg = ocfg(case)
     s = hweno.Solver(case.params())
     s.set_state(torch.from_numpy(q).cuda())
@@ -158,9 +159,11 @@ def test_mach2000_steps_and_stall():
 
 
 def test_sedov_first_step_stalls_as_in_the_oracle():
-    """Example 5.7 at 24^2 with E = 1e-12 away from the corner cell: the PP wave-speed
-    bound (about 2.5e12) keeps the first step inadmissible through 20 halvings in both"""
+    """Example 5.7 at 24^2 with E = 1e-12 away from the corner cell and the restarts
+    capped at 20: the PP wave-speed bound (about 2.5e12) keeps the first step
+    inadmissible through 20 halvings in both"""
     case, q = I.sedov_2d(24)
+    case.max_halvings = 20
     _, st = O.step(ocfg(case), q)
     assert st["status"] == -3
     s = hweno.Solver(case.params())
@@ -169,6 +172,26 @@ def test_sedov_first_step_stalls_as_in_the_oracle():
         s.step()
     assert e.value.code == hweno.HWENO_ERR_INADMISSIBLE
     assert np.array_equal(s.get_state().cpu().numpy(), q)
+    s.close()
+
+
+def test_sedov_steps_with_the_default_halvings():
+    """with the default cap (60) Sedov's first step is taken after 37 halvings (dt =
+    1.5e-14) and the next ones after 27, 12 and 7, as in the oracle; the step sizes
+    agree to 1e-6 and the states to 1e-5 (a one-ulp change of the data moves them by
+    1e-7: E = 1e-12 away from the blast)"""
+    case, q = I.sedov_2d(24)
+    cfg = ocfg(case)
+    s = hweno.Solver(case.params())
+    s.set_state(torch.from_numpy(q).cuda())
+    qo, t = q, 0.0
+    for expect in (37, 27, 12, 7):
+        qo, st = O.step(cfg, qo, t=t)
+        t += st["dt"]
+        dt, rej = s.step()
+        assert st["status"] == 0 and st["rejections"] == expect == rej
+        assert abs(dt - st["dt"]) <= 1e-6 * st["dt"]
+        assert rel_linf(s.get_state().cpu().numpy(), qo, state_scale(q)) <= 1e-5
     s.close()
 
 
