@@ -496,7 +496,8 @@ def _bounded_run(s, t_end, max_steps, wall_s):
 def run_next(args):
     """The widened rows on the GPU, a JSON line after each block (the last one complete):
     - the 1D solver (one thread block per problem): an ensemble of 4 x 148 periodic
-      problems of 256 cells, 50 steps each, for the throughput of a full GPU; and, last,
+      problems of 256 cells, 50 steps each, for the throughput of a full GPU; Example 5.4
+      (the double rarefaction, 200 cells, T = 0.6) for both schemes; and, last,
       Example 5.1's convergence study, Table 5.1's seven meshes for both schemes in one
       launch to T = 0.1, with the density errors, orders and step rates;
     - the inflow and outflow faces: the shock tube's 1024 x 512 box with open faces
@@ -538,6 +539,16 @@ def run_next(args):
                                        "failed": sum(1 for r in res if r["status"] != 0),
                                        "Gcell_stage_per_s": 3.0 * n * done / (ms * 1e-3) / 1e9}
         snapshot()
+
+    # ---- 1D: Example 5.4, the double rarefaction, both schemes in one launch -------------
+    p, q = I.double_rarefaction(200)
+    params = [dict(p, scheme="gr"), dict(p, scheme="dr")]
+    states = [torch.from_numpy(q).cuda() for _ in params]
+    res, ms = timed(lambda: hweno.advance1d(params, states, 0.0, 0.6, max_steps=100000, stream=stream))
+    out["example_5_4_200"] = {"launches": 1, "ms": ms, "T": 0.6,
+                              "gr": res[0], "dr": res[1],
+                              "min_rho": [float(st.cpu().numpy()[0].min()) for st in states]}
+    snapshot()
 
     # ---- open faces: the shock tube's box --------------------------------------------
     case, q = I.open_shock_tube(args.nx, args.ny)
