@@ -490,7 +490,10 @@ def _bounded_run(s, t_end, max_steps, wall_s):
     d = s.diag()
     return {"status": status, "t": d["t"], "steps": d["steps"], "rejected": d["rejected"], "pp_percent": pp_pct(d),
             "dt_last": d["dt_last"], "beta_max_first": beta[0] if beta else None,
-            "beta_max_last": beta[-1] if beta else None, "wall_s": time.perf_counter() - t0}
+            "beta_max_last": beta[-1] if beta else None,
+            # the range the paper's beta_max figure describes, over the steps taken
+            "beta_max_percentiles_10_50_90": [float(v) for v in np.percentile(beta, [10, 50, 90])] if beta else None,
+            "wall_s": time.perf_counter() - t0}
 
 
 def run_next(args):
