@@ -65,18 +65,19 @@ int hweno1d_config_default(hweno1d_config* c);
 
 /* Advance nprob independent problems from t0 to t_end (at most max_steps steps each)
  * under the step rule of Sec. 5, one thread block per problem.  q[k] is problem k's
- * state (device, [2][3][n_k]), updated in place.  out (host, 4*nprob doubles, may be
- * NULL): per problem the time reached, the steps taken, the restarts and the status
- * (0, HWENO_ERR_INADMISSIBLE when a stage stays inadmissible after max_halvings
- * restarts, HWENO_ERR_NONFINITE when a residual is not finite; the state is then the
- * last accepted one).  Errors: HWENO_ERR_ARG for an invalid configuration,
- * HWENO_ERR_CUDA. */
+ * state (device, [2][3][n_k]), updated in place.  out (host, 5*nprob doubles, may be
+ * NULL): per problem the time reached, the steps taken, the restarts, the status (0,
+ * HWENO_ERR_INADMISSIBLE when a stage stays inadmissible after max_halvings restarts,
+ * HWENO_ERR_NONFINITE when a residual is not finite; the state is then the last
+ * accepted one) and the limiter activations (interior cells the PP limiter acted on,
+ * summed over the three stage evaluations of every accepted step: Table 5.3's count).
+ * Errors: HWENO_ERR_ARG for an invalid configuration, HWENO_ERR_CUDA. */
 int hweno1d_advance(const hweno1d_config* cfgs, int nprob, double* const* q, double t0, double t_end,
                     int max_steps, double* out, void* stream);
 
 /* One SSP-RK3 step of one problem from time t: dt > 0 a trial step, dt <= 0 the rule
- * of Sec. 5.  out (host, 3 doubles, may be NULL): the step taken, the restarts, the
- * status as in hweno1d_advance. */
+ * of Sec. 5.  out (host, 4 doubles, may be NULL): the step taken, the restarts, the
+ * status and the limiter activations, as in hweno1d_advance. */
 int hweno1d_step(const hweno1d_config* cfg, double* q, double t, double dt, double* out, void* stream);
 
 /* One evaluation of the spatial operator at time t (the source's time): rhs [2][3][n]

@@ -159,7 +159,7 @@ __host__ __device__ void eigen(const double* ub, double g, double L[3][3], doubl
 
 // characteristic reconstruction of padded cell k (Sec. 2.1, Eq. (2.4)): the Lobatto
 // values, their x-derivatives (Eq. (2.5)) and the modified moment, then the limiter
-__host__ __device__ void cons_cell(const Prob& p, const Ptrs& s, int k) {
+__host__ __device__ int cons_cell(const Prob& p, const Ptrs& s, int k) {
   const long long P = p.n + 2 * G;
   double ub[3], ql[6], qr[6];
   for (int v = 0; v < 3; v++) ub[v] = s.Q[v * P + k];
@@ -202,7 +202,9 @@ __host__ __device__ void cons_cell(const Prob& p, const Ptrs& s, int k) {
     for (int f = 0; f < 3; f++) a += R[v][f] * cm[f];
     s.mom[v * P + k] = a;
   }
-  // PP limiter (Sec. 2.1): all four Lobatto values rescaled about the cell average
+  // PP limiter (Sec. 2.1): all four Lobatto values rescaled about the cell average;
+  // active when either factor is below 1
+  int active = 0;
   const double pb = pressure(ub, p.gamma);
   if (ub[0] > 0.0 && pb > 0.0) {
     double eps = fmin(p.eps_pp, fmin(ub[0], pb));
@@ -234,9 +236,11 @@ __host__ __device__ void cons_cell(const Prob& p, const Ptrs& s, int k) {
     }
     for (int g = 0; g < 4; g++)
       for (int v = 0; v < 3; v++) pts[g][v] = ub[v] + thp * (pts[g][v] - ub[v]);
+    active = thr < 1.0 || thp < 1.0;
   }
   for (int g = 0; g < 4; g++)
     for (int v = 0; v < 3; v++) s.pts[(3 * g + v) * P + k] = pts[g][v];
+  return active;
 }
 
 __host__ __device__ __forceinline__ void dissip(const double* st, double* w) {
@@ -355,11 +359,29 @@ __device__ double block_max(double v, double* sh) {
   return r;
 }
 
+// block sum of small non-negative integers held as doubles (exact)
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = sh[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); k++) m += sh[k];
+    sh[0] = m;
+  }
+  __syncthreads();
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
 // one evaluation of Eq. (2.2) at state q (averages and moments, [6][n]) and time t:
-// rhs [6][n], mom [3][n]; returns alpha* and beta through the block; *bad is set when
-// an output is not finite
+// rhs [6][n], mom [3][n]; returns alpha*, beta and the interior cells the limiter acted
+// on through the block; *bad is set when an output is not finite
 __device__ void residual(const Prob& p, const Ptrs& s, const double* q, double t, double* rhs, double* mom,
-                         double* sh, double* alpha, double* beta, int* bad) {
+                         double* sh, double* alpha, double* beta, double* act, int* bad) {
   const int n = p.n;
   const long long P = n + 2 * G;
   for (int k = threadIdx.x; k < P; k += blockDim.x) {
@@ -368,7 +390,11 @@ __device__ void residual(const Prob& p, const Ptrs& s, const double* q, double t
     for (int m = 0; m < 6; m++) s.Q[m * P + k] = v[m];
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < n + 6; k += blockDim.x) cons_cell(p, s, k + 1);  // cells -3 .. n+2
+  double act_local = 0.0;
+  for (int k = threadIdx.x; k < n + 6; k += blockDim.x) {  // cells -3 .. n+2
+    const int a = cons_cell(p, s, k + 1);
+    if (k >= 3 && k < n + 3) act_local += a;
+  }
   __syncthreads();
   if (p.scheme == 1) {
     for (int k = threadIdx.x; k < n + 2; k += blockDim.x) dr_cell(p, s, k + 3);  // cells -1 .. n
@@ -435,6 +461,7 @@ __device__ void residual(const Prob& p, const Ptrs& s, const double* q, double t
   }
   *alpha = block_max(amax, sh);
   *beta = block_max(bmax, sh);
+  *act = block_sum(act_local, sh);
   *bad = __syncthreads_or(nonfinite);
 }
 
@@ -461,29 +488,35 @@ __device__ void stage(const Prob& p, double a, const double* base, const double*
 }
 
 // mode 0: advance to t_end (max_steps); mode 1: one step (dt_in > 0 forced); mode 2:
-// one residual (rhs into r0, modified moments into m0).  out per problem: the time
-// reached (mode 0) or the step taken (mode 1), steps, rejections, status.
+// one residual (rhs into r0, modified moments into m0).  out per problem (OUT doubles):
+// the time reached (mode 0) or the step taken (mode 1), steps, rejections, status, and
+// the limiter activations (interior cells the limiter acted on, summed over the three
+// stage evaluations of the accepted steps; mode 2: of the one evaluation).
+constexpr int OUT = 5;
 __global__ void __launch_bounds__(THREADS) k_solve(const Prob* probs, int mode, double t0, double t_end,
                                                     int max_steps, double dt_in, double* out) {
   const Prob& p = probs[blockIdx.x];
   const Ptrs s = layout(p);
   __shared__ double sh[THREADS / 32];
   __shared__ double s_dt;
-  double t = t0, dt_last = 0.0, alpha, beta;
+  double t = t0, dt_last = 0.0, alpha, beta, act, pp_total = 0.0;
   int steps = 0, rej_total = 0, status = 0, bad;
+  double* o = out + (long long)OUT * blockIdx.x;
   if (mode == 2) {
-    residual(p, s, p.q, t0, s.r0, s.m0, sh, &alpha, &beta, &bad);
+    residual(p, s, p.q, t0, s.r0, s.m0, sh, &alpha, &beta, &act, &bad);
     if (threadIdx.x == 0) {
-      out[4 * blockIdx.x] = t0;
-      out[4 * blockIdx.x + 3] = bad ? HWENO_ERR_NONFINITE : 0;
+      o[0] = t0;
+      o[3] = bad ? HWENO_ERR_NONFINITE : 0;
+      o[4] = act;
     }
     return;
   }
   const int n = p.n;
   for (int it = 0; it < (mode == 1 ? 1 : max_steps); it++) {
     if (mode == 0 && !(t < t_end)) break;
-    residual(p, s, p.q, t, s.r0, s.m0, sh, &alpha, &beta, &bad);
+    residual(p, s, p.q, t, s.r0, s.m0, sh, &alpha, &beta, &act, &bad);
     if (bad) { status = HWENO_ERR_NONFINITE; break; }
+    const double act0 = act;
     if (threadIdx.x == 0) {
       double dt = dt_in > 0.0 ? dt_in : fmin(p.cfl * p.dx / alpha, p.visc_cap);
       if (mode == 0 && t + dt > t_end) dt = t_end - t;
@@ -492,7 +525,9 @@ __global__ void __launch_bounds__(THREADS) k_solve(const Prob* probs, int mode, 
     __syncthreads();
     double dt = s_dt;
     int rej = 0, ok = 0;
+    double sa = act0;
     for (int h = 0; h <= p.max_halvings; h++) {
+      sa = act0;  // the activations of an attempt count only when it is accepted
       // stage 1: [u; vhat]^n + dt F
       for (int i = threadIdx.x; i < n; i += blockDim.x)
         for (int v = 0; v < 3; v++) {
@@ -502,7 +537,8 @@ __global__ void __launch_bounds__(THREADS) k_solve(const Prob* probs, int mode, 
       __syncthreads();
       ok = admissible(p, s.q1);
       if (ok) {
-        residual(p, s, s.q1, t + dt, s.r, s.m, sh, &alpha, &beta, &bad);
+        residual(p, s, s.q1, t + dt, s.r, s.m, sh, &alpha, &beta, &act, &bad);
+        sa += act;
         ok = !bad;
       }
       if (ok) {
@@ -510,7 +546,8 @@ __global__ void __launch_bounds__(THREADS) k_solve(const Prob* probs, int mode, 
         ok = admissible(p, s.q2);
       }
       if (ok) {
-        residual(p, s, s.q2, t + 0.5 * dt, s.r, s.m, sh, &alpha, &beta, &bad);
+        residual(p, s, s.q2, t + 0.5 * dt, s.r, s.m, sh, &alpha, &beta, &act, &bad);
+        sa += act;
         ok = !bad;
       }
       if (ok) {
@@ -528,13 +565,15 @@ __global__ void __launch_bounds__(THREADS) k_solve(const Prob* probs, int mode, 
     dt_last = dt;
     steps++;
     rej_total += rej;
+    pp_total += sa;
     if (mode == 0 && t_end - t <= 1e-14 * fmax(1.0, fabs(t_end))) t = t_end;
   }
   if (threadIdx.x == 0) {
-    out[4 * blockIdx.x] = mode == 0 ? t : dt_last;
-    out[4 * blockIdx.x + 1] = steps;
-    out[4 * blockIdx.x + 2] = rej_total;
-    out[4 * blockIdx.x + 3] = status;
+    o[0] = mode == 0 ? t : dt_last;
+    o[1] = steps;
+    o[2] = rej_total;
+    o[3] = status;
+    o[4] = pp_total;
   }
 }
 
@@ -590,7 +629,7 @@ static hw1::Prob make_prob(const hweno1d_config& c, double* q, double* w) {
   return p;
 }
 
-// runs mode on nprob problems; out_host 4*nprob doubles
+// runs mode on nprob problems; out_host OUT*nprob doubles
 static int run(const hweno1d_config* cfgs, int nprob, double* const* q, int mode, double t0, double t_end,
                int max_steps, double dt_in, double* out_host, double* rhs, double* vhat, void* stream) {
   if (!cfgs || nprob < 1 || !q) return fail1(HWENO_ERR_ARG, "NULL argument or no problem");
@@ -607,14 +646,14 @@ static int run(const hweno1d_config* cfgs, int nprob, double* const* q, int mode
   double* dout = nullptr;
   cudaError_t e = cudaMalloc(&work, (size_t)total * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&dprob, nprob * sizeof(hw1::Prob));
-  if (e == cudaSuccess) e = cudaMalloc(&dout, 4 * nprob * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dout, hw1::OUT * nprob * sizeof(double));
   std::vector<hw1::Prob> hp(nprob);
   long long off = 0;
   for (int k = 0; k < nprob; k++) {
     hp[k] = make_prob(cfgs[k], q[k], work + off);
     off += hw1::workspace_doubles(cfgs[k].n);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, 4 * nprob * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, hw1::OUT * nprob * sizeof(double), st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dprob, hp.data(), nprob * sizeof(hw1::Prob), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
@@ -631,8 +670,9 @@ static int run(const hweno1d_config* cfgs, int nprob, double* const* q, int mode
     if (e == cudaSuccess && vhat)
       e = cudaMemcpyAsync(vhat, m0, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st);
   }
-  std::vector<double> ho(4 * nprob, 0.0);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ho.data(), dout, 4 * nprob * sizeof(double), cudaMemcpyDeviceToHost, st);
+  std::vector<double> ho(hw1::OUT * nprob, 0.0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ho.data(), dout, hw1::OUT * nprob * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(work);
   cudaFree(dprob);
@@ -661,13 +701,14 @@ int hweno1d_advance(const hweno1d_config* cfgs, int nprob, double* const* q, dou
 }
 
 int hweno1d_step(const hweno1d_config* cfg, double* q, double t, double dt, double* out, void* stream) {
-  double o[4];
+  double o[hw1::OUT];
   int rc = run(cfg, 1, &q, 1, t, INFINITY, 1, dt, o, nullptr, nullptr, stream);
   if (rc) return rc;
   if (out) {
     out[0] = o[0];
     out[1] = o[2];
     out[2] = o[3];
+    out[3] = o[4];
   }
   return HWENO_OK;
 }
@@ -676,7 +717,7 @@ int hweno1d_residual(const hweno1d_config* cfg, const double* q, double t, doubl
                      void* stream) {
   if (!rhs) return fail1(HWENO_ERR_ARG, "rhs is NULL");
   double* qq = const_cast<double*>(q);
-  double o[4];
+  double o[hw1::OUT];
   int rc = run(cfg, 1, &qq, 2, t, t, 0, 0.0, o, rhs, vhat, stream);
   if (rc) return rc;
   if (o[3] != 0.0) return fail1(HWENO_ERR_NONFINITE, "non-finite residual");

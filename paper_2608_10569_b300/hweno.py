@@ -576,30 +576,30 @@ def _check1d(rc):
 def advance1d(params_list, states, t0, t_end, max_steps=2 ** 31 - 1, stream=None):
     """Advance several 1D problems together (one thread block each) from t0 to t_end.
     states: CUDA float64 tensors of shape (6, n_k), updated in place.  Returns one
-    dict per problem: t, steps, rejections, status."""
+    dict per problem: t, steps, rejections, status, pp_active (limiter activations)."""
     lib = load()
     n = len(params_list)
     cfgs = (hweno1d_config * n)(*[make_config1d(**p) for p in params_list])
     if len(states) != n:
         raise ValueError("one state per problem: %d problems, %d states" % (n, len(states)))
     ptrs = (ctypes.c_void_p * n)(*[_dev1d(q, 6 * cfgs[k].n).value for k, q in enumerate(states)])
-    out = np.zeros(4 * n)
+    out = np.zeros(5 * n)
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check1d(lib.hweno1d_advance(cfgs, n, ptrs, float(t0), float(t_end), int(max_steps),
                                  out.ctypes.data_as(_D), s))
-    return [{"t": out[4 * k], "steps": int(out[4 * k + 1]), "rejections": int(out[4 * k + 2]),
-             "status": int(out[4 * k + 3])} for k in range(n)]
+    return [{"t": out[5 * k], "steps": int(out[5 * k + 1]), "rejections": int(out[5 * k + 2]),
+             "status": int(out[5 * k + 3]), "pp_active": int(out[5 * k + 4])} for k in range(n)]
 
 
 def step1d(params, state, t, dt=0.0, stream=None):
     """One SSP-RK3 step of a 1D problem (state a CUDA (6, n) tensor, in place)."""
     lib = load()
     c = make_config1d(**params)
-    out = np.zeros(3)
+    out = np.zeros(4)
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check1d(lib.hweno1d_step(ctypes.byref(c), _dev1d(state, 6 * c.n), float(t), float(dt),
                               out.ctypes.data_as(_D), s))
-    return {"dt": out[0], "rejections": int(out[1]), "status": int(out[2])}
+    return {"dt": out[0], "rejections": int(out[1]), "status": int(out[2]), "pp_active": int(out[3])}
 
 
 def residual1d(params, state, t=0.0, stream=None):

@@ -24,7 +24,7 @@ int main(int argc, char** argv) {
   const int max_steps = (int)dh[17];
   if (check_cfg(c)) return 4;
   const int n = c.n;
-  std::vector<double> q(6 * n), work(hw1::workspace_doubles(n)), out(4, 0.0);
+  std::vector<double> q(6 * n), work(hw1::workspace_doubles(n)), out(hw1::OUT, 0.0);
   if (fread(q.data(), sizeof(double), 6 * n, f) != (size_t)(6 * n)) return 3;
   fclose(f);
   hw1::Prob p = make_prob(c, q.data(), work.data());
@@ -38,7 +38,7 @@ int main(int argc, char** argv) {
   } else {
     fwrite(q.data(), sizeof(double), 6 * n, o);
   }
-  fwrite(out.data(), sizeof(double), 4, o);
+  fwrite(out.data(), sizeof(double), hw1::OUT, o);
   fclose(o);
   return 0;
 }

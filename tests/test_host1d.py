@@ -118,6 +118,7 @@ def test_forced_and_rule_steps(exe, tmp_path):
     qh, st = run(exe, tmp_path, p, q, 1, dt=0.2)
     qo, so = O.step1d(O.make_cfg1d(**p), q, dt_fixed=0.2)
     assert st[0] == so["dt"] and int(st[2]) == so["rejections"] > 0 and st[3] == 0
+    assert st[4] == so["pp_active"]
     assert rel(qh, qo, np.abs(q[:3]).max(axis=1)) <= 1e-12
     p, q = I.random_smooth_1d(37, seed=6, bc=("reflective", "outflow"))
     qh, st = run(exe, tmp_path, p, q, 1)
@@ -133,6 +134,7 @@ def test_example_5_1_run(exe, tmp_path, scheme):
     qh, st = run(exe, tmp_path, p, q, 0, 0.0, 0.1, 10 ** 6)
     qo, so = O.advance1d(O.make_cfg1d(**p), q, 0.0, 0.1)
     assert st[3] == 0 and int(st[1]) == so["steps"] and st[0] == so["t"]
+    assert st[4] == so["pp_active"] == 0
     assert max(np.abs(qh[k] - qo[k]).sum() / np.abs(qo[k]).sum() for k in range(6)) <= 1e-9
 
 
@@ -144,7 +146,7 @@ def test_restart_path(exe, tmp_path):
     qh, st = run(exe, tmp_path, p, q, 0, 0.0, 0.6, 200)
     qo, so = O.advance1d(O.make_cfg1d(**p), q, 0.0, 0.6, max_steps=200)
     assert int(st[3]) == so["status"] == -3
-    assert int(st[1]) == so["steps"] and int(st[2]) == so["rejections"]
+    assert int(st[1]) == so["steps"] and int(st[2]) == so["rejections"] and st[4] == so["pp_active"]
     assert rel(qh, qo, np.abs(q[:3]).max(axis=1)) <= 1e-12
 
 
@@ -158,7 +160,7 @@ def test_example_5_4_runs_with_the_default_halvings(exe, tmp_path):
     qh, st = run(exe, tmp_path, dict(p, scheme="dr"), q, 0, 0.0, 0.6, 3000)
     qo, so = O.advance1d(O.make_cfg1d(**dict(p, scheme="dr")), q, 0.0, 0.6, max_steps=3000)
     assert st[3] == so["status"] == 0 and st[0] == so["t"] == 0.6
-    assert int(st[1]) == so["steps"] and int(st[2]) == so["rejections"] == 0
+    assert int(st[1]) == so["steps"] and int(st[2]) == so["rejections"] == 0 and st[4] == so["pp_active"]
     assert max(np.abs(qh[k] - qo[k]).sum() / np.abs(qo[k]).sum() for k in range(6)) <= 1e-9
     qh, st = run(exe, tmp_path, p, q, 0, 0.0, 0.6, 3000)
     qo, so = O.advance1d(O.make_cfg1d(**p), q, 0.0, 0.6, max_steps=3000)

@@ -120,6 +120,7 @@ def test_restarts_like_the_oracle():
     qo, so = O.step1d(O.make_cfg1d(**p), q, dt_fixed=0.2)
     assert so["status"] == 0 and so["rejections"] > 0
     assert st["status"] == 0 and st["rejections"] == so["rejections"] and st["dt"] == so["dt"]
+    assert st["pp_active"] == so["pp_active"]
     assert rel(qd.cpu().numpy(), qo, state_scale(q)) <= TOL
     qd = torch.from_numpy(q).cuda()
     p20 = dict(p, max_halvings=20)
@@ -142,6 +143,7 @@ def test_example_5_4_runs_with_the_default_halvings():
     qo, so = O.advance1d(O.make_cfg1d(**params[0]), q, 0.0, 0.6, max_steps=3000)
     assert out[0]["status"] == so["status"] == 0 and out[0]["t"] == 0.6
     assert out[0]["steps"] == so["steps"] and out[0]["rejections"] == so["rejections"] == 0
+    assert out[0]["pp_active"] == so["pp_active"]
     g = states[0].cpu().numpy()
     assert max(np.abs(g[k] - qo[k]).sum() / np.abs(qo[k]).sum() for k in range(6)) <= 1e-9
     _, so = O.advance1d(O.make_cfg1d(**params[1]), q, 0.0, 0.6, max_steps=3000)
