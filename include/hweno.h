@@ -116,7 +116,8 @@ typedef struct {
                                  face (y on x-faces, x on y-faces; w = 0: state [1] alone) */
     int linear_grad;          /* 1: the linear weights in the gradient reconstruction
                                  (Eq. (3.9)) only, the ablation of Remark 3.1; HWENO_SCHEME_GR
-                                 handles and hweno_residual_noalloc; 0 otherwise */
+                                 handles, batches (the same for every case) and
+                                 hweno_residual_noalloc, not the adjoint; 0 otherwise */
     int pad_;                 /* unused, 0 */
 } hweno_config;
 
@@ -300,7 +301,7 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 typedef struct hweno_batch hweno_batch;
 
 /* Create ncases solvers (cfgs[0..ncases-1], as for hweno_init, all with the same
- * precision and scheme, no source term and linear_grad 0; HWENO_SCHEME_DR in
+ * precision, scheme and linear_grad, no source term; HWENO_SCHEME_DR in
  * HWENO_FP64 only) sharing one stream; NULL stream: the batch creates its own
  * non-blocking stream (graph capture needs one).  Allocates everything.  Errors as
  * hweno_init; HWENO_ERR_ARG for cases that differ in precision or scheme. */

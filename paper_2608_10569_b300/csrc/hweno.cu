@@ -1261,7 +1261,8 @@ struct BatchList {
 struct hweno_batch {
   int n = 0;
   int mixed = 0;
-  int dr = 0;  // HWENO-DR: kb_dr on the BR_GRAD list in place of the three gradient kernels
+  int dr = 0;   // HWENO-DR: kb_dr on the BR_GRAD list in place of the three gradient kernels
+  int lin = 0;  // the linear-gradient ablation: the LIN instantiations of kb_grad
   cudaStream_t st = nullptr;
   bool own_stream = false;
   std::vector<hweno_handle*> h;
@@ -1366,7 +1367,8 @@ static void batch_enqueue_step(hweno_batch* b) {
       kb_cons<1><<<grid(BR_CONS), dims(BR_CONS), 0, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n, which);
       kb_face_moments<1><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
       kb_weak_moments<1><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
-      kb_grad<1><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+      if (b->lin) kb_grad<1, true><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+      else kb_grad<1><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
       kb_flux<1><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
       kb_assemble<1><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
       b->launches += 6;
@@ -1382,7 +1384,8 @@ static void batch_enqueue_step(hweno_batch* b) {
                                                                            which);
       kb_face_moments<0><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
       kb_weak_moments<0><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
-      kb_grad<0><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+      if (b->lin) kb_grad<0, true><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+      else kb_grad<0><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
       kb_flux<0><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
       kb_assemble<0><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
       b->launches += 6;
@@ -1405,7 +1408,8 @@ static int batch_grids(hweno_batch* b) {
     b->L[BR_CONS].grid = persistent_grid(b, kb_cons<1>, b->L[BR_CONS].total);
     b->L[BR_FACE].grid = persistent_grid(b, kb_face_moments<1>, b->L[BR_FACE].total);
     b->L[BR_WEAK].grid = persistent_grid(b, kb_weak_moments<1>, b->L[BR_WEAK].total);
-    b->L[BR_GRAD].grid = persistent_grid(b, kb_grad<1>, b->L[BR_GRAD].total);
+    b->L[BR_GRAD].grid = b->lin ? persistent_grid(b, kb_grad<1, true>, b->L[BR_GRAD].total)
+                                : persistent_grid(b, kb_grad<1>, b->L[BR_GRAD].total);
     b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<1>, b->L[BR_FLUX].total);
     b->L[BR_INT].grid = persistent_grid(b, kb_assemble<1>, b->L[BR_INT].total);
   } else if (b->dr) {
@@ -1417,7 +1421,8 @@ static int batch_grids(hweno_batch* b) {
     b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0>, b->L[BR_CONS].total, CONS_SMEM_BYTES);
     b->L[BR_FACE].grid = persistent_grid(b, kb_face_moments<0>, b->L[BR_FACE].total);
     b->L[BR_WEAK].grid = persistent_grid(b, kb_weak_moments<0>, b->L[BR_WEAK].total);
-    b->L[BR_GRAD].grid = persistent_grid(b, kb_grad<0>, b->L[BR_GRAD].total);
+    b->L[BR_GRAD].grid = b->lin ? persistent_grid(b, kb_grad<0, true>, b->L[BR_GRAD].total)
+                                : persistent_grid(b, kb_grad<0>, b->L[BR_GRAD].total);
     b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<0>, b->L[BR_FLUX].total);
     b->L[BR_INT].grid = persistent_grid(b, kb_assemble<0>, b->L[BR_INT].total);
   }
@@ -1484,14 +1489,15 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   for (int c = 0; c < ncases; c++)
     if (check_inflow(cfgs[c])) return HWENO_ERR_ARG;
   for (int c = 0; c < ncases; c++)
-    if (cfgs[c].linear_grad)
-      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels run the nonlinear gradient reconstruction");
+    if (cfgs[c].linear_grad != cfgs[0].linear_grad)
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same linear_grad");
   hweno_batch* b = new (std::nothrow) hweno_batch();
   if (!b) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
   snprintf(b->err, sizeof(b->err), "no error");
   b->n = ncases;
   b->mixed = cfgs[0].precision == HWENO_MIXED;
   b->dr = cfgs[0].scheme == HWENO_SCHEME_DR;
+  b->lin = cfgs[0].linear_grad != 0;
   b->st = (cudaStream_t)stream;
   if (!b->st) {  // graphs cannot be captured on the legacy default stream
     if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1673,7 +1679,9 @@ int hweno_batch_autotune(hweno_batch* b, int* chosen) {
             else kb_weak_moments<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
             break;
           case BR_GRAD:
-            if (b->mixed) kb_grad<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            if (b->mixed && b->lin) kb_grad<1, true><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            else if (b->mixed) kb_grad<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            else if (b->lin) kb_grad<0, true><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
             else kb_grad<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
             break;
           case BR_FLUX:

@@ -101,11 +101,12 @@ __global__ void kb_weak_moments(const CaseDev* __restrict__ cases, TileList L, i
   HW_BATCH_END
 }
 
-template <int MIXED>
+// LIN: the linear weights in the gradient reconstruction (Remark 3.1's ablation)
+template <int MIXED, bool LIN = false>
 __global__ void __launch_bounds__(128) kb_grad(const CaseDev* __restrict__ cases, TileList L, int ncase) {
   HW_BATCH_LOOP(L, ncase)
-  if (MIXED) grad_mixed_body(cg, cw, gx, gy);
-  else grad_body<double>(cg, cw, gx, gy);
+  if (MIXED) grad_mixed_body<LIN>(cg, cw, gx, gy);
+  else grad_body<double, false, LIN>(cg, cw, gx, gy);
   HW_BATCH_END
 }
 

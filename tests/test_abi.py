@@ -221,7 +221,8 @@ def test_open_faces_are_validated_before_any_device_call(lib):
 
 
 def test_linear_gradient_ablation_is_validated_before_any_device_call(lib):
-    """linear_grad is 0 or 1, ablates HWENO-GR only, and is not taken by the batch"""
+    """linear_grad is 0 or 1, ablates HWENO-GR only, and is the same for every case of a
+    batch"""
     from paper_2608_10569_b300 import hweno
     h = ctypes.c_void_p()
     c = hweno.make_config(8, 8, linear_grad=True)
@@ -231,9 +232,9 @@ def test_linear_gradient_ablation_is_validated_before_any_device_call(lib):
     assert lib.hweno_init(ctypes.byref(c), None, ctypes.byref(h)) == hweno.HWENO_ERR_ARG
     assert h.value is None
     b = ctypes.c_void_p()
-    cfgs = (hweno.hweno_config * 1)(hweno.make_config(8, 8, linear_grad=True))
-    assert lib.hweno_batch_init(cfgs, 1, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
-    assert b.value is None
+    cfgs = (hweno.hweno_config * 2)(hweno.make_config(8, 8, linear_grad=True), hweno.make_config(8, 8))
+    assert lib.hweno_batch_init(cfgs, 2, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
+    assert b.value is None and b"linear_grad" in lib.hweno_last_error(None)
 
 
 def test_binding_refuses_buffers_of_the_wrong_size():

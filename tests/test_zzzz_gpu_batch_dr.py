@@ -1,8 +1,9 @@
-"""GPU parity of HWENO-DR in the batch (hweno_batch_init with HWENO_SCHEME_DR cases): the
-batched kernels run the single-grid bodies, so a DR batch must give the DR handles'
-states (to 1e-13 of the state scale: the bodies are inlined into other kernels, whose
-multiply-add contractions may differ) and the oracle's DR step to 1e-12.  Collected
-last, so that a failure here cannot stop the other files under -x.
+"""GPU parity of HWENO-DR and of the linear-gradient ablation in the batch
+(hweno_batch_init with HWENO_SCHEME_DR or linear_grad cases): the batched kernels run
+the single-grid bodies, so a batch must give the handles' states (to 1e-13 of the state
+scale in FP64, 1e-6 mixed: the bodies are inlined into other kernels, whose multiply-add
+contractions may differ) and the oracle's DR step to 1e-12.  Collected last, so that a
+failure here cannot stop the other files under -x.
 """
 import numpy as np
 import pytest
@@ -63,4 +64,29 @@ def test_dr_batch_step_matches_the_oracle():
     scale = np.abs(q[:4]).reshape(4, -1).max(1)
     err = max(np.abs(got[k] - qo[k]).max() / max(np.abs(qo[k]).max(), scale[k % 4]) for k in range(12))
     assert st["status"] == 0 and err <= 1e-12
+    b.close()
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-13), ("mixed", 1e-6)])
+def test_linear_gradient_batch_matches_handles(precision, bound):
+    """Remark 3.1's ablation in a batch: three steps of three cases against the ablated
+    handles"""
+    cases = _cases()
+    stream = torch.cuda.Stream()
+    b = hweno.Batch([dict(c.params(), linear_grad=True) for c, _ in cases], precision=precision, stream=stream)
+    for k, (_, q) in enumerate(cases):
+        b.cases[k].set_state(q.copy())
+    for _ in range(3):
+        b.step(1)
+    for k, (case, q) in enumerate(cases):
+        s = hweno.Solver(dict(case.params(), linear_grad=True), precision=precision, stream=stream)
+        s.set_state(q.copy())
+        for _ in range(3):
+            s.step()
+        ref = s.get_state().cpu().numpy()
+        s.close()
+        got = b.cases[k].get_state(np.zeros_like(q))
+        scale = np.abs(q[:4]).reshape(4, -1).max(1)
+        err = max(np.abs(got[j] - ref[j]).max() / max(np.abs(ref[j]).max(), scale[j % 4]) for j in range(12))
+        assert err <= bound, (k, err)
     b.close()
