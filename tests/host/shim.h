@@ -37,6 +37,7 @@ template <class T>
 static inline T atomicMax(T* a, T v) { const T o = *a; *a = o > v ? o : v; return o; }
 static inline long long __double_as_longlong(double x) { long long b; memcpy(&b, &x, 8); return b; }
 static inline int __double2hiint(double x) { return (int)(__double_as_longlong(x) >> 32); }
+static inline double __longlong_as_double(long long b) { double x; memcpy(&x, &b, 8); return x; }
 static inline unsigned __float_as_uint(float x) { unsigned b; memcpy(&b, &x, 4); return b; }
 static inline float __int_as_float(int b) { float x; memcpy(&x, &b, 4); return x; }
 static inline float __fdividef(float a, float b) { return a / b; }
