@@ -36,7 +36,7 @@ def exe(tmp_path_factory):
     return out
 
 
-def steps(exe, tmp_path, case, q, nsteps, t=0.0, dt=0.0, **kw):
+def steps(exe, tmp_path, case, q, nsteps, t=0.0, dt=0.0, mixed=False, **kw):
     """(state, status, [(dt, restarts) per step]) of the host steps"""
     p = dict(case.params(), **kw)
     nx, ny = p["nx"], p["ny"]
@@ -52,7 +52,7 @@ def steps(exe, tmp_path, case, q, nsteps, t=0.0, dt=0.0, **kw):
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(fin, "wb") as f:
         f.write(struct.pack("11i", nx, ny, *[BC[b] for b in p["bc"]], 1 if p.get("scheme") == "dr" else 0,
-                            int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 0, 0))
+                            int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 0, 1 if mixed else 0))
         f.write(struct.pack("50d", p["x0"], p["x1"], p["y0"], p["y1"], p["gamma"], p["Pr"], p["Re"], p["eps_pp"],
                             p["eps_weno"], t, *st, *bd))
         f.write(struct.pack("i", nsteps))
@@ -135,3 +135,15 @@ def test_dr_rule_steps(exe, tmp_path):
     qo, st = O.advance(O.make_cfg(**dict(case.params(), scheme="dr")), q, 0.0, 1e9, max_steps=2)
     assert status == 0 and len(log) == 2 and abs(sum(a for a, _ in log) - st["t"]) <= 1e-13 * st["t"]
     assert rel_linf(qh, qo, state_scale(q)) <= 1e-12
+
+
+def test_mixed_run_through_open_faces(exe, tmp_path):
+    """the mixed path's 20 steps through the jet's inflow face: the time within 1e-6 and
+    the state within 1e-5 of the oracle's FP64 run (the mixed path's wave speeds come from
+    FP32 traces)"""
+    case, q = y_jet()
+    qh, status, log = steps(exe, tmp_path, case, q, 20, mixed=True)
+    qo, st = O.advance(O.make_cfg(**case.params()), q, 0.0, 1e9, max_steps=20)
+    assert status == 0 and len(log) == 20
+    assert abs(sum(a for a, _ in log) - st["t"]) <= 1e-6 * st["t"]
+    assert rel_l1(qh, qo) <= 1e-5
