@@ -1,7 +1,9 @@
 // One evaluation of the 2D spatial operator with the CUDA path's own code compiled for
 // the host (operator2d.h): FP64 or the mixed path.  Input: the configuration record of
 // operator2d.h, then q[12][ny][nx].  Output (doubles): rhs[12][ny][nx], vhat[8][ny][nx],
-// theta[2][ny][nx], then alpha*, beta_max, limiter activations, flags.
+// theta[2][ny][nx], then alpha*, beta_max, limiter activations, flags, then the
+// intermediate fields as hweno_debug_fields exports them (FP64 path): the 12 face and 9
+// volume points as (rho, rho u, rho v, E), the 18 weak moments and the 126 gradients.
 #include <cstdio>
 #include "operator2d.h"
 
@@ -46,6 +48,25 @@ int main(int argc, char** argv) {
   memcpy(&beta, &diag.beta_bits, sizeof(beta));
   const double tail[4] = {alpha, beta, (double)diag.pp_count, (double)diag.flags};
   fwrite(tail, sizeof(double), 4, out);
+  // points stored as (rho, u, v, e), exported as the conservative variables
+  auto put_cons = [&](const std::vector<double>& a, int npts) {
+    std::vector<double> row(nx);
+    for (int k = 0; k < npts; k++)
+      for (int v = 0; v < 4; v++)
+        for (int j = 0; j < ny; j++) {
+          for (int i = 0; i < nx; i++) {
+            const long long c = cidx(g, i, j);
+            const double rho = a[(4 * k) * g.ps + c], u = a[(4 * k + 1) * g.ps + c];
+            const double w = a[(4 * k + 2) * g.ps + c], e = a[(4 * k + 3) * g.ps + c];
+            row[i] = v == 0 ? rho : v == 1 ? rho * u : v == 2 ? rho * w : rho * (e + 0.5 * (u * u + w * w));
+          }
+          fwrite(row.data(), sizeof(double), nx, out);
+        }
+  };
+  put_cons(s.face, 12);
+  put_cons(s.vol, 9);
+  put(s.rm, 18);
+  put(s.gr, 126);
   fclose(out);
   return 0;
 }

@@ -3,9 +3,8 @@ GPU: for the duration of each test, `hweno.Solver` and `hweno.Batch` are replace
 stand-ins whose residuals come from `host/residual2d_host.cc` and whose steps (forced or
 by the rule, with the restart rule) come from `host/step2d_host.cc`, and CUDA tensors by
 host copies.  The assertions of `test_zzy_gpu_open.py` then meet an arithmetic other
-than the oracle's before they meet the GPU's.  Tests that read the intermediate fields
-beyond theta, `hweno_residual_noalloc` or the adjoint have no stand-in and are not run
-here.
+than the oracle's before they meet the GPU's.  Tests of `hweno_residual_noalloc` and
+of the adjoint have no stand-in and are not run here.
 """
 import inspect
 
@@ -19,8 +18,7 @@ import test_host_step2d as S  # noqa: E402
 import test_zzy_gpu_open as G  # noqa: E402
 from paper_2608_10569_b300 import hweno  # noqa: E402
 
-NOT_HERE = {"test_intermediate_fields_parity_open_faces", "test_linear_gradient_ablation_parity",
-            "test_noalloc_with_open_faces", "test_adjoint_dot_products_with_open_faces"}
+NOT_HERE = {"test_noalloc_with_open_faces", "test_adjoint_dot_products_with_open_faces"}
 
 
 @pytest.fixture(scope="module")
@@ -80,15 +78,14 @@ def _solver_class(exes, tmp_path):
             self.q = np.array(q.numpy() if torch.is_tensor(q) else q, dtype=np.float64)
 
         def residual(self):
-            r = R.run(exes["residual2d_host"], tmp_path, self.p, self.q, self.t, mixed=self.mixed)
-            self.theta, self.d = r[2], (r[3], r[4])
+            r = R.run(exes["residual2d_host"], tmp_path, self.p, self.q, self.t, mixed=self.mixed, dumps=True)
+            self.fields = dict(r[7])
+            self.fields[4] = r[2]
+            self.d = (r[3], r[4])
             return torch.from_numpy(r[0].copy()), torch.from_numpy(r[1].copy())
 
         def debug_fields(self, which):
-            if which != 4:
-                raise NotImplementedError("only theta has a host stand-in")
-            self.residual()
-            return torch.from_numpy(self.theta.copy())
+            return torch.from_numpy(self.fields[which].copy())
 
         def step(self, dt=0.0):
             q, status, log = S.steps(exes["step2d_host"], tmp_path, _Case(self.p), self.q, 1, t=self.t, dt=dt,

@@ -45,8 +45,10 @@ def exe(tmp_path_factory):
     return out
 
 
-def run(exe, tmp_path, p, q, t=0.0, mixed=False):
-    """(rhs, vhat, theta, alpha*, beta_max, limiter activations, flags) of the host run"""
+def run(exe, tmp_path, p, q, t=0.0, mixed=False, dumps=False):
+    """(rhs, vhat, theta, alpha*, beta_max, limiter activations, flags) of the host run,
+    and with dumps the intermediate fields {0: face, 1: vol, 2: rm, 3: grad} as
+    hweno_debug_fields exports them"""
     nx, ny = p["nx"], p["ny"]
     inflow = p.get("inflow") or (None,) * 4
     band = p.get("band") or (None,) * 4
@@ -67,8 +69,15 @@ def run(exe, tmp_path, p, q, t=0.0, mixed=False):
     subprocess.check_call([exe, fin, fout])
     o = np.fromfile(fout, dtype=np.float64)
     m = nx * ny
-    return (o[:12 * m].reshape(12, ny, nx), o[12 * m:20 * m].reshape(8, ny, nx), o[20 * m:22 * m].reshape(2, ny, nx),
-            *o[22 * m:])
+    head = (o[:12 * m].reshape(12, ny, nx), o[12 * m:20 * m].reshape(8, ny, nx), o[20 * m:22 * m].reshape(2, ny, nx),
+            *o[22 * m:22 * m + 4])
+    if not dumps:
+        return head
+    fields, at = {}, 22 * m + 4
+    for k, n in ((0, 48), (1, 36), (2, 18), (3, 126)):
+        fields[k] = o[at:at + n * m].reshape(n, ny, nx)
+        at += n * m
+    return head + (fields,)
 
 
 def open_rough():
@@ -187,3 +196,17 @@ def test_mixed_path_conserves_to_fp64_roundoff(exe, tmp_path):
     rhs = run(exe, tmp_path, case.params(), q, mixed=True)[0]
     for v in range(4):
         assert abs(rhs[v].sum()) <= 1e-13 * np.abs(rhs[v]).sum()
+
+
+@pytest.mark.parametrize("name", ["rough_walls_45x21", "open_rough_40x36", "y_jet_33x29"])
+def test_intermediate_fields(exe, tmp_path, name):
+    """traces, volume values, weak moments and gradients as hweno_debug_fields exports
+    them, against the oracle's, at the GPU parity test's bounds"""
+    case, q = CASES[name]()
+    *head, fields = run(exe, tmp_path, case.params(), q, dumps=True)
+    o = O.residual(O.make_cfg(**case.params()), q, dumps=True)
+    assert rel_linf(fields[0], o["face"], state_scale(q)) <= 1e-12
+    assert rel_linf(fields[1], o["vol"], state_scale(q)) <= 1e-12
+    assert rel_linf(fields[2], o["rm"]) <= 1e-12
+    assert rel_linf(fields[3], o["grad"]) <= 1e-12
+    assert np.abs(head[2] - o["theta"]).max() <= 1e-13
