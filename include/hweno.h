@@ -116,8 +116,8 @@ typedef struct {
                                  face (y on x-faces, x on y-faces; w = 0: state [1] alone) */
     int linear_grad;          /* 1: the linear weights in the gradient reconstruction
                                  (Eq. (3.9)) only, the ablation of Remark 3.1; HWENO_SCHEME_GR
-                                 handles, batches (the same for every case) and
-                                 hweno_residual_noalloc, not the adjoint; 0 otherwise */
+                                 handles, batches (the same for every case),
+                                 hweno_residual_noalloc and the adjoint; 0 otherwise */
     int pad_;                 /* unused, 0 */
 } hweno_config;
 

@@ -50,8 +50,9 @@ __global__ void __launch_bounds__(BX * BY) k_source(Grid g, Quad4 qd, double t0,
                                                     double* __restrict__ rhs) {
   source_body(g, qd, t0, cst, diag, rhs, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
+template <bool LIN = false>
 __global__ void __launch_bounds__(BX * BY) k_grad_rec(Grid g, Work w) {
-  grad_body<double, true>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+  grad_body<double, true, LIN>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 __global__ void k_face_moments(Grid g, Work w) {
   face_moments_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
@@ -416,7 +417,8 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, d
     {
       Prof p(h, K_GRAD);
       if (h->w.yrec)
-        k_grad_rec<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+        if (h->cfg.linear_grad) k_grad_rec<true><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+        else k_grad_rec<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
       else if (h->cfg.linear_grad)
         k_grad<double, true><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
       else
@@ -972,7 +974,8 @@ static int adjoint_operator(hweno_handle* h, const double* x) {
   const dim3 blk(BX, BY);
   ka_assemble<<<grid2(g.nx, g.ny), blk, 0, h->st>>>(g, h->w, a);
   ka_flux<<<grid2(g.nx + 1, g.ny + 1, 2), blk, 0, h->st>>>(g, h->w, a);
-  ka_grad<<<grid2(g.nx + 2, g.ny + 2), blk, 0, h->st>>>(g, h->w, a);
+  if (h->cfg.linear_grad) ka_grad<true><<<grid2(g.nx + 2, g.ny + 2), blk, 0, h->st>>>(g, h->w, a);
+  else ka_grad<<<grid2(g.nx + 2, g.ny + 2), blk, 0, h->st>>>(g, h->w, a);
   ka_gather_rm<<<grid2(g.nx + 4, g.ny + 4), blk, 0, h->st>>>(g, a);
   ka_face_moments<<<grid2(g.nx + 5, g.ny + 5, 2), blk, 0, h->st>>>(g, a);
   ka_cons<<<grid2(g.nx + 6, g.ny + 6), blk, 0, h->st>>>(g, x, h->w, a);
@@ -992,7 +995,6 @@ int hweno_adjoint_init(hweno_handle* h) {
   if (h->cfg.precision != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_FP64");
   if (h->cfg.scheme != HWENO_SCHEME_GR || h->cfg.source != HWENO_SOURCE_NONE)
     return fail(h, HWENO_ERR_ARG, "the adjoint is implemented for HWENO_SCHEME_GR without a source term");
-  if (h->cfg.linear_grad) return fail(h, HWENO_ERR_ARG, "the adjoint runs the nonlinear gradient reconstruction");
   if (h->apool) return HWENO_OK;
   const Grid& g = h->g;
   // R 12, M 8, face 48, vol 36, gr 126, rm 18, cg 102, cc 68, q 12, stage-1 state 12,

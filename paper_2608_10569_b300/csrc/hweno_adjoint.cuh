@@ -648,7 +648,10 @@ __global__ void __launch_bounds__(128) ka_flux(Grid g, Work w, Adj a) {
 }
 
 // gradient HWENO (cells of the interior grown by 1): per field, the adjoint of the
-// combination, written as contributions to the 17 stencil data
+// combination, written as contributions to the 17 stencil data.  LIN: the linear
+// weights of Remark 3.1's ablation, whose combination is p0 itself (C = P0 d), so the
+// adjoint is P0^T applied to the coefficients' adjoint
+template <bool LIN = false>
 __global__ void __launch_bounds__(128) ka_grad(Grid g, Work w, Adj a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x - 1;
   const int j = blockIdx.y * blockDim.y + threadIdx.y - 1;
@@ -665,21 +668,25 @@ __global__ void __launch_bounds__(128) ka_grad(Grid g, Work w, Adj a) {
     d[4] = A[c];
     d[5] = A[cidx(g, i + 1, j)];
     d[7] = A[cidx(g, i, j + 1)];
-    const double* y = w.yrec + (long long)(YREC_GR + 17 * comp) * g.ps + c;
-    double c0[15];
-    for (int k = 0; k < 15; k++) c0[k] = y[(long long)k * g.ps];
-    const double b0 = y[(long long)15 * g.ps], rs = y[(long long)16 * g.ps];
     double ob[21];
     for (int k = 0; k < 21; k++) ob[k] = a.gr[(long long)(6 * k + comp) * g.ps + c];
     double Cb[15] = {0};
     eval_xfaces_T(ob, Cb);
     eval_yfaces_T(ob + 6, Cb);
     eval_vol_T(ob + 12, Cb);
-    const double s[4] = {d[4] - d[3], d[5] - d[4], d[4] - d[1], d[7] - d[4]};
-    double gr[15];
-    hw_beta_quartic_grad<double>(c0, gr);
     double c0b[15] = {0}, sb[4] = {0, 0, 0, 0}, ctrb = 0.0;
-    hweno_combine_T(c0, s, d[4], g.eps_weno, b0, rs, gr, Cb, c0b, sb, ctrb);
+    if constexpr (LIN) {
+      for (int k = 0; k < 15; k++) c0b[k] = Cb[k];
+    } else {
+      const double* y = w.yrec + (long long)(YREC_GR + 17 * comp) * g.ps + c;
+      double c0[15];
+      for (int k = 0; k < 15; k++) c0[k] = y[(long long)k * g.ps];
+      const double b0 = y[(long long)15 * g.ps], rs = y[(long long)16 * g.ps];
+      const double s[4] = {d[4] - d[3], d[5] - d[4], d[4] - d[1], d[7] - d[4]};
+      double gr[15];
+      hw_beta_quartic_grad<double>(c0, gr);
+      hweno_combine_T(c0, s, d[4], g.eps_weno, b0, rs, gr, Cb, c0b, sb, ctrb);
+    }
     double db[17] = {0};
     hw_p0_coeffs_T<double>(c0b, db);
     db[4] += ctrb + sb[0] - sb[1] + sb[2] - sb[3];

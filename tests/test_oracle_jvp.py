@@ -103,3 +103,17 @@ def test_uniform_flow_has_no_tangent_along_uniform_directions():
     scale = 1.0 + np.abs(q).max()
     assert np.abs(j["rhs_dot"]).max() <= 1e-12 * scale
     assert np.abs(j["vhat_dot"]).max() <= 1e-12 * scale
+
+
+def test_linear_gradient_tangent_matches_differences():
+    """the dual build honours Remark 3.1's ablation: its tangent with linear_grad matches
+    the differences of the plain oracle's ablated residual, and differs from the
+    nonlinear one"""
+    case, q = _open()
+    cfg = O.make_cfg(**case.params(), linear_grad=True)
+    v = _direction(q, 3)
+    t = O.residual_jvp(cfg, q, v)["rhs_dot"]
+    fd = richardson(lambda e: O.residual(cfg, q + e * v)["rhs"], 1e-6)
+    assert np.abs(t - fd).max() <= 1e-8 * np.abs(t).max()
+    tn = O.residual_jvp(O.make_cfg(**case.params()), q, v)["rhs_dot"]
+    assert np.abs(t - tn).max() > 1e-6 * np.abs(t).max()

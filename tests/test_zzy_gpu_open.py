@@ -199,6 +199,33 @@ def test_sedov_steps_with_the_default_halvings():
     s.close()
 
 
+def test_adjoint_with_the_linear_gradient_ablation():
+    """the adjoint of the ablated gradient reconstruction (its combination is p0
+    itself): residual and step VJPs against the dual oracle run with linear_grad, to
+    1e-10"""
+    case, q = y_jet()
+    p = dict(case.params(), linear_grad=True)
+    rng = np.random.default_rng(74)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    rbar = rng.normal(size=q.shape)
+    mbar = rng.normal(size=(8,) + q.shape[1:])
+    lam_next = rng.normal(size=q.shape)
+    dt = 1e-3
+    s = hweno.Solver(p)
+    s.adjoint_init()
+    xbar, mub = s.adjoint_residual(q.copy(), rbar, mbar)
+    lam, _ = s.adjoint_step(q.copy(), dt, lam_next, np.zeros_like(q))
+    s.close()
+    cfg = O.make_cfg(**p)
+    t = O.residual_jvp(cfg, q, v)
+    tm = O.residual_jvp(cfg, q, None, dmu=1.0)
+    assert _rel((rbar * t["rhs_dot"]).sum() + (mbar * t["vhat_dot"]).sum(), (xbar * v).sum()) <= 1e-10
+    assert _rel((rbar * tm["rhs_dot"]).sum() + (mbar * tm["vhat_dot"]).sum(), mub) <= 1e-10
+    _, ts, st = O.step_jvp(cfg, q, v, dt)
+    assert st["status"] == 0 and st["rejections"] == 0
+    assert _rel((lam_next * ts).sum(), (lam * v).sum()) <= 1e-10
+
+
 def test_noalloc_with_open_faces():
     case, q = y_jet()
     lib = hweno.load()
