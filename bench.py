@@ -644,9 +644,9 @@ def next_rows_child(args):
 
 
 def run_single(args):
-    """configs 1, 3 and 5 on one solver: FP64 and mixed step rates (config 3, whose
-    limited states make the step rule restart ~20 times per step, reports residual
-    evaluations instead)."""
+    """the smooth periodic flow, the colliding streams and the Taylor-Green flow on one
+    solver: FP64 and mixed step rates (the colliding streams, whose limited states make
+    the step rule restart ~20 times per step, report residual evaluations instead)."""
     import torch
     from paper_2608_10569_b300 import hweno, inputs as I
     if args.workload == "smooth_periodic":

@@ -199,7 +199,7 @@ def test_limiter_vjp_dot_products_with_the_dual_oracle(name):
     assert _rel((lam_next * tms).sum(), mub) <= 1e-10
 
 
-def test_config5_replica_dot_product_with_the_dual_oracle():
+def test_adjoint_taylor_green_replica_dot_product_with_the_dual_oracle():
     """the adjoint Taylor-Green flow (Re 1600, Mach 0.3) on a 64^2 replica: three
     recorded steps under the step rule against the oracle's forward-mode tangent, for
     the initial state and for mu, to 1e-10 or ten times the products' own sensitivity

@@ -281,11 +281,11 @@ def test_mixed_precision_limiter_route_and_intermediates():
 
 CONVERGENCE = {
     # a random smooth periodic field (several Fourier modes in every variable): the
-    # rate is fifth order; config 1's flow without its cell noise, a single density
+    # rate is fifth order; the smooth periodic flow without its cell noise, a single density
     # wave at constant velocity and pressure, converges faster still (the leading
     # error terms cancel for it), so only at least fifth order is asked there
     "random_smooth": (lambda n: I.random_smooth(n, n, seed=31), 0.02, 4.6, 5.8),
-    "config1_smooth": (lambda n: I.smooth_periodic(n, noise=0.0), 0.05, 4.6, None),
+    "smooth_periodic_wave": (lambda n: I.smooth_periodic(n, noise=0.0), 0.05, 4.6, None),
 }
 
 

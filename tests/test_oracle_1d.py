@@ -1,5 +1,5 @@
-"""Pins of the one-dimensional oracle (the scheme of Sec. 2, Appendix A.1), the
-survey's NEXT-3 row: printed constants and error tables of the paper, exact polynomial
+"""Pins of the one-dimensional oracle (the scheme of Sec. 2, Appendix A.1): printed
+constants and error tables of the paper, exact polynomial
 results, integration identities, symmetries and convergence orders.
 """
 import math

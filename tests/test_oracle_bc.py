@@ -1,6 +1,6 @@
 """Pins of the oracle's inflow and outflow boundaries (Remark 4.1) and of the
-rectangular 2D benchmarks built on them (Examples 5.7 and 5.9, the survey's NEXT-4
-row): the ghost-cell rules as Remark 4.1 states them, free stream through open faces,
+rectangular 2D benchmarks built on them (Examples 5.7 and 5.9): the ghost-cell rules as
+Remark 4.1 states them, free stream through open faces,
 the symmetries of the Sedov and Mach-2000 setups, and the linear-gradient ablation of
 Remark 3.1 acting on the gradients alone.
 """
