@@ -106,7 +106,9 @@ typedef struct {
     int scheme;               /* HWENO_SCHEME_GR or HWENO_SCHEME_DR (handles, and FP64
                                  batches whose cases all take DR; the adjoint and
                                  hweno_residual_noalloc take GR) */
-    int source;               /* HWENO_SOURCE_NONE or HWENO_SOURCE_MMS52 (handles only) */
+    int source;               /* HWENO_SOURCE_NONE or HWENO_SOURCE_MMS52 (handles and
+                                 batches, at each case's time; not the adjoint or
+                                 hweno_residual_noalloc) */
     double inflow[4][2][4];   /* per face (xlo, xhi, ylo, yhi) with HWENO_BC_INFLOW: the
                                  conserved state (rho, rho u, rho v, E) of a ghost cell whose
                                  centre lies inside [0] or outside [1] the face's band;
@@ -301,7 +303,7 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 typedef struct hweno_batch hweno_batch;
 
 /* Create ncases solvers (cfgs[0..ncases-1], as for hweno_init, all with the same
- * precision, scheme and linear_grad, no source term; HWENO_SCHEME_DR in
+ * precision, scheme and linear_grad; HWENO_SCHEME_DR in
  * HWENO_FP64 only) sharing one stream; NULL stream: the batch creates its own
  * non-blocking stream (graph capture needs one).  Allocates everything.  Errors as
  * hweno_init; HWENO_ERR_ARG for cases that differ in precision or scheme. */

@@ -1264,7 +1264,8 @@ struct hweno_batch {
   int n = 0;
   int mixed = 0;
   int dr = 0;   // HWENO-DR: kb_dr on the BR_GRAD list in place of the three gradient kernels
-  int lin = 0;  // the linear-gradient ablation: the LIN instantiations of kb_grad
+  int lin = 0;     // the linear-gradient ablation: the LIN instantiations of kb_grad
+  int source = 0;  // some case has a source term: kb_source after each stage's balances
   cudaStream_t st = nullptr;
   bool own_stream = false;
   std::vector<hweno_handle*> h;
@@ -1392,6 +1393,12 @@ static void batch_enqueue_step(hweno_batch* b) {
       kb_assemble<0><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
       b->launches += 6;
     }
+    if (b->source) {
+      // stage times of SSP-RK3: t^n, t^n + dt, t^n + dt/2 (stage 1's is t^n, before dt)
+      const double cst = stage == 1 ? 0.0 : (stage == 2 ? 1.0 : 0.5);
+      kb_source<<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which, cst);
+      b->launches++;
+    }
     if (stage == 1) {
       kb_dt<<<(n + 127) / 128, 128, 0, b->st>>>(b->d_cases, n);
       b->launches++;
@@ -1460,6 +1467,9 @@ static void batch_refresh_case(hweno_batch* b, int c) {
   cd.g = h->g;
   cd.w = h->w;
   cd.open = h->open;
+  cd.quad = h->quad;
+  cd.t = h->t;
+  cd.source = h->cfg.source;
   cd.Q = h->Q; cd.QS = h->QS; cd.BASE = h->BASE; cd.RHS0 = h->RHS0; cd.RHS = h->RHS;
   cd.MOM0 = h->MOM0; cd.MOM = h->MOM;
   cd.diag = b->d_diag + c;
@@ -1481,8 +1491,6 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
     if (cfgs[c].precision != cfgs[0].precision)
       return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same precision");
   for (int c = 0; c < ncases; c++) {
-    if (cfgs[c].source != HWENO_SOURCE_NONE)
-      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: the batched kernels run without a source term");
     if (cfgs[c].scheme != cfgs[0].scheme)
       return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same scheme");
     if (cfgs[c].scheme == HWENO_SCHEME_DR && cfgs[c].precision != HWENO_FP64)
@@ -1500,6 +1508,8 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   b->mixed = cfgs[0].precision == HWENO_MIXED;
   b->dr = cfgs[0].scheme == HWENO_SCHEME_DR;
   b->lin = cfgs[0].linear_grad != 0;
+  for (int c = 0; c < ncases; c++)
+    if (cfgs[c].source != HWENO_SOURCE_NONE) b->source = 1;
   b->st = (cudaStream_t)stream;
   if (!b->st) {  // graphs cannot be captured on the legacy default stream
     if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {

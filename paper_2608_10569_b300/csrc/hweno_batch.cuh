@@ -4,6 +4,7 @@
 // cover that kernel's launch region.  The per-cell work is the single-grid bodies.
 #pragma once
 #include "hweno_mixed.cuh"
+#include "hweno_source.cuh"
 
 namespace hw {
 
@@ -18,6 +19,10 @@ struct CaseDev {
   int active;                  // 0: the case does no work in this launch
   int pad;
   Open open;                   // prescribed states of the case's inflow faces
+  Quad4 quad;                  // the source term's Gauss rule
+  double t;                    // the case's time at the start of the step
+  int source;                  // HWENO_SOURCE_* of the case
+  int pad2;
 };
 
 // work list of one kernel: case c owns items [start[c], start[c+1]); its tiles are
@@ -125,6 +130,16 @@ __global__ void __launch_bounds__(128) kb_assemble(const CaseDev* __restrict__ c
   double* rhs = which == 0 ? cd.RHS0 : cd.RHS;
   if (MIXED) assemble_mixed_body(cg, cw, rhs, cd.diag, gx, gy);
   else assemble_body<double>(cg, cw, rhs, cd.diag, gx, gy);
+  HW_BATCH_END
+}
+
+// Example 5.2's manufactured source of the cases that have it, added to the residual at
+// the stage time t + cst * dt (dt of the current attempt, read on the device)
+__global__ void __launch_bounds__(128) kb_source(const CaseDev* __restrict__ cases, TileList L, int ncase,
+                                                 int which, double cst) {
+  HW_BATCH_LOOP(L, ncase)
+  if (cd.source == HWENO_SOURCE_MMS52)
+    source_body(cg, cd.quad, cd.t, cst, cd.diag, which == 0 ? cd.RHS0 : cd.RHS, gx, gy);
   HW_BATCH_END
 }
 

@@ -101,16 +101,13 @@ def test_mixed_precision_with_source():
     assert rel_linf(g["vhat"], o["vhat"], state_scale(q)) <= 1e-6
 
 
-def test_gr_only_entry_points_reject_a_source():
+def test_the_adjoint_rejects_a_source():
     case, q = I.manufactured(16, 0.0)
     s = hweno.Solver(case.params())
     with pytest.raises(hweno.HwenoError) as e:
         s.adjoint_init()
     assert e.value.code == hweno.HWENO_ERR_ARG
     s.close()
-    with pytest.raises(hweno.HwenoError) as e:
-        hweno.Batch([case.params()], precision="fp64")
-    assert e.value.code == hweno.HWENO_ERR_ARG
 
 
 def _table_5_2_gr():

@@ -1,9 +1,9 @@
-"""GPU parity of HWENO-DR and of the linear-gradient ablation in the batch
-(hweno_batch_init with HWENO_SCHEME_DR or linear_grad cases): the batched kernels run
-the single-grid bodies, so a batch must give the handles' states (to 1e-13 of the state
-scale in FP64, 1e-6 mixed: the bodies are inlined into other kernels, whose multiply-add
-contractions may differ) and the oracle's DR step to 1e-12.  Collected last, so that a
-failure here cannot stop the other files under -x.
+"""GPU parity of HWENO-DR, of the linear-gradient ablation and of Example 5.2's source in
+the batch (hweno_batch_init with such cases): the batched kernels run the single-grid
+bodies, so a batch must give the handles' states (to 1e-13 of the state scale in FP64,
+1e-6 mixed: the bodies are inlined into other kernels, whose multiply-add contractions
+may differ) and the oracle's steps to 1e-12.  Collected last, so that a failure here
+cannot stop the other files under -x.
 """
 import numpy as np
 import pytest
@@ -89,4 +89,42 @@ def test_linear_gradient_batch_matches_handles(precision, bound):
         scale = np.abs(q[:4]).reshape(4, -1).max(1)
         err = max(np.abs(got[j] - ref[j]).max() / max(np.abs(ref[j]).max(), scale[j % 4]) for j in range(12))
         assert err <= bound, (k, err)
+    b.close()
+
+
+def test_source_batch_matches_handles_and_the_oracle():
+    """Example 5.2's source in a batch, with a case on a shifted domain and one without a
+    source: three steps from t = 0.02 against source handles (the stage times t, t + dt,
+    t + dt/2 with each case's own dt), and the first step against the oracle's"""
+    t0 = 0.02
+    c1, q1 = I.manufactured(24, t0)
+    c2 = I.Case("manufactured_shifted_20", 20, 20, 0.3, 1.3, -0.4, 0.6, 1.4, 0.72, 100.0, source=1)
+    q2 = I.cell_moments(c2, lambda x, y: I.manufactured_prim(x, y, t0, c2.gamma))
+    c3, q3 = I.random_smooth(16, 16, seed=1)
+    cases = [(c1, q1), (c2, q2), (c3, q3)]
+    stream = torch.cuda.Stream()
+    b = hweno.Batch([c.params() for c, _ in cases], precision="fp64", stream=stream)
+    for k, (_, q) in enumerate(cases):
+        b.cases[k].set_state(q.copy())
+        b.cases[k].set_time(t0)
+    b.step(1)
+    first = [b.cases[k].get_state(np.zeros_like(q)) for k, (_, q) in enumerate(cases)]
+    dts = [b.cases[k].diag()["dt_last"] for k in range(3)]
+    for _ in range(2):
+        b.step(1)
+    for k, (case, q) in enumerate(cases):
+        qo, st = O.step(O.make_cfg(**case.params()), q, t=t0, dt_fixed=dts[k])
+        scale = np.abs(q[:4]).reshape(4, -1).max(1)
+        err = max(np.abs(first[k][j] - qo[j]).max() / max(np.abs(qo[j]).max(), scale[j % 4]) for j in range(12))
+        assert st["status"] == 0 and err <= 1e-12, (k, err)
+        s = hweno.Solver(case.params(), stream=stream)
+        s.set_state(q.copy())
+        s.set_time(t0)
+        for _ in range(3):
+            s.step()
+        ref = s.get_state().cpu().numpy()
+        s.close()
+        got = b.cases[k].get_state(np.zeros_like(q))
+        err = max(np.abs(got[j] - ref[j]).max() / max(np.abs(ref[j]).max(), scale[j % 4]) for j in range(12))
+        assert err <= 1e-13, (k, err)
     b.close()
