@@ -1229,6 +1229,12 @@ double or_theta_root_export(const double* ub, const double* uq, double eps, doub
     return or_theta_root(ub, uq, eps, g);
 }
 
+/* PP wave-speed bound of Eq. (3.3) at one face-point state s (conserved) with the
+ * gradients gr = (u_x, u_y, v_x, v_y, e_x, e_y), for the positivity pin */
+double or_wave_bound_export(const or_cfg* c, int dir, const double* s, const double* gr) {
+    return or_wave_bound(c, dir, s, gr);
+}
+
 /* eigenvector pair for pins */
 int or_eigen_export(const double* ub, double g, int dir, double* L, double* R) {
     double l[4][4], r[4][4];

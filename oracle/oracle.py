@@ -101,8 +101,25 @@ def _load():
             lib.or_theta_root_export.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double]
             lib.or_theta_root_export.restype = ctypes.c_double
             lib.or_eigen_export.argtypes = [dp, ctypes.c_double, ctypes.c_int, dp, dp]
+            _bind_wave_bound(lib)
             _lib = lib
     return _lib
+
+
+def _bind_wave_bound(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.or_wave_bound_export.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int, dp, dp]
+    lib.or_wave_bound_export.restype = ctypes.c_double
+
+
+def wave_bound(cfg, direction, s, gr, lib=None):
+    """max(|u_n| + c, PP wave-speed bound of Eq. (3.3)) at one face-point state: s the
+    conserved state (4), gr = (u_x, u_y, v_x, v_y, e_x, e_y); lib: a library built from
+    this source (default: the oracle's own)"""
+    lib = lib or _load()
+    s = np.ascontiguousarray(s, dtype=float)
+    gr = np.ascontiguousarray(gr, dtype=float)
+    return lib.or_wave_bound_export(ctypes.byref(cfg), int(direction), _ptr(s), _ptr(gr))
 
 
 def _ptr(a):

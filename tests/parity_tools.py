@@ -1,8 +1,10 @@
 """Tolerance helpers shared by the parity tests (CPU and GPU): the scales that relative
-errors divide by, and the conditioning bound of the characteristic projection."""
+errors divide by, the conditioning bound of the characteristic projection, the
+residual parity cases, and the oracle's own rounding floor on them."""
 import numpy as np
 
 from oracle import oracle as O
+from paper_2608_10569_b300 import inputs as I
 
 RES_TOL = 1e-12
 
@@ -86,3 +88,47 @@ def rel_l1(a, b):
         d = np.abs(a[k] - b[k]).sum()
         worst = max(worst, d / s if s > 0 else d)
     return worst
+
+
+# the residual parity cases: periodic, every wall type, ragged grids, the minimum grid
+RESIDUAL_CASES = {
+    "smooth_periodic_64": lambda: I.smooth_periodic(64),
+    "rough_periodic_40x36": lambda: I.random_rough(40, 36, seed=1),
+    "smooth_walls_37x29": lambda: I.random_smooth(37, 29, seed=2, bc=("noslip", "slip", "symmetry", "noslip")),
+    "rough_walls_45x21": lambda: I.random_rough(45, 21, seed=3, bc=("noslip", "noslip", "noslip", "symmetry")),
+    "shock_tube_64x32": lambda: I.shock_tube(64, 32),
+    "taylor_green_48": lambda: I.taylor_green(48, 0.4, 300.0, 1 / 1.4, rho_pert=1e-2),
+    "minimum_grid_4x4": lambda: I.random_smooth(4, 4, seed=5),
+    "thin_grid_5x70": lambda: I.random_smooth(5, 70, seed=6, bc=("slip", "slip", "periodic", "periodic")),
+}
+
+
+def ulp_perturbed(q, seed):
+    """every value moved by one unit in the last place, up or down at random"""
+    rng = np.random.default_rng(seed)
+    return np.nextafter(q, rng.choice([-np.inf, np.inf], size=q.shape))
+
+
+def far_from(mask, r):
+    """cells whose (2r+1)^2 neighbourhood (periodic) holds no True of mask"""
+    out = mask.copy()
+    for dj in range(-r, r + 1):
+        for di in range(-r, r + 1):
+            out |= np.roll(np.roll(mask, dj, 0), di, 1)
+    return ~out
+
+
+def oracle_floor(case, q, seeds=(0, 1, 2), mask=None):
+    """the oracle's residual against itself on one-ulp perturbations of its input: the
+    largest plane-relative and flux-scale-relative L-infinity differences over the seeds.
+    Two correct implementations that round differently cannot be expected to agree
+    more closely than this."""
+    cfg = O.make_cfg(**case.params())
+    r0 = O.residual(cfg, q)["rhs"]
+    fs = flux_scale(case, q)
+    plane = flux = 0.0
+    for sd in seeds:
+        r1 = O.residual(cfg, ulp_perturbed(q, sd))["rhs"]
+        plane = max(plane, rel_linf(r1, r0, None, mask))
+        flux = max(flux, rel_linf(r1, r0, fs, mask))
+    return plane, flux
