@@ -11,16 +11,24 @@ The metric is Gcell-RK-stage/s = cells x stages / seconds, summed over ranks.
   e2e       the same steps through the C ABI with host buffers: each step loads
             the state from pinned host memory and reads the new state back
   mixed     the FP32-reconstruction path on the same steps, with its L1 error
-            against the FP64 path after the K steps
+            against the FP64 path after the K steps and its roofline
   dr        the paper's comparison scheme HWENO-DR (differentiated candidates for
             the viscous gradients) on the same workload and steps, FP64
-  roofline  the dominant kernel's algorithmic FP64 flops per launch / its mean
-            event-timed duration, against the FP64 FMA peak measured live
+  roofline  the dominant kernel's algorithmic FP64 flops per launch (the oracle's
+            operation count per interior cell) / its mean event-timed duration,
+            against the FP64 FMA peak measured live; the whole step on the same basis
+  adjoint   config 5: the gradient of a final-time misfit through 200 steps of the
+            512^2 Taylor-Green flow, checkpoints every 20; backward / forward time and
+            central differences on 16 seeded directions
+  ensemble  config 4: 64 Taylor-Green cases (sides 128-1024) in batched mixed steps,
+            with the worst case's error against FP64
+  colliding_streams  config 3: the 2048^2 near-vacuum colliding streams, FP64 and
+            mixed
   cpu_baseline  the FP64 CPU oracle on the host cores, one SSP-RK3 step of the
             same workload (rank 0, N = 1 only)
 
 --impl reference times the CPU oracle (the only other implementation of the
-method) on a bounded 256 x 128 version of the workload per step.
+method) on full-size steps of the same workload, as many as fit a bounded time.
 
 Multi-GPU: independent replicas, one per rank (torchrun), no collective in the
 data path; the barrier and max-over-ranks timing use torch.distributed.
@@ -43,24 +51,54 @@ sys.path.insert(0, ROOT)
 METRIC = "Gcell-RK-stage/s"
 WORKLOAD = "viscous shock tube 1024x512, no-slip walls + symmetry, Re 1000, Pr 0.73, SSP-RK3 under the CFL/viscous step rule"
 
-# FP64 flops per cell of one launch of the two reconstruction kernels: executed
-# DADD + DMUL + 2 DFMA counted by ncu on the 256x128 shock tube, divided by the
-# cells the launch processes (profiles/fp64_op_counts_shock_tube_256x128.md).
-# `achieved` multiplies them by the INTERIOR cells only, so the halo ring each launch
-# also reconstructs (interior grown by 3, resp. 1) is not credited.
-FLOPS_PER_CELL_FP64 = {
-    "cons_recon": 5011.0,
-    "grad_recon": 3108.0,
+# Algorithmic floating-point work per interior cell and RK stage, by phase of the
+# spatial operator: the distinct state-dependent additions, multiplications, divisions
+# and square roots of the FP64 oracle's own algebra (each candidate evaluated at each
+# point and combined as Eq. (3.4) prints), counted by the oracle's operation-counting
+# build on a periodic grid, where no halo is counted.  The CPU suite checks these numbers
+# against that build.  A kernel whose algebra needs fewer operations than the oracle's
+# (the GPU combines the candidates' coefficients before evaluating, and projects p0's
+# coefficients instead of the data) can reach a fraction above 1 on this basis.
+ALG_FLOPS = {
+    "gr": {"traces": 8126.0, "limiter": 285.0, "weak_moments": 351.0, "gradients": 6516.0,
+           "face_fluxes": 846.0, "balances": 736.0, "alpha": 12.0, "stage_update": 151.0 / 3.0},
+    "dr": {"traces": 12905.0, "limiter": 285.0, "weak_moments": 0.0, "gradients": 609.0,
+           "face_fluxes": 846.0, "balances": 736.0, "alpha": 12.0, "stage_update": 151.0 / 3.0},
 }
+# the phases each kernel of the FP64 GR operator performs
+KERNEL_PHASES = {"cons_recon": ("traces", "limiter"), "grad_recon": ("gradients",),
+                 "flux": ("face_fluxes", "alpha"), "assemble": ("balances",)}
+# phases the mixed path keeps in FP64: the limiter's checks and theta solve, the stage update
+MIXED_FP64_PHASES = ("limiter", "stage_update")
 
-# the same for HWENO-DR's gradient kernel k_dr, profiled under the "grad_recon" slot
-# (profiles/dr_kernels_shock_tube_256x128.md)
-FLOPS_PER_CELL_FP64_DR = {"grad_recon": 2782.0}
+# FP64 flops the kernels themselves execute per processed cell (DADD + DMUL + 2 DFMA,
+# counted by ncu on the 256x128 shock tube): the pipe-efficiency view beside the
+# algorithmic one
+EXECUTED_FLOPS_PER_CELL = {"cons_recon": 5011.0, "grad_recon": 3108.0}
+
+# algorithmic bytes per cell-stage of the unfused residual and stage update: the
+# residual reads 12 state values and writes 12 residual values and 8 modified moments,
+# the stage update reads 12 stage, 12 base and 20 residual/moment values and writes 12
+ALG_BYTES_PER_CELL_STAGE = 8 * ((12 + 20) + (12 + 12 + 20 + 12))
 
 # DRAM bytes of one cons_recon (k_cons<double>) launch on the 1024x512 shock tube,
-# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this build
-# (profiles/k_cons_traffic_shock_tube_1024x512.md); valid for that grid only
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the current
+# k_cons; valid for that grid only
 K_CONS_TRAFFIC = {(1024, 512): 56465152 + 534104832}
+
+
+def MEASURED_HBM_GBS():
+    """the HBM copy bandwidth of MEASURED_PEAKS.json (written on the B300s), or None"""
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return None
+
+
+def alg_flops(scheme, phases=None):
+    f = ALG_FLOPS[scheme]
+    return sum(f[p] for p in (phases or f))
 
 
 def k_cons_algorithmic_bytes(nx, ny):
@@ -82,6 +120,10 @@ def parse():
     ap.add_argument("--adj-n", type=int, default=512)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dr", action="store_true")
+    ap.add_argument("--fd-plain", action="store_true",
+                    help="adjoint: one central difference per direction instead of the Richardson pair")
+    ap.add_argument("--no-metric-children", action="store_true",
+                    help="skip the child processes that measure the adjoint, the ensemble and the colliding streams")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the child process that measures the 1D solver and the open faces")
     ap.add_argument("--mms-meshes", default="40,80,120,160")
@@ -239,32 +281,57 @@ def state_errors(q, ref, gamma):
 
 
 def cpu_threads():
+    """the host threads the oracle's OpenMP loops use: OMP_NUM_THREADS, else the CPUs
+    this process may run on"""
     n = os.environ.get("OMP_NUM_THREADS")
-    return int(n) if n else os.cpu_count()
+    return int(n) if n else len(os.sched_getaffinity(0))
+
+
+REFERENCE_BUDGET_S = 180.0
+
+
+def workload_config(nx, ny, ws):
+    """the static description of the headline workload, the same in both arms"""
+    return {"workload": WORKLOAD, "nx": nx, "ny": ny, "cells": nx * ny, "stages_per_step": 3,
+            "l2": "inputs larger than L2 (~1.5 GB state and scratch per step)",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
 
 
 def run_reference(args):
+    """the oracle on the host cores, on the headline's own workload: --warmup and --steps
+    SSP-RK3 steps, each of the full 1024x512 shock tube when all of them fit
+    REFERENCE_BUDGET_S at the first step's pace, else each of the largest box of its
+    cells (the domain halved in both directions until they fit) that does"""
     ws, rank, _ = dist_setup(args)
     if rank != 0:
         return
     from paper_2608_10569_b300 import inputs as I
-    case, q = I.shock_tube(256, 128)
     from oracle import oracle as O
     O.build()
-    cfg = O.make_cfg(**case.params())
-    qq = q
-    for _ in range(args.warmup):
+    nx, ny = args.nx, args.ny
+    total = args.steps + args.warmup
+    while True:
+        case, q = I.shock_tube(nx, ny)
+        cfg = O.make_cfg(**case.params())
+        t0 = time.perf_counter()
+        qq, _ = O.step(cfg, q)
+        first = time.perf_counter() - t0
+        if first * total <= REFERENCE_BUDGET_S or nx <= 64:
+            break
+        nx, ny = nx // 2, ny // 2
+    for _ in range(args.warmup - 1):
         qq, _ = O.step(cfg, qq)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         qq, _ = O.step(cfg, qq)
     el = time.perf_counter() - t0
-    val = case.nx * case.ny * 3.0 * args.steps / el / 1e9
-    sample = "each step: one SSP-RK3 step of the shock tube at 256x128 (1/16 of the cells)"
+    val = nx * ny * 3.0 * args.steps / el / 1e9
+    sample = "each step: one SSP-RK3 step of the shock tube at %dx%d (%s)" % (
+        nx, ny, "the full workload" if nx == args.nx else "%d/%d of its cells" % (nx * ny, args.nx * args.ny))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "256x128"},
+            "data": "synthetic", "config": workload_config(args.nx, args.ny, ws),
             "cpu_baseline": {"value": val, "unit": METRIC, "cores": cpu_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -328,7 +395,7 @@ def run_ensemble(args):
     for case, q in ens:
         if case.nx not in seen:
             seen.add(case.nx)
-            acc.append(dict(mixed_error(case.params(), q), side=case.nx))
+            acc.append(dict(mixed_error(case.params(), q, nsteps=args.steps), side=case.nx))
     errs = [a for a in acc if "error" not in a]
     line = {"metric": METRIC, "value": cells * 3.0 * args.steps / (ms * 1e-3) / 1e9, "unit": METRIC,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -340,7 +407,8 @@ def run_ensemble(args):
             "pp_active_cell_stages": pp,
             "accuracy": {"rel_l1_rho_vs_fp64": max(a["rel_l1_rho_vs_fp64"] for a in errs) if errs else None,
                          "rel_linf_rho_vs_fp64": max(a["rel_linf_rho_vs_fp64"] for a in errs) if errs else None,
-                         "sample": "one case of each side, mixed vs FP64 over 10 steps at the FP64 step sizes",
+                         "sample": "one case of each side, mixed vs FP64 over the run's steps at the FP64 "
+                                   "step sizes",
                          "cases": acc}}
     print(json.dumps(line), flush=True)
 
@@ -400,6 +468,8 @@ def run_adjoint(args):
 
     def rich(f, h):  # central differences at h and h/2, Richardson-extrapolated
         d1 = dJ(f(h), f(-h)) / (2 * h)
+        if args.fd_plain:
+            return d1
         d2 = dJ(f(h / 2), f(-h / 2)) / h
         return (4 * d2 - d1) / 3
 
@@ -417,6 +487,9 @@ def run_adjoint(args):
             "forward_s": t1 - t0, "backward_s": t2 - t1, "value": (t2 - t1) / (t1 - t0), "unit": "ratio",
             "higher_is_better": False, "dtype": "f64", "J": float(loss),
             "fd_directions": args.fd_directions, "fd_max_rel_err": max(errs) if errs else None,
+            "fd_rel_errs": [float(e) for e in errs],
+            "fd": "central differences at h = 1e-7 of the state scale per plane%s, the forward's step sizes "
+                  "frozen" % ("" if args.fd_plain else ", Richardson-extrapolated with h/2"),
             "dJ_dmu": gmu, "mu_fd_rel_err": abs(gmu - fdmu) / abs(fdmu)}
     print(json.dumps(line), flush=True)
 
@@ -617,10 +690,10 @@ def run_next(args):
     print(json.dumps(out), flush=True)
 
 
-def next_rows_child(args):
-    """run_next in a child process (its own CUDA context), bounded in time: a failure
-    there is reported in the line, never taken into the headline measurement"""
-    cmd = [sys.executable, os.path.join(HERE, "bench.py"), "--workload", "next", "--steps", "3", "--warmup", "1"]
+def child_line(argv, timeout):
+    """bench.py with argv in a child process (its own CUDA context), bounded in time: its
+    last JSON line, or the error; a failure there never reaches the headline measurement"""
+    cmd = [sys.executable, os.path.join(HERE, "bench.py")] + list(argv)
 
     def last_line(text):
         for line in reversed((text or "").strip().splitlines()):
@@ -631,16 +704,34 @@ def next_rows_child(args):
         return {}
 
     try:
-        r = subprocess.run(cmd, capture_output=True, text=True, timeout=360)
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout)
         out = last_line(r.stdout)
         if r.returncode != 0:
             out["error"] = "exit %d: %s" % (r.returncode, r.stderr.strip()[-300:])
         return out
     except subprocess.TimeoutExpired as e:
         so = e.stdout.decode() if isinstance(e.stdout, bytes) else e.stdout
-        return dict(last_line(so), error="time limit of 360 s reached; the rows above are those completed")
+        return dict(last_line(so), error="time limit of %d s reached; the rows above are those completed" % timeout)
     except Exception as e:
         return {"error": str(e)[:300]}
+
+
+def next_rows_child(args):
+    """run_next in a child process, bounded to 360 s"""
+    return child_line(["--workload", "next", "--steps", "3", "--warmup", "1"], 360)
+
+
+def metric_children(args):
+    """the rest of the metric, each in a child process: config 5's adjoint (200 steps,
+    checkpoints every 20, forward and backward times, central differences on 16 seeded
+    directions), config 4's ensemble (64 cases, 100 batched mixed steps, the worst case
+    against FP64) and config 3's colliding streams (2048^2)"""
+    return {
+        "adjoint": child_line(["--workload", "adjoint", "--steps", "200", "--warmup", "2", "--fd-directions", "16",
+                               "--fd-plain"], 420),
+        "ensemble": child_line(["--workload", "ensemble", "--steps", "100", "--warmup", "3"], 300),
+        "colliding_streams": child_line(["--workload", "colliding_streams", "--steps", "3", "--warmup", "1"], 300),
+    }
 
 
 def run_single(args):
@@ -761,21 +852,34 @@ def main():
     t_reached = s.diag()["t"]
     pp_percent = pp_pct(s.diag())
 
-    # dominant kernel of the operator and its roofline against the FP64 FMA peak
+    # dominant kernel of the operator and its roofline against the FP64 FMA peak, on the
+    # algorithmic flop count; the whole step on the same basis
     dom = max((k for k in prof if k != "rk_update"), key=lambda k: prof[k][1])
     n_l, tot_ms = prof[dom]
-    fpc = FLOPS_PER_CELL_FP64.get(dom)
     roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak64,
             "peak_source": "measured FP64 FMA peak (hweno_measure_peak, this run)",
+            "flops_basis": "algorithmic: the FP64 oracle's distinct operations per interior cell "
+                           "(its operation-counting build), not the kernel's own count",
             "launches": n_l, "mean_launch_ms": tot_ms / max(n_l, 1),
             "share_of_step": tot_ms / ms if ms > 0 else None,
             "traffic": K_CONS_TRAFFIC.get((case.nx, case.ny)) if dom == "cons_recon" else None,
             "algorithmic_bytes": k_cons_algorithmic_bytes(case.nx, case.ny) if dom == "cons_recon" else None}
-    if fpc:
-        achieved = fpc * cells / (tot_ms / n_l * 1e-3) / 1e12
+    if dom in KERNEL_PHASES and n_l:
+        fpc = alg_flops("gr", KERNEL_PHASES[dom])
+        launch_s = tot_ms / n_l * 1e-3
+        achieved = fpc * cells / launch_s / 1e12
         roof.update({"achieved": achieved, "frac": achieved / peak64, "flops_per_cell": fpc})
+        if dom in EXECUTED_FLOPS_PER_CELL:
+            ex = EXECUTED_FLOPS_PER_CELL[dom] * cells / launch_s / 1e12
+            roof.update({"executed_flops_per_cell": EXECUTED_FLOPS_PER_CELL[dom], "executed_achieved": ex,
+                         "executed_frac": ex / peak64})
     else:
         roof.update({"achieved": None, "frac": None, "flops_per_cell": None})
+    step_flops = alg_flops("gr")
+    step_achieved = step_flops * cells * stages / (ms * 1e-3) / 1e12
+    roof["step"] = {"flops_per_cell_stage": step_flops, "achieved": step_achieved, "frac": step_achieved / peak64,
+                    "per_kernel_frac": {k: alg_flops("gr", ph) * cells / (prof[k][1] / prof[k][0] * 1e-3) / 1e12
+                                        / peak64 for k, ph in KERNEL_PHASES.items() if prof.get(k, (0,))[0]}}
     kernel_ms = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}
 
     # ---- end to end through the C ABI with host buffers ---------------------------
@@ -827,8 +931,24 @@ def main():
         s64.close()
         l1 = float(np.abs(qm[0] - q64[0]).sum() / np.abs(q64[0]).sum())
         linf = float(np.abs(qm[0] - q64[0]).max() / np.abs(q64[0]).max())
+        # the mixed step's roofline on the same algorithmic basis: the FP32 phases against
+        # the measured FP32 FMA peak, the FP64 phases against the FP64 one, the unfused
+        # bytes against the HBM bandwidth; the slowest bounds the cell-stage rate
+        f64 = alg_flops("gr", MIXED_FP64_PHASES)
+        f32 = alg_flops("gr") - f64
+        hbm = MEASURED_HBM_GBS()
+        bound_rate = min(peak32 * 1e12 / f32, peak64 * 1e12 / f64,
+                         hbm * 1e9 / ALG_BYTES_PER_CELL_STAGE if hbm else float("inf"))
+        mrate = cells * stages / (mms * 1e-3)
+        mixed_roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak32,
+                      "peak_source": "measured FP32 FMA peak (hweno_measure_peak, this run)",
+                      "fp32_flops_per_cell_stage": f32, "fp64_flops_per_cell_stage": f64,
+                      "achieved": f32 * mrate / 1e12, "frac": f32 * mrate / 1e12 / peak32,
+                      "fp64_achieved": f64 * mrate / 1e12, "fp64_frac": f64 * mrate / 1e12 / peak64,
+                      "bytes_per_cell_stage": ALG_BYTES_PER_CELL_STAGE, "hbm_peak_gbs": hbm,
+                      "rate_bound": bound_rate / 1e9, "frac_of_rate_bound": mrate / bound_rate}
         mixed = {"value": replica_value(ws, cells, stages, mms), "unit": METRIC,
-                 "ms_per_step": mms / args.steps, "fp32_peak_tflops": peak32,
+                 "ms_per_step": mms / args.steps, "fp32_peak_tflops": peak32, "roofline": mixed_roof,
                  "rel_l1_rho_vs_fp64": l1, "rel_linf_rho_vs_fp64": linf,
                  "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in mprof.items()}}
         m.close()
@@ -861,13 +981,10 @@ def main():
               "gpu_launches": dlaunch, "t_reached": d.diag()["t"], "t_reached_gr": t_reached,
               "rel_l1_rho_vs_gr": float(np.abs(qdr[0] - q_fp64[0]).sum() / np.abs(q_fp64[0]).sum()),
               "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in dprof.items()}}
-        fpc = FLOPS_PER_CELL_FP64_DR.get("grad_recon")
-        n_l, tot_ms = dprof["grad_recon"]
-        if fpc and n_l:
-            achieved = fpc * cells / (tot_ms / n_l * 1e-3) / 1e12
-            dr["k_dr_roofline"] = {"bound": "alu", "kernel": "k_dr", "unit": "TFLOP/s", "peak": peak64,
-                                   "achieved": achieved, "frac": achieved / peak64, "flops_per_cell": fpc,
-                                   "mean_launch_ms": tot_ms / n_l}
+        dstep = alg_flops("dr")
+        dach = dstep * cells * stages / (dms * 1e-3) / 1e12
+        dr["step_roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak64, "flops_per_cell_stage": dstep,
+                               "achieved": dach, "frac": dach / peak64}
         d.close()
 
     # ---- CPU baseline: the oracle on the host cores --------------------------------
@@ -887,7 +1004,10 @@ def main():
             parity[prec] = state_errors(sv.get_state().cpu().numpy(), q_or, case.gamma)
             sv.close()
 
-    # ---- the widened rows (1D solver, open faces), in a child process ------------------
+    # ---- the rest of the metric and the widened rows, in child processes -------------
+    children = {}
+    if rank == 0 and ws == 1 and not args.no_metric_children:
+        children = metric_children(args)
     next_rows = None
     if rank == 0 and ws == 1 and not args.no_next:
         next_rows = next_rows_child(args)
@@ -896,12 +1016,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny, "cells": cells,
-                           "stages_per_step": 3, "l2": "inputs larger than L2 (~1.5 GB state and scratch per step)",
-                           "parallelism": "replicas" if ws > 1 else "single GPU",
-                           "t_reached": t_reached, "rejected_steps": rejected, "pp_percent": pp_percent},
+                "config": workload_config(case.nx, case.ny, ws),
+                "run": {"t_reached": t_reached, "rejected_steps": rejected, "pp_percent": pp_percent},
                 "roofline": roof, "cpu_baseline": cpu, "parity_vs_oracle": parity, "e2e": e2e, "mixed": mixed,
-                "dr": dr, "next_rows": next_rows,
+                "dr": dr, **children, "next_rows": next_rows,
                 "clocks": clk, "gpu_launches": launches, "kernel_ms": kernel_ms}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -28,9 +28,12 @@ _HDR = os.path.join(_HERE, "oracle_tables.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _JVP_SRC = os.path.join(_HERE, "hweno_oracle_jvp.cpp")
 _JVP_LIB = os.path.join(_HERE, "liboracle_jvp.so")
+_CNT_SRC = os.path.join(_HERE, "hweno_oracle_count.cpp")
+_CNT_LIB = os.path.join(_HERE, "liboracle_count.so")
 _lock = threading.Lock()
 _lib = None
 _jvp = None
+_cnt = None
 
 BC = {"periodic": 0, "noslip": 1, "symmetry": 2, "slip": 3, "inflow": 4, "outflow": 5}
 # viscous gradients: HWENO-GR (weak-derivative moments) or HWENO-DR (differentiated
@@ -75,6 +78,15 @@ def build(force=False):
                "-std=c++17", "-fpermissive", "-w", "-o", _JVP_LIB + ".tmp", _JVP_SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_JVP_LIB + ".tmp", _JVP_LIB)
+    stale = (not os.path.exists(_CNT_LIB) or
+             os.path.getmtime(_CNT_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR),
+                                               os.path.getmtime(_CNT_SRC)))
+    if force or stale:
+        # serial (no OpenMP): the counters are plain globals
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-std=c++17", "-fpermissive", "-w", "-o", _CNT_LIB + ".tmp", _CNT_SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_CNT_LIB + ".tmp", _CNT_LIB)
     return _LIB
 
 
@@ -450,3 +462,101 @@ def mms_source1d(cfg, x, t):
     S = np.zeros(3)
     lib.or1_mms_source_export(ctypes.byref(cfg), float(x), float(t), _ptr(S))
     return S
+
+
+# ---------------------------------------------------------------------------
+# operation counts (hweno_oracle_count.cpp): the oracle's state-dependent, non-trivial
+# floating-point operations, by kind
+OP_KINDS = ("add", "mul", "div", "sqrt", "trans")
+PHASES = ("traces", "limiter", "weak_moments", "gradients", "face_fluxes", "balances", "alpha")
+
+
+def _load_cnt():
+    global _cnt
+    with _lock:
+        if _cnt is None:
+            build()
+            lib = ctypes.CDLL(_CNT_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lp = ctypes.POINTER(ctypes.c_longlong)
+            lib.or_count_phases.argtypes = [ctypes.POINTER(_Cfg), dp, lp]
+            lib.or_count_call.argtypes = [ctypes.POINTER(_Cfg), dp, ctypes.c_int, ctypes.c_double, lp]
+            lib.or_count_theta_root.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, lp]
+            lib.or_count_theta_root.restype = ctypes.c_double
+            lib.or_count_hweno.argtypes = [dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, lp]
+            _cnt = lib
+    return _cnt
+
+
+def _counts(a):
+    return dict(zip(OP_KINDS, (int(x) for x in a)))
+
+
+def op_count_phases(cfg, q):
+    """{phase: {kind: count}} of one residual (phases PHASES), each distinct computation
+    counted once, where it first occurs"""
+    lib = _load_cnt()
+    q = _state(cfg, q)
+    out = np.zeros(len(PHASES) * len(OP_KINDS), dtype=np.int64)
+    if lib.or_count_phases(ctypes.byref(cfg), _ptr(q), out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))):
+        raise RuntimeError("or_count_phases failed")
+    return {p: _counts(out[k * len(OP_KINDS):(k + 1) * len(OP_KINDS)]) for k, p in enumerate(PHASES)}
+
+
+def op_count_call(cfg, q, what, dt=0.0):
+    """counts of a whole call: what = "residual" (with diagnostics), "residual_nodiag",
+    or "step" (one SSP-RK3 step of size dt)"""
+    lib = _load_cnt()
+    q = _state(cfg, q)
+    out = np.zeros(len(OP_KINDS), dtype=np.int64)
+    code = {"residual": 0, "residual_nodiag": 1, "step": 2}[what]
+    if lib.or_count_call(ctypes.byref(cfg), _ptr(q), code, float(dt),
+                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))):
+        raise RuntimeError("or_count_call failed")
+    return _counts(out)
+
+
+def op_count_theta_root(ub, uq, eps, gamma):
+    lib = _load_cnt()
+    ub = np.ascontiguousarray(ub, dtype=float)
+    uq = np.ascontiguousarray(uq, dtype=float)
+    out = np.zeros(len(OP_KINDS), dtype=np.int64)
+    t = lib.or_count_theta_root(_ptr(ub), _ptr(uq), float(eps), float(gamma),
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    return t, _counts(out)
+
+
+def op_count_hweno(d17, points, eps=1e-8, linear=False):
+    """(build counts, evaluation counts) of one scalar reconstruction and its values at
+    the points [(xi, eta), ...]"""
+    lib = _load_cnt()
+    d = np.ascontiguousarray(d17, dtype=float)
+    pts = np.asarray(points, dtype=float).reshape(-1, 2)
+    xi = np.ascontiguousarray(pts[:, 0])
+    eta = np.ascontiguousarray(pts[:, 1])
+    out = np.zeros(2 * len(OP_KINDS), dtype=np.int64)
+    lib.or_count_hweno(_ptr(d), float(eps), int(bool(linear)), len(pts), _ptr(xi), _ptr(eta),
+                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    return _counts(out[:len(OP_KINDS)]), _counts(out[len(OP_KINDS):])
+
+
+def flops(counts):
+    """floating-point operations of a count record: additions, multiplications,
+    divisions and square roots one each (transcendentals kept apart)"""
+    return counts["add"] + counts["mul"] + counts["div"] + counts["sqrt"]
+
+
+def algorithmic_flops(cfg, q):
+    """algorithmic floating-point work of the method per cell and RK stage, by phase of
+    the spatial operator plus the stage update: the distinct state-dependent operations
+    of the oracle on the state q, on a periodic grid (every ghost cell a copy, so no halo
+    is counted; see hweno_oracle_count.cpp), divided by the number of cells.  Returns
+    {phase: flops per cell} with the phases PHASES and "stage_update" (the SSP-RK3
+    combination and the admissibility check)."""
+    assert all(b == BC["periodic"] for b in cfg.bc), "counts per cell need a periodic grid"
+    n = cfg.nx * cfg.ny
+    out = {p: flops(c) / n for p, c in op_count_phases(cfg, q).items()}
+    with_diag = flops(op_count_call(cfg, q, "residual"))
+    step = flops(op_count_call(cfg, q, "step", dt=1e-6))
+    out["stage_update"] = (step - 3 * with_diag) / (3 * n)
+    return out
