@@ -70,7 +70,13 @@ extern "C" {
 #define HWENO_FP64 0  /* everything in FP64 */
 #define HWENO_MIXED 1 /* reconstruction, weights and fluxes in FP32; the stored state,
                          the RK update, the positivity limiter's checks and theta
-                         solve, and all reductions in FP64 */
+                         solve, and all reductions in FP64.  A step or residual whose
+                         state has, in some cell, an internal energy below 1e-4 of the
+                         total (kinetic share |m|^2 / (2 rho E) above 1 - 1e-4) runs the
+                         FP64 operator instead: FP32 fluxes of E move such an internal
+                         energy by more than 6e-4 of itself per stage (hweno_diag
+                         counts these steps).  Handles only: the mixed cases of a
+                         batch always run in FP32. */
 
 /* viscous gradients */
 #define HWENO_SCHEME_GR 0 /* weak-derivative moments through the scalar HWENO (Eqs. (3.6)-(3.9)) */
@@ -137,6 +143,14 @@ typedef struct {
                                  fixed-order deterministic sum) */
     long long steps;          /* accepted steps since set_state */
     long long rejected;       /* rejected (halved) step attempts since set_state */
+    long long fp64_steps;     /* HWENO_MIXED handles: accepted steps since set_state that
+                                 ran the FP64 operator because the state's largest kinetic
+                                 share |m|^2 / (2 rho E) exceeded 1 - 1e-4 (internal
+                                 energy below 1e-4 of the total, which FP32 fluxes of E
+                                 cannot resolve); 0 for HWENO_FP64 handles */
+    double max_kinetic_share; /* HWENO_MIXED handles: that share over the cells of the
+                                 state after set_state or the last accepted step (1 for
+                                 an inadmissible cell); 0 for HWENO_FP64 handles */
 } hweno_diag;
 
 /* Fill *cfg with the paper's defaults (Sec. 5, Appendix A): periodic boxes on
@@ -254,7 +268,10 @@ int hweno_adjoint_residual(hweno_handle* h, const double* x, const double* rbar,
  * max_steps steps and, with keep_intermediates, the forward intermediates the reverse
  * reads (about 4.3 KB per padded cell and stage), so that the reverse recomputes nothing.  When those do
  * not fit in 80 % of the free device memory only the states are kept and every stage is
- * re-evaluated during the reverse.  Returns 1 if intermediates are kept, 0 if not. */
+ * re-evaluated during the reverse.  Returns 1 if intermediates are kept, 0 if not.
+ * Storage of at least max_steps steps that is already reserved serves again, unchanged
+ * (recorded steps included), when it keeps intermediates, when none are asked for, or
+ * when an earlier request for them was refused for lack of memory. */
 int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_intermediates);
 
 /* Recording for the adjoint.  With on != 0 (after hweno_adjoint_reserve), each step
@@ -303,10 +320,11 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 typedef struct hweno_batch hweno_batch;
 
 /* Create ncases solvers (cfgs[0..ncases-1], as for hweno_init, all with the same
- * precision, scheme and linear_grad; HWENO_SCHEME_DR in
+ * precision, scheme, linear_grad and max_halvings; HWENO_SCHEME_DR in
  * HWENO_FP64 only) sharing one stream; NULL stream: the batch creates its own
  * non-blocking stream (graph capture needs one).  Allocates everything.  Errors as
- * hweno_init; HWENO_ERR_ARG for cases that differ in precision or scheme. */
+ * hweno_init; HWENO_ERR_ARG for cases that differ in precision, scheme, linear_grad or
+ * max_halvings. */
 int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_batch** out);
 void hweno_batch_destroy(hweno_batch* b);
 const char* hweno_batch_last_error(const hweno_batch* b);

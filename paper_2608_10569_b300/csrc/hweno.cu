@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -78,12 +79,34 @@ __global__ void k_rk(Grid g, int stage, const double* __restrict__ qin, const do
   rk_body(g, stage, qin, mom, rhs, base, qout, diag, blockIdx.x * blockDim.x + threadIdx.x,
           blockIdx.y * blockDim.y + threadIdx.y);
 }
-// the mixed path's stage update: also the hi/lo split of the new state
+// the mixed path's stage update: also the hi/lo split of the new state and its largest
+// kinetic share
 __global__ void k_rk_split(Grid g, int stage, const double* __restrict__ qin, const double* __restrict__ mom,
                            const double* __restrict__ rhs, double* __restrict__ base, double* __restrict__ qout,
                            Diag* diag, float* __restrict__ hilo) {
-  rk_body<true>(g, stage, qin, mom, rhs, base, qout, diag, blockIdx.x * blockDim.x + threadIdx.x,
-                blockIdx.y * blockDim.y + threadIdx.y, hilo);
+  rk_body<true, true>(g, stage, qin, mom, rhs, base, qout, diag, blockIdx.x * blockDim.x + threadIdx.x,
+                      blockIdx.y * blockDim.y + threadIdx.y, hilo);
+}
+// a mixed handle's stage update on the FP64 route: the largest kinetic share, no split
+__global__ void k_rk_kef(Grid g, int stage, const double* __restrict__ qin, const double* __restrict__ mom,
+                         const double* __restrict__ rhs, double* __restrict__ base, double* __restrict__ qout,
+                         Diag* diag) {
+  rk_body<false, true>(g, stage, qin, mom, rhs, base, qout, diag, blockIdx.x * blockDim.x + threadIdx.x,
+                       blockIdx.y * blockDim.y + threadIdx.y);
+}
+// the largest kinetic share |m|^2 / (2 rho E) over the cells of q (1 where a cell is
+// inadmissible), into diag->kefrac_bits
+__global__ void k_kinetic_share(Grid g, const double* __restrict__ q, Diag* diag) {
+  const long long N = (long long)g.nx * g.ny;
+  double kef = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    const long long c = cidx(g, (int)(t % g.nx), (int)(t / g.nx));
+    const double r = q[c], m = q[g.ps + c], n = q[2 * g.ps + c], E = q[3 * g.ps + c];
+    const double rp = E * r - 0.5 * (m * m + n * n);
+    kef = fmax(kef, (r > 0.0 && rp > 0.0) ? 1.0 - rp / (E * r) : 1.0);
+  }
+  kef = warp_max(kef);
+  if (lane_id() == 0) atomic_max_pos(&diag->kefrac_bits, kef);
 }
 
 // time step of Sec. 5: dt = min(CFL h / alpha*, b Re h^2), or a forced trial
@@ -220,6 +243,12 @@ struct hweno_handle {
   double* d_red = nullptr;
   bool have_state = false, have_residual = false;
   const double* split_of = nullptr;  // mixed path: the state whose hi/lo split is current
+  // mixed path: the largest kinetic share |m|^2 / (2 rho E) over the cells of the state
+  // (measured at set_state and by every accepted step), and whether the current step
+  // or residual runs the FP64 operator because that share exceeds MIXED_MAX_KINETIC_SHARE
+  double ke_share = 0.0;
+  bool route64 = false;
+  long long steps64 = 0;
   double t = 0.0;
   // counters
   double pp_total = 0.0, cell_stages = 0.0;
@@ -235,6 +264,7 @@ struct hweno_handle {
   double* spool = nullptr;
   int seg_max = 0;
   int seg_keep = 0;
+  bool seg_keep_refused = false;  // intermediates were asked for and did not fit
   bool recording = false;        // do_step records each accepted step into the next slot
   int rec_count = 0;             // recorded steps
   std::vector<double> rec_dts;   // their step sizes
@@ -247,6 +277,16 @@ struct hweno_handle {
   double prof_ms[K_NKIND];
   char err[512];
 };
+
+// The mixed path's precision bound.  Its FP32 face fluxes of the total energy carry
+// rounding of about 2^-24 of that flux; a stage then moves the internal energy by about
+// 2^-24 x (kinetic / internal energy) x the CFL-sized factor dt |u| / h.  Where the
+// internal energy falls below 1e-4 of the total (the kinetic share above 1 - 1e-4) that
+// is 6e-4 of the internal energy per stage, and the Mach-1500 colliding streams
+// (internal share 7.5e-7) would lose positivity within a few steps.  A mixed handle
+// therefore runs the FP64 operator for a step or residual whose state exceeds this share
+// anywhere, and returns to FP32 once the state is back under it.
+constexpr double MIXED_MAX_KINETIC_SHARE = 1.0 - 1e-4;
 
 static char g_init_err[512] = "no error";
 
@@ -313,11 +353,11 @@ static void launch_ghost(hweno_handle* h, double* q, float* hilo = nullptr) {
 // the FP64 cell-trace kernels take CONS_SMEM_BYTES of dynamic shared memory (above the
 // 48 KB default): allowed once per device
 static cudaError_t cons_smem_allow() {
-  static unsigned int done = 0;  // bit per device
+  static std::atomic<unsigned int> done{0};  // bit per device; callers may be on several threads
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 32 && (done >> dev) & 1u) return cudaSuccess;
+  if (dev < 32 && (done.load() >> dev) & 1u) return cudaSuccess;
   e = cudaFuncSetAttribute(k_cons<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cons_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
@@ -329,7 +369,7 @@ static cudaError_t cons_smem_allow() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kb_cons<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_dr, cudaFuncAttributeMaxDynamicSharedMemorySize, DR_SMEM_BYTES);
-  if (e == cudaSuccess && dev < 32) done |= 1u << dev;
+  if (e == cudaSuccess && dev < 32) done.fetch_or(1u << dev);
   return e;
 }
 
@@ -338,7 +378,7 @@ static cudaError_t cons_smem_allow() {
 // handle's time, dt the device-side step of the current attempt)
 static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, double cst = 0.0) {
   const Grid& g = h->g;
-  if (h->cfg.precision == HWENO_MIXED) {
+  if (h->cfg.precision == HWENO_MIXED && !h->route64) {
     float* hilo = mixed_planes(h->w, g.ps).hilo;
     if (h->split_of == q) {
       // the stage update that wrote q also wrote the interior of its split
@@ -445,10 +485,13 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, d
 static int launch_rk(hweno_handle* h, int stage, const double* qin, const double* mom,
                      const double* rhs, double* qout) {
   Prof p(h, K_RK);
-  if (h->cfg.precision == HWENO_MIXED) {
+  if (h->cfg.precision == HWENO_MIXED && !h->route64) {
     k_rk_split<<<grid2(h->g.nx, h->g.ny), dim3(BX, BY), 0, h->st>>>(h->g, stage, qin, mom, rhs, h->BASE, qout,
                                                                   h->d_diag, mixed_planes(h->w, h->g.ps).hilo);
     h->split_of = qout;
+  } else if (h->cfg.precision == HWENO_MIXED) {
+    k_rk_kef<<<grid2(h->g.nx, h->g.ny), dim3(BX, BY), 0, h->st>>>(h->g, stage, qin, mom, rhs, h->BASE, qout,
+                                                                h->d_diag);
   } else {
     k_rk<<<grid2(h->g.nx, h->g.ny), dim3(BX, BY), 0, h->st>>>(h->g, stage, qin, mom, rhs, h->BASE, qout,
                                                               h->d_diag);
@@ -658,9 +701,26 @@ int hweno_set_state(hweno_handle* h, const double* q, int on_device) {
   h->steps = 0;
   h->rejected = 0;
   h->launches = 0;
+  h->steps64 = 0;
   h->t = 0.0;
+  if (h->cfg.precision == HWENO_MIXED) {
+    // the precision route of the first step or residual: one reduction and one read
+    CK(cudaMemsetAsync(&h->d_diag->kefrac_bits, 0, sizeof(unsigned long long), h->st), "diag");
+    k_kinetic_share<<<2 * 148, 256, 0, h->st>>>(h->g, h->Q, h->d_diag);
+    h->launches++;
+    CK(cudaGetLastError(), "kinetic share launch");
+    if ((rc = read_diag(h))) return rc;
+    h->ke_share = bits_to_double(h->h_diag->kefrac_bits);
+  }
   if (!on_device) CK(cudaStreamSynchronize(h->st), "stream synchronize");
   return HWENO_OK;
+}
+
+// the precision route of a mixed handle's next step or residual (see
+// MIXED_MAX_KINETIC_SHARE); the FP64 operator overwrites the planes of the FP32 split
+static void choose_route(hweno_handle* h) {
+  h->route64 = h->cfg.precision == HWENO_MIXED && !(h->ke_share <= MIXED_MAX_KINETIC_SHARE);
+  if (h->route64) h->split_of = nullptr;
 }
 
 int hweno_set_time(hweno_handle* h, double t) {
@@ -681,6 +741,7 @@ int hweno_get_state(hweno_handle* h, double* q, int on_device) {
 int hweno_residual(hweno_handle* h, double* rhs, double* vhat, int on_device) {
   if (!h) return HWENO_ERR_ARG;
   if (!h->have_state) return fail(h, HWENO_ERR_STATE, "hweno_residual before hweno_set_state");
+  choose_route(h);
   int rc = reset_diag(h);
   if (!rc) rc = residual_eval(h, h->Q, h->RHS, h->MOM);
   if (rc) return rc;
@@ -735,6 +796,7 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
     return fail(h, HWENO_ERR_STATE, "recording more steps than hweno_adjoint_reserve allowed");
   const bool keep = rec >= 0 && h->seg_keep;
   WorkGuard wg(h);
+  choose_route(h);
   double* q1 = rec >= 0 ? seg_state(h, rec, 1) : h->QS;
   double* q2 = rec >= 0 ? seg_state(h, rec, 2) : h->QS;
   if (keep) h->w = seg_work(h, rec, 0);
@@ -758,6 +820,7 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
     // stage flags and counters of this attempt; keep dt and the stage-1 maxima
     CK(cudaMemsetAsync(&h->d_diag->pp_count, 0, sizeof(unsigned long long), h->st), "diag");
     CK(cudaMemsetAsync(&h->d_diag->flags, 0, sizeof(unsigned int), h->st), "diag");
+    CK(cudaMemsetAsync(&h->d_diag->kefrac_bits, 0, sizeof(unsigned long long), h->st), "diag");
     if ((rc = launch_rk(h, 1, h->Q, h->MOM0, h->RHS0, q1))) return rc;
     if (keep) h->w = seg_work(h, rec, 1);
     // stage times of SSP-RK3 (a source term's t): t^n, t^n + dt, t^n + dt/2
@@ -784,6 +847,10 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
       h->dt_last = dt;
       h->steps++;
       h->rejected += rej;
+      if (h->cfg.precision == HWENO_MIXED) {
+        h->ke_share = bits_to_double(d.kefrac_bits);
+        if (h->route64) h->steps64++;
+      }
       if (rec >= 0) {
         h->rec_dts.push_back(dt);
         h->rec_count++;
@@ -845,6 +912,8 @@ int hweno_get_diag(hweno_handle* h, hweno_diag* d) {
   d->cell_stages = h->cell_stages;
   d->steps = h->steps;
   d->rejected = h->rejected;
+  d->fp64_steps = h->steps64;
+  d->max_kinetic_share = h->cfg.precision == HWENO_MIXED ? h->ke_share : 0.0;
   if (h->have_state) {
     k_state_rows<<<h->g.ny, 32, 0, h->st>>>(h->g, h->Q, h->PART);
     k_state_final<<<1, 32, 0, h->st>>>(h->g, h->PART, h->d_red);
@@ -865,7 +934,7 @@ int hweno_debug_fields(hweno_handle* h, int which, double* out, int on_device) {
   const Grid& g = h->g;
   const long long N = (long long)g.nx * g.ny;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (h->cfg.precision == HWENO_MIXED && which <= 3) {
+  if (h->cfg.precision == HWENO_MIXED && !h->route64 && which <= 3) {
     // FP32 intermediates of the mixed path, widened to FP64
     const WorkF f = mixed_planes(h->w, g.ps);
     if (which <= 1) {
@@ -1018,7 +1087,11 @@ int hweno_adjoint_init(hweno_handle* h) {
 extern "C" int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_intermediates) {
   if (!h || max_steps < 1) return fail(h, HWENO_ERR_ARG, "hweno_adjoint_reserve: bad argument");
   if (!h->apool) return fail(h, HWENO_ERR_STATE, "hweno_adjoint_reserve before hweno_adjoint_init");
-  if (h->spool && h->seg_max >= max_steps && (h->seg_keep || !keep_intermediates)) return HWENO_OK;
+  // storage that is large enough serves again, and so does storage whose request for
+  // intermediates was already refused for lack of memory: reallocating it would drop
+  // what has been recorded
+  if (h->spool && h->seg_max >= max_steps && (h->seg_keep || !keep_intermediates || h->seg_keep_refused))
+    return h->seg_keep ? 1 : HWENO_OK;
   if (h->spool) {
     CK(cudaStreamSynchronize(h->st), "stream synchronize");
     cudaFree(h->spool);
@@ -1039,6 +1112,7 @@ extern "C" int hweno_adjoint_reserve(hweno_handle* h, int max_steps, int keep_in
   h->rec_dts.clear();
   h->seg_max = max_steps;
   h->seg_keep = keep;
+  h->seg_keep_refused = keep_intermediates && !keep;
   return keep ? 1 : HWENO_OK;
 }
 
@@ -1501,6 +1575,10 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   for (int c = 0; c < ncases; c++)
     if (cfgs[c].linear_grad != cfgs[0].linear_grad)
       return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same linear_grad");
+  // hweno_batch_step counts restart rounds for all cases together
+  for (int c = 0; c < ncases; c++)
+    if (cfgs[c].max_halvings != cfgs[0].max_halvings)
+      return fail(nullptr, HWENO_ERR_ARG, "hweno_batch_init: all cases must use the same max_halvings");
   hweno_batch* b = new (std::nothrow) hweno_batch();
   if (!b) return fail(nullptr, HWENO_ERR_ARG, "host allocation failed");
   snprintf(b->err, sizeof(b->err), "no error");
@@ -1747,6 +1825,7 @@ constexpr long long NOALLOC_PLANES = 12 + 12 + 8 + 48 + 36 + 3 + 6 + 6 + 18 + 12
 // (for example grids up to 56 x 56, or 120 x 24)
 constexpr long long NOALLOC_MAX_PLANE = 4096;
 constexpr long long NOALLOC_DOUBLES = NOALLOC_PLANES * NOALLOC_MAX_PLANE + 16;  // + Diag
+static_assert(sizeof(Diag) <= 16 * sizeof(double), "the reductions' words fit the array's tail");
 constexpr int NOALLOC_MAX_DEVICES = 64;
 double* g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address of the array, per device
 std::mutex g_noalloc_mu;

@@ -69,6 +69,9 @@ struct Diag {
                                   // bit 2: inadmissible cell average met by the limiter
   unsigned int pad;
   double dt;                      // time step of the current step
+  unsigned long long kefrac_bits; // mixed handles: max over cells of the kinetic share
+                                  // |m|^2 / (2 rho E) of the stage-3 state, as the bits of a
+                                  // double in [0, 1] (1 where that state is inadmissible)
 };
 
 enum { FLAG_INADMISSIBLE = 1u, FLAG_NONFINITE = 2u, FLAG_BADAVG = 4u };

@@ -560,8 +560,10 @@ __device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, doub
 //   stage 3: out = 1/3 base + 2/3 ([u^(2); vhat^(2)] + dt F)
 // plus the admissibility test of the output averages (Sec. 5).
 // SPLIT (mixed path): also write the hi/lo split of the new state (24 float planes at
-// hilo), so that the next evaluation needs no separate split pass
-template <bool SPLIT = false>
+// hilo), so that the next evaluation needs no separate split pass.
+// KEF (mixed handles): at stage 3, also the largest kinetic share |m|^2 / (2 rho E) of
+// the new state over the cells, the measure that routes a mixed handle's next step
+template <bool SPLIT = false, bool KEF = false>
 __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* __restrict__ qin,
                                         const double* __restrict__ mom, const double* __restrict__ rhs,
                                         double* __restrict__ base, double* __restrict__ qout, Diag* diag,
@@ -569,6 +571,7 @@ __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* 
   const int i = gx;
   const int j = gy;
   unsigned int bad = 0;
+  double kef = 0.0;
   if (i < g.nx && j < g.ny) {
     const long long c = cidx(g, i, j);
     const double dt = diag->dt;
@@ -597,9 +600,18 @@ __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* 
     // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
     const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
     if (!(out[0] > 0.0) || !(rp > 0.0)) bad = FLAG_INADMISSIBLE;
+    if constexpr (KEF) {
+      if (stage == 3) kef = (out[0] > 0.0 && rp > 0.0) ? 1.0 - rp / (out[3] * out[0]) : 1.0;
+    }
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
+  if constexpr (KEF) {
+    if (stage == 3) {
+      kef = warp_max(fmax(kef, 0.0));
+      if (lane_id() == 0) atomic_max_pos(&diag->kefrac_bits, kef);
+    }
+  }
 }
 
 }  // namespace hw

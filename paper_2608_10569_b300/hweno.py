@@ -63,7 +63,8 @@ class hweno_diag(ctypes.Structure):
                 ("pp_active", ctypes.c_double), ("cell_stages", ctypes.c_double),
                 ("min_rho", ctypes.c_double), ("min_p", ctypes.c_double),
                 ("totals", ctypes.c_double * 4),
-                ("steps", ctypes.c_longlong), ("rejected", ctypes.c_longlong)]
+                ("steps", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
+                ("fp64_steps", ctypes.c_longlong), ("max_kinetic_share", ctypes.c_double)]
 
 
 class hweno1d_config(ctypes.Structure):
@@ -289,7 +290,8 @@ class Solver:
         _check(self.h, self.lib.hweno_get_diag(self.h, ctypes.byref(d)))
         return {"t": d.t, "dt_last": d.dt_last, "alpha_star": d.alpha_star, "beta_max": d.beta_max,
                 "pp_active": d.pp_active, "cell_stages": d.cell_stages, "min_rho": d.min_rho,
-                "min_p": d.min_p, "totals": list(d.totals), "steps": d.steps, "rejected": d.rejected}
+                "min_p": d.min_p, "totals": list(d.totals), "steps": d.steps, "rejected": d.rejected,
+                "fp64_steps": d.fp64_steps, "max_kinetic_share": d.max_kinetic_share}
 
     def debug_fields(self, which):
         import torch
@@ -460,6 +462,7 @@ class Batch:
 
 def _rollout_autograd():
     import torch
+    from torch.autograd.function import once_differentiable
 
     class Rollout(torch.autograd.Function):
         """q_T = Phi^n(q_0) for n SSP-RK3 steps of the FP64 solver, differentiable with
@@ -495,6 +498,9 @@ def _rollout_autograd():
             if recorded:
                 s.adjoint_record(False)
             qT = s.get_state().clone()
+            if not record:  # no gradient will be taken: release the device memory now
+                s.close()
+                s = None
             ctx.solver = s
             ctx.dts = dts
             ctx.ckpts = ckpts
@@ -503,12 +509,21 @@ def _rollout_autograd():
             return qT
 
         @staticmethod
+        @once_differentiable
         def backward(ctx, qbar):
             s = ctx.solver
-            s.adjoint_init()
+            if s is None:
+                raise RuntimeError("hweno.rollout: a second backward through the same rollout; its solver "
+                                   "was released by the first (run the rollout again)")
+            ctx.solver = None
             dts, ckpts, K = ctx.dts, ctx.ckpts, ctx.ckpt
             n = len(dts)
-            s.adjoint_reserve(min(K, n), keep_intermediates=True)
+            if ctx.recorded is None:
+                # nothing recorded in the forward: storage for the recomputed segments.
+                # A forward that recorded reserved it already, and reserving again could
+                # drop its recording
+                s.adjoint_init()
+                s.adjoint_reserve(min(K, n), keep_intermediates=True)
             lam = qbar.detach().contiguous().clone()
             mubar = 0.0
             for a in reversed(sorted(ckpts)):

@@ -255,3 +255,13 @@ def test_binding_refuses_buffers_of_the_wrong_size():
             call()
     with pytest.raises(ValueError):
         hweno.advance1d([dict(n=8)], [], 0.0, 1.0)
+
+
+def test_batch_cases_share_the_restart_cap(lib):
+    """hweno_batch_step counts restart rounds for all cases together, so the cases of a
+    batch must agree on max_halvings"""
+    from paper_2608_10569_b300 import hweno
+    b = ctypes.c_void_p()
+    cfgs = (hweno.hweno_config * 2)(hweno.make_config(8, 8, max_halvings=20), hweno.make_config(8, 8))
+    assert lib.hweno_batch_init(cfgs, 2, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
+    assert b.value is None and b"max_halvings" in lib.hweno_last_error(None)
