@@ -41,7 +41,7 @@ def _noalloc(case, qd):
 
 
 def _with_handle(case, qd):
-    s = hweno.Solver(case.params())
+    s = hweno.Solver(case.params(), precision="mixed" if case.params().get("precision") == "mixed" else "fp64")
     s.set_state(qd)
     rhs, vhat = s.residual()
     out = rhs.cpu().numpy(), vhat.cpu().numpy()
@@ -60,6 +60,46 @@ def test_noalloc_matches_hweno_residual_on_two_calls_in_a_row():
         assert np.isfinite(r1).all() and np.isfinite(v1).all()
         assert _rel(r1, r0) <= RES_TOL
         assert _rel(v1, v0) <= RES_TOL
+
+
+def _open_rough():
+    case, q = I.random_rough(40, 36, seed=9, bc=("inflow", "outflow", "symmetry", "outflow"), Re=200.0)
+    case.inflow = ((tuple(q[:4, 18, 0]), tuple(q[:4, 5, 0])), None, None, None)
+    case.band = ((0.5, 0.15), None, None, None)
+    return case, q
+
+
+def _variant(case, **kw):
+    p = dict(case.params(), **kw)
+    case.params = lambda: p
+    return case
+
+
+@pytest.mark.parametrize("variant", ["mixed", "open_faces", "linear_grad", "mixed_open_faces"])
+def test_noalloc_variants_match_a_handle_of_the_same_setting(variant):
+    """the mixed precision (its FP32 split of the state lives in the static array too),
+    inflow and outflow faces, and the linear-gradient ablation, each against a handle with
+    the same setting, on two calls in a row of different grids"""
+    def make(k):
+        if "open" in variant:
+            case, q = _open_rough() if k == 0 else I.random_smooth(31, 27, seed=24, bc=("outflow",) * 4)
+        else:
+            case, q = I.random_rough(40, 36, seed=23) if k == 0 else I.random_smooth(31, 27, seed=24)
+        kw = {}
+        if "mixed" in variant:
+            kw["precision"] = "mixed"
+        if variant == "linear_grad":
+            kw["linear_grad"] = True
+        return _variant(case, **kw), q
+
+    for k in range(2):
+        case, q = make(k)
+        qd = torch.from_numpy(q).cuda()
+        r1, v1 = _noalloc(case, qd)
+        r0, v0 = _with_handle(case, qd)
+        assert np.isfinite(r1).all() and np.isfinite(v1).all()
+        assert _rel(r1, r0) <= RES_TOL, (variant, k)
+        assert _rel(v1, v0) <= RES_TOL, (variant, k)
 
 
 def test_noalloc_rejects_grids_beyond_the_static_scratch():

@@ -150,3 +150,40 @@ def test_example_5_4_runs_with_the_default_halvings():
     assert out[1]["status"] == so["status"] == 0 and out[1]["t"] == 0.6
     assert abs(out[1]["steps"] - so["steps"]) <= 0.02 * so["steps"]
     assert states[1].cpu().numpy()[0].min() > 0
+
+
+def test_example_5_1_fine_meshes_against_table_5_1():
+    """Table 5.1's fine meshes on the GPU, both schemes at 200 and 280 cells in one launch
+    with the viscous cap at b = 0.01 (ten times fewer steps than b = 0.001, whose FP64
+    round-off floors the errors near 1e-11): the density errors within 25 % of the
+    table's, GR's L1 order above 4.8, and the oracle's steps and errors to 1e-9"""
+    import os
+    tab = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table_5_1.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                sc, n, linf, l1 = line.split()
+                tab[(sc, int(n))] = (float(linf), float(l1))
+    params, states, keys = [], [], []
+    for scheme in ("gr", "dr"):
+        for n in (200, 280):
+            p, q = I.manufactured_1d(n, 0.0)
+            params.append(dict(p, scheme=scheme, b_visc=0.01))
+            states.append(torch.from_numpy(q).cuda())
+            keys.append((scheme, n))
+    out = hweno.advance1d(params, states, 0.0, 0.1)
+    errs = {}
+    for p, st, r, key in zip(params, states, out, keys):
+        assert r["status"] == 0 and abs(r["t"] - 0.1) < 1e-15
+        _, qe = I.manufactured_1d(key[1], 0.1)
+        e = np.abs(st.cpu().numpy()[0] - qe[0])
+        errs[key] = (e.max(), e.mean())
+        for k in range(2):
+            assert 0.75 < errs[key][k] / tab[key][k] < 1.25, (key, errs[key], tab[key])
+    order = np.log(errs[("gr", 200)][1] / errs[("gr", 280)][1]) / np.log(280 / 200)
+    assert order > 4.8
+    # the GR run at 280 cells against the oracle's
+    p, q = I.manufactured_1d(280, 0.0)
+    qo, so = O.advance1d(O.make_cfg1d(**params[1]), q, 0.0, 0.1)
+    assert so["steps"] == out[1]["steps"]
+    assert np.abs(states[1].cpu().numpy() - qo).sum() / np.abs(qo).sum() <= 1e-9
