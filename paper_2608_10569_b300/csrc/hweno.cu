@@ -19,6 +19,7 @@
 #include "hweno_batch.cuh"
 #include "hweno_adjoint.cuh"
 #include "hweno_source.cuh"
+#include "hweno_tma.cuh"
 
 namespace hw {
 
@@ -271,6 +272,10 @@ struct hweno_handle {
   // profiling
   bool prof = false;
   std::vector<EventPair> ev;
+  // mixed path: tensor maps of the FP32 traces and cell means for the TMA-staged
+  // gradient kernel (tma false: the separate face-moment, weak-moment and gradient kernels)
+  CUtensorMap tr_map, wb_map;
+  bool tma = false;
   Quad4 quad{};  // the source term's 4-point Gauss rule
   Open open{};   // prescribed states of the inflow faces
   long long prof_n[K_NKIND];
@@ -369,6 +374,10 @@ static cudaError_t cons_smem_allow() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kb_cons<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONS_SMEM_BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_dr, cudaFuncAttributeMaxDynamicSharedMemorySize, DR_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grad_tma_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grad_tma_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM_BYTES);
   if (e == cudaSuccess && dev < 32) done.fetch_or(1u << dev);
   return e;
 }
@@ -376,38 +385,98 @@ static cudaError_t cons_smem_allow() {
 // one spatial-operator evaluation of state q (12 planes): rhs (12 planes) and the
 // modified moments mom (8 planes); a source term is taken at t + cst * dt (t the
 // handle's time, dt the device-side step of the current attempt)
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link to the driver
+// library); null where the driver does not provide it
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static std::atomic<EncodeTiledFn> fn{nullptr};
+  static std::atomic<bool> tried{false};
+  if (!tried.load()) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess && p)
+      fn.store((EncodeTiledFn)p);
+    tried.store(true);
+  }
+  return fn.load();
+}
+
+// tensor maps of the mixed path's FP32 face traces (x: pitch, y: padded rows, variable,
+// point; the face group's float plane 4 k + v) and cell means (x, y, variable) for the
+// boxes k_grad_tma_mixed copies; false if they cannot be made
+static bool encode_trace_maps(const Grid& g, const Work& w, CUtensorMap* tr, CUtensorMap* wb) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const WorkF f = mixed_planes(w, g.ps);
+  const cuuint64_t row = (cuuint64_t)g.pitch * sizeof(float), plane = (cuuint64_t)g.ps * sizeof(float);
+  const cuuint64_t dt[4] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * NG), 4, 12};
+  const cuuint64_t st[3] = {row, plane, 4 * plane};
+  const cuuint32_t bt[4] = {GB_X, GB_Y, 3, 12};
+  const cuuint32_t one[4] = {1, 1, 1, 1};
+  if (enc(tr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f.face, dt, st, bt, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint64_t dw[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * NG), 3};
+  const cuuint64_t sw[2] = {row, plane};
+  const cuuint32_t bw[3] = {GB_X, GB_Y, 3};
+  return enc(wb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f.wbar, dw, sw, bw, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the mixed path's operator up to the gradients: ghost cells (and the FP32 split of a
+// state set from outside), traces and limiter, then face moments, weak-derivative
+// moments and gradients (one TMA-staged kernel where the handle has the tensor maps)
+static void mixed_front(hweno_handle* h, double* q, double* mom) {
+  const Grid& g = h->g;
+  float* hilo = mixed_planes(h->w, g.ps).hilo;
+  if (h->split_of == q) {
+    // the stage update that wrote q also wrote the interior of its split
+    launch_ghost(h, q, hilo);
+  } else {
+    launch_ghost(h, q);
+    Prof p(h, K_GHOST);
+    k_split<<<4 * 148, 256, 0, h->st>>>(g, q, hilo);
+    h->split_of = q;
+  }
+  {
+    Prof p(h, K_CONS);
+    k_cons_mixed<<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
+  }
+  if (h->tma) {
+    Prof p(h, K_GRAD);
+    const dim3 grid((unsigned)((g.nx + 2 + GT_X - 1) / GT_X), (unsigned)((g.ny + 2 + GT_Y - 1) / GT_Y));
+    if (h->cfg.linear_grad)
+      k_grad_tma_mixed<true><<<grid, GT_THREADS, GT_SMEM_BYTES, h->st>>>(g, h->w, h->tr_map, h->wb_map, h->d_diag);
+    else
+      k_grad_tma_mixed<false><<<grid, GT_THREADS, GT_SMEM_BYTES, h->st>>>(g, h->w, h->tr_map, h->wb_map, h->d_diag);
+    return;
+  }
+  {
+    Prof p(h, K_FACEMOM);
+    k_face_moments_mixed<<<grid2(g.nx + 5, g.ny + 5, 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+  }
+  {
+    Prof p(h, K_WEAK);
+    k_weak_moments_mixed<<<grid2(g.nx + 4, g.ny + 4), dim3(BX, BY), 0, h->st>>>(g, h->w);
+  }
+  {
+    Prof p(h, K_GRAD);
+    if (h->cfg.linear_grad)
+      k_grad_mixed<true><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+    else
+      k_grad_mixed<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+  }
+}
+
 static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, double cst = 0.0) {
   const Grid& g = h->g;
   if (h->cfg.precision == HWENO_MIXED && !h->route64) {
-    float* hilo = mixed_planes(h->w, g.ps).hilo;
-    if (h->split_of == q) {
-      // the stage update that wrote q also wrote the interior of its split
-      launch_ghost(h, q, hilo);
-    } else {
-      launch_ghost(h, q);
-      Prof p(h, K_GHOST);
-      k_split<<<4 * 148, 256, 0, h->st>>>(g, q, hilo);
-      h->split_of = q;
-    }
-    {
-      Prof p(h, K_CONS);
-      k_cons_mixed<<<grid2(g.nx + 6, g.ny + 6), dim3(BX, BY), 0, h->st>>>(g, q, h->w, mom, h->d_diag);
-    }
-    {
-      Prof p(h, K_FACEMOM);
-      k_face_moments_mixed<<<grid2(g.nx + 5, g.ny + 5, 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
-    }
-    {
-      Prof p(h, K_WEAK);
-      k_weak_moments_mixed<<<grid2(g.nx + 4, g.ny + 4), dim3(BX, BY), 0, h->st>>>(g, h->w);
-    }
-    {
-      Prof p(h, K_GRAD);
-      if (h->cfg.linear_grad)
-        k_grad_mixed<true><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
-      else
-        k_grad_mixed<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
-    }
+    mixed_front(h, q, mom);
     {
       Prof p(h, K_FLUX);
       k_flux_mixed<<<grid2(g.nx + 1, g.ny + 1, 2), dim3(BX, BY), 0, h->st>>>(g, h->w, h->d_diag);
@@ -480,6 +549,33 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, d
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "spatial operator launch");
   return HWENO_OK;
+}
+
+static int launch_rk(hweno_handle* h, int stage, const double* qin, const double* mom,
+                     const double* rhs, double* qout);
+
+// stage 2 or 3 of a step: the operator on the stage state q and the stage update into
+// qout.  On the mixed path (without a source term) the face fluxes, the balances and the
+// update run as one tile kernel, k_flux_rk_mixed, whose result equals the separate
+// kernels' bit for bit; otherwise the residual goes through HBM.
+static int stage_eval_rk(hweno_handle* h, double* q, int stage, double* qout, double cst) {
+  const Grid& g = h->g;
+  if (h->cfg.precision == HWENO_MIXED && !h->route64 && h->cfg.source == HWENO_SOURCE_NONE) {
+    mixed_front(h, q, h->MOM);
+    {
+      Prof p(h, K_FLUX);
+      const dim3 grid((unsigned)((g.nx + FR_TX - 1) / FR_TX), (unsigned)((g.ny + FR_TY - 1) / FR_TY));
+      k_flux_rk_mixed<<<grid, FR_THREADS, 0, h->st>>>(g, h->w, stage, q, h->MOM, h->BASE, qout, h->d_diag,
+                                                      mixed_planes(h->w, g.ps).hilo);
+    }
+    h->split_of = qout;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "fused stage launch");
+    return HWENO_OK;
+  }
+  int rc = residual_eval(h, q, h->RHS, h->MOM, cst);
+  if (!rc) rc = launch_rk(h, stage, q, h->MOM, h->RHS, qout);
+  return rc;
 }
 
 static int launch_rk(hweno_handle* h, int stage, const double* qin, const double* mom,
@@ -608,6 +704,7 @@ int hweno_init(const hweno_config* cfg, void* stream, hweno_handle** out) {
   h->w.face = take(48); h->w.vol = take(36); h->w.wbar = take(3); h->w.wx = take(6); h->w.wy = take(6);
   h->w.rm = take(18); h->w.gr = take(126); h->w.fx = take(12); h->w.fy = take(12); h->w.theta = take(2);
   if (ndr) h->w.dr = take(ndr);
+  if (c.precision == HWENO_MIXED) h->tma = encode_trace_maps(g, h->w, &h->tr_map, &h->wb_map);
   h->STAGE = p; p += 4 * N;
   h->PART = p; p += 6LL * c.ny;
   h->d_red = p;
@@ -751,6 +848,7 @@ int hweno_residual(hweno_handle* h, double* rhs, double* vhat, int on_device) {
   if ((rc = read_diag(h))) return rc;
   h->alpha = bits_to_double(h->h_diag->alpha_bits);
   h->beta = bits_to_double(h->h_diag->beta_bits);
+  if (h->h_diag->flags & FLAG_TIMEOUT) return fail(h, HWENO_ERR_TIMEOUT, "a tensor copy's wait gave up");
   if (h->h_diag->flags & FLAG_NONFINITE) return fail(h, HWENO_ERR_NONFINITE, "non-finite residual");
   return HWENO_OK;
 }
@@ -824,14 +922,13 @@ static int do_step(hweno_handle* h, double dt_forced, double t_cap, double* dt_u
     if ((rc = launch_rk(h, 1, h->Q, h->MOM0, h->RHS0, q1))) return rc;
     if (keep) h->w = seg_work(h, rec, 1);
     // stage times of SSP-RK3 (a source term's t): t^n, t^n + dt, t^n + dt/2
-    if ((rc = residual_eval(h, q1, h->RHS, h->MOM, 1.0))) return rc;
-    if ((rc = launch_rk(h, 2, q1, h->MOM, h->RHS, q2))) return rc;
+    if ((rc = stage_eval_rk(h, q1, 2, q2, 1.0))) return rc;
     if (keep) h->w = seg_work(h, rec, 2);
-    if ((rc = residual_eval(h, q2, h->RHS, h->MOM, 0.5))) return rc;
-    if ((rc = launch_rk(h, 3, q2, h->MOM, h->RHS, h->QS))) return rc;
+    if ((rc = stage_eval_rk(h, q2, 3, h->QS, 0.5))) return rc;
     if ((rc = read_diag(h))) return rc;
     const Diag first = h->h_diag[1];
     const Diag& d = h->h_diag[0];
+    if ((first.flags | d.flags) & FLAG_TIMEOUT) return fail(h, HWENO_ERR_TIMEOUT, "a tensor copy's wait gave up");
     if (first.flags & FLAG_NONFINITE) return fail(h, HWENO_ERR_NONFINITE, "non-finite residual at t^n");
     const double dt = d.dt;
     if (!(dt > 0.0) || !isfinite(dt)) return fail(h, HWENO_ERR_NONFINITE, "time step is not positive and finite");
@@ -1322,7 +1419,7 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 // kernel for all cases, one CUDA graph per SSP-RK3 step of the whole ensemble.
 
 namespace {
-enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_N };
+enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_FR, BR_N };
 
 struct BatchList {
   int bx = 32, by = 4;  // block shape of the kernels that use this list
@@ -1379,7 +1476,7 @@ static void region_of(int k, const Grid& g, int& wx, int& wy, int& wz) {
     case BR_WEAK: wx = g.nx + 4; wy = g.ny + 4; break;
     case BR_GRAD: wx = g.nx + 2; wy = g.ny + 2; break;
     case BR_FLUX: wx = g.nx + 1; wy = g.ny + 1; wz = 2; break;
-    case BR_INT: wx = g.nx; wy = g.ny; break;
+    case BR_INT: case BR_FR: wx = g.nx; wy = g.ny; break;
     case BR_GX: wx = 8 * g.ny; wy = 1; break;
     case BR_GY: wx = 8 * (g.nx + 2 * NG); wy = 1; break;
     default: wx = (int)(12 * g.ps); wy = 1; break;  // BR_SPLIT
@@ -1446,9 +1543,16 @@ static void batch_enqueue_step(hweno_batch* b) {
       kb_weak_moments<1><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
       if (b->lin) kb_grad<1, true><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
       else kb_grad<1><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+      b->launches += 4;
+      if (stage > 1 && !b->source) {
+        // stages 2 and 3: fluxes, balances and the stage update in one tile kernel
+        kb_flux_rk_mixed<<<grid(BR_FR), FR_THREADS, 0, b->st>>>(b->d_cases, b->L[BR_FR].tl(), n, stage);
+        b->launches++;
+        continue;
+      }
       kb_flux<1><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
       kb_assemble<1><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
-      b->launches += 6;
+      b->launches += 2;
     } else if (b->dr) {
       kb_cons<0, true><<<grid(BR_CONS), dims(BR_CONS), CONS_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_CONS].tl(),
                                                                                  n, which);
@@ -1495,6 +1599,7 @@ static int batch_grids(hweno_batch* b) {
                                 : persistent_grid(b, kb_grad<1>, b->L[BR_GRAD].total);
     b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<1>, b->L[BR_FLUX].total);
     b->L[BR_INT].grid = persistent_grid(b, kb_assemble<1>, b->L[BR_INT].total);
+    b->L[BR_FR].grid = persistent_grid(b, kb_flux_rk_mixed, b->L[BR_FR].total, 0, FR_THREADS);
   } else if (b->dr) {
     b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0, true>, b->L[BR_CONS].total, CONS_SMEM_BYTES);
     b->L[BR_GRAD].grid = persistent_grid(b, kb_dr, b->L[BR_GRAD].total, DR_SMEM_BYTES, DR_THREADS);
@@ -1615,6 +1720,7 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   }
   for (int k = 0; k < BR_N && !rc; k++) {
     if (b->dr && k == BR_GRAD) rc = build_list(b, k, 32, DR_THREADS / 32);  // kb_dr's block
+    else if (k == BR_FR) rc = build_list(b, k, FR_TX, FR_TY);             // kb_flux_rk_mixed's tiles
     else rc = build_list(b, k, k <= BR_INT ? 32 : 128, k <= BR_INT ? 4 : 1);
   }
   if (!rc) rc = batch_grids(b);

@@ -154,6 +154,41 @@ __global__ void __launch_bounds__(128) kb_rk(const CaseDev* __restrict__ cases, 
   HW_BATCH_END
 }
 
+// stages 2 and 3 of a mixed batch, after the gradients: k_flux_rk_mixed's tile (the
+// face sums of FR_TX x FR_TY cells in shared memory, then the balances and the in-place
+// stage update of QS) over a work list of (case, tile) items, the same arithmetic as a
+// single handle's stage
+__global__ void __launch_bounds__(FR_THREADS) kb_flux_rk_mixed(const CaseDev* __restrict__ cases, TileList L,
+                                                                int ncase, int stage) {
+  __shared__ FluxTile ft;
+  const int total = L.start[ncase];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_case(L.start, ncase, item);
+    const CaseDev& cd = cases[c];
+    if (!cd.active) continue;  // the same for every thread of the block
+    const Grid cg = cd.g;
+    const Work cw = cd.w;
+    const int l = item - L.start[c];
+    const int by = l / L.tx[c], bx = l - by * L.tx[c];
+    const int i0 = bx * FR_TX, j0 = by * FR_TY;
+    const WorkF f = mixed_planes(cw, cg.ps);
+    float amax = 0.f, bmax = 0.f;
+    flux_tile_faces(cg, f, i0, j0, threadIdx.x, ft, amax, bmax);
+    amax = warp_max(amax);
+    bmax = warp_max(bmax);
+    if (lane_id() == 0) {
+      atomic_max_pos(&cd.diag->alpha_bits, (double)amax);
+      atomic_max_pos(&cd.diag->beta_bits, (double)bmax);
+    }
+    __syncthreads();
+    double kef = 0.0;
+    const unsigned int bad = flux_tile_cell(cg, f, i0, j0, threadIdx.x, ft, stage, cd.diag->dt, cd.QS, cd.MOM,
+                                            cd.BASE, cd.QS, mixed_planes(cw, cg.ps).hilo, kef);
+    rk_reduce<false>(stage, bad, kef, cd.diag);
+    __syncthreads();  // the next item writes the tile again
+  }
+}
+
 // ghost fill: 1D items, gx = element index (x pass: 8 ny, y pass: 8 (nx + 8)); with
 // split, also the 24 planes of the state's hi/lo split
 __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int pass,

@@ -355,8 +355,64 @@ __device__ __forceinline__ void grad_mixed_body(const Grid& g, const Work& w, in
   }
 }
 
-// Eq. (3.3) in FP32; the face fluxes are stored in FP64 so that the moment balances
-// difference them exactly
+// Eq. (3.3) in FP32 at one face (dir 0: the x-face between cells cl and cr = cl + 1 in
+// x; dir 1: the y-face): the weighted sums S0[v] = sum_g w_g fhat_g and S1[v] = sum_g
+// w_g s_g fhat_g of the PP-LLF fluxes at its three Gauss points (s_g the tangential
+// node); returns the Lax-Friedrichs coefficient beta and raises amax to the face's
+// largest max(|u| + c, |v| + c)
+__device__ __forceinline__ float face_sums_mixed(const Grid& g, const WorkF& f, int dir, long long cl, long long cr,
+                                                 float* S0, float* S1, float& amax) {
+  const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
+  const float gam = (float)g.gamma, rPr = (float)g.rPr, rRe = (float)g.rRe;
+  float st[2][3][4], gs[2][3][6];
+#pragma unroll
+  for (int gp = 0; gp < 3; gp++)
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      const long long cc = s == 0 ? cl : cr;
+      const int k = (s == 0 ? kl : kr) + gp;
+#pragma unroll
+      for (int v = 0; v < 4; v++) st[s][gp][v] = f.face[(long long)(4 * k + v) * g.ps + cc];
+#pragma unroll
+      for (int n = 0; n < 6; n++) gs[s][gp][n] = f.gr[(long long)(6 * k + n) * g.ps + cc];
+    }
+  float beta = 0.f;
+#pragma unroll
+  for (int gp = 0; gp < 3; gp++)
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      beta = fmaxf(beta, wave_bound<float>(dir, st[s][gp], gs[s][gp], gam, rPr, rRe));
+      const float cs = sqrtf(gam * (gam - 1.f) * st[s][gp][3]);
+      amax = fmaxf(amax, fmaxf(fabsf(st[s][gp][1]) + cs, fabsf(st[s][gp][2]) + cs));
+    }
+#pragma unroll
+  for (int v = 0; v < 4; v++) S0[v] = S1[v] = 0.f;
+#pragma unroll
+  for (int gp = 0; gp < 3; gp++) {
+    float fl[4], fr[4], ul[4], ur[4];
+    phys_flux<float>(dir, st[0][gp], gs[0][gp], gam, rPr, rRe, fl);
+    phys_flux<float>(dir, st[1][gp], gs[1][gp], gam, rPr, rRe, fr);
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      float* u = s == 0 ? ul : ur;
+      const float* p = st[s][gp];
+      u[0] = p[0];
+      u[1] = p[0] * p[1];
+      u[2] = p[0] * p[2];
+      u[3] = p[0] * (p[3] + 0.5f * (p[1] * p[1] + p[2] * p[2]));
+    }
+    const float wg = gweight<float>(gp), wt = gweight<float>(gp) * gnode<float>(gp);
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const float fh = 0.5f * (fl[v] + fr[v] - beta * (ur[v] - ul[v]));
+      S0[v] += wg * fh;
+      if (gp != 1) S1[v] += wt * fh;
+    }
+  }
+  return beta;
+}
+
+// the face fluxes are stored in FP64 so that the moment balances difference them exactly
 __device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Diag* diag, int gx, int gy, int gz) {
   const int dir = gz;
   const int i = gx - (dir == 0 ? 1 : 0);
@@ -366,53 +422,8 @@ __device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Di
   if (i < g.nx && j < g.ny) {
     const long long cl = cidx(g, i, j);
     const long long cr = dir == 0 ? cidx(g, i + 1, j) : cidx(g, i, j + 1);
-    const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
-    const float gam = (float)g.gamma, rPr = (float)g.rPr, rRe = (float)g.rRe;
-    float st[2][3][4], gs[2][3][6];
-#pragma unroll
-    for (int gp = 0; gp < 3; gp++)
-#pragma unroll
-      for (int s = 0; s < 2; s++) {
-        const long long cc = s == 0 ? cl : cr;
-        const int k = (s == 0 ? kl : kr) + gp;
-#pragma unroll
-        for (int v = 0; v < 4; v++) st[s][gp][v] = f.face[(long long)(4 * k + v) * g.ps + cc];
-#pragma unroll
-        for (int n = 0; n < 6; n++) gs[s][gp][n] = f.gr[(long long)(6 * k + n) * g.ps + cc];
-      }
-    float beta = 0.f;
-#pragma unroll
-    for (int gp = 0; gp < 3; gp++)
-#pragma unroll
-      for (int s = 0; s < 2; s++) {
-        beta = fmaxf(beta, wave_bound<float>(dir, st[s][gp], gs[s][gp], gam, rPr, rRe));
-        const float cs = sqrtf(gam * (gam - 1.f) * st[s][gp][3]);
-        amax = fmaxf(amax, fmaxf(fabsf(st[s][gp][1]) + cs, fabsf(st[s][gp][2]) + cs));
-      }
-    bmax = beta;
-    float S0[4] = {0.f, 0.f, 0.f, 0.f}, S1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int gp = 0; gp < 3; gp++) {
-      float fl[4], fr[4], ul[4], ur[4];
-      phys_flux<float>(dir, st[0][gp], gs[0][gp], gam, rPr, rRe, fl);
-      phys_flux<float>(dir, st[1][gp], gs[1][gp], gam, rPr, rRe, fr);
-#pragma unroll
-      for (int s = 0; s < 2; s++) {
-        float* u = s == 0 ? ul : ur;
-        const float* p = st[s][gp];
-        u[0] = p[0];
-        u[1] = p[0] * p[1];
-        u[2] = p[0] * p[2];
-        u[3] = p[0] * (p[3] + 0.5f * (p[1] * p[1] + p[2] * p[2]));
-      }
-      const float wg = gweight<float>(gp), wt = gweight<float>(gp) * gnode<float>(gp);
-#pragma unroll
-      for (int v = 0; v < 4; v++) {
-        const float fh = 0.5f * (fl[v] + fr[v] - beta * (ur[v] - ul[v]));
-        S0[v] += wg * fh;
-        if (gp != 1) S1[v] += wt * fh;
-      }
-    }
+    float S0[4], S1[4];
+    bmax = face_sums_mixed(g, f, dir, cl, cr, S0, S1, amax);
     // S0 in FP64 planes 0-3: the average balances difference it in FP64, so their sum
     // over a periodic grid telescopes to FP64 rounding; S0 and S1 again as FP32 planes
     // (in double planes 8-11) for the moment balances, which run in FP32
@@ -433,7 +444,51 @@ __device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Di
   }
 }
 
-// Eq. (3.2): volume fluxes in FP32, face-flux sums and the balances in FP64
+// Eq. (3.2) for one cell: the volume fluxes in FP32 from its volume values and gradients,
+// and the three balances from the face sums (S0 in [0, 4), S1 in [4, 8)) of its right
+// (sR) and left (sL) x-faces and top (tT) and bottom (tB) y-faces: the average balance
+// r[0..4) in FP64 (the FP32 S0 are exact in FP64, so a periodic sum telescopes to FP64
+// rounding), the moment balances r[4..12) in FP32 like the volume fluxes they combine
+// with.  Returns FLAG_NONFINITE for a non-finite balance.
+__device__ __forceinline__ unsigned int balance_mixed(const Grid& g, const WorkF& f, long long c, const float* sR,
+                                                      const float* sL, const float* tT, const float* tB, double* r) {
+  unsigned int bad = 0;
+  const float gam = (float)g.gamma, rPr = (float)g.rPr, rRe = (float)g.rRe;
+  float vf[4] = {0.f, 0.f, 0.f, 0.f}, vg[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+  for (int G = 0; G < 3; G++)
+#pragma unroll
+    for (int H = 0; H < 3; H++) {
+      const int k = 3 * G + H;
+      float st[4], gs[6], fx[4], gy[4];
+#pragma unroll
+      for (int v = 0; v < 4; v++) st[v] = f.vol[(long long)(4 * k + v) * g.ps + c];
+#pragma unroll
+      for (int n = 0; n < 6; n++) gs[n] = f.gr[(long long)(6 * (12 + k) + n) * g.ps + c];
+      phys_flux<float>(0, st, gs, gam, rPr, rRe, fx);
+      phys_flux<float>(1, st, gs, gam, rPr, rRe, gy);
+      const float wgt = gweight<float>(G) * gweight<float>(H);
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        vf[v] += wgt * fx[v];
+        vg[v] += wgt * gy[v];
+      }
+    }
+  const double rdx = g.rdx, rdy = g.rdy;
+  const float rdxf = (float)g.rdx, rdyf = (float)g.rdy;
+#pragma unroll
+  for (int v = 0; v < 4; v++) {
+    const double r0 = -((double)sR[v] - (double)sL[v]) * rdx - ((double)tT[v] - (double)tB[v]) * rdy;
+    const float r1 = -(sL[v] + sR[v]) * (0.5f * rdxf) - (tT[4 + v] - tB[4 + v]) * rdyf + vf[v] * rdxf;
+    const float r2 = -(sR[4 + v] - sL[4 + v]) * rdxf - (tB[v] + tT[v]) * (0.5f * rdyf) + vg[v] * rdyf;
+    r[v] = r0;
+    r[4 + v] = (double)r1;
+    r[8 + v] = (double)r2;
+    if (!finite_d(r0) || !finite_f(r1) || !finite_f(r2)) bad = FLAG_NONFINITE;
+  }
+  return bad;
+}
+
 __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w, double* __restrict__ rhs,
                                                     Diag* diag, int gx, int gy) {
   const int i = gx;
@@ -442,52 +497,113 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
   const WorkF f = mixed_planes(w, g.ps);
   if (i < g.nx && j < g.ny) {
     const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
-    const float gam = (float)g.gamma, rPr = (float)g.rPr, rRe = (float)g.rRe;
-    float vf[4] = {0.f, 0.f, 0.f, 0.f}, vg[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-    for (int G = 0; G < 3; G++)
-#pragma unroll
-      for (int H = 0; H < 3; H++) {
-        const int k = 3 * G + H;
-        float st[4], gs[6], fx[4], gy[4];
-#pragma unroll
-        for (int v = 0; v < 4; v++) st[v] = f.vol[(long long)(4 * k + v) * g.ps + c];
-#pragma unroll
-        for (int n = 0; n < 6; n++) gs[n] = f.gr[(long long)(6 * (12 + k) + n) * g.ps + c];
-        phys_flux<float>(0, st, gs, gam, rPr, rRe, fx);
-        phys_flux<float>(1, st, gs, gam, rPr, rRe, gy);
-        const float wgt = gweight<float>(G) * gweight<float>(H);
-#pragma unroll
-        for (int v = 0; v < 4; v++) {
-          vf[v] += wgt * fx[v];
-          vg[v] += wgt * gy[v];
-        }
-      }
-    const double rdx = g.rdx, rdy = g.rdy;
-    const float rdxf = (float)g.rdx, rdyf = (float)g.rdy;
     const float* fxf = mixed_face_sums(w.fx, g.ps);
     const float* fyf = mixed_face_sums(w.fy, g.ps);
+    float sR[8], sL[8], tT[8], tB[8];
 #pragma unroll
-    for (int v = 0; v < 4; v++) {
-      // average balance in FP64 from the FP64 face sums
-      const double fR0 = w.fx[(long long)v * g.ps + c], fL0 = w.fx[(long long)v * g.ps + cl];
-      const double gT0 = w.fy[(long long)v * g.ps + c], gB0 = w.fy[(long long)v * g.ps + cb];
-      const double r0 = -(fR0 - fL0) * rdx - (gT0 - gB0) * rdy;
-      // moment balances in FP32, like the volume fluxes they combine with
-      const float sR0 = fxf[(long long)v * g.ps + c], sL0 = fxf[(long long)v * g.ps + cl];
-      const float sR1 = fxf[(long long)(4 + v) * g.ps + c], sL1 = fxf[(long long)(4 + v) * g.ps + cl];
-      const float tT0 = fyf[(long long)v * g.ps + c], tB0 = fyf[(long long)v * g.ps + cb];
-      const float tT1 = fyf[(long long)(4 + v) * g.ps + c], tB1 = fyf[(long long)(4 + v) * g.ps + cb];
-      const float r1 = -(sL0 + sR0) * (0.5f * rdxf) - (tT1 - tB1) * rdyf + vf[v] * rdxf;
-      const float r2 = -(sR1 - sL1) * rdxf - (tB0 + tT0) * (0.5f * rdyf) + vg[v] * rdyf;
-      rhs[(long long)v * g.ps + c] = r0;
-      rhs[(long long)(4 + v) * g.ps + c] = (double)r1;
-      rhs[(long long)(8 + v) * g.ps + c] = (double)r2;
-      if (!finite_d(r0) || !finite_f(r1) || !finite_f(r2)) bad = FLAG_NONFINITE;
+    for (int k = 0; k < 8; k++) {
+      sR[k] = fxf[(long long)k * g.ps + c];
+      sL[k] = fxf[(long long)k * g.ps + cl];
+      tT[k] = fyf[(long long)k * g.ps + c];
+      tB[k] = fyf[(long long)k * g.ps + cb];
     }
+    double r[12];
+    bad = balance_mixed(g, f, c, sR, sL, tT, tB, r);
+#pragma unroll
+    for (int k = 0; k < 12; k++) rhs[(long long)k * g.ps + c] = r[k];
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
+}
+
+// Stages 2 and 3 of a mixed step, after the gradients: the face flux sums of a tile of
+// FR_TX x FR_TY cells in shared memory (a face on the tile's edge is also computed by the
+// neighbouring tile, with the same operations on the same data, so both cells of a face
+// difference the same value and conservation is kept), then the balances and the stage
+// update of the tile's cells.  The residual and the face sums never go to HBM.  The
+// arithmetic is that of flux_mixed_body, assemble_mixed_body and rk_body, so the result
+// equals theirs bit for bit.  Stage 1 cannot be fused this way: its step size needs
+// alpha* over every face first, and its residual is kept for restarts.
+constexpr int FR_TX = 32, FR_TY = 7, FR_THREADS = 256;
+static_assert((FR_TX + 1) * FR_TY <= FR_THREADS && FR_TX * (FR_TY + 1) <= FR_THREADS, "one face per thread");
+
+// the tile's face sums: x-face right of cell (i0 - 1 + a, j0 + b) at sx[k][b][a], y-face
+// above cell (i0 + a, j0 - 1 + b) at sy[k][b][a], k = S0 (0-3), S1 (4-7)
+struct FluxTile {
+  float sx[8][FR_TY][FR_TX + 1];
+  float sy[8][FR_TY + 1][FR_TX];
+};
+
+// thread t's x-face and y-face of the tile at (i0, j0)
+__device__ __forceinline__ void flux_tile_faces(const Grid& g, const WorkF& f, int i0, int j0, int t, FluxTile& ft,
+                                                float& amax, float& bmax) {
+  if (t < (FR_TX + 1) * FR_TY) {
+    const int a = t % (FR_TX + 1), b = t / (FR_TX + 1);
+    const int i = i0 - 1 + a, j = j0 + b;
+    if (i < g.nx && j < g.ny) {
+      float S[8];
+      bmax = fmaxf(bmax, face_sums_mixed(g, f, 0, cidx(g, i, j), cidx(g, i + 1, j), S, S + 4, amax));
+#pragma unroll
+      for (int k = 0; k < 8; k++) ft.sx[k][b][a] = S[k];
+    }
+  }
+  if (t < FR_TX * (FR_TY + 1)) {
+    const int a = t % FR_TX, b = t / FR_TX;
+    const int i = i0 + a, j = j0 - 1 + b;
+    if (i < g.nx && j < g.ny) {
+      float S[8];
+      bmax = fmaxf(bmax, face_sums_mixed(g, f, 1, cidx(g, i, j), cidx(g, i, j + 1), S, S + 4, amax));
+#pragma unroll
+      for (int k = 0; k < 8; k++) ft.sy[k][b][a] = S[k];
+    }
+  }
+}
+
+// thread t's cell of the tile: its balances from the tile's face sums and its stage
+// update; returns the flags, and the kinetic share at stage 3 in kef
+__device__ __forceinline__ unsigned int flux_tile_cell(const Grid& g, const WorkF& f, int i0, int j0, int t,
+                                                       const FluxTile& ft, int stage, double dt,
+                                                       const double* __restrict__ qin, const double* __restrict__ mom,
+                                                       double* __restrict__ base, double* __restrict__ qout,
+                                                       float* __restrict__ hilo, double& kef) {
+  if (t >= FR_TX * FR_TY) return 0;
+  const int a = t % FR_TX, b = t / FR_TX;
+  const int i = i0 + a, j = j0 + b;
+  if (i >= g.nx || j >= g.ny) return 0;
+  float sR[8], sL[8], tT[8], tB[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    sR[k] = ft.sx[k][b][a + 1];
+    sL[k] = ft.sx[k][b][a];
+    tT[k] = ft.sy[k][b + 1][a];
+    tB[k] = ft.sy[k][b][a];
+  }
+  const long long c = cidx(g, i, j);
+  double r[12];
+  unsigned int bad = balance_mixed(g, f, c, sR, sL, tT, tB, r);
+  bad |= rk_cell<true, true>(g, stage, c, dt, qin, mom, r, base, qout, hilo, kef);
+  return bad;
+}
+
+__global__ void __launch_bounds__(FR_THREADS) k_flux_rk_mixed(Grid g, Work w, int stage, const double* __restrict__ qin,
+                                                               const double* __restrict__ mom, double* __restrict__ base,
+                                                               double* __restrict__ qout, Diag* diag,
+                                                               float* __restrict__ hilo) {
+  __shared__ FluxTile ft;
+  const WorkF f = mixed_planes(w, g.ps);
+  const int i0 = blockIdx.x * FR_TX, j0 = blockIdx.y * FR_TY, t = threadIdx.x;
+  float amax = 0.f, bmax = 0.f;
+  flux_tile_faces(g, f, i0, j0, t, ft, amax, bmax);
+  amax = warp_max(amax);
+  bmax = warp_max(bmax);
+  if (lane_id() == 0) {
+    atomic_max_pos(&diag->alpha_bits, (double)amax);
+    atomic_max_pos(&diag->beta_bits, (double)bmax);
+  }
+  __syncthreads();
+  double kef = 0.0;
+  const unsigned int bad = flux_tile_cell(g, f, i0, j0, t, ft, stage, diag->dt, qin, mom, base, qout, hilo, kef);
+  rk_reduce<true>(stage, bad, kef, diag);
 }
 
 // float planes back to a contiguous double array (debug output of the mixed path)

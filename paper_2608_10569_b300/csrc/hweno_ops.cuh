@@ -559,10 +559,62 @@ __device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, doub
 //   stage 2: out = 3/4 base + 1/4 ([u^(1); vhat^(1)] + dt F)
 //   stage 3: out = 1/3 base + 2/3 ([u^(2); vhat^(2)] + dt F)
 // plus the admissibility test of the output averages (Sec. 5).
+// The SSP-RK3 stage update of one cell from its 12 residual values f (Eq. (2.12) in
+// its 2D form): writes qout, and the base at stage 1; returns FLAG_INADMISSIBLE when the
+// new cell average is not admissible or not finite.
 // SPLIT (mixed path): also write the hi/lo split of the new state (24 float planes at
 // hilo), so that the next evaluation needs no separate split pass.
-// KEF (mixed handles): at stage 3, also the largest kinetic share |m|^2 / (2 rho E) of
-// the new state over the cells, the measure that routes a mixed handle's next step
+// KEF (mixed handles): at stage 3, also the kinetic share |m|^2 / (2 rho E) of the new
+// state in kef, the measure that routes a mixed handle's next step
+template <bool SPLIT = false, bool KEF = false>
+__device__ __forceinline__ unsigned int rk_cell(const Grid& g, int stage, long long c, double dt,
+                                                const double* __restrict__ qin, const double* __restrict__ mom,
+                                                const double* f, double* __restrict__ base,
+                                                double* __restrict__ qout, float* __restrict__ hilo, double& kef) {
+  unsigned int bad = 0;
+  double out[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    const double cur = k < 4 ? qin[(long long)k * g.ps + c] : mom[(long long)(k - 4) * g.ps + c];
+    if (stage == 1) {
+      base[(long long)k * g.ps + c] = cur;
+      out[k] = cur + dt * f[k];
+    } else if (stage == 2) {
+      out[k] = 0.75 * base[(long long)k * g.ps + c] + 0.25 * (cur + dt * f[k]);
+    } else {
+      out[k] = base[(long long)k * g.ps + c] * (1.0 / 3.0) + (2.0 / 3.0) * (cur + dt * f[k]);
+    }
+    qout[(long long)k * g.ps + c] = out[k];
+    if constexpr (SPLIT) {
+      float hi, lo;
+      split_hilo(out[k], hi, lo);
+      hilo[(long long)k * g.ps + c] = hi;
+      hilo[(long long)(12 + k) * g.ps + c] = lo;
+    }
+    if (!finite_d(out[k])) bad = FLAG_INADMISSIBLE;
+  }
+  // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
+  const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
+  if (!(out[0] > 0.0) || !(rp > 0.0)) bad = FLAG_INADMISSIBLE;
+  if constexpr (KEF) {
+    if (stage == 3) kef = (out[0] > 0.0 && rp > 0.0) ? 1.0 - rp / (out[3] * out[0]) : 1.0;
+  }
+  return bad;
+}
+
+// the warp's flags and (KEF, stage 3) kinetic shares into the step's reductions
+template <bool KEF>
+__device__ __forceinline__ void rk_reduce(int stage, unsigned int bad, double kef, Diag* diag) {
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
+  if constexpr (KEF) {
+    if (stage == 3) {
+      kef = warp_max(fmax(kef, 0.0));
+      if (lane_id() == 0) atomic_max_pos(&diag->kefrac_bits, kef);
+    }
+  }
+}
+
 template <bool SPLIT = false, bool KEF = false>
 __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* __restrict__ qin,
                                         const double* __restrict__ mom, const double* __restrict__ rhs,
@@ -574,44 +626,12 @@ __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* 
   double kef = 0.0;
   if (i < g.nx && j < g.ny) {
     const long long c = cidx(g, i, j);
-    const double dt = diag->dt;
-    double out[12];
+    double f[12];
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      const double cur = k < 4 ? qin[(long long)k * g.ps + c] : mom[(long long)(k - 4) * g.ps + c];
-      const double f = rhs[(long long)k * g.ps + c];
-      if (stage == 1) {
-        base[(long long)k * g.ps + c] = cur;
-        out[k] = cur + dt * f;
-      } else if (stage == 2) {
-        out[k] = 0.75 * base[(long long)k * g.ps + c] + 0.25 * (cur + dt * f);
-      } else {
-        out[k] = base[(long long)k * g.ps + c] * (1.0 / 3.0) + (2.0 / 3.0) * (cur + dt * f);
-      }
-      qout[(long long)k * g.ps + c] = out[k];
-      if constexpr (SPLIT) {
-        float hi, lo;
-        split_hilo(out[k], hi, lo);
-        hilo[(long long)k * g.ps + c] = hi;
-        hilo[(long long)(12 + k) * g.ps + c] = lo;
-      }
-      if (!finite_d(out[k])) bad = FLAG_INADMISSIBLE;
-    }
-    // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
-    const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
-    if (!(out[0] > 0.0) || !(rp > 0.0)) bad = FLAG_INADMISSIBLE;
-    if constexpr (KEF) {
-      if (stage == 3) kef = (out[0] > 0.0 && rp > 0.0) ? 1.0 - rp / (out[3] * out[0]) : 1.0;
-    }
+    for (int k = 0; k < 12; k++) f[k] = rhs[(long long)k * g.ps + c];
+    bad = rk_cell<SPLIT, KEF>(g, stage, c, diag->dt, qin, mom, f, base, qout, hilo, kef);
   }
-  bad = __reduce_or_sync(0xffffffffu, bad);
-  if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
-  if constexpr (KEF) {
-    if (stage == 3) {
-      kef = warp_max(fmax(kef, 0.0));
-      if (lane_id() == 0) atomic_max_pos(&diag->kefrac_bits, kef);
-    }
-  }
+  rk_reduce<KEF>(stage, bad, kef, diag);
 }
 
 }  // namespace hw

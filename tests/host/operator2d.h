@@ -9,6 +9,7 @@
 #include <vector>
 #include "hweno_mixed.cuh"
 #include "hweno_source.cuh"
+#include "hweno_tma.cuh"
 
 namespace hw {
 double cons_smem[CONS_SMEM_BYTES / sizeof(double)];
@@ -41,31 +42,102 @@ struct Scratch {
   }
 };
 
+// k_grad_tma_mixed on the host: per tile, the two boxes the tensor copies bring into
+// shared memory (copied here from the float planes, zero outside them, as the copies
+// fill), then the weak moments of the grown tile and the gradients of the tile's cells
+inline void grad_tma_emulated(const hweno_config& c, const Grid& g, const Work& w) {
+  const WorkF f = mixed_planes(w, g.ps);
+  const long long rows = g.ny + 2 * NG;
+  std::vector<float> sm(GT_TR_FLOATS + GT_WB_FLOATS + GT_R_FLOATS);
+  const int ntx = (g.nx + 2 + GT_X - 1) / GT_X, nty = (g.ny + 2 + GT_Y - 1) / GT_Y;
+  for (int by = 0; by < nty; by++)
+    for (int bx = 0; bx < ntx; bx++) {
+      const int a = -1 + GT_X * bx, b = -1 + GT_Y * by;
+      const long long x0 = GT_X * bx, y0 = b - 2 + NG;
+      auto fetch = [&](const float* plane, long long y, long long x) {
+        return (x < g.pitch && y < rows) ? plane[y * g.pitch + x] : 0.0f;
+      };
+      for (int k = 0; k < 12; k++)
+        for (int n = 0; n < 3; n++)
+          for (int y = 0; y < GB_Y; y++)
+            for (int x = 0; x < GB_X; x++)
+              sm[((k * 3 + n) * GB_Y + y) * GB_X + x] = fetch(f.face + (long long)(4 * k + 1 + n) * g.ps, y0 + y, x0 + x);
+      for (int n = 0; n < 3; n++)
+        for (int y = 0; y < GB_Y; y++)
+          for (int x = 0; x < GB_X; x++)
+            sm[GT_TR_FLOATS + (n * GB_Y + y) * GB_X + x] = fetch(f.wbar + (long long)n * g.ps, y0 + y, x0 + x);
+      GradTile tt{sm.data(), sm.data() + GT_TR_FLOATS, sm.data() + GT_TR_FLOATS + GT_WB_FLOATS};
+      for (int k = 0; k < GR_X * GR_Y; k++) gradtile_weak_cell(g, tt, k % GR_X, k / GR_X);
+      for (int t = 0; t < GT_THREADS; t++) {
+        const int tx = t % GT_X, ty = t / GT_X, i = a + tx, j = b + ty;
+        if (i < g.nx + 1 && j < g.ny + 1) {
+          if (c.linear_grad) gradtile_grad_cell<true>(g, w, tt, tx, ty, i, j);
+          else gradtile_grad_cell<false>(g, w, tt, tx, ty, i, j);
+        }
+      }
+    }
+}
+
+// the mixed path up to the gradients at state q (ghost cells already filled): the split
+// of the ghost-filled state (k_split), traces, face and weak moments, gradients (tma: as
+// k_grad_tma_mixed forms the last three)
+inline void mixed_front(const hweno_config& c, const Grid& g, Scratch& s, double* q, double* mom, Diag* diag,
+                        bool tma = false) {
+  const int nx = g.nx, ny = g.ny;
+  Work& w = s.w;
+  float* hilo = mixed_planes(w, g.ps).hilo;
+  const long long np = 12 * g.ps;
+  for (long long k = 0; k < np; k++) split_hilo(q[k], hilo[k], hilo[np + k]);
+  for (int gy = 0; gy < ny + 6; gy++)
+    for (int gx = 0; gx < nx + 6; gx++) cons_mixed_body(g, q, w, mom, diag, gx, gy);
+  if (tma) {
+    grad_tma_emulated(c, g, w);
+    return;
+  }
+  for (int gz = 0; gz < 2; gz++)
+    for (int gy = 0; gy < ny + 5; gy++)
+      for (int gx = 0; gx < nx + 5; gx++) face_moments_mixed_body(g, w, gx, gy, gz);
+  for (int gy = 0; gy < ny + 4; gy++)
+    for (int gx = 0; gx < nx + 4; gx++) weak_moments_mixed_body(g, w, gx, gy);
+  for (int gy = 0; gy < ny + 2; gy++)
+    for (int gx = 0; gx < nx + 2; gx++) {
+      if (c.linear_grad) grad_mixed_body<true>(g, w, gx, gy);
+      else grad_mixed_body(g, w, gx, gy);
+    }
+}
+
+// stage 2 or 3 of a mixed step as k_flux_rk_mixed runs it: the front at q (ghosts filled
+// here), then per tile the face sums of every thread of the block, then every thread's
+// cell (the barrier between the two phases)
+inline void fused_stage(const hweno_config& c, const Grid& g, const Open& o, Scratch& s, double* q, double* mom,
+                        double* base, double* qout, int stage, Diag* diag, bool tma) {
+  for (int k = 0; k < 8 * g.ny; k++) ghost_x_body(g, &o, q, k);
+  for (int k = 0; k < 8 * (g.nx + 2 * NG); k++) ghost_y_body(g, &o, q, k);
+  mixed_front(c, g, s, q, mom, diag, tma);
+  const WorkF f = mixed_planes(s.w, g.ps);
+  std::vector<float> hilo_out(24 * (size_t)g.ps);
+  static FluxTile ft;
+  for (int j0 = 0; j0 < g.ny; j0 += FR_TY)
+    for (int i0 = 0; i0 < g.nx; i0 += FR_TX) {
+      float amax = 0.f, bmax = 0.f;
+      for (int t = 0; t < FR_THREADS; t++) flux_tile_faces(g, f, i0, j0, t, ft, amax, bmax);
+      for (int t = 0; t < FR_THREADS; t++) {
+        double kef = 0.0;
+        diag->flags |= flux_tile_cell(g, f, i0, j0, t, ft, stage, diag->dt, q, mom, base, qout, hilo_out.data(), kef);
+      }
+    }
+}
+
 // one evaluation at state q (12 padded planes, ghosts filled here): rhs (12) and the
 // modified moments mom (8); the source term, when configured, at time t
 inline void residual(const hweno_config& c, const Grid& g, const Open& o, const Quad4& quad, Scratch& s,
-                     double* q, double* rhs, double* mom, Diag* diag, double t, bool mixed) {
+                     double* q, double* rhs, double* mom, Diag* diag, double t, bool mixed, bool tma = false) {
   const int nx = g.nx, ny = g.ny;
   Work& w = s.w;
   for (int k = 0; k < 8 * ny; k++) ghost_x_body(g, &o, q, k);
   for (int k = 0; k < 8 * (nx + 2 * NG); k++) ghost_y_body(g, &o, q, k);
   if (mixed) {
-    // the split of the ghost-filled state (k_split), then the FP32 bodies
-    float* hilo = mixed_planes(w, g.ps).hilo;
-    const long long np = 12 * g.ps;
-    for (long long k = 0; k < np; k++) split_hilo(q[k], hilo[k], hilo[np + k]);
-    for (int gy = 0; gy < ny + 6; gy++)
-      for (int gx = 0; gx < nx + 6; gx++) cons_mixed_body(g, q, w, mom, diag, gx, gy);
-    for (int gz = 0; gz < 2; gz++)
-      for (int gy = 0; gy < ny + 5; gy++)
-        for (int gx = 0; gx < nx + 5; gx++) face_moments_mixed_body(g, w, gx, gy, gz);
-    for (int gy = 0; gy < ny + 4; gy++)
-      for (int gx = 0; gx < nx + 4; gx++) weak_moments_mixed_body(g, w, gx, gy);
-    for (int gy = 0; gy < ny + 2; gy++)
-      for (int gx = 0; gx < nx + 2; gx++) {
-        if (c.linear_grad) grad_mixed_body<true>(g, w, gx, gy);
-        else grad_mixed_body(g, w, gx, gy);
-      }
+    mixed_front(c, g, s, q, mom, diag, tma);
     for (int gz = 0; gz < 2; gz++)
       for (int gy = 0; gy < ny + 1; gy++)
         for (int gx = 0; gx < nx + 1; gx++) flux_mixed_body(g, w, diag, gx, gy, gz);
@@ -105,11 +177,13 @@ inline void residual(const hweno_config& c, const Grid& g, const Open& o, const 
 }
 
 // the configuration record of the harnesses' input files: 11 ints (nx, ny, bc[4], scheme,
-// source, linear_grad, nan_fill, mixed), 50 doubles (x0, x1, y0, y1, gamma, Pr, Re,
+// source, linear_grad, nan_fill, mixed: 0 FP64, 1 mixed, 2 mixed with stages 2 and 3 fused, 3 that and the
+// TMA-staged gradients), 50 doubles (x0, x1, y0, y1, gamma, Pr, Re,
 // eps_pp, eps_weno, t, inflow[4][2][4], band[4][2])
 struct Input {
   hweno_config c;
-  bool nan_fill, mixed;
+  bool nan_fill, mixed, fused;  // fused: the mixed path with stages 2 and 3 fused
+  bool tma;                     // the mixed path's gradients as k_grad_tma_mixed forms them
   double t;
 };
 inline bool read_input(FILE* f, Input& in) {
@@ -126,6 +200,8 @@ inline bool read_input(FILE* f, Input& in) {
   c.linear_grad = hi[8];
   in.nan_fill = hi[9] != 0;
   in.mixed = hi[10] != 0;
+  in.fused = hi[10] >= 2;
+  in.tma = hi[10] == 3;
   c.x0 = hd[0]; c.x1 = hd[1]; c.y0 = hd[2]; c.y1 = hd[3];
   c.gamma = hd[4]; c.Pr = hd[5]; c.Re = hd[6]; c.eps_pp = hd[7]; c.eps_weno = hd[8];
   in.t = hd[9];

@@ -4,7 +4,8 @@
 // the three stage updates with their evaluations, then the flags; an attempt whose stage
 // output is inadmissible or not finite is repeated with dt / 2, at most max_halvings
 // times.  FP64, or the mixed path (each evaluation splits its ghost-filled state: the
-// split a handle's stage update writes, ghost-filled, is the same).  Input: the
+// split a handle's stage update writes, ghost-filled, is the same), or the mixed path
+// with stages 2 and 3 as its fused kernel runs them.  Input: the
 // configuration record of operator2d.h, then an int nsteps,
 // doubles cfl, b_visc, dt_forced, an int max_halvings, and q[12][ny][nx].  Output
 // (doubles): q[12][ny][nx] after the steps taken, the status (0, or -3 when a step stays
@@ -55,7 +56,7 @@ int main(int argc, char** argv) {
   for (int step = 0; step < nsteps && !status; step++) {
     Diag d[2];  // the attempt's counters and flags, and the stage-1 ones
     memset(d, 0, sizeof(d));
-    residual(c, g, o, quad, s, Q.data(), RHS0.data(), MOM0.data(), &d[0], t, in.mixed);
+    residual(c, g, o, quad, s, Q.data(), RHS0.data(), MOM0.data(), &d[0], t, in.mixed, in.tma);
     double alpha;
     memcpy(&alpha, &d[0].alpha_bits, sizeof(alpha));
     d[0].dt = dt_forced > 0.0 ? dt_forced : fmin(cfl * hmin / alpha, b_visc * c.Re * hmin * hmin);
@@ -65,10 +66,15 @@ int main(int argc, char** argv) {
       d[0].flags = 0;
       const double dt = d[0].dt;
       stage(1, Q.data(), MOM0.data(), RHS0.data(), Q1.data(), &d[0]);
-      residual(c, g, o, quad, s, Q1.data(), RHS.data(), MOM.data(), &d[0], t + dt, in.mixed);
-      stage(2, Q1.data(), MOM.data(), RHS.data(), Q2.data(), &d[0]);
-      residual(c, g, o, quad, s, Q2.data(), RHS.data(), MOM.data(), &d[0], t + 0.5 * dt, in.mixed);
-      stage(3, Q2.data(), MOM.data(), RHS.data(), QS.data(), &d[0]);
+      if (in.fused) {  // stages 2 and 3 as the mixed path's fused kernel runs them
+        fused_stage(c, g, o, s, Q1.data(), MOM.data(), BASE.data(), Q2.data(), 2, &d[0], in.tma);
+        fused_stage(c, g, o, s, Q2.data(), MOM.data(), BASE.data(), QS.data(), 3, &d[0], in.tma);
+      } else {
+        residual(c, g, o, quad, s, Q1.data(), RHS.data(), MOM.data(), &d[0], t + dt, in.mixed);
+        stage(2, Q1.data(), MOM.data(), RHS.data(), Q2.data(), &d[0]);
+        residual(c, g, o, quad, s, Q2.data(), RHS.data(), MOM.data(), &d[0], t + 0.5 * dt, in.mixed);
+        stage(3, Q2.data(), MOM.data(), RHS.data(), QS.data(), &d[0]);
+      }
       if (d[1].flags & FLAG_NONFINITE) {
         status = -4;
         break;

@@ -1,7 +1,10 @@
 """Batched ensembles (hweno_batch_*): every case of a batch must follow exactly the
-steps its own single-grid solver takes (same kernels, same per-case time step), in
-FP64 and in the mixed path, also after the autotuner changed the tile shapes, and with
-per-case restarts."""
+steps its own single-grid solver takes (same per-cell bodies, same per-case time step),
+in FP64 and in the mixed path, also after the autotuner changed the tile shapes, and with
+per-case restarts.  In the mixed path a single handle forms the gradients in the
+TMA-staged kernel and a batch in the separate face-moment, weak-moment and gradient
+kernels: the same FP32 expressions, compiled to the same operations, so the states
+agree bit for bit there too."""
 import numpy as np
 import pytest
 

@@ -58,7 +58,8 @@ def run(exe, tmp_path, p, q, mode, t0=0.0, t_end=0.0, max_steps=0, dt=0.0):
     hdr = [n, BC[p["bc"][0]], BC[p["bc"][1]], 1 if p.get("scheme") == "dr" else 0, p.get("source", 0),
            p.get("max_halvings", 60), mode]
     inflow = p.get("inflow", ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)))
-    dh = ([p["x0"], p["x1"], p["gamma"], p["Pr"], p["Re"], 0.6, 1e-3, 1e-12, 1e-8] + list(inflow[0]) +
+    dh = ([p["x0"], p["x1"], p["gamma"], p["Pr"], p["Re"], p.get("cfl", 0.6), p.get("b_visc", 1e-3),
+           p.get("eps_pp", 1e-12), p.get("eps_weno", 1e-8)] + list(inflow[0]) +
           list(inflow[1]) + [t0, t_end, float(max_steps), dt])
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(fin, "wb") as f:

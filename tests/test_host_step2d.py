@@ -52,7 +52,8 @@ def steps(exe, tmp_path, case, q, nsteps, t=0.0, dt=0.0, mixed=False, **kw):
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(fin, "wb") as f:
         f.write(struct.pack("11i", nx, ny, *[BC[b] for b in p["bc"]], 1 if p.get("scheme") == "dr" else 0,
-                            int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 0, 1 if mixed else 0))
+                            int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 0,
+                            {"fused": 2, "tma": 3}.get(mixed, 1 if mixed else 0)))
         f.write(struct.pack("50d", p["x0"], p["x1"], p["y0"], p["y1"], p["gamma"], p["Pr"], p["Re"], p["eps_pp"],
                             p["eps_weno"], t, *st, *bd))
         f.write(struct.pack("i", nsteps))
@@ -147,3 +148,24 @@ def test_mixed_run_through_open_faces(exe, tmp_path):
     assert status == 0 and len(log) == 20
     assert abs(sum(a for a, _ in log) - st["t"]) <= 1e-6 * st["t"]
     assert rel_l1(qh, qo) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["rough_walls", "open_jet", "taylor_green"])
+def test_fused_mixed_stages_equal_the_separate_kernels(exe, tmp_path, name):
+    """stages 2 and 3 of a mixed step as k_flux_rk_mixed runs them (a tile's face sums in
+    shared memory, then the balances and the stage update of its cells), and the
+    gradients as k_grad_tma_mixed forms them, give the same steps as the separate face
+    moment, weak moment, gradient, flux, balance and stage-update kernels, bit for bit:
+    step sizes, restarts and states, on ragged tiles (no multiples of the tile sizes)"""
+    case, q = {"rough_walls": lambda: I.random_rough(45, 23, seed=3, bc=("noslip", "noslip", "noslip", "symmetry")),
+               "open_jet": y_jet,
+               "taylor_green": lambda: I.taylor_green(40, 0.4, 300.0, 1 / 1.4, rho_pert=1e-2)}[name]()
+    qa, sa, la = steps(exe, tmp_path, case, q, 4, mixed=True)
+    qb, sb, lb = steps(exe, tmp_path, case, q, 4, mixed="fused")
+    assert sa == sb == 0 and la == lb
+    assert np.array_equal(qa, qb)
+    # and with the gradients formed as k_grad_tma_mixed forms them (its two boxes staged,
+    # zero outside the planes), in every evaluation of the step
+    qc, sc, lc = steps(exe, tmp_path, case, q, 4, mixed="tma")
+    assert sc == 0 and lc == la
+    assert np.array_equal(qa, qc)
