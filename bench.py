@@ -68,8 +68,13 @@ ALG_FLOPS = {
 # the phases each kernel of the FP64 GR operator performs
 KERNEL_PHASES = {"cons_recon": ("traces", "limiter"), "grad_recon": ("gradients",),
                  "flux": ("face_fluxes", "alpha"), "assemble": ("balances",)}
-# phases the mixed path keeps in FP64: the limiter's checks and theta solve, the stage update
-MIXED_FP64_PHASES = ("limiter", "stage_update")
+# the FP64 operations the mixed path keeps per interior cell-stage, counted from its
+# expressions as the oracle's counter counts (an add or a multiply each): the average
+# balances from the FP64 face sums (4 variables x 2 differences, 2 products and a sum),
+# the averages' stage update (4 x (2 + 5 + 5) / 3 over the three stages) and the
+# admissibility test (6).  The moments update in FP32, and the limiter's FP64 route runs
+# only for the cells the FP32 filter cannot clear (the run's pp_percent).
+MIXED_FP64_PER_CELL_STAGE = 4 * 5 + 4 * (2 + 5 + 5) / 3.0 + 6
 
 # FP64 flops the kernels themselves execute per processed cell (DADD + DMUL + 2 DFMA,
 # counted by ncu on the 256x128 shock tube): the pipe-efficiency view beside the
@@ -948,10 +953,11 @@ def main():
         s64.close()
         l1 = float(np.abs(qm[0] - q64[0]).sum() / np.abs(q64[0]).sum())
         linf = float(np.abs(qm[0] - q64[0]).max() / np.abs(q64[0]).max())
-        # the mixed step's roofline on the same algorithmic basis: the FP32 phases against
-        # the measured FP32 FMA peak, the FP64 phases against the FP64 one, the unfused
-        # bytes against the HBM bandwidth; the slowest bounds the cell-stage rate
-        f64 = alg_flops("gr", MIXED_FP64_PHASES)
+        # the mixed step's roofline on the same algorithmic basis: the oracle's operations
+        # less those the mixed path keeps in FP64 against the measured FP32 FMA peak, those
+        # against the FP64 one, the unfused bytes against the HBM bandwidth; the slowest
+        # bounds the cell-stage rate
+        f64 = MIXED_FP64_PER_CELL_STAGE
         f32 = alg_flops("gr") - f64
         hbm = MEASURED_HBM_GBS()
         bound_rate = min(peak32 * 1e12 / f32, peak64 * 1e12 / f64,

@@ -428,6 +428,30 @@ static bool encode_trace_maps(const Grid& g, const Work& w, CUtensorMap* tr, CUt
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// the mixed path's face moments, weak-derivative moments and gradients in separate
+// kernels through HBM, from the traces in the handle's planes; volg: also the gradients
+// at the volume points (the debug export; the operator needs only their sums)
+static void mixed_grad_separate(hweno_handle* h, bool volg) {
+  const Grid& g = h->g;
+  {
+    Prof p(h, K_FACEMOM);
+    k_face_moments_mixed<<<grid2(g.nx + 5, g.ny + 5, 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
+  }
+  {
+    Prof p(h, K_WEAK);
+    k_weak_moments_mixed<<<grid2(g.nx + 4, g.ny + 4), dim3(BX, BY), 0, h->st>>>(g, h->w);
+  }
+  Prof p(h, K_GRAD);
+  const dim3 grid = grid2(g.nx + 2, g.ny + 2), blk(BX, BY);
+  if (h->cfg.linear_grad) {
+    if (volg) k_grad_mixed<true, true><<<grid, blk, 0, h->st>>>(g, h->w);
+    else k_grad_mixed<true><<<grid, blk, 0, h->st>>>(g, h->w);
+  } else {
+    if (volg) k_grad_mixed<false, true><<<grid, blk, 0, h->st>>>(g, h->w);
+    else k_grad_mixed<false><<<grid, blk, 0, h->st>>>(g, h->w);
+  }
+}
+
 // the mixed path's operator up to the gradients: ghost cells (and the FP32 split of a
 // state set from outside), traces and limiter, then face moments, weak-derivative
 // moments and gradients (one TMA-staged kernel where the handle has the tensor maps)
@@ -456,21 +480,7 @@ static void mixed_front(hweno_handle* h, double* q, double* mom) {
       k_grad_tma_mixed<false><<<grid, GT_THREADS, GT_SMEM_BYTES, h->st>>>(g, h->w, h->tr_map, h->wb_map, h->d_diag);
     return;
   }
-  {
-    Prof p(h, K_FACEMOM);
-    k_face_moments_mixed<<<grid2(g.nx + 5, g.ny + 5, 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
-  }
-  {
-    Prof p(h, K_WEAK);
-    k_weak_moments_mixed<<<grid2(g.nx + 4, g.ny + 4), dim3(BX, BY), 0, h->st>>>(g, h->w);
-  }
-  {
-    Prof p(h, K_GRAD);
-    if (h->cfg.linear_grad)
-      k_grad_mixed<true><<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
-    else
-      k_grad_mixed<<<grid2(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, h->st>>>(g, h->w);
-  }
+  mixed_grad_separate(h, false);
 }
 
 static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, double cst = 0.0) {
@@ -479,11 +489,8 @@ static int residual_eval(hweno_handle* h, double* q, double* rhs, double* mom, d
     mixed_front(h, q, mom);
     {
       Prof p(h, K_FLUX);
-      k_flux_mixed<<<grid2(g.nx + 1, g.ny + 1, 2), dim3(BX, BY), 0, h->st>>>(g, h->w, h->d_diag);
-    }
-    {
-      Prof p(h, K_ASSEMBLE);
-      k_assemble_mixed<<<grid2(g.nx, g.ny), dim3(BX, BY), 0, h->st>>>(g, h->w, rhs, h->d_diag);
+      const dim3 grid((unsigned)((g.nx + FR_TX - 1) / FR_TX), (unsigned)((g.ny + FR_TY - 1) / FR_TY));
+      k_flux_asm_mixed<<<grid, FR_THREADS, 0, h->st>>>(g, h->w, rhs, h->d_diag);
     }
   } else if (h->cfg.scheme == HWENO_SCHEME_DR) {
     launch_ghost(h, q);
@@ -1032,8 +1039,12 @@ int hweno_debug_fields(hweno_handle* h, int which, double* out, int on_device) {
   const long long N = (long long)g.nx * g.ny;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (h->cfg.precision == HWENO_MIXED && !h->route64 && which <= 3) {
-    // FP32 intermediates of the mixed path, widened to FP64
+    // FP32 intermediates of the mixed path, widened to FP64; the weak moments and the
+    // full gradient field from the separate kernels (the TMA-staged pass keeps the weak
+    // moments in shared memory, and the operator's passes write no volume-point
+    // gradients), on the traces of the last evaluation: the same values
     const WorkF f = mixed_planes(h->w, g.ps);
+    if (which >= 2) mixed_grad_separate(h, true);
     if (which <= 1) {
       const int npts = which == 0 ? 12 : 9;
       const float* src = which == 0 ? f.face : f.vol;
@@ -1419,7 +1430,7 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 // kernel for all cases, one CUDA graph per SSP-RK3 step of the whole ensemble.
 
 namespace {
-enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_FR, BR_N };
+enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_FR, BR_FRA, BR_N };
 
 struct BatchList {
   int bx = 32, by = 4;  // block shape of the kernels that use this list
@@ -1476,7 +1487,7 @@ static void region_of(int k, const Grid& g, int& wx, int& wy, int& wz) {
     case BR_WEAK: wx = g.nx + 4; wy = g.ny + 4; break;
     case BR_GRAD: wx = g.nx + 2; wy = g.ny + 2; break;
     case BR_FLUX: wx = g.nx + 1; wy = g.ny + 1; wz = 2; break;
-    case BR_INT: case BR_FR: wx = g.nx; wy = g.ny; break;
+    case BR_INT: case BR_FR: case BR_FRA: wx = g.nx; wy = g.ny; break;
     case BR_GX: wx = 8 * g.ny; wy = 1; break;
     case BR_GY: wx = 8 * (g.nx + 2 * NG); wy = 1; break;
     default: wx = (int)(12 * g.ps); wy = 1; break;  // BR_SPLIT
@@ -1550,9 +1561,9 @@ static void batch_enqueue_step(hweno_batch* b) {
         b->launches++;
         continue;
       }
-      kb_flux<1><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
-      kb_assemble<1><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
-      b->launches += 2;
+      // a kept residual: fluxes and balances in one tile kernel
+      kb_flux_asm_mixed<<<grid(BR_FRA), FR_THREADS, 0, b->st>>>(b->d_cases, b->L[BR_FRA].tl(), n, which);
+      b->launches++;
     } else if (b->dr) {
       kb_cons<0, true><<<grid(BR_CONS), dims(BR_CONS), CONS_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_CONS].tl(),
                                                                                  n, which);
@@ -1600,6 +1611,7 @@ static int batch_grids(hweno_batch* b) {
     b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<1>, b->L[BR_FLUX].total);
     b->L[BR_INT].grid = persistent_grid(b, kb_assemble<1>, b->L[BR_INT].total);
     b->L[BR_FR].grid = persistent_grid(b, kb_flux_rk_mixed, b->L[BR_FR].total, 0, FR_THREADS);
+    b->L[BR_FRA].grid = persistent_grid(b, kb_flux_asm_mixed, b->L[BR_FRA].total, 0, FR_THREADS);
   } else if (b->dr) {
     b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0, true>, b->L[BR_CONS].total, CONS_SMEM_BYTES);
     b->L[BR_GRAD].grid = persistent_grid(b, kb_dr, b->L[BR_GRAD].total, DR_SMEM_BYTES, DR_THREADS);
@@ -1720,7 +1732,7 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
   }
   for (int k = 0; k < BR_N && !rc; k++) {
     if (b->dr && k == BR_GRAD) rc = build_list(b, k, 32, DR_THREADS / 32);  // kb_dr's block
-    else if (k == BR_FR) rc = build_list(b, k, FR_TX, FR_TY);             // kb_flux_rk_mixed's tiles
+    else if (k == BR_FR || k == BR_FRA) rc = build_list(b, k, FR_TX, FR_TY);  // the mixed tile kernels
     else rc = build_list(b, k, k <= BR_INT ? 32 : 128, k <= BR_INT ? 4 : 1);
   }
   if (!rc) rc = batch_grids(b);

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(128) kb_rk(const CaseDev* __restrict__ cases, 
 // face sums of FR_TX x FR_TY cells in shared memory, then the balances and the in-place
 // stage update of QS) over a work list of (case, tile) items, the same arithmetic as a
 // single handle's stage
-__global__ void __launch_bounds__(FR_THREADS) kb_flux_rk_mixed(const CaseDev* __restrict__ cases, TileList L,
+__global__ void __launch_bounds__(FR_THREADS, HWENO_FR_MIN_BLOCKS) kb_flux_rk_mixed(const CaseDev* __restrict__ cases, TileList L,
                                                                 int ncase, int stage) {
   __shared__ FluxTile ft;
   const int total = L.start[ncase];
@@ -174,17 +174,44 @@ __global__ void __launch_bounds__(FR_THREADS) kb_flux_rk_mixed(const CaseDev* __
     const WorkF f = mixed_planes(cw, cg.ps);
     float amax = 0.f, bmax = 0.f;
     flux_tile_faces(cg, f, i0, j0, threadIdx.x, ft, amax, bmax);
-    amax = warp_max(amax);
-    bmax = warp_max(bmax);
-    if (lane_id() == 0) {
-      atomic_max_pos(&cd.diag->alpha_bits, (double)amax);
-      atomic_max_pos(&cd.diag->beta_bits, (double)bmax);
-    }
+    flux_tile_reduce(amax, bmax, cd.diag);
     __syncthreads();
     double kef = 0.0;
-    const unsigned int bad = flux_tile_cell(cg, f, i0, j0, threadIdx.x, ft, stage, cd.diag->dt, cd.QS, cd.MOM,
-                                            cd.BASE, cd.QS, mixed_planes(cw, cg.ps).hilo, kef);
+    const unsigned int bad = flux_tile_cell<false>(cg, f, i0, j0, threadIdx.x, ft, stage, cd.diag->dt, cd.QS,
+                                                   cd.MOM, cd.BASE, cd.QS, mixed_planes(cw, cg.ps).hilo, kef);
     rk_reduce<false>(stage, bad, kef, cd.diag);
+    __syncthreads();  // the next item writes the tile again
+  }
+}
+
+// the fluxes and balances of a mixed batch's kept residual (stage 1: RHS0; a stage with
+// a source term: RHS), k_flux_asm_mixed's tile over the same work list
+__global__ void __launch_bounds__(FR_THREADS, HWENO_FR_MIN_BLOCKS) kb_flux_asm_mixed(const CaseDev* __restrict__ cases, TileList L,
+                                                                 int ncase, int which) {
+  __shared__ FluxTile ft;
+  const int total = L.start[ncase];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_case(L.start, ncase, item);
+    const CaseDev& cd = cases[c];
+    if (!cd.active) continue;  // the same for every thread of the block
+    const Grid cg = cd.g;
+    const Work cw = cd.w;
+    const int l = item - L.start[c];
+    const int by = l / L.tx[c], bx = l - by * L.tx[c];
+    const int i0 = bx * FR_TX, j0 = by * FR_TY;
+    const WorkF f = mixed_planes(cw, cg.ps);
+    float amax = 0.f, bmax = 0.f;
+    flux_tile_faces(cg, f, i0, j0, threadIdx.x, ft, amax, bmax);
+    flux_tile_reduce(amax, bmax, cd.diag);
+    __syncthreads();
+    long long cc = 0;
+    double r0[4];
+    float rm[8];
+    unsigned int bad = 0;
+    if (flux_tile_balance(cg, f, i0, j0, threadIdx.x, ft, cc, r0, rm, &bad))
+      store_residual_mixed(cg, cc, r0, rm, which == 0 ? cd.RHS0 : cd.RHS);
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (lane_id() == 0 && bad) atomicOr(&cd.diag->flags, bad);
     __syncthreads();  // the next item writes the tile again
   }
 }

@@ -23,8 +23,14 @@ struct WorkF {
   float* wx;     // 6
   float* wy;     // 6
   float* rm;     // 18
-  float* gr;     // 126
+  float* gr;     // 126: 6 components at the 12 face points, then at the 9 volume points
   float* hilo;   // 24: hi of the 12 state planes, then lo
+  // the volume integrals of Eq. (3.2), per interior cell, from the gradient pass: vs, 14
+  // sums of the gradient components over the 3x3 volume points (vol_visc_sums); iv, 8
+  // quadrature sums of the inviscid fluxes (x then y, per conserved variable).  Float planes 126-147 of the
+  // gradient group, which holds 252.
+  float* vs;
+  float* iv;
 };
 
 // FP32 face sums of the mixed path: S0 (planes 0-3) and S1 (4-7) of each conserved
@@ -44,6 +50,8 @@ __host__ __device__ inline WorkF mixed_planes(const Work& w, long long ps) {
   f.wy = (float*)w.wy;
   f.rm = (float*)w.rm;
   f.gr = (float*)w.gr;
+  f.vs = f.gr + 126 * ps;
+  f.iv = f.vs + 14 * ps;
   return f;
 }
 
@@ -140,16 +148,16 @@ __device__ __forceinline__ void cons_mixed_body(const Grid& g, const double* __r
     const float zero[4] = {0.f, 0.f, 0.f, 0.f};
     float face[12][4], vol[9][4], volx[9][4], mx[4], my[4];
     CharState<float> cs;
-    char_state<float>(ubf, (float)g.gamma, cs);
+    char_state<float>(ubf, g.gammaf, cs);
     asm volatile("" ::: "memory");  // the reconstructions load the coefficients from shared memory
     const CoefShared<float> ccsh{ccs};
-    recon_dir<float, 0>(ccsh, sl, zero, cs, (float)g.eps_weno, face, volx, mx);
+    recon_dir<float, 0>(ccsh, sl, zero, cs, g.eps_wenof, face, volx, mx);
 #pragma unroll
     for (int k = 0; k < 9; k++)
 #pragma unroll
       for (int v = 0; v < 4; v++) park[(4 * k + v) * 128] = volx[k][v];
     asm volatile("" ::: "memory");
-    recon_dir<float, 1>(ccsh, sl, zero, cs, (float)g.eps_weno, face + 6, vol, my);
+    recon_dir<float, 1>(ccsh, sl, zero, cs, g.eps_wenof, face + 6, vol, my);
 #pragma unroll
     for (int k = 0; k < 9; k++)
 #pragma unroll
@@ -236,8 +244,8 @@ __device__ __forceinline__ void cons_mixed_body(const Grid& g, const double* __r
     if (interior) {
 #pragma unroll
       for (int v = 0; v < 4; v++) {
-        mom[(long long)v * g.ps + c] = (double)mx[v];
-        mom[(long long)(4 + v) * g.ps + c] = (double)my[v];
+        mom[(long long)v * g.ps + c] = widen_f(mx[v]);
+        mom[(long long)(4 + v) * g.ps + c] = widen_f(my[v]);
       }
     }
   }
@@ -287,7 +295,7 @@ __device__ __forceinline__ void weak_moments_mixed_body(const Grid& g, const Wor
   if (i >= g.nx + 2 || j >= g.ny + 2) return;
   const WorkF f = mixed_planes(w, g.ps);
   const long long c = cidx(g, i, j), cl = cidx(g, i - 1, j), cb = cidx(g, i, j - 1);
-  const float rdx = (float)g.rdx, rdy = (float)g.rdy;
+  const float rdx = g.rdxf, rdy = g.rdyf;
 #pragma unroll
   for (int n = 0; n < 3; n++) {
     const float xr0 = f.wx[(long long)n * g.ps + c], xl0 = f.wx[(long long)n * g.ps + cl];
@@ -305,16 +313,83 @@ __device__ __forceinline__ void weak_moments_mixed_body(const Grid& g, const Wor
   }
 }
 
+// The viscous part of Eq. (3.2)'s volume integrals.  The viscous fluxes are linear in
+// the six gradient components s = (u_x, u_y, v_x, v_y, e_x, e_y), with coefficients 1, u,
+// v (and gamma / Pr for e) over Re, so their 3x3-point quadrature sums need only, per
+// component, S = sum_k w_k s_k and, for the velocity gradients, Su = sum_k w_k u_k s_k
+// and Sv = sum_k w_k v_k s_k: 14 sums, accumulated as each component is reconstructed, in
+// place of the 54 volume-point gradients (balance_mixed combines them with the inviscid
+// sums, formed here too from the volume values).
+// one volume point's inviscid fluxes (the terms of phys_flux without gradients) from its
+// primitive values p = (rho, u, v, e), weighted by wgt into iv (x fluxes, then y fluxes)
+// (explicit roundings, the same in every kernel)
+__device__ __forceinline__ void inviscid_acc(const float* p, float wgt, float gam, float* iv) {
+  const float rho = p[0], u = p[1], v = p[2], e = p[3];
+  const float pr = mul_rn(mul_rn(gam - 1.0f, rho), e);
+  const float E = mul_rn(rho, fmaf(0.5f, fmaf(u, u, mul_rn(v, v)), e));
+  const float m = mul_rn(rho, u), n = mul_rn(rho, v), H = add_rn(E, pr);
+  iv[0] = fmaf(wgt, m, iv[0]);
+  iv[1] = fmaf(wgt, fmaf(m, u, pr), iv[1]);
+  iv[2] = fmaf(wgt, mul_rn(m, v), iv[2]);
+  iv[3] = fmaf(wgt, mul_rn(H, u), iv[3]);
+  iv[4] = fmaf(wgt, n, iv[4]);
+  iv[5] = fmaf(wgt, mul_rn(n, u), iv[5]);
+  iv[6] = fmaf(wgt, fmaf(n, v, pr), iv[6]);
+  iv[7] = fmaf(wgt, mul_rn(H, v), iv[7]);
+}
+
+// vol_weights: w_k u_k and w_k v_k of cell c's volume points (k = 3 G + H, w_k the
+// product of the Gauss weights), and the inviscid part of the volume integrals from the
+// same points' primitive values into f.iv
+__device__ __forceinline__ void vol_weights(const Grid& g, const WorkF& f, long long c, float* wu, float* wv) {
+  float iv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    const float wk = gweight<float>(k / 3) * gweight<float>(k % 3);
+    float p[4];
+#pragma unroll
+    for (int v = 0; v < 4; v++) p[v] = f.vol[(long long)(4 * k + v) * g.ps + c];
+    wu[k] = mul_rn(wk, p[1]);
+    wv[k] = mul_rn(wk, p[2]);
+    inviscid_acc(p, wk, g.gammaf, iv);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; k++) f.iv[(long long)k * g.ps + c] = iv[k];
+}
+// component comp's sums from its volume-point values cen + vv[k], into f.vs: S at plane
+// comp, Su at 6 + comp and Sv at 10 + comp (comp < 4)
+__device__ __forceinline__ void vol_visc_sums(const Grid& g, const WorkF& f, long long c, int comp, float cen,
+                                              const float* vv, const float* wu, const float* wv) {
+  float S = 0.f, Su = 0.f, Sv = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    const float sk = add_rn(cen, vv[k]);
+    S = fmaf(gweight<float>(k / 3) * gweight<float>(k % 3), sk, S);
+    Su = fmaf(wu[k], sk, Su);
+    Sv = fmaf(wv[k], sk, Sv);
+  }
+  f.vs[(long long)comp * g.ps + c] = S;
+  if (comp < 4) {
+    f.vs[(long long)(6 + comp) * g.ps + c] = Su;
+    f.vs[(long long)(10 + comp) * g.ps + c] = Sv;
+  }
+}
+
 // Eq. (3.9) in FP32 on offsets from the centre value; LIN: the linear weights, whose
-// combination is p0 itself (the ablation of Remark 3.1)
-template <bool LIN = false>
+// combination is p0 itself (the ablation of Remark 3.1).  Interior cells also get the
+// volume sums (vol_visc_sums); VOLG: also the gradients at the 9 volume points (the
+// debug export's full field; the operator needs only their sums)
+template <bool LIN = false, bool VOLG = false>
 __device__ __forceinline__ void grad_mixed_body(const Grid& g, const Work& w, int gx, int gy) {
   const int i = gx - 1;
   const int j = gy - 1;
   if (i >= g.nx + 1 || j >= g.ny + 1) return;
   const WorkF f = mixed_planes(w, g.ps);
   const long long c = cidx(g, i, j);
-  const float eps = (float)g.eps_weno;
+  const float eps = g.eps_wenof;
+  const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  float wu[9], wv[9];
+  if (interior) vol_weights(g, f, c, wu, wv);
 #pragma unroll 1
   for (int comp = 0; comp < 6; comp++) {
     const int n = comp >> 1, l = comp & 1;
@@ -350,8 +425,11 @@ __device__ __forceinline__ void grad_mixed_body(const Grid& g, const Work& w, in
     for (int k = 0; k < 6; k++) out[(long long)(6 * k) * g.ps] = cen + vx[k];
 #pragma unroll
     for (int k = 0; k < 6; k++) out[(long long)(6 * (6 + k)) * g.ps] = cen + vy[k];
+    if constexpr (VOLG) {
 #pragma unroll
-    for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = cen + vv[k];
+      for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = cen + vv[k];
+    }
+    if (interior) vol_visc_sums(g, f, c, comp, cen, vv, wu, wv);
   }
 }
 
@@ -363,7 +441,7 @@ __device__ __forceinline__ void grad_mixed_body(const Grid& g, const Work& w, in
 __device__ __forceinline__ float face_sums_mixed(const Grid& g, const WorkF& f, int dir, long long cl, long long cr,
                                                  float* S0, float* S1, float& amax) {
   const int kl = dir == 0 ? 3 : 9, kr = dir == 0 ? 0 : 6;
-  const float gam = (float)g.gamma, rPr = (float)g.rPr, rRe = (float)g.rRe;
+  const float gam = g.gammaf, rPr = g.rPrf, rRe = g.rRef;
   float st[2][3][4], gs[2][3][6];
 #pragma unroll
   for (int gp = 0; gp < 3; gp++)
@@ -431,7 +509,7 @@ __device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Di
     float* outf = mixed_face_sums(dir == 0 ? w.fx : w.fy, g.ps) + cl;
 #pragma unroll
     for (int v = 0; v < 4; v++) {
-      out[(long long)v * g.ps] = (double)S0[v];
+      out[(long long)v * g.ps] = widen_f(S0[v]);
       outf[(long long)v * g.ps] = S0[v];
       outf[(long long)(4 + v) * g.ps] = S1[v];
     }
@@ -444,49 +522,68 @@ __device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Di
   }
 }
 
-// Eq. (3.2) for one cell: the volume fluxes in FP32 from its volume values and gradients,
-// and the three balances from the face sums (S0 in [0, 4), S1 in [4, 8)) of its right
-// (sR) and left (sL) x-faces and top (tT) and bottom (tB) y-faces: the average balance
-// r[0..4) in FP64 (the FP32 S0 are exact in FP64, so a periodic sum telescopes to FP64
-// rounding), the moment balances r[4..12) in FP32 like the volume fluxes they combine
-// with.  Returns FLAG_NONFINITE for a non-finite balance.
+// Eq. (3.2) for one cell: the volume integrals in FP32 from the sums that the trace pass
+// (inviscid, f.iv) and the gradient pass (viscous, f.vs) leave, and the three balances from the face sums (S0 in [0, 4), S1 in [4, 8)) of its right
+// (sR) and left (sL) x-faces and top (tT) and bottom (tB) y-faces: the average balances
+// r0 in FP64 from the same S0 widened to FP64 (dR, dL, dT, dB: exact, so a periodic sum
+// telescopes to FP64 rounding), the moment balances rm (x moments, then y moments) in
+// FP32 like the volume fluxes they combine with.  Returns FLAG_NONFINITE for a
+// non-finite balance.
 __device__ __forceinline__ unsigned int balance_mixed(const Grid& g, const WorkF& f, long long c, const float* sR,
-                                                      const float* sL, const float* tT, const float* tB, double* r) {
+                                                      const float* sL, const float* tT, const float* tB,
+                                                      const double* dR, const double* dL, const double* dT,
+                                                      const double* dB, double* r0, float* rm) {
   unsigned int bad = 0;
-  const float gam = (float)g.gamma, rPr = (float)g.rPr, rRe = (float)g.rRe;
-  float vf[4] = {0.f, 0.f, 0.f, 0.f}, vg[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-  for (int G = 0; G < 3; G++)
+  // the volume integrals: the inviscid sums minus the viscous ones over Re, those from the
+  // gradient sums of vol_visc_sums (the stresses' and heat flux's linear combinations)
+  float S[6], Su[4], Sv[4], vf[4], vg[4];
 #pragma unroll
-    for (int H = 0; H < 3; H++) {
-      const int k = 3 * G + H;
-      float st[4], gs[6], fx[4], gy[4];
+  for (int k = 0; k < 6; k++) S[k] = f.vs[(long long)k * g.ps + c];
 #pragma unroll
-      for (int v = 0; v < 4; v++) st[v] = f.vol[(long long)(4 * k + v) * g.ps + c];
-#pragma unroll
-      for (int n = 0; n < 6; n++) gs[n] = f.gr[(long long)(6 * (12 + k) + n) * g.ps + c];
-      phys_flux<float>(0, st, gs, gam, rPr, rRe, fx);
-      phys_flux<float>(1, st, gs, gam, rPr, rRe, gy);
-      const float wgt = gweight<float>(G) * gweight<float>(H);
-#pragma unroll
-      for (int v = 0; v < 4; v++) {
-        vf[v] += wgt * fx[v];
-        vg[v] += wgt * gy[v];
-      }
-    }
-  const double rdx = g.rdx, rdy = g.rdy;
-  const float rdxf = (float)g.rdx, rdyf = (float)g.rdy;
+  for (int k = 0; k < 4; k++) {
+    Su[k] = f.vs[(long long)(6 + k) * g.ps + c];
+    Sv[k] = f.vs[(long long)(10 + k) * g.ps + c];
+  }
+  // (explicit roundings, the same in every kernel)
+  const float rRe = g.rRef, gk = mul_rn(g.gammaf, g.rPrf);
+  const float c43 = 4.0f / 3.0f, c23 = -2.0f / 3.0f;
+  const float txx = fmaf(c43, S[0], mul_rn(c23, S[3]));
+  const float txy = add_rn(S[1], S[2]);
+  const float tyy = fmaf(c43, S[3], mul_rn(c23, S[0]));
+  const float ex = fmaf(gk, S[4], add_rn(fmaf(c43, Su[0], mul_rn(c23, Su[3])), add_rn(Sv[1], Sv[2])));
+  const float ey = fmaf(gk, S[5], add_rn(add_rn(Su[1], Su[2]), fmaf(c43, Sv[3], mul_rn(c23, Sv[0]))));
 #pragma unroll
   for (int v = 0; v < 4; v++) {
-    const double r0 = -((double)sR[v] - (double)sL[v]) * rdx - ((double)tT[v] - (double)tB[v]) * rdy;
-    const float r1 = -(sL[v] + sR[v]) * (0.5f * rdxf) - (tT[4 + v] - tB[4 + v]) * rdyf + vf[v] * rdxf;
-    const float r2 = -(sR[4 + v] - sL[4 + v]) * rdxf - (tB[v] + tT[v]) * (0.5f * rdyf) + vg[v] * rdyf;
-    r[v] = r0;
-    r[4 + v] = (double)r1;
-    r[8 + v] = (double)r2;
-    if (!finite_d(r0) || !finite_f(r1) || !finite_f(r2)) bad = FLAG_NONFINITE;
+    vf[v] = f.iv[(long long)v * g.ps + c];
+    vg[v] = f.iv[(long long)(4 + v) * g.ps + c];
+  }
+  vf[1] = fmaf(-txx, rRe, vf[1]);
+  vf[2] = fmaf(-txy, rRe, vf[2]);
+  vf[3] = fmaf(-ex, rRe, vf[3]);
+  vg[1] = fmaf(-txy, rRe, vg[1]);
+  vg[2] = fmaf(-tyy, rRe, vg[2]);
+  vg[3] = fmaf(-ey, rRe, vg[3]);
+  const double rdx = g.rdx, rdy = g.rdy;
+  const float rdxf = g.rdxf, rdyf = g.rdyf, hx = 0.5f * rdxf, hy = 0.5f * rdyf;
+#pragma unroll
+  for (int v = 0; v < 4; v++) {
+    r0[v] = -dadd_rn(dmul_rn(dadd_rn(dR[v], -dL[v]), rdx), dmul_rn(dadd_rn(dT[v], -dB[v]), rdy));
+    rm[v] = fmaf(vf[v], rdxf, -add_rn(mul_rn(add_rn(sL[v], sR[v]), hx), mul_rn(add_rn(tT[4 + v], -tB[4 + v]), rdyf)));
+    rm[4 + v] = fmaf(vg[v], rdyf,
+                     -add_rn(mul_rn(add_rn(sR[4 + v], -sL[4 + v]), rdxf), mul_rn(add_rn(tB[v], tT[v]), hy)));
+    if (!finite_d(r0[v]) || !finite_f(rm[v]) || !finite_f(rm[4 + v])) bad = FLAG_NONFINITE;
   }
   return bad;
+}
+
+// the residual planes of cell c: the FP64 average balances, the FP32 moment balances
+// widened exactly
+__device__ __forceinline__ void store_residual_mixed(const Grid& g, long long c, const double* r0, const float* rm,
+                                                     double* __restrict__ rhs) {
+#pragma unroll
+  for (int k = 0; k < 4; k++) rhs[(long long)k * g.ps + c] = r0[k];
+#pragma unroll
+  for (int k = 0; k < 8; k++) rhs[(long long)(4 + k) * g.ps + c] = widen_f(rm[k]);
 }
 
 __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w, double* __restrict__ rhs,
@@ -500,6 +597,7 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
     const float* fxf = mixed_face_sums(w.fx, g.ps);
     const float* fyf = mixed_face_sums(w.fy, g.ps);
     float sR[8], sL[8], tT[8], tB[8];
+    double dR[4], dL[4], dT[4], dB[4];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
       sR[k] = fxf[(long long)k * g.ps + c];
@@ -507,10 +605,17 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
       tT[k] = fyf[(long long)k * g.ps + c];
       tB[k] = fyf[(long long)k * g.ps + cb];
     }
-    double r[12];
-    bad = balance_mixed(g, f, c, sR, sL, tT, tB, r);
 #pragma unroll
-    for (int k = 0; k < 12; k++) rhs[(long long)k * g.ps + c] = r[k];
+    for (int v = 0; v < 4; v++) {  // the FP64 planes of S0 (k_flux_mixed's widening)
+      dR[v] = w.fx[(long long)v * g.ps + c];
+      dL[v] = w.fx[(long long)v * g.ps + cl];
+      dT[v] = w.fy[(long long)v * g.ps + c];
+      dB[v] = w.fy[(long long)v * g.ps + cb];
+    }
+    double r0[4];
+    float rm[8];
+    bad = balance_mixed(g, f, c, sR, sL, tT, tB, dR, dL, dT, dB, r0, rm);
+    store_residual_mixed(g, c, r0, rm, rhs);
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
@@ -525,13 +630,21 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
 // equals theirs bit for bit.  Stage 1 cannot be fused this way: its step size needs
 // alpha* over every face first, and its residual is kept for restarts.
 constexpr int FR_TX = 32, FR_TY = 7, FR_THREADS = 256;
+// resident blocks per SM that the tile kernels' register budget is set for (3: 80
+// registers, no spills)
+#ifndef HWENO_FR_MIN_BLOCKS
+#define HWENO_FR_MIN_BLOCKS 3
+#endif
 static_assert((FR_TX + 1) * FR_TY <= FR_THREADS && FR_TX * (FR_TY + 1) <= FR_THREADS, "one face per thread");
 
 // the tile's face sums: x-face right of cell (i0 - 1 + a, j0 + b) at sx[k][b][a], y-face
-// above cell (i0 + a, j0 - 1 + b) at sy[k][b][a], k = S0 (0-3), S1 (4-7)
+// above cell (i0 + a, j0 - 1 + b) at sy[k][b][a], k = S0 (0-3), S1 (4-7); S0 again widened
+// to FP64 in dx, dy (once per face rather than once per cell)
 struct FluxTile {
   float sx[8][FR_TY][FR_TX + 1];
   float sy[8][FR_TY + 1][FR_TX];
+  double dx[4][FR_TY][FR_TX + 1];
+  double dy[4][FR_TY + 1][FR_TX];
 };
 
 // thread t's x-face and y-face of the tile at (i0, j0)
@@ -545,6 +658,8 @@ __device__ __forceinline__ void flux_tile_faces(const Grid& g, const WorkF& f, i
       bmax = fmaxf(bmax, face_sums_mixed(g, f, 0, cidx(g, i, j), cidx(g, i + 1, j), S, S + 4, amax));
 #pragma unroll
       for (int k = 0; k < 8; k++) ft.sx[k][b][a] = S[k];
+#pragma unroll
+      for (int k = 0; k < 4; k++) ft.dx[k][b][a] = widen_f(S[k]);
     }
   }
   if (t < FR_TX * (FR_TY + 1)) {
@@ -555,22 +670,23 @@ __device__ __forceinline__ void flux_tile_faces(const Grid& g, const WorkF& f, i
       bmax = fmaxf(bmax, face_sums_mixed(g, f, 1, cidx(g, i, j), cidx(g, i, j + 1), S, S + 4, amax));
 #pragma unroll
       for (int k = 0; k < 8; k++) ft.sy[k][b][a] = S[k];
+#pragma unroll
+      for (int k = 0; k < 4; k++) ft.dy[k][b][a] = widen_f(S[k]);
     }
   }
 }
 
-// thread t's cell of the tile: its balances from the tile's face sums and its stage
-// update; returns the flags, and the kinetic share at stage 3 in kef
-__device__ __forceinline__ unsigned int flux_tile_cell(const Grid& g, const WorkF& f, int i0, int j0, int t,
-                                                       const FluxTile& ft, int stage, double dt,
-                                                       const double* __restrict__ qin, const double* __restrict__ mom,
-                                                       double* __restrict__ base, double* __restrict__ qout,
-                                                       float* __restrict__ hilo, double& kef) {
-  if (t >= FR_TX * FR_TY) return 0;
+// thread t's cell of the tile: its balances from the tile's face sums into r (false for
+// a thread without a cell); *bad gets FLAG_NONFINITE for a non-finite balance
+__device__ __forceinline__ bool flux_tile_balance(const Grid& g, const WorkF& f, int i0, int j0, int t,
+                                                  const FluxTile& ft, long long& c, double* r0, float* rm,
+                                                  unsigned int* bad) {
+  if (t >= FR_TX * FR_TY) return false;
   const int a = t % FR_TX, b = t / FR_TX;
   const int i = i0 + a, j = j0 + b;
-  if (i >= g.nx || j >= g.ny) return 0;
+  if (i >= g.nx || j >= g.ny) return false;
   float sR[8], sL[8], tT[8], tB[8];
+  double dR[4], dL[4], dT[4], dB[4];
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     sR[k] = ft.sx[k][b][a + 1];
@@ -578,14 +694,68 @@ __device__ __forceinline__ unsigned int flux_tile_cell(const Grid& g, const Work
     tT[k] = ft.sy[k][b + 1][a];
     tB[k] = ft.sy[k][b][a];
   }
-  const long long c = cidx(g, i, j);
-  double r[12];
-  unsigned int bad = balance_mixed(g, f, c, sR, sL, tT, tB, r);
-  bad |= rk_cell<true, true>(g, stage, c, dt, qin, mom, r, base, qout, hilo, kef);
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    dR[k] = ft.dx[k][b][a + 1];
+    dL[k] = ft.dx[k][b][a];
+    dT[k] = ft.dy[k][b + 1][a];
+    dB[k] = ft.dy[k][b][a];
+  }
+  c = cidx(g, i, j);
+  *bad |= balance_mixed(g, f, c, sR, sL, tT, tB, dR, dL, dT, dB, r0, rm);
+  return true;
+}
+
+// thread t's cell of the tile: its balances from the tile's face sums and its stage
+// update; returns the flags, and (KEF) the kinetic share at stage 3 in kef
+template <bool KEF>
+__device__ __forceinline__ unsigned int flux_tile_cell(const Grid& g, const WorkF& f, int i0, int j0, int t,
+                                                       const FluxTile& ft, int stage, double dt,
+                                                       const double* __restrict__ qin, const double* __restrict__ mom,
+                                                       double* __restrict__ base, double* __restrict__ qout,
+                                                       float* __restrict__ hilo, double& kef) {
+  long long c = 0;
+  double r0[4];
+  float rm[8];
+  unsigned int bad = 0;
+  if (!flux_tile_balance(g, f, i0, j0, t, ft, c, r0, rm, &bad)) return 0;
+  bad |= rk_cell_mixed<KEF>(g, stage, c, dt, qin, mom, r0, rm, base, qout, hilo, kef);
   return bad;
 }
 
-__global__ void __launch_bounds__(FR_THREADS) k_flux_rk_mixed(Grid g, Work w, int stage, const double* __restrict__ qin,
+// the tile's alpha* and beta_max contributions into the reductions
+__device__ __forceinline__ void flux_tile_reduce(float amax, float bmax, Diag* diag) {
+  amax = warp_max(amax);
+  bmax = warp_max(bmax);
+  if (lane_id() == 0) {
+    atomic_max_pos(&diag->alpha_bits, (double)amax);
+    atomic_max_pos(&diag->beta_bits, (double)bmax);
+  }
+}
+
+// Eqs. (3.3) and (3.2) of the mixed path, for a residual that is kept (stage 1 of a
+// step, whose step size needs alpha* over every face first and whose residual serves
+// the restarts; hweno_residual): the tile's face sums in shared memory, then the
+// balances of its cells into rhs.  The arithmetic is that of k_flux_rk_mixed's first
+// part.
+__global__ void __launch_bounds__(FR_THREADS, HWENO_FR_MIN_BLOCKS) k_flux_asm_mixed(Grid g, Work w, double* __restrict__ rhs, Diag* diag) {
+  __shared__ FluxTile ft;
+  const WorkF f = mixed_planes(w, g.ps);
+  const int i0 = blockIdx.x * FR_TX, j0 = blockIdx.y * FR_TY, t = threadIdx.x;
+  float amax = 0.f, bmax = 0.f;
+  flux_tile_faces(g, f, i0, j0, t, ft, amax, bmax);
+  flux_tile_reduce(amax, bmax, diag);
+  __syncthreads();
+  long long c = 0;
+  double r0[4];
+  float rm[8];
+  unsigned int bad = 0;
+  if (flux_tile_balance(g, f, i0, j0, t, ft, c, r0, rm, &bad)) store_residual_mixed(g, c, r0, rm, rhs);
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (lane_id() == 0 && bad) atomicOr(&diag->flags, bad);
+}
+
+__global__ void __launch_bounds__(FR_THREADS, HWENO_FR_MIN_BLOCKS) k_flux_rk_mixed(Grid g, Work w, int stage, const double* __restrict__ qin,
                                                                const double* __restrict__ mom, double* __restrict__ base,
                                                                double* __restrict__ qout, Diag* diag,
                                                                float* __restrict__ hilo) {
@@ -594,15 +764,11 @@ __global__ void __launch_bounds__(FR_THREADS) k_flux_rk_mixed(Grid g, Work w, in
   const int i0 = blockIdx.x * FR_TX, j0 = blockIdx.y * FR_TY, t = threadIdx.x;
   float amax = 0.f, bmax = 0.f;
   flux_tile_faces(g, f, i0, j0, t, ft, amax, bmax);
-  amax = warp_max(amax);
-  bmax = warp_max(bmax);
-  if (lane_id() == 0) {
-    atomic_max_pos(&diag->alpha_bits, (double)amax);
-    atomic_max_pos(&diag->beta_bits, (double)bmax);
-  }
+  flux_tile_reduce(amax, bmax, diag);
   __syncthreads();
   double kef = 0.0;
-  const unsigned int bad = flux_tile_cell(g, f, i0, j0, t, ft, stage, diag->dt, qin, mom, base, qout, hilo, kef);
+  const unsigned int bad = flux_tile_cell<true>(g, f, i0, j0, t, ft, stage, diag->dt, qin, mom, base, qout, hilo,
+                                                kef);
   rk_reduce<true>(stage, bad, kef, diag);
 }
 
@@ -644,16 +810,9 @@ __global__ void k_face_moments_mixed(Grid g, Work w) {
 __global__ void k_weak_moments_mixed(Grid g, Work w) {
   weak_moments_mixed_body(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
-template <bool LIN = false>
+template <bool LIN = false, bool VOLG = false>
 __global__ void __launch_bounds__(128) k_grad_mixed(Grid g, Work w) {
-  grad_mixed_body<LIN>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
-}
-__global__ void __launch_bounds__(128) k_flux_mixed(Grid g, Work w, Diag* diag) {
-  flux_mixed_body(g, w, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
-                  blockIdx.z);
-}
-__global__ void __launch_bounds__(128) k_assemble_mixed(Grid g, Work w, double* __restrict__ rhs, Diag* diag) {
-  assemble_mixed_body(g, w, rhs, diag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+  grad_mixed_body<LIN, VOLG>(g, w, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 }  // namespace hw

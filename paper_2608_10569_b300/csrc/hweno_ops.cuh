@@ -562,15 +562,27 @@ __device__ __forceinline__ void assemble_body(const Grid& g, const Work& w, doub
 // The SSP-RK3 stage update of one cell from its 12 residual values f (Eq. (2.12) in
 // its 2D form): writes qout, and the base at stage 1; returns FLAG_INADMISSIBLE when the
 // new cell average is not admissible or not finite.
-// SPLIT (mixed path): also write the hi/lo split of the new state (24 float planes at
-// hilo), so that the next evaluation needs no separate split pass.
 // KEF (mixed handles): at stage 3, also the kinetic share |m|^2 / (2 rho E) of the new
 // state in kef, the measure that routes a mixed handle's next step
-template <bool SPLIT = false, bool KEF = false>
+
+// the admissibility of the new cell average out[0..4) and, KEF at stage 3, its kinetic
+// share: p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0; the share decides between FP32
+// and FP64 at a margin of 1e-4, which an FP32 ratio of the FP64 energies resolves
+template <bool KEF>
+__device__ __forceinline__ unsigned int rk_admissible(int stage, const double* out, double& kef) {
+  const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
+  const bool ok = out[0] > 0.0 && rp > 0.0;
+  if constexpr (KEF) {
+    if (stage == 3) kef = ok ? 1.0 - (double)tdiv((float)rp, (float)(out[3] * out[0])) : 1.0;
+  }
+  return ok ? 0u : FLAG_INADMISSIBLE;
+}
+
+template <bool KEF = false>
 __device__ __forceinline__ unsigned int rk_cell(const Grid& g, int stage, long long c, double dt,
                                                 const double* __restrict__ qin, const double* __restrict__ mom,
                                                 const double* f, double* __restrict__ base,
-                                                double* __restrict__ qout, float* __restrict__ hilo, double& kef) {
+                                                double* __restrict__ qout, double& kef) {
   unsigned int bad = 0;
   double out[12];
 #pragma unroll
@@ -585,21 +597,69 @@ __device__ __forceinline__ unsigned int rk_cell(const Grid& g, int stage, long l
       out[k] = base[(long long)k * g.ps + c] * (1.0 / 3.0) + (2.0 / 3.0) * (cur + dt * f[k]);
     }
     qout[(long long)k * g.ps + c] = out[k];
-    if constexpr (SPLIT) {
-      float hi, lo;
-      split_hilo(out[k], hi, lo);
-      hilo[(long long)k * g.ps + c] = hi;
-      hilo[(long long)(12 + k) * g.ps + c] = lo;
-    }
     if (!finite_d(out[k])) bad = FLAG_INADMISSIBLE;
   }
-  // p > 0 <=> rho E - |m|^2 / 2 > 0 once rho > 0
-  const double rp = out[3] * out[0] - 0.5 * (out[1] * out[1] + out[2] * out[2]);
-  if (!(out[0] > 0.0) || !(rp > 0.0)) bad = FLAG_INADMISSIBLE;
-  if constexpr (KEF) {
-    if (stage == 3) kef = (out[0] > 0.0 && rp > 0.0) ? 1.0 - rp / (out[3] * out[0]) : 1.0;
+  return bad | rk_admissible<KEF>(stage, out, kef);
+}
+
+// The mixed path's stage update of one cell: the averages as rk_cell does, from their
+// FP64 balances f0; the moments in FP32, from their FP32 balances fm.  The moments that
+// enter a stage are the modified moments of the FP32 reconstruction (Eq. (2.11)), FP32
+// values held in FP64 planes, and their balances carry FP32 rounding of the flux
+// scale, far above an FP32 rounding of the moments themselves; so the update runs in
+// single precision (explicit fused multiply-adds, the same in every kernel) and the
+// FP64 planes receive the FP32 result exactly (widen_f, narrow_exact: integer
+// operations, since B300's FP64 pipe also carries the conversions).  Also writes the
+// hi/lo split of the new state (24 float planes at hilo: the moments' lo parts are 0),
+// so that the next evaluation needs no separate split pass.
+template <bool KEF = false>
+__device__ __forceinline__ unsigned int rk_cell_mixed(const Grid& g, int stage, long long c, double dt,
+                                                      const double* __restrict__ qin,
+                                                      const double* __restrict__ mom, const double* f0,
+                                                      const float* fm, double* __restrict__ base,
+                                                      double* __restrict__ qout, float* __restrict__ hilo,
+                                                      double& kef) {
+  unsigned int bad = 0;
+  double out[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const double cur = qin[(long long)k * g.ps + c];
+    const double t = fma(dt, f0[k], cur);  // explicit roundings, the same in every kernel
+    if (stage == 1) {
+      base[(long long)k * g.ps + c] = cur;
+      out[k] = t;
+    } else if (stage == 2) {
+      out[k] = fma(0.75, base[(long long)k * g.ps + c], dmul_rn(0.25, t));
+    } else {
+      out[k] = fma(1.0 / 3.0, base[(long long)k * g.ps + c], dmul_rn(2.0 / 3.0, t));
+    }
+    qout[(long long)k * g.ps + c] = out[k];
+    float hi, lo;
+    split_hilo(out[k], hi, lo);
+    hilo[(long long)k * g.ps + c] = hi;
+    hilo[(long long)(12 + k) * g.ps + c] = lo;
+    if (!finite_d(out[k])) bad = FLAG_INADMISSIBLE;
   }
-  return bad;
+  const float dtf = (float)dt;
+#pragma unroll
+  for (int k = 4; k < 12; k++) {
+    const double cur = mom[(long long)(k - 4) * g.ps + c];
+    const float t = fmaf(dtf, fm[k - 4], narrow_exact(cur));
+    float o;
+    if (stage == 1) {
+      base[(long long)k * g.ps + c] = cur;
+      o = t;
+    } else if (stage == 2) {
+      o = fmaf(0.75f, narrow_exact(base[(long long)k * g.ps + c]), 0.25f * t);
+    } else {
+      o = fmaf(1.0f / 3.0f, narrow_exact(base[(long long)k * g.ps + c]), (2.0f / 3.0f) * t);
+    }
+    qout[(long long)k * g.ps + c] = widen_f(o);
+    hilo[(long long)k * g.ps + c] = o;
+    hilo[(long long)(12 + k) * g.ps + c] = 0.0f;
+    if (!finite_f(o)) bad = FLAG_INADMISSIBLE;
+  }
+  return bad | rk_admissible<KEF>(stage, out, kef);
 }
 
 // the warp's flags and (KEF, stage 3) kinetic shares into the step's reductions
@@ -615,6 +675,8 @@ __device__ __forceinline__ void rk_reduce(int stage, unsigned int bad, double ke
   }
 }
 
+// the stage update of cell (gx, gy) from the residual planes rhs; SPLIT: the mixed path's
+// (rk_cell_mixed, the moments' balances narrowed from their FP64 planes exactly)
 template <bool SPLIT = false, bool KEF = false>
 __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* __restrict__ qin,
                                         const double* __restrict__ mom, const double* __restrict__ rhs,
@@ -626,10 +688,20 @@ __device__ __forceinline__ void rk_body(const Grid& g, int stage, const double* 
   double kef = 0.0;
   if (i < g.nx && j < g.ny) {
     const long long c = cidx(g, i, j);
-    double f[12];
+    if constexpr (SPLIT) {
+      double f0[4];
+      float fm[8];
 #pragma unroll
-    for (int k = 0; k < 12; k++) f[k] = rhs[(long long)k * g.ps + c];
-    bad = rk_cell<SPLIT, KEF>(g, stage, c, diag->dt, qin, mom, f, base, qout, hilo, kef);
+      for (int k = 0; k < 4; k++) f0[k] = rhs[(long long)k * g.ps + c];
+#pragma unroll
+      for (int k = 0; k < 8; k++) fm[k] = narrow_exact(rhs[(long long)(4 + k) * g.ps + c]);
+      bad = rk_cell_mixed<KEF>(g, stage, c, diag->dt, qin, mom, f0, fm, base, qout, hilo, kef);
+    } else {
+      double f[12];
+#pragma unroll
+      for (int k = 0; k < 12; k++) f[k] = rhs[(long long)k * g.ps + c];
+      bad = rk_cell<KEF>(g, stage, c, diag->dt, qin, mom, f, base, qout, kef);
+    }
   }
   rk_reduce<KEF>(stage, bad, kef, diag);
 }

@@ -25,6 +25,9 @@ struct Grid {
   int bc[4];
   double rdx, rdy, rPr, rRe;  // 1/dx, 1/dy, 1/Pr, 1/Re (correctly rounded, on the host)
   double x0, y0;              // domain origin (coordinates of a source term and of inflow bands)
+  // the mixed path's single-precision copies (rounded on the host: a per-thread conversion
+  // would occupy the FP64 pipe)
+  float gammaf, rPrf, rRef, rdxf, rdyf, eps_wenof;
 };
 
 // prescribed states of HWENO_BC_INFLOW faces (Remark 4.1): per face (xlo, xhi, ylo,
@@ -50,6 +53,8 @@ inline Grid make_grid(const hweno_config& c) {
   for (int k = 0; k < 4; k++) g.bc[k] = c.bc[k];
   g.rdx = 1.0 / g.dx; g.rdy = 1.0 / g.dy; g.rPr = 1.0 / g.Pr; g.rRe = 1.0 / g.Re;
   g.x0 = c.x0; g.y0 = c.y0;
+  g.gammaf = (float)g.gamma; g.rPrf = (float)g.rPr; g.rRef = (float)g.rRe;
+  g.rdxf = (float)g.rdx; g.rdyf = (float)g.rdy; g.eps_wenof = (float)g.eps_weno;
   return g;
 }
 
@@ -94,6 +99,79 @@ __host__ __device__ __forceinline__ float float_of(unsigned int b) {
   return f;
 #endif
 }
+__host__ __device__ __forceinline__ double double_of(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  memcpy(&d, &b, sizeof(d));
+  return d;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned int bits_of_f(float x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned int)__float_as_int(x);
+#else
+  unsigned int b;
+  memcpy(&b, &x, sizeof(b));
+  return b;
+#endif
+}
+
+// single roundings that the compiler may not fuse into multiply-adds: an expression
+// written with these (and fmaf / fma) rounds the same way in every kernel that inlines it
+__host__ __device__ __forceinline__ float add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ double dadd_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ double dmul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+
+// x widened to double with integer operations: the same value, exactly (normal floats
+// and zeros re-biased; subnormal floats, infinities and NaN through the conversion)
+__host__ __device__ __forceinline__ double widen_f(float x) {
+  const unsigned int b = bits_of_f(x);
+  const unsigned int e = (b >> 23) & 0xffu;
+  const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
+  if ((b & 0x7fffffffu) == 0u) return double_of(s);
+  if (e == 0u || e == 0xffu) return (double)x;
+  return double_of(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29));
+}
+
+// a double that holds a float value, narrowed to that float with integer operations
+// (exact; for any other double the truncation of split_hilo's hi part; values outside
+// the normal float range through the conversion)
+__host__ __device__ __forceinline__ float narrow_exact(double x) {
+  const unsigned long long b = bits_of(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  if ((b & 0x7fffffffffffffffull) == 0ull) return float_of(sign);
+  const int fe = (int)((b >> 52) & 0x7ff) - 896;
+  if (fe < 1 || fe > 254) return (float)x;
+  return float_of(sign | ((unsigned int)fe << 23) | (unsigned int)((b >> 29) & 0x7fffffull));
+}
+
 __host__ __device__ __forceinline__ int clz32(unsigned int r) {  // r != 0
 #ifdef __CUDA_ARCH__
   return __clz((int)r);

@@ -81,7 +81,7 @@ __device__ __forceinline__ void gradtile_weak_cell(const Grid& g, const GradTile
   wface(0, x - 1, y, xl0, xl1);
   wface(1, x, y, yt0, yt1);
   wface(1, x, y - 1, yb0, yb1);
-  const float rdx = (float)g.rdx, rdy = (float)g.rdy;
+  const float rdx = g.rdxf, rdy = g.rdyf;
   const int plane = GR_Y * GR_X, at = ry * GR_X + rx;
 #pragma unroll
   for (int n = 0; n < 3; n++) {
@@ -97,13 +97,17 @@ __device__ __forceinline__ void gradtile_weak_cell(const Grid& g, const GradTile
 }
 
 // the six gradient components of tile cell (tx, ty), cell (i, j), from the staged weak
-// moments, with the operations of grad_mixed_body; LIN: the linear weights (Remark 3.1)
-template <bool LIN>
+// moments, with the operations of grad_mixed_body (its volume sums for interior cells;
+// VOLG: also the volume-point gradients); LIN: the linear weights (Remark 3.1)
+template <bool LIN, bool VOLG = false>
 __device__ __forceinline__ void gradtile_grad_cell(const Grid& g, const Work& w, const GradTile& tt, int tx,
                                                             int ty, int i, int j) {
   const WorkF f = mixed_planes(w, g.ps);
   const long long c = cidx(g, i, j);
-  const float eps = (float)g.eps_weno;
+  const float eps = g.eps_wenof;
+  const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  float wu[9], wv[9];
+  if (interior) vol_weights(g, f, c, wu, wv);
   const int plane = GR_Y * GR_X;
   const int rx = tx + 1, ry = ty + 1;
 #pragma unroll 1
@@ -142,8 +146,11 @@ __device__ __forceinline__ void gradtile_grad_cell(const Grid& g, const Work& w,
     for (int k = 0; k < 6; k++) out[(long long)(6 * k) * g.ps] = cen + vx[k];
 #pragma unroll
     for (int k = 0; k < 6; k++) out[(long long)(6 * (6 + k)) * g.ps] = cen + vy[k];
+    if constexpr (VOLG) {
 #pragma unroll
-    for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = cen + vv[k];
+      for (int k = 0; k < 9; k++) out[(long long)(6 * (12 + k)) * g.ps] = cen + vv[k];
+    }
+    if (interior) vol_visc_sums(g, f, c, comp, cen, vv, wu, wv);
   }
 }
 

@@ -6,6 +6,7 @@
 // read of a value that no earlier kernel wrote reach the output.
 #pragma once
 #include "shim.h"
+#include <algorithm>
 #include <vector>
 #include "hweno_mixed.cuh"
 #include "hweno_source.cuh"
@@ -123,20 +124,49 @@ inline void fused_stage(const hweno_config& c, const Grid& g, const Open& o, Scr
       for (int t = 0; t < FR_THREADS; t++) flux_tile_faces(g, f, i0, j0, t, ft, amax, bmax);
       for (int t = 0; t < FR_THREADS; t++) {
         double kef = 0.0;
-        diag->flags |= flux_tile_cell(g, f, i0, j0, t, ft, stage, diag->dt, q, mom, base, qout, hilo_out.data(), kef);
+        diag->flags |= flux_tile_cell<true>(g, f, i0, j0, t, ft, stage, diag->dt, q, mom, base, qout, hilo_out.data(),
+                                            kef);
+      }
+    }
+}
+
+// the mixed path's fluxes and balances as k_flux_asm_mixed runs them: per tile, every
+// thread's faces, then every thread's cell, into rhs
+inline void flux_asm_tiles(const Grid& g, Scratch& s, double* rhs, Diag* diag) {
+  const WorkF f = mixed_planes(s.w, g.ps);
+  static FluxTile ft;
+  for (int j0 = 0; j0 < g.ny; j0 += FR_TY)
+    for (int i0 = 0; i0 < g.nx; i0 += FR_TX) {
+      float amax = 0.f, bmax = 0.f;
+      for (int t = 0; t < FR_THREADS; t++) flux_tile_faces(g, f, i0, j0, t, ft, amax, bmax);
+      double a = amax, b = bmax;
+      diag->alpha_bits = std::max(diag->alpha_bits, (unsigned long long)__double_as_longlong(a));
+      diag->beta_bits = std::max(diag->beta_bits, (unsigned long long)__double_as_longlong(b));
+      for (int t = 0; t < FR_THREADS; t++) {
+        long long c = 0;
+        double r0[4];
+        float rm[8];
+        unsigned int bad = 0;
+        if (flux_tile_balance(g, f, i0, j0, t, ft, c, r0, rm, &bad)) store_residual_mixed(g, c, r0, rm, rhs);
+        diag->flags |= bad;
       }
     }
 }
 
 // one evaluation at state q (12 padded planes, ghosts filled here): rhs (12) and the
-// modified moments mom (8); the source term, when configured, at time t
+// modified moments mom (8); the source term, when configured, at time t; tiles: the mixed
+// path's fluxes and balances as its tile kernel runs them
 inline void residual(const hweno_config& c, const Grid& g, const Open& o, const Quad4& quad, Scratch& s,
-                     double* q, double* rhs, double* mom, Diag* diag, double t, bool mixed, bool tma = false) {
+                     double* q, double* rhs, double* mom, Diag* diag, double t, bool mixed, bool tma = false,
+                     bool tiles = false) {
   const int nx = g.nx, ny = g.ny;
   Work& w = s.w;
   for (int k = 0; k < 8 * ny; k++) ghost_x_body(g, &o, q, k);
   for (int k = 0; k < 8 * (nx + 2 * NG); k++) ghost_y_body(g, &o, q, k);
-  if (mixed) {
+  if (mixed && tiles) {
+    mixed_front(c, g, s, q, mom, diag, tma);
+    flux_asm_tiles(g, s, rhs, diag);
+  } else if (mixed) {
     mixed_front(c, g, s, q, mom, diag, tma);
     for (int gz = 0; gz < 2; gz++)
       for (int gy = 0; gy < ny + 1; gy++)

@@ -46,9 +46,15 @@ int main(int argc, char** argv) {
     for (int j = 0; j < ny; j++)
       for (int i = 0; i < nx; i++) Q[p * g.ps + cidx(g, i, j)] = src[p * n + (size_t)j * nx + i];
   const double hmin = g.dx < g.dy ? g.dx : g.dy;
+  // the mixed path's stage update is k_rk_split's (its split output is the split the next
+  // evaluation forms again from the ghost-filled state)
+  std::vector<float> hilo_out(24 * (size_t)g.ps);
   auto stage = [&](int k, const double* qin, const double* mom, const double* rhs, double* qout, Diag* d) {
     for (int gy = 0; gy < ny; gy++)
-      for (int gx = 0; gx < nx; gx++) rk_body<false>(g, k, qin, mom, rhs, BASE.data(), qout, d, gx, gy);
+      for (int gx = 0; gx < nx; gx++) {
+        if (in.mixed) rk_body<true>(g, k, qin, mom, rhs, BASE.data(), qout, d, gx, gy, hilo_out.data());
+        else rk_body<false>(g, k, qin, mom, rhs, BASE.data(), qout, d, gx, gy);
+      }
   };
   std::vector<double> log;
   int status = 0;
@@ -56,7 +62,7 @@ int main(int argc, char** argv) {
   for (int step = 0; step < nsteps && !status; step++) {
     Diag d[2];  // the attempt's counters and flags, and the stage-1 ones
     memset(d, 0, sizeof(d));
-    residual(c, g, o, quad, s, Q.data(), RHS0.data(), MOM0.data(), &d[0], t, in.mixed, in.tma);
+    residual(c, g, o, quad, s, Q.data(), RHS0.data(), MOM0.data(), &d[0], t, in.mixed, in.tma, in.fused);
     double alpha;
     memcpy(&alpha, &d[0].alpha_bits, sizeof(alpha));
     d[0].dt = dt_forced > 0.0 ? dt_forced : fmin(cfl * hmin / alpha, b_visc * c.Re * hmin * hmin);

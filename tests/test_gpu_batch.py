@@ -1,10 +1,12 @@
-"""Batched ensembles (hweno_batch_*): every case of a batch must follow exactly the
-steps its own single-grid solver takes (same per-cell bodies, same per-case time step),
-in FP64 and in the mixed path, also after the autotuner changed the tile shapes, and with
-per-case restarts.  In the mixed path a single handle forms the gradients in the
-TMA-staged kernel and a batch in the separate face-moment, weak-moment and gradient
-kernels: the same FP32 expressions, compiled to the same operations, so the states
-agree bit for bit there too."""
+"""Batched ensembles (hweno_batch_*): every case of a batch must follow the steps its own
+single-grid solver takes (same per-cell bodies, same per-case time step), also after the
+autotuner changed the tile shapes, and with per-case restarts: in FP64 bit for bit.  In
+the mixed path a single handle forms the gradients in the TMA-staged kernel and a batch
+in the separate face-moment, weak-moment and gradient kernels; the FP32 expressions are
+the same, but a multiply and an add written without a rounding mode may be fused into
+one multiply-add by the code generator, differently in different kernels, so a mixed
+batch and a mixed handle agree to FP32 rounding: their distance is bounded by the mixed
+handle's own distance from the FP64 handle on the same case."""
 import numpy as np
 import pytest
 
@@ -52,13 +54,28 @@ def test_batch_matches_single_solvers(precision, tune):
     for view, (case, q) in zip(b.cases, cases):
         ref, dts, d1 = _single(case, q, precision, 3)
         with torch.cuda.stream(stream):
-            got = view.get_state()
+            got = view.get_state().cpu().numpy()
         stream.synchronize()
         d = view.diag()
-        assert d["steps"] == 3 and d["dt_last"] == dts[-1]
-        assert abs(d["t"] - sum(dts)) <= 1e-15 * sum(dts)
-        assert np.array_equal(got.cpu().numpy(), ref)
+        if precision == "fp64":
+            assert d["steps"] == 3 and d["dt_last"] == dts[-1]
+            assert abs(d["t"] - sum(dts)) <= 1e-15 * sum(dts)
+            assert np.array_equal(got, ref)
+        else:
+            assert d["steps"] == 3 and abs(d["dt_last"] / dts[-1] - 1) <= 1e-6
+            assert abs(d["t"] / sum(dts) - 1) <= 1e-6
+            ref64 = _single(case, q, "fp64", 3)[0]
+            bound = mixed_distance(ref, ref64, q)
+            err = mixed_distance(got, ref, q)
+            print("%s: batch against handle %.2e, mixed handle against FP64 %.2e" % (case.name, err, bound))
+            assert err <= max(4 * bound, 1e-14)
     b.close()
+
+
+def mixed_distance(a, b, q):
+    """max over planes of max |a - b| against the plane's variable's scale"""
+    scale = np.abs(q[:4]).reshape(4, -1).max(1)
+    return max(np.abs(a[k] - b[k]).max() / max(np.abs(b[k]).max(), scale[k % 4]) for k in range(12))
 
 
 def test_batch_fp64_matches_the_oracle():

@@ -14,10 +14,13 @@
   them within a few steps (the kernels' own arithmetic on the host follows the oracle's
   restarts for two steps, then takes 20 where it takes 19; on the GPU, with its
   multiply-add contractions, the first step agrees); the two runs are then different
-  valid trajectories.  So the steps up to the first different restart count
-  are compared cell by cell, and all 20 for validity: admissible states, totals
-  conserved to round-off, restarts per step and the time reached within the oracle's
-  range.  The mixed handle takes the FP64 route there (its internal energy is 7.5e-7
+  valid trajectories.  So the steps up to the first different restart count are
+  compared cell by cell (two at most), each cell within 32 times the oracle's own spread
+  there over 32 trajectories from inputs moved by one ulp (next to clipped pressures a step
+  moves states by O(1) through the PP bound and can switch a face's branch; elsewhere the
+  cells agree to 1e-10), and all 20 for validity: admissible states, totals conserved to
+  round-off, the restarts over the 20 steps within 25 % of the oracle's and the time reached
+  within a factor 10.  The mixed handle takes the FP64 route there (its internal energy is 7.5e-7
   of the total) and equals the FP64 handle bit for bit.
 """
 import os
@@ -30,7 +33,7 @@ torch = pytest.importorskip("torch")
 from oracle import oracle as O  # noqa: E402
 from paper_2608_10569_b300 import hweno, inputs as I  # noqa: E402
 
-from parity_tools import rel_linf, res_tol, state_scale  # noqa: E402
+from parity_tools import state_scale, ulp_perturbed  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -166,10 +169,31 @@ def test_colliding_streams_20_step_window():
     print("restarts per step: GPU %s, oracle %s; the first %d agree"
           % ([r for _, r in rows], [r for _, r in orows], lead))
     assert lead >= 1
-    tol = res_tol(case, q)
-    for k in range(lead):
+    # next to clipped pressures a step moves states by O(1) through the PP bound (beta ~ 1/e
+    # there), and a rounding-level change can switch a face's branch there (at the seam face
+    # of row 19 the GPU's step differs from the oracle's by 0.38 of the variable's scale, and
+    # so do two of 32 oracle runs from inputs moved by one ulp), while elsewhere the step is
+    # well-conditioned.  So each cell's bound is the oracle's own spread there: its
+    # trajectories from 32 inputs moved by one ulp, while their restart counts still agree,
+    # per cell and per variable's scale, over the first two steps at most
+    scale = np.tile(state_scale(q), 3).reshape(12, 1, 1)
+    trajs = [ulp_perturbed(q, sd) for sd in range(32)]
+    for k in range(min(lead, 2)):
+        spread = np.zeros(q.shape[1:])
+        alive = []
+        for qp in trajs:
+            qp, stp = O.step(cfg, qp)
+            if stp["rejections"] == orows[k][1]:
+                spread = np.maximum(spread, (np.abs(qp - ostates[k]) / scale).max(0))
+                alive.append(qp)
+        trajs = alive
+        if not trajs:
+            break
+        err = (np.abs(states[k] - ostates[k]) / scale).max(0)
+        print("step %d: GPU against the oracle %.2e, the oracle's one-ulp spread %.2e; cells within 1e-9: %d of %d"
+              % (k + 1, err.max(), spread.max(), (err <= 1e-9).sum(), err.size))
         assert abs(rows[k][0] / orows[k][0] - 1) <= 1e-12
-        assert rel_linf(states[k], ostates[k], state_scale(q)) <= tol
+        assert (err <= 32 * spread + 1e-12).all(), np.max(err / (spread + 1e-300))
     # every step: a valid trajectory of the scheme
     area = case.dx * case.dy
     tot0 = q[:4].reshape(4, -1).sum(1) * area
@@ -178,9 +202,10 @@ def test_colliding_streams_20_step_window():
         assert rho.min() > 0 and (E - 0.5 * (m * m + n * n) / rho).min() > 0
         tot = qs[:4].reshape(4, -1).sum(1) * area
         assert np.abs(tot - tot0).max() <= 1e-12 * np.abs(q[:4]).reshape(4, -1).sum(1).max() * area
-    gr = [r for _, r in rows]
-    orr = [r for _, r in orows]
-    assert min(orr) - 3 <= min(gr) and max(gr) <= max(orr) + 3
+    # the restarts and the time reached, over the 20 steps of the two trajectories
+    gr = sum(r for _, r in rows)
+    orr = sum(r for _, r in orows)
+    assert abs(gr / orr - 1) <= 0.25, (gr, orr)
     t_gpu, t_or = sum(dt for dt, _ in rows), sum(dt for dt, _ in orows)
     assert 0.1 < t_gpu / t_or < 10
 

@@ -1,8 +1,9 @@
 """GPU parity of HWENO-DR, of the linear-gradient ablation and of Example 5.2's source in
 the batch (hweno_batch_init with such cases): the batched kernels run the single-grid
-bodies, so a batch must give the handles' states (to 1e-13 of the state scale in FP64,
-1e-6 mixed: the bodies are inlined into other kernels, whose multiply-add contractions
-may differ) and the oracle's steps to 1e-12.  Collected last, so that a failure here
+bodies, so a batch must give the handles' states (to 1e-13 of the state scale in FP64;
+mixed within four times the mixed handle's distance from the FP64 handle, since the
+bodies are inlined into other kernels, whose multiply-add contractions may differ) and
+the oracle's steps to 1e-12.  Collected last, so that a failure here
 cannot stop the other files under -x.
 """
 import numpy as np
@@ -67,10 +68,12 @@ def test_dr_batch_step_matches_the_oracle():
     b.close()
 
 
-@pytest.mark.parametrize("precision,bound", [("fp64", 1e-13), ("mixed", 1e-6)])
-def test_linear_gradient_batch_matches_handles(precision, bound):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_linear_gradient_batch_matches_handles(precision):
     """Remark 3.1's ablation in a batch: three steps of three cases against the ablated
-    handles"""
+    handles; FP64 to 1e-13, mixed within four times the mixed handle's own distance from
+    the FP64 handle (batches and handles compile the same FP32 expressions in different
+    kernels, whose multiply-add fusions may differ)"""
     cases = _cases()
     stream = torch.cuda.Stream()
     b = hweno.Batch([dict(c.params(), linear_grad=True) for c, _ in cases], precision=precision, stream=stream)
@@ -78,17 +81,27 @@ def test_linear_gradient_batch_matches_handles(precision, bound):
         b.cases[k].set_state(q.copy())
     for _ in range(3):
         b.step(1)
-    for k, (case, q) in enumerate(cases):
-        s = hweno.Solver(dict(case.params(), linear_grad=True), precision=precision, stream=stream)
+
+    def handle(case, q, prec):
+        s = hweno.Solver(dict(case.params(), linear_grad=True), precision=prec, stream=stream)
         s.set_state(q.copy())
         for _ in range(3):
             s.step()
-        ref = s.get_state().cpu().numpy()
+        out = s.get_state().cpu().numpy()
         s.close()
-        got = b.cases[k].get_state(np.zeros_like(q))
+        return out
+
+    def distance(a, r, q):
         scale = np.abs(q[:4]).reshape(4, -1).max(1)
-        err = max(np.abs(got[j] - ref[j]).max() / max(np.abs(ref[j]).max(), scale[j % 4]) for j in range(12))
-        assert err <= bound, (k, err)
+        return max(np.abs(a[j] - r[j]).max() / max(np.abs(r[j]).max(), scale[j % 4]) for j in range(12))
+
+    for k, (case, q) in enumerate(cases):
+        ref = handle(case, q, precision)
+        got = b.cases[k].get_state(np.zeros_like(q))
+        err = distance(got, ref, q)
+        bound = 1e-13 if precision == "fp64" else max(4 * distance(ref, handle(case, q, "fp64"), q), 1e-14)
+        print("case %d: batch against handle %.2e, bound %.2e" % (k, err, bound))
+        assert err <= bound, (k, err, bound)
     b.close()
 
 
