@@ -149,29 +149,6 @@ __host__ __device__ __forceinline__ double dmul_rn(double a, double b) {
 #endif
 }
 
-// x widened to double with integer operations: the same value, exactly (normal floats
-// and zeros re-biased; subnormal floats, infinities and NaN through the conversion)
-__host__ __device__ __forceinline__ double widen_f(float x) {
-  const unsigned int b = bits_of_f(x);
-  const unsigned int e = (b >> 23) & 0xffu;
-  const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
-  if ((b & 0x7fffffffu) == 0u) return double_of(s);
-  if (e == 0u || e == 0xffu) return (double)x;
-  return double_of(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29));
-}
-
-// a double that holds a float value, narrowed to that float with integer operations
-// (exact; for any other double the truncation of split_hilo's hi part; values outside
-// the normal float range through the conversion)
-__host__ __device__ __forceinline__ float narrow_exact(double x) {
-  const unsigned long long b = bits_of(x);
-  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-  if ((b & 0x7fffffffffffffffull) == 0ull) return float_of(sign);
-  const int fe = (int)((b >> 52) & 0x7ff) - 896;
-  if (fe < 1 || fe > 254) return (float)x;
-  return float_of(sign | ((unsigned int)fe << 23) | (unsigned int)((b >> 29) & 0x7fffffull));
-}
-
 __host__ __device__ __forceinline__ int clz32(unsigned int r) {  // r != 0
 #ifdef __CUDA_ARCH__
   return __clz((int)r);
@@ -180,10 +157,52 @@ __host__ __device__ __forceinline__ int clz32(unsigned int r) {  // r != 0
 #endif
 }
 
+// Conversions between float values and their FP64 planes in integer operations only:
+// on B300 the FP64 pipe also carries float/double conversions, and a conversion left in
+// a rarely taken branch is often evaluated for every value and selected afterwards.
+
+// x widened to double: the same value, exactly, for every float (subnormal ones
+// normalised; infinities and NaN, whose payload is kept, to their doubles)
+__host__ __device__ __forceinline__ double widen_f(float x) {
+  const unsigned int b = bits_of_f(x);
+  const unsigned int e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  const unsigned long long s = (unsigned long long)(b & 0x80000000u) << 32;
+  if (e == 0u) {
+    if (m == 0u) return double_of(s);
+    const int sh = clz32(m) - 8;  // brings the leading bit to position 23
+    return double_of(s | ((unsigned long long)(897 - sh) << 52) | ((unsigned long long)((m << sh) & 0x7fffffu) << 29));
+  }
+  const unsigned long long ed = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+  return double_of(s | (ed << 52) | ((unsigned long long)m << 29));
+}
+
+// x truncated to a float: its sign, exponent and leading 23 mantissa bits in the normal
+// float range, the truncated subnormal below it (zero below 2^-149), infinity beyond
+// it; NaN stays NaN.  Exact for a double that holds a float value.
+__host__ __device__ __forceinline__ float narrow_trunc(double x) {
+  const unsigned long long b = bits_of(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const int fe = E - 896;
+  if (fe >= 1 && fe <= 254) return float_of(sign | ((unsigned int)fe << 23) | (unsigned int)(m >> 29));
+  if (E == 0x7ff) {  // infinity; NaN keeps its leading payload bits (a quiet bit if none is left)
+    const unsigned int pl = (unsigned int)(m >> 29);
+    return float_of(sign | 0x7f800000u | (m == 0ull ? 0u : (pl != 0u ? pl : 0x400000u)));
+  }
+  if (fe > 254) return float_of(sign | 0x7f800000u);
+  const int sh = 30 - fe;  // the subnormal's integer mantissa is (2^52 + m) >> sh
+  return float_of(sign | (sh < 64 ? (unsigned int)((m | (1ull << 52)) >> sh) : 0u));
+}
+
+// a double that holds a float value, narrowed to that float (exactly)
+__host__ __device__ __forceinline__ float narrow_exact(double x) { return narrow_trunc(x); }
+
 // hi/lo split of a state value, with integer operations only: hi keeps the sign, the
 // exponent and the leading 23 mantissa bits of x (truncation), lo is the float nearest
 // below the exact remainder x - hi (the trailing 29 mantissa bits, normalised).  Zero
-// gives (0, 0); magnitudes below 2^-74 or beyond the float range take hi = fl(x), lo = 0.
+// gives (0, 0); magnitudes below 2^-74 or beyond the float range take hi =
+// narrow_trunc(x), lo = 0.
 __host__ __device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
   const unsigned long long b = bits_of(x);
   const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
@@ -196,7 +215,7 @@ __host__ __device__ __forceinline__ void split_hilo(double x, float& hi, float& 
   }
   // the remainder's float exponent field is fe - 52 + top >= fe - 52: keep it >= 1
   if (fe < 53 || fe > 254) {  // |x| < 2^-74, beyond the float range, inf or nan
-    hi = (float)x;
+    hi = narrow_trunc(x);
     lo = 0.0f;
     return;
   }
