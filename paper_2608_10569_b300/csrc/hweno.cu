@@ -339,10 +339,11 @@ static dim3 grid2(int wx, int wy, int z = 1) {
 }
 
 // ghost fill of a 12-plane state set
-// ghost fill of q's 12 planes and, with hilo, of the 24 planes of its hi/lo split
+// ghost fill of q's 12 planes and, with hilo, of the kept planes of its hi/lo split
+// (HILO_KEPT: the 12 hi planes and the averages' 4 lo planes)
 static void launch_ghost(hweno_handle* h, double* q, float* hilo = nullptr) {
   const Grid& g = h->g;
-  const int planes = hilo ? 36 : 12;
+  const int planes = hilo ? 12 + HILO_KEPT : 12;
   {
     Prof p(h, K_GHOST);
     const int n = 8 * g.ny;

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(FR_THREADS, HWENO_FR_MIN_BLOCKS) kb_flux_asm_m
 }
 
 // ghost fill: 1D items, gx = element index (x pass: 8 ny, y pass: 8 (nx + 8)); with
-// split, also the 24 planes of the state's hi/lo split
+// split, also the kept planes of the state's hi/lo split
 __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int pass,
                          int split) {
   HW_BATCH_LOOP(L, ncase)
@@ -226,8 +226,8 @@ __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncas
   else ghost_y_body(cg, &cd.open, q, gx);
   if (split) {
     float* hilo = mixed_planes(cw, cg.ps).hilo;
-    if (pass == 0) ghost_x_body(cg, &cd.open, hilo, gx, 0, 24);
-    else ghost_y_body(cg, &cd.open, hilo, gx, 0, 24);
+    if (pass == 0) ghost_x_body(cg, &cd.open, hilo, gx, 0, HILO_KEPT);
+    else ghost_y_body(cg, &cd.open, hilo, gx, 0, HILO_KEPT);
   }
   HW_BATCH_END
 }
@@ -242,7 +242,7 @@ __global__ void kb_split(const CaseDev* __restrict__ cases, TileList L, int ncas
     float hi, lo;
     split_hilo(q[gx], hi, lo);
     hilo[gx] = hi;
-    hilo[n + gx] = lo;
+    if (gx < 4 * cg.ps) hilo[n + gx] = lo;  // the averages' lo planes
   }
   HW_BATCH_END
 }

@@ -102,7 +102,9 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 }
 
 // one plane per blockIdx.y: 12 x the threads of a cell-wise loop over the planes;
-// with hilo, blockIdx.y = 12..35 fills the 24 planes of the state's hi/lo split too
+// with hilo, blockIdx.y = 12..27 fills the 16 planes of the state's hi/lo split that are
+// kept (the 12 hi planes and the averages' 4 lo planes; the moments' lo parts are 0)
+constexpr int HILO_KEPT = 16;
 __global__ void k_ghost_x(Grid g, const __grid_constant__ Open o, double* q, float* hilo) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
   if (p < 12) ghost_x_body(g, &o, q, t, p, p + 1);

@@ -24,7 +24,7 @@ struct WorkF {
   float* wy;     // 6
   float* rm;     // 18
   float* gr;     // 126: 6 components at the 12 face points, then at the 9 volume points
-  float* hilo;   // 24: hi of the 12 state planes, then lo
+  float* hilo;   // 24: hi of the 12 state planes, then lo (kept for the 4 average planes only)
   // the volume integrals of Eq. (3.2), per interior cell, from the gradient pass: vs, 14
   // sums of the gradient components over the 3x3 volume points (vol_visc_sums); iv, 8
   // quadrature sums of the inviscid fluxes (x then y, per conserved variable).  Float planes 126-147 of the
@@ -62,7 +62,7 @@ __global__ void k_split(Grid g, const double* __restrict__ q, float* __restrict_
     float hi, lo;
     split_hilo(q[t], hi, lo);
     hilo[t] = hi;
-    hilo[n + t] = lo;
+    if (t < 4 * g.ps) hilo[n + t] = lo;  // the averages' lo planes (no kernel reads the moments')
   }
 }
 

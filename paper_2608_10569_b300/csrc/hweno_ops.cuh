@@ -602,6 +602,10 @@ __device__ __forceinline__ unsigned int rk_cell(const Grid& g, int stage, long l
   return bad | rk_admissible<KEF>(stage, out, kef);
 }
 
+// the mixed path's base of the moments (float values): 8 float planes in the room of the
+// base group's double planes 4-7
+__host__ __device__ inline float* mixed_moment_base(double* base, long long ps) { return (float*)(base + 4 * ps); }
+
 // The mixed path's stage update of one cell: the averages as rk_cell does, from their
 // FP64 balances f0; the moments in FP32, from their FP32 balances fm.  The moments that
 // enter a stage are the modified moments of the FP32 reconstruction (Eq. (2.11)), FP32
@@ -610,8 +614,9 @@ __device__ __forceinline__ unsigned int rk_cell(const Grid& g, int stage, long l
 // single precision (explicit fused multiply-adds, the same in every kernel) and the
 // FP64 planes receive the FP32 result exactly (widen_f, narrow_exact: integer
 // operations, since B300's FP64 pipe also carries the conversions).  Also writes the
-// hi/lo split of the new state (24 float planes at hilo: the moments' lo parts are 0),
-// so that the next evaluation needs no separate split pass.
+// hi/lo split of the new state (the 12 hi planes and the averages' 4 lo planes at hilo:
+// the moments are float values, and no kernel reads their lo planes), so that the next
+// evaluation needs no separate split pass.
 template <bool KEF = false>
 __device__ __forceinline__ unsigned int rk_cell_mixed(const Grid& g, int stage, long long c, double dt,
                                                       const double* __restrict__ qin,
@@ -641,22 +646,23 @@ __device__ __forceinline__ unsigned int rk_cell_mixed(const Grid& g, int stage, 
     if (!finite_d(out[k])) bad = FLAG_INADMISSIBLE;
   }
   const float dtf = (float)dt;
+  float* basef = mixed_moment_base(base, g.ps);
 #pragma unroll
   for (int k = 4; k < 12; k++) {
-    const double cur = mom[(long long)(k - 4) * g.ps + c];
-    const float t = fmaf(dtf, fm[k - 4], narrow_exact(cur));
+    const float cur = narrow_exact(mom[(long long)(k - 4) * g.ps + c]);
+    const float t = fmaf(dtf, fm[k - 4], cur);
+    float* b = basef + (long long)(k - 4) * g.ps + c;
     float o;
     if (stage == 1) {
-      base[(long long)k * g.ps + c] = cur;
+      *b = cur;
       o = t;
     } else if (stage == 2) {
-      o = fmaf(0.75f, narrow_exact(base[(long long)k * g.ps + c]), 0.25f * t);
+      o = fmaf(0.75f, *b, 0.25f * t);
     } else {
-      o = fmaf(1.0f / 3.0f, narrow_exact(base[(long long)k * g.ps + c]), (2.0f / 3.0f) * t);
+      o = fmaf(1.0f / 3.0f, *b, (2.0f / 3.0f) * t);
     }
     qout[(long long)k * g.ps + c] = widen_f(o);
-    hilo[(long long)k * g.ps + c] = o;
-    hilo[(long long)(12 + k) * g.ps + c] = 0.0f;
+    hilo[(long long)k * g.ps + c] = o;  // a float value: no lo part
     if (!finite_f(o)) bad = FLAG_INADMISSIBLE;
   }
   return bad | rk_admissible<KEF>(stage, out, kef);
