@@ -343,7 +343,9 @@ int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections);
  * the fastest per kernel and re-captures the step graph.  chosen (6 ints, may be
  * NULL): the index of the kept shape for cons, face moments, weak moments, gradients,
  * fluxes and assembly/RK; -1 for the three gradient kinds of an HWENO-DR batch, whose
- * derivative kernel keeps its 32x2 block.  Does not change the states. */
+ * derivative kernel keeps its 32x2 block, and for the fluxes of a mixed batch, whose
+ * flux tile kernels keep their 32x7 tiles (a mixed batch's assembly/RK index is timed
+ * on its stage update).  Does not change the states. */
 int hweno_batch_autotune(hweno_batch* b, int* chosen);
 
 /* Kernel launches issued by the batch (graph replays count their nodes). */

@@ -1459,6 +1459,7 @@ struct hweno_batch {
   BatchList L[BR_N];
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;
+  int graph_launches = 0;  // kernels in the captured step graph
   int sms = 148;
   char err[512];
 };
@@ -1539,8 +1540,9 @@ static void batch_enqueue_step(hweno_batch* b) {
   b->launches++;
   for (int stage = 1; stage <= 3; stage++) {
     const int which = stage == 1 ? 0 : 1;
-    // mixed: stages 2 and 3 read the split their stage update wrote; stage 1 splits its
-    // state (a case may be repeated after a rejected attempt, or set from outside)
+    // mixed: stages 2 and 3 read the split their stage update wrote, and so does stage 1
+    // of a case whose last accepted step wrote it (split_ok); the other cases' stage 1
+    // splits its state (a case repeated after a rejected attempt, or set from outside)
     const int split = b->mixed && stage > 1;
     kb_ghost<<<grid(BR_GX), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GX].tl(), n, which, 0, split);
     kb_ghost<<<grid(BR_GY), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GY].tl(), n, which, 1, split);
@@ -1569,8 +1571,8 @@ static void batch_enqueue_step(hweno_batch* b) {
       kb_cons<0, true><<<grid(BR_CONS), dims(BR_CONS), CONS_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_CONS].tl(),
                                                                                  n, which);
       kb_dr<<<grid(BR_GRAD), dims(BR_GRAD), DR_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n, which);
-      kb_flux<0><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
-      kb_assemble<0><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
+      kb_flux<<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
+      kb_assemble<<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
       b->launches += 4;
     } else {
       kb_cons<0><<<grid(BR_CONS), dims(BR_CONS), CONS_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n,
@@ -1579,8 +1581,8 @@ static void batch_enqueue_step(hweno_batch* b) {
       kb_weak_moments<0><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
       if (b->lin) kb_grad<0, true><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
       else kb_grad<0><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
-      kb_flux<0><<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
-      kb_assemble<0><<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
+      kb_flux<<<grid(BR_FLUX), dims(BR_FLUX), 0, b->st>>>(b->d_cases, b->L[BR_FLUX].tl(), n);
+      kb_assemble<<<grid(BR_INT), dims(BR_INT), 0, b->st>>>(b->d_cases, b->L[BR_INT].tl(), n, which);
       b->launches += 6;
     }
     if (b->source) {
@@ -1609,23 +1611,22 @@ static int batch_grids(hweno_batch* b) {
     b->L[BR_WEAK].grid = persistent_grid(b, kb_weak_moments<1>, b->L[BR_WEAK].total);
     b->L[BR_GRAD].grid = b->lin ? persistent_grid(b, kb_grad<1, true>, b->L[BR_GRAD].total)
                                 : persistent_grid(b, kb_grad<1>, b->L[BR_GRAD].total);
-    b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<1>, b->L[BR_FLUX].total);
-    b->L[BR_INT].grid = persistent_grid(b, kb_assemble<1>, b->L[BR_INT].total);
+    b->L[BR_INT].grid = persistent_grid(b, kb_rk<1>, b->L[BR_INT].total);  // BR_FLUX: unused
     b->L[BR_FR].grid = persistent_grid(b, kb_flux_rk_mixed, b->L[BR_FR].total, 0, FR_THREADS);
     b->L[BR_FRA].grid = persistent_grid(b, kb_flux_asm_mixed, b->L[BR_FRA].total, 0, FR_THREADS);
   } else if (b->dr) {
     b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0, true>, b->L[BR_CONS].total, CONS_SMEM_BYTES);
     b->L[BR_GRAD].grid = persistent_grid(b, kb_dr, b->L[BR_GRAD].total, DR_SMEM_BYTES, DR_THREADS);
-    b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<0>, b->L[BR_FLUX].total);
-    b->L[BR_INT].grid = persistent_grid(b, kb_assemble<0>, b->L[BR_INT].total);
+    b->L[BR_FLUX].grid = persistent_grid(b, kb_flux, b->L[BR_FLUX].total);
+    b->L[BR_INT].grid = persistent_grid(b, kb_assemble, b->L[BR_INT].total);
   } else {
     b->L[BR_CONS].grid = persistent_grid(b, kb_cons<0>, b->L[BR_CONS].total, CONS_SMEM_BYTES);
     b->L[BR_FACE].grid = persistent_grid(b, kb_face_moments<0>, b->L[BR_FACE].total);
     b->L[BR_WEAK].grid = persistent_grid(b, kb_weak_moments<0>, b->L[BR_WEAK].total);
     b->L[BR_GRAD].grid = b->lin ? persistent_grid(b, kb_grad<0, true>, b->L[BR_GRAD].total)
                                 : persistent_grid(b, kb_grad<0>, b->L[BR_GRAD].total);
-    b->L[BR_FLUX].grid = persistent_grid(b, kb_flux<0>, b->L[BR_FLUX].total);
-    b->L[BR_INT].grid = persistent_grid(b, kb_assemble<0>, b->L[BR_INT].total);
+    b->L[BR_FLUX].grid = persistent_grid(b, kb_flux, b->L[BR_FLUX].total);
+    b->L[BR_INT].grid = persistent_grid(b, kb_assemble, b->L[BR_INT].total);
   }
   return HWENO_OK;
 }
@@ -1639,6 +1640,7 @@ static int batch_capture(hweno_batch* b) {
   BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal), "graph capture begin");
   const long long l0 = b->launches;
   batch_enqueue_step(b);
+  b->graph_launches = (int)(b->launches - l0);
   b->launches = l0;  // captured launches run (and are counted) at each replay
   BCK(cudaStreamEndCapture(b->st, &graph), "graph capture end");
   cudaError_t e = cudaGraphInstantiate(&b->exec, graph, 0);
@@ -1670,7 +1672,7 @@ static void batch_refresh_case(hweno_batch* b, int c) {
   cd.visc_cap = h->cfg.b_visc * h->cfg.Re * cd.hmin * cd.hmin;
   cd.dt_scale = 1.0;
   cd.active = 1;
-  cd.pad = 0;
+  cd.split_ok = b->mixed && h->split_of == h->Q ? 1 : 0;
 }
 
 extern "C" {
@@ -1780,7 +1782,7 @@ static int batch_attempt(hweno_batch* b) {
   int rc = batch_upload(b);
   if (rc) return rc;
   BCK(cudaGraphLaunch(b->exec, b->st), "graph launch");
-  b->launches += 1 + 3 * (6 + 3) + 1 + (b->mixed ? 1 : 0);  // reset, 3 stages, dt, stage-1 split
+  b->launches += b->graph_launches;
   BCK(cudaMemcpyAsync(b->h_diag, b->d_diag, b->n * sizeof(Diag), cudaMemcpyDeviceToHost, b->st), "diag read");
   BCK(cudaStreamSynchronize(b->st), "stream synchronize");
   return HWENO_OK;
@@ -1809,7 +1811,8 @@ int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections) {
           double* tmp = h->Q;
           h->Q = h->QS;
           h->QS = tmp;
-          h->split_of = nullptr;  // the batched stage update does not write the split
+          // the accepted stage-3 update wrote the split of its output, the new Q
+          h->split_of = b->mixed ? h->Q : nullptr;
           h->t += d.dt;
           h->dt_last = d.dt;
           h->steps++;
@@ -1825,6 +1828,8 @@ int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections) {
           left++;
           b->h_cases[c].dt_scale *= 0.5;
           b->h_cases[c].active = 1;
+          b->h_cases[c].split_ok = 0;  // the attempt's stage updates overwrote the split
+          h->split_of = nullptr;
         }
       }
       if (!left) break;
@@ -1862,6 +1867,11 @@ int hweno_batch_autotune(hweno_batch* b, int* chosen) {
       if (chosen) chosen[k] = -1;
       continue;
     }
+    // mixed: the face fluxes run in the flux tile kernels, whose tiles are fixed
+    if (b->mixed && k == BR_FLUX) {
+      if (chosen) chosen[k] = -1;
+      continue;
+    }
     float best = 1e30f;
     int bi = 0;
     for (int si = 0; si < 4; si++) {
@@ -1894,12 +1904,12 @@ int hweno_batch_autotune(hweno_batch* b, int* chosen) {
             else kb_grad<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
             break;
           case BR_FLUX:
-            if (b->mixed) kb_flux<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
-            else kb_flux<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
+            kb_flux<<<gr, blk, 0, b->st>>>(b->d_cases, tl, n);
             break;
           default:
-            if (b->mixed) kb_assemble<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
-            else kb_assemble<0><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
+            // mixed: the list's kernel is the stage update (on the scratch stage state)
+            if (b->mixed) kb_rk<1><<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 2);
+            else kb_assemble<<<gr, blk, 0, b->st>>>(b->d_cases, tl, n, 1);
             break;
         }
         b->launches++;
@@ -1919,6 +1929,8 @@ int hweno_batch_autotune(hweno_batch* b, int* chosen) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  // the discarded step and the timed stage updates overwrote the split planes
+  for (int c = 0; c < b->n; c++) b->h[c]->split_of = nullptr;
   batch_grids(b);
   BCK(cudaStreamSynchronize(b->st), "stream synchronize");
   return batch_capture(b);

@@ -17,7 +17,8 @@ struct CaseDev {
   double cfl, hmin, visc_cap;  // time-step rule of Sec. 5
   double dt_scale;             // 1, or 2^-k after k restarts of this step
   int active;                  // 0: the case does no work in this launch
-  int pad;
+  int split_ok;                // mixed: the kept split planes hold the split of Q (the last
+                               // accepted stage update wrote them), so stage 1 needs no split pass
   Open open;                   // prescribed states of the case's inflow faces
   Quad4 quad;                  // the source term's Gauss rule
   double t;                    // the case's time at the start of the step
@@ -115,21 +116,18 @@ __global__ void __launch_bounds__(128) kb_grad(const CaseDev* __restrict__ cases
   HW_BATCH_END
 }
 
-template <int MIXED>
+// the FP64 face fluxes and balances (a mixed batch runs them in the flux tile kernels below)
 __global__ void __launch_bounds__(128) kb_flux(const CaseDev* __restrict__ cases, TileList L, int ncase) {
   HW_BATCH_LOOP(L, ncase)
-  if (MIXED) flux_mixed_body(cg, cw, cd.diag, gx, gy, gz);
-  else flux_body<double>(cg, cw, cd.diag, gx, gy, gz);
+  flux_body<double>(cg, cw, cd.diag, gx, gy, gz);
   HW_BATCH_END
 }
 
-template <int MIXED>
 __global__ void __launch_bounds__(128) kb_assemble(const CaseDev* __restrict__ cases, TileList L, int ncase,
                                                    int which) {
   HW_BATCH_LOOP(L, ncase)
   double* rhs = which == 0 ? cd.RHS0 : cd.RHS;
-  if (MIXED) assemble_mixed_body(cg, cw, rhs, cd.diag, gx, gy);
-  else assemble_body<double>(cg, cw, rhs, cd.diag, gx, gy);
+  assemble_body<double>(cg, cw, rhs, cd.diag, gx, gy);
   HW_BATCH_END
 }
 
@@ -217,14 +215,15 @@ __global__ void __launch_bounds__(FR_THREADS, HWENO_FR_MIN_BLOCKS) kb_flux_asm_m
 }
 
 // ghost fill: 1D items, gx = element index (x pass: 8 ny, y pass: 8 (nx + 8)); with
-// split, also the kept planes of the state's hi/lo split
+// split (or for a case whose split is current), also the kept planes of the state's
+// hi/lo split
 __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int pass,
                          int split) {
   HW_BATCH_LOOP(L, ncase)
   double* q = which == 0 ? cd.Q : cd.QS;
   if (pass == 0) ghost_x_body(cg, &cd.open, q, gx);
   else ghost_y_body(cg, &cd.open, q, gx);
-  if (split) {
+  if (split || cd.split_ok) {
     float* hilo = mixed_planes(cw, cg.ps).hilo;
     if (pass == 0) ghost_x_body(cg, &cd.open, hilo, gx, 0, HILO_KEPT);
     else ghost_y_body(cg, &cd.open, hilo, gx, 0, HILO_KEPT);
@@ -232,12 +231,13 @@ __global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncas
   HW_BATCH_END
 }
 
-// hi/lo split of the mixed path: 1D items over the 12 whole padded planes
+// hi/lo split of the mixed path: 1D items over the 12 whole padded planes (none for a
+// case whose split is current)
 __global__ void kb_split(const CaseDev* __restrict__ cases, TileList L, int ncase, int which) {
   HW_BATCH_LOOP(L, ncase)
   const double* q = which == 0 ? cd.Q : cd.QS;
   const long long n = 12 * cg.ps;
-  if (gx < n) {
+  if (gx < n && !cd.split_ok) {
     float* hilo = mixed_planes(cw, cg.ps).hilo;
     float hi, lo;
     split_hilo(q[gx], hi, lo);

@@ -47,7 +47,9 @@ def test_batch_matches_single_solvers(precision, tune):
     stream.synchronize()
     if tune:
         chosen = b.autotune()
-        assert len(chosen) == 6 and all(0 <= c < 4 for c in chosen)
+        # a mixed batch's fluxes run in fixed tiles: not tuned
+        assert len(chosen) == 6 and all(0 <= c < 4 for k, c in enumerate(chosen) if not (precision == "mixed" and k == 4))
+        assert precision != "mixed" or chosen[4] == -1
     n0 = b.launch_count()
     assert b.step(3) == 0
     assert b.launch_count() > n0
