@@ -564,8 +564,8 @@ static int launch_rk(hweno_handle* h, int stage, const double* qin, const double
 
 // stage 2 or 3 of a step: the operator on the stage state q and the stage update into
 // qout.  On the mixed path (without a source term) the face fluxes, the balances and the
-// update run as one tile kernel, k_flux_rk_mixed, whose result equals the separate
-// kernels' bit for bit; otherwise the residual goes through HBM.
+// update run as one tile kernel, k_flux_rk_mixed, with the separate kernels' operations
+// in their order; otherwise the residual goes through HBM.
 static int stage_eval_rk(hweno_handle* h, double* q, int stage, double* qout, double cst) {
   const Grid& g = h->g;
   if (h->cfg.precision == HWENO_MIXED && !h->route64 && h->cfg.source == HWENO_SOURCE_NONE) {

@@ -608,7 +608,7 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
       tB[k] = fyf[(long long)k * g.ps + cb];
     }
 #pragma unroll
-    for (int v = 0; v < 4; v++) {  // the FP64 planes of S0 (k_flux_mixed's widening)
+    for (int v = 0; v < 4; v++) {  // the FP64 planes of S0 (flux_mixed_body's widening)
       dR[v] = w.fx[(long long)v * g.ps + c];
       dL[v] = w.fx[(long long)v * g.ps + cl];
       dT[v] = w.fy[(long long)v * g.ps + c];
@@ -628,9 +628,11 @@ __device__ __forceinline__ void assemble_mixed_body(const Grid& g, const Work& w
 // neighbouring tile, with the same operations on the same data, so both cells of a face
 // difference the same value and conservation is kept), then the balances and the stage
 // update of the tile's cells.  The residual and the face sums never go to HBM.  The
-// arithmetic is that of flux_mixed_body, assemble_mixed_body and rk_body, so the result
-// equals theirs bit for bit.  Stage 1 cannot be fused this way: its step size needs
-// alpha* over every face first, and its residual is kept for restarts.
+// operations are those of flux_mixed_body, assemble_mixed_body and rk_body in their
+// order (the host build, which fuses no multiply-add, finds the results equal bit for
+// bit; on the GPU each kernel's fusions may differ, within FP32 rounding).  Stage 1's
+// update cannot be fused this way: its step size needs alpha* over every face first, and
+// its residual is kept for restarts (k_flux_asm_mixed writes it).
 constexpr int FR_TX = 32, FR_TY = 7, FR_THREADS = 256;
 // resident blocks per SM that the tile kernels' register budget is set for (3: 80
 // registers, no spills)

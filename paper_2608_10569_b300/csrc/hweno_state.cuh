@@ -259,7 +259,7 @@ __host__ __device__ __forceinline__ bool is_mirror(int bc) {
   return bc == HWENO_BC_NOSLIP || bc == HWENO_BC_SYMMETRY || bc == HWENO_BC_SLIP;
 }
 
-// value of inflow plane p: the FP64 state itself, or on the 24 float planes of the
+// value of inflow plane p: the FP64 state itself, or on the float planes of the
 // hi/lo split (planes 0..11 hi, 12..23 lo) the part that split_hilo gives
 __host__ __device__ __forceinline__ double open_value(double x, int, const double*) { return x; }
 __host__ __device__ __forceinline__ float open_value(double x, int p, const float*) {
@@ -274,7 +274,8 @@ __host__ __device__ __forceinline__ const double* inflow_state(const Open& o, in
 }
 
 // planes [p0, p1) of the state (plane 4 m + v: moment m of variable v), or of its
-// hi/lo split (24 float planes: plane p holds state plane p mod 12).  o may be NULL
+// hi/lo split (24 float planes, of which the mixed path keeps 16: plane p holds state
+// plane p mod 12).  o may be NULL
 // where no face is an inflow face.
 template <class E>
 __host__ __device__ __forceinline__ void ghost_x_body(const Grid& g, const Open* o, E* q, int t, int p0 = 0,

@@ -11,8 +11,9 @@
 // block sets FLAG_TIMEOUT and returns).  The weak moments of the tile grown by 1 are
 // then formed in shared memory from the face moments of each cell's four faces, and
 // each thread reconstructs the six gradient components of its cell from them.  The
-// arithmetic of each quantity is that of the separate kernels, so the gradients equal
-// theirs bit for bit.
+// operations of each quantity are those of the separate kernels in their order (the
+// host build finds the gradients equal bit for bit; on the GPU the kernels' multiply-add
+// fusions may differ, within FP32 rounding).
 #pragma once
 #ifdef __CUDACC__
 #include <cuda.h>
