@@ -119,6 +119,51 @@ def test_batch_restarts_only_the_rejected_case():
     b.close()
 
 
+def test_mixed_batch_restarts_only_the_rejected_case():
+    """The same pair in the mixed path over three steps: the rejected case's stage 1
+    splits its state again on each retry (the attempt's stage updates overwrote the
+    split), the accepted cases reuse the split their last stage-3 update wrote.  Each case
+    ends with its mixed single-grid solver's restarts, within FP32 rounding of its state
+    (four times the mixed solver's own distance from the FP64 solver)."""
+    fast, qf = I.shock_tube(48, 24)
+    fast.cfl = 8.0
+    fast.b_visc = 10.0
+    calm, qc = I.random_smooth(20, 20, seed=4)
+    b = hweno.Batch([fast.params(), calm.params()], precision="mixed", stream=torch.cuda.Stream())
+    b.cases[0].set_state(qf.copy())
+    b.cases[1].set_state(qc.copy())
+    rej = b.step(3)
+    assert rej > 0
+    for view, (case, q) in zip(b.cases, [(fast, qf), (calm, qc)]):
+        out = {}
+        for prec in ("mixed", "fp64"):
+            s = hweno.Solver(case.params(), precision=prec)
+            s.set_state(q.copy())
+            for _ in range(3):
+                s.step()
+            out[prec] = (s.get_state(np.zeros_like(q)), s.diag())
+            s.close()
+        got = view.get_state(np.zeros_like(q))
+        assert view.diag()["steps"] == 3 and view.diag()["rejected"] == out["mixed"][1]["rejected"]
+        err = mixed_distance(got, out["mixed"][0], q)
+        bound = mixed_distance(out["mixed"][0], out["fp64"][0], q)
+        print("%s: batch against handle %.2e, mixed handle against FP64 %.2e" % (case.name, err, bound))
+        assert err <= max(4 * bound, 1e-14)
+        # the case's own residual reuses the split the batch's last update wrote: the same
+        # kernels on the same split as a fresh handle, which splits the state itself
+        rhs_view = view.residual()[0]
+        torch.cuda.synchronize()  # the view works on the batch's stream
+        rhs_view = rhs_view.cpu().numpy()
+        s = hweno.Solver(case.params(), precision="mixed")
+        s.set_state(got.copy())
+        rhs_fresh = s.residual()[0]
+        torch.cuda.synchronize()
+        assert np.array_equal(rhs_view, rhs_fresh.cpu().numpy())
+        s.close()
+    assert b.cases[0].diag()["rejected"] == rej and b.cases[1].diag()["rejected"] == 0
+    b.close()
+
+
 def test_ensemble_case_against_the_oracle_at_full_length():
     """The 64-case ensemble's first 128^2 case, stepped by the batch for its 100 steps
     in FP64 and in mixed precision, against the FP64 oracle run at the batch's step
