@@ -492,7 +492,10 @@ __device__ __forceinline__ float face_sums_mixed(const Grid& g, const WorkF& f, 
   return beta;
 }
 
-// the face fluxes are stored in FP64 so that the moment balances difference them exactly
+// One face's sums written to the face-flux planes (S0 in FP64 planes 0-3 and again, with
+// S1, as FP32 planes in 8-11), and assemble_mixed_body below: the per-face and per-cell
+// form of what the flux tile kernels compute in shared memory.  No GPU kernel launches
+// them; the host checks run them as the reference the tiles must equal.
 __device__ __forceinline__ void flux_mixed_body(const Grid& g, const Work& w, Diag* diag, int gx, int gy, int gz) {
   const int dir = gz;
   const int i = gx - (dir == 0 ? 1 : 0);
