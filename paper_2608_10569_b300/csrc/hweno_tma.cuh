@@ -98,17 +98,16 @@ __device__ __forceinline__ void gradtile_weak_cell(const Grid& g, const GradTile
 }
 
 // the six gradient components of tile cell (tx, ty), cell (i, j), from the staged weak
-// moments, with the operations of grad_mixed_body (its volume sums for interior cells;
-// VOLG: also the volume-point gradients); LIN: the linear weights (Remark 3.1)
+// moments, with the operations of grad_mixed_body (its volume sums for interior cells,
+// from the weights wu, wv that vol_weights formed; VOLG: also the volume-point
+// gradients); LIN: the linear weights (Remark 3.1)
 template <bool LIN, bool VOLG = false>
 __device__ __forceinline__ void gradtile_grad_cell(const Grid& g, const Work& w, const GradTile& tt, int tx,
-                                                            int ty, int i, int j) {
+                                                            int ty, int i, int j, const float* wu, const float* wv) {
   const WorkF f = mixed_planes(w, g.ps);
   const long long c = cidx(g, i, j);
   const float eps = g.eps_wenof;
   const bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
-  float wu[9], wv[9];
-  if (interior) vol_weights(g, f, c, wu, wv);
   const int plane = GR_Y * GR_X;
   const int rx = tx + 1, ry = ty + 1;
 #pragma unroll 1
@@ -225,6 +224,12 @@ __global__ void __launch_bounds__(GT_THREADS) k_grad_tma_mixed(Grid g, Work w, c
     tma_load_4d(smem_addr(gt_smem), &tr_map, GT_X * (int)blockIdx.x, b - 2 + NG, 1, 0, b_addr);
     tma_load_3d(smem_addr(gt_smem + GT_TR_FLOATS), &wb_map, GT_X * (int)blockIdx.x, b - 2 + NG, 0, b_addr);
   }
+  // while the copies are in flight: this thread's cell's volume values (global loads),
+  // their weights for the viscous volume sums and the inviscid sums
+  const int tx = t % GT_X, ty = t / GT_X;
+  const int i = a + tx, j = b + ty;
+  float wu[9], wv[9];
+  if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) vol_weights(g, mixed_planes(w, g.ps), cidx(g, i, j), wu, wv);
   if (!mbar_wait_bounded(b_addr, 0, GT_WAIT_LIMIT)) {
     if (t == 0) {
       atomicOr(&diag->flags, FLAG_TIMEOUT);
@@ -235,9 +240,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_grad_tma_mixed(Grid g, Work w, c
   GradTile tt{gt_smem, gt_smem + GT_TR_FLOATS, gt_smem + GT_TR_FLOATS + GT_WB_FLOATS};
   for (int k = t; k < GR_X * GR_Y; k += GT_THREADS) gradtile_weak_cell(g, tt, k % GR_X, k / GR_X);
   __syncthreads();
-  const int tx = t % GT_X, ty = t / GT_X;
-  const int i = a + tx, j = b + ty;
-  if (i < g.nx + 1 && j < g.ny + 1) gradtile_grad_cell<LIN>(g, w, tt, tx, ty, i, j);
+  if (i < g.nx + 1 && j < g.ny + 1) gradtile_grad_cell<LIN>(g, w, tt, tx, ty, i, j, wu, wv);
 }
 #endif
 

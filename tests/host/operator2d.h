@@ -71,9 +71,12 @@ inline void grad_tma_emulated(const hweno_config& c, const Grid& g, const Work& 
       for (int k = 0; k < GR_X * GR_Y; k++) gradtile_weak_cell(g, tt, k % GR_X, k / GR_X);
       for (int t = 0; t < GT_THREADS; t++) {
         const int tx = t % GT_X, ty = t / GT_X, i = a + tx, j = b + ty;
+        // the kernel forms the volume weights (and the inviscid sums) while its copies fly
+        float wu[9], wv[9];
+        if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) vol_weights(g, f, cidx(g, i, j), wu, wv);
         if (i < g.nx + 1 && j < g.ny + 1) {
-          if (c.linear_grad) gradtile_grad_cell<true>(g, w, tt, tx, ty, i, j);
-          else gradtile_grad_cell<false>(g, w, tt, tx, ty, i, j);
+          if (c.linear_grad) gradtile_grad_cell<true>(g, w, tt, tx, ty, i, j, wu, wv);
+          else gradtile_grad_cell<false>(g, w, tt, tx, ty, i, j, wu, wv);
         }
       }
     }
