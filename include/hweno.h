@@ -345,7 +345,9 @@ int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections);
  * fluxes and assembly/RK; -1 for the three gradient kinds of an HWENO-DR batch, whose
  * derivative kernel keeps its 32x2 block, and for the fluxes of a mixed batch, whose
  * flux tile kernels keep their 32x7 tiles (a mixed batch's assembly/RK index is timed
- * on its stage update).  Does not change the states. */
+ * on its stage update), and for its three gradient kinds when it runs them in the
+ * TMA-staged pass over 32x8 tiles (at most 64 cases, as a handle does).  Does not change
+ * the states. */
 int hweno_batch_autotune(hweno_batch* b, int* chosen);
 
 /* Kernel launches issued by the batch (graph replays count their nodes). */

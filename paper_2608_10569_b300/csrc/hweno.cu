@@ -379,6 +379,10 @@ static cudaError_t cons_smem_allow() {
     e = cudaFuncSetAttribute(k_grad_tma_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM_BYTES);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grad_tma_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_grad_tma_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_grad_tma_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM_BYTES);
   if (e == cudaSuccess && dev < 32) done.fetch_or(1u << dev);
   return e;
 }
@@ -1431,7 +1435,7 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 // kernel for all cases, one CUDA graph per SSP-RK3 step of the whole ensemble.
 
 namespace {
-enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_FR, BR_FRA, BR_N };
+enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_FR, BR_FRA, BR_GT, BR_N };
 
 struct BatchList {
   int bx = 32, by = 4;  // block shape of the kernels that use this list
@@ -1449,6 +1453,10 @@ struct hweno_batch {
   int dr = 0;   // HWENO-DR: kb_dr on the BR_GRAD list in place of the three gradient kernels
   int lin = 0;     // the linear-gradient ablation: the LIN instantiations of kb_grad
   int source = 0;  // some case has a source term: kb_source after each stage's balances
+  // mixed: the cases' tensor maps for kb_grad_tma_mixed (tma: every case has them and the
+  // batch holds at most BT_MAX_CASES cases; else the separate gradient kernels)
+  bool tma = false;
+  BatchTraceMaps* maps = nullptr;
   cudaStream_t st = nullptr;
   bool own_stream = false;
   std::vector<hweno_handle*> h;
@@ -1487,7 +1495,7 @@ static void region_of(int k, const Grid& g, int& wx, int& wy, int& wz) {
     case BR_CONS: wx = g.nx + 6; wy = g.ny + 6; break;
     case BR_FACE: wx = g.nx + 5; wy = g.ny + 5; wz = 2; break;
     case BR_WEAK: wx = g.nx + 4; wy = g.ny + 4; break;
-    case BR_GRAD: wx = g.nx + 2; wy = g.ny + 2; break;
+    case BR_GRAD: case BR_GT: wx = g.nx + 2; wy = g.ny + 2; break;
     case BR_FLUX: wx = g.nx + 1; wy = g.ny + 1; wz = 2; break;
     case BR_INT: case BR_FR: case BR_FRA: wx = g.nx; wy = g.ny; break;
     case BR_GX: wx = 8 * g.ny; wy = 1; break;
@@ -1553,11 +1561,23 @@ static void batch_enqueue_step(hweno_batch* b) {
         b->launches++;
       }
       kb_cons<1><<<grid(BR_CONS), dims(BR_CONS), 0, b->st>>>(b->d_cases, b->L[BR_CONS].tl(), n, which);
-      kb_face_moments<1><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
-      kb_weak_moments<1><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
-      if (b->lin) kb_grad<1, true><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
-      else kb_grad<1><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
-      b->launches += 4;
+      b->launches++;
+      if (b->tma) {
+        // face moments, weak moments and gradients in one TMA-staged pass, as a handle does
+        if (b->lin)
+          kb_grad_tma_mixed<true><<<grid(BR_GT), GT_THREADS, GT_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_GT].tl(), n,
+                                                                                     *b->maps);
+        else
+          kb_grad_tma_mixed<false><<<grid(BR_GT), GT_THREADS, GT_SMEM_BYTES, b->st>>>(b->d_cases, b->L[BR_GT].tl(),
+                                                                                      n, *b->maps);
+        b->launches++;
+      } else {
+        kb_face_moments<1><<<grid(BR_FACE), dims(BR_FACE), 0, b->st>>>(b->d_cases, b->L[BR_FACE].tl(), n);
+        kb_weak_moments<1><<<grid(BR_WEAK), dims(BR_WEAK), 0, b->st>>>(b->d_cases, b->L[BR_WEAK].tl(), n);
+        if (b->lin) kb_grad<1, true><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+        else kb_grad<1><<<grid(BR_GRAD), dims(BR_GRAD), 0, b->st>>>(b->d_cases, b->L[BR_GRAD].tl(), n);
+        b->launches += 3;
+      }
       if (stage > 1 && !b->source) {
         // stages 2 and 3: fluxes, balances and the stage update in one tile kernel
         kb_flux_rk_mixed<<<grid(BR_FR), FR_THREADS, 0, b->st>>>(b->d_cases, b->L[BR_FR].tl(), n, stage);
@@ -1611,6 +1631,11 @@ static int batch_grids(hweno_batch* b) {
     b->L[BR_WEAK].grid = persistent_grid(b, kb_weak_moments<1>, b->L[BR_WEAK].total);
     b->L[BR_GRAD].grid = b->lin ? persistent_grid(b, kb_grad<1, true>, b->L[BR_GRAD].total)
                                 : persistent_grid(b, kb_grad<1>, b->L[BR_GRAD].total);
+    if (b->tma)
+      b->L[BR_GT].grid = b->lin ? persistent_grid(b, kb_grad_tma_mixed<true>, b->L[BR_GT].total, GT_SMEM_BYTES,
+                                                  GT_THREADS)
+                                : persistent_grid(b, kb_grad_tma_mixed<false>, b->L[BR_GT].total, GT_SMEM_BYTES,
+                                                  GT_THREADS);
     b->L[BR_INT].grid = persistent_grid(b, kb_rk<1>, b->L[BR_INT].total);  // BR_FLUX: unused
     b->L[BR_FR].grid = persistent_grid(b, kb_flux_rk_mixed, b->L[BR_FR].total, 0, FR_THREADS);
     b->L[BR_FRA].grid = persistent_grid(b, kb_flux_asm_mixed, b->L[BR_FRA].total, 0, FR_THREADS);
@@ -1733,9 +1758,25 @@ int hweno_batch_init(const hweno_config* cfgs, int ncases, void* stream, hweno_b
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_diag, 0, ncases * sizeof(Diag), b->st);
     if (e != cudaSuccess) rc = bfail(b, HWENO_ERR_CUDA, "hweno_batch_init: allocation failed");
   }
+  if (!rc && b->mixed && ncases <= BT_MAX_CASES) {
+    b->tma = true;
+    for (int c = 0; c < ncases; c++) b->tma = b->tma && b->h[c]->tma;
+    if (b->tma) {
+      b->maps = new (std::nothrow) BatchTraceMaps();
+      if (!b->maps) {
+        b->tma = false;
+      } else {
+        for (int c = 0; c < ncases; c++) {
+          b->maps->tr[c] = b->h[c]->tr_map;
+          b->maps->wb[c] = b->h[c]->wb_map;
+        }
+      }
+    }
+  }
   for (int k = 0; k < BR_N && !rc; k++) {
     if (b->dr && k == BR_GRAD) rc = build_list(b, k, 32, DR_THREADS / 32);  // kb_dr's block
     else if (k == BR_FR || k == BR_FRA) rc = build_list(b, k, FR_TX, FR_TY);  // the mixed tile kernels
+    else if (k == BR_GT) rc = build_list(b, k, GT_X, GT_Y);                   // kb_grad_tma_mixed's tiles
     else rc = build_list(b, k, k <= BR_INT ? 32 : 128, k <= BR_INT ? 4 : 1);
   }
   if (!rc) rc = batch_grids(b);
@@ -1764,6 +1805,7 @@ void hweno_batch_destroy(hweno_batch* b) {
   if (b->d_diag) cudaFree(b->d_diag);
   if (b->h_diag) cudaFreeHost(b->h_diag);
   if (b->own_stream) cudaStreamDestroy(b->st);
+  delete b->maps;
   delete b;
 }
 
@@ -1803,6 +1845,9 @@ int hweno_batch_step(hweno_batch* b, int nsteps, int* rejections) {
       int rc = batch_attempt(b);
       if (rc) return rc;
       int left = 0;
+      for (int c = 0; c < b->n; c++)
+        if (pending[c] && (b->h_diag[c].flags & FLAG_TIMEOUT))
+          return bfail(b, HWENO_ERR_TIMEOUT, "hweno_batch_step: a tensor copy's wait gave up");
       for (int c = 0; c < b->n; c++) {
         if (!pending[c]) continue;
         const Diag& d = b->h_diag[c];
@@ -1867,8 +1912,9 @@ int hweno_batch_autotune(hweno_batch* b, int* chosen) {
       if (chosen) chosen[k] = -1;
       continue;
     }
-    // mixed: the face fluxes run in the flux tile kernels, whose tiles are fixed
-    if (b->mixed && k == BR_FLUX) {
+    // mixed: the face fluxes run in the flux tile kernels, whose tiles are fixed, and with
+    // the tensor maps the gradient kinds in kb_grad_tma_mixed's fixed tiles
+    if ((b->mixed && k == BR_FLUX) || (b->tma && (k == BR_FACE || k == BR_WEAK || k == BR_GRAD))) {
       if (chosen) chosen[k] = -1;
       continue;
     }

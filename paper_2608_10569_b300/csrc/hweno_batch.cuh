@@ -5,6 +5,7 @@
 #pragma once
 #include "hweno_mixed.cuh"
 #include "hweno_source.cuh"
+#include "hweno_tma.cuh"
 
 namespace hw {
 
@@ -265,5 +266,43 @@ __global__ void kb_dt(const CaseDev* __restrict__ cases, int ncase) {
   const double a = __longlong_as_double((long long)cd.diag->alpha_bits);
   cd.diag->dt = fmin(cd.cfl * cd.hmin / a, cd.visc_cap) * cd.dt_scale;
 }
+
+#ifdef __CUDACC__
+// the tensor maps of a mixed batch's cases (traces and cell means, as a handle builds them
+// for its own TMA-staged gradient pass), passed to kb_grad_tma_mixed as one kernel
+// parameter: at most BT_MAX_CASES cases (a larger batch runs the separate kernels)
+constexpr int BT_MAX_CASES = 64;
+struct BatchTraceMaps {
+  CUtensorMap tr[BT_MAX_CASES];
+  CUtensorMap wb[BT_MAX_CASES];
+};
+
+// the gradient pass of a mixed batch: k_grad_tma_mixed's tiles (GT_X x GT_Y cells of each
+// case's gradient region, copied into shared memory by the Tensor Memory Accelerator)
+// over a work list of (case, tile) items; the block's mbarrier completes one phase per
+// tile it processes
+template <bool LIN>
+__global__ void __launch_bounds__(GT_THREADS) kb_grad_tma_mixed(const CaseDev* __restrict__ cases, TileList L,
+                                                                int ncase,
+                                                                const __grid_constant__ BatchTraceMaps maps) {
+  extern __shared__ __align__(16) unsigned char gt_raw[];
+  unsigned b_addr;
+  float* gt_smem = grad_tma_smem(gt_raw, &b_addr);
+  unsigned parity = 0;
+  const int total = L.start[ncase];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_case(L.start, ncase, item);
+    const CaseDev& cd = cases[c];
+    if (!cd.active) continue;  // the same for every thread of the block
+    const Grid cg = cd.g;
+    const Work cw = cd.w;
+    const int l = item - L.start[c];
+    const int by = l / L.tx[c], bx = l - by * L.tx[c];
+    if (!grad_tma_tile<LIN>(cg, cw, &maps.tr[c], &maps.wb[c], bx, by, gt_smem, b_addr, parity, cd.diag)) return;
+    parity ^= 1u;
+    __syncthreads();  // the next tile overwrites the staged data and the weak moments
+  }
+}
+#endif
 
 }  // namespace hw

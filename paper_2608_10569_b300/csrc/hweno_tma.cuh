@@ -206,23 +206,25 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
 // attempts of the bounded waits: far longer than any copy of a ~75 KB box takes
 constexpr long long GT_WAIT_LIMIT = 1ll << 22;
 
-template <bool LIN = false>
-__global__ void __launch_bounds__(GT_THREADS) k_grad_tma_mixed(Grid g, Work w, const __grid_constant__ CUtensorMap tr_map,
-                                                               const __grid_constant__ CUtensorMap wb_map, Diag* diag) {
-  extern __shared__ __align__(16) unsigned char gt_raw[];
-  float* gt_smem = (float*)(((unsigned long long)gt_raw + 127) & ~127ull);
-  unsigned long long* bar = (unsigned long long*)((unsigned char*)gt_smem + GT_DATA_BYTES);
+// One tile of the gradient pass, tile (bx, by) of the gradient region: origin cell
+// (a, b) = (-1 + GT_X bx, -1 + GT_Y by).  Thread 0 issues the two tensor copies on the
+// block's mbarrier at b_addr (parity: the phase this use completes); while they fly every
+// thread forms its cell's volume weights and inviscid sums (global loads); then each
+// waits (bounded), the block forms the weak moments of the grown tile and each thread
+// its cell's gradients.  Returns false when a wait gave up (FLAG_TIMEOUT set in diag):
+// the block must stop.  The caller separates two uses of the shared tile by a barrier.
+template <bool LIN>
+__device__ __forceinline__ bool grad_tma_tile(const Grid& g, const Work& w, const CUtensorMap* tr_map,
+                                              const CUtensorMap* wb_map, int bx, int by, float* gt_smem,
+                                              unsigned b_addr, unsigned parity, Diag* diag) {
   const int t = threadIdx.x;
-  const int a = -1 + GT_X * (int)blockIdx.x, b = -1 + GT_Y * (int)blockIdx.y;  // tile origin (cell)
-  const unsigned b_addr = smem_addr(bar);
-  if (t == 0) mbar_init(b_addr, 1);
-  __syncthreads();
+  const int a = -1 + GT_X * bx, b = -1 + GT_Y * by;  // tile origin (cell)
   if (t == 0) {
     mbar_expect_tx(b_addr, GT_TX_BYTES);
-    // padded column 32 blockIdx.x is cell a - 3; padded row b - 2 + NG; variables 1..3
-    // (u, v, e) of every point; the w-bar planes over the same columns and rows
-    tma_load_4d(smem_addr(gt_smem), &tr_map, GT_X * (int)blockIdx.x, b - 2 + NG, 1, 0, b_addr);
-    tma_load_3d(smem_addr(gt_smem + GT_TR_FLOATS), &wb_map, GT_X * (int)blockIdx.x, b - 2 + NG, 0, b_addr);
+    // padded column 32 bx is cell a - 3; padded row b - 2 + NG; variables 1..3 (u, v, e)
+    // of every point; the w-bar planes over the same columns and rows
+    tma_load_4d(smem_addr(gt_smem), tr_map, GT_X * bx, b - 2 + NG, 1, 0, b_addr);
+    tma_load_3d(smem_addr(gt_smem + GT_TR_FLOATS), wb_map, GT_X * bx, b - 2 + NG, 0, b_addr);
   }
   // while the copies are in flight: this thread's cell's volume values (global loads),
   // their weights for the viscous volume sums and the inviscid sums
@@ -230,17 +232,38 @@ __global__ void __launch_bounds__(GT_THREADS) k_grad_tma_mixed(Grid g, Work w, c
   const int i = a + tx, j = b + ty;
   float wu[9], wv[9];
   if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) vol_weights(g, mixed_planes(w, g.ps), cidx(g, i, j), wu, wv);
-  if (!mbar_wait_bounded(b_addr, 0, GT_WAIT_LIMIT)) {
+  if (!mbar_wait_bounded(b_addr, parity, GT_WAIT_LIMIT)) {
     if (t == 0) {
       atomicOr(&diag->flags, FLAG_TIMEOUT);
-      mbar_wait_bounded(b_addr, 0, GT_WAIT_LIMIT);  // the copies may still land: give them time
+      mbar_wait_bounded(b_addr, parity, GT_WAIT_LIMIT);  // the copies may still land: give them time
     }
-    return;
+    return false;
   }
   GradTile tt{gt_smem, gt_smem + GT_TR_FLOATS, gt_smem + GT_TR_FLOATS + GT_WB_FLOATS};
   for (int k = t; k < GR_X * GR_Y; k += GT_THREADS) gradtile_weak_cell(g, tt, k % GR_X, k / GR_X);
   __syncthreads();
   if (i < g.nx + 1 && j < g.ny + 1) gradtile_grad_cell<LIN>(g, w, tt, tx, ty, i, j, wu, wv);
+  return true;
+}
+
+// the block's staged tile (from a 128-byte boundary of the dynamic shared memory, whose
+// base the launch guarantees only to 16 bytes) and its mbarrier after it, initialised by
+// thread 0 (one arrival per phase)
+__device__ __forceinline__ float* grad_tma_smem(unsigned char* raw, unsigned* b_addr) {
+  float* gt_smem = (float*)(((unsigned long long)raw + 127) & ~127ull);
+  *b_addr = smem_addr((unsigned char*)gt_smem + GT_DATA_BYTES);
+  if (threadIdx.x == 0) mbar_init(*b_addr, 1);
+  __syncthreads();
+  return gt_smem;
+}
+
+template <bool LIN = false>
+__global__ void __launch_bounds__(GT_THREADS) k_grad_tma_mixed(Grid g, Work w, const __grid_constant__ CUtensorMap tr_map,
+                                                               const __grid_constant__ CUtensorMap wb_map, Diag* diag) {
+  extern __shared__ __align__(16) unsigned char gt_raw[];
+  unsigned b_addr;
+  float* gt_smem = grad_tma_smem(gt_raw, &b_addr);
+  grad_tma_tile<LIN>(g, w, &tr_map, &wb_map, (int)blockIdx.x, (int)blockIdx.y, gt_smem, b_addr, 0u, diag);
 }
 #endif
 

@@ -1,11 +1,11 @@
 """Batched ensembles (hweno_batch_*): every case of a batch must follow the steps its own
 single-grid solver takes (same per-cell bodies, same per-case time step), also after the
 autotuner changed the tile shapes, and with per-case restarts: in FP64 bit for bit.  In
-the mixed path a single handle forms the gradients in the TMA-staged kernel and a batch
-in the separate face-moment, weak-moment and gradient kernels; the FP32 expressions are
-the same, but a multiply and an add written without a rounding mode may be fused into
-one multiply-add by the code generator, differently in different kernels, so a mixed
-batch and a mixed handle agree to FP32 rounding: their distance is bounded by the mixed
+the mixed path a batch runs the handles' FP32 expressions in its own kernels (the
+TMA-staged gradient pass over its work list, the flux tile kernels); a multiply and an
+add written without a rounding mode may be fused into one multiply-add by the code
+generator, differently in different kernels, so a mixed batch and a mixed handle agree
+to FP32 rounding: their distance is bounded by the mixed
 handle's own distance from the FP64 handle on the same case."""
 import numpy as np
 import pytest
@@ -47,9 +47,10 @@ def test_batch_matches_single_solvers(precision, tune):
     stream.synchronize()
     if tune:
         chosen = b.autotune()
-        # a mixed batch's fluxes run in fixed tiles: not tuned
-        assert len(chosen) == 6 and all(0 <= c < 4 for k, c in enumerate(chosen) if not (precision == "mixed" and k == 4))
-        assert precision != "mixed" or chosen[4] == -1
+        # a mixed batch's fluxes and (TMA-staged) gradient kinds run in fixed tiles: not tuned
+        fixed = (1, 2, 3, 4) if precision == "mixed" else ()
+        assert len(chosen) == 6 and all(0 <= c < 4 for k, c in enumerate(chosen) if k not in fixed)
+        assert all(chosen[k] == -1 for k in fixed)
     n0 = b.launch_count()
     assert b.step(3) == 0
     assert b.launch_count() > n0
