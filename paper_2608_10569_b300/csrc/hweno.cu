@@ -344,16 +344,9 @@ static dim3 grid2(int wx, int wy, int z = 1) {
 static void launch_ghost(hweno_handle* h, double* q, float* hilo = nullptr) {
   const Grid& g = h->g;
   const int planes = hilo ? 12 + HILO_KEPT : 12;
-  {
-    Prof p(h, K_GHOST);
-    const int n = 8 * g.ny;
-    k_ghost_x<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, h->open, q, hilo);
-  }
-  {
-    Prof p(h, K_GHOST);
-    const int n = 8 * (g.nx + 2 * NG);
-    k_ghost_y<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, h->open, q, hilo);
-  }
+  Prof p(h, K_GHOST);
+  const int n = 8 * g.ny + 8 * (g.nx + 2 * NG);
+  k_ghost<<<dim3((n + 127) / 128, planes), 128, 0, h->st>>>(g, h->open, q, hilo);
 }
 
 // the FP64 cell-trace kernels take CONS_SMEM_BYTES of dynamic shared memory (above the
@@ -1435,7 +1428,7 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 // kernel for all cases, one CUDA graph per SSP-RK3 step of the whole ensemble.
 
 namespace {
-enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GX, BR_GY, BR_SPLIT, BR_FR, BR_FRA, BR_GT, BR_N };
+enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GHOST, BR_SPLIT, BR_FR, BR_FRA, BR_GT, BR_N };
 
 struct BatchList {
   int bx = 32, by = 4;  // block shape of the kernels that use this list
@@ -1498,8 +1491,7 @@ static void region_of(int k, const Grid& g, int& wx, int& wy, int& wz) {
     case BR_GRAD: case BR_GT: wx = g.nx + 2; wy = g.ny + 2; break;
     case BR_FLUX: wx = g.nx + 1; wy = g.ny + 1; wz = 2; break;
     case BR_INT: case BR_FR: case BR_FRA: wx = g.nx; wy = g.ny; break;
-    case BR_GX: wx = 8 * g.ny; wy = 1; break;
-    case BR_GY: wx = 8 * (g.nx + 2 * NG); wy = 1; break;
+    case BR_GHOST: wx = 8 * g.ny + 8 * (g.nx + 2 * NG); wy = 1; break;
     default: wx = (int)(12 * g.ps); wy = 1; break;  // BR_SPLIT
   }
 }
@@ -1552,9 +1544,8 @@ static void batch_enqueue_step(hweno_batch* b) {
     // of a case whose last accepted step wrote it (split_ok); the other cases' stage 1
     // splits its state (a case repeated after a rejected attempt, or set from outside)
     const int split = b->mixed && stage > 1;
-    kb_ghost<<<grid(BR_GX), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GX].tl(), n, which, 0, split);
-    kb_ghost<<<grid(BR_GY), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GY].tl(), n, which, 1, split);
-    b->launches += 2;
+    kb_ghost<<<grid(BR_GHOST), blk1, 0, b->st>>>(b->d_cases, b->L[BR_GHOST].tl(), n, which, split);
+    b->launches++;
     if (b->mixed) {
       if (stage == 1) {
         kb_split<<<grid(BR_SPLIT), blk1, 0, b->st>>>(b->d_cases, b->L[BR_SPLIT].tl(), n, which);
@@ -1622,8 +1613,7 @@ static void batch_enqueue_step(hweno_batch* b) {
 }
 
 static int batch_grids(hweno_batch* b) {
-  b->L[BR_GX].grid = persistent_grid(b, kb_ghost, b->L[BR_GX].total);
-  b->L[BR_GY].grid = persistent_grid(b, kb_ghost, b->L[BR_GY].total);
+  b->L[BR_GHOST].grid = persistent_grid(b, kb_ghost, b->L[BR_GHOST].total);
   b->L[BR_SPLIT].grid = persistent_grid(b, kb_split, b->L[BR_SPLIT].total);
   if (b->mixed) {
     b->L[BR_CONS].grid = persistent_grid(b, kb_cons<1>, b->L[BR_CONS].total);

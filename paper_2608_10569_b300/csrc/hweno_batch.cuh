@@ -215,20 +215,14 @@ __global__ void __launch_bounds__(FR_THREADS, HWENO_FR_MIN_BLOCKS) kb_flux_asm_m
   }
 }
 
-// ghost fill: 1D items, gx = element index (x pass: 8 ny, y pass: 8 (nx + 8)); with
-// split (or for a case whose split is current), also the kept planes of the state's
-// hi/lo split
-__global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int pass,
-                         int split) {
+// ghost fill, both passes in one launch (ghost_xy_body): 1D items, gx = element index (the
+// 8 ny x ghosts, then the 8 (nx + 8) y ghosts); with split (or for a case whose split is
+// current), also the kept planes of the state's hi/lo split
+__global__ void kb_ghost(const CaseDev* __restrict__ cases, TileList L, int ncase, int which, int split) {
   HW_BATCH_LOOP(L, ncase)
   double* q = which == 0 ? cd.Q : cd.QS;
-  if (pass == 0) ghost_x_body(cg, &cd.open, q, gx);
-  else ghost_y_body(cg, &cd.open, q, gx);
-  if (split || cd.split_ok) {
-    float* hilo = mixed_planes(cw, cg.ps).hilo;
-    if (pass == 0) ghost_x_body(cg, &cd.open, hilo, gx, 0, HILO_KEPT);
-    else ghost_y_body(cg, &cd.open, hilo, gx, 0, HILO_KEPT);
-  }
+  ghost_xy_body(cg, &cd.open, q, gx);
+  if (split || cd.split_ok) ghost_xy_body(cg, &cd.open, mixed_planes(cw, cg.ps).hilo, gx, 0, HILO_KEPT);
   HW_BATCH_END
 }
 

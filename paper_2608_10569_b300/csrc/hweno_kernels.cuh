@@ -105,15 +105,12 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // with hilo, blockIdx.y = 12..27 fills the 16 planes of the state's hi/lo split that are
 // kept (the 12 hi planes and the averages' 4 lo planes; the moments' lo parts are 0)
 constexpr int HILO_KEPT = 16;
-__global__ void k_ghost_x(Grid g, const __grid_constant__ Open o, double* q, float* hilo) {
+// both ghost passes in one launch (ghost_xy_body): threads 0 .. 8 ny - 1 the x ghosts,
+// the next 8 (nx + 8) the y ghosts
+__global__ void k_ghost(Grid g, const __grid_constant__ Open o, double* q, float* hilo) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
-  if (p < 12) ghost_x_body(g, &o, q, t, p, p + 1);
-  else ghost_x_body(g, &o, hilo, t, p - 12, p - 11);
-}
-__global__ void k_ghost_y(Grid g, const __grid_constant__ Open o, double* q, float* hilo) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
-  if (p < 12) ghost_y_body(g, &o, q, t, p, p + 1);
-  else ghost_y_body(g, &o, hilo, t, p - 12, p - 11);
+  if (p < 12) ghost_xy_body(g, &o, q, t, p, p + 1);
+  else ghost_xy_body(g, &o, hilo, t, p - 12, p - 11);
 }
 
 // ---------------------------------------------------------------------------

@@ -330,4 +330,55 @@ __host__ __device__ __forceinline__ void ghost_y_body(const Grid& g, const Open*
   }
 }
 
+// Both passes in one launch: thread t < 8 ny fills an x ghost as ghost_x_body does; the
+// others fill the y ghosts as ghost_y_body does, except that a corner's source cell,
+// an x ghost that the x pass writes in the same launch, is formed here by the x rule
+// instead of read (the same operations on the same interior value, so the result equals
+// the two passes' bit for bit).  The two parts write disjoint cells and read interior
+// cells only.
+template <class E>
+__host__ __device__ __forceinline__ void ghost_xy_body(const Grid& g, const Open* o, E* q, int t, int p0 = 0,
+                                                       int p1 = 12) {
+  if (t < 8 * g.ny) {
+    ghost_x_body(g, o, q, t, p0, p1);
+    return;
+  }
+  t -= 8 * g.ny;
+  const int W = g.nx + 2 * NG;
+  if (t >= 8 * W) return;
+  const int r = t / W, i = t % W - NG;
+  const int side = r / 4, k = r % 4;
+  const int j = side == 0 ? -1 - k : g.ny + k;
+  const int bc = g.bc[2 + side];
+  if (bc == HWENO_BC_INFLOW || (i >= 0 && i < g.nx)) {
+    ghost_y_body(g, o, q, t, p0, p1);
+    return;
+  }
+  // a corner: the y rule applied to the x rule's value at the source row js
+  const long long d = cidx(g, i, j);
+  const int js = ghost_src(bc, j, g.ny);
+  const int xside = i < 0 ? 0 : 1, bcx = g.bc[xside];
+  const bool mir = is_mirror(bc), mirx = is_mirror(bcx);
+  const double* st = nullptr;
+  if (bcx == HWENO_BC_INFLOW) {
+    if (!o) return;
+    st = inflow_state(*o, xside, centre(g.y0, js, g.dy));
+  }
+  const long long sx = bcx == HWENO_BC_INFLOW ? 0 : cidx(g, ghost_src(bcx, i, g.nx), js);
+  for (int p = p0; p < p1; p++) {
+    const int m = (p % 12) >> 2, v = p & 3;
+    E src;
+    if (st) {
+      src = (p % 12) < 4 ? E(open_value(st[p & 3], p, q)) : E(0);
+    } else {
+      E sgx = E(1);
+      if (mirx) sgx = E(bc_sign(bcx, 0, v) * (m == 1 ? -1.0 : 1.0));
+      src = sgx * q[p * g.ps + sx];
+    }
+    E sg = E(1);
+    if (mir) sg = E(bc_sign(bc, 1, v) * (m == 2 ? -1.0 : 1.0));
+    q[p * g.ps + d] = sg * src;
+  }
+}
+
 }  // namespace hw

@@ -1,5 +1,5 @@
 // Runs the 2D ghost-cell rules of hweno_state.cuh (the device code, compiled for the
-// host) over a whole state: the x pass over every thread index, then the y pass, on
+// host) over a whole state: the one-launch form ghost_xy_body over every thread index, on
 // the 12 FP64 planes and on the 24 float planes of their hi/lo split (split from the
 // interior, ghosts filled by the same passes).  Input: 6 ints (nx, ny, bc[4]), 44
 // doubles (x0, x1, y0, y1, inflow[4][2][4], band[4][2]), then q[12][ny][nx].  Output:
@@ -46,13 +46,12 @@ int main(int argc, char** argv) {
         q[p * g.ps + cidx(g, i, j)] = x;
         split_hilo(x, hilo[p * g.ps + cidx(g, i, j)], hilo[(12 + p) * g.ps + cidx(g, i, j)]);
       }
-  for (int t = 0; t < 8 * g.ny; t++) {
-    ghost_x_body(g, &o, q.data(), t);
-    ghost_x_body(g, &o, hilo.data(), t, 0, 24);
-  }
-  for (int t = 0; t < 8 * (g.nx + 2 * NG); t++) {
-    ghost_y_body(g, &o, q.data(), t);
-    ghost_y_body(g, &o, hilo.data(), t, 0, 24);
+  // the kernels' one-launch form: x ghosts and y ghosts by thread index, a corner formed
+  // from the x rule in place of reading the x pass's cell (the threads run in reverse
+  // order here, so no y thread can see an x ghost its x thread wrote first)
+  for (int t = 8 * g.ny + 8 * (g.nx + 2 * NG) - 1; t >= 0; t--) {
+    ghost_xy_body(g, &o, q.data(), t);
+    ghost_xy_body(g, &o, hilo.data(), t, 0, 24);
   }
   FILE* w = fopen(argv[2], "wb");
   if (!w) return 4;

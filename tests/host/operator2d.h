@@ -115,8 +115,7 @@ inline void mixed_front(const hweno_config& c, const Grid& g, Scratch& s, double
 // cell (the barrier between the two phases)
 inline void fused_stage(const hweno_config& c, const Grid& g, const Open& o, Scratch& s, double* q, double* mom,
                         double* base, double* qout, int stage, Diag* diag, bool tma) {
-  for (int k = 0; k < 8 * g.ny; k++) ghost_x_body(g, &o, q, k);
-  for (int k = 0; k < 8 * (g.nx + 2 * NG); k++) ghost_y_body(g, &o, q, k);
+  for (int k = 0; k < 8 * g.ny + 8 * (g.nx + 2 * NG); k++) ghost_xy_body(g, &o, q, k);  // k_ghost
   mixed_front(c, g, s, q, mom, diag, tma);
   const WorkF f = mixed_planes(s.w, g.ps);
   std::vector<float> hilo_out(24 * (size_t)g.ps);
@@ -164,8 +163,7 @@ inline void residual(const hweno_config& c, const Grid& g, const Open& o, const 
                      bool tiles = false) {
   const int nx = g.nx, ny = g.ny;
   Work& w = s.w;
-  for (int k = 0; k < 8 * ny; k++) ghost_x_body(g, &o, q, k);
-  for (int k = 0; k < 8 * (nx + 2 * NG); k++) ghost_y_body(g, &o, q, k);
+  for (int k = 0; k < 8 * ny + 8 * (nx + 2 * NG); k++) ghost_xy_body(g, &o, q, k);  // k_ghost
   if (mixed && tiles) {
     mixed_front(c, g, s, q, mom, diag, tma);
     flux_asm_tiles(g, s, rhs, diag);
