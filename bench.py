@@ -17,12 +17,12 @@ The metric is Gcell-RK-stage/s = cells x stages / seconds, summed over ranks.
   roofline  the dominant kernel's algorithmic FP64 flops per launch (the oracle's
             operation count per interior cell) / its mean event-timed duration,
             against the FP64 FMA peak measured live; the whole step on the same basis
-  adjoint   config 5: the gradient of a final-time misfit through 200 steps of the
+  adjoint   the gradient of a final-time misfit through 200 steps of the
             512^2 Taylor-Green flow, checkpoints every 20; backward / forward time and
             central differences on 16 seeded directions
-  ensemble  config 4: 64 Taylor-Green cases (sides 128-1024) in batched mixed steps,
+  ensemble  64 Taylor-Green cases (sides 128-1024) in batched mixed steps,
             with the worst case's error against FP64
-  colliding_streams  config 3: the 2048^2 near-vacuum colliding streams, FP64 and
+  colliding_streams  the 2048^2 near-vacuum colliding streams, FP64 and
             mixed
   cpu_baseline  the FP64 CPU oracle on the host cores, one SSP-RK3 step of the
             same workload (rank 0, N = 1 only)
@@ -732,10 +732,10 @@ def next_rows_child(args):
 
 
 def metric_children(args):
-    """the rest of the metric, each in a child process: config 5's adjoint (200 steps,
+    """the rest of the metric, each in a child process: the 512^2 adjoint (200 steps,
     checkpoints every 20, forward and backward times, central differences on 16 seeded
-    directions), config 4's ensemble (64 cases, 100 batched mixed steps, the worst case
-    against FP64) and config 3's colliding streams (2048^2)"""
+    directions), the ensemble (64 cases, 100 batched mixed steps, the worst case
+    against FP64) and the colliding streams (2048^2)"""
     return {
         "adjoint": child_line(["--workload", "adjoint", "--steps", "200", "--warmup", "2", "--fd-directions", "16",
                                "--fd-plain"], 420),
