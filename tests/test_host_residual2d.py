@@ -45,11 +45,8 @@ def exe(tmp_path_factory):
     return out
 
 
-def run(exe, tmp_path, p, q, t=0.0, mixed=False, dumps=False):
-    """(rhs, vhat, theta, alpha*, beta_max, limiter activations, flags) of the host run,
-    and with dumps the intermediate fields {0: face, 1: vol, 2: rm, 3: grad} as
-    hweno_debug_fields exports them"""
-    nx, ny = p["nx"], p["ny"]
+def write_header(f, p, t=0.0, mixed=False):
+    """the configuration record of host/operator2d.h (NaN-filled scratch)"""
     inflow = p.get("inflow") or (None,) * 4
     band = p.get("band") or (None,) * 4
     st = []
@@ -59,12 +56,20 @@ def run(exe, tmp_path, p, q, t=0.0, mixed=False, dumps=False):
     bd = []
     for k in range(4):
         bd += list(band[k]) if band[k] is not None else [0.0, 0.0]
+    f.write(struct.pack("11i", p["nx"], p["ny"], *[BC[b] for b in p["bc"]], 1 if p.get("scheme") == "dr" else 0,
+                        int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 1, 1 if mixed else 0))
+    f.write(struct.pack("50d", p["x0"], p["x1"], p["y0"], p["y1"], p["gamma"], p["Pr"], p["Re"],
+                        p.get("eps_pp", 1e-12), p.get("eps_weno", 1e-8), t, *st, *bd))
+
+
+def run(exe, tmp_path, p, q, t=0.0, mixed=False, dumps=False):
+    """(rhs, vhat, theta, alpha*, beta_max, limiter activations, flags) of the host run,
+    and with dumps the intermediate fields {0: face, 1: vol, 2: rm, 3: grad} as
+    hweno_debug_fields exports them"""
+    nx, ny = p["nx"], p["ny"]
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(fin, "wb") as f:
-        f.write(struct.pack("11i", nx, ny, *[BC[b] for b in p["bc"]], 1 if p.get("scheme") == "dr" else 0,
-                            int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 1, 1 if mixed else 0))
-        f.write(struct.pack("50d", p["x0"], p["x1"], p["y0"], p["y1"], p["gamma"], p["Pr"], p["Re"],
-                            p.get("eps_pp", 1e-12), p.get("eps_weno", 1e-8), t, *st, *bd))
+        write_header(f, p, t, mixed)
         f.write(np.ascontiguousarray(q, dtype=np.float64).tobytes())
     subprocess.check_call([exe, fin, fout])
     o = np.fromfile(fout, dtype=np.float64)
