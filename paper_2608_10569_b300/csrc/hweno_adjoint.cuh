@@ -1067,13 +1067,18 @@ __global__ void ka_finish(Grid g, const Adj a, const double* __restrict__ lam, d
   }
 }
 
-// bvec = alpha * bvec + beta * v  over the 12 planes (interior)
+// bvec = alpha * bvec + beta * v  over the 12 planes (interior); alpha = 0 overwrites
+// without reading bvec, whose old contents (a previous sweep's, possibly non-finite)
+// must not reach the result as 0 * inf or 0 * NaN
 __global__ void ka_axpby(Grid g, double* __restrict__ bvec, double alpha, const double* __restrict__ v, double beta) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const long long c = cidx(g, i, j);
-  for (int k = 0; k < 12; k++) bvec[(long long)k * g.ps + c] = alpha * bvec[(long long)k * g.ps + c] + beta * v[(long long)k * g.ps + c];
+  for (int k = 0; k < 12; k++) {
+    const double b = alpha == 0.0 ? 0.0 : alpha * bvec[(long long)k * g.ps + c];
+    bvec[(long long)k * g.ps + c] = b + beta * v[(long long)k * g.ps + c];
+  }
 }
 
 }  // namespace hw

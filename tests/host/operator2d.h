@@ -21,7 +21,7 @@ namespace host2d {
 using namespace hw;
 
 inline double nan_fill() {
-  const unsigned long long b = 0x7FC000007FC00000ull;
+  const unsigned long long b = 0x7FF800007FC00000ull;  // high half 0x7FF80000, low 0x7FC00000
   double f;
   memcpy(&f, &b, sizeof(f));
   return f;

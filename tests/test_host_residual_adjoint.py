@@ -1,18 +1,21 @@
-"""The reverse sweep of the spatial operator (the discrete adjoint of Eq. (3.2), with the
-PP limiter and the modified moments) run on the host, against the oracle's forward-mode
-(dual-number) tangents.
+"""The discrete adjoints of the spatial operator (Eq. (3.2), with the PP limiter and the
+modified moments) and of one SSP-RK3 step at a fixed dt, run on the host, against the
+oracle's forward-mode (dual-number) tangents.
 
-`host/residual_adjoint_host.cc` compiles the CUDA path's recording forward and its nine
-reverse kernels (`hweno_adjoint.cuh`) as plain C++ with `host/shim.h`, calls each over
-the index range of its launch, and starts every plane the sweep does not clear as NaN,
-under AddressSanitizer and UBSan where the compiler has them.  For seeds (rbar, mbar) and
-a tangent (v, dmu), <(rbar, mbar), J (v, dmu)> from the oracle's tangent must equal
-<xbar, v> + mubar dmu from the sweep: the GPU adjoint tests' dot products, with the same
-1e-10, here without the GPU's arithmetic and thread interleaving (which those tests
-cover).  The recording forward's residual must also be the oracle's.
+`host/residual_adjoint_host.cc` compiles the CUDA path's recording forward, its stage
+update and its reverse kernels (`hweno_adjoint.cuh`) as plain C++ with `host/shim.h`,
+calls each over the index range of its launch in the order of hweno_adjoint_residual or
+hweno_adjoint_step, and starts every plane that the sequence does not clear or seed as
+NaN, under AddressSanitizer and UBSan where the compiler has them.  For seeds (rbar,
+mbar) and a tangent (v, dmu), <(rbar, mbar), J (v, dmu)> from the oracle's tangent must
+equal <xbar, v> + mubar dmu from the sweep, and <lam', J_step v> must equal <lam, v> for
+the step: the GPU adjoint tests' dot products, with the same 1e-10, here without the
+GPU's arithmetic and thread interleaving (which those tests cover).  The recording
+forward's residual and step must also be the oracle's.
 """
 import os
 import shutil
+import struct
 import subprocess
 
 import numpy as np
@@ -38,18 +41,28 @@ def exe(tmp_path_factory):
     return out
 
 
-def sweep(exe, tmp_path, p, q, rbar, mbar):
-    """(xbar, mubar, rhs) of the host sweep"""
+def _run(exe, tmp_path, p, mode, dt, arrays):
     nx, ny = p["nx"], p["ny"]
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(fin, "wb") as f:
         write_header(f, p)
-        for a in (q, rbar, mbar):
+        f.write(struct.pack("=id", mode, dt))
+        for a in arrays:
             f.write(np.ascontiguousarray(a, dtype=np.float64).tobytes())
     subprocess.check_call([exe, fin, fout])
     o = np.fromfile(fout, dtype=np.float64)
     m = nx * ny
     return o[:12 * m].reshape(12, ny, nx), o[12 * m], o[12 * m + 1:24 * m + 1].reshape(12, ny, nx)
+
+
+def sweep(exe, tmp_path, p, q, rbar, mbar):
+    """(xbar, mubar, rhs) of the host sweep"""
+    return _run(exe, tmp_path, p, 0, 0.0, (q, rbar, mbar))
+
+
+def step_adjoint(exe, tmp_path, p, q, dt, lam_next):
+    """(lam, mubar, q_next) of the host step adjoint at the fixed dt"""
+    return _run(exe, tmp_path, p, 1, dt, (q, lam_next))
 
 
 def open_jet():
@@ -116,3 +129,23 @@ def test_a_wrong_seed_is_seen(exe, tmp_path):
     r2[5, 7, 3] += 1e-3
     xbar, _, _ = sweep(exe, tmp_path, p, q, r2, mbar)
     assert _rel(lhs, (xbar * v).sum()) > 1e-8
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_step_adjoint_is_the_transpose_of_the_oracle_tangent(exe, tmp_path, name):
+    case, q, extra = CASES[name]()
+    p = dict(case.params(), **extra)
+    cfg = O.make_cfg(**p)
+    dt = 0.25 * O.step(cfg, q)[1]["dt"]
+    rng = np.random.default_rng(83)
+    v = rng.normal(size=q.shape) * np.abs(q).reshape(12, -1).max(1)[:, None, None]
+    lam_next = rng.normal(size=q.shape)
+    lam, mub, q_next = step_adjoint(exe, tmp_path, p, q, dt, lam_next)
+    q_or, t, st = O.step_jvp(cfg, q, v, dt)
+    assert st["status"] == 0 and st["rejections"] == 0
+    scale = np.abs(q[:4]).reshape(4, -1).max(1)
+    err = max(np.abs(q_next[k] - q_or[k]).max() / max(np.abs(q_or[k]).max(), scale[k % 4]) for k in range(12))
+    assert err <= 1e-12, err
+    assert _rel((lam_next * t).sum(), (lam * v).sum()) <= 1e-10
+    _, tm, _ = O.step_jvp(cfg, q, np.zeros_like(q), dt, dmu=1.0)
+    assert _rel((lam_next * tm).sum(), mub) <= 1e-10
