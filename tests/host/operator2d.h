@@ -55,6 +55,7 @@ inline void grad_tma_emulated(const hweno_config& c, const Grid& g, const Work& 
     for (int bx = 0; bx < ntx; bx++) {
       const int a = -1 + GT_X * bx, b = -1 + GT_Y * by;
       const long long x0 = GT_X * bx, y0 = b - 2 + NG;
+      memset(sm.data(), 0xFF, sm.size() * sizeof(float));  // shared memory starts undefined: NaN
       auto fetch = [&](const float* plane, long long y, long long x) {
         return (x < g.pitch && y < rows) ? plane[y * g.pitch + x] : 0.0f;
       };
@@ -91,7 +92,12 @@ inline void mixed_front(const hweno_config& c, const Grid& g, Scratch& s, double
   Work& w = s.w;
   float* hilo = mixed_planes(w, g.ps).hilo;
   const long long np = 12 * g.ps;
-  for (long long k = 0; k < np; k++) split_hilo(q[k], hilo[k], hilo[np + k]);
+  for (long long k = 0; k < np; k++) {  // as k_split: the moments' lo planes stay unwritten
+    float hi, lo;
+    split_hilo(q[k], hi, lo);
+    hilo[k] = hi;
+    if (k < 4 * g.ps) hilo[np + k] = lo;
+  }
   for (int gy = 0; gy < ny + 6; gy++)
     for (int gx = 0; gx < nx + 6; gx++) cons_mixed_body(g, q, w, mom, diag, gx, gy);
   if (tma) {
@@ -123,6 +129,7 @@ inline void fused_stage(const hweno_config& c, const Grid& g, const Open& o, Scr
   for (int j0 = 0; j0 < g.ny; j0 += FR_TY)
     for (int i0 = 0; i0 < g.nx; i0 += FR_TX) {
       float amax = 0.f, bmax = 0.f;
+      memset(&ft, 0xFF, sizeof(ft));  // shared memory starts undefined: NaN
       for (int t = 0; t < FR_THREADS; t++) flux_tile_faces(g, f, i0, j0, t, ft, amax, bmax);
       for (int t = 0; t < FR_THREADS; t++) {
         double kef = 0.0;
@@ -140,6 +147,7 @@ inline void flux_asm_tiles(const Grid& g, Scratch& s, double* rhs, Diag* diag) {
   for (int j0 = 0; j0 < g.ny; j0 += FR_TY)
     for (int i0 = 0; i0 < g.nx; i0 += FR_TX) {
       float amax = 0.f, bmax = 0.f;
+      memset(&ft, 0xFF, sizeof(ft));  // shared memory starts undefined: NaN
       for (int t = 0; t < FR_THREADS; t++) flux_tile_faces(g, f, i0, j0, t, ft, amax, bmax);
       double a = amax, b = bmax;
       diag->alpha_bits = std::max(diag->alpha_bits, (unsigned long long)__double_as_longlong(a));

@@ -1,6 +1,8 @@
 // One evaluation of the 2D spatial operator with the CUDA path's own code compiled for
-// the host (operator2d.h): FP64 or the mixed path.  Input: the configuration record of
-// operator2d.h, then q[12][ny][nx].  Output (doubles): rhs[12][ny][nx], vhat[8][ny][nx],
+// the host (operator2d.h): FP64 or the mixed path (its separate kernels; with the record's
+// mixed mode 2 or 3 the flux tiles, and with 3 the TMA-staged gradients too).  Input: the
+// configuration record of operator2d.h, then q[12][ny][nx].  Output (doubles):
+// rhs[12][ny][nx], vhat[8][ny][nx],
 // theta[2][ny][nx], then alpha*, beta_max, limiter activations, flags, then the
 // intermediate fields as hweno_debug_fields exports them (FP64 path): the 12 face and 9
 // volume points as (rho, rho u, rho v, E), the 18 weak moments and the 126 gradients.
@@ -32,7 +34,7 @@ int main(int argc, char** argv) {
   for (int p = 0; p < 12; p++)
     for (int j = 0; j < ny; j++)
       for (int i = 0; i < nx; i++) q[p * g.ps + cidx(g, i, j)] = src[p * n + (size_t)j * nx + i];
-  residual(c, g, o, quad, s, q.data(), rhs.data(), mom.data(), &diag, in.t, in.mixed);
+  residual(c, g, o, quad, s, q.data(), rhs.data(), mom.data(), &diag, in.t, in.mixed, in.tma, in.fused);
 
   FILE* out = fopen(argv[2], "wb");
   if (!out) return 4;

@@ -57,7 +57,7 @@ def write_header(f, p, t=0.0, mixed=False):
     for k in range(4):
         bd += list(band[k]) if band[k] is not None else [0.0, 0.0]
     f.write(struct.pack("11i", p["nx"], p["ny"], *[BC[b] for b in p["bc"]], 1 if p.get("scheme") == "dr" else 0,
-                        int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 1, 1 if mixed else 0))
+                        int(p.get("source", 0)), 1 if p.get("linear_grad") else 0, 1, int(mixed)))
     f.write(struct.pack("50d", p["x0"], p["x1"], p["y0"], p["y1"], p["gamma"], p["Pr"], p["Re"],
                         p.get("eps_pp", 1e-12), p.get("eps_weno", 1e-8), t, *st, *bd))
 
@@ -178,16 +178,20 @@ def test_limiter_engaged(exe, tmp_path):
     assert pp == limited.sum()
 
 
+@pytest.mark.parametrize("kernels", ["separate", "tiles"])
 @pytest.mark.parametrize("linear_grad", [False, True])
 @pytest.mark.parametrize("name", ["smooth_periodic_64", "rough_walls_45x21", "shock_tube_64x32", "open_rough_40x36",
                                   "y_jet_33x29", "thin_grid_5x70"])
-def test_mixed_path(exe, tmp_path, name, linear_grad):
+def test_mixed_path(exe, tmp_path, name, linear_grad, kernels):
     """the mixed path's FP32 bodies on the hi/lo split of the ghost-filled state: within
     the mixed path's bounds of the FP64 oracle (1e-5 of the flux scale, 1e-6 of the state
-    for the modified moments), with inflow ghosts holding the split of their state"""
+    for the modified moments), with inflow ghosts holding the split of their state; with
+    the separate kernels, or as a handle runs them (the gradients as k_grad_tma_mixed
+    stages them, the fluxes and balances as k_flux_asm_mixed's tiles, each tile's shared
+    memory starting as NaN)"""
     case, q = CASES[name]()
     p = dict(case.params(), linear_grad=linear_grad)
-    rhs, vhat, theta, alpha, beta, pp, flags = run(exe, tmp_path, p, q, mixed=True)
+    rhs, vhat, theta, alpha, beta, pp, flags = run(exe, tmp_path, p, q, mixed=1 if kernels == "separate" else 3)
     o = O.residual(O.make_cfg(**p), q)
     assert rel_linf(rhs, o["rhs"], flux_scale(case, q)) <= 1e-5
     assert rel_linf(vhat, o["vhat"], state_scale(q)) <= 1e-6
