@@ -91,7 +91,7 @@ ALG_BYTES_PER_CELL_STAGE = 8 * ((12 + 20) + (12 + 12 + 20 + 12))
 # DRAM bytes of one cons_recon (k_cons<double>) launch on the 1024x512 shock tube,
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the current
 # k_cons; valid for that grid only
-K_CONS_TRAFFIC = {(1024, 512): 56465152 + 534104832}
+K_CONS_TRAFFIC = {(1024, 512): 56591616 + 533202688}
 
 
 def MEASURED_HBM_GBS():
