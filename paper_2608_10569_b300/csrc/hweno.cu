@@ -1428,7 +1428,6 @@ int hweno_adjoint_step(hweno_handle* h, const double* q, double dt, const double
 // kernel for all cases, one CUDA graph per SSP-RK3 step of the whole ensemble.
 
 namespace {
-enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GHOST, BR_SPLIT, BR_FR, BR_FRA, BR_GT, BR_N };
 
 struct BatchList {
   int bx = 32, by = 4;  // block shape of the kernels that use this list
@@ -1481,35 +1480,10 @@ static int bfail(hweno_batch* b, int code, const char* msg) {
     }                                                                           \
   } while (0)
 
-// launch-region extents (x, y, z) of list kind k for a grid
-static void region_of(int k, const Grid& g, int& wx, int& wy, int& wz) {
-  wz = 1;
-  switch (k) {
-    case BR_CONS: wx = g.nx + 6; wy = g.ny + 6; break;
-    case BR_FACE: wx = g.nx + 5; wy = g.ny + 5; wz = 2; break;
-    case BR_WEAK: wx = g.nx + 4; wy = g.ny + 4; break;
-    case BR_GRAD: case BR_GT: wx = g.nx + 2; wy = g.ny + 2; break;
-    case BR_FLUX: wx = g.nx + 1; wy = g.ny + 1; wz = 2; break;
-    case BR_INT: case BR_FR: case BR_FRA: wx = g.nx; wy = g.ny; break;
-    case BR_GHOST: wx = 8 * g.ny + 8 * (g.nx + 2 * NG); wy = 1; break;
-    default: wx = (int)(12 * g.ps); wy = 1; break;  // BR_SPLIT
-  }
-}
-
 static int build_list(hweno_batch* b, int k, int bx, int by) {
   BatchList& L = b->L[k];
   std::vector<int> host(3 * b->n + 1);
-  int total = 0;
-  for (int c = 0; c < b->n; c++) {
-    int wx, wy, wz;
-    region_of(k, b->h[c]->g, wx, wy, wz);
-    const int tx = (wx + bx - 1) / bx, ty = (wy + by - 1) / by;
-    host[c] = total;
-    host[b->n + 1 + c] = tx;
-    host[2 * b->n + 1 + c] = ty;
-    total += tx * ty * wz;
-  }
-  host[b->n] = total;
+  const int total = batch_layout(k, b->n, [&](int c) -> const Grid& { return b->h[c]->g; }, bx, by, host.data());
   L.n = b->n;
   L.bx = bx;
   L.by = by;

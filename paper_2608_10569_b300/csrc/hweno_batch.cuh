@@ -56,6 +56,45 @@ __device__ __forceinline__ void tile_pos(const TileList& L, int c, int t, int& g
   gy = by * blockDim.y + threadIdx.y;
 }
 
+// the batch's work lists, one per kind of launch region
+enum { BR_CONS = 0, BR_FACE, BR_WEAK, BR_GRAD, BR_FLUX, BR_INT, BR_GHOST, BR_SPLIT, BR_FR, BR_FRA, BR_GT, BR_N };
+
+// launch-region extents (x, y, z) of list kind k for a grid: those of the single-grid
+// kernel the kind stands for
+inline void batch_region(int k, const Grid& g, int& wx, int& wy, int& wz) {
+  wz = 1;
+  switch (k) {
+    case BR_CONS: wx = g.nx + 6; wy = g.ny + 6; break;
+    case BR_FACE: wx = g.nx + 5; wy = g.ny + 5; wz = 2; break;
+    case BR_WEAK: wx = g.nx + 4; wy = g.ny + 4; break;
+    case BR_GRAD: case BR_GT: wx = g.nx + 2; wy = g.ny + 2; break;
+    case BR_FLUX: wx = g.nx + 1; wy = g.ny + 1; wz = 2; break;
+    case BR_INT: case BR_FR: case BR_FRA: wx = g.nx; wy = g.ny; break;
+    case BR_GHOST: wx = 8 * g.ny + 8 * (g.nx + 2 * NG); wy = 1; break;
+    default: wx = (int)(12 * g.ps); wy = 1; break;  // BR_SPLIT
+  }
+}
+
+// the work list of kind k over n cases with bx x by tiles, as TileList reads it:
+// out[c] the first item of case c and out[n] the total, out[n + 1 + c] and
+// out[2n + 1 + c] the case's tiles across and down (3n + 1 ints); grid_of(c) gives
+// case c's grid.  Returns the total.
+template <class GridOf>
+inline int batch_layout(int k, int n, GridOf grid_of, int bx, int by, int* out) {
+  int total = 0;
+  for (int c = 0; c < n; c++) {
+    int wx, wy, wz;
+    batch_region(k, grid_of(c), wx, wy, wz);
+    const int tx = (wx + bx - 1) / bx, ty = (wy + by - 1) / by;
+    out[c] = total;
+    out[n + 1 + c] = tx;
+    out[2 * n + 1 + c] = ty;
+    total += tx * ty * wz;
+  }
+  out[n] = total;
+  return total;
+}
+
 #define HW_BATCH_LOOP(L, ncase)                                   \
   const int total_ = (L).start[ncase];                             \
   for (int t_ = blockIdx.x; t_ < total_; t_ += gridDim.x) {        \
