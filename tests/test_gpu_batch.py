@@ -165,6 +165,41 @@ def test_mixed_batch_restarts_only_the_rejected_case():
     b.close()
 
 
+def test_mixed_batch_beyond_the_tensor_map_limit():
+    """A mixed batch of more cases than its kernel parameter holds tensor maps for (64)
+    runs its face moments, weak moments and gradients in the separate work-list kernels,
+    whose block shapes the autotuner then picks: 65 small cases of mixed sizes and
+    faces, two steps after tuning, each within four times its mixed handle's own
+    distance from the FP64 handle of that handle's state"""
+    bcs = [("periodic",) * 4, ("noslip", "noslip", "noslip", "symmetry"), ("slip", "symmetry", "periodic", "periodic")]
+    cases = [I.random_smooth(8 + k % 7, 6 + (3 * k) % 9, seed=200 + k, bc=bcs[k % 3]) for k in range(65)]
+    stream = torch.cuda.Stream()
+    b = hweno.Batch([c.params() for c, _ in cases], precision="mixed", stream=stream)
+    for view, (_, q) in zip(b.cases, cases):
+        view.set_state(q.copy())
+    chosen = b.autotune()
+    assert chosen[4] == -1 and all(0 <= chosen[k] < 4 for k in (0, 1, 2, 3, 5))
+    assert b.step(2) == 0
+    worst = 0.0
+    for view, (case, q) in zip(b.cases, cases):
+        out = {}
+        for prec in ("mixed", "fp64"):
+            s = hweno.Solver(case.params(), precision=prec, stream=stream)
+            s.set_state(q.copy())
+            for _ in range(2):
+                s.step()
+            out[prec] = s.get_state(np.zeros_like(q))
+            s.close()
+        got = view.get_state(np.zeros_like(q))
+        assert view.diag()["steps"] == 2
+        err = mixed_distance(got, out["mixed"], q)
+        bound = mixed_distance(out["mixed"], out["fp64"], q)
+        worst = max(worst, err / max(bound, 1e-300))
+        assert err <= max(4 * bound, 1e-14), (case.name, err, bound)
+    print("worst batch-against-handle distance over the handle's distance from FP64: %.2f" % worst)
+    b.close()
+
+
 def test_ensemble_case_against_the_oracle_at_full_length():
     """The 64-case ensemble's first 128^2 case, stepped by the batch for its 100 steps
     in FP64 and in mixed precision, against the FP64 oracle run at the batch's step
