@@ -141,3 +141,47 @@ def test_source_batch_matches_handles_and_the_oracle():
         err = max(np.abs(got[j] - ref[j]).max() / max(np.abs(ref[j]).max(), scale[j % 4]) for j in range(12))
         assert err <= 1e-13, (k, err)
     b.close()
+
+
+def test_mixed_source_batch_matches_mixed_handles():
+    """Example 5.2's source in a mixed batch, whose stages 2 and 3 then keep their
+    residual (the flux tiles' balances, the source, then the stage update) instead of
+    the fused stage kernel: three steps from t = 0.02 of two source cases and one
+    without, each within four times its mixed handle's own distance from the FP64
+    handle"""
+    t0 = 0.02
+    c1, q1 = I.manufactured(24, t0)
+    c2 = I.Case("manufactured_shifted_20", 20, 20, 0.3, 1.3, -0.4, 0.6, 1.4, 0.72, 100.0, source=1)
+    q2 = I.cell_moments(c2, lambda x, y: I.manufactured_prim(x, y, t0, c2.gamma))
+    c3, q3 = I.random_smooth(16, 16, seed=1)
+    cases = [(c1, q1), (c2, q2), (c3, q3)]
+    stream = torch.cuda.Stream()
+    b = hweno.Batch([c.params() for c, _ in cases], precision="mixed", stream=stream)
+    for k, (_, q) in enumerate(cases):
+        b.cases[k].set_state(q.copy())
+        b.cases[k].set_time(t0)
+    b.step(3)
+
+    def handle(case, q, prec):
+        s = hweno.Solver(case.params(), precision=prec, stream=stream)
+        s.set_state(q.copy())
+        s.set_time(t0)
+        for _ in range(3):
+            s.step()
+        out = s.get_state().cpu().numpy()
+        s.close()
+        return out
+
+    def distance(a, r, q):
+        scale = np.abs(q[:4]).reshape(4, -1).max(1)
+        return max(np.abs(a[j] - r[j]).max() / max(np.abs(r[j]).max(), scale[j % 4]) for j in range(12))
+
+    for k, (case, q) in enumerate(cases):
+        ref = handle(case, q, "mixed")
+        got = b.cases[k].get_state(np.zeros_like(q))
+        assert b.cases[k].diag()["steps"] == 3
+        err = distance(got, ref, q)
+        bound = max(4 * distance(ref, handle(case, q, "fp64"), q), 1e-14)
+        print("case %d: batch against handle %.2e, bound %.2e" % (k, err, bound))
+        assert err <= bound, (k, err, bound)
+    b.close()
