@@ -265,3 +265,17 @@ def test_batch_cases_share_the_restart_cap(lib):
     cfgs = (hweno.hweno_config * 2)(hweno.make_config(8, 8, max_halvings=20), hweno.make_config(8, 8))
     assert lib.hweno_batch_init(cfgs, 2, None, ctypes.byref(b)) == hweno.HWENO_ERR_ARG
     assert b.value is None and b"max_halvings" in lib.hweno_last_error(None)
+
+
+def test_noalloc_grid_limit_is_checked_before_any_device_call(lib):
+    """hweno_residual_noalloc's static scratch holds (ny + 8) * round_up(nx + 8, 16) <= 4096
+    padded cells per plane (56 x 56 fills it): 57 x 56 (64 * 80), 56 x 57 (65 * 64),
+    400 x 4 (12 * 416) and 4 x 4089 are refused on the host, before any device call,
+    with the sizes in the message"""
+    from paper_2608_10569_b300 import hweno
+    buf = (ctypes.c_double * 12)()
+    for nx, ny in ((57, 56), (56, 57), (400, 4), (4, 4089)):
+        c = hweno.make_config(nx, ny)
+        assert lib.hweno_residual_noalloc(ctypes.byref(c), buf, buf, None, None) == hweno.HWENO_ERR_ARG
+        msg = lib.hweno_last_error(None)
+        assert b"padded cells" in msg and (b"%d x %d" % (nx, ny)) in msg
